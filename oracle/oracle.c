@@ -1,0 +1,407 @@
+/*
+ * FP64 reference state-vector simulator -- TEST INFRASTRUCTURE ONLY.
+ *
+ * This file is the oracle that the CUDA library is checked against.  It is
+ * written for a reader who wants to compare it with the paper by eye: every
+ * gate is applied with a plain loop over the whole amplitude array, Pauli
+ * strings are applied factor by factor to a copy, and gradients come from the
+ * textbook adjoint sweep.  There is no blocking, fusion or reordering.  Only
+ * tests, the package smoke check and the benchmark's CPU-baseline leg may
+ * load it; the product path never does.
+ *
+ * Passages followed (DeepQuantum, arXiv 2512.18995):
+ *   - Sec. "Quantum Computing with Qubits", Background: single-qubit basis
+ *     |0>, |1> as Z eigenstates and the Bloch form cos(t/2)|0> +
+ *     e^{i p} sin(t/2)|1>, and the evolution |psi_n> = U_n ... U_1 |psi_0>.
+ *   - Same section, API Overview: circuits built by appending gates, forward
+ *     execution, expectation values of observables given as Pauli strings.
+ *   - Sec. "Large-Scale Simulations", Distributed Simulations: gradients of
+ *     expectations with respect to trainable parameters and encoded inputs by
+ *     the adjoint differentiation method (Jones & Gacon, arXiv:2009.02823).
+ *   - Sec. "Simulation of Large Quantum Systems with MPS" (Trotterised TFIM
+ *     with rx(-h dt), rzz(-2 J dt)): rotations are R_P(t) = exp(-i t P / 2).
+ *   - Sec. "Distributed Quantum Fourier Transform": controlled phase
+ *     CP(phi) = diag(1, 1, 1, e^{i phi}), Hadamard, SWAP.
+ *
+ * Readings where the paper is silent (also listed in the design notes):
+ *   - wire 0 is the most significant bit of the amplitude index:
+ *       index = sum_q b_q 2^(n-1-q).
+ *   - RZ(t) = diag(e^{-i t/2}, e^{i t/2}) (the exp(-i t Z / 2) form).
+ *   - a Pauli term carries bit q of xmask/zmask for wire q; both bits = Y.
+ *
+ * Parity: pinned (closed forms, brute-force dense products, parameter-shift
+ * and finite differences in the test-suite).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+/* Gate codes of the oracle (independent of the library's own enum). */
+enum {
+    O_H = 0, O_X, O_Y, O_Z, O_S,
+    O_RX, O_RY, O_RZ,
+    O_CNOT, O_CZ, O_CP, O_SWAP,
+    O_CRX, O_CRY, O_CRZ,
+    O_NKINDS
+};
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gate matrices.                                                             */
+/* ------------------------------------------------------------------------ */
+
+/* 2x2 matrix m = [[m0, m1], [m2, m3]] acting on the target qubit.  For a
+ * controlled gate this is the block applied when the control is |1>.
+ * Rotations follow R_P(t) = cos(t/2) I - i sin(t/2) P, which is exp(-i t P/2)
+ * because P^2 = I. */
+static void target_matrix(int kind, double t, cplx m[4])
+{
+    const double c = cos(0.5 * t), s = sin(0.5 * t);
+    const double r = 1.0 / sqrt(2.0);
+    switch (kind) {
+    case O_H:    m[0] = r;  m[1] = r;   m[2] = r;  m[3] = -r;  break;
+    case O_X:
+    case O_CNOT: m[0] = 0;  m[1] = 1;   m[2] = 1;  m[3] = 0;   break;
+    case O_Y:    m[0] = 0;  m[1] = -I;  m[2] = I;  m[3] = 0;   break;
+    case O_Z:
+    case O_CZ:   m[0] = 1;  m[1] = 0;   m[2] = 0;  m[3] = -1;  break;
+    case O_S:    m[0] = 1;  m[1] = 0;   m[2] = 0;  m[3] = I;   break;
+    case O_RX:
+    case O_CRX:  m[0] = c;  m[1] = -I * s; m[2] = -I * s; m[3] = c; break;
+    case O_RY:
+    case O_CRY:  m[0] = c;  m[1] = -s;  m[2] = s;  m[3] = c;   break;
+    case O_RZ:
+    case O_CRZ:  m[0] = c - I * s; m[1] = 0; m[2] = 0; m[3] = c + I * s; break;
+    case O_CP:   m[0] = 1;  m[1] = 0;   m[2] = 0;  m[3] = cexp(I * t); break;
+    default:     m[0] = 1;  m[1] = 0;   m[2] = 0;  m[3] = 1;   break;
+    }
+}
+
+/* Generator G with U(t) = exp(-i t G) for the parametric gates, as a 2x2
+ * block on the target (restricted to the control = |1> subspace for
+ * controlled gates).  d/dt U = -i G U. */
+static void generator_matrix(int kind, cplx g[4])
+{
+    g[0] = g[1] = g[2] = g[3] = 0;
+    switch (kind) {
+    case O_RX: case O_CRX: g[1] = 0.5;       g[2] = 0.5;      break;  /* X/2 */
+    case O_RY: case O_CRY: g[1] = -0.5 * I;  g[2] = 0.5 * I;  break;  /* Y/2 */
+    case O_RZ: case O_CRZ: g[0] = 0.5;       g[3] = -0.5;     break;  /* Z/2 */
+    case O_CP:             g[3] = -1.0;                        break;  /* CP = exp(i t |11><11|) */
+    default: break;
+    }
+}
+
+static int is_parametric(int kind)
+{
+    return kind == O_RX || kind == O_RY || kind == O_RZ || kind == O_CP ||
+           kind == O_CRX || kind == O_CRY || kind == O_CRZ;
+}
+
+static int is_controlled(int kind)
+{
+    return kind == O_CNOT || kind == O_CZ || kind == O_CP ||
+           kind == O_CRX || kind == O_CRY || kind == O_CRZ;
+}
+
+/* Bit position of wire q: wire 0 is the most significant bit. */
+static inline int bitpos(int n, int q) { return n - 1 - q; }
+
+/* ------------------------------------------------------------------------ */
+/* Plain per-gate application over the whole array.                          */
+/* ------------------------------------------------------------------------ */
+
+/* Apply 2x2 block m to the target wire, on the amplitudes whose control wire
+ * is |1> (ctrl < 0: no control). */
+static void apply_block(int n, cplx *psi, int target, int ctrl, const cplx m[4])
+{
+    const int64_t dim = (int64_t)1 << n;
+    const int64_t tb = (int64_t)1 << bitpos(n, target);
+    const int64_t cb = ctrl >= 0 ? ((int64_t)1 << bitpos(n, ctrl)) : 0;
+#pragma omp parallel for schedule(static) if (dim >= (1 << 16))
+    for (int64_t i = 0; i < dim; ++i) {
+        if (i & tb) continue;                 /* visit each pair once */
+        if (cb && !(i & cb)) continue;        /* control must be |1> */
+        const int64_t j = i | tb;
+        const cplx a = psi[i], b = psi[j];
+        psi[i] = m[0] * a + m[1] * b;
+        psi[j] = m[2] * a + m[3] * b;
+    }
+}
+
+static void apply_swap(int n, cplx *psi, int qa, int qb)
+{
+    const int64_t dim = (int64_t)1 << n;
+    const int64_t ba = (int64_t)1 << bitpos(n, qa);
+    const int64_t bb = (int64_t)1 << bitpos(n, qb);
+#pragma omp parallel for schedule(static) if (dim >= (1 << 16))
+    for (int64_t i = 0; i < dim; ++i) {
+        if ((i & ba) && !(i & bb)) {          /* |..1..0..> <-> |..0..1..> */
+            const int64_t j = (i & ~ba) | bb;
+            const cplx t = psi[i];
+            psi[i] = psi[j];
+            psi[j] = t;
+        }
+    }
+}
+
+/* Angle of gate g for batch row `row`. */
+static double gate_angle(int g, const int *pidx, const int *didx, const double *angle,
+                         const double *params, int nparams, int params_per_row,
+                         const double *data, int nfeat, int row)
+{
+    if (pidx[g] >= 0)
+        return params_per_row ? params[(int64_t)row * nparams + pidx[g]] : params[pidx[g]];
+    if (didx[g] >= 0)
+        return data[(int64_t)row * nfeat + didx[g]];
+    return angle[g];
+}
+
+static void conj_transpose(const cplx m[4], cplx d[4])
+{
+    d[0] = conj(m[0]); d[1] = conj(m[2]); d[2] = conj(m[1]); d[3] = conj(m[3]);
+}
+
+/* Apply gate g (or its inverse when `dagger`). */
+static void apply_gate(int n, cplx *psi, int kind, int w0, int w1, double t, int dagger)
+{
+    if (kind == O_SWAP) {
+        apply_swap(n, psi, w0, w1);
+        return;
+    }
+    cplx m[4], d[4];
+    target_matrix(kind, t, m);
+    if (dagger) {
+        conj_transpose(m, d);
+        memcpy(m, d, sizeof(m));
+    }
+    if (is_controlled(kind))
+        apply_block(n, psi, w1, w0, m);
+    else
+        apply_block(n, psi, w0, -1, m);
+}
+
+/* Single-row forward run from |0...0>. */
+static void run_row(int n, int ngates, const int *kind, const int *w0, const int *w1,
+                    const int *pidx, const int *didx, const double *angle,
+                    const double *params, int nparams, int params_per_row,
+                    const double *data, int nfeat, int row, cplx *psi)
+{
+    const int64_t dim = (int64_t)1 << n;
+    for (int64_t i = 0; i < dim; ++i) psi[i] = 0;
+    psi[0] = 1;
+    for (int g = 0; g < ngates; ++g) {
+        const double t = gate_angle(g, pidx, didx, angle, params, nparams, params_per_row,
+                                    data, nfeat, row);
+        apply_gate(n, psi, kind[g], w0[g], w1[g], t, 0);
+    }
+}
+
+/* Apply one Pauli string (masks by wire) factor by factor. */
+static void apply_pauli(int n, cplx *v, uint64_t xmask, uint64_t zmask)
+{
+    for (int q = 0; q < n; ++q) {
+        const int x = (int)((xmask >> q) & 1), z = (int)((zmask >> q) & 1);
+        if (!x && !z) continue;
+        const int kind = (x && z) ? O_Y : (x ? O_X : O_Z);
+        cplx m[4];
+        target_matrix(kind, 0.0, m);
+        apply_block(n, v, q, -1, m);
+    }
+}
+
+static cplx inner(int64_t dim, const cplx *a, const cplx *b)  /* <a|b> */
+{
+    cplx s = 0;
+    for (int64_t i = 0; i < dim; ++i) s += conj(a[i]) * b[i];
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported API.                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Gate matrix for checking against independent definitions (2x2 target block
+ * for one-qubit and controlled kinds). */
+void oracle_gate_block(int kind, double t, double *out8)
+{
+    cplx m[4];
+    target_matrix(kind, t, m);
+    for (int i = 0; i < 4; ++i) { out8[2 * i] = creal(m[i]); out8[2 * i + 1] = cimag(m[i]); }
+}
+
+/* Apply a gate list to `batch` given states in place (used for unitarity and
+ * dense-matrix checks, where the input is not |0...0>). */
+void oracle_apply(int n, int ngates, const int *kind, const int *w0, const int *w1,
+                  const int *pidx, const int *didx, const double *angle,
+                  const double *params, int nparams, int params_per_row,
+                  const double *data, int nfeat, int batch, int dagger, double *states_ri)
+{
+    const int64_t dim = (int64_t)1 << n;
+    cplx *states = (cplx *)states_ri;
+#pragma omp parallel for schedule(dynamic, 1) if (batch > 1)
+    for (int r = 0; r < batch; ++r) {
+        cplx *psi = states + (int64_t)r * dim;
+        if (!dagger) {
+            for (int g = 0; g < ngates; ++g) {
+                const double t = gate_angle(g, pidx, didx, angle, params, nparams,
+                                            params_per_row, data, nfeat, r);
+                apply_gate(n, psi, kind[g], w0[g], w1[g], t, 0);
+            }
+        } else {
+            for (int g = ngates - 1; g >= 0; --g) {
+                const double t = gate_angle(g, pidx, didx, angle, params, nparams,
+                                            params_per_row, data, nfeat, r);
+                apply_gate(n, psi, kind[g], w0[g], w1[g], t, 1);
+            }
+        }
+    }
+}
+
+/* |psi_row> = U_G ... U_1 |0...0> for every batch row. */
+void oracle_run(int n, int ngates, const int *kind, const int *w0, const int *w1,
+                const int *pidx, const int *didx, const double *angle,
+                const double *params, int nparams, int params_per_row,
+                const double *data, int nfeat, int batch, double *states_ri)
+{
+    const int64_t dim = (int64_t)1 << n;
+    cplx *states = (cplx *)states_ri;
+#pragma omp parallel for schedule(dynamic, 1) if (batch > 1)
+    for (int r = 0; r < batch; ++r)
+        run_row(n, ngates, kind, w0, w1, pidx, didx, angle, params, nparams,
+                params_per_row, data, nfeat, r, states + (int64_t)r * dim);
+}
+
+/* out[row*nobs + o] = sum_{k in obs o} coeff_k Re <psi_row| P_k |psi_row>. */
+void oracle_expect(int n, const double *coeff, const uint64_t *xmask, const uint64_t *zmask,
+                   const int *term_offsets, int nobs, int batch, const double *states_ri,
+                   double *out)
+{
+    const int64_t dim = (int64_t)1 << n;
+    const cplx *states = (const cplx *)states_ri;
+#pragma omp parallel for schedule(dynamic, 1) if (batch > 1)
+    for (int r = 0; r < batch; ++r) {
+        const cplx *psi = states + (int64_t)r * dim;
+        cplx *tmp = (cplx *)malloc((size_t)dim * sizeof(cplx));
+        for (int o = 0; o < nobs; ++o) {
+            double acc = 0.0;
+            for (int k = term_offsets[o]; k < term_offsets[o + 1]; ++k) {
+                memcpy(tmp, psi, (size_t)dim * sizeof(cplx));
+                apply_pauli(n, tmp, xmask[k], zmask[k]);
+                acc += coeff[k] * creal(inner(dim, psi, tmp));
+            }
+            out[(int64_t)r * nobs + o] = acc;
+        }
+        free(tmp);
+    }
+}
+
+/*
+ * Adjoint differentiation (Jones & Gacon 2020) of
+ *     L = sum_row sum_o w[row, o] * E[row, o],
+ * with E[row, o] = <psi_row| O_o |psi_row> and w = row_weights (NULL = 1).
+ *
+ *   psi <- U_G ... U_1 |0>,   lambda <- (sum_o w_o O_o) psi
+ *   for j = G .. 1:
+ *       if gate j has an angle t_j = exp(-i t G_j):
+ *           dL/dt_j += 2 Im <lambda | G_j | psi>
+ *       psi <- U_j^dagger psi,  lambda <- U_j^dagger lambda
+ *
+ * The derivative is routed to the trainable parameter (summed over rows when
+ * params are shared, per row when params_per_row) or to the encoded feature
+ * (per row).  expect_out (batch x nobs) receives E.
+ */
+void oracle_adjoint(int n, int ngates, const int *kind, const int *w0, const int *w1,
+                    const int *pidx, const int *didx, const double *angle,
+                    const double *params, int nparams, int params_per_row,
+                    const double *data, int nfeat, int batch,
+                    const double *coeff, const uint64_t *xmask, const uint64_t *zmask,
+                    const int *term_offsets, int nobs, const double *row_weights,
+                    double *expect_out, double *grad_params, double *grad_data)
+{
+    const int64_t dim = (int64_t)1 << n;
+    const int gp_rows = params_per_row ? batch : 1;
+    double *gp_row = (double *)calloc((size_t)batch * (nparams > 0 ? nparams : 1), sizeof(double));
+
+#pragma omp parallel for schedule(dynamic, 1) if (batch > 1)
+    for (int r = 0; r < batch; ++r) {
+        cplx *psi = (cplx *)malloc((size_t)dim * sizeof(cplx));
+        cplx *lam = (cplx *)calloc((size_t)dim, sizeof(cplx));
+        cplx *tmp = (cplx *)malloc((size_t)dim * sizeof(cplx));
+        double *gp = gp_row + (int64_t)r * (nparams > 0 ? nparams : 1);
+
+        run_row(n, ngates, kind, w0, w1, pidx, didx, angle, params, nparams,
+                params_per_row, data, nfeat, r, psi);
+
+        /* expectations and lambda = sum_o w_o O_o psi */
+        for (int o = 0; o < nobs; ++o) {
+            const double w = row_weights ? row_weights[(int64_t)r * nobs + o] : 1.0;
+            double acc = 0.0;
+            for (int k = term_offsets[o]; k < term_offsets[o + 1]; ++k) {
+                memcpy(tmp, psi, (size_t)dim * sizeof(cplx));
+                apply_pauli(n, tmp, xmask[k], zmask[k]);
+                acc += coeff[k] * creal(inner(dim, psi, tmp));
+                for (int64_t i = 0; i < dim; ++i) lam[i] += w * coeff[k] * tmp[i];
+            }
+            if (expect_out) expect_out[(int64_t)r * nobs + o] = acc;
+        }
+        if (grad_data)
+            for (int f = 0; f < nfeat; ++f) grad_data[(int64_t)r * nfeat + f] = 0.0;
+
+        for (int g = ngates - 1; g >= 0; --g) {
+            const double t = gate_angle(g, pidx, didx, angle, params, nparams,
+                                        params_per_row, data, nfeat, r);
+            if (is_parametric(kind[g]) && (pidx[g] >= 0 || didx[g] >= 0)) {
+                cplx gm[4];
+                generator_matrix(kind[g], gm);
+                memcpy(tmp, psi, (size_t)dim * sizeof(cplx));
+                if (is_controlled(kind[g])) {
+                    /* generator lives on the control=|1> subspace */
+                    const int64_t cb = (int64_t)1 << bitpos(n, w0[g]);
+                    for (int64_t i = 0; i < dim; ++i)
+                        if (!(i & cb)) tmp[i] = 0;
+                    apply_block(n, tmp, w1[g], w0[g], gm);
+                } else {
+                    apply_block(n, tmp, w0[g], -1, gm);
+                }
+                const double d = 2.0 * cimag(inner(dim, lam, tmp));
+                if (pidx[g] >= 0) gp[pidx[g]] += d;
+                else if (grad_data) grad_data[(int64_t)r * nfeat + didx[g]] += d;
+            }
+            apply_gate(n, psi, kind[g], w0[g], w1[g], t, 1);
+            apply_gate(n, lam, kind[g], w0[g], w1[g], t, 1);
+        }
+        free(psi);
+        free(lam);
+        free(tmp);
+    }
+
+    if (grad_params && nparams > 0) {
+        if (params_per_row) {
+            memcpy(grad_params, gp_row, (size_t)batch * nparams * sizeof(double));
+        } else {
+            for (int p = 0; p < nparams; ++p) {
+                double s = 0.0;
+                for (int r = 0; r < batch; ++r) s += gp_row[(int64_t)r * nparams + p];
+                grad_params[p] = s;
+            }
+        }
+    }
+    (void)gp_rows;
+    free(gp_row);
+}

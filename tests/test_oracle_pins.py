@@ -1,0 +1,359 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle.
+
+Each check compares the oracle with something fixed by the paper or by the
+mathematics: gate matrices as exponentials of their generators (rotations are
+exp(-i t P / 2), the convention the paper's Trotterised TFIM example relies
+on), closed forms (Bell/GHZ amplitudes, the QFT of a basis state equals the
+DFT, <Z> of RY(t)|0> = cos t from the Bloch form), brute-force dense
+Kronecker products for n <= 6, unitarity and norm invariants, and gradients by
+the exact parameter-shift rule and by central finite differences.  The last
+test compiles deliberately mutated copies of the oracle and checks that the
+pins reject every one of them.
+"""
+import math
+import os
+import re
+import shutil
+import tempfile
+
+import numpy as np
+import pytest
+
+import workloads as W
+from workloads import Gate
+from tests import dense_reference as D
+
+RNG = np.random.default_rng(1234)
+
+
+def random_gates(n, depth, rng, nparams_box, data_features=0, kinds=None):
+    """Random gate list over every kind; parameters each used once."""
+    kinds = kinds or W.GATE_KINDS
+    gates = []
+    np_ = 0
+    for _ in range(depth):
+        k = kinds[rng.integers(len(kinds))]
+        if k in W.TWO_QUBIT:
+            if n < 2:
+                continue
+            a, b = rng.choice(n, size=2, replace=False)
+            wires = (int(a), int(b))
+        else:
+            wires = (int(rng.integers(n)),)
+        if k in W.PARAMETRIC:
+            if data_features and rng.random() < 0.3:
+                gates.append(Gate(k, wires, data=int(rng.integers(data_features))))
+            elif rng.random() < 0.15:
+                gates.append(Gate(k, wires, angle=float(rng.uniform(-4, 4))))
+            else:
+                gates.append(Gate(k, wires, param=np_))
+                np_ += 1
+        else:
+            gates.append(Gate(k, wires))
+    nparams_box.append(np_)
+    return gates
+
+
+# ---------------------------------------------------------------------------
+# pin suite shared with the mutation check
+# ---------------------------------------------------------------------------
+def pin_failures(oracle, lib=None):
+    """Run quick pins; return the names of those that fail."""
+    bad = []
+
+    def check(name, ok):
+        if not ok:
+            bad.append(name)
+
+    # gate blocks = exponentials of generators / textbook matrices
+    for kind in ("h", "x", "y", "z", "s", "rx", "ry", "rz"):
+        for t in (0.0, 0.3, -1.7, 2.9):
+            got = oracle.gate_block(kind, t, lib=lib)
+            check(f"block-{kind}", np.allclose(got, D.one_qubit(kind, t), atol=1e-14))
+    # closed forms: Bell, GHZ
+    st = oracle.run(2, [Gate("h", (0,)), Gate("cnot", (0, 1))], lib=lib)[0]
+    bell = np.zeros(4, complex)
+    bell[0] = bell[3] = 1 / math.sqrt(2)
+    check("bell", np.allclose(st, bell, atol=1e-15))
+    # Bloch: RZ(phi) RY(theta)|0> = e^{-i phi/2}(cos t/2|0> + e^{i phi} sin t/2 |1>)
+    th, ph = 1.1, 0.7
+    st = oracle.run(1, [Gate("ry", (0,), angle=th), Gate("rz", (0,), angle=ph)], lib=lib)[0]
+    ref = np.exp(-0.5j * ph) * np.array([math.cos(th / 2), np.exp(1j * ph) * math.sin(th / 2)])
+    check("bloch", np.allclose(st, ref, atol=1e-15))
+    # wire order + every kind against dense products (n = 3, 4)
+    rng = np.random.default_rng(7)
+    for n in (3, 4):
+        box = []
+        gates = random_gates(n, 40, rng, box)
+        params = rng.uniform(-3, 3, size=max(box[0], 1))
+        got = oracle.run(n, gates, params, lib=lib)[0]
+        ref = D.circuit_operator(n, gates, params)[:, 0]
+        check(f"dense-{n}", np.allclose(got, ref, atol=1e-12))
+    # QFT of basis states = DFT
+    n = 4
+    N = 1 << n
+    basis = np.eye(N, dtype=complex)
+    got = oracle.apply(n, W.qft_gates(n), basis, lib=lib)
+    F = np.exp(2j * np.pi * np.outer(np.arange(N), np.arange(N)) / N) / math.sqrt(N)
+    check("qft", np.allclose(got, F.T, atol=1e-12))
+    # expectation with Y terms against dense
+    n = 3
+    psi = rng.normal(size=N // 2) + 1j * rng.normal(size=N // 2)
+    psi /= np.linalg.norm(psi)
+    terms = [(0.7, 0b101, 0b001), (-1.3, 0b010, 0b110), (0.4, 0, 0b011)]
+    got = oracle.expect(n, psi[None], [terms], lib=lib)[0, 0]
+    ref = np.real(np.vdot(psi, D.observable_operator(n, terms) @ psi))
+    check("expect", abs(got - ref) < 1e-13)
+    # adjoint gradient vs central differences (all parametric kinds)
+    n = 3
+    box = []
+    gates = random_gates(n, 30, rng, box, kinds=("h", "rx", "ry", "rz", "cnot", "cp",
+                                                  "crx", "cry", "crz", "swap", "cz"))
+    params = rng.uniform(-3, 3, size=max(box[0], 1))
+    obs = [[(1.0, 0, 0b001), (0.5, 0b010, 0)]]
+    _, gp, _ = oracle.adjoint(n, gates, obs, params, lib=lib)
+    fd = np.zeros_like(params)
+    h = 1e-5
+    for p in range(params.size):
+        e = np.zeros_like(params)
+        e[p] = h
+        fp = oracle.expect(n, oracle.run(n, gates, params + e, lib=lib), obs, lib=lib)[0, 0]
+        fm = oracle.expect(n, oracle.run(n, gates, params - e, lib=lib), obs, lib=lib)[0, 0]
+        fd[p] = (fp - fm) / (2 * h)
+    check("adjoint-fd", np.allclose(gp, fd, atol=1e-8))
+    return bad
+
+
+def test_pin_suite_passes(oracle_mod):
+    assert pin_failures(oracle_mod) == []
+
+
+# ---------------------------------------------------------------------------
+# individual pins, larger
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["h", "x", "y", "z", "s", "rx", "ry", "rz"])
+def test_one_qubit_blocks_unitary_and_match_definition(oracle_mod, kind):
+    for t in np.linspace(-7, 7, 15):
+        U = oracle_mod.gate_block(kind, t)
+        np.testing.assert_allclose(U.conj().T @ U, np.eye(2), atol=1e-15)
+        np.testing.assert_allclose(U, D.one_qubit(kind, t), atol=1e-14)
+
+
+@pytest.mark.parametrize("n", range(2, 11))
+def test_ghz(oracle_mod, n):
+    gates = [Gate("h", (0,))] + [Gate("cnot", (q, q + 1)) for q in range(n - 1)]
+    st = oracle_mod.run(n, gates)[0]
+    ref = np.zeros(1 << n, complex)
+    ref[0] = ref[-1] = 1 / math.sqrt(2)
+    np.testing.assert_allclose(st, ref, atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 6, 8])
+def test_qft_of_basis_states_is_dft(oracle_mod, n):
+    """QFT|x> = N^{-1/2} sum_y exp(2 pi i x y / N) |y> (paper's QFT gate order,
+    with the final swaps)."""
+    N = 1 << n
+    xs = range(N) if n <= 6 else [0, 1, 77, 128, 255]
+    basis = np.zeros((len(xs), N), complex)
+    for r, x in enumerate(xs):
+        basis[r, x] = 1
+    got = oracle_mod.apply(n, W.qft_gates(n), basis)
+    y = np.arange(N)
+    for r, x in enumerate(xs):
+        ref = np.exp(2j * np.pi * x * y / N) / math.sqrt(N)
+        np.testing.assert_allclose(got[r], ref, atol=1e-13)
+
+
+def test_ry_expectation_closed_form(oracle_mod):
+    """<Z> of RY(t)|0> = cos t and d<Z>/dt = -sin t (Bloch form)."""
+    for t in np.linspace(-6, 6, 25):
+        exp, gp, _ = oracle_mod.adjoint(1, [Gate("ry", (0,), param=0)], [W.obs_z(0)],
+                                        np.array([t]))
+        assert abs(exp[0, 0] - math.cos(t)) < 1e-14
+        assert abs(gp[0] + math.sin(t)) < 1e-14
+
+
+def test_cnot_equals_h_cz_h(oracle_mod):
+    """CNOT = (I x H) CZ (I x H) (identity used in the dual-rail CNOT section)."""
+    n = 2
+    basis = np.eye(4, dtype=complex)
+    a = oracle_mod.apply(n, [Gate("cnot", (0, 1))], basis)
+    b = oracle_mod.apply(n, [Gate("h", (1,)), Gate("cz", (0, 1)), Gate("h", (1,))], basis)
+    np.testing.assert_allclose(a, b, atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
+def test_random_circuits_match_dense_products(oracle_mod, n):
+    rng = np.random.default_rng(100 + n)
+    for trial in range(3):
+        box = []
+        gates = random_gates(n, 12 * n + 5, rng, box, data_features=3)
+        params = rng.uniform(-4, 4, size=max(box[0], 1))
+        data = rng.uniform(-3, 3, size=(2, 3))
+        U0 = D.circuit_operator(n, gates, params, data[0])
+        U1 = D.circuit_operator(n, gates, params, data[1])
+        st = oracle_mod.run(n, gates, params, data, batch=2)
+        np.testing.assert_allclose(st[0], U0[:, 0], atol=1e-12)
+        np.testing.assert_allclose(st[1], U1[:, 0], atol=1e-12)
+        # arbitrary input states, and the inverse sweep
+        psi = rng.normal(size=(2, 1 << n)) + 1j * rng.normal(size=(2, 1 << n))
+        out = oracle_mod.apply(n, gates, psi, params, data)
+        np.testing.assert_allclose(out[0], U0 @ psi[0], atol=1e-11)
+        np.testing.assert_allclose(out[1], U1 @ psi[1], atol=1e-11)
+        back = oracle_mod.apply(n, gates, out, params, data, dagger=True)
+        np.testing.assert_allclose(back, psi, atol=1e-11)
+
+
+def test_norm_preserved_after_every_gate(oracle_mod):
+    n = 12
+    rng = np.random.default_rng(5)
+    box = []
+    gates = random_gates(n, 60, rng, box)
+    params = rng.uniform(-4, 4, size=max(box[0], 1))
+    psi = oracle_mod.run(n, [], None)[0]
+    for g in gates:
+        psi = oracle_mod.apply(n, [g], psi, params)[0]
+        assert abs(np.linalg.norm(psi) - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("n", [2, 3, 5])
+def test_expectation_matches_dense(oracle_mod, n):
+    rng = np.random.default_rng(n)
+    N = 1 << n
+    psi = rng.normal(size=(3, N)) + 1j * rng.normal(size=(3, N))
+    psi /= np.linalg.norm(psi, axis=1, keepdims=True)
+    obs = []
+    for _ in range(3):
+        terms = [(float(rng.normal()), int(rng.integers(N)), int(rng.integers(N))) for _ in range(4)]
+        obs.append(terms)
+    got = oracle_mod.expect(n, psi, obs)
+    for r in range(3):
+        for o, terms in enumerate(obs):
+            ref = np.real(np.vdot(psi[r], D.observable_operator(n, terms) @ psi[r]))
+            assert abs(got[r, o] - ref) < 1e-13
+
+
+def test_adjoint_matches_parameter_shift(oracle_mod):
+    """Two-term shift rule, exact for RX/RY/RZ: d f = [f(t+pi/2) - f(t-pi/2)]/2."""
+    n = 5
+    rng = np.random.default_rng(11)
+    box = []
+    gates = random_gates(n, 50, rng, box, kinds=("h", "rx", "ry", "rz", "cnot", "cz", "swap"))
+    gates = [g if g.param >= 0 or g.kind not in W.PARAMETRIC else g._replace(angle=0.4) for g in gates]
+    params = rng.uniform(0, 2 * math.pi, size=box[0])
+    obs = [W.obs_tfim_open(n, 0.5)]
+    _, gp, _ = oracle_mod.adjoint(n, gates, obs, params)
+    for p in range(params.size):
+        e = np.zeros_like(params)
+        e[p] = math.pi / 2
+        fp = oracle_mod.expect(n, oracle_mod.run(n, gates, params + e), obs)[0, 0]
+        fm = oracle_mod.expect(n, oracle_mod.run(n, gates, params - e), obs)[0, 0]
+        assert abs(gp[p] - 0.5 * (fp - fm)) < 1e-12
+
+
+def test_adjoint_matches_finite_differences_everything(oracle_mod):
+    """Controlled rotations, CP, encoded data, several observables, row
+    weights, shared and per-row parameters against central differences."""
+    n = 4
+    batch = 3
+    rng = np.random.default_rng(21)
+    box = []
+    gates = random_gates(n, 45, rng, box, data_features=2)
+    nparams = max(box[0], 1)
+    obs = [W.obs_tfim_open(n, 0.5), [(0.3, 0b0110, 0b0010), (1.0, 0, 0b1001)]]
+    data = rng.uniform(-3, 3, size=(batch, 2))
+    w = rng.normal(size=(batch, 2))
+    h = 1e-5
+
+    def loss(params, data, ppr):
+        st = oracle_mod.run(n, gates, params, data, batch=batch, params_per_row=ppr)
+        return float(np.sum(w * oracle_mod.expect(n, st, obs)))
+
+    for ppr in (False, True):
+        params = rng.uniform(-3, 3, size=(batch, nparams) if ppr else nparams)
+        exp, gp, gd = oracle_mod.adjoint(n, gates, obs, params, data, batch=batch,
+                                         params_per_row=ppr, row_weights=w)
+        st = oracle_mod.run(n, gates, params, data, batch=batch, params_per_row=ppr)
+        np.testing.assert_allclose(exp, oracle_mod.expect(n, st, obs), atol=1e-14)
+        flat = params.reshape(-1)
+        for i in range(flat.size):
+            e = np.zeros_like(flat)
+            e[i] = h
+            fd = (loss((flat + e).reshape(params.shape), data, ppr)
+                  - loss((flat - e).reshape(params.shape), data, ppr)) / (2 * h)
+            assert abs(gp.reshape(-1)[i] - fd) < 1e-7, (ppr, i)
+        for i in range(data.size):
+            e = np.zeros(data.size)
+            e[i] = h
+            fd = (loss(params, (data.reshape(-1) + e).reshape(data.shape), ppr)
+                  - loss(params, (data.reshape(-1) - e).reshape(data.shape), ppr)) / (2 * h)
+            assert abs(gd.reshape(-1)[i] - fd) < 1e-7
+
+
+def test_distributed_example_four_qubits(oracle_mod):
+    """The paper's minimal distributed example: data = arange(4) encoded by an
+    RY layer, a CNOT ring, observables Z_0 and X_1, loss = their sum, gradient
+    with respect to the data -- checked against dense products and central
+    differences."""
+    n = 4
+    gates = W.encode_layer(n) + [Gate("cnot", (q, (q + 1) % n)) for q in range(n)]
+    data = np.arange(4, dtype=np.float64)[None]
+    obs = [W.obs_z(0), [W.pauli_term(1.0, {1: "X"})]]
+    exp, _, gd = oracle_mod.adjoint(n, gates, obs, None, data)
+    U = D.circuit_operator(n, gates, None, data[0])
+    psi = U[:, 0]
+    for o, terms in enumerate(obs):
+        ref = np.real(np.vdot(psi, D.observable_operator(n, terms) @ psi))
+        assert abs(exp[0, o] - ref) < 1e-13
+    h = 1e-6
+    for f in range(4):
+        e = np.zeros((1, 4))
+        e[0, f] = h
+        fp = oracle_mod.expect(n, oracle_mod.run(n, gates, None, data + e), obs).sum()
+        fm = oracle_mod.expect(n, oracle_mod.run(n, gates, None, data - e), obs).sum()
+        assert abs(gd[0, f] - (fp - fm) / (2 * h)) < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# planted mistakes: each mutant of the oracle must fail at least one pin
+# ---------------------------------------------------------------------------
+MUTANTS = {
+    "rx-sign": ("case O_CRX:  m[0] = c;  m[1] = -I * s; m[2] = -I * s;",
+                "case O_CRX:  m[0] = c;  m[1] = I * s; m[2] = I * s;"),
+    "ry-transposed": ("case O_CRY:  m[0] = c;  m[1] = -s;  m[2] = s;",
+                      "case O_CRY:  m[0] = c;  m[1] = s;  m[2] = -s;"),
+    "full-angle": ("const double c = cos(0.5 * t), s = sin(0.5 * t);",
+                   "const double c = cos(t), s = sin(t);"),
+    "lsb-wire-order": ("static inline int bitpos(int n, int q) { return n - 1 - q; }",
+                       "static inline int bitpos(int n, int q) { (void)n; return q; }"),
+    "cp-phase-sign": ("case O_CP:   m[0] = 1;  m[1] = 0;   m[2] = 0;  m[3] = cexp(I * t);",
+                      "case O_CP:   m[0] = 1;  m[1] = 0;   m[2] = 0;  m[3] = cexp(-I * t);"),
+    "grad-factor": ("const double d = 2.0 * cimag(inner(dim, lam, tmp));",
+                    "const double d = cimag(inner(dim, lam, tmp));"),
+    "generator-sign": ("case O_RZ: case O_CRZ: g[0] = 0.5;       g[3] = -0.5;",
+                       "case O_RZ: case O_CRZ: g[0] = -0.5;       g[3] = 0.5;"),
+    "y-pauli-sign": ("case O_Y:    m[0] = 0;  m[1] = -I;  m[2] = I;",
+                     "case O_Y:    m[0] = 0;  m[1] = I;  m[2] = -I;"),
+    "swap-dropped": ("            psi[j] = t;\n",
+                     "            psi[j] = psi[i];\n"),
+    "hadamard-sign": ("case O_H:    m[0] = r;  m[1] = r;   m[2] = r;  m[3] = -r;",
+                      "case O_H:    m[0] = r;  m[1] = r;   m[2] = r;  m[3] = r;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_planted_mistake(oracle_mod, name):
+    src_path = os.path.join(os.path.dirname(oracle_mod.__file__), "oracle.c")
+    src = open(src_path).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    tmpdir = tempfile.mkdtemp(prefix="oracle_mutant_")
+    try:
+        mpath = os.path.join(tmpdir, "oracle_mutant.c")
+        with open(mpath, "w") as f:
+            f.write(src.replace(old, new))
+        so = oracle_mod.compile_source(mpath, os.path.join(tmpdir, f"lib_{re.sub('[^a-z]', '_', name)}.so"))
+        lib = oracle_mod.load_library(so)
+        assert pin_failures(oracle_mod, lib=lib), f"mutant {name} passed every pin"
+    finally:
+        shutil.rmtree(tmpdir, ignore_errors=True)
