@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 state-vector hot path; prints ONE JSON line.
+
+Workload (one step): the 20-qubit hardware-efficient ansatz, 8 layers of
+per-qubit RY, RZ and a CNOT ring (480 gates, 320 parameters), complex64,
+batch 1: state preparation, evolution and the expectation of sum_i Z_i.
+value = gate-equivalent amplitude throughput: every gate counts the bytes of
+one full read+write sweep of the state (2 * 2^n * 8 bytes), whatever the
+implementation actually moves, divided by the device time of the step.  L2 is
+flushed (a 512 MiB write) between timed steps.
+
+Extra objects on the line: the dominant kernel's roofline, the CPU oracle
+baseline, the end-to-end figure through the public API with host buffers,
+SM clocks sampled during the timed region, the HBM-bound single-gate sweep at
+30 qubits, and fused vs plain batched forward+adjoint gradients (12 qubits x
+4096 samples).
+
+--impl reference runs the FP64 CPU oracle on the same workload and prints the
+same line with "impl": "reference".
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "amplitude-GB/s vs HBM peak; batched fwd+adjoint grads/s vs plain path at 1e-4"
+UNIT = "GB/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def gate_pass_bytes(n, gates, amp=8):
+    """Gate-equivalent bytes: one full read+write sweep per gate."""
+    return len(gates) * 2 * (1 << n) * amp
+
+
+def touched_bytes(n, g, amp=8):
+    """Bytes the per-gate sweep kernel must move for one gate."""
+    full = 2 * (1 << n) * amp
+    if g.kind in ("cnot", "cz", "cp", "crx", "cry", "crz"):
+        return full // 2
+    return full
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_rate(wl, budget_s, max_steps=None):
+    """Gate-equivalent GB/s of the oracle on the workload: full forward +
+    expectation steps, as many as fit the time budget (at least one)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    st = oracle.run(wl.n, wl.gates, wl.params)
+    oracle.expect(wl.n, st, wl.observables)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    steps = max(1, int(budget_s / max(per, 1e-6)))
+    if max_steps:
+        steps = min(steps, max_steps)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = oracle.run(wl.n, wl.gates, wl.params)
+        oracle.expect(wl.n, st, wl.observables)
+    dt = time.perf_counter() - t0
+    rate = gate_pass_bytes(wl.n, wl.gates) * steps / dt / 1e9
+    return rate, steps, dt, oracle.num_threads()
+
+
+def reference_arm(args, rank, world):
+    """The oracle on the host cores, as the reference arm."""
+    if rank != 0:
+        return
+    wl = W.config_c2()
+    import oracle
+    oracle.build()
+    # bounded steps: each step is a full forward + expectation when K*W fits
+    # ~3 minutes, else a prefix of the gate list (the unit stays per gate).
+    t0 = time.perf_counter()
+    st = oracle.run(wl.n, wl.gates, wl.params)
+    oracle.expect(wl.n, st, wl.observables)
+    full = time.perf_counter() - t0
+    total_steps = args.steps + args.warmup
+    frac = min(1.0, 180.0 / max(total_steps * full, 1e-9))
+    ng = max(1, int(len(wl.gates) * frac))
+    gates = wl.gates[:ng]
+    for _ in range(args.warmup):
+        s = oracle.run(wl.n, gates, wl.params)
+        oracle.expect(wl.n, s, wl.observables)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s = oracle.run(wl.n, gates, wl.params)
+        oracle.expect(wl.n, s, wl.observables)
+    dt = time.perf_counter() - t0
+    value = gate_pass_bytes(wl.n, gates) * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
+        "data": "synthetic",
+        "config": {"workload": "c2_hea20_c64", "nqubits": 20, "layers": 8, "gates": len(wl.gates),
+                   "params": wl.nparams, "batch": 1, "gates_per_step": ng},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} steps of the first {ng} of {len(wl.gates)} gates + <sum Z>"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def our_arm(args, rank, world, dist):
+    import torch
+    import paper_2512_18995_gb300 as dq
+    from paper_2512_18995_gb300 import build as dqbuild
+
+    dqbuild.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device(f"cuda:{local}")
+    ctx = dq.Context(local, path={"auto": dq.PATH_AUTO, "plain": dq.PATH_PLAIN, "fused": dq.PATH_FUSED}[args.path])
+    hbm_peak, peak_kind = peaks()
+
+    wl = W.config_c2()
+    n = wl.n
+    circ = dq.Circuit(n, wl.gates, nparams=wl.nparams)
+    obs = dq.Observables(wl.observables)
+    params = torch.tensor(wl.params, dtype=torch.float64, device=device)
+    state = torch.empty((1, 1 << n), dtype=torch.complex64, device=device)
+    expect = torch.empty((1, 1), dtype=torch.float64, device=device)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
+    if args.path != "plain":
+        ctx.plan_autotune(circ, state)
+
+    def step():
+        ctx.forward_grad(circ, params, obs, 1, torch.complex64, want_grad=False, state_out=state, expect_out=expect)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    launches0 = ctx.launch_count
+    with ClockSampler(local) as clk:
+        barrier()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record()
+            step()
+            ends[i].record()
+        barrier()
+    launches = ctx.launch_count - launches0
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    bytes_step = gate_pass_bytes(n, wl.gates)
+    value = world * bytes_step * args.steps / (ms / 1e3) / 1e9
+    clocks = clk.summary()
+
+    # per-kernel device time (a traced repetition of the same timed steps)
+    ctx.set_tracing(True)
+    for i in range(args.steps):
+        flush.zero_()
+        step()
+    trace = ctx.trace()
+    ctx.set_tracing(False)
+    top = max(trace.items(), key=lambda kv: kv[1][1])
+    kname, (klaunch, kms) = top
+    # algorithmic bytes of the dominant kernel per step
+    if kname == "k_sweep":
+        kbytes = sum(touched_bytes(n, g) for g in wl.gates if g.kind != "swap") * args.steps
+    elif kname.startswith("k_tile"):
+        kbytes = ctx_tile_bytes(ctx, n, klaunch)
+    else:
+        kbytes = 2 * (1 << n) * 8 * klaunch
+    achieved = kbytes / (kms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                "launches": klaunch // args.steps, "avg_launch_us": 1e3 * kms / klaunch,
+                "note": "20-qubit state (8 MiB) is L2-resident within a step"}
+
+    # end to end through the public API with host buffers
+    host_params = torch.tensor(wl.params, dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        p_dev = host_params.to(device, non_blocking=True)
+        e, _, _, _ = ctx.forward_grad(circ, p_dev, obs, 1, torch.complex64, want_grad=False, state_out=state)
+        _ = e.cpu()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * bytes_step * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(host_params.numel() * 8), "d2h_bytes_per_step": 8}
+
+    extras = {}
+    if not args.no_extras:
+        extras["hbm_sweep"] = hbm_sweep(ctx, device, hbm_peak, peak_kind)
+        extras["grads"] = batched_grads(ctx, device)
+        ctx.set_path({"auto": dq.PATH_AUTO, "plain": dq.PATH_PLAIN, "fused": dq.PATH_FUSED}[args.path])
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            rate, steps, dt, cores = oracle_rate(wl, budget_s=args.cpu_budget)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{steps} full steps (480-gate forward + <sum Z>) in {dt:.1f} s"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "c2_hea20_c64", "nqubits": n, "layers": 8, "gates": len(wl.gates),
+                       "params": wl.nparams, "batch": 1, "path": args.path,
+                       "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def ctx_tile_bytes(ctx, n, launches):
+    # each fused tile pass reads and writes the whole state once
+    return 2 * (1 << n) * 8 * launches
+
+
+def hbm_sweep(ctx, device, hbm_peak, peak_kind, n=30, reps=3):
+    """Single one-qubit gate sweeps on an 8 GiB state (far beyond L2)."""
+    import torch
+    import paper_2512_18995_gb300 as dq
+    ctx.set_path(dq.PATH_PLAIN)
+    try:
+        state = torch.empty((1, 1 << n), dtype=torch.complex64, device=device)
+    except RuntimeError:
+        return None
+    ctx.state_init(state, n)
+    targets = [0, 1, 3, 7, 12, 18, 24, 29]
+    gates = [W.Gate("ry", (q,), angle=0.3 + 0.01 * q) for q in targets]
+    circ = dq.Circuit(n, gates)
+    ctx.apply_circuit(circ, None, state)
+    torch.cuda.synchronize()
+    ctx.set_tracing(True)
+    for _ in range(reps):
+        ctx.apply_circuit(circ, None, state)
+    tr = ctx.trace()
+    ctx.set_tracing(False)
+    cnt, tot = tr["k_sweep"]
+    per_ms = tot / cnt
+    gbs = 2 * (1 << n) * 8 / (per_ms / 1e3) / 1e9
+    del state
+    torch.cuda.empty_cache()
+    return {"n": n, "kernel": "k_sweep", "launches": cnt, "avg_launch_ms": per_ms, "GB/s": gbs,
+            "peak": hbm_peak, "frac": gbs / hbm_peak, "peak_kind": peak_kind, "targets": targets}
+
+
+def batched_grads(ctx, device, steps=5):
+    """12 qubits x 4096 encoded samples, 6 layers (144 shared params):
+    forward + adjoint gradient, fused path vs plain per-gate path."""
+    import torch
+    import paper_2512_18995_gb300 as dq
+    wl = W.config_c3()
+    circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams, nfeatures=wl.nfeatures)
+    obs = dq.Observables(wl.observables)
+    params = torch.tensor(wl.params, device=device)
+    data = torch.tensor(wl.data, device=device)
+    out = {}
+    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+        ctx.set_path(path)
+        for _ in range(2):
+            ctx.forward_grad(circ, params, obs, wl.batch, torch.complex64, data=data)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            ctx.forward_grad(circ, params, obs, wl.batch, torch.complex64, data=data)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out[name] = {"ms_per_step": ms, "grads_per_s": wl.batch * wl.nparams / (ms / 1e3)}
+    out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
+    out["workload"] = "c3_qml12x4096_c64"
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--path", choices=["auto", "plain", "fused"], default="auto")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend="nccl")
+    our_arm(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

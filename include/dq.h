@@ -1,0 +1,264 @@
+/*
+ * dq.h -- C ABI of libdq, a batched state-vector simulator for parameterised
+ * qubit circuits on NVIDIA GB300 (sm_103a).
+ *
+ * The library computes, on the GPU, what the qubit-circuit backend of
+ * DeepQuantum (arXiv 2512.18995) computes: the evolution of a batch of pure
+ * states |psi_n> = U_n ... U_1 |psi_0> (Sec. "Quantum Computing with Qubits",
+ * Background), expectation values of observables given as (weighted sums of)
+ * Pauli strings (same section, API Overview: observable()/expectation()), and
+ * gradients of those expectations with respect to trainable parameters and
+ * encoded inputs by adjoint differentiation (Sec. "Distributed Simulations":
+ * a custom autograd function using the adjoint method).
+ *
+ * Conventions
+ *   - Wire q of an n-qubit register is bit (n-1-q) of the amplitude index:
+ *     wire 0 is the most significant bit.
+ *   - Rotations are R_P(t) = exp(-i t P / 2) for P in {X, Y, Z}; RZ(t) =
+ *     diag(e^{-it/2}, e^{it/2}).  CP(t) = diag(1, 1, 1, e^{it}) (the
+ *     controlled phase of Sec. "Distributed Quantum Fourier Transform").
+ *     Controlled rotations apply R_P(t) to the target when the control is |1>.
+ *   - A state batch is `batch` contiguous rows of 2^n amplitudes.  DQ_C64
+ *     amplitudes are interleaved float pairs (re, im), 8 bytes; DQ_C128 are
+ *     interleaved double pairs, 16 bytes.  Row r starts at element r * 2^n.
+ *     State pointers must be 16-byte aligned.
+ *   - Angles: gate g uses params[g.param_idx] (or params[row * nparams +
+ *     g.param_idx] when params_per_row != 0) when param_idx >= 0, else
+ *     data[row * nfeatures + g.data_idx] when data_idx >= 0 (an encoded input
+ *     feature), else the fixed g.angle.  params and data are FP64.
+ *
+ * Ownership and streams
+ *   - All device buffers (states, params, data, outputs) are allocated and
+ *     freed by the caller; the library never frees caller memory.  Host
+ *     arrays (gate lists, Pauli terms, offsets) are only read during the call.
+ *   - Scratch memory comes from the context's workspace: attach one with
+ *     dq_ctx_set_workspace (size from dq_workspace_bytes); otherwise the
+ *     context grows its own device workspace with cudaMalloc on first need.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every compute call is asynchronous on that stream.
+ *
+ * Errors
+ *   Every call returns a dq_status.  Arguments are validated on the host
+ *   before any launch (DQ_ERR_INVALID_ARG, nothing launched); CUDA failures
+ *   return DQ_ERR_CUDA.  Device-side bounded waits that give up record
+ *   DQ_ERR_TIMEOUT in the context, reported by dq_ctx_check.  A
+ *   human-readable message for the last failure is in dq_last_error.  The
+ *   library never aborts the process and throws nothing across the ABI.
+ */
+#ifndef DQ_H_INCLUDED
+#define DQ_H_INCLUDED
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DQ_API __attribute__((visibility("default")))
+#else
+#define DQ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dq_status {
+    DQ_OK = 0,
+    DQ_ERR_INVALID_ARG = 1,
+    DQ_ERR_UNSUPPORTED = 2,
+    DQ_ERR_OOM = 3,
+    DQ_ERR_CUDA = 4,
+    DQ_ERR_TIMEOUT = 5
+} dq_status;
+
+typedef enum dq_dtype { DQ_C64 = 0, DQ_C128 = 1 } dq_dtype;
+
+/* Gate kinds.  One-qubit kinds use wires[0] as the target.  Controlled kinds
+ * use wires[0] as the control and wires[1] as the target.  SWAP exchanges
+ * wires[0] and wires[1].  Parametric kinds: RX RY RZ CP CRX CRY CRZ. */
+typedef enum dq_gate_kind {
+    DQ_H = 0, DQ_X, DQ_Y, DQ_Z, DQ_S,
+    DQ_RX, DQ_RY, DQ_RZ,
+    DQ_CNOT, DQ_CZ, DQ_CP, DQ_SWAP,
+    DQ_CRX, DQ_CRY, DQ_CRZ,
+    DQ_NUM_GATE_KINDS
+} dq_gate_kind;
+
+/* Which implementation runs the circuit.
+ *   DQ_PATH_PLAIN: one kernel launch per gate (and per adjoint step), each a
+ *                  full sweep over the batch -- the paper's gate-by-gate
+ *                  evolution, kept as the baseline.
+ *   DQ_PATH_FUSED: whole states in shared memory for small n, otherwise
+ *                  k-qubit tiles staged in shared memory by TMA with many
+ *                  gates applied per HBM pass.
+ *   DQ_PATH_AUTO:  fused where supported (default). */
+typedef enum dq_path { DQ_PATH_AUTO = 0, DQ_PATH_PLAIN = 1, DQ_PATH_FUSED = 2 } dq_path;
+
+typedef struct dq_gate {
+    int32_t kind;        /* dq_gate_kind */
+    int32_t wires[2];    /* see dq_gate_kind; wires[1] unused for 1-qubit kinds */
+    int32_t param_idx;   /* >= 0: trainable parameter index, else -1 */
+    int32_t data_idx;    /* >= 0: encoded feature index, else -1 */
+    int32_t reserved;    /* must be 0 */
+    double angle;        /* fixed angle when param_idx < 0 and data_idx < 0 */
+} dq_gate;
+
+typedef struct dq_circuit {
+    int32_t nqubits;       /* 1 .. 34 */
+    int32_t ngates;        /* >= 0 */
+    const dq_gate *gates;  /* host array of ngates */
+    int32_t nparams;       /* number of trainable parameters (per row if per-row) */
+    int32_t nfeatures;     /* encoded features per row (0 if none) */
+} dq_circuit;
+
+/* One Pauli string with a real weight.  Bit q of xmask / zmask refers to wire
+ * q: X only -> X, Z only -> Z, both -> Y. */
+typedef struct dq_pauli_term {
+    double coeff;
+    uint64_t xmask;
+    uint64_t zmask;
+} dq_pauli_term;
+
+/* nobs observables; observable o is sum_{k in [term_offsets[o],
+ * term_offsets[o+1])} terms[k].coeff * P_k.  Host arrays. */
+typedef struct dq_observables {
+    int32_t nobs;
+    const int32_t *term_offsets;   /* nobs + 1 entries, non-decreasing, [0] = 0 */
+    const dq_pauli_term *terms;
+} dq_observables;
+
+typedef struct dq_ctx dq_ctx;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (made current for the calls of
+ * this context).  *out receives the handle.  Holds plan caches and the
+ * workspace; not thread-safe: use one context per host thread. */
+DQ_API dq_status dq_ctx_create(dq_ctx **out, int device);
+
+/* Destroy a context, freeing its own allocations (never caller memory).
+ * Synchronises the device first. */
+DQ_API dq_status dq_ctx_destroy(dq_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none).  Valid until the
+ * next call on the context. */
+DQ_API const char *dq_last_error(const dq_ctx *ctx);
+
+/* Select the implementation (dq_path) used by later calls. */
+DQ_API dq_status dq_ctx_set_path(dq_ctx *ctx, int path);
+
+/* Attach caller-owned device memory of `bytes` bytes (16-byte aligned) as the
+ * workspace; ptr == NULL detaches it.  The memory must stay valid while calls
+ * that use it are in flight. */
+DQ_API dq_status dq_ctx_set_workspace(dq_ctx *ctx, void *ptr, size_t bytes);
+
+/* Bytes of workspace that dq_apply_circuit / dq_expect / dq_adjoint_grad /
+ * dq_forward_grad need for this circuit, observable set (may be NULL), batch
+ * and dtype under the context's current path, written to *out. */
+DQ_API dq_status dq_workspace_bytes(dq_ctx *ctx, const dq_circuit *circuit,
+                             const dq_observables *obs, int batch, int dtype,
+                             size_t *out);
+
+/* Synchronise `stream` and report device-side failures recorded by earlier
+ * calls (DQ_ERR_TIMEOUT for a bounded wait that gave up), then clear them. */
+DQ_API dq_status dq_ctx_check(dq_ctx *ctx, void *stream);
+
+/* Number of kernels this context has launched since creation (for launch
+ * accounting by callers). */
+DQ_API int64_t dq_ctx_launch_count(const dq_ctx *ctx);
+
+/* Tracing (the library's profiling hook).  With tracing on, every kernel the
+ * context launches is bracketed by a CUDA event pair on its stream and the
+ * device time is aggregated per kernel name.  Turning tracing on or off
+ * clears the records.  dq_ctx_trace_count synchronises the device, then
+ * returns the number of distinct kernel names recorded (or -1 on error);
+ * dq_ctx_trace_get copies entry i's name (NUL-terminated, truncated to
+ * name_len) and writes its launch count and total device milliseconds. */
+DQ_API dq_status dq_ctx_set_tracing(dq_ctx *ctx, int on);
+DQ_API int dq_ctx_trace_count(dq_ctx *ctx);
+DQ_API dq_status dq_ctx_trace_get(dq_ctx *ctx, int i, char *name, size_t name_len,
+                                  int64_t *launches, double *total_ms);
+
+/* ---- hot path ----------------------------------------------------------- */
+
+/* State preparation |psi_0> = |0...0> for every row (the initial state of
+ * the evolution in Sec. "Quantum Computing with Qubits", Background).
+ * state: device, batch * 2^nqubits amplitudes of `dtype`, overwritten. */
+DQ_API dq_status dq_state_init(dq_ctx *ctx, int nqubits, int batch, int dtype,
+                        void *state, void *stream);
+
+/* In-place evolution |psi> <- U_G ... U_1 |psi> of every row (Sec. "Quantum
+ * Computing with Qubits": discrete time evolution of a pure state; API
+ * Overview: forward execution).  params: device FP64, nparams values (shared)
+ * or batch * nparams (params_per_row != 0); may be NULL if no gate uses a
+ * parameter.  data: device FP64 batch * nfeatures, or NULL. */
+DQ_API dq_status dq_apply_circuit(dq_ctx *ctx, const dq_circuit *circuit,
+                           const double *params, int params_per_row,
+                           const double *data, void *state, int batch,
+                           int dtype, void *stream);
+
+/* Expectations out[row * nobs + o] = sum_k c_k Re <psi_row| P_k |psi_row>
+ * (API Overview: expectation() of predefined observables; weighted sums as
+ * in the TFIM Hamiltonian of Sec. "Simulation of Large Quantum Systems with
+ * MPS").  Products are formed in the state precision and summed in FP64.
+ * state: device, read only.  out: device FP64, batch * nobs. */
+DQ_API dq_status dq_expect(dq_ctx *ctx, int nqubits, const dq_observables *obs,
+                    const void *state, int batch, int dtype, double *out,
+                    void *stream);
+
+/* Adjoint differentiation (Sec. "Distributed Simulations", adjoint method)
+ * of L = sum_row sum_o w[row, o] <psi_row| O_o |psi_row>, where state holds
+ * the final states psi_row produced by dq_apply_circuit with the same
+ * circuit, params and data.  row_weights: device FP64 batch * nobs, or NULL
+ * for all ones.  Outputs (device FP64, overwritten; either may be NULL):
+ *   grad_params: nparams values summed over rows (shared params) or
+ *                batch * nparams (params_per_row != 0);
+ *   grad_data:   batch * nfeatures.
+ * flags: DQ_ADJ_CLOBBER_STATE lets the call use `state` as the reverse-sweep
+ * vector (it is left holding an approximation of |0...0>); without it the
+ * state is preserved and one extra state-sized buffer of workspace is used. */
+#define DQ_ADJ_CLOBBER_STATE 1
+DQ_API dq_status dq_adjoint_grad(dq_ctx *ctx, const dq_circuit *circuit,
+                          const double *params, int params_per_row,
+                          const double *data, const dq_observables *obs,
+                          const double *row_weights, void *state, int batch,
+                          int dtype, int flags, double *grad_params,
+                          double *grad_data, void *stream);
+
+/* One call for the whole batched hot path: state preparation, evolution,
+ * expectations and adjoint gradients.  expect_out: device FP64 batch * nobs
+ * (may be NULL).  grad_params / grad_data as in dq_adjoint_grad (either may
+ * be NULL; both NULL = forward only).  state_out: device buffer for the final
+ * states (batch * 2^n), or NULL when the states are not needed -- the small-n
+ * fused path then keeps them on chip only. */
+DQ_API dq_status dq_forward_grad(dq_ctx *ctx, const dq_circuit *circuit,
+                          const double *params, int params_per_row,
+                          const double *data, const dq_observables *obs,
+                          const double *row_weights, int batch, int dtype,
+                          double *expect_out, double *grad_params,
+                          double *grad_data, void *state_out, void *stream);
+
+/* Uneven batch: ncirc independent circuits (own qubit count, depth and
+ * parameters) run to expectations and per-circuit adjoint gradients in one
+ * persistent launch.  circuits: host array.  params: device FP64, circuit c's
+ * parameters at params[param_offsets[c] ...]; param_offsets: host, ncirc + 1
+ * entries.  expect_out: device FP64 ncirc * nobs.  grad_params: device FP64
+ * laid out like params (may be NULL for forward only).  The observable must
+ * act on wires below every circuit's qubit count. */
+DQ_API dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit *circuits,
+                                const double *params, const int64_t *param_offsets,
+                                const dq_observables *obs, int dtype,
+                                double *expect_out, double *grad_params,
+                                void *stream);
+
+/* Time the fused-path variants (fusion width k and tile schedule) for this
+ * circuit shape on `state` (device, batch rows, contents destroyed) and
+ * cache the fastest for later calls with the same circuit structure.
+ * Synchronises `stream`. */
+DQ_API dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch,
+                           int dtype, void *state, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DQ_H_INCLUDED */

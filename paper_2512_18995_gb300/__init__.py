@@ -1,0 +1,20 @@
+"""GB300-native batched state-vector simulation of parameterised qubit
+circuits: evolution, Pauli-sum expectations and adjoint gradients (the
+qubit-circuit hot path of DeepQuantum, arXiv 2512.18995), implemented as
+hand-written CUDA for sm_103a behind the C ABI in ``include/dq.h``.
+
+Typical use::
+
+    import torch, paper_2512_18995_gb300 as dq
+    ctx = dq.Context()
+    circ = dq.Circuit(n, gates)                  # gates: workloads.Gate tuples
+    obs = dq.Observables([[(1.0, 0, 1)]])        # <Z_0>
+    e = dq.expectation(circ, params, obs, context=ctx)   # differentiable
+    e.sum().backward()                                   # adjoint method
+"""
+from ._lib import (ADJ_CLOBBER_STATE, DQ_C64, DQ_C128, PATH_AUTO, PATH_FUSED, PATH_PLAIN, Circuit, Context,
+                   DQError, Observables, load_library)
+from .autograd import expectation, ExpectationFunction
+
+__all__ = ["Circuit", "Context", "DQError", "Observables", "expectation", "ExpectationFunction",
+           "load_library", "PATH_AUTO", "PATH_PLAIN", "PATH_FUSED", "DQ_C64", "DQ_C128", "ADJ_CLOBBER_STATE"]

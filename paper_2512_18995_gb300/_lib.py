@@ -1,0 +1,357 @@
+"""ctypes binding of libdq (include/dq.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  PyTorch supplies device memory (states, parameters, outputs, the
+workspace) and the current CUDA stream.  If ``libdq.so`` cannot be loaded the
+import fails loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdq.so")
+
+# dq_status
+DQ_OK = 0
+STATUS = {0: "DQ_OK", 1: "DQ_ERR_INVALID_ARG", 2: "DQ_ERR_UNSUPPORTED", 3: "DQ_ERR_OOM",
+          4: "DQ_ERR_CUDA", 5: "DQ_ERR_TIMEOUT"}
+DQ_C64, DQ_C128 = 0, 1
+PATH_AUTO, PATH_PLAIN, PATH_FUSED = 0, 1, 2
+ADJ_CLOBBER_STATE = 1
+
+KIND = {k: i for i, k in enumerate(
+    ["h", "x", "y", "z", "s", "rx", "ry", "rz", "cnot", "cz", "cp", "swap", "crx", "cry", "crz"])}
+
+
+class DQError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class dq_gate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("wires", ctypes.c_int32 * 2), ("param_idx", ctypes.c_int32),
+                ("data_idx", ctypes.c_int32), ("reserved", ctypes.c_int32), ("angle", ctypes.c_double)]
+
+
+class dq_circuit(ctypes.Structure):
+    _fields_ = [("nqubits", ctypes.c_int32), ("ngates", ctypes.c_int32), ("gates", ctypes.POINTER(dq_gate)),
+                ("nparams", ctypes.c_int32), ("nfeatures", ctypes.c_int32)]
+
+
+class dq_pauli_term(ctypes.Structure):
+    _fields_ = [("coeff", ctypes.c_double), ("xmask", ctypes.c_uint64), ("zmask", ctypes.c_uint64)]
+
+
+class dq_observables(ctypes.Structure):
+    _fields_ = [("nobs", ctypes.c_int32), ("term_offsets", ctypes.POINTER(ctypes.c_int32)),
+                ("terms", ctypes.POINTER(dq_pauli_term))]
+
+
+EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path", "dq_ctx_set_workspace",
+           "dq_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_tracing",
+           "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
+           "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune")
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdq.so and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libdq.so not found at {path}: build it with paper_2512_18995_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    C = ctypes.POINTER(dq_circuit)
+    O = ctypes.POINTER(dq_observables)
+    sig = {
+        "dq_ctx_create": ([ctypes.POINTER(P), I], I),
+        "dq_ctx_destroy": ([P], I),
+        "dq_last_error": ([P], ctypes.c_char_p),
+        "dq_ctx_set_path": ([P, I], I),
+        "dq_ctx_set_workspace": ([P, P, ctypes.c_size_t], I),
+        "dq_workspace_bytes": ([P, C, O, I, I, ctypes.POINTER(ctypes.c_size_t)], I),
+        "dq_ctx_check": ([P, P], I),
+        "dq_ctx_launch_count": ([P], ctypes.c_int64),
+        "dq_ctx_set_tracing": ([P, I], I),
+        "dq_ctx_trace_count": ([P], I),
+        "dq_ctx_trace_get": ([P, I, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_double)], I),
+        "dq_state_init": ([P, I, I, I, P, P], I),
+        "dq_apply_circuit": ([P, C, P, I, P, P, I, I, P], I),
+        "dq_expect": ([P, I, O, P, I, I, P, P], I),
+        "dq_adjoint_grad": ([P, C, P, I, P, O, P, P, I, I, I, P, P, P], I),
+        "dq_forward_grad": ([P, C, P, I, P, O, P, I, I, P, P, P, P, P], I),
+        "dq_batch_forward_grad": ([P, I, C, P, ctypes.POINTER(ctypes.c_int64), O, I, P, P, P], I),
+        "dq_plan_autotune": ([P, C, I, I, P, P], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def dtype_code(dt: torch.dtype) -> int:
+    if dt == torch.complex64:
+        return DQ_C64
+    if dt == torch.complex128:
+        return DQ_C128
+    raise TypeError(f"state dtype must be complex64 or complex128, got {dt}")
+
+
+# ---------------------------------------------------------------------------
+# circuit and observable descriptions
+# ---------------------------------------------------------------------------
+class Circuit:
+    """A gate list in the C layout.  ``gates`` are objects with ``kind``,
+    ``wires``, ``param``, ``data``, ``angle`` (e.g. ``workloads.Gate``) or
+    tuples in that order."""
+
+    def __init__(self, nqubits: int, gates: Sequence, nparams: Optional[int] = None,
+                 nfeatures: Optional[int] = None):
+        gl = list(gates)
+        arr = (dq_gate * max(1, len(gl)))()
+        maxp = maxd = -1
+        for i, g in enumerate(gl):
+            kind, wires, param, data, angle = (g.kind, g.wires, g.param, g.data, g.angle) \
+                if hasattr(g, "kind") else tuple(g)
+            arr[i].kind = KIND[kind] if isinstance(kind, str) else int(kind)
+            arr[i].wires[0] = int(wires[0])
+            arr[i].wires[1] = int(wires[1]) if len(wires) > 1 else -1
+            arr[i].param_idx = int(param)
+            arr[i].data_idx = int(data)
+            arr[i].reserved = 0
+            arr[i].angle = float(angle)
+            maxp = max(maxp, int(param))
+            maxd = max(maxd, int(data))
+        self.nqubits = int(nqubits)
+        self.ngates = len(gl)
+        self.nparams = int(nparams) if nparams is not None else maxp + 1
+        self.nfeatures = int(nfeatures) if nfeatures is not None else maxd + 1
+        self._arr = arr
+        self.c = dq_circuit(self.nqubits, self.ngates, ctypes.cast(arr, ctypes.POINTER(dq_gate)),
+                            self.nparams, self.nfeatures)
+
+    def ref(self):
+        return ctypes.byref(self.c)
+
+
+class Observables:
+    """``observables``: list of observables, each a list of
+    ``(coeff, xmask, zmask)`` with bit q of a mask referring to wire q."""
+
+    def __init__(self, observables: Sequence[Sequence[Tuple[float, int, int]]]):
+        obs = [list(o) for o in observables]
+        terms = [t for o in obs for t in o]
+        self._terms = (dq_pauli_term * max(1, len(terms)))()
+        for i, (c, x, z) in enumerate(terms):
+            self._terms[i].coeff = float(c)
+            self._terms[i].xmask = int(x)
+            self._terms[i].zmask = int(z)
+        offs = [0]
+        for o in obs:
+            offs.append(offs[-1] + len(o))
+        self._offs = (ctypes.c_int32 * len(offs))(*offs)
+        self.nobs = len(obs)
+        self.c = dq_observables(self.nobs, ctypes.cast(self._offs, ctypes.POINTER(ctypes.c_int32)),
+                                ctypes.cast(self._terms, ctypes.POINTER(dq_pauli_term)))
+
+    def ref(self):
+        return ctypes.byref(self.c)
+
+
+# ---------------------------------------------------------------------------
+# context
+# ---------------------------------------------------------------------------
+class Context:
+    """One libdq context on one CUDA device.  The workspace is a torch uint8
+    tensor attached to the context and grown on demand."""
+
+    def __init__(self, device: int = 0, path: int = PATH_AUTO):
+        self.lib = load_library()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        st = self.lib.dq_ctx_create(ctypes.byref(h), self.device)
+        if st != DQ_OK:
+            raise DQError(st, f"dq_ctx_create(device={device}) failed")
+        self.h = h
+        self._ws = None
+        self.set_path(path)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dq_ctx_destroy(self.h)
+            self.h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str):
+        if st != DQ_OK:
+            msg = self.lib.dq_last_error(self.h)
+            raise DQError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def set_path(self, path: int):
+        self._check(self.lib.dq_ctx_set_path(self.h, int(path)), "dq_ctx_set_path")
+        self.path = int(path)
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.dq_ctx_launch_count(self.h))
+
+    def check(self):
+        self._check(self.lib.dq_ctx_check(self.h, _stream()), "dq_ctx_check")
+
+    def set_tracing(self, on: bool):
+        self._check(self.lib.dq_ctx_set_tracing(self.h, int(bool(on))), "dq_ctx_set_tracing")
+
+    def trace(self):
+        """{kernel name: (launches, total device ms)} since tracing was turned on."""
+        n = self.lib.dq_ctx_trace_count(self.h)
+        if n < 0:
+            raise DQError(4, "dq_ctx_trace_count failed")
+        out = {}
+        buf = ctypes.create_string_buffer(128)
+        for i in range(n):
+            cnt = ctypes.c_int64(0)
+            ms = ctypes.c_double(0.0)
+            self._check(self.lib.dq_ctx_trace_get(self.h, i, buf, 128, ctypes.byref(cnt), ctypes.byref(ms)),
+                        "dq_ctx_trace_get")
+            out[buf.value.decode()] = (int(cnt.value), float(ms.value))
+        return out
+
+    def ensure_workspace(self, circuit: Optional[Circuit], obs: Optional[Observables], batch: int, dtype: int):
+        if circuit is None:
+            circuit = Circuit(1, [])
+        need = ctypes.c_size_t(0)
+        self._check(self.lib.dq_workspace_bytes(self.h, circuit.ref(), obs.ref() if obs else None, int(batch),
+                                                int(dtype), ctypes.byref(need)), "dq_workspace_bytes")
+        if self._ws is None or self._ws.numel() < need.value:
+            self._ws = None
+            self._check(self.lib.dq_ctx_set_workspace(self.h, None, 0), "dq_ctx_set_workspace")
+            size = max(int(need.value), 1 << 20)
+            self._ws = torch.empty(size, dtype=torch.uint8, device=f"cuda:{self.device}")
+            self._check(self.lib.dq_ctx_set_workspace(self.h, _ptr(self._ws), size), "dq_ctx_set_workspace")
+
+    # ---- hot path --------------------------------------------------------
+    def state_init(self, state: torch.Tensor, nqubits: int):
+        batch = state.numel() >> nqubits
+        self._check(self.lib.dq_state_init(self.h, int(nqubits), int(batch), dtype_code(state.dtype), _ptr(state),
+                                           _stream()), "dq_state_init")
+
+    def apply_circuit(self, circuit: Circuit, params: Optional[torch.Tensor], state: torch.Tensor,
+                      data: Optional[torch.Tensor] = None, params_per_row: bool = False):
+        batch = state.numel() >> circuit.nqubits
+        dt = dtype_code(state.dtype)
+        self.ensure_workspace(circuit, None, batch, dt)
+        self._check(self.lib.dq_apply_circuit(self.h, circuit.ref(), _ptr(params), int(params_per_row), _ptr(data),
+                                              _ptr(state), int(batch), dt, _stream()), "dq_apply_circuit")
+
+    def expect(self, nqubits: int, obs: Observables, state: torch.Tensor,
+               out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        batch = state.numel() >> nqubits
+        dt = dtype_code(state.dtype)
+        if out is None:
+            out = torch.empty((batch, obs.nobs), dtype=torch.float64, device=state.device)
+        self.ensure_workspace(Circuit(nqubits, []), obs, batch, dt)
+        self._check(self.lib.dq_expect(self.h, int(nqubits), obs.ref(), _ptr(state), int(batch), dt, _ptr(out),
+                                       _stream()), "dq_expect")
+        return out
+
+    def adjoint_grad(self, circuit: Circuit, params: Optional[torch.Tensor], obs: Observables,
+                     state: torch.Tensor, data: Optional[torch.Tensor] = None,
+                     row_weights: Optional[torch.Tensor] = None, params_per_row: bool = False,
+                     clobber: bool = False, grad_params: Optional[torch.Tensor] = None,
+                     grad_data: Optional[torch.Tensor] = None):
+        batch = state.numel() >> circuit.nqubits
+        dt = dtype_code(state.dtype)
+        dev = state.device
+        if grad_params is None and circuit.nparams > 0:
+            shape = (batch, circuit.nparams) if params_per_row else (circuit.nparams,)
+            grad_params = torch.empty(shape, dtype=torch.float64, device=dev)
+        if grad_data is None and circuit.nfeatures > 0 and data is not None:
+            grad_data = torch.empty((batch, circuit.nfeatures), dtype=torch.float64, device=dev)
+        self.ensure_workspace(circuit, obs, batch, dt)
+        self._check(self.lib.dq_adjoint_grad(self.h, circuit.ref(), _ptr(params), int(params_per_row), _ptr(data),
+                                             obs.ref(), _ptr(row_weights), _ptr(state), int(batch), dt,
+                                             ADJ_CLOBBER_STATE if clobber else 0, _ptr(grad_params),
+                                             _ptr(grad_data), _stream()), "dq_adjoint_grad")
+        return grad_params, grad_data
+
+    def forward_grad(self, circuit: Circuit, params: Optional[torch.Tensor], obs: Optional[Observables],
+                     batch: int, dtype: torch.dtype = torch.complex64, data: Optional[torch.Tensor] = None,
+                     row_weights: Optional[torch.Tensor] = None, params_per_row: bool = False,
+                     want_expect: bool = True, want_grad: bool = True, state_out: Optional[torch.Tensor] = None,
+                     expect_out: Optional[torch.Tensor] = None, grad_params: Optional[torch.Tensor] = None,
+                     grad_data: Optional[torch.Tensor] = None):
+        dt = dtype_code(dtype)
+        dev = torch.device(f"cuda:{self.device}")
+        if want_expect and expect_out is None and obs is not None:
+            expect_out = torch.empty((batch, obs.nobs), dtype=torch.float64, device=dev)
+        if want_grad:
+            if grad_params is None and circuit.nparams > 0:
+                shape = (batch, circuit.nparams) if params_per_row else (circuit.nparams,)
+                grad_params = torch.empty(shape, dtype=torch.float64, device=dev)
+            if grad_data is None and circuit.nfeatures > 0 and data is not None:
+                grad_data = torch.empty((batch, circuit.nfeatures), dtype=torch.float64, device=dev)
+        else:
+            grad_params = grad_data = None
+        self.ensure_workspace(circuit, obs, batch, dt)
+        self._check(self.lib.dq_forward_grad(self.h, circuit.ref(), _ptr(params), int(params_per_row), _ptr(data),
+                                             obs.ref() if obs is not None else None, _ptr(row_weights), int(batch),
+                                             dt, _ptr(expect_out), _ptr(grad_params), _ptr(grad_data),
+                                             _ptr(state_out), _stream()), "dq_forward_grad")
+        return expect_out, grad_params, grad_data, state_out
+
+    def batch_forward_grad(self, circuits: Sequence[Circuit], params: torch.Tensor, obs: Observables,
+                           dtype: torch.dtype = torch.complex64, want_grad: bool = True,
+                           expect_out: Optional[torch.Tensor] = None, grad_params: Optional[torch.Tensor] = None):
+        nc = len(circuits)
+        arr = (dq_circuit * max(1, nc))()
+        offs = (ctypes.c_int64 * (nc + 1))()
+        for i, c in enumerate(circuits):
+            arr[i] = c.c
+            offs[i + 1] = offs[i] + c.nparams
+        dev = torch.device(f"cuda:{self.device}")
+        if expect_out is None:
+            expect_out = torch.empty((nc, obs.nobs), dtype=torch.float64, device=dev)
+        if want_grad and grad_params is None:
+            grad_params = torch.empty(max(1, int(offs[nc])), dtype=torch.float64, device=dev)
+        if not want_grad:
+            grad_params = None
+        self._keep = (arr, offs)
+        self._check(self.lib.dq_batch_forward_grad(self.h, nc, ctypes.cast(arr, ctypes.POINTER(dq_circuit)),
+                                                   _ptr(params), offs, obs.ref(), dtype_code(dtype),
+                                                   _ptr(expect_out), _ptr(grad_params), _stream()),
+                    "dq_batch_forward_grad")
+        return expect_out, grad_params
+
+    def plan_autotune(self, circuit: Circuit, state: torch.Tensor):
+        batch = state.numel() >> circuit.nqubits
+        dt = dtype_code(state.dtype)
+        self.ensure_workspace(circuit, None, batch, dt)
+        self._check(self.lib.dq_plan_autotune(self.h, circuit.ref(), int(batch), dt, _ptr(state), _stream()),
+                    "dq_plan_autotune")

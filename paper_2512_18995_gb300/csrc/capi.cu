@@ -1,0 +1,1019 @@
+// C ABI of libdq: context, validation, plan caches, workspace and dispatch.
+// The entry points are declared and documented in dq.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "dq.h"
+#include "dq_common.cuh"
+#include "dq_plan.h"
+#include "dq_tile.h"
+
+using namespace dq;
+
+namespace {
+
+struct ObsDev {
+    int nobs = 0;
+    int n = 0;
+    std::vector<DevTerm> bits;     // bit-space terms (host copy)
+    std::vector<int32_t> ptr;      // nobs + 1
+    DevTerm *d_bits = nullptr;     // bit-space
+    DevTerm *d_wires = nullptr;    // wire-space (f = xmask, s = zmask by wire)
+    int32_t *d_ptr = nullptr;
+    void release() {
+        cudaFree(d_bits);
+        cudaFree(d_wires);
+        cudaFree(d_ptr);
+        d_bits = d_wires = nullptr;
+        d_ptr = nullptr;
+    }
+};
+
+struct BatchDev {
+    int ncirc = 0, nmax = 0, maxparams = 0, ngates = 0;
+    BatchCirc *d_circ = nullptr;
+    int32_t *d_order = nullptr;
+    DevGate *d_gates = nullptr;
+    BindGate *d_bind = nullptr;
+    void release() {
+        cudaFree(d_circ);
+        cudaFree(d_order);
+        cudaFree(d_gates);
+        cudaFree(d_bind);
+        d_circ = nullptr;
+        d_order = nullptr;
+        d_gates = nullptr;
+        d_bind = nullptr;
+    }
+};
+
+uint64_t fnv(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+}  // namespace
+
+void Plan::release() {
+    cudaFree(d_gates);
+    cudaFree(d_bind);
+    cudaFree(d_pslot_ptr);
+    cudaFree(d_pslots);
+    cudaFree(d_dslot_ptr);
+    cudaFree(d_dslots);
+    d_gates = nullptr;
+    d_bind = nullptr;
+    d_pslot_ptr = d_pslots = d_dslot_ptr = d_dslots = nullptr;
+}
+
+struct dq_ctx {
+    int device = 0;
+    int nsm = 0;
+    size_t smem_optin = 0;
+    int path = DQ_PATH_AUTO;
+    std::string err;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false;
+    int *d_flag = nullptr;
+    int64_t launches = 0;
+    std::unordered_map<uint64_t, std::unique_ptr<Plan>> plans;
+    std::unordered_map<uint64_t, std::unique_ptr<ObsDev>> obs;
+    std::unordered_map<uint64_t, std::unique_ptr<BatchDev>> batches;
+    std::unordered_map<uint64_t, TileTune> tuned;     // autotuned tile configs
+    TileCache tiles;
+    Tracer tracer;
+    std::vector<std::pair<std::string, std::pair<int64_t, double>>> trace_table;
+};
+
+namespace {
+
+dq_status fail(dq_ctx *ctx, dq_status st, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+dq_status cuda_fail(dq_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, DQ_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define DQ_CUDA(call, where)                                   \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+int amp_bytes(int dtype) { return dtype == DQ_C128 ? 16 : 8; }
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+dq_status check_ctx(dq_ctx *ctx) {
+    if (!ctx) return DQ_ERR_INVALID_ARG;
+    ctx->err.clear();
+    g_tracer = &ctx->tracer;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return DQ_OK;
+}
+
+dq_status check_dtype(dq_ctx *ctx, int dtype) {
+    if (dtype != DQ_C64 && dtype != DQ_C128) return fail(ctx, DQ_ERR_INVALID_ARG, "unknown dtype %d", dtype);
+    return DQ_OK;
+}
+
+dq_status check_n(dq_ctx *ctx, int n) {
+    if (n < 1 || n > 34) return fail(ctx, DQ_ERR_INVALID_ARG, "nqubits %d outside [1, 34]", n);
+    return DQ_OK;
+}
+
+template <typename T>
+dq_status upload(dq_ctx *ctx, T **dst, const T *src, size_t count) {
+    *dst = nullptr;
+    if (count == 0) count = 1;
+    DQ_CUDA(cudaMalloc((void **)dst, count * sizeof(T)), "cudaMalloc(plan)");
+    if (src) DQ_CUDA(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice), "cudaMemcpy(plan)");
+    return DQ_OK;
+}
+
+// Validate a circuit and translate it to bit-space gates.
+dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<DevGate> &dg,
+                        std::vector<BindGate> &bg, int param_base, int *ncoef_shared, int *ncoef_rows,
+                        bool batch_mode) {
+    if (!c) return fail(ctx, DQ_ERR_INVALID_ARG, "circuit is NULL");
+    dq_status st = check_n(ctx, c->nqubits);
+    if (st != DQ_OK) return st;
+    if (c->ngates < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "ngates < 0");
+    if (c->ngates > 0 && !c->gates) return fail(ctx, DQ_ERR_INVALID_ARG, "gates is NULL");
+    if (c->nparams < 0 || c->nfeatures < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "negative nparams/nfeatures");
+    const int n = c->nqubits;
+    // First pass: count per-row coefficient slots (their row stride).
+    int nrows = 0, nshared = 0;
+    for (int i = 0; i < c->ngates; ++i) {
+        const dq_gate &g = c->gates[i];
+        const bool rowwise = (g.data_idx >= 0) || (g.param_idx >= 0 && ppr);
+        if (rowwise) ++nrows; else ++nshared;
+    }
+    int ks = *ncoef_shared, kr = 0;
+    for (int i = 0; i < c->ngates; ++i) {
+        const dq_gate &g = c->gates[i];
+        if (g.kind < 0 || g.kind >= DQ_NUM_GATE_KINDS)
+            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: unknown kind %d", i, g.kind);
+        if (g.reserved != 0) return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: reserved field must be 0", i);
+        const bool two = kind_controlled(g.kind) || g.kind == DQ_SWAP;
+        if (g.wires[0] < 0 || g.wires[0] >= n)
+            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: wire %d outside [0, %d)", i, g.wires[0], n);
+        if (two) {
+            if (g.wires[1] < 0 || g.wires[1] >= n)
+                return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: wire %d outside [0, %d)", i, g.wires[1], n);
+            if (g.wires[1] == g.wires[0])
+                return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: control and target coincide", i);
+        }
+        const bool par = kind_parametric(g.kind);
+        if (!par && (g.param_idx >= 0 || g.data_idx >= 0))
+            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: kind %d takes no angle", i, g.kind);
+        if (g.param_idx >= 0 && g.data_idx >= 0)
+            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: both param_idx and data_idx set", i);
+        if (g.param_idx >= c->nparams)
+            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: param_idx %d >= nparams %d", i, g.param_idx, c->nparams);
+        if (g.data_idx >= c->nfeatures)
+            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: data_idx %d >= nfeatures %d", i, g.data_idx, c->nfeatures);
+        if (batch_mode && g.data_idx >= 0)
+            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: encoded data is not supported in uneven batches", i);
+        DevGate d{};
+        d.kind = g.kind;
+        d.cls = gate_class(g.kind);
+        if (g.kind == DQ_SWAP) {
+            const int a = n - 1 - g.wires[0], b = n - 1 - g.wires[1];
+            d.t = std::min(a, b);
+            d.c = std::max(a, b);
+        } else if (two) {
+            d.c = n - 1 - g.wires[0];
+            d.t = n - 1 - g.wires[1];
+        } else {
+            d.t = n - 1 - g.wires[0];
+            d.c = -1;
+        }
+        const bool rowwise = (g.data_idx >= 0) || (g.param_idx >= 0 && ppr);
+        BindGate b{};
+        b.kind = g.kind;
+        b.pidx = g.param_idx >= 0 ? g.param_idx + param_base : -1;
+        b.didx = g.data_idx;
+        b.angle = g.angle;
+        if (rowwise) {
+            d.coef = *ncoef_shared + nshared + kr;   // placeholder, fixed below
+            d.rowstep = nrows;
+            b.rowstep = nrows;
+            ++kr;
+        } else {
+            d.coef = ks++;
+            d.rowstep = 0;
+            b.rowstep = 0;
+        }
+        d.gkind = 0;
+        d.gout = -1;
+        if (par && g.param_idx >= 0) {
+            d.gkind = ppr || batch_mode ? 2 : 1;
+            d.gout = g.param_idx;
+        } else if (par && g.data_idx >= 0) {
+            d.gkind = 3;
+            d.gout = g.data_idx;
+        }
+        b.coef = d.coef;
+        dg.push_back(d);
+        bg.push_back(b);
+    }
+    // Row-wise slots start after every shared slot: [shared...][row 0: k..][row 1: k..]...
+    const int shared_end = ks;
+    int k = 0;
+    for (size_t i = dg.size() - c->ngates; i < dg.size(); ++i) {
+        if (dg[i].rowstep) {
+            dg[i].coef = shared_end + k;
+            bg[i].coef = shared_end + k;
+            ++k;
+        }
+    }
+    *ncoef_shared = ks;
+    *ncoef_rows = nrows;
+    return DQ_OK;
+}
+
+dq_status get_plan(dq_ctx *ctx, const dq_circuit *c, int ppr, Plan **out) {
+    if (!c) return fail(ctx, DQ_ERR_INVALID_ARG, "circuit is NULL");
+    uint64_t h = fnv(&c->nqubits, sizeof(int32_t));
+    h = fnv(&c->nparams, sizeof(int32_t), h);
+    h = fnv(&c->nfeatures, sizeof(int32_t), h);
+    h = fnv(&ppr, sizeof(int), h);
+    if (c->ngates > 0 && c->gates) h = fnv(c->gates, sizeof(dq_gate) * (size_t)c->ngates, h);
+    h = fnv(&c->ngates, sizeof(int32_t), h);
+    auto it = ctx->plans.find(h);
+    if (it != ctx->plans.end()) {
+        *out = it->second.get();
+        return DQ_OK;
+    }
+    std::unique_ptr<Plan> p(new Plan());
+    int ncs = 0, ncr = 0;
+    dq_status st = compile_gates(ctx, c, ppr, p->gates, p->bind, 0, &ncs, &ncr, false);
+    if (st != DQ_OK) return st;
+    p->key = h;
+    p->n = c->nqubits;
+    p->ngates = c->ngates;
+    p->nparams = c->nparams;
+    p->nfeat = c->nfeatures;
+    p->ppr = ppr;
+    p->ncoef_shared = ncs;
+    p->ncoef_rows = ncr;
+    // gradient slots and CSR lists
+    p->slot_of_gate.assign(p->ngates, -1);
+    std::vector<std::vector<int>> ps(std::max(1, p->nparams)), ds(std::max(1, p->nfeat));
+    for (int i = 0; i < p->ngates; ++i) {
+        const DevGate &g = p->gates[i];
+        if (g.gkind == 0) continue;
+        const int slot = p->nslots++;
+        p->slot_of_gate[i] = slot;
+        if (g.gkind == 3) ds[g.gout].push_back(slot);
+        else ps[g.gout].push_back(slot);
+    }
+    auto csr = [](const std::vector<std::vector<int>> &lists, int count, std::vector<int32_t> &ptr,
+                  std::vector<int32_t> &idx) {
+        ptr.assign(count + 1, 0);
+        for (int i = 0; i < count; ++i) {
+            ptr[i + 1] = ptr[i] + (int)lists[i].size();
+            for (int s : lists[i]) idx.push_back(s);
+        }
+    };
+    std::vector<int32_t> pptr, pidx, dptr, didx;
+    csr(ps, p->nparams, pptr, pidx);
+    csr(ds, p->nfeat, dptr, didx);
+    if ((st = upload(ctx, &p->d_gates, p->gates.data(), p->gates.size())) != DQ_OK) return st;
+    if ((st = upload(ctx, &p->d_bind, p->bind.data(), p->bind.size())) != DQ_OK) return st;
+    if ((st = upload(ctx, &p->d_pslot_ptr, pptr.data(), pptr.size())) != DQ_OK) return st;
+    if ((st = upload(ctx, &p->d_pslots, pidx.empty() ? nullptr : pidx.data(), pidx.size())) != DQ_OK) return st;
+    if ((st = upload(ctx, &p->d_dslot_ptr, dptr.data(), dptr.size())) != DQ_OK) return st;
+    if ((st = upload(ctx, &p->d_dslots, didx.empty() ? nullptr : didx.data(), didx.size())) != DQ_OK) return st;
+    *out = p.get();
+    ctx->plans.emplace(h, std::move(p));
+    return DQ_OK;
+}
+
+dq_status get_obs(dq_ctx *ctx, const dq_observables *o, int n, ObsDev **out) {
+    if (!o) return fail(ctx, DQ_ERR_INVALID_ARG, "observables is NULL");
+    if (o->nobs < 1) return fail(ctx, DQ_ERR_INVALID_ARG, "nobs must be >= 1");
+    if (!o->term_offsets) return fail(ctx, DQ_ERR_INVALID_ARG, "term_offsets is NULL");
+    if (o->term_offsets[0] != 0) return fail(ctx, DQ_ERR_INVALID_ARG, "term_offsets[0] must be 0");
+    for (int i = 0; i < o->nobs; ++i)
+        if (o->term_offsets[i + 1] < o->term_offsets[i])
+            return fail(ctx, DQ_ERR_INVALID_ARG, "term_offsets must be non-decreasing");
+    const int nt = o->term_offsets[o->nobs];
+    if (nt > 0 && !o->terms) return fail(ctx, DQ_ERR_INVALID_ARG, "terms is NULL");
+    const uint64_t allowed = n >= 64 ? ~0ull : ((uint64_t(1) << n) - 1);
+    for (int k = 0; k < nt; ++k)
+        if ((o->terms[k].xmask | o->terms[k].zmask) & ~allowed)
+            return fail(ctx, DQ_ERR_INVALID_ARG, "term %d acts on a wire >= nqubits %d", k, n);
+    uint64_t h = fnv(&n, sizeof(int));
+    h = fnv(&o->nobs, sizeof(int32_t), h);
+    h = fnv(o->term_offsets, sizeof(int32_t) * (o->nobs + 1), h);
+    if (nt) h = fnv(o->terms, sizeof(dq_pauli_term) * nt, h);
+    auto it = ctx->obs.find(h);
+    if (it != ctx->obs.end()) {
+        *out = it->second.get();
+        return DQ_OK;
+    }
+    std::unique_ptr<ObsDev> d(new ObsDev());
+    d->nobs = o->nobs;
+    d->n = n;
+    std::vector<DevTerm> wires;
+    for (int ob = 0; ob < o->nobs; ++ob) {
+        for (int k = o->term_offsets[ob]; k < o->term_offsets[ob + 1]; ++k) {
+            const dq_pauli_term &t = o->terms[k];
+            DevTerm w{};
+            w.f = t.xmask;
+            w.s = t.zmask;
+            w.nY = __builtin_popcountll(t.xmask & t.zmask);
+            w.obs = ob;
+            w.coeff = t.coeff;
+            wires.push_back(w);
+            DevTerm b = w;
+            b.f = 0;
+            b.s = 0;
+            for (int q = 0; q < n; ++q) {
+                if ((t.xmask >> q) & 1) b.f |= uint64_t(1) << (n - 1 - q);
+                if ((t.zmask >> q) & 1) b.s |= uint64_t(1) << (n - 1 - q);
+            }
+            d->bits.push_back(b);
+        }
+    }
+    d->ptr.assign(o->term_offsets, o->term_offsets + o->nobs + 1);
+    dq_status st;
+    if ((st = upload(ctx, &d->d_bits, d->bits.empty() ? nullptr : d->bits.data(), d->bits.size())) != DQ_OK) return st;
+    if ((st = upload(ctx, &d->d_wires, wires.empty() ? nullptr : wires.data(), wires.size())) != DQ_OK) return st;
+    if ((st = upload(ctx, &d->d_ptr, d->ptr.data(), d->ptr.size())) != DQ_OK) return st;
+    *out = d.get();
+    ctx->obs.emplace(h, std::move(d));
+    return DQ_OK;
+}
+
+// Make the workspace at least `bytes` large.
+dq_status reserve(dq_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return DQ_OK;
+    if (ctx->ws && !ctx->ws_owned)
+        return fail(ctx, DQ_ERR_OOM, "attached workspace of %zu bytes is smaller than the %zu bytes needed",
+                    ctx->ws_bytes, bytes);
+    if (ctx->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    const size_t want = std::max(bytes, (size_t)1 << 20);
+    cudaError_t e = cudaMalloc((void **)&ctx->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, DQ_ERR_OOM, "cannot allocate %zu bytes of workspace", want);
+    }
+    ctx->ws_bytes = want;
+    ctx->ws_owned = true;
+    return DQ_OK;
+}
+
+bool use_fused(dq_ctx *ctx) { return ctx->path != DQ_PATH_PLAIN; }
+
+size_t coef_bytes(const Plan &p, int batch, int dtype) {
+    const size_t mat = dtype == DQ_C128 ? sizeof(Mat2<double>) : sizeof(Mat2<float>);
+    return ((size_t)p.ncoef_shared + (size_t)p.ncoef_rows * batch + 1) * mat;
+}
+
+template <typename R>
+cudaError_t bind_coef(dq_ctx *ctx, const Plan &p, const double *params, const double *data, int batch,
+                      void *coef, cudaStream_t s) {
+    return plain_bind<R>(p, params, data, batch, coef, s, &ctx->launches);
+}
+
+dq_status check_angles(dq_ctx *ctx, const Plan &p, const double *params, const double *data) {
+    bool needp = false, needd = false;
+    for (const BindGate &b : p.bind) {
+        needp |= b.pidx >= 0;
+        needd |= b.didx >= 0;
+    }
+    if (needp && !params) return fail(ctx, DQ_ERR_INVALID_ARG, "circuit uses parameters but params is NULL");
+    if (needd && !data) return fail(ctx, DQ_ERR_INVALID_ARG, "circuit uses encoded data but data is NULL");
+    return DQ_OK;
+}
+
+// ---- templated bodies ------------------------------------------------------
+
+template <typename R>
+dq_status apply_impl(dq_ctx *ctx, Plan &p, const double *params, const double *data, void *state, int batch,
+                     cudaStream_t s) {
+    const bool small = use_fused(ctx) && wsv_supported(p.n, (int)sizeof(cx<R>), false, ctx->smem_optin, wsv_doubles(p, 1));
+    const bool tile = use_fused(ctx) && !small && tile_supported(p.n, (int)sizeof(cx<R>));
+    Arena a;
+    a.measuring = true;
+    a.take(coef_bytes(p, batch, sizeof(R) == 8 ? DQ_C128 : DQ_C64));
+    if (tile) a.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>)));
+    dq_status st = reserve(ctx, a.used);
+    if (st != DQ_OK) return st;
+    Arena w;
+    w.base = ctx->ws;
+    w.cap = ctx->ws_bytes;
+    void *coef = w.take(coef_bytes(p, batch, sizeof(R) == 8 ? DQ_C128 : DQ_C64));
+    DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
+    if (small) {
+        DQ_CUDA(wsv_launch<R>(p, coef, state, 1, nullptr, 0, 1, nullptr, batch, state, nullptr, nullptr, nullptr,
+                              nullptr, ctx->nsm, s, &ctx->launches),
+                "fused apply");
+    } else if (tile) {
+        void *tws = w.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>)));
+        DQ_CUDA(tile_apply<R>(ctx->tiles, ctx->tuned, p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches),
+                "tiled apply");
+    } else {
+        DQ_CUDA(plain_apply<R>(p, coef, state, batch, 0, s, &ctx->launches), "plain apply");
+    }
+    return DQ_OK;
+}
+
+template <typename R>
+dq_status expect_impl(dq_ctx *ctx, int n, ObsDev &o, const void *state, int batch, double *out, cudaStream_t s) {
+    const bool small = use_fused(ctx) && wsv_supported(n, (int)sizeof(cx<R>), false, ctx->smem_optin, o.nobs);
+    if (small) {
+        Plan p;
+        p.n = n;
+        DQ_CUDA(wsv_launch<R>(p, nullptr, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, nullptr, batch, nullptr,
+                              out, nullptr, nullptr, nullptr, ctx->nsm, s, &ctx->launches),
+                "fused expect");
+        return DQ_OK;
+    }
+    const size_t part = plain_expect_part_bytes(n, (int)o.bits.size(), batch);
+    dq_status st = reserve(ctx, part + 256);
+    if (st != DQ_OK) return st;
+    double *pbuf = (double *)ctx->ws;
+    DQ_CUDA(plain_expect<R>(n, o.bits, o.nobs, state, batch, pbuf, out, s, &ctx->launches), "expect");
+    DQ_CUDA(plain_expect_finalize(pbuf, o.d_bits, o.d_ptr, o.nobs, n, batch, out, s, &ctx->launches),
+            "expect finalize");
+    return DQ_OK;
+}
+
+template <typename R>
+dq_status adjoint_impl(dq_ctx *ctx, Plan &p, ObsDev &o, const double *params, const double *data,
+                       const double *rw, void *state, int batch, int flags, double *gp, double *gd,
+                       cudaStream_t s) {
+    const int dt = sizeof(R) == 8 ? DQ_C128 : DQ_C64;
+    const size_t sbytes = ((size_t)batch << p.n) * sizeof(cx<R>);
+    const bool small = use_fused(ctx) && wsv_supported(p.n, (int)sizeof(cx<R>), true, ctx->smem_optin, wsv_doubles(p, o.nobs));
+    const bool clobber = (flags & DQ_ADJ_CLOBBER_STATE) != 0;
+    Arena a;
+    a.measuring = true;
+    a.take(coef_bytes(p, batch, dt));
+    if (small) {
+        a.take(wsv_part_bytes(p, ctx->nsm));
+    } else {
+        if (!clobber) a.take(sbytes);
+        a.take(sbytes);
+        a.take(plain_adjoint_part_bytes(p, batch));
+    }
+    dq_status st = reserve(ctx, a.used);
+    if (st != DQ_OK) return st;
+    Arena w;
+    w.base = ctx->ws;
+    w.cap = ctx->ws_bytes;
+    void *coef = w.take(coef_bytes(p, batch, dt));
+    DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
+    if (small) {
+        double *part = (double *)w.take(wsv_part_bytes(p, ctx->nsm));
+        DQ_CUDA(wsv_launch<R>(p, coef, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, rw, batch, nullptr, nullptr,
+                              gp, gd, part, ctx->nsm, s, &ctx->launches),
+                "fused adjoint");
+        return DQ_OK;
+    }
+    void *psi = state;
+    if (!clobber) {
+        psi = w.take(sbytes);
+        DQ_CUDA(cudaMemcpyAsync(psi, state, sbytes, cudaMemcpyDeviceToDevice, s), "copy state");
+    }
+    void *lam = w.take(sbytes);
+    double *part = (double *)w.take(plain_adjoint_part_bytes(p, batch));
+    DQ_CUDA(plain_adjoint<R>(p, coef, o.bits, o.nobs, rw, psi, lam, batch, part, gp, gd, s, &ctx->launches),
+            "plain adjoint");
+    return DQ_OK;
+}
+
+template <typename R>
+dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *params, const double *data,
+                            const double *rw, int batch, double *eo, double *gp, double *gd, void *state_out,
+                            cudaStream_t s) {
+    const int dt = sizeof(R) == 8 ? DQ_C128 : DQ_C64;
+    const bool grad = gp || gd;
+    const size_t sbytes = ((size_t)batch << p.n) * sizeof(cx<R>);
+    const bool small = use_fused(ctx) && wsv_supported(p.n, (int)sizeof(cx<R>), grad, ctx->smem_optin, wsv_doubles(p, o ? o->nobs : 1));
+    if (small) {
+        Arena a;
+        a.measuring = true;
+        a.take(coef_bytes(p, batch, dt));
+        a.take(wsv_part_bytes(p, ctx->nsm));
+        dq_status st = reserve(ctx, a.used);
+        if (st != DQ_OK) return st;
+        Arena w;
+        w.base = ctx->ws;
+        w.cap = ctx->ws_bytes;
+        void *coef = w.take(coef_bytes(p, batch, dt));
+        double *part = (double *)w.take(wsv_part_bytes(p, ctx->nsm));
+        DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
+        DQ_CUDA(wsv_launch<R>(p, coef, nullptr, 1, o ? o->d_wires : nullptr, o ? (int)o->bits.size() : 0,
+                              o ? o->nobs : 1, rw, batch, state_out, eo, gp, gd, part, ctx->nsm, s, &ctx->launches),
+                "fused forward+adjoint");
+        return DQ_OK;
+    }
+    // Large states: prepare, evolve, measure, then the adjoint sweep.
+    const bool tile = use_fused(ctx) && tile_supported(p.n, (int)sizeof(cx<R>));
+    Arena a;
+    a.measuring = true;
+    a.take(coef_bytes(p, batch, dt));
+    if (!state_out) a.take(sbytes);
+    if (grad) {
+        a.take(sbytes);                      // lambda
+        if (state_out) a.take(sbytes);       // working copy of psi (state_out preserved)
+        a.take(tile ? tile_adjoint_part_bytes(p, batch) : plain_adjoint_part_bytes(p, batch));
+    }
+    if (o) a.take(tile ? tile_expect_part_bytes(p.n, (int)o->bits.size(), batch)
+                       : plain_expect_part_bytes(p.n, (int)o->bits.size(), batch));
+    if (tile) a.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>)));
+    dq_status st = reserve(ctx, a.used);
+    if (st != DQ_OK) return st;
+    Arena w;
+    w.base = ctx->ws;
+    w.cap = ctx->ws_bytes;
+    void *coef = w.take(coef_bytes(p, batch, dt));
+    void *psi = state_out ? state_out : w.take(sbytes);
+    void *lam = nullptr, *work = psi;
+    double *gpart = nullptr;
+    if (grad) {
+        lam = w.take(sbytes);
+        if (state_out) work = w.take(sbytes);
+        gpart = (double *)w.take(tile ? tile_adjoint_part_bytes(p, batch) : plain_adjoint_part_bytes(p, batch));
+    }
+    double *epart = nullptr;
+    if (o) epart = (double *)w.take(tile ? tile_expect_part_bytes(p.n, (int)o->bits.size(), batch)
+                                         : plain_expect_part_bytes(p.n, (int)o->bits.size(), batch));
+    void *tws = tile ? w.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>))) : nullptr;
+    DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
+    DQ_CUDA(plain_init_zero<R>(psi, p.n, batch, s, &ctx->launches), "init");
+    if (tile) {
+        DQ_CUDA(tile_apply<R>(ctx->tiles, ctx->tuned, p, coef, psi, batch, tws, ctx->nsm, s, &ctx->launches),
+                "tiled apply");
+    } else {
+        DQ_CUDA(plain_apply<R>(p, coef, psi, batch, 0, s, &ctx->launches), "plain apply");
+    }
+    if (o && eo) {
+        if (tile) {
+            DQ_CUDA(tile_expect<R>(ctx->tiles, p.n, o->bits, o->d_bits, o->d_ptr, o->nobs, psi, batch, epart, eo,
+                                   tws, ctx->nsm, s, &ctx->launches),
+                    "tiled expect");
+        } else {
+            DQ_CUDA(plain_expect<R>(p.n, o->bits, o->nobs, psi, batch, epart, eo, s, &ctx->launches), "expect");
+            DQ_CUDA(plain_expect_finalize(epart, o->d_bits, o->d_ptr, o->nobs, p.n, batch, eo, s, &ctx->launches),
+                    "expect finalize");
+        }
+    }
+    if (grad) {
+        if (work != psi) DQ_CUDA(cudaMemcpyAsync(work, psi, sbytes, cudaMemcpyDeviceToDevice, s), "copy state");
+        if (tile) {
+            DQ_CUDA(tile_adjoint<R>(ctx->tiles, ctx->tuned, p, coef, o->bits, o->nobs, rw, work, lam, batch, gpart,
+                                    gp, gd, tws, ctx->nsm, s, &ctx->launches),
+                    "tiled adjoint");
+        } else {
+            DQ_CUDA(plain_adjoint<R>(p, coef, o->bits, o->nobs, rw, work, lam, batch, gpart, gp, gd, s,
+                                     &ctx->launches),
+                    "plain adjoint");
+        }
+    }
+    return DQ_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported entry points
+// ===========================================================================
+extern "C" {
+
+dq_status dq_ctx_create(dq_ctx **out, int device) {
+    if (!out) return DQ_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return DQ_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return DQ_ERR_CUDA;
+    std::unique_ptr<dq_ctx> c(new dq_ctx());
+    c->device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return DQ_ERR_CUDA;
+    c->nsm = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    if (cudaMalloc((void **)&c->d_flag, 256) != cudaSuccess) return DQ_ERR_OOM;
+    if (cudaMemset(c->d_flag, 0, 256) != cudaSuccess) return DQ_ERR_CUDA;
+    *out = c.release();
+    return DQ_OK;
+}
+
+dq_status dq_ctx_destroy(dq_ctx *ctx) {
+    if (!ctx) return DQ_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->plans) kv.second->release();
+    for (auto &kv : ctx->obs) kv.second->release();
+    for (auto &kv : ctx->batches) kv.second->release();
+    ctx->tiles.release();
+    ctx->tracer.release();
+    if (g_tracer == &ctx->tracer) g_tracer = nullptr;
+    if (ctx->ws_owned) cudaFree(ctx->ws);
+    cudaFree(ctx->d_flag);
+    delete ctx;
+    return DQ_OK;
+}
+
+const char *dq_last_error(const dq_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dq_status dq_ctx_set_path(dq_ctx *ctx, int path) {
+    if (!ctx) return DQ_ERR_INVALID_ARG;
+    if (path != DQ_PATH_AUTO && path != DQ_PATH_PLAIN && path != DQ_PATH_FUSED)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "unknown path %d", path);
+    ctx->path = path;
+    return DQ_OK;
+}
+
+dq_status dq_ctx_set_workspace(dq_ctx *ctx, void *ptr, size_t bytes) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if (ptr && !aligned16(ptr)) return fail(ctx, DQ_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+    if (ctx->ws_owned && ctx->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->ws);
+    }
+    ctx->ws = (char *)ptr;
+    ctx->ws_bytes = ptr ? bytes : 0;
+    ctx->ws_owned = false;
+    return DQ_OK;
+}
+
+int64_t dq_ctx_launch_count(const dq_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+dq_status dq_ctx_set_tracing(dq_ctx *ctx, int on) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    cudaDeviceSynchronize();
+    for (auto &r : ctx->tracer.recs) {
+        ctx->tracer.pool.push_back(r.a);
+        ctx->tracer.pool.push_back(r.b);
+    }
+    ctx->tracer.recs.clear();
+    ctx->tracer.names.clear();
+    ctx->trace_table.clear();
+    ctx->tracer.on = on != 0;
+    return DQ_OK;
+}
+
+int dq_ctx_trace_count(dq_ctx *ctx) {
+    if (check_ctx(ctx) != DQ_OK) return -1;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    std::vector<std::pair<int64_t, double>> agg(ctx->tracer.names.size(), {0, 0.0});
+    for (auto &r : ctx->tracer.recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            agg[r.name].first += 1;
+            agg[r.name].second += ms;
+        }
+    }
+    ctx->trace_table.clear();
+    for (size_t i = 0; i < agg.size(); ++i) ctx->trace_table.push_back({ctx->tracer.names[i], agg[i]});
+    return (int)ctx->trace_table.size();
+}
+
+dq_status dq_ctx_trace_get(dq_ctx *ctx, int i, char *name, size_t name_len, int64_t *launches, double *total_ms) {
+    if (!ctx) return DQ_ERR_INVALID_ARG;
+    if (i < 0 || i >= (int)ctx->trace_table.size()) return fail(ctx, DQ_ERR_INVALID_ARG, "trace index %d", i);
+    const auto &e = ctx->trace_table[i];
+    if (name && name_len) {
+        std::strncpy(name, e.first.c_str(), name_len - 1);
+        name[name_len - 1] = 0;
+    }
+    if (launches) *launches = e.second.first;
+    if (total_ms) *total_ms = e.second.second;
+    return DQ_OK;
+}
+
+dq_status dq_ctx_check(dq_ctx *ctx, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    DQ_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+    int flag = 0;
+    DQ_CUDA(cudaMemcpy(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+    if (flag != DEVERR_NONE) {
+        cudaMemset(ctx->d_flag, 0, sizeof(int));
+        if (flag == DEVERR_TIMEOUT) return fail(ctx, DQ_ERR_TIMEOUT, "a device-side bounded wait gave up");
+        return fail(ctx, DQ_ERR_CUDA, "device-side check failed (code %d)", flag);
+    }
+    return DQ_OK;
+}
+
+dq_status dq_workspace_bytes(dq_ctx *ctx, const dq_circuit *circuit, const dq_observables *obs, int batch,
+                             int dtype, size_t *out) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if (!out) return fail(ctx, DQ_ERR_INVALID_ARG, "out is NULL");
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    Plan *p = nullptr;
+    if ((st = get_plan(ctx, circuit, 0, &p)) != DQ_OK) return st;
+    const size_t sb = ((size_t)batch << p->n) * amp_bytes(dtype);
+    int nterms = 0;
+    if (obs && obs->term_offsets && obs->nobs > 0) nterms = obs->term_offsets[obs->nobs];
+    Arena a;
+    a.measuring = true;
+    a.take(coef_bytes(*p, batch, dtype));
+    a.take(3 * sb);
+    a.take(plain_adjoint_part_bytes(*p, batch));
+    a.take(plain_expect_part_bytes(p->n, nterms, batch));
+    a.take(wsv_part_bytes(*p, ctx->nsm));
+    a.take(tile_workspace_bytes(*p, batch, amp_bytes(dtype)));
+    a.take(tile_adjoint_part_bytes(*p, batch));
+    a.take(tile_expect_part_bytes(p->n, nterms, batch));
+    *out = a.used;
+    return DQ_OK;
+}
+
+dq_status dq_state_init(dq_ctx *ctx, int nqubits, int batch, int dtype, void *state, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if ((st = check_n(ctx, nqubits)) != DQ_OK) return st;
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    if (batch == 0) return DQ_OK;
+    if (!state || !aligned16(state)) return fail(ctx, DQ_ERR_INVALID_ARG, "state must be a 16-byte aligned device pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == DQ_C64) DQ_CUDA(plain_init_zero<float>(state, nqubits, batch, s, &ctx->launches), "init");
+    else DQ_CUDA(plain_init_zero<double>(state, nqubits, batch, s, &ctx->launches), "init");
+    return DQ_OK;
+}
+
+dq_status dq_apply_circuit(dq_ctx *ctx, const dq_circuit *circuit, const double *params, int params_per_row,
+                           const double *data, void *state, int batch, int dtype, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    Plan *p = nullptr;
+    if ((st = get_plan(ctx, circuit, params_per_row ? 1 : 0, &p)) != DQ_OK) return st;
+    if (batch == 0 || p->ngates == 0) return DQ_OK;
+    if (!state || !aligned16(state)) return fail(ctx, DQ_ERR_INVALID_ARG, "state must be a 16-byte aligned device pointer");
+    if ((st = check_angles(ctx, *p, params, data)) != DQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return dtype == DQ_C64 ? apply_impl<float>(ctx, *p, params, data, state, batch, s)
+                           : apply_impl<double>(ctx, *p, params, data, state, batch, s);
+}
+
+dq_status dq_expect(dq_ctx *ctx, int nqubits, const dq_observables *obs, const void *state, int batch, int dtype,
+                    double *out, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if ((st = check_n(ctx, nqubits)) != DQ_OK) return st;
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    ObsDev *o = nullptr;
+    if ((st = get_obs(ctx, obs, nqubits, &o)) != DQ_OK) return st;
+    if (batch == 0) return DQ_OK;
+    if (!state || !aligned16(state)) return fail(ctx, DQ_ERR_INVALID_ARG, "state must be a 16-byte aligned device pointer");
+    if (!out) return fail(ctx, DQ_ERR_INVALID_ARG, "out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (o->bits.empty()) {
+        DQ_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)batch * o->nobs, s), "memset");
+        return DQ_OK;
+    }
+    return dtype == DQ_C64 ? expect_impl<float>(ctx, nqubits, *o, state, batch, out, s)
+                           : expect_impl<double>(ctx, nqubits, *o, state, batch, out, s);
+}
+
+dq_status dq_adjoint_grad(dq_ctx *ctx, const dq_circuit *circuit, const double *params, int params_per_row,
+                          const double *data, const dq_observables *obs, const double *row_weights, void *state,
+                          int batch, int dtype, int flags, double *grad_params, double *grad_data, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    if (flags & ~DQ_ADJ_CLOBBER_STATE) return fail(ctx, DQ_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+    Plan *p = nullptr;
+    if ((st = get_plan(ctx, circuit, params_per_row ? 1 : 0, &p)) != DQ_OK) return st;
+    ObsDev *o = nullptr;
+    if ((st = get_obs(ctx, obs, p->n, &o)) != DQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (batch == 0) return DQ_OK;
+    if (!state || !aligned16(state)) return fail(ctx, DQ_ERR_INVALID_ARG, "state must be a 16-byte aligned device pointer");
+    if ((st = check_angles(ctx, *p, params, data)) != DQ_OK) return st;
+    if (!grad_params && !grad_data) return DQ_OK;
+    if (grad_data && p->nfeat == 0) grad_data = nullptr;
+    if (grad_params && p->nparams == 0) grad_params = nullptr;
+    if (!grad_params && !grad_data) return DQ_OK;
+    return dtype == DQ_C64
+               ? adjoint_impl<float>(ctx, *p, *o, params, data, row_weights, state, batch, flags, grad_params, grad_data, s)
+               : adjoint_impl<double>(ctx, *p, *o, params, data, row_weights, state, batch, flags, grad_params, grad_data, s);
+}
+
+dq_status dq_forward_grad(dq_ctx *ctx, const dq_circuit *circuit, const double *params, int params_per_row,
+                          const double *data, const dq_observables *obs, const double *row_weights, int batch,
+                          int dtype, double *expect_out, double *grad_params, double *grad_data, void *state_out,
+                          void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    Plan *p = nullptr;
+    if ((st = get_plan(ctx, circuit, params_per_row ? 1 : 0, &p)) != DQ_OK) return st;
+    if (grad_data && p->nfeat == 0) grad_data = nullptr;
+    if (grad_params && p->nparams == 0) grad_params = nullptr;
+    ObsDev *o = nullptr;
+    if (obs) {
+        if ((st = get_obs(ctx, obs, p->n, &o)) != DQ_OK) return st;
+    } else if (expect_out || grad_params || grad_data) {
+        return fail(ctx, DQ_ERR_INVALID_ARG, "expectations or gradients need observables");
+    }
+    if (batch == 0) return DQ_OK;
+    if (state_out && !aligned16(state_out)) return fail(ctx, DQ_ERR_INVALID_ARG, "state_out must be 16-byte aligned");
+    if ((st = check_angles(ctx, *p, params, data)) != DQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return dtype == DQ_C64 ? forward_grad_impl<float>(ctx, *p, o, params, data, row_weights, batch, expect_out,
+                                                      grad_params, grad_data, state_out, s)
+                           : forward_grad_impl<double>(ctx, *p, o, params, data, row_weights, batch, expect_out,
+                                                       grad_params, grad_data, state_out, s);
+}
+
+dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit *circuits, const double *params,
+                                const int64_t *param_offsets, const dq_observables *obs, int dtype,
+                                double *expect_out, double *grad_params, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (ncirc < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "ncirc < 0");
+    if (ncirc == 0) return DQ_OK;
+    if (!circuits || !param_offsets) return fail(ctx, DQ_ERR_INVALID_ARG, "circuits/param_offsets is NULL");
+    if (!expect_out) return fail(ctx, DQ_ERR_INVALID_ARG, "expect_out is NULL");
+    int nmin = 64;
+    uint64_t h = fnv(&ncirc, sizeof(int));
+    for (int c = 0; c < ncirc; ++c) {
+        if ((st = check_n(ctx, circuits[c].nqubits)) != DQ_OK) return st;
+        nmin = std::min(nmin, circuits[c].nqubits);
+        if (param_offsets[c + 1] - param_offsets[c] != circuits[c].nparams)
+            return fail(ctx, DQ_ERR_INVALID_ARG, "circuit %d: param_offsets span %lld != nparams %d", c,
+                        (long long)(param_offsets[c + 1] - param_offsets[c]), circuits[c].nparams);
+        h = fnv(&circuits[c].nqubits, sizeof(int32_t), h);
+        h = fnv(&circuits[c].nparams, sizeof(int32_t), h);
+        h = fnv(&circuits[c].ngates, sizeof(int32_t), h);
+        if (circuits[c].ngates > 0 && circuits[c].gates)
+            h = fnv(circuits[c].gates, sizeof(dq_gate) * circuits[c].ngates, h);
+    }
+    h = fnv(param_offsets, sizeof(int64_t) * (ncirc + 1), h);
+    ObsDev *o = nullptr;
+    if ((st = get_obs(ctx, obs, nmin, &o)) != DQ_OK) return st;
+    if (param_offsets[0] != 0) return fail(ctx, DQ_ERR_INVALID_ARG, "param_offsets[0] must be 0");
+    const int64_t ptotal = param_offsets[ncirc];
+    if (ptotal > 0 && !params) return fail(ctx, DQ_ERR_INVALID_ARG, "params is NULL");
+    if (ptotal >= (int64_t(1) << 31)) return fail(ctx, DQ_ERR_INVALID_ARG, "too many parameters");
+    BatchDev *bd = nullptr;
+    std::vector<BindGate> allbind;
+    auto it = ctx->batches.find(h);
+    int ncoef = 0;
+    if (it != ctx->batches.end()) {
+        bd = it->second.get();
+        ncoef = bd->ngates;
+    } else {
+        std::unique_ptr<BatchDev> b(new BatchDev());
+        std::vector<DevGate> allg;
+        std::vector<BatchCirc> bc(ncirc);
+        std::vector<std::pair<double, int>> cost(ncirc);
+        int nmax = 0, maxp = 0;
+        for (int c = 0; c < ncirc; ++c) {
+            BatchCirc x{};
+            x.n = circuits[c].nqubits;
+            x.gate0 = (int)allg.size();
+            x.ngates = circuits[c].ngates;
+            x.param0 = (int)param_offsets[c];
+            x.nparams = circuits[c].nparams;
+            int ncr = 0;
+            st = compile_gates(ctx, &circuits[c], 0, allg, allbind, (int)param_offsets[c], &ncoef, &ncr, true);
+            if (st != DQ_OK) return fail(ctx, st, "circuit %d: %s", c, ctx->err.c_str());
+            bc[c] = x;
+            nmax = std::max(nmax, x.n);
+            maxp = std::max(maxp, x.nparams);
+            cost[c] = {std::ldexp((double)std::max(1, x.ngates), x.n), c};
+        }
+        if (nmax > 20) return fail(ctx, DQ_ERR_UNSUPPORTED, "uneven batches support up to 20 qubits per circuit");
+        std::stable_sort(cost.begin(), cost.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+            return a.first > b.first;
+        });
+        std::vector<int32_t> order(ncirc);
+        for (int i = 0; i < ncirc; ++i) order[i] = cost[i].second;
+        b->ncirc = ncirc;
+        b->nmax = nmax;
+        b->maxparams = maxp;
+        b->ngates = (int)allg.size();
+        if ((st = upload(ctx, &b->d_circ, bc.data(), bc.size())) != DQ_OK) return st;
+        if ((st = upload(ctx, &b->d_order, order.data(), order.size())) != DQ_OK) return st;
+        if ((st = upload(ctx, &b->d_gates, allg.empty() ? nullptr : allg.data(), allg.size())) != DQ_OK) return st;
+        if ((st = upload(ctx, &b->d_bind, allbind.empty() ? nullptr : allbind.data(), allbind.size())) != DQ_OK)
+            return st;
+        bd = b.get();
+        ctx->batches.emplace(h, std::move(b));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ab = amp_bytes(dtype);
+    const size_t mat = dtype == DQ_C128 ? sizeof(Mat2<double>) : sizeof(Mat2<float>);
+    Arena a;
+    a.measuring = true;
+    a.take(mat * (size_t)(bd->ngates + 1));
+    a.take(batch_scratch_bytes(bd->nmax, ab, ctx->nsm, ctx->smem_optin));
+    a.take(256);
+    if ((st = reserve(ctx, a.used)) != DQ_OK) return st;
+    Arena w;
+    w.base = ctx->ws;
+    w.cap = ctx->ws_bytes;
+    void *coef = w.take(mat * (size_t)(bd->ngates + 1));
+    void *scratch = w.take(batch_scratch_bytes(bd->nmax, ab, ctx->nsm, ctx->smem_optin));
+    int *counter = (int *)w.take(256);
+    // bind all gate angles (global parameter indices, shared rows)
+    Plan bp;
+    bp.ngates = bd->ngates;
+    bp.d_bind = bd->d_bind;
+    bp.nparams = (int)ptotal;
+    if (bd->ngates > 0) {
+        if (dtype == DQ_C64) DQ_CUDA(plain_bind<float>(bp, params, nullptr, 1, coef, s, &ctx->launches), "bind");
+        else DQ_CUDA(plain_bind<double>(bp, params, nullptr, 1, coef, s, &ctx->launches), "bind");
+    }
+    const int nterms = (int)o->bits.size();
+    if (dtype == DQ_C64)
+        DQ_CUDA(batch_run<float>(bd->d_circ, ncirc, bd->d_order, bd->d_gates, coef, o->d_wires, nterms, o->nobs,
+                                 bd->nmax, bd->maxparams, expect_out, grad_params, scratch, counter, ctx->nsm,
+                                 ctx->smem_optin, s, &ctx->launches),
+                "batch");
+    else
+        DQ_CUDA(batch_run<double>(bd->d_circ, ncirc, bd->d_order, bd->d_gates, coef, o->d_wires, nterms, o->nobs,
+                                  bd->nmax, bd->maxparams, expect_out, grad_params, scratch, counter, ctx->nsm,
+                                  ctx->smem_optin, s, &ctx->launches),
+                "batch");
+    return DQ_OK;
+}
+
+dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch, int dtype, void *state, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (batch < 1) return fail(ctx, DQ_ERR_INVALID_ARG, "batch must be >= 1");
+    if (!state || !aligned16(state)) return fail(ctx, DQ_ERR_INVALID_ARG, "state must be a 16-byte aligned device pointer");
+    Plan *p = nullptr;
+    if ((st = get_plan(ctx, circuit, 0, &p)) != DQ_OK) return st;
+    if (!tile_supported(p->n, amp_bytes(dtype))) return DQ_OK;   // nothing to tune
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t need = coef_bytes(*p, batch, dtype) + 512 + tile_workspace_bytes(*p, batch, amp_bytes(dtype));
+    if ((st = reserve(ctx, need)) != DQ_OK) return st;
+    Arena w;
+    w.base = ctx->ws;
+    w.cap = ctx->ws_bytes;
+    void *coef = w.take(coef_bytes(*p, batch, dtype));
+    void *tws = w.take(tile_workspace_bytes(*p, batch, amp_bytes(dtype)));
+    // Angles: all zero parameters are fine for timing (same sweeps run).
+    double *zeros = nullptr;
+    const size_t pb = sizeof(double) * (size_t)std::max(1, p->nparams) * 1;
+    DQ_CUDA(cudaMalloc((void **)&zeros, pb + sizeof(double) * (size_t)std::max(1, p->nfeat) * batch), "alloc");
+    cudaMemsetAsync(zeros, 0, pb + sizeof(double) * (size_t)std::max(1, p->nfeat) * batch, s);
+    cudaError_t e;
+    if (dtype == DQ_C64) {
+        e = bind_coef<float>(ctx, *p, zeros, zeros, batch, coef, s);
+        if (e == cudaSuccess) e = tile_autotune<float>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+    } else {
+        e = bind_coef<double>(ctx, *p, zeros, zeros, batch, coef, s);
+        if (e == cudaSuccess) e = tile_autotune<double>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(zeros);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+    return DQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+// Shared device/host definitions of libdq (internal).
+//
+// Conventions: wire q of an n-qubit row is bit p = n-1-q of the amplitude
+// index.  Inside the library every gate is stored by bit position.  A
+// complex amplitude is float2 (DQ_C64) or double2 (DQ_C128).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dq.h"
+
+namespace dq {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on float2 / double2
+// ---------------------------------------------------------------------------
+template <typename R> struct CT;
+template <> struct CT<float> { using type = float2; using unit = float4; };
+template <> struct CT<double> { using type = double2; };
+
+template <typename R> using cx = typename CT<R>::type;
+
+template <typename R> __host__ __device__ __forceinline__ cx<R> mk(R x, R y) { cx<R> c; c.x = x; c.y = y; return c; }
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
+
+// 2x2 block acting on the target qubit (applied on control = |1> for
+// controlled kinds).  m[0] m[1] / m[2] m[3] row-major.
+template <typename R> struct Mat2 { cx<R> m[4]; };
+
+// Gate classes used to specialise the sweeps.
+enum GateClass : int {
+    CLS_GENERAL = 0,   // full complex 2x2
+    CLS_REAL = 1,      // real 2x2 (H, RY, CRY)
+    CLS_DIAG = 2,      // diagonal (Z, S, RZ, CZ, CP, CRZ)
+    CLS_ANTI = 3,      // X / CNOT: exchange
+    CLS_SWAP = 4       // SWAP of two qubits
+};
+
+__host__ __device__ inline int gate_class(int kind) {
+    switch (kind) {
+    case DQ_H: case DQ_RY: case DQ_CRY: return CLS_REAL;
+    case DQ_Z: case DQ_S: case DQ_RZ: case DQ_CZ: case DQ_CP: case DQ_CRZ: return CLS_DIAG;
+    case DQ_X: case DQ_CNOT: return CLS_ANTI;
+    case DQ_SWAP: return CLS_SWAP;
+    default: return CLS_GENERAL;   // Y, RX, CRX
+    }
+}
+
+__host__ __device__ inline bool kind_controlled(int k) {
+    return k == DQ_CNOT || k == DQ_CZ || k == DQ_CP || k == DQ_CRX || k == DQ_CRY || k == DQ_CRZ;
+}
+__host__ __device__ inline bool kind_parametric(int k) {
+    return k == DQ_RX || k == DQ_RY || k == DQ_RZ || k == DQ_CP || k == DQ_CRX || k == DQ_CRY || k == DQ_CRZ;
+}
+
+// Target block of `kind` at angle t, evaluated in double and rounded to R.
+// R_P(t) = cos(t/2) I - i sin(t/2) P;  CP(t): diag(1, e^{i t}).
+template <typename R>
+__host__ __device__ inline Mat2<R> gate_matrix(int kind, double t) {
+    double c = 1.0, s = 0.0;
+    if (kind_parametric(kind)) {
+        const double h = (kind == DQ_CP) ? t : 0.5 * t;
+#ifdef __CUDA_ARCH__
+        sincos(h, &s, &c);
+#else
+        s = ::sin(h); c = ::cos(h);
+#endif
+    }
+    const double r2 = 0.70710678118654752440;
+    double a[8] = {1, 0, 0, 0, 0, 0, 1, 0};   // identity, (re, im) x 4
+    switch (kind) {
+    case DQ_H: a[0] = r2; a[2] = r2; a[4] = r2; a[6] = -r2; break;
+    case DQ_X: case DQ_CNOT: a[0] = 0; a[2] = 1; a[4] = 1; a[6] = 0; break;
+    case DQ_Y: a[0] = 0; a[3] = -1; a[5] = 1; a[6] = 0; break;
+    case DQ_Z: case DQ_CZ: a[6] = -1; break;
+    case DQ_S: a[6] = 0; a[7] = 1; break;
+    case DQ_RX: case DQ_CRX: a[0] = c; a[3] = -s; a[5] = -s; a[6] = c; break;
+    case DQ_RY: case DQ_CRY: a[0] = c; a[2] = -s; a[4] = s; a[6] = c; break;
+    case DQ_RZ: case DQ_CRZ: a[0] = c; a[1] = -s; a[6] = c; a[7] = s; break;
+    case DQ_CP: a[6] = c; a[7] = s; break;
+    default: break;
+    }
+    Mat2<R> m;
+    for (int i = 0; i < 4; ++i) m.m[i] = mk<R>((R)a[2 * i], (R)a[2 * i + 1]);
+    return m;
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ Mat2<R> dagger(const Mat2<R>& u) {
+    Mat2<R> d;
+    d.m[0] = cconj(u.m[0]); d.m[1] = cconj(u.m[2]);
+    d.m[2] = cconj(u.m[1]); d.m[3] = cconj(u.m[3]);
+    return d;
+}
+
+// (a0, a1) <- M (a0, a1), specialised by class.
+template <typename R, int CLS>
+__device__ __forceinline__ void apply2(const Mat2<R>& u, cx<R>& a0, cx<R>& a1) {
+    if (CLS == CLS_ANTI) {
+        cx<R> t = a0; a0 = a1; a1 = t;
+    } else if (CLS == CLS_DIAG) {
+        a0 = cmul(u.m[0], a0);
+        a1 = cmul(u.m[3], a1);
+    } else if (CLS == CLS_REAL) {
+        const R u0 = u.m[0].x, u1 = u.m[1].x, u2 = u.m[2].x, u3 = u.m[3].x;
+        cx<R> b0, b1;
+        b0.x = u0 * a0.x + u1 * a1.x; b0.y = u0 * a0.y + u1 * a1.y;
+        b1.x = u2 * a0.x + u3 * a1.x; b1.y = u2 * a0.y + u3 * a1.y;
+        a0 = b0; a1 = b1;
+    } else {
+        cx<R> b0 = cadd(cmul(u.m[0], a0), cmul(u.m[1], a1));
+        cx<R> b1 = cadd(cmul(u.m[2], a0), cmul(u.m[3], a1));
+        a0 = b0; a1 = b1;
+    }
+}
+
+// Runtime-class variant (used where the class is data, e.g. fused programs).
+template <typename R>
+__device__ __forceinline__ void apply2_rt(int cls, const Mat2<R>& u, cx<R>& a0, cx<R>& a1) {
+    switch (cls) {
+    case CLS_ANTI: apply2<R, CLS_ANTI>(u, a0, a1); break;
+    case CLS_DIAG: apply2<R, CLS_DIAG>(u, a0, a1); break;
+    case CLS_REAL: apply2<R, CLS_REAL>(u, a0, a1); break;
+    default: apply2<R, CLS_GENERAL>(u, a0, a1); break;
+    }
+}
+
+// Contribution of one target pair to dL/dt = 2 Im <lambda| G |psi>, where
+// U(t) = exp(-i t G) and (l0, l1), (p0, p1) are the pair's amplitudes after
+// the gate.  G is P/2 for R_P (restricted to control = |1>) and -|11><11| for
+// CP; the factor 2 is folded in.
+template <typename R>
+__device__ __forceinline__ R grad_pair(int kind, cx<R> l0, cx<R> l1, cx<R> p0, cx<R> p1) {
+    switch (kind) {
+    case DQ_RX: case DQ_CRX:   // Im(conj(l0) p1 + conj(l1) p0)
+        return (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
+    case DQ_RY: case DQ_CRY:   // Im(-i conj(l0) p1 + i conj(l1) p0) = -Re(conj(l0) p1) + Re(conj(l1) p0)
+        return -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
+    case DQ_RZ: case DQ_CRZ:   // Im(conj(l0) p0 - conj(l1) p1)
+        return (l0.x * p0.y - l0.y * p0.x) - (l1.x * p1.y - l1.y * p1.x);
+    case DQ_CP:                // 2 Im(conj(l1) (-p1))
+        return (R)(-2) * (l1.x * p1.y - l1.y * p1.x);
+    default:
+        return (R)0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// bit helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t insert0(uint64_t x, int p) {
+    const uint64_t lo = x & ((uint64_t(1) << p) - 1);
+    return ((x >> p) << (p + 1)) | lo;
+}
+// Insert zeros at bit positions a < b (positions in the result).
+__host__ __device__ __forceinline__ uint64_t insert0x2(uint64_t x, int a, int b) {
+    return insert0(insert0(x, a), b);
+}
+
+__device__ __forceinline__ int parity64(uint64_t x) { return __popcll(x) & 1; }
+
+// ---------------------------------------------------------------------------
+// Pauli phase: P|b> = ph(b) |b ^ f>, ph(b) = i^{nY} (-1)^{popc(b & s)}.
+// Returns ph as (re, im) in {+-1, +-i}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pauli_phase(uint64_t b, uint64_t s, int nY, float& pr, float& pi) {
+    const int k = (nY + 2 * parity64(b & s)) & 3;   // i^k
+    pr = (k == 0) ? 1.f : (k == 2 ? -1.f : 0.f);
+    pi = (k == 1) ? 1.f : (k == 3 ? -1.f : 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// reductions: FP64 warp sum
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Device-side error flag codes (written with atomicCAS so the first wins).
+enum DevErr : int { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1, DEVERR_BOUNDS = 2 };
+
+}  // namespace dq

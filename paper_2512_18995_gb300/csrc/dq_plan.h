@@ -1,0 +1,164 @@
+// Host-side plan structures and kernel launcher declarations (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dq.h"
+
+namespace dq {
+
+// Gate as the kernels see it (bit positions, not wires).  32 bytes.
+struct DevGate {
+    int32_t kind;       // dq_gate_kind
+    int32_t cls;        // GateClass
+    int32_t t;          // target bit (SWAP: lower bit)
+    int32_t c;          // control bit, or -1 (SWAP: upper bit)
+    int32_t coef;       // index of this gate's Mat2 in the bound table (row 0)
+    int32_t rowstep;    // row stride of its Mat2 (0: one shared angle)
+    int32_t gout;       // gradient output: -1 none; >= 0 see grad_kind
+    int32_t gkind;      // 0 none, 1 shared param, 2 per-row param, 3 per-row data
+};
+
+// Gate angle source for the bind kernel.  32 bytes.
+struct BindGate {
+    int32_t kind;
+    int32_t pidx;       // parameter index (already offset for uneven batches)
+    int32_t didx;       // data feature index
+    int32_t coef;       // output slot (row 0)
+    int32_t rowstep;    // row stride of the output slot (0: shared angle)
+    int32_t pad;
+    double angle;
+};
+
+// One Pauli term in bit space.
+struct DevTerm {
+    uint64_t f;         // flip mask (bit space)
+    uint64_t s;         // sign mask (bit space)
+    int32_t nY;         // number of Y factors
+    int32_t obs;        // observable index
+    double coeff;
+};
+
+// Compiled circuit (cached by structure).
+struct Plan {
+    uint64_t key = 0;
+    int n = 0;
+    int ngates = 0;
+    int nparams = 0;
+    int nfeat = 0;
+    int ppr = 0;                       // per-row params
+    std::vector<DevGate> gates;        // host copy
+    std::vector<BindGate> bind;        // host copy
+    int ncoef_shared = 0;              // Mat2 slots with rowstep 0
+    int ncoef_rows = 0;                // gates with rowstep 1
+    DevGate *d_gates = nullptr;
+    BindGate *d_bind = nullptr;
+    // Gradient slots: one per gate with a trainable/encoded angle.
+    int nslots = 0;
+    std::vector<int> slot_of_gate;     // -1 or slot id
+    // CSR: output index -> slots (params then data features)
+    int32_t *d_pslot_ptr = nullptr, *d_pslots = nullptr;
+    int32_t *d_dslot_ptr = nullptr, *d_dslots = nullptr;
+    void release();
+};
+
+// Workspace bump allocator over the context's device buffer.
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0, used = 0;
+    bool measuring = false;            // only count bytes
+    void *take(size_t bytes) {
+        used = (used + 255) & ~size_t(255);
+        void *p = measuring ? nullptr : (void *)(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+// Per-launch accounting.  Every kernel launch of the library is wrapped in a
+// LaunchScope: it bumps the context's launch counter and, when tracing is on,
+// records a CUDA event pair around the launch on its stream so per-kernel
+// device time can be read back (dq_ctx_trace_get).
+struct Tracer {
+    bool on = false;
+    std::vector<std::string> names;
+    struct Rec { int name; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get_event();
+    int name_id(const char *n);
+    void release();
+};
+extern thread_local Tracer *g_tracer;
+
+struct LaunchScope {
+    LaunchScope(cudaStream_t s, const char *name, int64_t *counter);
+    ~LaunchScope();
+    cudaStream_t s;
+    int64_t *counter;
+    int rec = -1;
+};
+
+// ---- plain per-gate path -------------------------------------------------
+template <typename R>
+cudaError_t plain_bind(const Plan &p, const double *params, const double *data, int batch,
+                       void *coef, cudaStream_t s, int64_t *launches);
+template <typename R>
+cudaError_t plain_init_zero(void *state, int n, int batch, cudaStream_t s, int64_t *launches);
+template <typename R>
+cudaError_t plain_apply(const Plan &p, const void *coef, void *state, int batch, int dagger,
+                        cudaStream_t s, int64_t *launches);
+template <typename R>
+cudaError_t plain_expect(int n, const std::vector<DevTerm> &terms, int nobs, const void *state,
+                         int batch, double *part, double *out, cudaStream_t s, int64_t *launches);
+size_t plain_expect_part_bytes(int n, int nterms, int batch);
+cudaError_t plain_expect_finalize(const double *part, const DevTerm *d_terms, const int32_t *d_obs_ptr,
+                                  int nobs, int n, int batch, double *out, cudaStream_t s,
+                                  int64_t *launches);
+template <typename R>
+cudaError_t plain_lambda(int n, const std::vector<DevTerm> &terms, int nobs, const double *w,
+                         const void *psi, void *lam, int batch, cudaStream_t s, int64_t *launches);
+template <typename R>
+cudaError_t plain_adjoint(const Plan &p, const void *coef, const std::vector<DevTerm> &terms,
+                          int nobs, const double *row_weights, void *psi, void *lam, int batch,
+                          double *part, double *grad_params, double *grad_data,
+                          cudaStream_t s, int64_t *launches);
+size_t plain_adjoint_part_bytes(const Plan &p, int batch);
+
+// ---- whole state in shared memory (small n) --------------------------------
+size_t wsv_smem_bytes(int n, int dtype_bytes, bool grad, int ngrad_acc);
+bool wsv_supported(int n, int amp_bytes, bool grad, size_t smem_optin, int ndouble);
+// doubles the whole-state kernel keeps next to the vectors
+inline int wsv_doubles(const Plan &p, int nobs) {
+    return (p.ppr ? 0 : p.nparams) + p.nfeat + (p.ppr ? p.nparams : 0) + nobs;
+}
+template <typename R>
+cudaError_t wsv_launch(const Plan &p, const void *coef, const void *state_in, int forward,
+                       const DevTerm *d_wterms, int nterms, int nobs,
+                       const double *row_weights, int batch, void *state_out, double *expect_out,
+                       double *grad_params, double *grad_data, double *part, int nsm, cudaStream_t s,
+                       int64_t *launches);
+size_t wsv_part_bytes(const Plan &p, int nsm);
+
+// ---- uneven batch, one persistent launch ----------------------------------
+struct BatchCirc {
+    int32_t n;
+    int32_t gate0;       // first gate in the concatenated table
+    int32_t ngates;
+    int32_t param0;      // first parameter (global index)
+    int32_t nparams;
+    int32_t pad[3];
+};
+template <typename R>
+cudaError_t batch_run(const BatchCirc *d_circ, int ncirc, const int32_t *d_order,
+                      const DevGate *d_gates, const void *coef, const DevTerm *d_terms, int nterms,
+                      int nobs, int nmax, int maxparams, double *expect_out, double *grad_params,
+                      void *scratch, int *d_counter, int nsm, size_t smem_optin,
+                      cudaStream_t s, int64_t *launches);
+size_t batch_scratch_bytes(int nmax, int amp_bytes, int nsm, size_t smem_optin);
+
+}  // namespace dq

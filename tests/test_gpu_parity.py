@@ -1,0 +1,401 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle,
+element by element, on seeded inputs -- random circuits over every gate kind
+and wire position, ragged batches, both the plain per-gate path and the fused
+paths, and the five workload configurations at full size (sampled outputs or
+exact factorised references where the oracle cannot run the whole thing)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from tests.gpu_helpers import (AMP_TOL, REL_TOL, assert_amps, assert_rel, dev, factorised_amplitude,
+                               factorised_c5, factorised_reference, np_state)
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("CUDA GPU required", allow_module_level=True)
+
+import paper_2512_18995_gb300 as dq  # noqa: E402
+from paper_2512_18995_gb300 import build as dqbuild  # noqa: E402
+
+dqbuild.build()
+
+PATHS = {"plain": dq.PATH_PLAIN, "fused": dq.PATH_FUSED}
+DTYPES = {"c64": torch.complex64, "c128": torch.complex128}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = dq.Context(0)
+    yield c
+    c.close()
+
+
+def random_gates(n, depth, rng, nfeat=0, kinds=None):
+    kinds = kinds or W.GATE_KINDS
+    gates, npar = [], 0
+    while len(gates) < depth:
+        k = kinds[rng.integers(len(kinds))]
+        if k in W.TWO_QUBIT:
+            if n < 2:
+                continue
+            a, b = rng.choice(n, size=2, replace=False)
+            wires = (int(a), int(b))
+        else:
+            wires = (int(rng.integers(n)),)
+        if k in W.PARAMETRIC:
+            u = rng.random()
+            if nfeat and u < 0.25:
+                gates.append(W.Gate(k, wires, data=int(rng.integers(nfeat))))
+            elif u < 0.35:
+                gates.append(W.Gate(k, wires, angle=float(rng.uniform(-4, 4))))
+            else:
+                gates.append(W.Gate(k, wires, param=npar))
+                npar += 1
+        else:
+            gates.append(W.Gate(k, wires))
+    return gates, max(npar, 1)
+
+
+def edge_gates(n):
+    """Every kind on the extreme wires (bit 0 and bit n-1) and in both
+    control/target orders."""
+    g = []
+    hi, lo = 0, n - 1          # wire 0 = top bit, wire n-1 = bit 0
+    for q in sorted({hi, lo, n // 2}):
+        for k in ("h", "x", "y", "z", "s"):
+            g.append(W.Gate(k, (q,)))
+        for k in ("rx", "ry", "rz"):
+            g.append(W.Gate(k, (q,), angle=0.37 + q))
+    if n >= 2:
+        pairs = {(hi, lo), (lo, hi), (0, 1), (1, 0), (n - 2, n - 1), (n - 1, n - 2)}
+        for a, b in sorted(pairs):
+            for k in ("cnot", "cz", "swap"):
+                g.append(W.Gate(k, (a, b)))
+            for k in ("cp", "crx", "cry", "crz"):
+                g.append(W.Gate(k, (a, b), angle=1.1 + 0.1 * a))
+    return g
+
+
+# ---------------------------------------------------------------------------
+# random circuits: states
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("path", sorted(PATHS))
+@pytest.mark.parametrize("dtype", sorted(DTYPES))
+@pytest.mark.parametrize("n,batch", [(1, 1), (2, 3), (3, 5), (5, 33), (8, 7), (11, 3), (13, 2), (14, 3), (16, 2)])
+def test_random_circuit_states(ctx, path, dtype, n, batch):
+    ctx.set_path(PATHS[path])
+    dt = DTYPES[dtype]
+    rng = np.random.default_rng(1000 + 37 * n + batch)
+    gates, npar = random_gates(n, 8 * n + 10, rng, nfeat=3)
+    gates = edge_gates(n) + gates
+    params = rng.uniform(-4, 4, size=npar)
+    data = rng.uniform(-3, 3, size=(batch, 3))
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=3)
+    st = torch.empty((batch, 1 << n), dtype=dt, device="cuda")
+    ctx.state_init(st, n)
+    ctx.apply_circuit(circ, dev(params), st, data=dev(data))
+    ref = oracle.run(n, gates, params, data, batch=batch)
+    assert_amps(np_state(st), ref, dt)
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_apply_to_given_state_and_inverse(ctx, path):
+    ctx.set_path(PATHS[path])
+    n, batch = 9, 4
+    rng = np.random.default_rng(5)
+    gates, npar = random_gates(n, 80, rng)
+    params = rng.uniform(-4, 4, size=npar)
+    psi = rng.normal(size=(batch, 1 << n)) + 1j * rng.normal(size=(batch, 1 << n))
+    psi /= np.linalg.norm(psi, axis=1, keepdims=True)
+    st = torch.as_tensor(psi, dtype=torch.complex128, device="cuda").contiguous()
+    ctx.apply_circuit(dq.Circuit(n, gates, nparams=npar), dev(params), st)
+    ref = oracle.apply(n, gates, psi, params)
+    assert_amps(np_state(st), ref, torch.complex128)
+
+
+# ---------------------------------------------------------------------------
+# expectations
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("path", sorted(PATHS))
+@pytest.mark.parametrize("dtype", sorted(DTYPES))
+@pytest.mark.parametrize("n,batch", [(1, 2), (3, 3), (7, 5), (12, 3), (15, 2)])
+def test_expectations(ctx, path, dtype, n, batch):
+    ctx.set_path(PATHS[path])
+    dt = DTYPES[dtype]
+    rng = np.random.default_rng(77 + n)
+    N = 1 << n
+    psi = rng.normal(size=(batch, N)) + 1j * rng.normal(size=(batch, N))
+    psi /= np.linalg.norm(psi, axis=1, keepdims=True)
+    obs = []
+    for _ in range(3):
+        obs.append([(float(rng.normal()), int(rng.integers(N)), int(rng.integers(N))) for _ in range(5)])
+    obs.append(W.obs_tfim_open(n, 0.5) if n > 1 else W.obs_z(0))
+    st = torch.as_tensor(psi, dtype=dt, device="cuda").contiguous()
+    got = ctx.expect(n, dq.Observables(obs), st).cpu().numpy()
+    ref = oracle.expect(n, np_state(st), obs)
+    assert_rel(got, ref, dt, "expectations")
+
+
+# ---------------------------------------------------------------------------
+# adjoint gradients
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("path", sorted(PATHS))
+@pytest.mark.parametrize("dtype", sorted(DTYPES))
+@pytest.mark.parametrize("ppr", [False, True])
+@pytest.mark.parametrize("n,batch", [(1, 2), (4, 3), (9, 17), (12, 5), (15, 2)])
+def test_adjoint_gradients(ctx, path, dtype, ppr, n, batch):
+    ctx.set_path(PATHS[path])
+    dt = DTYPES[dtype]
+    rng = np.random.default_rng(300 + n + 7 * batch + ppr)
+    gates, npar = random_gates(n, 6 * n + 12, rng, nfeat=2)
+    params = rng.uniform(-4, 4, size=(batch, npar) if ppr else npar)
+    data = rng.uniform(-3, 3, size=(batch, 2))
+    obs = [W.obs_tfim_open(n, 0.5) if n > 1 else W.obs_z(0),
+           [(0.7, 1 % (1 << n), (1 << n) - 1), (-0.4, 0, 1)]]
+    w = rng.normal(size=(batch, 2))
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=2)
+    dobs = dq.Observables(obs)
+    st = torch.empty((batch, 1 << n), dtype=dt, device="cuda")
+    ctx.state_init(st, n)
+    ctx.apply_circuit(circ, dev(params), st, data=dev(data), params_per_row=ppr)
+    keep = st.clone()
+    gp, gd = ctx.adjoint_grad(circ, dev(params), dobs, st, data=dev(data), row_weights=dev(w),
+                              params_per_row=ppr)
+    assert torch.equal(st, keep), "state must be preserved without the clobber flag"
+    e_ref, gp_ref, gd_ref = oracle.adjoint(n, gates, obs, params, data, batch=batch, params_per_row=ppr,
+                                           row_weights=w)
+    assert_rel(gp.cpu().numpy(), gp_ref, dt, "grad params")
+    assert_rel(gd.cpu().numpy(), gd_ref, dt, "grad data")
+    # the one-call path gives the same expectations and gradients
+    e2, gp2, gd2, _ = ctx.forward_grad(circ, dev(params), dobs, batch, dt, data=dev(data), row_weights=dev(w),
+                                       params_per_row=ppr)
+    assert_rel(e2.cpu().numpy(), e_ref, dt, "expectations (forward_grad)")
+    assert_rel(gp2.cpu().numpy(), gp_ref, dt, "grad params (forward_grad)")
+    assert_rel(gd2.cpu().numpy(), gd_ref, dt, "grad data (forward_grad)")
+
+
+def test_clobber_flag_uses_state(ctx):
+    ctx.set_path(dq.PATH_PLAIN)
+    n, batch = 6, 2
+    rng = np.random.default_rng(9)
+    gates, npar = random_gates(n, 40, rng)
+    params = rng.uniform(-3, 3, size=npar)
+    circ = dq.Circuit(n, gates, nparams=npar)
+    obs = [W.obs_sum_z(n)]
+    st = torch.empty((batch, 1 << n), dtype=torch.complex128, device="cuda")
+    ctx.state_init(st, n)
+    ctx.apply_circuit(circ, dev(params), st)
+    gp, _ = ctx.adjoint_grad(circ, dev(params), dq.Observables(obs), st, clobber=True)
+    _, gp_ref, _ = oracle.adjoint(n, gates, obs, params, batch=batch)
+    assert_rel(gp.cpu().numpy(), gp_ref, torch.complex128)
+    zero = np.zeros((batch, 1 << n), complex)
+    zero[:, 0] = 1
+    assert_amps(np_state(st), zero, torch.complex128, "un-applied state")
+
+
+# ---------------------------------------------------------------------------
+# workload configurations
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_config_c1_hea10_c128(ctx, path):
+    ctx.set_path(PATHS[path])
+    wl = W.config_c1()
+    circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
+    st = torch.empty((1, 1 << wl.n), dtype=torch.complex128, device="cuda")
+    e, _, _, _ = ctx.forward_grad(circ, dev(wl.params), dq.Observables(wl.observables), 1, torch.complex128,
+                                  want_grad=False, state_out=st)
+    ref = oracle.run(wl.n, wl.gates, wl.params)
+    assert_amps(np_state(st), ref, torch.complex128)
+    assert_rel(e.cpu().numpy(), oracle.expect(wl.n, ref, wl.observables), torch.complex128)
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_config_c2_hea20_c64(ctx, path):
+    ctx.set_path(PATHS[path])
+    wl = W.config_c2()
+    circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
+    st = torch.empty((1, 1 << wl.n), dtype=torch.complex64, device="cuda")
+    e, _, _, _ = ctx.forward_grad(circ, dev(wl.params), dq.Observables(wl.observables), 1, torch.complex64,
+                                  want_grad=False, state_out=st)
+    ref = oracle.run(wl.n, wl.gates, wl.params)
+    assert_amps(np_state(st), ref, torch.complex64)
+    assert_rel(e.cpu().numpy(), oracle.expect(wl.n, ref, wl.observables), torch.complex64)
+    assert abs(torch.linalg.vector_norm(st.to(torch.complex128)).item() - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_config_c3_qml_batch(ctx, path):
+    ctx.set_path(PATHS[path])
+    wl = W.config_c3()
+    circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams, nfeatures=wl.nfeatures)
+    e, gp, gd, _ = ctx.forward_grad(circ, dev(wl.params), dq.Observables(wl.observables), wl.batch,
+                                    torch.complex64, data=dev(wl.data))
+    e_ref, gp_ref, gd_ref = oracle.adjoint(wl.n, wl.gates, wl.observables, wl.params, wl.data, batch=wl.batch)
+    assert_rel(e.cpu().numpy(), e_ref, torch.complex64, "per-sample <Z0>")
+    assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, "grad params (batch sum)")
+    assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, "grad data")
+
+
+def test_config_c4_uneven_batch(ctx):
+    circs = W.config_c4(1024)
+    obs = [W.obs_zz01_x0()]
+    dcs = [dq.Circuit(n, g, nparams=len(a)) for n, g, a in circs]
+    params = np.concatenate([a for _, _, a in circs])
+    offs = np.cumsum([0] + [len(a) for _, _, a in circs])
+    e, gp = ctx.batch_forward_grad(dcs, dev(params), dq.Observables(obs), torch.complex64)
+    e = e.cpu().numpy()
+    gp = gp.cpu().numpy()
+    # sampled circuits: every 16th plus every 16-qubit one
+    pick = sorted(set(range(0, 1024, 16)) | {i for i, c in enumerate(circs) if c[0] == 16})
+    for i in pick:
+        n, g, a = circs[i]
+        er, gr, _ = oracle.adjoint(n, g, obs, a)
+        assert_rel(e[i], er[0], torch.complex64, f"circuit {i} expectation")
+        assert_rel(gp[offs[i]:offs[i + 1]], gr, torch.complex64, f"circuit {i} gradient")
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+@pytest.mark.parametrize("n", [14, 17])
+def test_config_c5_structure_reduced(ctx, path, n):
+    """QFT + 10 layers + TFIM at reduced n, compared in full with the oracle."""
+    ctx.set_path(PATHS[path])
+    wl = W.config_c5(n)
+    circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
+    st = torch.empty((1, 1 << n), dtype=torch.complex64, device="cuda")
+    e, gp, _, _ = ctx.forward_grad(circ, dev(wl.params), dq.Observables(wl.observables), 1, torch.complex64,
+                                   state_out=st)
+    e_ref, gp_ref, _ = oracle.adjoint(n, wl.gates, wl.observables, wl.params)
+    assert_amps(np_state(st), oracle.run(n, wl.gates, wl.params), torch.complex64)
+    assert_rel(e.cpu().numpy(), e_ref, torch.complex64, "TFIM energy")
+    assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, "TFIM gradient")
+
+
+@pytest.mark.parametrize("path", ["fused"])
+def test_config_c5_full_size_factorised(ctx, path):
+    """30 qubits, 1380 gates, 600 params, three resident vectors: the ring is
+    split into three interleaved 10-qubit rings so the exact answer is a
+    product the oracle computes from 10-qubit pieces."""
+    ctx.set_path(PATHS[path])
+    n = 30
+    wl, rings = factorised_c5(n)
+    energy, grad, states = factorised_reference(oracle, n, rings, wl)
+    circ = dq.Circuit(n, wl.gates, nparams=wl.nparams)
+    st = torch.empty((1, 1 << n), dtype=torch.complex64, device="cuda")
+    e, gp, _, _ = ctx.forward_grad(circ, dev(wl.params), dq.Observables(wl.observables), 1, torch.complex64,
+                                   state_out=st)
+    assert_rel(e.cpu().numpy(), [energy], torch.complex64, "energy")
+    assert_rel(gp.cpu().numpy(), grad, torch.complex64, "gradient")
+    rng = np.random.default_rng(30)
+    idx = np.concatenate([[0, (1 << n) - 1], rng.integers(0, 1 << n, size=400)])
+    got = st.view(-1)[torch.as_tensor(idx, device="cuda")].cpu().numpy().astype(np.complex128)
+    ref = np.array([factorised_amplitude(n, rings, states, int(b)) for b in idx])
+    assert_amps(got, ref, torch.complex64, "sampled amplitudes")
+    assert np.max(np.abs(got - ref)) <= 1e-3 * np.max(np.abs(ref))
+    del st
+    torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------
+# autograd boundary
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,budget", [(10, None), (15, None), (15, 0)])
+def test_autograd_function(ctx, n, budget):
+    ctx.set_path(dq.PATH_AUTO)
+    rng = np.random.default_rng(n)
+    batch = 6
+    gates = W.encode_layer(n) + W.hea_layers(n, 2)
+    npar = 4 * n
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=n)
+    obs = [W.obs_z(0), W.obs_tfim_open(n, 0.5)]
+    params = torch.tensor(rng.uniform(0, 6, npar), device="cuda", requires_grad=True)
+    data = torch.tensor(rng.uniform(-3, 3, (batch, n)), device="cuda", requires_grad=True)
+    wts = torch.tensor(rng.normal(size=(batch, 2)), device="cuda")
+    e = dq.expectation(circ, params, dq.Observables(obs), data=data, context=ctx, memory_budget=budget)
+    (e * wts).sum().backward()
+    e_ref, gp_ref, gd_ref = oracle.adjoint(n, gates, obs, params.detach().cpu().numpy(),
+                                           data.detach().cpu().numpy(), batch=batch,
+                                           row_weights=wts.cpu().numpy())
+    assert_rel(e.detach().cpu().numpy(), e_ref, torch.complex64)
+    assert_rel(params.grad.cpu().numpy(), gp_ref, torch.complex64)
+    assert_rel(data.grad.cpu().numpy(), gd_ref, torch.complex64)
+
+
+# ---------------------------------------------------------------------------
+# edge cases and validation
+# ---------------------------------------------------------------------------
+def test_empty_and_degenerate(ctx):
+    ctx.set_path(dq.PATH_AUTO)
+    st = torch.empty((0, 8), dtype=torch.complex64, device="cuda")
+    ctx.apply_circuit(dq.Circuit(3, [W.Gate("h", (0,))]), None, st)       # batch 0: no-op
+    st = torch.empty((2, 8), dtype=torch.complex64, device="cuda")
+    ctx.state_init(st, 3)
+    ctx.apply_circuit(dq.Circuit(3, []), None, st)                           # no gates
+    ref = np.zeros((2, 8))
+    ref[:, 0] = 1
+    assert_amps(np_state(st), ref, torch.complex64)
+    e, gp, _, _ = ctx.forward_grad(dq.Circuit(3, [], nparams=0), None, dq.Observables([W.obs_z(2)]), 2,
+                                   torch.complex64)
+    assert np.allclose(e.cpu().numpy(), 1.0)
+    e = ctx.expect(3, dq.Observables([[]]), st)                              # empty observable
+    assert np.allclose(e.cpu().numpy(), 0.0)
+
+
+@pytest.mark.parametrize("bad", ["wire", "same", "kind", "param", "data_missing", "fixed_angle_param",
+                                 "reserved", "dtype", "null_state", "misaligned"])
+def test_invalid_arguments_are_rejected(ctx, bad):
+    n = 4
+    st = torch.empty((1, 16), dtype=torch.complex64, device="cuda")
+    ctx.state_init(st, n)
+    before = st.clone()
+    params = dev(np.zeros(2))
+    gates = [W.Gate("h", (0,))]
+    circ_kw = {}
+    state = st
+    if bad == "wire":
+        gates = [W.Gate("h", (4,))]
+    elif bad == "same":
+        gates = [W.Gate("cnot", (1, 1))]
+    elif bad == "kind":
+        gates = [(99, (0,), -1, -1, 0.0)]
+    elif bad == "param":
+        gates = [W.Gate("rx", (0,), param=5)]
+        circ_kw = {"nparams": 2}
+    elif bad == "data_missing":
+        gates = [W.Gate("rx", (0,), data=0)]
+        circ_kw = {"nfeatures": 1}
+    elif bad == "fixed_angle_param":
+        gates = [W.Gate("h", (0,), param=0)]
+        circ_kw = {"nparams": 1}
+    circ = dq.Circuit(n, gates, **circ_kw)
+    if bad == "reserved":
+        circ._arr[0].reserved = 3
+    with pytest.raises(dq.DQError) as ei:
+        if bad == "dtype":
+            ctx.lib.dq_state_init(ctx.h, n, 1, 7, st.data_ptr(), None) and ctx._check(7 and 1, "x")
+            ctx._check(ctx.lib.dq_state_init(ctx.h, n, 1, 7, st.data_ptr(), None), "state_init")
+        elif bad == "null_state":
+            ctx._check(ctx.lib.dq_apply_circuit(ctx.h, circ.ref(), None, 0, None, None, 1, 0, None), "apply")
+        elif bad == "misaligned":
+            ctx._check(ctx.lib.dq_apply_circuit(ctx.h, circ.ref(), None, 0, None, st.data_ptr() + 8, 1, 0, None),
+                       "apply")
+        else:
+            ctx.apply_circuit(circ, params if bad != "data_missing" else params, state)
+    assert ei.value.status == 1
+    torch.cuda.synchronize()
+    assert torch.equal(st, before), "nothing may be launched on invalid input"
+
+
+def test_launch_counter_counts_kernels(ctx):
+    ctx.set_path(dq.PATH_PLAIN)
+    n = 8
+    gates = [W.Gate("h", (q,)) for q in range(n)]
+    st = torch.empty((1, 1 << n), dtype=torch.complex64, device="cuda")
+    c0 = ctx.launch_count
+    ctx.state_init(st, n)
+    ctx.apply_circuit(dq.Circuit(n, gates), None, st)
+    assert ctx.launch_count - c0 == 1 + 1 + n      # init, bind, one sweep per gate

@@ -1,0 +1,146 @@
+"""CPU-only checks of the C ABI library and the input generators (no GPU
+compute: loading, exported symbols, struct layouts, host-side validation
+reachable without a device)."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dq.h")
+
+
+@pytest.fixture(scope="module")
+def libdq():
+    from paper_2512_18995_gb300 import build
+    build.build()
+    from paper_2512_18995_gb300 import _lib
+    return _lib.load_library()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^DQ_API\s+[\w\s\*]+?\b(dq_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("dq_state_init", "dq_apply_circuit", "dq_expect", "dq_adjoint_grad"):
+        assert required in names
+    assert len(names) >= 15
+
+
+def test_library_exports_every_declared_symbol(libdq):
+    out = subprocess.run(["nm", "-D", "--defined-only", libdq._name], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (dq_\w+)", out))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    for s in declared_symbols():
+        assert hasattr(libdq, s)
+
+
+def test_binding_exports_list_matches_header():
+    from paper_2512_18995_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == declared_symbols()
+
+
+def test_struct_layouts_match_header():
+    """Compile a probe against dq.h and compare sizes/offsets with ctypes."""
+    from paper_2512_18995_gb300 import _lib
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "dq.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(dq_gate), offsetof(dq_gate, angle), offsetof(dq_gate, param_idx),
+         sizeof(dq_circuit), offsetof(dq_circuit, gates), offsetof(dq_circuit, nfeatures));
+  printf("%zu %zu %zu %zu\n", sizeof(dq_pauli_term), sizeof(dq_observables),
+         offsetof(dq_observables, term_offsets), offsetof(dq_observables, terms));
+  printf("%d %d %d %d\n", (int)DQ_CRZ, (int)DQ_SWAP, (int)DQ_NUM_GATE_KINDS, (int)DQ_ERR_TIMEOUT);
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "probe.c")
+        exe = os.path.join(d, "probe")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), c, "-o", exe])
+        lines = subprocess.check_output([exe], text=True).split("\n")
+    a = list(map(int, lines[0].split()))
+    assert a == [ctypes.sizeof(_lib.dq_gate), _lib.dq_gate.angle.offset, _lib.dq_gate.param_idx.offset,
+                 ctypes.sizeof(_lib.dq_circuit), _lib.dq_circuit.gates.offset, _lib.dq_circuit.nfeatures.offset]
+    b = list(map(int, lines[1].split()))
+    assert b == [ctypes.sizeof(_lib.dq_pauli_term), ctypes.sizeof(_lib.dq_observables),
+                 _lib.dq_observables.term_offsets.offset, _lib.dq_observables.terms.offset]
+    k = list(map(int, lines[2].split()))
+    assert k == [_lib.KIND["crz"], _lib.KIND["swap"], len(_lib.KIND), 5]
+
+
+def test_context_creation_fails_cleanly_without_device(libdq):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = libdq.dq_ctx_create(ctypes.byref(h), 0)
+    assert st != 0 and not h.value
+    assert libdq.dq_ctx_launch_count(None) == 0
+
+
+def test_null_context_is_rejected(libdq):
+    from paper_2512_18995_gb300 import _lib
+    c = _lib.Circuit(2, [W.Gate("h", (0,))])
+    st = libdq.dq_apply_circuit(None, c.ref(), None, 0, None, None, 1, 0, None)
+    assert st == 1   # DQ_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------------------
+# input generators
+# ---------------------------------------------------------------------------
+def test_splitmix64_reference_value():
+    # First output of splitmix64 seeded with 0 (the generator's published
+    # reference stream).
+    assert W.SplitMix64(0).next_u64() == 0xE220A8397B1DCDAF
+
+
+def test_uniform_ranges_and_determinism():
+    a = W.uniform_array(7, 1000, -np.pi, np.pi)
+    b = W.uniform_array(7, 1000, -np.pi, np.pi)
+    assert np.array_equal(a, b)
+    assert a.min() >= -np.pi and a.max() < np.pi
+    assert abs(a.mean()) < 0.3
+
+
+def test_config_shapes():
+    c1, c2, c3, c5 = W.config_c1(), W.config_c2(), W.config_c3(), W.config_c5()
+    assert (c1.n, len(c1.gates), c1.nparams) == (10, 120, 80)
+    assert (c2.n, len(c2.gates), c2.nparams) == (20, 480, 320)
+    assert (c3.n, len(c3.gates), c3.nparams, c3.data.shape) == (12, 228, 144, (4096, 12))
+    assert (c5.n, len(c5.gates), c5.nparams) == (30, 1380, 600)
+    assert np.all((c1.params >= 0) & (c1.params < 2 * np.pi))
+    assert np.all((c3.data >= -np.pi) & (c3.data < np.pi))
+    qft = W.qft_gates(30)
+    assert sum(g.kind == "h" for g in qft) == 30
+    assert sum(g.kind == "cp" for g in qft) == 435
+    assert sum(g.kind == "swap" for g in qft) == 15
+
+
+def test_uneven_batch_generator():
+    circs = W.config_c4(1024)
+    ns = np.array([c[0] for c in circs])
+    ds = np.array([len(c[1]) for c in circs])
+    assert ns.min() == 8 and ns.max() == 16
+    assert ds.min() >= 10 and ds.max() <= 40
+    kinds = {g.kind for c in circs for g in c[1]}
+    assert kinds == {"h", "rx", "ry", "rz", "cnot", "cz"}
+    for n, gates, angles in circs[:50]:
+        for g in gates:
+            assert all(0 <= w < n for w in g.wires)
+            if len(g.wires) == 2:
+                assert g.wires[0] != g.wires[1]
+        assert len(angles) == sum(g.param >= 0 for g in gates)
