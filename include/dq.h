@@ -158,6 +158,11 @@ DQ_API dq_status dq_workspace_bytes(dq_ctx *ctx, const dq_circuit *circuit,
                              const dq_observables *obs, int batch, int dtype,
                              size_t *out);
 
+/* Bytes of workspace that dq_batch_forward_grad needs for these circuits
+ * and dtype, written to *out. */
+DQ_API dq_status dq_batch_workspace_bytes(dq_ctx *ctx, int ncirc, const dq_circuit *circuits,
+                                          int dtype, size_t *out);
+
 /* Synchronise `stream` and report device-side failures recorded by earlier
  * calls (DQ_ERR_TIMEOUT for a bounded wait that gave up), then clear them. */
 DQ_API dq_status dq_ctx_check(dq_ctx *ctx, void *stream);

@@ -54,7 +54,7 @@ class dq_observables(ctypes.Structure):
 
 
 EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path", "dq_ctx_set_workspace",
-           "dq_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_tracing",
+           "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_tracing",
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
            "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune")
 
@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH):
         "dq_ctx_set_path": ([P, I], I),
         "dq_ctx_set_workspace": ([P, P, ctypes.c_size_t], I),
         "dq_workspace_bytes": ([P, C, O, I, I, ctypes.POINTER(ctypes.c_size_t)], I),
+        "dq_batch_workspace_bytes": ([P, I, C, I, ctypes.POINTER(ctypes.c_size_t)], I),
         "dq_ctx_check": ([P, P], I),
         "dq_ctx_launch_count": ([P], ctypes.c_int64),
         "dq_ctx_set_tracing": ([P, I], I),
@@ -243,12 +244,16 @@ class Context:
             out[buf.value.decode()] = (int(cnt.value), float(ms.value))
         return out
 
-    def ensure_workspace(self, circuit: Optional[Circuit], obs: Optional[Observables], batch: int, dtype: int):
-        if circuit is None:
-            circuit = Circuit(1, [])
-        need = ctypes.c_size_t(0)
-        self._check(self.lib.dq_workspace_bytes(self.h, circuit.ref(), obs.ref() if obs else None, int(batch),
-                                                int(dtype), ctypes.byref(need)), "dq_workspace_bytes")
+    def ensure_workspace(self, circuit: Optional[Circuit], obs: Optional[Observables], batch: int, dtype: int,
+                         need_bytes: Optional[int] = None):
+        if need_bytes is None:
+            if circuit is None:
+                circuit = Circuit(1, [])
+            need = ctypes.c_size_t(0)
+            self._check(self.lib.dq_workspace_bytes(self.h, circuit.ref(), obs.ref() if obs else None, int(batch),
+                                                    int(dtype), ctypes.byref(need)), "dq_workspace_bytes")
+        else:
+            need = ctypes.c_size_t(int(need_bytes))
         if self._ws is None or self._ws.numel() < need.value:
             self._ws = None
             self._check(self.lib.dq_ctx_set_workspace(self.h, None, 0), "dq_ctx_set_workspace")
@@ -343,6 +348,11 @@ class Context:
         if not want_grad:
             grad_params = None
         self._keep = (arr, offs)
+        need = ctypes.c_size_t(0)
+        self._check(self.lib.dq_batch_workspace_bytes(self.h, nc, ctypes.cast(arr, ctypes.POINTER(dq_circuit)),
+                                                      dtype_code(dtype), ctypes.byref(need)),
+                    "dq_batch_workspace_bytes")
+        self.ensure_workspace(None, None, 0, dtype_code(dtype), need_bytes=need.value)
         self._check(self.lib.dq_batch_forward_grad(self.h, nc, ctypes.cast(arr, ctypes.POINTER(dq_circuit)),
                                                    _ptr(params), offs, obs.ref(), dtype_code(dtype),
                                                    _ptr(expect_out), _ptr(grad_params), _stream()),

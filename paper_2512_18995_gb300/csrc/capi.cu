@@ -761,6 +761,29 @@ dq_status dq_workspace_bytes(dq_ctx *ctx, const dq_circuit *circuit, const dq_ob
     return DQ_OK;
 }
 
+dq_status dq_batch_workspace_bytes(dq_ctx *ctx, int ncirc, const dq_circuit *circuits, int dtype, size_t *out) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if (!out) return fail(ctx, DQ_ERR_INVALID_ARG, "out is NULL");
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (ncirc < 0 || (ncirc > 0 && !circuits)) return fail(ctx, DQ_ERR_INVALID_ARG, "bad circuit array");
+    int nmax = 1;
+    int64_t ngates = 0;
+    for (int c = 0; c < ncirc; ++c) {
+        if ((st = check_n(ctx, circuits[c].nqubits)) != DQ_OK) return st;
+        nmax = std::max(nmax, circuits[c].nqubits);
+        ngates += std::max(0, circuits[c].ngates);
+    }
+    const size_t mat = dtype == DQ_C128 ? sizeof(Mat2<double>) : sizeof(Mat2<float>);
+    Arena a;
+    a.measuring = true;
+    a.take(mat * (size_t)(ngates + 1));
+    a.take(batch_scratch_bytes(nmax, amp_bytes(dtype), ctx->nsm, ctx->smem_optin));
+    a.take(256);
+    *out = a.used;
+    return DQ_OK;
+}
+
 dq_status dq_state_init(dq_ctx *ctx, int nqubits, int batch, int dtype, void *state, void *stream) {
     dq_status st = check_ctx(ctx);
     if (st != DQ_OK) return st;

@@ -8,8 +8,10 @@ import workloads as W
 
 # Tolerances (BASELINE targets): amplitudes max-abs 1e-5 (c64) / 1e-12
 # (c128); expectations and gradients 1e-4 relative (c64) / 1e-12 (c128),
-# relative to max(|ref|, max-norm of the reference vector) so that entries
-# near zero are judged on the vector's scale.
+# relative to max(|ref|, max-norm of the reference vector, floor).  The floor
+# is the natural scale of the quantity (sum of |coefficients| for an
+# expectation, times sum of |row weights| for a gradient), so that a vector
+# that is analytically zero is judged on that scale, not on rounding noise.
 AMP_TOL = {torch.complex64: 1e-5, torch.complex128: 1e-12}
 REL_TOL = {torch.complex64: 1e-4, torch.complex128: 1e-12}
 
@@ -21,12 +23,16 @@ def assert_amps(got, ref, dtype, what="state"):
     return err
 
 
-def assert_rel(got, ref, dtype, what="value"):
+def obs_scale(observables):
+    return max(sum(abs(t[0]) for t in o) for o in observables) if observables else 1.0
+
+
+def assert_rel(got, ref, dtype, what="value", floor=0.0):
     got = np.asarray(got, dtype=np.float64).reshape(-1)
     ref = np.asarray(ref, dtype=np.float64).reshape(-1)
     if ref.size == 0:
         return 0.0
-    scale = np.maximum(np.abs(ref), np.max(np.abs(ref)))
+    scale = np.maximum(np.maximum(np.abs(ref), np.max(np.abs(ref))), floor)
     scale = np.where(scale == 0, 1.0, scale)
     rel = np.abs(got - ref) / scale
     worst = float(np.max(rel))
