@@ -255,6 +255,41 @@ DQ_API dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit 
                                 double *expect_out, double *grad_params,
                                 void *stream);
 
+/* Allocation-free variant of dq_forward_grad, for callers that must not
+ * allocate device memory at call time -- for example a serving loop that
+ * reserves all its memory at start-up because cudaMalloc/cudaFree can stall
+ * the whole device, or a host application whose own allocator owns the GPU's
+ * memory budget.  It takes no context and calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The paper has no counterpart to this entry
+ * point.
+ *
+ * It runs the on-chip path (every row's state and adjoint vector held in one
+ * CTA's shared memory), so it accepts only circuits for which that path
+ * applies (about 13 qubits for complex64, 12 for complex128) and returns
+ * DQ_ERR_UNSUPPORTED otherwise.  Its scratch (gate tables, bound gate
+ * coefficients, Pauli terms and per-CTA gradient partials) is a fixed
+ * static device array of DQ_NOALLOC_SCRATCH_BYTES bytes that every GPU that
+ * loads the library holds until the process exits; a call needing more
+ * returns DQ_ERR_UNSUPPORTED with the required size in `err`.
+ *
+ * The first call on each device looks up that array's device address (with
+ * that device current), so make that first call before any stream capture.
+ * All calls on a device share the one array and it keeps the last call's
+ * contents, so two calls whose work overlaps on the GPU (different streams,
+ * or host threads) race: serialise them, e.g. on one stream.
+ *
+ * Arguments are those of dq_forward_grad (expect_out, grad_params and
+ * grad_data may each be NULL), without a context and without state_out; the
+ * current CUDA device is used.  err (may be NULL) receives a message of up to
+ * err_len bytes on failure. */
+#define DQ_NOALLOC_SCRATCH_BYTES (8u << 20)
+DQ_API dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const double *params,
+                                         int params_per_row, const double *data,
+                                         const dq_observables *obs, const double *row_weights,
+                                         int batch, int dtype, double *expect_out,
+                                         double *grad_params, double *grad_data, void *stream,
+                                         char *err, size_t err_len);
+
 /* Time the fused-path variants (fusion width k and tile schedule) for this
  * circuit shape on `state` (device, batch rows, contents destroyed) and
  * cache the fastest for later calls with the same circuit structure.

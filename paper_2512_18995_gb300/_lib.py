@@ -56,7 +56,8 @@ class dq_observables(ctypes.Structure):
 EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path", "dq_ctx_set_workspace",
            "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_tracing",
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
-           "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune")
+           "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
+           "dq_forward_grad_noalloc")
 
 _lib = None
 
@@ -94,6 +95,7 @@ def load_library(path: str = LIB_PATH):
         "dq_forward_grad": ([P, C, P, I, P, O, P, I, I, P, P, P, P, P], I),
         "dq_batch_forward_grad": ([P, I, C, P, ctypes.POINTER(ctypes.c_int64), O, I, P, P, P], I),
         "dq_plan_autotune": ([P, C, I, I, P, P], I),
+        "dq_forward_grad_noalloc": ([C, P, I, P, O, P, I, I, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -365,3 +367,29 @@ class Context:
         self.ensure_workspace(circuit, None, batch, dt)
         self._check(self.lib.dq_plan_autotune(self.h, circuit.ref(), int(batch), dt, _ptr(state), _stream()),
                     "dq_plan_autotune")
+
+
+def forward_grad_noalloc(circuit: Circuit, params: Optional[torch.Tensor], obs: Observables, batch: int,
+                         dtype: torch.dtype = torch.complex64, data: Optional[torch.Tensor] = None,
+                         row_weights: Optional[torch.Tensor] = None, params_per_row: bool = False,
+                         expect_out: Optional[torch.Tensor] = None, grad_params: Optional[torch.Tensor] = None,
+                         grad_data: Optional[torch.Tensor] = None):
+    """Call dq_forward_grad_noalloc: the whole on-chip hot path without any
+    device allocation inside the library (scratch is a static device array).
+    Output tensors are supplied by the caller (allocated here if None)."""
+    lib = load_library()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if expect_out is None:
+        expect_out = torch.empty((batch, obs.nobs), dtype=torch.float64, device=dev)
+    if grad_params is None and circuit.nparams > 0:
+        shape = (batch, circuit.nparams) if params_per_row else (circuit.nparams,)
+        grad_params = torch.empty(shape, dtype=torch.float64, device=dev)
+    if grad_data is None and circuit.nfeatures > 0 and data is not None:
+        grad_data = torch.empty((batch, circuit.nfeatures), dtype=torch.float64, device=dev)
+    err = ctypes.create_string_buffer(256)
+    st = lib.dq_forward_grad_noalloc(circuit.ref(), _ptr(params), int(params_per_row), _ptr(data), obs.ref(),
+                                     _ptr(row_weights), int(batch), dtype_code(dtype), _ptr(expect_out),
+                                     _ptr(grad_params), _ptr(grad_data), _stream(), err, 256)
+    if st != DQ_OK:
+        raise DQError(st, f"dq_forward_grad_noalloc: {err.value.decode()}")
+    return expect_out, grad_params, grad_data

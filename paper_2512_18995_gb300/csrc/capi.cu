@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -1040,3 +1041,179 @@ dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch, in
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free entry point (dq_forward_grad_noalloc).
+//
+// Scratch is one static device array per GPU.  Host code must not use the
+// symbol's name as an address: it is a host-side stand-in.  The device
+// address is looked up once per device with cudaGetSymbolAddress (with that
+// device current) and passed to the kernels.
+// ===========================================================================
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DQ_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+dq_status noalloc_fail(char *err, size_t len, dq_status st, const char *fmt, ...) {
+    if (err && len) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(err, len, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+// Device address of the static scratch array on the current device.
+dq_status noalloc_scratch(int dev, void **out, char *err, size_t len) {
+    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(err, len, DQ_ERR_UNSUPPORTED, "device %d", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return noalloc_fail(err, len, DQ_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return DQ_OK;
+}
+
+}  // namespace
+
+extern "C" dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const double *params, int params_per_row,
+                                             const double *data, const dq_observables *obs,
+                                             const double *row_weights, int batch, int dtype, double *expect_out,
+                                             double *grad_params, double *grad_data, void *stream, char *err,
+                                             size_t err_len) {
+    if (err && err_len) err[0] = 0;
+    if (dtype != DQ_C64 && dtype != DQ_C128) return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "unknown dtype");
+    if (batch < 0) return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "batch < 0");
+    if (!circuit) return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "circuit is NULL");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(err, err_len, DQ_ERR_CUDA, "no current device");
+    // Validate and translate with a throw-away context-free helper context
+    // (only its error string is used; nothing is allocated on the device).
+    dq_ctx scratch_ctx;
+    std::vector<DevGate> gates;
+    std::vector<BindGate> bind;
+    int ncs = 0, ncr = 0;
+    const int ppr = params_per_row ? 1 : 0;
+    dq_status st = compile_gates(&scratch_ctx, circuit, ppr, gates, bind, 0, &ncs, &ncr, false);
+    if (st != DQ_OK) return noalloc_fail(err, err_len, st, "%s", scratch_ctx.err.c_str());
+    const int n = circuit->nqubits;
+    // observables (validated like dq_expect), kept in wire space for the on-chip kernel
+    std::vector<DevTerm> wterms;
+    int nobs = 1;
+    if (obs) {
+        if (obs->nobs < 1 || !obs->term_offsets || obs->term_offsets[0] != 0)
+            return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "malformed observables");
+        nobs = obs->nobs;
+        const uint64_t allowed = (uint64_t(1) << n) - 1;
+        for (int o = 0; o < nobs; ++o) {
+            if (obs->term_offsets[o + 1] < obs->term_offsets[o])
+                return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "term_offsets must be non-decreasing");
+            for (int k = obs->term_offsets[o]; k < obs->term_offsets[o + 1]; ++k) {
+                const dq_pauli_term &t = obs->terms[k];
+                if ((t.xmask | t.zmask) & ~allowed)
+                    return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "term %d acts on a wire >= %d", k, n);
+                DevTerm w{};
+                w.f = t.xmask;
+                w.s = t.zmask;
+                w.nY = __builtin_popcountll(t.xmask & t.zmask);
+                w.obs = o;
+                w.coeff = t.coeff;
+                wterms.push_back(w);
+            }
+        }
+    } else if (expect_out || grad_params || grad_data) {
+        return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "expectations or gradients need observables");
+    }
+    if (batch == 0) return DQ_OK;
+    bool needp = false, needd = false;
+    for (const BindGate &b : bind) {
+        needp |= b.pidx >= 0;
+        needd |= b.didx >= 0;
+    }
+    if (needp && !params) return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "params is NULL");
+    if (needd && !data) return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "data is NULL");
+    if (grad_params && circuit->nparams == 0) grad_params = nullptr;
+    if (grad_data && circuit->nfeatures == 0) grad_data = nullptr;
+
+    Plan p;
+    p.n = n;
+    p.ngates = circuit->ngates;
+    p.nparams = circuit->nparams;
+    p.nfeat = circuit->nfeatures;
+    p.ppr = ppr;
+    p.ncoef_shared = ncs;
+    p.ncoef_rows = ncr;
+    int nsm = 0, optin = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return noalloc_fail(err, err_len, DQ_ERR_CUDA, "cannot query device %d", dev);
+    const bool grad = grad_params || grad_data;
+    const int amp = amp_bytes(dtype);
+    if (!wsv_supported(n, amp, grad, (size_t)optin, wsv_doubles(p, nobs)))
+        return noalloc_fail(err, err_len, DQ_ERR_UNSUPPORTED,
+                            "%d qubits do not fit the on-chip path of this entry point", n);
+    // carve the static array
+    Arena a;
+    a.measuring = true;
+    a.take(sizeof(DevGate) * (size_t)std::max(1, p.ngates));
+    a.take(sizeof(BindGate) * (size_t)std::max(1, p.ngates));
+    a.take(sizeof(DevTerm) * (size_t)std::max<size_t>(1, wterms.size()));
+    a.take(coef_bytes(p, batch, dtype));
+    a.take(wsv_part_bytes(p, nsm));
+    if (a.used > DQ_NOALLOC_SCRATCH_BYTES)
+        return noalloc_fail(err, err_len, DQ_ERR_UNSUPPORTED,
+                            "this call needs %zu bytes of scratch; the static limit is %u bytes", a.used,
+                            (unsigned)DQ_NOALLOC_SCRATCH_BYTES);
+    void *base = nullptr;
+    if ((st = noalloc_scratch(dev, &base, err, err_len)) != DQ_OK) return st;
+    Arena w;
+    w.base = (char *)base;
+    w.cap = DQ_NOALLOC_SCRATCH_BYTES;
+    p.d_gates = (DevGate *)w.take(sizeof(DevGate) * (size_t)std::max(1, p.ngates));
+    p.d_bind = (BindGate *)w.take(sizeof(BindGate) * (size_t)std::max(1, p.ngates));
+    DevTerm *d_terms = (DevTerm *)w.take(sizeof(DevTerm) * (size_t)std::max<size_t>(1, wterms.size()));
+    void *coef = w.take(coef_bytes(p, batch, dtype));
+    double *part = (double *)w.take(wsv_part_bytes(p, nsm));
+    cudaStream_t s = (cudaStream_t)stream;
+    // Tables are copied on the caller's stream, so back-to-back calls on one
+    // stream never see each other's contents.
+    if (p.ngates > 0) {
+        if (cudaMemcpyAsync(p.d_gates, gates.data(), sizeof(DevGate) * gates.size(), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(p.d_bind, bind.data(), sizeof(BindGate) * bind.size(), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess)
+            return noalloc_fail(err, err_len, DQ_ERR_CUDA, "copying gate tables: %s",
+                                cudaGetErrorString(cudaGetLastError()));
+    }
+    if (!wterms.empty() &&
+        cudaMemcpyAsync(d_terms, wterms.data(), sizeof(DevTerm) * wterms.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+        return noalloc_fail(err, err_len, DQ_ERR_CUDA, "copying terms: %s", cudaGetErrorString(cudaGetLastError()));
+    Tracer *saved = g_tracer;
+    g_tracer = nullptr;
+    int64_t launches = 0;
+    cudaError_t e = cudaSuccess;
+    if (dtype == DQ_C64) {
+        if (p.ngates > 0) e = plain_bind<float>(p, params, data, batch, coef, s, &launches);
+        if (e == cudaSuccess)
+            e = wsv_launch<float>(p, coef, nullptr, 1, d_terms, (int)wterms.size(), nobs, row_weights, batch, nullptr,
+                                  expect_out, grad_params, grad_data, part, nsm, s, &launches);
+    } else {
+        if (p.ngates > 0) e = plain_bind<double>(p, params, data, batch, coef, s, &launches);
+        if (e == cudaSuccess)
+            e = wsv_launch<double>(p, coef, nullptr, 1, d_terms, (int)wterms.size(), nobs, row_weights, batch,
+                                   nullptr, expect_out, grad_params, grad_data, part, nsm, s, &launches);
+    }
+    g_tracer = saved;
+    if (e != cudaSuccess) return noalloc_fail(err, err_len, DQ_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+    return DQ_OK;
+}
