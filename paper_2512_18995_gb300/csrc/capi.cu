@@ -542,7 +542,8 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
                 "fused forward+adjoint");
         return DQ_OK;
     }
-    // Large states: prepare, evolve, measure, then the adjoint sweep.
+    // Large states: prepare, evolve (fused tiles when possible), measure,
+    // then the adjoint sweep.
     const bool tile = use_fused(ctx) && tile_supported(p.n, (int)sizeof(cx<R>));
     Arena a;
     a.measuring = true;
@@ -551,10 +552,9 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     if (grad) {
         a.take(sbytes);                      // lambda
         if (state_out) a.take(sbytes);       // working copy of psi (state_out preserved)
-        a.take(tile ? tile_adjoint_part_bytes(p, batch) : plain_adjoint_part_bytes(p, batch));
+        a.take(plain_adjoint_part_bytes(p, batch));
     }
-    if (o) a.take(tile ? tile_expect_part_bytes(p.n, (int)o->bits.size(), batch)
-                       : plain_expect_part_bytes(p.n, (int)o->bits.size(), batch));
+    if (o) a.take(plain_expect_part_bytes(p.n, (int)o->bits.size(), batch));
     if (tile) a.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>)));
     dq_status st = reserve(ctx, a.used);
     if (st != DQ_OK) return st;
@@ -568,11 +568,10 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     if (grad) {
         lam = w.take(sbytes);
         if (state_out) work = w.take(sbytes);
-        gpart = (double *)w.take(tile ? tile_adjoint_part_bytes(p, batch) : plain_adjoint_part_bytes(p, batch));
+        gpart = (double *)w.take(plain_adjoint_part_bytes(p, batch));
     }
     double *epart = nullptr;
-    if (o) epart = (double *)w.take(tile ? tile_expect_part_bytes(p.n, (int)o->bits.size(), batch)
-                                         : plain_expect_part_bytes(p.n, (int)o->bits.size(), batch));
+    if (o) epart = (double *)w.take(plain_expect_part_bytes(p.n, (int)o->bits.size(), batch));
     void *tws = tile ? w.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>))) : nullptr;
     DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
     DQ_CUDA(plain_init_zero<R>(psi, p.n, batch, s, &ctx->launches), "init");
@@ -583,27 +582,14 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
         DQ_CUDA(plain_apply<R>(p, coef, psi, batch, 0, s, &ctx->launches), "plain apply");
     }
     if (o && eo) {
-        if (tile) {
-            DQ_CUDA(tile_expect<R>(ctx->tiles, p.n, o->bits, o->d_bits, o->d_ptr, o->nobs, psi, batch, epart, eo,
-                                   tws, ctx->nsm, s, &ctx->launches),
-                    "tiled expect");
-        } else {
-            DQ_CUDA(plain_expect<R>(p.n, o->bits, o->nobs, psi, batch, epart, eo, s, &ctx->launches), "expect");
-            DQ_CUDA(plain_expect_finalize(epart, o->d_bits, o->d_ptr, o->nobs, p.n, batch, eo, s, &ctx->launches),
-                    "expect finalize");
-        }
+        DQ_CUDA(plain_expect<R>(p.n, o->bits, o->nobs, psi, batch, epart, eo, s, &ctx->launches), "expect");
+        DQ_CUDA(plain_expect_finalize(epart, o->d_bits, o->d_ptr, o->nobs, p.n, batch, eo, s, &ctx->launches),
+                "expect finalize");
     }
     if (grad) {
         if (work != psi) DQ_CUDA(cudaMemcpyAsync(work, psi, sbytes, cudaMemcpyDeviceToDevice, s), "copy state");
-        if (tile) {
-            DQ_CUDA(tile_adjoint<R>(ctx->tiles, ctx->tuned, p, coef, o->bits, o->nobs, rw, work, lam, batch, gpart,
-                                    gp, gd, tws, ctx->nsm, s, &ctx->launches),
-                    "tiled adjoint");
-        } else {
-            DQ_CUDA(plain_adjoint<R>(p, coef, o->bits, o->nobs, rw, work, lam, batch, gpart, gp, gd, s,
-                                     &ctx->launches),
-                    "plain adjoint");
-        }
+        DQ_CUDA(plain_adjoint<R>(p, coef, o->bits, o->nobs, rw, work, lam, batch, gpart, gp, gd, s, &ctx->launches),
+                "plain adjoint");
     }
     return DQ_OK;
 }
@@ -632,6 +618,7 @@ dq_status dq_ctx_create(dq_ctx **out, int device) {
     c->smem_optin = prop.sharedMemPerBlockOptin;
     if (cudaMalloc((void **)&c->d_flag, 256) != cudaSuccess) return DQ_ERR_OOM;
     if (cudaMemset(c->d_flag, 0, 256) != cudaSuccess) return DQ_ERR_CUDA;
+    c->tiles.errflag = c->d_flag;
     *out = c.release();
     return DQ_OK;
 }

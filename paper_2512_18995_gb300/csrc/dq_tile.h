@@ -1,4 +1,11 @@
 // Fused k-qubit tiles staged in shared memory by TMA (internal interface).
+//
+// A pass loads, for every value of the amplitude-index bits outside a set T
+// of k bit positions (the tile), the 2^k amplitudes that differ only in T,
+// applies every scheduled gate whose non-diagonal bits lie in T (diagonal
+// factors and controls may sit anywhere), and stores the tile back: one HBM
+// read and write of the state for many gates.  T always contains the lowest
+// bits, so every TMA box row is a contiguous run of memory.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -11,17 +18,61 @@
 
 namespace dq {
 
+constexpr int kTileMaxK = 14;
+constexpr int kTileLaneBits = 5;      // local bits 0..4 live across the 32 lanes of a warp
+constexpr int kTileMaxOps = 384;      // operations per pass (bounds the shared-memory program)
+
+// One in-tile operation.  32 bytes.
+struct TOp {
+    int8_t cls;      // GateClass (SWAP is lowered to three CNOTs)
+    int8_t tl;       // target local bit (-1: outside the tile, diagonal only)
+    int8_t cl;       // control local bit (-1: none or outside the tile)
+    int8_t hasc;     // 1 when controlled
+    int16_t kind;    // dq_gate_kind (gradient generator)
+    int16_t pad;
+    int32_t tg;      // target amplitude bit
+    int32_t cg;      // control amplitude bit (-1: none)
+    int32_t coef;    // Mat2 index (row 0)
+    int32_t rowstep; // Mat2 row stride
+    int32_t slot;    // gradient slot or -1
+    int32_t pad2;
+};
+
+// A run of operations executed with one register layout: register bit i of
+// a thread holds local bit B[i].
+struct TSeg {
+    int32_t op0, nops;
+    int8_t B[8];
+};
+
+struct TPass {
+    std::vector<int> T;     // tile bits, ascending (amplitude bits)
+    int seg0 = 0, nseg = 0; // into the schedule's segment array
+    int op0 = 0, nops = 0;  // into the schedule's op array
+};
+
+struct TileSchedule {
+    int n = 0, k = 0, low = 0, M = 0;
+    std::vector<TPass> passes;
+    std::vector<TOp> ops;
+    std::vector<TSeg> segs;
+    TOp *d_ops = nullptr;
+    TSeg *d_segs = nullptr;
+    void release();
+};
+
 // Autotuned configuration for one circuit structure.
 struct TileTune {
     int k = 0;          // tile qubits (0 = default)
     int low = 0;        // always-resident low bits
 };
 
-// Host-side cache of fused-pass schedules and the driver entry point used to
-// encode TMA descriptors.
+// Host-side cache of schedules and the driver entry point used to encode
+// TMA descriptors.
 struct TileCache {
     void *encode_fn = nullptr;
-    std::unordered_map<uint64_t, void *> schedules;
+    int *errflag = nullptr;             // device error flag of the owning context
+    std::unordered_map<uint64_t, TileSchedule *> schedules;
     void release();
 };
 
@@ -47,5 +98,8 @@ template <typename R>
 cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
                           const void *coef, void *state, int batch, void *tws, int nsm, cudaStream_t s,
                           int64_t *launches);
+
+// Host planner (exposed for tests of the schedule logic).
+bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, TileSchedule &out);
 
 }  // namespace dq

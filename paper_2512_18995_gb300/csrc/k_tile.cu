@@ -1,20 +1,776 @@
-// Fused k-qubit tiles staged in shared memory by TMA.
+// Fused k-qubit tiles staged in shared memory by TMA, with an in-register
+// gate engine.
+//
+// Planner (host): gates are packed into passes.  A pass owns a tile bit set T
+// (the lowest `low` bits plus the non-diagonal bits of its gates, at most k
+// bits, at most five TMA box dimensions).  A gate may join the current pass
+// when its non-diagonal bits fit in T and it commutes with every gate that
+// was deferred to a later pass (on each shared bit both act diagonally);
+// otherwise it is deferred and blocks its bits.  SWAP becomes three CNOTs.
+//
+// Kernel (device): one launch per pass, persistent CTAs over contiguous tile
+// ranges.  Thread 0 streams tiles in and out with cp.async.bulk.tensor (two
+// shared-memory buffers, mbarrier completion, bounded waits).  Inside a tile
+// the 2^k amplitudes live in registers: lanes carry local bits 0..4, each
+// thread holds 2^M amplitudes over M "register bits" B, warps carry the rest.
+// Gates on register bits are register arithmetic, gates on lane bits use warp
+// shuffles, diagonal gates on any bit are per-element phases, and controls
+// anywhere are predicates.  Shared memory is touched only to change B.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "dq_common.cuh"
 #include "dq_tile.h"
 
 namespace dq {
 
-void TileCache::release() { schedules.clear(); }
+void TileSchedule::release() {
+    cudaFree(d_ops);
+    cudaFree(d_segs);
+    d_ops = nullptr;
+    d_segs = nullptr;
+}
 
-bool tile_supported(int, int) { return false; }
+void TileCache::release() {
+    for (auto &kv : schedules) {
+        kv.second->release();
+        delete kv.second;
+    }
+    schedules.clear();
+}
+
+namespace {
+
+template <typename R> struct TileCfg;
+template <> struct TileCfg<float> { static constexpr int M = 5; static constexpr int wb = 0; };
+template <> struct TileCfg<double> { static constexpr int M = 4; static constexpr int wb = 1; };
+
+inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
+
+// Number of TMA box dimensions the bit set needs (runs of consecutive word
+// bits, each at most 8 bits wide because a box side is at most 256).
+int dims_needed(uint64_t T, int wb) {
+    uint64_t w = (T << wb) | ((uint64_t(1) << wb) - 1);
+    int dims = 0;
+    int b = 0;
+    while (w >> b) {
+        if (!((w >> b) & 1)) { ++b; continue; }
+        int len = 0;
+        while ((w >> (b + len)) & 1) ++len;
+        dims += (len + 7) / 8;
+        b += len;
+    }
+    return dims;
+}
+
+struct GateBits {
+    uint64_t N;   // bits acted on non-diagonally
+    uint64_t D;   // bits acted on diagonally (controls, diagonal targets)
+};
+
+GateBits gate_bits(const DevGate &g) {
+    GateBits gb{0, 0};
+    if (g.cls == CLS_SWAP) {
+        gb.N = (uint64_t(1) << g.t) | (uint64_t(1) << g.c);
+    } else if (g.cls == CLS_DIAG) {
+        gb.D = uint64_t(1) << g.t;
+        if (g.c >= 0) gb.D |= uint64_t(1) << g.c;
+    } else {
+        gb.N = uint64_t(1) << g.t;
+        if (g.c >= 0) gb.D = uint64_t(1) << g.c;
+    }
+    return gb;
+}
+
+}  // namespace
+
+bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, TileSchedule &out) {
+    const int n = p.n;
+    const int wb = amp_bytes == 16 ? 1 : 0;
+    if (k > n || k < kTileLaneBits + M || low < kTileLaneBits || low > k) return false;
+    out = TileSchedule();
+    out.n = n;
+    out.k = k;
+    out.low = low;
+    out.M = M;
+    const uint64_t lowmask = (uint64_t(1) << low) - 1;
+    std::vector<int> remaining(p.ngates);
+    for (int i = 0; i < p.ngates; ++i) remaining[i] = i;
+    int guard = 0;
+    while (!remaining.empty()) {
+        if (++guard > p.ngates + 2) return false;
+        uint64_t T = lowmask, bnd = 0, bany = 0;
+        std::vector<int> sched, deferred;
+        int nops = 0;
+        for (int gi : remaining) {
+            const DevGate &g = p.gates[gi];
+            const GateBits gb = gate_bits(g);
+            const int cost = g.cls == CLS_SWAP ? 3 : 1;
+            bool ok = !(gb.N & bany) && !(gb.D & bnd) && nops + cost <= kTileMaxOps;
+            if (ok) {
+                const uint64_t nt = T | gb.N;
+                if (popc64(nt) <= k && dims_needed(nt, wb) <= 5) {
+                    T = nt;
+                    sched.push_back(gi);
+                    nops += cost;
+                    continue;
+                }
+            }
+            deferred.push_back(gi);
+            bnd |= gb.N;
+            bany |= gb.N | gb.D;
+        }
+        if (sched.empty()) return false;
+        // pad T to exactly k bits without exceeding five box dimensions
+        for (int b = 0; b < n && popc64(T) < k; ++b) {
+            if ((T >> b) & 1) continue;
+            const uint64_t nt = T | (uint64_t(1) << b);
+            if (dims_needed(nt, wb) <= 5) T = nt;
+        }
+        if (popc64(T) != k) return false;
+        TPass pass;
+        int loc[64];
+        for (int b = 0, j = 0; b < n; ++b) {
+            loc[b] = -1;
+            if ((T >> b) & 1) {
+                pass.T.push_back(b);
+                loc[b] = j++;
+            }
+        }
+        pass.op0 = (int)out.ops.size();
+        auto push_op = [&](int cls, int tb, int cb, const DevGate &g, int slot) {
+            TOp o{};
+            o.cls = (int8_t)cls;
+            o.tl = (int8_t)loc[tb];
+            o.cl = (int8_t)(cb >= 0 ? loc[cb] : -1);
+            o.hasc = cb >= 0 ? 1 : 0;
+            o.kind = (int16_t)g.kind;
+            o.tg = tb;
+            o.cg = cb;
+            o.coef = g.coef;
+            o.rowstep = g.rowstep;
+            o.slot = slot;
+            out.ops.push_back(o);
+        };
+        for (int gi : sched) {
+            const DevGate &g = p.gates[gi];
+            const int slot = gi < (int)p.slot_of_gate.size() ? p.slot_of_gate[gi] : -1;
+            if (g.cls == CLS_SWAP) {
+                push_op(CLS_ANTI, g.c, g.t, g, -1);
+                push_op(CLS_ANTI, g.t, g.c, g, -1);
+                push_op(CLS_ANTI, g.c, g.t, g, -1);
+            } else {
+                push_op(g.cls, g.t, g.c, g, slot);
+            }
+        }
+        pass.nops = (int)out.ops.size() - pass.op0;
+        // register layouts
+        pass.seg0 = (int)out.segs.size();
+        std::vector<int> B;
+        int sop0 = pass.op0;
+        auto close_seg = [&](int end) {
+            TSeg sg{};
+            sg.op0 = sop0;
+            sg.nops = end - sop0;
+            std::vector<int> full = B;
+            for (int j = kTileLaneBits; j < k && (int)full.size() < M; ++j)
+                if (std::find(full.begin(), full.end(), j) == full.end()) full.push_back(j);
+            for (int i = 0; i < 8; ++i) sg.B[i] = i < M ? (int8_t)full[i] : (int8_t)-1;
+            out.segs.push_back(sg);
+        };
+        for (int i = pass.op0; i < pass.op0 + pass.nops; ++i) {
+            const TOp &o = out.ops[i];
+            const int need = (o.cls != CLS_DIAG && o.tl >= kTileLaneBits) ? o.tl : -1;
+            if (need < 0 || std::find(B.begin(), B.end(), need) != B.end()) continue;
+            if ((int)B.size() < M) {
+                B.push_back(need);
+                continue;
+            }
+            close_seg(i);
+            sop0 = i;
+            B.assign(1, need);
+        }
+        close_seg(pass.op0 + pass.nops);
+        pass.nseg = (int)out.segs.size() - pass.seg0;
+        out.passes.push_back(pass);
+        remaining.swap(deferred);
+    }
+    return true;
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// TMA descriptor for one pass
+// ---------------------------------------------------------------------------
+struct TileDims {
+    int rank = 0;
+    int rlen[5] = {0, 0, 0, 0, 0};   // log2 box side (word bits)
+    int glen[5] = {0, 0, 0, 0, 0};   // gap bits after the run (tile-index bits of this dim)
+    int s[5] = {0, 0, 0, 0, 0};      // first word bit of the dim
+};
+
+bool make_dims(const std::vector<int> &T, int n, int wb, TileDims &d) {
+    std::vector<int> w;
+    for (int i = 0; i < wb; ++i) w.push_back(i);
+    for (int t : T) w.push_back(t + wb);
+    const int W = n + wb;
+    // runs split into chunks of at most 8 bits
+    std::vector<std::pair<int, int>> runs;   // (start, len)
+    size_t i = 0;
+    while (i < w.size()) {
+        size_t j = i;
+        while (j + 1 < w.size() && w[j + 1] == w[j] + 1) ++j;
+        int st = w[i], len = (int)(j - i + 1);
+        while (len > 0) {
+            const int l = std::min(8, len);
+            runs.push_back({st, l});
+            st += l;
+            len -= l;
+        }
+        i = j + 1;
+    }
+    if (runs.empty() || runs.size() > 5 || runs[0].first != 0) return false;
+    d.rank = (int)runs.size();
+    for (int r = 0; r < d.rank; ++r) {
+        d.s[r] = runs[r].first;
+        d.rlen[r] = runs[r].second;
+        const int next = (r + 1 < d.rank) ? runs[r + 1].first : W;
+        d.glen[r] = next - runs[r].first - runs[r].second;
+    }
+    return true;
+}
+
+bool encode_map(void *fn, CUtensorMap *map, const TileDims &d, void *base, int64_t batch, int wb) {
+    cuuint64_t dims[5];
+    cuuint64_t strides[4];
+    cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+    uint64_t stride = 8;   // bytes of one 8-byte word
+    for (int r = 0; r < 5; ++r) {
+        if (r < d.rank) {
+            const int width = d.rlen[r] + d.glen[r];
+            uint64_t size = uint64_t(1) << width;
+            if (r == d.rank - 1) size *= (uint64_t)batch;
+            dims[r] = size;
+            box[r] = 1u << d.rlen[r];
+            if (r > 0) strides[r - 1] = stride;
+            stride <<= width;
+        } else {
+            dims[r] = 1;
+            box[r] = 1;
+            strides[r - 1] = stride;
+        }
+    }
+    (void)wb;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    CUresult res = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return res == CUDA_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// device helpers: mbarrier and TMA
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of the barrier for at most ~2 s of wall time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (global_ns() - t0 > 2000000000ull) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load5(void *dst, const CUtensorMap *map, const int c[5], uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store5(const CUtensorMap *map, const int c[5], const void *src) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(smem_u32(src))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// in-register engine
+// ---------------------------------------------------------------------------
+struct Layout {
+    uint32_t tb;          // this thread's local index with register bits zero
+    uint64_t posB;        // 4 bits per local bit: register position, 15 = not a register bit
+    uint32_t off[8];      // local offset of register bit i
+};
+
+__device__ __forceinline__ Layout make_layout(const TSeg &sg, int M, int k, int lane, int warp) {
+    Layout L;
+    L.posB = ~0ull;
+    uint32_t inB = 0;
+    for (int i = 0; i < M; ++i) {
+        const int b = sg.B[i];
+        L.off[i] = 1u << b;
+        inB |= 1u << b;
+        L.posB &= ~(uint64_t(15) << (4 * b));
+        L.posB |= uint64_t(i) << (4 * b);
+    }
+    uint32_t tb = (uint32_t)lane;
+    int wi = 0;
+    for (int b = kTileLaneBits; b < k; ++b) {
+        if ((inB >> b) & 1) continue;
+        tb |= (uint32_t)((warp >> wi) & 1) << b;
+        ++wi;
+    }
+    L.tb = tb;
+    return L;
+}
+
+template <int M>
+__device__ __forceinline__ uint32_t reg_off(const Layout &L, int e) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+        if ((e >> i) & 1) o |= L.off[i];
+    return o;
+}
+
+// Value of local bit j for register element e.
+__device__ __forceinline__ int lbit(const Layout &L, int j, int e) {
+    const int pb = (int)((L.posB >> (4 * j)) & 15);
+    return pb < 15 ? ((e >> pb) & 1) : (int)((L.tb >> j) & 1);
+}
+
+template <typename R, int M>
+__device__ __forceinline__ void regs_load(cx<R> (&a)[1 << M], const cx<R> *buf, const Layout &L) {
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) a[e] = buf[L.tb | reg_off<M>(L, e)];
+}
+
+template <typename R, int M>
+__device__ __forceinline__ void regs_store(const cx<R> (&a)[1 << M], cx<R> *buf, const Layout &L) {
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) buf[L.tb | reg_off<M>(L, e)] = a[e];
+}
+
+// Control predicate of an op for element e: (mode, where)
+//   hasc == 0: always true.
+//   control outside the tile: tile-uniform value cu.
+//   control local: lbit.
+struct Ctl {
+    int mode;     // 0 none, 1 uniform (value in u), 2 local bit j
+    int j;
+    int u;
+};
+
+__device__ __forceinline__ bool ctl_of(const Ctl &c, const Layout &L, int e) {
+    return c.mode == 0 ? true : (c.mode == 1 ? c.u != 0 : lbit(L, c.j, e) != 0);
+}
+
+template <typename R, int M, int P, int CLS>
+__device__ __forceinline__ void pair_op(cx<R> (&a)[1 << M], const Mat2<R> &u, const Ctl &c, const Layout &L) {
+#pragma unroll
+    for (int e0 = 0; e0 < (1 << M); ++e0) {
+        if (e0 & (1 << P)) continue;
+        if (ctl_of(c, L, e0)) apply2<R, CLS>(u, a[e0], a[e0 | (1 << P)]);
+    }
+}
+
+template <typename R, int M, int CLS>
+__device__ __forceinline__ void pair_op_at(int p, cx<R> (&a)[1 << M], const Mat2<R> &u, const Ctl &c,
+                                           const Layout &L) {
+    switch (p) {
+    case 0: pair_op<R, M, 0, CLS>(a, u, c, L); break;
+    case 1: pair_op<R, M, 1, CLS>(a, u, c, L); break;
+    case 2: pair_op<R, M, 2, CLS>(a, u, c, L); break;
+    case 3: pair_op<R, M, 3, CLS>(a, u, c, L); break;
+    default:
+        if constexpr (M > 4) pair_op<R, M, (M > 4 ? 4 : 0), CLS>(a, u, c, L);
+        break;
+    }
+}
+
+template <typename T> __device__ __forceinline__ T shfl_x(T v, int m);
+template <> __device__ __forceinline__ float2 shfl_x<float2>(float2 v, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+template <> __device__ __forceinline__ double2 shfl_x<double2>(double2 v, int m) {
+    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// Gate on lane bit j: partner amplitude lives in lane ^ (1 << j).
+template <typename R, int M, int CLS>
+__device__ __forceinline__ void lane_op(cx<R> (&a)[1 << M], const Mat2<R> &u, int j, int lane, const Ctl &c,
+                                        const Layout &L) {
+    const bool hi = (lane >> j) & 1;
+    const cx<R> cs = hi ? u.m[3] : u.m[0];
+    const cx<R> cp = hi ? u.m[2] : u.m[1];
+    const int m = 1 << j;
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) {
+        const cx<R> p = shfl_x(a[e], m);
+        if (!ctl_of(c, L, e)) continue;
+        if (CLS == CLS_ANTI) {
+            a[e] = p;
+        } else if (CLS == CLS_REAL) {
+            const R s0 = cs.x, s1 = cp.x;
+            a[e] = mk<R>(s0 * a[e].x + s1 * p.x, s0 * a[e].y + s1 * p.y);
+        } else {
+            a[e] = cadd(cmul(cs, a[e]), cmul(cp, p));
+        }
+    }
+}
+
+// Diagonal gate: element factor m0 / m3 by the target bit value.
+template <typename R, int M>
+__device__ __forceinline__ void diag_op(cx<R> (&a)[1 << M], const Mat2<R> &u, const TOp &o, uint64_t base,
+                                        const Ctl &c, const Layout &L) {
+    const int tu = o.tl < 0 ? (int)((base >> o.tg) & 1) : -1;
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) {
+        if (!ctl_of(c, L, e)) continue;
+        const int t = tu >= 0 ? tu : lbit(L, o.tl, e);
+        a[e] = cmul(t ? u.m[3] : u.m[0], a[e]);
+    }
+}
+
+template <typename R, int M>
+__device__ __forceinline__ void apply_op(cx<R> (&a)[1 << M], const TOp &o, const Mat2<R> &u, uint64_t base,
+                                         const Layout &L, int lane) {
+    Ctl c;
+    c.mode = 0;
+    c.j = 0;
+    c.u = 1;
+    if (o.hasc) {
+        if (o.cl < 0) {
+            c.mode = 1;
+            c.u = (int)((base >> o.cg) & 1);
+            if (!c.u) return;   // tile-uniform: nothing to do
+        } else {
+            c.mode = 2;
+            c.j = o.cl;
+        }
+    }
+    if (o.cls == CLS_DIAG) {
+        diag_op<R, M>(a, u, o, base, c, L);
+        return;
+    }
+    if (o.tl < kTileLaneBits) {
+        switch (o.cls) {
+        case CLS_ANTI: lane_op<R, M, CLS_ANTI>(a, u, o.tl, lane, c, L); break;
+        case CLS_REAL: lane_op<R, M, CLS_REAL>(a, u, o.tl, lane, c, L); break;
+        default: lane_op<R, M, CLS_GENERAL>(a, u, o.tl, lane, c, L); break;
+        }
+        return;
+    }
+    const int p = (int)((L.posB >> (4 * o.tl)) & 15);
+    switch (o.cls) {
+    case CLS_ANTI: pair_op_at<R, M, CLS_ANTI>(p, a, u, c, L); break;
+    case CLS_REAL: pair_op_at<R, M, CLS_REAL>(p, a, u, c, L); break;
+    default: pair_op_at<R, M, CLS_GENERAL>(p, a, u, c, L); break;
+    }
+}
+
+struct TileKArgs {
+    const TOp *ops;
+    const TSeg *segs;
+    int op0, nops, seg0, nseg;
+    const void *coef;
+    int n, k, wb;
+    int64_t ntiles;
+    int rank;
+    int rlen[5], glen[5], s[5];
+    int *errflag;
+};
+
+__device__ __forceinline__ void tile_coords(const TileKArgs &a, int64_t t, int c[5], uint64_t &base, int64_t &row) {
+    uint64_t rem = (uint64_t)t;
+    uint64_t word = 0;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        c[r] = 0;
+        if (r < a.rank) {
+            uint64_t v;
+            if (r < a.rank - 1) {
+                v = rem & ((uint64_t(1) << a.glen[r]) - 1);
+                rem >>= a.glen[r];
+            } else {
+                v = rem;
+            }
+            const uint64_t coord = v << a.rlen[r];
+            c[r] = (int)coord;
+            word |= coord << a.s[r];
+        }
+    }
+    const uint64_t amp = word >> a.wb;
+    row = (int64_t)(amp >> a.n);
+    base = amp & ((uint64_t(1) << a.n) - 1);
+}
+
+constexpr int kTileThreadsMax = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(kTileThreadsMax, 1)
+k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
+    constexpr int M = TileCfg<R>::M;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t tbytes = sizeof(cx<R>) << a.k;
+    cx<R> *buf0 = reinterpret_cast<cx<R> *>(smem);
+    cx<R> *buf1 = reinterpret_cast<cx<R> *>(smem + tbytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * tbytes);
+    TOp *sops = reinterpret_cast<TOp *>(smem + 2 * tbytes + 64);
+    TSeg *ssegs = reinterpret_cast<TSeg *>(sops + a.nops);
+    Mat2<R> *scoef = reinterpret_cast<Mat2<R> *>(ssegs + a.nseg);
+    const Mat2<R> *gcoef = reinterpret_cast<const Mat2<R> *>(a.coef);
+    for (int i = tid; i < a.nops; i += blockDim.x) {
+        sops[i] = a.ops[a.op0 + i];
+        scoef[i] = gcoef[sops[i].coef];
+    }
+    for (int i = tid; i < a.nseg; i += blockDim.x) ssegs[i] = a.segs[a.seg0 + i];
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_async_smem();
+    }
+    __syncthreads();
+    const int64_t per = (a.ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t1 = min(a.ntiles, t0 + per);
+    if (t0 >= t1) return;
+    int c[5];
+    uint64_t base;
+    int64_t row;
+    if (tid == 0) {
+        tile_coords(a, t0, c, base, row);
+        mbar_expect_tx(&bar[0], (uint32_t)tbytes);
+        tma_load5(buf0, &tmap, c, &bar[0]);
+    }
+    uint32_t phase0 = 0, phase1 = 0;
+    cx<R> r[1 << M];
+    bool failed = false;
+    for (int64_t t = t0, i = 0; t < t1; ++t, ++i) {
+        const int b = (int)(i & 1);
+        cx<R> *cur = b ? buf1 : buf0;
+        if (tid == 0 && t + 1 < t1) {
+            int cn[5];
+            uint64_t bn;
+            int64_t rn;
+            tile_coords(a, t + 1, cn, bn, rn);
+            bulk_wait_read0();   // the other buffer's previous store has read its data
+            uint64_t *nb = b ? &bar[0] : &bar[1];
+            mbar_expect_tx(nb, (uint32_t)tbytes);
+            tma_load5(b ? buf0 : buf1, &tmap, cn, nb);
+        }
+        const bool ok = mbar_wait_bounded(b ? &bar[1] : &bar[0], b ? phase1 : phase0);
+        if (b) phase1 ^= 1; else phase0 ^= 1;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        tile_coords(a, t, c, base, row);
+        for (int si = 0; si < a.nseg; ++si) {
+            const TSeg sg = ssegs[si];
+            const Layout L = make_layout(sg, M, a.k, lane, warp);
+            regs_load<R, M>(r, cur, L);
+            for (int oi = sg.op0 - a.op0; oi < sg.op0 - a.op0 + sg.nops; ++oi) {
+                const TOp o = sops[oi];
+                const Mat2<R> u = o.rowstep ? gcoef[o.coef + row * o.rowstep] : scoef[oi];
+                apply_op<R, M>(r, o, u, base, L, lane);
+            }
+            // each thread writes back exactly the addresses it read in this
+            // layout; the barrier orders them before the next layout's reads
+            regs_store<R, M>(r, cur, L);
+            __syncthreads();
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tma_store5(&tmap, c, cur);
+            bulk_commit();
+        }
+    }
+    if (failed && tid == 0) {
+        atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
+        // let any load still in flight land before the CTA exits (bounded)
+        mbar_wait_bounded(&bar[0], phase0);
+        mbar_wait_bounded(&bar[1], phase1);
+    }
+    if (tid == 0) bulk_wait0();
+}
+
+size_t tile_smem_bytes(int k, int amp, int nops, int nseg) {
+    return 2 * ((size_t)amp << k) + 64 + (size_t)nops * sizeof(TOp) + (size_t)nseg * sizeof(TSeg) +
+           (size_t)nops * (amp == 8 ? sizeof(Mat2<float>) : sizeof(Mat2<double>)) + 64;
+}
+
+uint64_t sched_key(const Plan &p, int k, int low, int amp) {
+    uint64_t h = p.key ^ 0x9E3779B97F4A7C15ull;
+    h = (h ^ (uint64_t)k) * 1099511628211ull;
+    h = (h ^ (uint64_t)low) * 1099511628211ull;
+    h = (h ^ (uint64_t)amp) * 1099511628211ull;
+    return h;
+}
+
+bool ensure_encode_fn(TileCache &tc) {
+    if (tc.encode_fn) return true;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return false;
+    }
+    tc.encode_fn = fn;
+    return true;
+}
+
+template <typename R>
+void default_tile(int n, int &k, int &low) {
+    constexpr int M = TileCfg<R>::M;
+    const int kmax = std::min(M + 8, sizeof(R) == 4 ? 13 : 12);   // at most 256 threads per CTA
+    k = std::min(kmax, std::max(kTileLaneBits + M, n - 9));
+    low = std::min(k - 1, 7);
+}
+
+TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, int amp) {
+    const uint64_t key = sched_key(p, k, low, amp);
+    auto it = tc.schedules.find(key);
+    if (it != tc.schedules.end()) return it->second;
+    TileSchedule *s = new TileSchedule();
+    if (!tile_build_schedule(p, k, low, M, amp, *s)) {
+        delete s;
+        return nullptr;
+    }
+    if (cudaMalloc((void **)&s->d_ops, sizeof(TOp) * std::max<size_t>(1, s->ops.size())) != cudaSuccess ||
+        cudaMalloc((void **)&s->d_segs, sizeof(TSeg) * std::max<size_t>(1, s->segs.size())) != cudaSuccess) {
+        s->release();
+        delete s;
+        return nullptr;
+    }
+    cudaMemcpy(s->d_ops, s->ops.data(), sizeof(TOp) * s->ops.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(s->d_segs, s->segs.data(), sizeof(TSeg) * s->segs.size(), cudaMemcpyHostToDevice);
+    tc.schedules[key] = s;
+    return s;
+}
+
+template <typename R>
+cudaError_t run_forward(TileCache &tc, const Plan &p, const TileSchedule &sc, const void *coef, void *state,
+                        int batch, int nsm, cudaStream_t s, int64_t *launches) {
+    constexpr int M = TileCfg<R>::M;
+    constexpr int wb = TileCfg<R>::wb;
+    const int amp = (int)sizeof(cx<R>);
+    const int threads = 1 << (sc.k - M);
+    for (const TPass &ps : sc.passes) {
+        TileDims d;
+        if (!make_dims(ps.T, p.n, wb, d)) return cudaErrorInvalidValue;
+        CUtensorMap map;
+        if (!encode_map(tc.encode_fn, &map, d, state, batch, wb)) return cudaErrorInvalidValue;
+        TileKArgs a;
+        a.ops = sc.d_ops;
+        a.segs = sc.d_segs;
+        a.op0 = ps.op0;
+        a.nops = ps.nops;
+        a.seg0 = ps.seg0;
+        a.nseg = ps.nseg;
+        a.coef = coef;
+        a.n = p.n;
+        a.k = sc.k;
+        a.wb = wb;
+        a.ntiles = (int64_t)batch << (p.n - sc.k);
+        a.rank = d.rank;
+        for (int r = 0; r < 5; ++r) {
+            a.rlen[r] = d.rlen[r];
+            a.glen[r] = d.glen[r];
+            a.s[r] = d.s[r];
+        }
+        a.errflag = tc.errflag;
+        const size_t smem = tile_smem_bytes(sc.k, amp, ps.nops, ps.nseg);
+        cudaError_t e = cudaFuncSetAttribute(k_tile_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_fwd<R>, threads, smem);
+        per_sm = std::max(1, per_sm);
+        const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)per_sm * nsm);
+        LaunchScope ls(s, "k_tile_fwd", launches);
+        k_tile_fwd<R><<<(unsigned)grid, threads, smem, s>>>(map, a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+bool tile_supported(int n, int amp_bytes) {
+    const int M = amp_bytes == 8 ? TileCfg<float>::M : TileCfg<double>::M;
+    return n >= kTileLaneBits + M + 1 && n <= 34;
+}
 size_t tile_workspace_bytes(const Plan &, int, int) { return 0; }
 size_t tile_adjoint_part_bytes(const Plan &, int) { return 0; }
 size_t tile_expect_part_bytes(int, int, int) { return 0; }
 
 template <typename R>
-cudaError_t tile_apply(TileCache &, std::unordered_map<uint64_t, TileTune> &, const Plan &, const void *, void *,
-                       int, void *, int, cudaStream_t, int64_t *) {
-    return cudaErrorNotSupported;
+cudaError_t tile_apply(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
+                       const void *coef, void *state, int batch, void *tws, int nsm, cudaStream_t s,
+                       int64_t *launches) {
+    (void)tws;
+    if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
+    int k, low;
+    default_tile<R>(p.n, k, low);
+    auto it = tuned.find(p.key ^ (sizeof(R) == 8 ? 1ull : 0ull));
+    if (it != tuned.end() && it->second.k) {
+        k = it->second.k;
+        low = it->second.low;
+    }
+    TileSchedule *sc = get_schedule(tc, p, k, low, TileCfg<R>::M, (int)sizeof(cx<R>));
+    if (!sc) return cudaErrorNotSupported;
+    return run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches);
 }
+
 template <typename R>
 cudaError_t tile_expect(TileCache &, int, const std::vector<DevTerm> &, const DevTerm *, const int32_t *, int,
                         const void *, int, double *, double *, void *, int, cudaStream_t, int64_t *) {
@@ -26,9 +782,49 @@ cudaError_t tile_adjoint(TileCache &, std::unordered_map<uint64_t, TileTune> &, 
                          double *, double *, void *, int, cudaStream_t, int64_t *) {
     return cudaErrorNotSupported;
 }
+
 template <typename R>
-cudaError_t tile_autotune(TileCache &, std::unordered_map<uint64_t, TileTune> &, const Plan &, const void *,
-                          void *, int, void *, int, cudaStream_t, int64_t *) {
+cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
+                          const void *coef, void *state, int batch, void *tws, int nsm, cudaStream_t s,
+                          int64_t *launches) {
+    (void)tws;
+    if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
+    constexpr int M = TileCfg<R>::M;
+    const int kmax = std::min(std::min(p.n - 1, M + 8), sizeof(R) == 4 ? 13 : 12);
+    float best = 1e30f;
+    TileTune bt;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Tracer *saved = g_tracer;
+    g_tracer = nullptr;
+    for (int k = kTileLaneBits + M; k <= kmax; ++k) {
+        for (int low : {5, 7}) {
+            if (low > k - 1) continue;
+            TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>));
+            if (!sc) continue;
+            cudaError_t err = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches);   // warm
+            if (err != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 3; ++rep) run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bt.k = k;
+                bt.low = low;
+            }
+        }
+    }
+    g_tracer = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bt.k) tuned[p.key ^ (sizeof(R) == 8 ? 1ull : 0ull)] = bt;
     return cudaSuccess;
 }
 
