@@ -368,6 +368,56 @@ def batched_grads(ctx, device, steps=5):
     return out
 
 
+def profile_case(args):
+    """Run one kernel family's workload a few times (for ncu captures): no
+    JSON line, a one-line timing summary only."""
+    import torch
+    import paper_2512_18995_gb300 as dq
+    from paper_2512_18995_gb300 import build as dqbuild
+    dqbuild.build()
+    dev = torch.device("cuda:0")
+    ctx = dq.Context(0)
+    iters = args.warmup + args.steps
+    t0 = time.perf_counter()
+    if args.profile_case == "tile":          # C2 forward on the fused tile path
+        wl = W.config_c2()
+        ctx.set_path(dq.PATH_FUSED)
+        circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
+        obs = dq.Observables(wl.observables)
+        params = torch.tensor(wl.params, device=dev)
+        st = torch.empty((1, 1 << wl.n), dtype=torch.complex64, device=dev)
+        for _ in range(iters):
+            ctx.forward_grad(circ, params, obs, 1, torch.complex64, want_grad=False, state_out=st)
+    elif args.profile_case == "wsv":         # C3 fused forward + adjoint
+        wl = W.config_c3()
+        ctx.set_path(dq.PATH_FUSED)
+        circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams, nfeatures=wl.nfeatures)
+        obs = dq.Observables(wl.observables)
+        params = torch.tensor(wl.params, device=dev)
+        data = torch.tensor(wl.data, device=dev)
+        for _ in range(iters):
+            ctx.forward_grad(circ, params, obs, wl.batch, torch.complex64, data=data)
+    elif args.profile_case == "sweep":       # one-qubit sweeps on a 2 GiB state
+        n = 28
+        ctx.set_path(dq.PATH_PLAIN)
+        st = torch.empty((1, 1 << n), dtype=torch.complex64, device=dev)
+        ctx.state_init(st, n)
+        circ = dq.Circuit(n, [W.Gate("ry", (q,), angle=0.3) for q in (0, 7, 14, 21, 27)])
+        for _ in range(iters):
+            ctx.apply_circuit(circ, None, st)
+    elif args.profile_case == "c5":          # QFT + layers, forward + adjoint, 26 qubits
+        wl = W.config_c5(26)
+        circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
+        obs = dq.Observables(wl.observables)
+        params = torch.tensor(wl.params, device=dev)
+        for _ in range(iters):
+            ctx.forward_grad(circ, params, obs, 1, torch.complex64)
+    torch.cuda.synchronize()
+    print(f"profile case {args.profile_case}: {iters} iterations in {time.perf_counter() - t0:.3f} s, "
+          f"{ctx.launch_count} launches", flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -378,7 +428,12 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--profile-case", choices=["tile", "wsv", "sweep", "c5"], default=None,
+                    help="run one kernel family's workload for profiling and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args)
+        return
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
