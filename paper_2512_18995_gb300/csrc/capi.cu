@@ -15,6 +15,7 @@
 #include "dq.h"
 #include "dq_common.cuh"
 #include "dq_plan.h"
+#include "dq_rows.h"
 #include "dq_tile.h"
 
 using namespace dq;
@@ -97,6 +98,7 @@ struct dq_ctx {
     TileCache tiles;
     Tracer tracer;
     std::vector<std::pair<std::string, std::pair<int64_t, double>>> trace_table;
+    std::unordered_map<uint64_t, std::unique_ptr<RowProgram>> rowprogs;
 };
 
 namespace {
@@ -419,12 +421,41 @@ dq_status check_angles(dq_ctx *ctx, const Plan &p, const double *params, const d
     return DQ_OK;
 }
 
+// Whole-row engine program for this plan (null when the engine does not
+// cover the row size or the shared memory does not fit).
+RowProgram *get_rows(dq_ctx *ctx, const Plan &p, int amp, bool grad, int nobs) {
+    const int M = rows_pick_M(p.n, amp);
+    if (!M) return nullptr;
+    const uint64_t key = (p.key * 1099511628211ull) ^ (uint64_t)(amp * 31 + M) ^ ((uint64_t)p.n << 56);
+    RowProgram *rp = nullptr;
+    auto it = ctx->rowprogs.find(key);
+    if (it != ctx->rowprogs.end()) {
+        rp = it->second.get();
+    } else {
+        std::unique_ptr<RowProgram> np(new RowProgram());
+        if (!rows_build_program(p, M, *np)) return nullptr;
+        if (upload(ctx, &np->d_ops, np->ops.empty() ? nullptr : np->ops.data(), np->ops.size()) != DQ_OK ||
+            upload(ctx, &np->d_fsegs, np->fsegs.data(), np->fsegs.size()) != DQ_OK ||
+            upload(ctx, &np->d_rsegs, np->rsegs.data(), np->rsegs.size()) != DQ_OK) {
+            np->release();
+            cudaGetLastError();
+            return nullptr;
+        }
+        rp = np.get();
+        ctx->rowprogs.emplace(key, std::move(np));
+    }
+    const int threads = 1 << (p.n - M);
+    if (rows_smem_bytes(*rp, amp, grad, std::max(1, nobs), threads) > ctx->smem_optin) return nullptr;
+    return rp;
+}
+
 // ---- templated bodies ------------------------------------------------------
 
 template <typename R>
 dq_status apply_impl(dq_ctx *ctx, Plan &p, const double *params, const double *data, void *state, int batch,
                      cudaStream_t s) {
-    const bool small = use_fused(ctx) && wsv_supported(p.n, (int)sizeof(cx<R>), false, ctx->smem_optin, wsv_doubles(p, 1));
+    RowProgram *rp = use_fused(ctx) ? get_rows(ctx, p, (int)sizeof(cx<R>), false, 1) : nullptr;
+    const bool small = rp || (use_fused(ctx) && wsv_supported(p.n, (int)sizeof(cx<R>), false, ctx->smem_optin, wsv_doubles(p, 1)));
     const bool tile = use_fused(ctx) && !small && tile_supported(p.n, (int)sizeof(cx<R>));
     Arena a;
     a.measuring = true;
@@ -437,14 +468,22 @@ dq_status apply_impl(dq_ctx *ctx, Plan &p, const double *params, const double *d
     w.cap = ctx->ws_bytes;
     void *coef = w.take(coef_bytes(p, batch, sizeof(R) == 8 ? DQ_C128 : DQ_C64));
     DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
-    if (small) {
+    if (rp) {
+        DQ_CUDA(rows_launch<R>(*rp, p, coef, state, 1, nullptr, 0, 1, nullptr, batch, state, nullptr, nullptr, nullptr,
+                               nullptr, ctx->nsm, ctx->smem_optin, s, &ctx->launches),
+                "fused apply (rows)");
+    } else if (small) {
         DQ_CUDA(wsv_launch<R>(p, coef, state, 1, nullptr, 0, 1, nullptr, batch, state, nullptr, nullptr, nullptr,
                               nullptr, ctx->nsm, s, &ctx->launches),
                 "fused apply");
     } else if (tile) {
         void *tws = w.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>)));
-        DQ_CUDA(tile_apply<R>(ctx->tiles, ctx->tuned, p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches),
-                "tiled apply");
+        cudaError_t e = tile_apply<R>(ctx->tiles, ctx->tuned, p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+        if (e == cudaErrorNotSupported) {   // no schedule for this shape: per-gate sweeps
+            cudaGetLastError();
+            e = plain_apply<R>(p, coef, state, batch, 0, s, &ctx->launches);
+        }
+        DQ_CUDA(e, "tiled apply");
     } else {
         DQ_CUDA(plain_apply<R>(p, coef, state, batch, 0, s, &ctx->launches), "plain apply");
     }
@@ -453,10 +492,18 @@ dq_status apply_impl(dq_ctx *ctx, Plan &p, const double *params, const double *d
 
 template <typename R>
 dq_status expect_impl(dq_ctx *ctx, int n, ObsDev &o, const void *state, int batch, double *out, cudaStream_t s) {
+    Plan p;
+    p.n = n;
+    p.key = 0x5bd1e995ull * (uint64_t)(n + 1);
+    RowProgram *rp = use_fused(ctx) ? get_rows(ctx, p, (int)sizeof(cx<R>), false, o.nobs) : nullptr;
+    if (rp) {
+        DQ_CUDA(rows_launch<R>(*rp, p, nullptr, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, nullptr, batch,
+                               nullptr, out, nullptr, nullptr, nullptr, ctx->nsm, ctx->smem_optin, s, &ctx->launches),
+                "fused expect (rows)");
+        return DQ_OK;
+    }
     const bool small = use_fused(ctx) && wsv_supported(n, (int)sizeof(cx<R>), false, ctx->smem_optin, o.nobs);
     if (small) {
-        Plan p;
-        p.n = n;
         DQ_CUDA(wsv_launch<R>(p, nullptr, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, nullptr, batch, nullptr,
                               out, nullptr, nullptr, nullptr, ctx->nsm, s, &ctx->launches),
                 "fused expect");
@@ -478,13 +525,14 @@ dq_status adjoint_impl(dq_ctx *ctx, Plan &p, ObsDev &o, const double *params, co
                        cudaStream_t s) {
     const int dt = sizeof(R) == 8 ? DQ_C128 : DQ_C64;
     const size_t sbytes = ((size_t)batch << p.n) * sizeof(cx<R>);
-    const bool small = use_fused(ctx) && wsv_supported(p.n, (int)sizeof(cx<R>), true, ctx->smem_optin, wsv_doubles(p, o.nobs));
+    RowProgram *rp = use_fused(ctx) ? get_rows(ctx, p, (int)sizeof(cx<R>), true, o.nobs) : nullptr;
+    const bool small = rp || (use_fused(ctx) && wsv_supported(p.n, (int)sizeof(cx<R>), true, ctx->smem_optin, wsv_doubles(p, o.nobs)));
     const bool clobber = (flags & DQ_ADJ_CLOBBER_STATE) != 0;
     Arena a;
     a.measuring = true;
     a.take(coef_bytes(p, batch, dt));
     if (small) {
-        a.take(wsv_part_bytes(p, ctx->nsm));
+        a.take(std::max(wsv_part_bytes(p, ctx->nsm), rows_part_bytes(p, ctx->nsm)));
     } else {
         if (!clobber) a.take(sbytes);
         a.take(sbytes);
@@ -498,10 +546,15 @@ dq_status adjoint_impl(dq_ctx *ctx, Plan &p, ObsDev &o, const double *params, co
     void *coef = w.take(coef_bytes(p, batch, dt));
     DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
     if (small) {
-        double *part = (double *)w.take(wsv_part_bytes(p, ctx->nsm));
-        DQ_CUDA(wsv_launch<R>(p, coef, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, rw, batch, nullptr, nullptr,
-                              gp, gd, part, ctx->nsm, s, &ctx->launches),
-                "fused adjoint");
+        double *part = (double *)w.take(std::max(wsv_part_bytes(p, ctx->nsm), rows_part_bytes(p, ctx->nsm)));
+        if (rp)
+            DQ_CUDA(rows_launch<R>(*rp, p, coef, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, rw, batch, nullptr,
+                                   nullptr, gp, gd, part, ctx->nsm, ctx->smem_optin, s, &ctx->launches),
+                    "fused adjoint (rows)");
+        else
+            DQ_CUDA(wsv_launch<R>(p, coef, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, rw, batch, nullptr,
+                                  nullptr, gp, gd, part, ctx->nsm, s, &ctx->launches),
+                    "fused adjoint");
         return DQ_OK;
     }
     void *psi = state;
@@ -523,23 +576,30 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     const int dt = sizeof(R) == 8 ? DQ_C128 : DQ_C64;
     const bool grad = gp || gd;
     const size_t sbytes = ((size_t)batch << p.n) * sizeof(cx<R>);
-    const bool small = use_fused(ctx) && wsv_supported(p.n, (int)sizeof(cx<R>), grad, ctx->smem_optin, wsv_doubles(p, o ? o->nobs : 1));
+    RowProgram *rp = use_fused(ctx) ? get_rows(ctx, p, (int)sizeof(cx<R>), grad, o ? o->nobs : 1) : nullptr;
+    const bool small = rp || (use_fused(ctx) && wsv_supported(p.n, (int)sizeof(cx<R>), grad, ctx->smem_optin, wsv_doubles(p, o ? o->nobs : 1)));
     if (small) {
         Arena a;
         a.measuring = true;
         a.take(coef_bytes(p, batch, dt));
-        a.take(wsv_part_bytes(p, ctx->nsm));
+        a.take(std::max(wsv_part_bytes(p, ctx->nsm), rows_part_bytes(p, ctx->nsm)));
         dq_status st = reserve(ctx, a.used);
         if (st != DQ_OK) return st;
         Arena w;
         w.base = ctx->ws;
         w.cap = ctx->ws_bytes;
         void *coef = w.take(coef_bytes(p, batch, dt));
-        double *part = (double *)w.take(wsv_part_bytes(p, ctx->nsm));
+        double *part = (double *)w.take(std::max(wsv_part_bytes(p, ctx->nsm), rows_part_bytes(p, ctx->nsm)));
         DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
-        DQ_CUDA(wsv_launch<R>(p, coef, nullptr, 1, o ? o->d_wires : nullptr, o ? (int)o->bits.size() : 0,
-                              o ? o->nobs : 1, rw, batch, state_out, eo, gp, gd, part, ctx->nsm, s, &ctx->launches),
-                "fused forward+adjoint");
+        if (rp)
+            DQ_CUDA(rows_launch<R>(*rp, p, coef, nullptr, 1, o ? o->d_wires : nullptr, o ? (int)o->bits.size() : 0,
+                                   o ? o->nobs : 1, rw, batch, state_out, eo, gp, gd, part, ctx->nsm, ctx->smem_optin,
+                                   s, &ctx->launches),
+                    "fused forward+adjoint (rows)");
+        else
+            DQ_CUDA(wsv_launch<R>(p, coef, nullptr, 1, o ? o->d_wires : nullptr, o ? (int)o->bits.size() : 0,
+                                  o ? o->nobs : 1, rw, batch, state_out, eo, gp, gd, part, ctx->nsm, s, &ctx->launches),
+                    "fused forward+adjoint");
         return DQ_OK;
     }
     // Large states: prepare, evolve (fused tiles when possible), measure,
@@ -576,8 +636,12 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
     DQ_CUDA(plain_init_zero<R>(psi, p.n, batch, s, &ctx->launches), "init");
     if (tile) {
-        DQ_CUDA(tile_apply<R>(ctx->tiles, ctx->tuned, p, coef, psi, batch, tws, ctx->nsm, s, &ctx->launches),
-                "tiled apply");
+        cudaError_t e = tile_apply<R>(ctx->tiles, ctx->tuned, p, coef, psi, batch, tws, ctx->nsm, s, &ctx->launches);
+        if (e == cudaErrorNotSupported) {   // no schedule for this shape: per-gate sweeps
+            cudaGetLastError();
+            e = plain_apply<R>(p, coef, psi, batch, 0, s, &ctx->launches);
+        }
+        DQ_CUDA(e, "tiled apply");
     } else {
         DQ_CUDA(plain_apply<R>(p, coef, psi, batch, 0, s, &ctx->launches), "plain apply");
     }
@@ -630,6 +694,7 @@ dq_status dq_ctx_destroy(dq_ctx *ctx) {
     for (auto &kv : ctx->plans) kv.second->release();
     for (auto &kv : ctx->obs) kv.second->release();
     for (auto &kv : ctx->batches) kv.second->release();
+    for (auto &kv : ctx->rowprogs) kv.second->release();
     ctx->tiles.release();
     ctx->tracer.release();
     if (g_tracer == &ctx->tracer) g_tracer = nullptr;
@@ -741,7 +806,7 @@ dq_status dq_workspace_bytes(dq_ctx *ctx, const dq_circuit *circuit, const dq_ob
     a.take(3 * sb);
     a.take(plain_adjoint_part_bytes(*p, batch));
     a.take(plain_expect_part_bytes(p->n, nterms, batch));
-    a.take(wsv_part_bytes(*p, ctx->nsm));
+    a.take(std::max(wsv_part_bytes(*p, ctx->nsm), rows_part_bytes(*p, ctx->nsm)));
     a.take(tile_workspace_bytes(*p, batch, amp_bytes(dtype)));
     a.take(tile_adjoint_part_bytes(*p, batch));
     a.take(tile_expect_part_bytes(p->n, nterms, batch));

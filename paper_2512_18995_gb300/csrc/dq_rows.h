@@ -1,0 +1,38 @@
+// Whole-row in-register kernel (internal interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "dq_engine.cuh"
+#include "dq_plan.h"
+
+namespace dq {
+
+// Engine program for whole rows of one circuit: ops in gate order (SWAP as
+// three CNOTs), register layouts for the forward and the reverse sweep.
+// Reverse segments list their first (highest) op in op0 and run downwards.
+struct RowProgram {
+    int n = 0, M = 0;
+    int nacc_shared = 0, nacc_row = 0;
+    std::vector<EOp> ops;
+    std::vector<ESeg> fsegs, rsegs;
+    EOp *d_ops = nullptr;
+    ESeg *d_fsegs = nullptr, *d_rsegs = nullptr;
+    void release();
+};
+
+int rows_pick_M(int n, int amp_bytes);
+bool rows_build_program(const Plan &p, int M, RowProgram &out);
+size_t rows_smem_bytes(const RowProgram &rp, int amp, bool grad, int nobs, int threads);
+size_t rows_part_bytes(const Plan &p, int nsm);
+
+template <typename R>
+cudaError_t rows_launch(const RowProgram &rp, const Plan &p, const void *coef, const void *state_in, int forward,
+                        const DevTerm *d_wterms, int nterms, int nobs, const double *row_weights, int batch,
+                        void *state_out, double *expect_out, double *grad_params, double *grad_data, double *part,
+                        int nsm, size_t smem_optin, cudaStream_t s, int64_t *launches);
+
+}  // namespace dq

@@ -14,6 +14,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "dq_engine.cuh"
 #include "dq_plan.h"
 
 namespace dq {
@@ -22,28 +23,9 @@ constexpr int kTileMaxK = 14;
 constexpr int kTileLaneBits = 5;      // local bits 0..4 live across the 32 lanes of a warp
 constexpr int kTileMaxOps = 384;      // operations per pass (bounds the shared-memory program)
 
-// One in-tile operation.  32 bytes.
-struct TOp {
-    int8_t cls;      // GateClass (SWAP is lowered to three CNOTs)
-    int8_t tl;       // target local bit (-1: outside the tile, diagonal only)
-    int8_t cl;       // control local bit (-1: none or outside the tile)
-    int8_t hasc;     // 1 when controlled
-    int16_t kind;    // dq_gate_kind (gradient generator)
-    int16_t pad;
-    int32_t tg;      // target amplitude bit
-    int32_t cg;      // control amplitude bit (-1: none)
-    int32_t coef;    // Mat2 index (row 0)
-    int32_t rowstep; // Mat2 row stride
-    int32_t slot;    // gradient slot or -1
-    int32_t pad2;
-};
-
-// A run of operations executed with one register layout: register bit i of
-// a thread holds local bit B[i].
-struct TSeg {
-    int32_t op0, nops;
-    int8_t B[8];
-};
+// Tile programs use the engine's operation and layout records.
+using TOp = EOp;
+using TSeg = ESeg;
 
 struct TPass {
     std::vector<int> T;     // tile bits, ascending (amplitude bits)
@@ -65,6 +47,7 @@ struct TileSchedule {
 struct TileTune {
     int k = 0;          // tile qubits (0 = default)
     int low = 0;        // always-resident low bits
+    int M = 0;          // register bits per thread
 };
 
 // Host-side cache of schedules and the driver entry point used to encode

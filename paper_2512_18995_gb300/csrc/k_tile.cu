@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "dq_common.cuh"
+#include "dq_engine.cuh"
 #include "dq_tile.h"
 
 namespace dq {
@@ -47,8 +48,8 @@ void TileCache::release() {
 namespace {
 
 template <typename R> struct TileCfg;
-template <> struct TileCfg<float> { static constexpr int M = 5; static constexpr int wb = 0; };
-template <> struct TileCfg<double> { static constexpr int M = 4; static constexpr int wb = 1; };
+template <> struct TileCfg<float> { static constexpr int wb = 0; static constexpr int Mmax = 5; };
+template <> struct TileCfg<double> { static constexpr int wb = 1; static constexpr int Mmax = 4; };
 
 inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
 
@@ -92,7 +93,8 @@ GateBits gate_bits(const DevGate &g) {
 bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, TileSchedule &out) {
     const int n = p.n;
     const int wb = amp_bytes == 16 ? 1 : 0;
-    if (k > n || k < kTileLaneBits + M || low < kTileLaneBits || low > k) return false;
+    // a SWAP of two high bits needs two free tile bits
+    if (k > n || k < kTileLaneBits + M || low < kTileLaneBits || low > k - 2) return false;
     out = TileSchedule();
     out.n = n;
     out.k = k;
@@ -338,182 +340,6 @@ __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// ---------------------------------------------------------------------------
-// in-register engine
-// ---------------------------------------------------------------------------
-struct Layout {
-    uint32_t tb;          // this thread's local index with register bits zero
-    uint64_t posB;        // 4 bits per local bit: register position, 15 = not a register bit
-    uint32_t off[8];      // local offset of register bit i
-};
-
-__device__ __forceinline__ Layout make_layout(const TSeg &sg, int M, int k, int lane, int warp) {
-    Layout L;
-    L.posB = ~0ull;
-    uint32_t inB = 0;
-    for (int i = 0; i < M; ++i) {
-        const int b = sg.B[i];
-        L.off[i] = 1u << b;
-        inB |= 1u << b;
-        L.posB &= ~(uint64_t(15) << (4 * b));
-        L.posB |= uint64_t(i) << (4 * b);
-    }
-    uint32_t tb = (uint32_t)lane;
-    int wi = 0;
-    for (int b = kTileLaneBits; b < k; ++b) {
-        if ((inB >> b) & 1) continue;
-        tb |= (uint32_t)((warp >> wi) & 1) << b;
-        ++wi;
-    }
-    L.tb = tb;
-    return L;
-}
-
-template <int M>
-__device__ __forceinline__ uint32_t reg_off(const Layout &L, int e) {
-    uint32_t o = 0;
-#pragma unroll
-    for (int i = 0; i < M; ++i)
-        if ((e >> i) & 1) o |= L.off[i];
-    return o;
-}
-
-// Value of local bit j for register element e.
-__device__ __forceinline__ int lbit(const Layout &L, int j, int e) {
-    const int pb = (int)((L.posB >> (4 * j)) & 15);
-    return pb < 15 ? ((e >> pb) & 1) : (int)((L.tb >> j) & 1);
-}
-
-template <typename R, int M>
-__device__ __forceinline__ void regs_load(cx<R> (&a)[1 << M], const cx<R> *buf, const Layout &L) {
-#pragma unroll
-    for (int e = 0; e < (1 << M); ++e) a[e] = buf[L.tb | reg_off<M>(L, e)];
-}
-
-template <typename R, int M>
-__device__ __forceinline__ void regs_store(const cx<R> (&a)[1 << M], cx<R> *buf, const Layout &L) {
-#pragma unroll
-    for (int e = 0; e < (1 << M); ++e) buf[L.tb | reg_off<M>(L, e)] = a[e];
-}
-
-// Control predicate of an op for element e: (mode, where)
-//   hasc == 0: always true.
-//   control outside the tile: tile-uniform value cu.
-//   control local: lbit.
-struct Ctl {
-    int mode;     // 0 none, 1 uniform (value in u), 2 local bit j
-    int j;
-    int u;
-};
-
-__device__ __forceinline__ bool ctl_of(const Ctl &c, const Layout &L, int e) {
-    return c.mode == 0 ? true : (c.mode == 1 ? c.u != 0 : lbit(L, c.j, e) != 0);
-}
-
-template <typename R, int M, int P, int CLS>
-__device__ __forceinline__ void pair_op(cx<R> (&a)[1 << M], const Mat2<R> &u, const Ctl &c, const Layout &L) {
-#pragma unroll
-    for (int e0 = 0; e0 < (1 << M); ++e0) {
-        if (e0 & (1 << P)) continue;
-        if (ctl_of(c, L, e0)) apply2<R, CLS>(u, a[e0], a[e0 | (1 << P)]);
-    }
-}
-
-template <typename R, int M, int CLS>
-__device__ __forceinline__ void pair_op_at(int p, cx<R> (&a)[1 << M], const Mat2<R> &u, const Ctl &c,
-                                           const Layout &L) {
-    switch (p) {
-    case 0: pair_op<R, M, 0, CLS>(a, u, c, L); break;
-    case 1: pair_op<R, M, 1, CLS>(a, u, c, L); break;
-    case 2: pair_op<R, M, 2, CLS>(a, u, c, L); break;
-    case 3: pair_op<R, M, 3, CLS>(a, u, c, L); break;
-    default:
-        if constexpr (M > 4) pair_op<R, M, (M > 4 ? 4 : 0), CLS>(a, u, c, L);
-        break;
-    }
-}
-
-template <typename T> __device__ __forceinline__ T shfl_x(T v, int m);
-template <> __device__ __forceinline__ float2 shfl_x<float2>(float2 v, int m) {
-    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
-}
-template <> __device__ __forceinline__ double2 shfl_x<double2>(double2 v, int m) {
-    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
-}
-
-// Gate on lane bit j: partner amplitude lives in lane ^ (1 << j).
-template <typename R, int M, int CLS>
-__device__ __forceinline__ void lane_op(cx<R> (&a)[1 << M], const Mat2<R> &u, int j, int lane, const Ctl &c,
-                                        const Layout &L) {
-    const bool hi = (lane >> j) & 1;
-    const cx<R> cs = hi ? u.m[3] : u.m[0];
-    const cx<R> cp = hi ? u.m[2] : u.m[1];
-    const int m = 1 << j;
-#pragma unroll
-    for (int e = 0; e < (1 << M); ++e) {
-        const cx<R> p = shfl_x(a[e], m);
-        if (!ctl_of(c, L, e)) continue;
-        if (CLS == CLS_ANTI) {
-            a[e] = p;
-        } else if (CLS == CLS_REAL) {
-            const R s0 = cs.x, s1 = cp.x;
-            a[e] = mk<R>(s0 * a[e].x + s1 * p.x, s0 * a[e].y + s1 * p.y);
-        } else {
-            a[e] = cadd(cmul(cs, a[e]), cmul(cp, p));
-        }
-    }
-}
-
-// Diagonal gate: element factor m0 / m3 by the target bit value.
-template <typename R, int M>
-__device__ __forceinline__ void diag_op(cx<R> (&a)[1 << M], const Mat2<R> &u, const TOp &o, uint64_t base,
-                                        const Ctl &c, const Layout &L) {
-    const int tu = o.tl < 0 ? (int)((base >> o.tg) & 1) : -1;
-#pragma unroll
-    for (int e = 0; e < (1 << M); ++e) {
-        if (!ctl_of(c, L, e)) continue;
-        const int t = tu >= 0 ? tu : lbit(L, o.tl, e);
-        a[e] = cmul(t ? u.m[3] : u.m[0], a[e]);
-    }
-}
-
-template <typename R, int M>
-__device__ __forceinline__ void apply_op(cx<R> (&a)[1 << M], const TOp &o, const Mat2<R> &u, uint64_t base,
-                                         const Layout &L, int lane) {
-    Ctl c;
-    c.mode = 0;
-    c.j = 0;
-    c.u = 1;
-    if (o.hasc) {
-        if (o.cl < 0) {
-            c.mode = 1;
-            c.u = (int)((base >> o.cg) & 1);
-            if (!c.u) return;   // tile-uniform: nothing to do
-        } else {
-            c.mode = 2;
-            c.j = o.cl;
-        }
-    }
-    if (o.cls == CLS_DIAG) {
-        diag_op<R, M>(a, u, o, base, c, L);
-        return;
-    }
-    if (o.tl < kTileLaneBits) {
-        switch (o.cls) {
-        case CLS_ANTI: lane_op<R, M, CLS_ANTI>(a, u, o.tl, lane, c, L); break;
-        case CLS_REAL: lane_op<R, M, CLS_REAL>(a, u, o.tl, lane, c, L); break;
-        default: lane_op<R, M, CLS_GENERAL>(a, u, o.tl, lane, c, L); break;
-        }
-        return;
-    }
-    const int p = (int)((L.posB >> (4 * o.tl)) & 15);
-    switch (o.cls) {
-    case CLS_ANTI: pair_op_at<R, M, CLS_ANTI>(p, a, u, c, L); break;
-    case CLS_REAL: pair_op_at<R, M, CLS_REAL>(p, a, u, c, L); break;
-    default: pair_op_at<R, M, CLS_GENERAL>(p, a, u, c, L); break;
-    }
-}
-
 struct TileKArgs {
     const TOp *ops;
     const TSeg *segs;
@@ -550,12 +376,14 @@ __device__ __forceinline__ void tile_coords(const TileKArgs &a, int64_t t, int c
     base = amp & ((uint64_t(1) << a.n) - 1);
 }
 
-constexpr int kTileThreadsMax = 256;
+// Threads per CTA are 2^(k - M); wide register sets (256 bytes of amplitudes
+// per thread) are limited to 256 threads so that they keep their registers.
+template <typename R, int M>
+constexpr int tile_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) >= 256) ? 256 : 512; }
 
-template <typename R>
-__global__ void __launch_bounds__(kTileThreadsMax, 1)
+template <typename R, int M>
+__global__ void __launch_bounds__(tile_max_threads<R, M>(), 1)
 k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
-    constexpr int M = TileCfg<R>::M;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t tbytes = sizeof(cx<R>) << a.k;
@@ -615,15 +443,15 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
         for (int si = 0; si < a.nseg; ++si) {
             const TSeg sg = ssegs[si];
             const Layout L = make_layout(sg, M, a.k, lane, warp);
-            regs_load<R, M>(r, cur, L);
+            eng_load<R, M>(r, cur, L);
             for (int oi = sg.op0 - a.op0; oi < sg.op0 - a.op0 + sg.nops; ++oi) {
                 const TOp o = sops[oi];
                 const Mat2<R> u = o.rowstep ? gcoef[o.coef + row * o.rowstep] : scoef[oi];
-                apply_op<R, M>(r, o, u, base, L, lane);
+                eng_apply<R, M>(r, o, u, base, L, lane);
             }
             // each thread writes back exactly the addresses it read in this
             // layout; the barrier orders them before the next layout's reads
-            regs_store<R, M>(r, cur, L);
+            eng_store<R, M>(r, cur, L);
             __syncthreads();
         }
         fence_async_smem();
@@ -647,8 +475,9 @@ size_t tile_smem_bytes(int k, int amp, int nops, int nseg) {
            (size_t)nops * (amp == 8 ? sizeof(Mat2<float>) : sizeof(Mat2<double>)) + 64;
 }
 
-uint64_t sched_key(const Plan &p, int k, int low, int amp) {
+uint64_t sched_key(const Plan &p, int k, int low, int amp, int M) {
     uint64_t h = p.key ^ 0x9E3779B97F4A7C15ull;
+    h = (h ^ (uint64_t)M) * 1099511628211ull;
     h = (h ^ (uint64_t)k) * 1099511628211ull;
     h = (h ^ (uint64_t)low) * 1099511628211ull;
     h = (h ^ (uint64_t)amp) * 1099511628211ull;
@@ -668,16 +497,35 @@ bool ensure_encode_fn(TileCache &tc) {
     return true;
 }
 
+// Default tile: HBM-resident states (>= 2^25 amplitudes) take wide tiles and
+// wide register sets; L2-resident ones take narrower tiles and more warps per
+// tile so that every SM has work.
 template <typename R>
-void default_tile(int n, int &k, int &low) {
-    constexpr int M = TileCfg<R>::M;
-    const int kmax = std::min(M + 8, sizeof(R) == 4 ? 13 : 12);   // at most 256 threads per CTA
-    k = std::min(kmax, std::max(kTileLaneBits + M, n - 9));
-    low = std::min(k - 1, 7);
+void default_tile(int n, int &k, int &low, int &M) {
+    if (n >= 25) {
+        M = sizeof(R) == 4 ? 5 : 4;
+        k = sizeof(R) == 4 ? 13 : 12;
+    } else {
+        M = 3;
+        k = std::max(kTileLaneBits + M, std::min(11, n - 9));
+    }
+    k = std::min(k, n - 1);
+    M = std::min(M, k - kTileLaneBits);
+    low = std::max(kTileLaneBits, std::min(7, k - 3));   // keep >= 2 free tile bits (SWAP)
+}
+
+template <typename R>
+const void *tile_kernel(int M) {
+    switch (M) {
+    case 2: return (const void *)k_tile_fwd<R, 2>;
+    case 3: return (const void *)k_tile_fwd<R, 3>;
+    case 4: return (const void *)k_tile_fwd<R, 4>;
+    default: return (const void *)k_tile_fwd<R, (TileCfg<R>::Mmax)>;
+    }
 }
 
 TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, int amp) {
-    const uint64_t key = sched_key(p, k, low, amp);
+    const uint64_t key = sched_key(p, k, low, amp, M);
     auto it = tc.schedules.find(key);
     if (it != tc.schedules.end()) return it->second;
     TileSchedule *s = new TileSchedule();
@@ -700,7 +548,7 @@ TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, 
 template <typename R>
 cudaError_t run_forward(TileCache &tc, const Plan &p, const TileSchedule &sc, const void *coef, void *state,
                         int batch, int nsm, cudaStream_t s, int64_t *launches) {
-    constexpr int M = TileCfg<R>::M;
+    const int M = sc.M;
     constexpr int wb = TileCfg<R>::wb;
     const int amp = (int)sizeof(cx<R>);
     const int threads = 1 << (sc.k - M);
@@ -729,14 +577,20 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, const TileSchedule &sc, co
         }
         a.errflag = tc.errflag;
         const size_t smem = tile_smem_bytes(sc.k, amp, ps.nops, ps.nseg);
-        cudaError_t e = cudaFuncSetAttribute(k_tile_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const void *kfn = tile_kernel<R>(M);
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_fwd<R>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem);
         per_sm = std::max(1, per_sm);
         const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)per_sm * nsm);
         LaunchScope ls(s, "k_tile_fwd", launches);
-        k_tile_fwd<R><<<(unsigned)grid, threads, smem, s>>>(map, a);
+        switch (M) {
+        case 2: k_tile_fwd<R, 2><<<(unsigned)grid, threads, smem, s>>>(map, a); break;
+        case 3: k_tile_fwd<R, 3><<<(unsigned)grid, threads, smem, s>>>(map, a); break;
+        case 4: k_tile_fwd<R, 4><<<(unsigned)grid, threads, smem, s>>>(map, a); break;
+        default: k_tile_fwd<R, (TileCfg<R>::Mmax)><<<(unsigned)grid, threads, smem, s>>>(map, a); break;
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -746,8 +600,8 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, const TileSchedule &sc, co
 }  // namespace
 
 bool tile_supported(int n, int amp_bytes) {
-    const int M = amp_bytes == 8 ? TileCfg<float>::M : TileCfg<double>::M;
-    return n >= kTileLaneBits + M + 1 && n <= 34;
+    (void)amp_bytes;
+    return n >= kTileLaneBits + 3 + 1 && n <= 34;
 }
 size_t tile_workspace_bytes(const Plan &, int, int) { return 0; }
 size_t tile_adjoint_part_bytes(const Plan &, int) { return 0; }
@@ -759,14 +613,15 @@ cudaError_t tile_apply(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tu
                        int64_t *launches) {
     (void)tws;
     if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
-    int k, low;
-    default_tile<R>(p.n, k, low);
+    int k, low, M;
+    default_tile<R>(p.n, k, low, M);
     auto it = tuned.find(p.key ^ (sizeof(R) == 8 ? 1ull : 0ull));
     if (it != tuned.end() && it->second.k) {
         k = it->second.k;
         low = it->second.low;
+        M = it->second.M;
     }
-    TileSchedule *sc = get_schedule(tc, p, k, low, TileCfg<R>::M, (int)sizeof(cx<R>));
+    TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>));
     if (!sc) return cudaErrorNotSupported;
     return run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches);
 }
@@ -789,8 +644,6 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
                           int64_t *launches) {
     (void)tws;
     if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
-    constexpr int M = TileCfg<R>::M;
-    const int kmax = std::min(std::min(p.n - 1, M + 8), sizeof(R) == 4 ? 13 : 12);
     float best = 1e30f;
     TileTune bt;
     cudaEvent_t e0, e1;
@@ -798,9 +651,12 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
     cudaEventCreate(&e1);
     Tracer *saved = g_tracer;
     g_tracer = nullptr;
-    for (int k = kTileLaneBits + M; k <= kmax; ++k) {
+    for (int M = 3; M <= TileCfg<R>::Mmax; ++M)
+    for (int k = kTileLaneBits + M; k <= std::min(p.n - 1, sizeof(R) == 4 ? 13 : 12); ++k) {
+        const int maxt = ((1 << M) * (int)sizeof(cx<R>) >= 256) ? 256 : 512;
+        if ((1 << (k - M)) > maxt) continue;
         for (int low : {5, 7}) {
-            if (low > k - 1) continue;
+            if (low > k - 2) continue;
             TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>));
             if (!sc) continue;
             cudaError_t err = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches);   // warm
@@ -818,6 +674,7 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
                 best = ms;
                 bt.k = k;
                 bt.low = low;
+                bt.M = M;
             }
         }
     }
