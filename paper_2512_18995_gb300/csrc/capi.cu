@@ -434,7 +434,8 @@ RowProgram *get_rows(dq_ctx *ctx, const Plan &p, int amp, bool grad, int nobs) {
     } else {
         std::unique_ptr<RowProgram> np(new RowProgram());
         if (!rows_build_program(p, M, *np)) return nullptr;
-        if (upload(ctx, &np->d_ops, np->ops.empty() ? nullptr : np->ops.data(), np->ops.size()) != DQ_OK ||
+        if (upload(ctx, &np->d_fops, np->fops.empty() ? nullptr : np->fops.data(), np->fops.size()) != DQ_OK ||
+            upload(ctx, &np->d_rops, np->rops.empty() ? nullptr : np->rops.data(), np->rops.size()) != DQ_OK ||
             upload(ctx, &np->d_fsegs, np->fsegs.data(), np->fsegs.size()) != DQ_OK ||
             upload(ctx, &np->d_rsegs, np->rsegs.data(), np->rsegs.size()) != DQ_OK) {
             np->release();

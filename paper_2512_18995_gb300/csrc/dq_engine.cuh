@@ -6,8 +6,12 @@
 // bits select the warp.  A gate whose non-diagonal bit is a register bit is
 // register arithmetic; on a lane bit it exchanges amplitudes with warp
 // shuffles; diagonal gates (and controls) on any bit become per-element
-// factors (predicates) computed from element bit masks.  Changing the set of
-// register bits is the only operation that goes through shared memory.
+// factors (predicates).  Changing the set of register bits is the only
+// operation that goes through shared memory.
+//
+// Operations are decoded on the host against the register layout they run
+// in (handler id, ready-made control mask), so the device dispatches with a
+// single switch into straight-line code.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,20 +23,43 @@ namespace dq {
 
 constexpr int kLaneBits = 5;
 
-// One operation of an engine program.  32 bytes.
+// Handlers: pair updates on register position P (REAL, GEN, ANTI), diagonal
+// factors on register position P, lane-bit updates, and a diagonal factor
+// that is uniform for the thread.
+enum Handler : int16_t {
+    H_REAL = 0,     // + P
+    H_GEN = 5,      // + P
+    H_ANTI = 10,    // + P
+    H_DIAG = 15,    // + P
+    H_LREAL = 20,
+    H_LGEN = 21,
+    H_LANTI = 22,
+    H_DUNI = 23,
+};
+
+// One operation decoded for one register layout.  32 bytes.
 struct EOp {
-    int8_t cls;      // GateClass (never CLS_SWAP: lowered to three CNOTs)
-    int8_t tl;       // target local bit (-1: outside the block; diagonal only)
-    int8_t cl;       // control local bit (-1: none or outside the block)
-    int8_t hasc;     // 1 when controlled
+    int16_t h;       // Handler
     int16_t kind;    // dq_gate_kind (gradient generator)
-    int16_t pad;
-    int32_t tg;      // target global amplitude bit
-    int32_t cg;      // control global amplitude bit (-1: none)
+    uint32_t cmc;    // control element mask (register-bit control), ~0 when uncontrolled
+    int8_t cmode;    // 0: use cmc; 1: control = local bit carg of the thread; 2: global bit carg of the block base
+    int8_t carg;
+    int8_t tmode;    // H_DUNI target: 1: local bit targ of the thread; 2: global bit targ of the block base
+    int8_t targ;     // lane bit (lane handlers) or the H_DUNI target bit
     int32_t coef;    // Mat2 index (row 0)
     int32_t rowstep; // Mat2 row stride
     int32_t slot;    // gradient accumulator or -1
-    int32_t pad2;
+    int32_t pad[2];
+};
+
+// Undecoded gate operation (bit positions in the block).
+struct GOp {
+    int cls;         // GateClass (never CLS_SWAP)
+    int tl;          // target local bit or -1 (outside the block, diagonal only)
+    int tg;          // target global bit
+    int cl;          // control local bit or -1
+    int cg;          // control global bit or -1 (none)
+    int kind, coef, rowstep, slot;
 };
 
 // A run of operations executed with one register layout.
@@ -41,22 +68,73 @@ struct ESeg {
     int8_t B[8];
 };
 
+// Host decode of a gate against a layout with register bits B[0..M-1].
+inline EOp decode_op(const GOp &g, const int8_t *B, int M) {
+    auto pos = [&](int j) {
+        for (int i = 0; i < M; ++i)
+            if (B[i] == j) return i;
+        return -1;
+    };
+    static const uint32_t regmask_h[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+    EOp o{};
+    o.kind = (int16_t)g.kind;
+    o.coef = g.coef;
+    o.rowstep = g.rowstep;
+    o.slot = g.slot;
+    o.cmc = ~0u;
+    o.cmode = 0;
+    if (g.cg >= 0) {
+        if (g.cl >= 0) {
+            const int pc = pos(g.cl);
+            if (pc >= 0) {
+                o.cmc = regmask_h[pc];
+            } else {
+                o.cmode = 1;
+                o.carg = (int8_t)g.cl;
+            }
+        } else {
+            o.cmode = 2;
+            o.carg = (int8_t)g.cg;
+        }
+    }
+    if (g.cls == CLS_DIAG) {
+        const int pt = g.tl >= 0 ? pos(g.tl) : -1;
+        if (pt >= 0) {
+            o.h = (int16_t)(H_DIAG + pt);
+        } else {
+            o.h = H_DUNI;
+            if (g.tl >= 0) {
+                o.tmode = 1;
+                o.targ = (int8_t)g.tl;
+            } else {
+                o.tmode = 2;
+                o.targ = (int8_t)g.tg;
+            }
+        }
+        return o;
+    }
+    if (g.tl < kLaneBits) {
+        o.h = g.cls == CLS_ANTI ? H_LANTI : (g.cls == CLS_REAL ? H_LREAL : H_LGEN);
+        o.targ = (int8_t)g.tl;
+        return o;
+    }
+    const int p = pos(g.tl);   // the planners guarantee p >= 0
+    o.h = (int16_t)((g.cls == CLS_ANTI ? H_ANTI : (g.cls == CLS_REAL ? H_REAL : H_GEN)) + (p < 0 ? 0 : p));
+    return o;
+}
+
 struct Layout {
     uint32_t tb;     // this thread's local index with register bits zero
-    uint64_t posB;   // 4 bits per local bit: register position, 15 = not a register bit
     uint32_t off[8]; // local offset of register bit i
 };
 
 __device__ __forceinline__ Layout make_layout(const ESeg &sg, int M, int k, int lane, int warp) {
     Layout L;
-    L.posB = ~0ull;
     uint32_t inB = 0;
     for (int i = 0; i < M; ++i) {
         const int b = sg.B[i];
         L.off[i] = 1u << b;
         inB |= 1u << b;
-        L.posB &= ~(uint64_t(15) << (4 * b));
-        L.posB |= uint64_t(i) << (4 * b);
     }
     uint32_t tb = (uint32_t)lane;
     int wi = 0;
@@ -76,22 +154,6 @@ __device__ __forceinline__ uint32_t reg_off(const Layout &L, int e) {
     for (int i = 0; i < M; ++i)
         if ((e >> i) & 1) o |= L.off[i];
     return o;
-}
-
-// Elements e (< 32) whose register bit p is set.
-__device__ __forceinline__ uint32_t regmask(int p) {
-    return p == 0 ? 0xAAAAAAAAu : p == 1 ? 0xCCCCCCCCu : p == 2 ? 0xF0F0F0F0u : p == 3 ? 0xFF00FF00u : 0xFFFF0000u;
-}
-
-__device__ __forceinline__ int pos_in_B(const Layout &L, int j) { return (int)((L.posB >> (4 * j)) & 15); }
-
-// Element mask of "bit is 1" for a local bit j (or, when j < 0, the global
-// bit g of the block base).
-__device__ __forceinline__ uint32_t bit_mask(int j, int g, uint64_t base, const Layout &L) {
-    if (j < 0) return ((base >> g) & 1) ? ~0u : 0u;
-    const int pb = pos_in_B(L, j);
-    if (pb < 15) return regmask(pb);
-    return ((L.tb >> j) & 1) ? ~0u : 0u;
 }
 
 template <typename R, int M>
@@ -114,97 +176,185 @@ template <> __device__ __forceinline__ double2 shfl_xor_cx<double2>(double2 v, i
     return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
+__device__ __forceinline__ uint32_t op_cmask(const EOp &o, const Layout &L, uint64_t base) {
+    if (o.cmode == 0) return o.cmc;
+    if (o.cmode == 1) return ((L.tb >> o.carg) & 1) ? ~0u : 0u;
+    return ((base >> o.carg) & 1) ? ~0u : 0u;
+}
+
 // ---------------------------------------------------------------------------
 // forward application
 // ---------------------------------------------------------------------------
-template <typename R, int M, int P, bool ANTI>
+template <typename R, int M, int P, int CLS>
 __device__ __forceinline__ void pairs_at(cx<R> (&a)[1 << M], const Mat2<R> &u, uint32_t cm) {
+    const bool all = cm == ~0u;
 #pragma unroll
     for (int e0 = 0; e0 < (1 << M); ++e0) {
         if (e0 & (1 << P)) continue;
-        if (!((cm >> e0) & 1)) continue;
-        const int e1 = e0 | (1 << P);
-        if (ANTI) {
-            const cx<R> t = a[e0];
-            a[e0] = a[e1];
-            a[e1] = t;
-        } else {
-            apply2<R, CLS_GENERAL>(u, a[e0], a[e1]);
-        }
+        if (!all && !((cm >> e0) & 1)) continue;
+        apply2<R, CLS>(u, a[e0], a[e0 | (1 << P)]);
     }
 }
 
-template <typename R, int M, bool ANTI>
-__device__ __forceinline__ void pairs_dispatch(int p, cx<R> (&a)[1 << M], const Mat2<R> &u, uint32_t cm) {
-    if (p == 0) pairs_at<R, M, 0, ANTI>(a, u, cm);
-    else if (p == 1) pairs_at<R, M, (M > 1 ? 1 : 0), ANTI>(a, u, cm);
-    else if (p == 2) pairs_at<R, M, (M > 2 ? 2 : 0), ANTI>(a, u, cm);
-    else if (p == 3) pairs_at<R, M, (M > 3 ? 3 : 0), ANTI>(a, u, cm);
-    else pairs_at<R, M, (M > 4 ? 4 : 0), ANTI>(a, u, cm);
+template <typename R, int M, int P>
+__device__ __forceinline__ void diag_at(cx<R> (&a)[1 << M], const Mat2<R> &u, uint32_t cm) {
+    const bool all = cm == ~0u;
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e)
+        if (all || ((cm >> e) & 1)) a[e] = cmul(((e >> P) & 1) ? u.m[3] : u.m[0], a[e]);
 }
 
-// Gate on lane bit j (partner amplitude in lane ^ (1 << j)).
-template <typename R, int M>
-__device__ __forceinline__ void lane_apply(cx<R> (&a)[1 << M], const Mat2<R> &u, int j, int lane, uint32_t cm,
-                                           bool anti) {
+template <typename R, int M, int CLS>
+__device__ __forceinline__ void lane_at(cx<R> (&a)[1 << M], const Mat2<R> &u, int j, int lane, uint32_t cm) {
     const bool hi = (lane >> j) & 1;
     const cx<R> cs = hi ? u.m[3] : u.m[0];
     const cx<R> cp = hi ? u.m[2] : u.m[1];
     const int m = 1 << j;
+    const bool all = cm == ~0u;
 #pragma unroll
     for (int e = 0; e < (1 << M); ++e) {
         const cx<R> p = shfl_xor_cx(a[e], m);
-        if (!((cm >> e) & 1)) continue;
-        a[e] = anti ? p : cadd(cmul(cs, a[e]), cmul(cp, p));
+        if (!all && !((cm >> e) & 1)) continue;
+        if (CLS == CLS_ANTI) a[e] = p;
+        else if (CLS == CLS_REAL) a[e] = mk<R>(cs.x * a[e].x + cp.x * p.x, cs.x * a[e].y + cp.x * p.y);
+        else a[e] = cadd(cmul(cs, a[e]), cmul(cp, p));
     }
 }
+
+template <typename R, int M>
+__device__ __forceinline__ void diag_uni(cx<R> (&a)[1 << M], const Mat2<R> &u, const EOp &o, const Layout &L,
+                                         uint64_t base, uint32_t cm) {
+    const int t = o.tmode == 1 ? (int)((L.tb >> o.targ) & 1) : (int)((base >> o.targ) & 1);
+    const cx<R> f = t ? u.m[3] : u.m[0];
+    const bool all = cm == ~0u;
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e)
+        if (all || ((cm >> e) & 1)) a[e] = cmul(f, a[e]);
+}
+
+#define DQ_ENG_P(MACRO) MACRO(0) MACRO(1) MACRO(2) MACRO(3) MACRO(4)
 
 // Apply one op (u already daggered by the caller when un-applying).
 template <typename R, int M>
 __device__ __forceinline__ void eng_apply(cx<R> (&a)[1 << M], const EOp &o, const Mat2<R> &u, uint64_t base,
                                           const Layout &L, int lane) {
-    const uint32_t cm = o.hasc ? bit_mask(o.cl, o.cg, base, L) : ~0u;
+    const uint32_t cm = op_cmask(o, L, base);
     // cm can differ between lanes (control on a lane bit): leave only when the
-    // whole warp has nothing to do, so lane operations below keep every lane
-    // in their full-mask shuffles.
+    // whole warp has nothing to do, so lane operations keep every lane in
+    // their full-mask shuffles.
     if (__all_sync(0xffffffffu, cm == 0)) return;
-    if (o.cls == CLS_DIAG) {
-        const uint32_t tm = bit_mask(o.tl, o.tg, base, L);
-#pragma unroll
-        for (int e = 0; e < (1 << M); ++e)
-            if ((cm >> e) & 1) a[e] = cmul(((tm >> e) & 1) ? u.m[3] : u.m[0], a[e]);
-        return;
+    switch (o.h) {
+#define DQ_CASE(P)                                                                         \
+    case H_REAL + P:                                                                       \
+        if (P < M) pairs_at<R, M, (P < M ? P : 0), CLS_REAL>(a, u, cm);                    \
+        break;                                                                             \
+    case H_GEN + P:                                                                        \
+        if (P < M) pairs_at<R, M, (P < M ? P : 0), CLS_GENERAL>(a, u, cm);                 \
+        break;                                                                             \
+    case H_ANTI + P:                                                                       \
+        if (P < M) pairs_at<R, M, (P < M ? P : 0), CLS_ANTI>(a, u, cm);                    \
+        break;                                                                             \
+    case H_DIAG + P:                                                                       \
+        if (P < M) diag_at<R, M, (P < M ? P : 0)>(a, u, cm);                               \
+        break;
+        DQ_ENG_P(DQ_CASE)
+#undef DQ_CASE
+    case H_LREAL: lane_at<R, M, CLS_REAL>(a, u, o.targ, lane, cm); break;
+    case H_LGEN: lane_at<R, M, CLS_GENERAL>(a, u, o.targ, lane, cm); break;
+    case H_LANTI: lane_at<R, M, CLS_ANTI>(a, u, o.targ, lane, cm); break;
+    default: diag_uni<R, M>(a, u, o, L, base, cm); break;
     }
-    const bool anti = o.cls == CLS_ANTI;
-    if (o.tl < kLaneBits) {
-        lane_apply<R, M>(a, u, o.tl, lane, cm, anti);
-        return;
-    }
-    const int p = pos_in_B(L, o.tl);
-    if (anti) pairs_dispatch<R, M, true>(p, a, u, cm);
-    else pairs_dispatch<R, M, false>(p, a, u, cm);
 }
 
 // ---------------------------------------------------------------------------
 // adjoint step: gradient partial 2 Im <lam|G|psi> (after the gate), then
 // un-apply U^dagger on both register sets.  Returns this thread's partial.
 // ---------------------------------------------------------------------------
-template <typename R, int M, int P>
+template <typename R, int M, int P, int CLS>
 __device__ __forceinline__ R adj_pairs_at(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud, uint32_t cm,
-                                          int kind, bool grad, bool anti) {
+                                          int kind, bool grad) {
     R g = R(0);
+    const bool all = cm == ~0u;
 #pragma unroll
     for (int e0 = 0; e0 < (1 << M); ++e0) {
         if (e0 & (1 << P)) continue;
-        if (!((cm >> e0) & 1)) continue;
+        if (!all && !((cm >> e0) & 1)) continue;
         const int e1 = e0 | (1 << P);
         if (grad) g += grad_pair<R>(kind, ls[e0], ls[e1], ps[e0], ps[e1]);
-        if (anti) {
-            cx<R> t = ps[e0]; ps[e0] = ps[e1]; ps[e1] = t;
-            t = ls[e0]; ls[e0] = ls[e1]; ls[e1] = t;
+        apply2<R, CLS>(ud, ps[e0], ps[e1]);
+        apply2<R, CLS>(ud, ls[e0], ls[e1]);
+    }
+    return g;
+}
+
+// Diagonal generator weights: RZ/CRZ +1 on target 0, -1 on target 1; CP 0 / -2.
+template <typename R>
+__device__ __forceinline__ void diag_weights(int kind, R &w0, R &w1) {
+    w0 = (kind == DQ_CP) ? R(0) : R(1);
+    w1 = (kind == DQ_CP) ? R(-2) : R(-1);
+}
+
+template <typename R, int M, int P>
+__device__ __forceinline__ R adj_diag_at(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud, uint32_t cm,
+                                         int kind, bool grad) {
+    R g = R(0), w0, w1;
+    diag_weights<R>(kind, w0, w1);
+    const bool all = cm == ~0u;
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) {
+        if (!all && !((cm >> e) & 1)) continue;
+        const bool t = (e >> P) & 1;
+        if (grad) g += (t ? w1 : w0) * (ls[e].x * ps[e].y - ls[e].y * ps[e].x);
+        const cx<R> f = t ? ud.m[3] : ud.m[0];
+        ps[e] = cmul(f, ps[e]);
+        ls[e] = cmul(f, ls[e]);
+    }
+    return g;
+}
+
+template <typename R, int M>
+__device__ __forceinline__ R adj_diag_uni(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud, const EOp &o,
+                                          const Layout &L, uint64_t base, uint32_t cm, bool grad) {
+    R g = R(0), w0, w1;
+    diag_weights<R>(o.kind, w0, w1);
+    const int t = o.tmode == 1 ? (int)((L.tb >> o.targ) & 1) : (int)((base >> o.targ) & 1);
+    const cx<R> f = t ? ud.m[3] : ud.m[0];
+    const R w = t ? w1 : w0;
+    const bool all = cm == ~0u;
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) {
+        if (!all && !((cm >> e) & 1)) continue;
+        if (grad) g += w * (ls[e].x * ps[e].y - ls[e].y * ps[e].x);
+        ps[e] = cmul(f, ps[e]);
+        ls[e] = cmul(f, ls[e]);
+    }
+    return g;
+}
+
+template <typename R, int M, int CLS>
+__device__ __forceinline__ R adj_lane_at(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud, int j, int lane,
+                                         uint32_t cm, int kind, bool grad) {
+    R g = R(0);
+    const int m = 1 << j;
+    const bool hi = (lane >> j) & 1;
+    const cx<R> cs = hi ? ud.m[3] : ud.m[0];
+    const cx<R> cp = hi ? ud.m[2] : ud.m[1];
+    const bool all = cm == ~0u;
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) {
+        const cx<R> pp = shfl_xor_cx(ps[e], m);
+        const cx<R> lp = shfl_xor_cx(ls[e], m);
+        if (!all && !((cm >> e) & 1)) continue;
+        if (grad && !hi) g += grad_pair<R>(kind, ls[e], lp, ps[e], pp);
+        if (CLS == CLS_ANTI) {
+            ps[e] = pp;
+            ls[e] = lp;
+        } else if (CLS == CLS_REAL) {
+            ps[e] = mk<R>(cs.x * ps[e].x + cp.x * pp.x, cs.x * ps[e].y + cp.x * pp.y);
+            ls[e] = mk<R>(cs.x * ls[e].x + cp.x * lp.x, cs.x * ls[e].y + cp.x * lp.y);
         } else {
-            apply2<R, CLS_GENERAL>(ud, ps[e0], ps[e1]);
-            apply2<R, CLS_GENERAL>(ud, ls[e0], ls[e1]);
+            ps[e] = cadd(cmul(cs, ps[e]), cmul(cp, pp));
+            ls[e] = cadd(cmul(cs, ls[e]), cmul(cp, lp));
         }
     }
     return g;
@@ -214,54 +364,25 @@ template <typename R, int M>
 __device__ __forceinline__ R eng_adjoint(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const EOp &o, const Mat2<R> &ud,
                                          uint64_t base, const Layout &L, int lane) {
     const bool grad = o.slot >= 0;
-    const uint32_t cm = o.hasc ? bit_mask(o.cl, o.cg, base, L) : ~0u;
-    R g = R(0);
-    if (__all_sync(0xffffffffu, cm == 0)) return g;   // warp-uniform exit (see eng_apply)
-    if (o.cls == CLS_DIAG) {
-        const uint32_t tm = bit_mask(o.tl, o.tg, base, L);
-        // generator weights: RZ/CRZ: +1 on target 0, -1 on target 1; CP: -2 on target 1
-        const R w0 = (o.kind == DQ_CP) ? R(0) : R(1);
-        const R w1 = (o.kind == DQ_CP) ? R(-2) : R(-1);
-#pragma unroll
-        for (int e = 0; e < (1 << M); ++e) {
-            if (!((cm >> e) & 1)) continue;
-            const bool t = (tm >> e) & 1;
-            if (grad) g += (t ? w1 : w0) * (ls[e].x * ps[e].y - ls[e].y * ps[e].x);
-            const cx<R> f = t ? ud.m[3] : ud.m[0];
-            ps[e] = cmul(f, ps[e]);
-            ls[e] = cmul(f, ls[e]);
-        }
-        return g;
+    const uint32_t cm = op_cmask(o, L, base);
+    if (__all_sync(0xffffffffu, cm == 0)) return R(0);   // warp-uniform exit (see eng_apply)
+    switch (o.h) {
+#define DQ_CASE(P)                                                                                       \
+    case H_REAL + P:                                                                                     \
+        return P < M ? adj_pairs_at<R, M, (P < M ? P : 0), CLS_REAL>(ps, ls, ud, cm, o.kind, grad) : R(0);    \
+    case H_GEN + P:                                                                                      \
+        return P < M ? adj_pairs_at<R, M, (P < M ? P : 0), CLS_GENERAL>(ps, ls, ud, cm, o.kind, grad) : R(0); \
+    case H_ANTI + P:                                                                                     \
+        return P < M ? adj_pairs_at<R, M, (P < M ? P : 0), CLS_ANTI>(ps, ls, ud, cm, o.kind, grad) : R(0);    \
+    case H_DIAG + P:                                                                                     \
+        return P < M ? adj_diag_at<R, M, (P < M ? P : 0)>(ps, ls, ud, cm, o.kind, grad) : R(0);
+        DQ_ENG_P(DQ_CASE)
+#undef DQ_CASE
+    case H_LREAL: return adj_lane_at<R, M, CLS_REAL>(ps, ls, ud, o.targ, lane, cm, o.kind, grad);
+    case H_LGEN: return adj_lane_at<R, M, CLS_GENERAL>(ps, ls, ud, o.targ, lane, cm, o.kind, grad);
+    case H_LANTI: return adj_lane_at<R, M, CLS_ANTI>(ps, ls, ud, o.targ, lane, cm, o.kind, grad);
+    default: return adj_diag_uni<R, M>(ps, ls, ud, o, L, base, cm, grad);
     }
-    const bool anti = o.cls == CLS_ANTI;
-    if (o.tl < kLaneBits) {
-        const int j = o.tl, m = 1 << j;
-        const bool hi = (lane >> j) & 1;
-        const cx<R> cs = hi ? ud.m[3] : ud.m[0];
-        const cx<R> cp = hi ? ud.m[2] : ud.m[1];
-#pragma unroll
-        for (int e = 0; e < (1 << M); ++e) {
-            const cx<R> pp = shfl_xor_cx(ps[e], m);
-            const cx<R> lp = shfl_xor_cx(ls[e], m);
-            if (!((cm >> e) & 1)) continue;
-            if (grad && !hi) g += grad_pair<R>(o.kind, ls[e], lp, ps[e], pp);
-            if (anti) {
-                ps[e] = pp;
-                ls[e] = lp;
-            } else {
-                ps[e] = cadd(cmul(cs, ps[e]), cmul(cp, pp));
-                ls[e] = cadd(cmul(cs, ls[e]), cmul(cp, lp));
-            }
-        }
-        return g;
-    }
-    const int p = pos_in_B(L, o.tl);
-    if (p == 0) g = adj_pairs_at<R, M, 0>(ps, ls, ud, cm, o.kind, grad, anti);
-    else if (p == 1) g = adj_pairs_at<R, M, (M > 1 ? 1 : 0)>(ps, ls, ud, cm, o.kind, grad, anti);
-    else if (p == 2) g = adj_pairs_at<R, M, (M > 2 ? 2 : 0)>(ps, ls, ud, cm, o.kind, grad, anti);
-    else if (p == 3) g = adj_pairs_at<R, M, (M > 3 ? 3 : 0)>(ps, ls, ud, cm, o.kind, grad, anti);
-    else g = adj_pairs_at<R, M, (M > 4 ? 4 : 0)>(ps, ls, ud, cm, o.kind, grad, anti);
-    return g;
 }
 
 // FP32 (or FP64) warp sum.

@@ -17,9 +17,9 @@ namespace dq {
 struct RowProgram {
     int n = 0, M = 0;
     int nacc_shared = 0, nacc_row = 0;
-    std::vector<EOp> ops;
+    std::vector<EOp> fops, rops;   // op i decoded for its forward / reverse layout
     std::vector<ESeg> fsegs, rsegs;
-    EOp *d_ops = nullptr;
+    EOp *d_fops = nullptr, *d_rops = nullptr;
     ESeg *d_fsegs = nullptr, *d_rsegs = nullptr;
     void release();
 };

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "dq_common.cuh"
@@ -24,23 +25,27 @@
 namespace dq {
 
 void RowProgram::release() {
-    cudaFree(d_ops);
+    cudaFree(d_fops);
+    cudaFree(d_rops);
     cudaFree(d_fsegs);
     cudaFree(d_rsegs);
-    d_ops = nullptr;
+    d_fops = d_rops = nullptr;
     d_fsegs = nullptr;
     d_rsegs = nullptr;
 }
 
 namespace {
 
-// Greedy register layouts over ops visited in `order`.
-void build_segments(const std::vector<EOp> &ops, const std::vector<int> &order, int M, int k,
-                    std::vector<ESeg> &segs) {
+// Greedy register layouts over ops visited in `order`; every op is decoded
+// against the layout of the segment it falls in (into dec[op index]).
+void build_segments(const std::vector<GOp> &ops, const std::vector<int> &order, int M, int k,
+                    std::vector<ESeg> &segs, std::vector<EOp> &dec) {
+    dec.assign(ops.size(), EOp{});
     std::vector<int> B;
     int first = order.empty() ? 0 : order[0];
     int count = 0;
-    auto close = [&]() {
+    size_t start = 0;
+    auto close = [&](size_t end) {
         ESeg sg{};
         sg.op0 = first;
         sg.nops = count;
@@ -48,34 +53,46 @@ void build_segments(const std::vector<EOp> &ops, const std::vector<int> &order, 
         for (int j = kLaneBits; j < k && (int)full.size() < M; ++j)
             if (std::find(full.begin(), full.end(), j) == full.end()) full.push_back(j);
         for (int i = 0; i < 8; ++i) sg.B[i] = i < M ? (int8_t)full[i] : (int8_t)-1;
+        for (size_t x = start; x < end; ++x) dec[order[x]] = decode_op(ops[order[x]], sg.B, M);
         segs.push_back(sg);
     };
     for (size_t idx = 0; idx < order.size(); ++idx) {
-        const EOp &o = ops[order[idx]];
+        const GOp &o = ops[order[idx]];
         const int need = (o.cls != CLS_DIAG && o.tl >= kLaneBits) ? o.tl : -1;
         if (need >= 0 && std::find(B.begin(), B.end(), need) == B.end()) {
             if ((int)B.size() < M) {
                 B.push_back(need);
             } else {
-                close();
+                close(idx);
                 B.assign(1, need);
                 first = order[idx];
                 count = 0;
+                start = idx;
             }
         }
         ++count;
     }
-    close();
+    close(order.size());
 }
 
 }  // namespace
 
-// Register bits per thread for an n-qubit row: as many as fit (4 for
-// complex64, 3 for complex128), with at most 256 threads (2^(n-M)) per CTA.
+// Register bits per thread for an n-qubit row.  The widest set that fits
+// (4 for complex64, 3 for complex128) with 256 threads, or 3 / 2 with 512
+// threads; rows whose set would exceed 512 threads use another path.  The
+// environment variable DQ_ROWS_M overrides the choice (tuning experiments).
 int rows_pick_M(int n, int amp_bytes) {
-    const int mmax = amp_bytes == 8 ? 4 : 3;
-    const int m = std::min(mmax, n - kLaneBits);
-    if (m < 2 || n - m > 8) return 0;
+    const int mwide = amp_bytes == 8 ? 4 : 3;
+    int m = std::min(mwide, n - kLaneBits);
+    if (n - m > 8) m = mwide - 1;                 // narrower set, up to 512 threads
+    if (const char *env = getenv("DQ_ROWS_M")) {
+        const int v = atoi(env);
+        if (v >= 2 && v <= mwide) m = v;
+    }
+    m = std::min(m, n - kLaneBits);
+    if (m < 2) return 0;
+    const int maxt = ((1 << m) * amp_bytes <= 64) ? 512 : 256;
+    if ((1 << (n - m)) > maxt) return 0;
     return m;
 }
 
@@ -93,21 +110,21 @@ bool rows_build_program(const Plan &p, int M, RowProgram &out) {
         if (g.gkind == 2) return out.nacc_shared + p.nfeat + g.gout;
         return -1;
     };
+    std::vector<GOp> ops;
     for (int gi = 0; gi < p.ngates; ++gi) {
         const DevGate &g = p.gates[gi];
         auto push = [&](int cls, int t, int c, int slot) {
-            EOp o{};
-            o.cls = (int8_t)cls;
-            o.tl = (int8_t)t;
-            o.cl = (int8_t)c;
-            o.hasc = c >= 0 ? 1 : 0;
-            o.kind = (int16_t)g.kind;
+            GOp o{};
+            o.cls = cls;
+            o.tl = t;
             o.tg = t;
+            o.cl = c;
             o.cg = c;
+            o.kind = g.kind;
             o.coef = g.coef;
             o.rowstep = g.rowstep;
             o.slot = slot;
-            out.ops.push_back(o);
+            ops.push_back(o);
         };
         if (g.cls == CLS_SWAP) {
             push(CLS_ANTI, g.c, g.t, -1);
@@ -117,20 +134,21 @@ bool rows_build_program(const Plan &p, int M, RowProgram &out) {
             push(g.cls, g.t, g.c, acc_of(g));
         }
     }
-    std::vector<int> fwd(out.ops.size()), rev(out.ops.size());
-    for (size_t i = 0; i < out.ops.size(); ++i) {
+    std::vector<int> fwd(ops.size()), rev(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i) {
         fwd[i] = (int)i;
-        rev[i] = (int)(out.ops.size() - 1 - i);
+        rev[i] = (int)(ops.size() - 1 - i);
     }
-    build_segments(out.ops, fwd, M, n, out.fsegs);
-    build_segments(out.ops, rev, M, n, out.rsegs);
+    build_segments(ops, fwd, M, n, out.fsegs, out.fops);
+    build_segments(ops, rev, M, n, out.rsegs, out.rops);
     return true;
 }
 
 namespace {
 
 struct RowArgs {
-    const EOp *ops;
+    const EOp *fops;
+    const EOp *rops;
     const ESeg *fsegs;
     const ESeg *rsegs;
     int nops, nfseg, nrseg;
@@ -151,8 +169,13 @@ struct RowArgs {
 
 __device__ __forceinline__ uint64_t wire_bits(uint64_t m, int n) { return m ? (__brevll(m) >> (64 - n)) : 0; }
 
+// Threads per CTA are 2^(n - M): narrow register sets (at most 64 bytes of
+// amplitudes per vector and thread) may use 512 threads.
 template <typename R, int M>
-__global__ void __launch_bounds__(256) k_rows(RowArgs a) {
+constexpr int rows_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) <= 64) ? 512 : 256; }
+
+template <typename R, int M>
+__global__ void __launch_bounds__(rows_max_threads<R, M>()) k_rows(RowArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int n = a.n;
@@ -160,8 +183,9 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs a) {
     cx<R> *bufP = reinterpret_cast<cx<R> *>(smem);
     cx<R> *bufL = bufP + dim;
     unsigned char *q = smem + (a.grad ? 2 : 1) * dim * sizeof(cx<R>);
-    EOp *sops = reinterpret_cast<EOp *>(q);
-    ESeg *sf = reinterpret_cast<ESeg *>(sops + a.nops);
+    EOp *sops = reinterpret_cast<EOp *>(q);          // forward decodings
+    EOp *srops = sops + a.nops;                        // reverse decodings
+    ESeg *sf = reinterpret_cast<ESeg *>(srops + a.nops);
     ESeg *sr = sf + a.nfseg;
     Mat2<R> *scoef = reinterpret_cast<Mat2<R> *>(sr + a.nrseg);
     const int nacc = a.nacc_shared + a.nacc_row;
@@ -169,7 +193,8 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs a) {
     double *expw = acc + (size_t)nw * nacc;                        // [nw][nobs]
     const Mat2<R> *gcoef = reinterpret_cast<const Mat2<R> *>(a.coef);
     for (int i = tid; i < a.nops; i += blockDim.x) {
-        sops[i] = a.ops[i];
+        sops[i] = a.fops[i];
+        srops[i] = a.rops[i];
         scoef[i] = gcoef[sops[i].coef];
     }
     for (int i = tid; i < a.nfseg; i += blockDim.x) sf[i] = a.fsegs[i];
@@ -290,7 +315,7 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs a) {
             // segment ops run from sg.op0 downwards
             for (int c = 0; c < sg.nops; ++c) {
                 const int oi = sg.op0 - c;
-                const EOp o = sops[oi];
+                const EOp o = srops[oi];
                 const Mat2<R> u = o.rowstep ? gcoef[o.coef + (int64_t)row * o.rowstep] : scoef[oi];
                 const R g = eng_adjoint<R, M>(ps, ls, o, dagger(u), 0, L, lane);
                 if (o.slot >= 0) {
@@ -337,8 +362,8 @@ __global__ void k_rows_part_reduce(const double *__restrict__ part, int nblk, in
 size_t rows_smem_bytes(const RowProgram &rp, int amp, bool grad, int nobs, int threads) {
     const int nw = threads / 32;
     const size_t matb = amp == 8 ? sizeof(Mat2<float>) : sizeof(Mat2<double>);
-    return (size_t)(grad ? 2 : 1) * ((size_t)amp << rp.n) + rp.ops.size() * sizeof(EOp) +
-           (rp.fsegs.size() + rp.rsegs.size()) * sizeof(ESeg) + rp.ops.size() * matb +
+    return (size_t)(grad ? 2 : 1) * ((size_t)amp << rp.n) + 2 * rp.fops.size() * sizeof(EOp) +
+           (rp.fsegs.size() + rp.rsegs.size()) * sizeof(ESeg) + rp.fops.size() * matb +
            (size_t)nw * (rp.nacc_shared + rp.nacc_row + nobs) * sizeof(double) + 64;
 }
 
@@ -356,10 +381,11 @@ cudaError_t rows_launch(const RowProgram &rp, const Plan &p, const void *coef, c
     const size_t smem = rows_smem_bytes(rp, (int)sizeof(cx<R>), grad, nobs, threads);
     if (smem > smem_optin) return cudaErrorInvalidValue;
     RowArgs a;
-    a.ops = rp.d_ops;
+    a.fops = rp.d_fops;
+    a.rops = rp.d_rops;
     a.fsegs = rp.d_fsegs;
     a.rsegs = rp.d_rsegs;
-    a.nops = (int)rp.ops.size();
+    a.nops = (int)rp.fops.size();
     a.nfseg = (int)rp.fsegs.size();
     a.nrseg = (int)rp.rsegs.size();
     a.coef = coef;

@@ -145,19 +145,19 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
             }
         }
         pass.op0 = (int)out.ops.size();
+        std::vector<GOp> gops;
         auto push_op = [&](int cls, int tb, int cb, const DevGate &g, int slot) {
-            TOp o{};
-            o.cls = (int8_t)cls;
-            o.tl = (int8_t)loc[tb];
-            o.cl = (int8_t)(cb >= 0 ? loc[cb] : -1);
-            o.hasc = cb >= 0 ? 1 : 0;
-            o.kind = (int16_t)g.kind;
+            GOp o{};
+            o.cls = cls;
+            o.tl = loc[tb];
             o.tg = tb;
+            o.cl = cb >= 0 ? loc[cb] : -1;
             o.cg = cb;
+            o.kind = g.kind;
             o.coef = g.coef;
             o.rowstep = g.rowstep;
             o.slot = slot;
-            out.ops.push_back(o);
+            gops.push_back(o);
         };
         for (int gi : sched) {
             const DevGate &g = p.gates[gi];
@@ -170,23 +170,24 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
                 push_op(g.cls, g.t, g.c, g, slot);
             }
         }
-        pass.nops = (int)out.ops.size() - pass.op0;
-        // register layouts
+        pass.nops = (int)gops.size();
+        // register layouts, then decode every op against its layout
         pass.seg0 = (int)out.segs.size();
         std::vector<int> B;
-        int sop0 = pass.op0;
+        int sop0 = 0;
         auto close_seg = [&](int end) {
             TSeg sg{};
-            sg.op0 = sop0;
+            sg.op0 = pass.op0 + sop0;
             sg.nops = end - sop0;
             std::vector<int> full = B;
             for (int j = kTileLaneBits; j < k && (int)full.size() < M; ++j)
                 if (std::find(full.begin(), full.end(), j) == full.end()) full.push_back(j);
             for (int i = 0; i < 8; ++i) sg.B[i] = i < M ? (int8_t)full[i] : (int8_t)-1;
+            for (int i = sop0; i < end; ++i) out.ops.push_back(decode_op(gops[i], sg.B, M));
             out.segs.push_back(sg);
         };
-        for (int i = pass.op0; i < pass.op0 + pass.nops; ++i) {
-            const TOp &o = out.ops[i];
+        for (int i = 0; i < pass.nops; ++i) {
+            const GOp &o = gops[i];
             const int need = (o.cls != CLS_DIAG && o.tl >= kTileLaneBits) ? o.tl : -1;
             if (need < 0 || std::find(B.begin(), B.end(), need) != B.end()) continue;
             if ((int)B.size() < M) {
@@ -197,7 +198,7 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
             sop0 = i;
             B.assign(1, need);
         }
-        close_seg(pass.op0 + pass.nops);
+        close_seg(pass.nops);
         pass.nseg = (int)out.segs.size() - pass.seg0;
         out.passes.push_back(pass);
         remaining.swap(deferred);
