@@ -239,7 +239,7 @@ template <typename R, int M>
 __device__ __forceinline__ void eng_apply(cx<R> (&a)[1 << M], const EOp &o, const Mat2<R> &u, uint64_t base,
                                           const Layout &L, int lane) {
     const uint32_t cm = op_cmask(o, L, base);
-    // cm can differ between lanes (control on a lane bit): leave only when the
+    // A control on a thread bit can differ between lanes: leave only when the
     // whole warp has nothing to do, so lane operations keep every lane in
     // their full-mask shuffles.
     if (__all_sync(0xffffffffu, cm == 0)) return;

@@ -128,6 +128,12 @@ cudaError_t plain_adjoint(const Plan &p, const void *coef, const std::vector<Dev
                           double *part, double *grad_params, double *grad_data,
                           cudaStream_t s, int64_t *launches);
 size_t plain_adjoint_part_bytes(const Plan &p, int batch);
+// grad[...] from partials laid out [slot][row][blk] (nblk blocks per row).
+cudaError_t grad_reduce(const Plan &p, const double *part, int batch, int nblk, double *grad_params,
+                        double *grad_data, cudaStream_t s, int64_t *launches);
+// out[row, o] from expectation partials laid out [term][row][blk].
+cudaError_t expect_finalize_nblk(const double *part, const DevTerm *d_terms, const int32_t *d_obs_ptr, int nobs,
+                                 int batch, int nblk, double *out, cudaStream_t s, int64_t *launches);
 
 // ---- whole state in shared memory (small n) --------------------------------
 size_t wsv_smem_bytes(int n, int dtype_bytes, bool grad, int ngrad_acc);

@@ -546,6 +546,11 @@ cudaError_t plain_adjoint(const Plan &p, const void *coef, const std::vector<Dev
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    return grad_reduce(p, part, batch, nblk, grad_params, grad_data, s, launches);
+}
+
+cudaError_t grad_reduce(const Plan &p, const double *part, int batch, int nblk, double *grad_params,
+                        double *grad_data, cudaStream_t s, int64_t *launches) {
     if (grad_params && p.nparams > 0) {
         const int per_row = p.ppr;
         const int64_t nb = per_row ? (int64_t)batch * p.nparams : p.nparams;
@@ -558,6 +563,14 @@ cudaError_t plain_adjoint(const Plan &p, const void *coef, const std::vector<Dev
         k_grad_reduce<<<(unsigned)((int64_t)batch * p.nfeat), kThreads, 0, s>>>(
             part, p.d_dslot_ptr, p.d_dslots, p.nfeat, batch, nblk, 1, grad_data);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t expect_finalize_nblk(const double *part, const DevTerm *d_terms, const int32_t *d_obs_ptr, int nobs,
+                                 int batch, int nblk, double *out, cudaStream_t s, int64_t *launches) {
+    LaunchScope ls(s, "k_expect_finalize", launches);
+    k_expect_finalize<<<(unsigned)((int64_t)batch * nobs), kThreads, 0, s>>>(part, d_terms, d_obs_ptr, nobs, batch,
+                                                                            nblk, out);
     return cudaGetLastError();
 }
 

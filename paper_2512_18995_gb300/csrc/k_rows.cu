@@ -189,8 +189,9 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>()) k_rows(RowArgs a) {
     ESeg *sr = sf + a.nfseg;
     Mat2<R> *scoef = reinterpret_cast<Mat2<R> *>(sr + a.nrseg);
     const int nacc = a.nacc_shared + a.nacc_row;
-    double *acc = reinterpret_cast<double *>(scoef + a.nops);     // [nw][nacc]
-    double *expw = acc + (size_t)nw * nacc;                        // [nw][nobs]
+    double *acc = reinterpret_cast<double *>(scoef + a.nops);     // [nacc] FP64 per CTA
+    double *expw = acc + nacc;                                     // [nw][nobs]
+    R *accw = reinterpret_cast<R *>(expw + (size_t)nw * a.nobs);   // [nw][nacc] per-row partials (state precision)
     const Mat2<R> *gcoef = reinterpret_cast<const Mat2<R> *>(a.coef);
     for (int i = tid; i < a.nops; i += blockDim.x) {
         sops[i] = a.fops[i];
@@ -199,7 +200,8 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>()) k_rows(RowArgs a) {
     }
     for (int i = tid; i < a.nfseg; i += blockDim.x) sf[i] = a.fsegs[i];
     for (int i = tid; i < a.nrseg; i += blockDim.x) sr[i] = a.rsegs[i];
-    for (int i = tid; i < nw * (nacc + a.nobs); i += blockDim.x) acc[i] = 0.0;
+    for (int i = tid; i < nacc + nw * a.nobs; i += blockDim.x) acc[i] = 0.0;
+    for (int i = tid; i < nw * nacc; i += blockDim.x) accw[i] = R(0);
     __syncthreads();
 
     cx<R> ps[1 << M], ls[1 << M];
@@ -319,18 +321,28 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>()) k_rows(RowArgs a) {
                 const Mat2<R> u = o.rowstep ? gcoef[o.coef + (int64_t)row * o.rowstep] : scoef[oi];
                 const R g = eng_adjoint<R, M>(ps, ls, o, dagger(u), 0, L, lane);
                 if (o.slot >= 0) {
+                    // this row's partial over the warp's amplitude pairs
                     const R gs = warp_sum_t(g);
-                    if (lane == 0) acc[warp * nacc + o.slot] += (double)gs;
+                    if (lane == 0) accw[warp * nacc + o.slot] += gs;
                 }
             }
         }
         __syncthreads();
-        // per-row outputs
+        // fold this row's warp partials into FP64: shared parameters
+        // accumulate over the CTA's rows, per-row outputs are written out
+        for (int i = tid; i < a.nacc_shared; i += blockDim.x) {
+            double s = 0.0;
+            for (int ww = 0; ww < nw; ++ww) {
+                s += (double)accw[ww * nacc + i];
+                accw[ww * nacc + i] = R(0);
+            }
+            acc[i] += s;
+        }
         for (int i = tid; i < a.nacc_row; i += blockDim.x) {
             double s = 0.0;
             for (int ww = 0; ww < nw; ++ww) {
-                s += acc[ww * nacc + a.nacc_shared + i];
-                acc[ww * nacc + a.nacc_shared + i] = 0.0;
+                s += (double)accw[ww * nacc + a.nacc_shared + i];
+                accw[ww * nacc + a.nacc_shared + i] = R(0);
             }
             if (i < a.nfeat) {
                 if (a.grad_data) a.grad_data[(int64_t)row * a.nfeat + i] = s;
@@ -340,13 +352,8 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>()) k_rows(RowArgs a) {
         }
         __syncthreads();
     }
-    if (a.grad && a.nacc_shared && a.part) {
-        for (int i = tid; i < a.nacc_shared; i += blockDim.x) {
-            double s = 0.0;
-            for (int ww = 0; ww < nw; ++ww) s += acc[ww * nacc + i];
-            a.part[(int64_t)blockIdx.x * a.nacc_shared + i] = s;
-        }
-    }
+    if (a.grad && a.nacc_shared && a.part)
+        for (int i = tid; i < a.nacc_shared; i += blockDim.x) a.part[(int64_t)blockIdx.x * a.nacc_shared + i] = acc[i];
 }
 
 __global__ void k_rows_part_reduce(const double *__restrict__ part, int nblk, int np, double *__restrict__ out) {
@@ -364,7 +371,8 @@ size_t rows_smem_bytes(const RowProgram &rp, int amp, bool grad, int nobs, int t
     const size_t matb = amp == 8 ? sizeof(Mat2<float>) : sizeof(Mat2<double>);
     return (size_t)(grad ? 2 : 1) * ((size_t)amp << rp.n) + 2 * rp.fops.size() * sizeof(EOp) +
            (rp.fsegs.size() + rp.rsegs.size()) * sizeof(ESeg) + rp.fops.size() * matb +
-           (size_t)nw * (rp.nacc_shared + rp.nacc_row + nobs) * sizeof(double) + 64;
+           (size_t)(rp.nacc_shared + rp.nacc_row + nw * nobs) * sizeof(double) +
+           (size_t)nw * (rp.nacc_shared + rp.nacc_row) * (amp == 8 ? sizeof(float) : sizeof(double)) + 64;
 }
 
 size_t rows_part_bytes(const Plan &p, int nsm) {
