@@ -510,10 +510,21 @@ dq_status expect_impl(dq_ctx *ctx, int n, ObsDev &o, const void *state, int batc
                 "fused expect");
         return DQ_OK;
     }
-    const size_t part = plain_expect_part_bytes(n, (int)o.bits.size(), batch);
+    const bool tile = use_fused(ctx) && tile_supported(n, (int)sizeof(cx<R>));
+    const size_t part = std::max(plain_expect_part_bytes(n, (int)o.bits.size(), batch),
+                                 tile_expect_part_bytes(n, (int)o.bits.size(), batch, ctx->nsm));
     dq_status st = reserve(ctx, part + 256);
     if (st != DQ_OK) return st;
     double *pbuf = (double *)ctx->ws;
+    if (tile) {
+        cudaError_t e = tile_observe<R>(ctx->tiles, n, o.bits, o.d_bits, o.d_ptr, o.nobs, nullptr, state, nullptr,
+                                        batch, pbuf, out, ctx->nsm, s, &ctx->launches);
+        if (e != cudaErrorNotSupported) {
+            DQ_CUDA(e, "tiled expect");
+            return DQ_OK;
+        }
+        cudaGetLastError();
+    }
     DQ_CUDA(plain_expect<R>(n, o.bits, o.nobs, state, batch, pbuf, out, s, &ctx->launches), "expect");
     DQ_CUDA(plain_expect_finalize(pbuf, o.d_bits, o.d_ptr, o.nobs, n, batch, out, s, &ctx->launches),
             "expect finalize");
@@ -535,9 +546,10 @@ dq_status adjoint_impl(dq_ctx *ctx, Plan &p, ObsDev &o, const double *params, co
     if (small) {
         a.take(std::max(wsv_part_bytes(p, ctx->nsm), rows_part_bytes(p, ctx->nsm)));
     } else {
-        if (!clobber) a.take(sbytes);
         a.take(sbytes);
-        a.take(plain_adjoint_part_bytes(p, batch));
+        a.take(std::max(plain_adjoint_part_bytes(p, batch), std::max(tile_adjoint_part_bytes(p, batch, ctx->nsm),
+                                                                   tile_expect_part_bytes(p.n, 1, batch, ctx->nsm))));
+        if (!clobber) a.take(sbytes);
     }
     dq_status st = reserve(ctx, a.used);
     if (st != DQ_OK) return st;
@@ -558,13 +570,35 @@ dq_status adjoint_impl(dq_ctx *ctx, Plan &p, ObsDev &o, const double *params, co
                     "fused adjoint");
         return DQ_OK;
     }
+    void *lam = w.take(sbytes);
+    double *part = (double *)w.take(std::max(plain_adjoint_part_bytes(p, batch),
+                                             std::max(tile_adjoint_part_bytes(p, batch, ctx->nsm),
+                                                      tile_expect_part_bytes(p.n, 1, batch, ctx->nsm))));
     void *psi = state;
-    if (!clobber) {
+    const bool tile = use_fused(ctx) && tile_supported(p.n, (int)sizeof(cx<R>));
+    if (tile) {
+        // lambda from the caller's state (read only), then the sweep on a copy
+        cudaError_t e = tile_observe<R>(ctx->tiles, p.n, o.bits, o.d_bits, o.d_ptr, o.nobs, rw, state, lam, batch,
+                                        part, nullptr, ctx->nsm, s, &ctx->launches);
+        if (e == cudaSuccess) {
+            if (!clobber) {
+                psi = w.take(sbytes);
+                DQ_CUDA(cudaMemcpyAsync(psi, state, sbytes, cudaMemcpyDeviceToDevice, s), "copy state");
+            }
+            e = tile_adjoint<R>(ctx->tiles, ctx->tuned, p, coef, psi, lam, batch, part, gp, gd, ctx->nsm, s,
+                                &ctx->launches);
+            if (e != cudaErrorNotSupported) {
+                DQ_CUDA(e, "tiled adjoint");
+                return DQ_OK;
+            }
+        }
+        if (e != cudaErrorNotSupported) DQ_CUDA(e, "tiled lambda");
+        cudaGetLastError();
+    }
+    if (!clobber && psi == state) {
         psi = w.take(sbytes);
         DQ_CUDA(cudaMemcpyAsync(psi, state, sbytes, cudaMemcpyDeviceToDevice, s), "copy state");
     }
-    void *lam = w.take(sbytes);
-    double *part = (double *)w.take(plain_adjoint_part_bytes(p, batch));
     DQ_CUDA(plain_adjoint<R>(p, coef, o.bits, o.nobs, rw, psi, lam, batch, part, gp, gd, s, &ctx->launches),
             "plain adjoint");
     return DQ_OK;
@@ -613,9 +647,10 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     if (grad) {
         a.take(sbytes);                      // lambda
         if (state_out) a.take(sbytes);       // working copy of psi (state_out preserved)
-        a.take(plain_adjoint_part_bytes(p, batch));
+        a.take(std::max(plain_adjoint_part_bytes(p, batch), tile_adjoint_part_bytes(p, batch, ctx->nsm)));
     }
-    if (o) a.take(plain_expect_part_bytes(p.n, (int)o->bits.size(), batch));
+    if (o) a.take(std::max(plain_expect_part_bytes(p.n, (int)o->bits.size(), batch),
+                           tile_expect_part_bytes(p.n, (int)o->bits.size(), batch, ctx->nsm)));
     if (tile) a.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>)));
     dq_status st = reserve(ctx, a.used);
     if (st != DQ_OK) return st;
@@ -629,10 +664,11 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     if (grad) {
         lam = w.take(sbytes);
         if (state_out) work = w.take(sbytes);
-        gpart = (double *)w.take(plain_adjoint_part_bytes(p, batch));
+        gpart = (double *)w.take(std::max(plain_adjoint_part_bytes(p, batch), tile_adjoint_part_bytes(p, batch, ctx->nsm)));
     }
     double *epart = nullptr;
-    if (o) epart = (double *)w.take(plain_expect_part_bytes(p.n, (int)o->bits.size(), batch));
+    if (o) epart = (double *)w.take(std::max(plain_expect_part_bytes(p.n, (int)o->bits.size(), batch),
+                                             tile_expect_part_bytes(p.n, (int)o->bits.size(), batch, ctx->nsm)));
     void *tws = tile ? w.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>))) : nullptr;
     DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
     DQ_CUDA(plain_init_zero<R>(psi, p.n, batch, s, &ctx->launches), "init");
@@ -646,12 +682,34 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     } else {
         DQ_CUDA(plain_apply<R>(p, coef, psi, batch, 0, s, &ctx->launches), "plain apply");
     }
-    if (o && eo) {
+    bool done_obs = false, done_grad = false;
+    if (tile && o && (eo || grad)) {
+        // expectations and lambda in one set of observable passes
+        cudaError_t e = tile_observe<R>(ctx->tiles, p.n, o->bits, o->d_bits, o->d_ptr, o->nobs, rw, psi,
+                                        grad ? lam : nullptr, batch, epart, eo, ctx->nsm, s, &ctx->launches);
+        if (e == cudaSuccess) {
+            done_obs = true;
+            if (grad) {
+                if (work != psi)
+                    DQ_CUDA(cudaMemcpyAsync(work, psi, sbytes, cudaMemcpyDeviceToDevice, s), "copy state");
+                e = tile_adjoint<R>(ctx->tiles, ctx->tuned, p, coef, work, lam, batch, gpart, gp, gd, ctx->nsm, s,
+                                    &ctx->launches);
+                if (e == cudaSuccess) done_grad = true;
+                else if (e != cudaErrorNotSupported) DQ_CUDA(e, "tiled adjoint");
+                else cudaGetLastError();
+            }
+        } else if (e != cudaErrorNotSupported) {
+            DQ_CUDA(e, "tiled observables");
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (o && eo && !done_obs) {
         DQ_CUDA(plain_expect<R>(p.n, o->bits, o->nobs, psi, batch, epart, eo, s, &ctx->launches), "expect");
         DQ_CUDA(plain_expect_finalize(epart, o->d_bits, o->d_ptr, o->nobs, p.n, batch, eo, s, &ctx->launches),
                 "expect finalize");
     }
-    if (grad) {
+    if (grad && !done_grad) {
         if (work != psi) DQ_CUDA(cudaMemcpyAsync(work, psi, sbytes, cudaMemcpyDeviceToDevice, s), "copy state");
         DQ_CUDA(plain_adjoint<R>(p, coef, o->bits, o->nobs, rw, work, lam, batch, gpart, gp, gd, s, &ctx->launches),
                 "plain adjoint");
@@ -809,8 +867,8 @@ dq_status dq_workspace_bytes(dq_ctx *ctx, const dq_circuit *circuit, const dq_ob
     a.take(plain_expect_part_bytes(p->n, nterms, batch));
     a.take(std::max(wsv_part_bytes(*p, ctx->nsm), rows_part_bytes(*p, ctx->nsm)));
     a.take(tile_workspace_bytes(*p, batch, amp_bytes(dtype)));
-    a.take(tile_adjoint_part_bytes(*p, batch));
-    a.take(tile_expect_part_bytes(p->n, nterms, batch));
+    a.take(tile_adjoint_part_bytes(*p, batch, ctx->nsm));
+    a.take(tile_expect_part_bytes(p->n, nterms, batch, ctx->nsm));
     *out = a.used;
     return DQ_OK;
 }

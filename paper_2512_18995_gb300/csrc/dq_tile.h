@@ -28,18 +28,27 @@ using TOp = EOp;
 using TSeg = ESeg;
 
 struct TPass {
-    std::vector<int> T;     // tile bits, ascending (amplitude bits)
-    int seg0 = 0, nseg = 0; // into the schedule's segment array
-    int op0 = 0, nops = 0;  // into the schedule's op array
+    std::vector<int> T;       // tile bits, ascending (amplitude bits)
+    int seg0 = 0, nseg = 0;   // into the schedule's segment array
+    int op0 = 0, nops = 0;    // into the schedule's op array
+    int rseg0 = 0, nrseg = 0; // reverse-sweep layouts (adjoint schedules)
+    int slot0 = 0, nslot = 0; // gradient slots of the pass (adjoint schedules)
 };
 
+// Passes of fused gates.  Adjoint schedules also carry, per pass, the ops
+// decoded for reverse-sweep layouts (rops[i] pairs with ops[i]; reverse
+// segments name their highest op in op0 and run downwards) and the global
+// gradient slots of the pass (rops carry local slot indices).
 struct TileSchedule {
     int n = 0, k = 0, low = 0, M = 0;
+    bool adjoint = false;
     std::vector<TPass> passes;
-    std::vector<TOp> ops;
-    std::vector<TSeg> segs;
-    TOp *d_ops = nullptr;
-    TSeg *d_segs = nullptr;
+    std::vector<TOp> ops, rops;
+    std::vector<TSeg> segs, rsegs;
+    std::vector<int32_t> slots;
+    TOp *d_ops = nullptr, *d_rops = nullptr;
+    TSeg *d_segs = nullptr, *d_rsegs = nullptr;
+    int32_t *d_slots = nullptr;
     void release();
 };
 
@@ -56,33 +65,42 @@ struct TileCache {
     void *encode_fn = nullptr;
     int *errflag = nullptr;             // device error flag of the owning context
     std::unordered_map<uint64_t, TileSchedule *> schedules;
+    std::unordered_map<uint64_t, void *> obs;   // observable-pass schedules
     void release();
 };
 
+void tile_release_obs(TileCache &tc);
+
 bool tile_supported(int n, int amp_bytes);
 size_t tile_workspace_bytes(const Plan &p, int batch, int amp_bytes);
-size_t tile_adjoint_part_bytes(const Plan &p, int batch);
-size_t tile_expect_part_bytes(int n, int nterms, int batch);
+size_t tile_adjoint_part_bytes(const Plan &p, int batch, int nsm);
+size_t tile_expect_part_bytes(int n, int nterms, int batch, int nsm);
 
 template <typename R>
 cudaError_t tile_apply(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
                        const void *coef, void *state, int batch, void *tws, int nsm, cudaStream_t s,
                        int64_t *launches);
+// Observable passes: expectations (when out != null) and, when lam != null,
+// lambda = sum_o w_o O_o psi for the adjoint sweep.  part: expectation
+// partials [term][row][cta].
 template <typename R>
-cudaError_t tile_expect(TileCache &tc, int n, const std::vector<DevTerm> &bits, const DevTerm *d_bits,
-                        const int32_t *d_ptr, int nobs, const void *state, int batch, double *part,
-                        double *out, void *tws, int nsm, cudaStream_t s, int64_t *launches);
+cudaError_t tile_observe(TileCache &tc, int n, const std::vector<DevTerm> &bits, const DevTerm *d_bits,
+                         const int32_t *d_ptr, int nobs, const double *rw, const void *psi, void *lam, int batch,
+                         double *part, double *out, int nsm, cudaStream_t s, int64_t *launches);
+// Reverse sweep on (psi, lam) with gradients.  part: [slot][row][cta].
 template <typename R>
 cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
-                         const void *coef, const std::vector<DevTerm> &bits, int nobs, const double *rw,
-                         void *psi, void *lam, int batch, double *part, double *gp, double *gd, void *tws,
+                         const void *coef, void *psi, void *lam, int batch, double *part, double *gp, double *gd,
                          int nsm, cudaStream_t s, int64_t *launches);
 template <typename R>
 cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
                           const void *coef, void *state, int batch, void *tws, int nsm, cudaStream_t s,
                           int64_t *launches);
 
-// Host planner (exposed for tests of the schedule logic).
-bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, TileSchedule &out);
+TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, int amp, bool adjoint);
+
+// Host planner.
+bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, TileSchedule &out,
+                         bool adjoint = false);
 
 }  // namespace dq

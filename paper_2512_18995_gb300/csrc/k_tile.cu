@@ -27,17 +27,23 @@
 #include "dq_common.cuh"
 #include "dq_engine.cuh"
 #include "dq_tile.h"
+#include "dq_tma.cuh"
 
 namespace dq {
 
 void TileSchedule::release() {
     cudaFree(d_ops);
     cudaFree(d_segs);
-    d_ops = nullptr;
-    d_segs = nullptr;
+    cudaFree(d_rops);
+    cudaFree(d_rsegs);
+    cudaFree(d_slots);
+    d_ops = d_rops = nullptr;
+    d_segs = d_rsegs = nullptr;
+    d_slots = nullptr;
 }
 
 void TileCache::release() {
+    tile_release_obs(*this);
     for (auto &kv : schedules) {
         kv.second->release();
         delete kv.second;
@@ -90,7 +96,7 @@ GateBits gate_bits(const DevGate &g) {
 
 }  // namespace
 
-bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, TileSchedule &out) {
+bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, TileSchedule &out, bool adjoint) {
     const int n = p.n;
     const int wb = amp_bytes == 16 ? 1 : 0;
     // a SWAP of two high bits needs two free tile bits
@@ -100,6 +106,7 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
     out.k = k;
     out.low = low;
     out.M = M;
+    out.adjoint = adjoint;
     const uint64_t lowmask = (uint64_t(1) << low) - 1;
     std::vector<int> remaining(p.ngates);
     for (int i = 0; i < p.ngates; ++i) remaining[i] = i;
@@ -200,6 +207,56 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
         }
         close_seg(pass.nops);
         pass.nseg = (int)out.segs.size() - pass.seg0;
+        if (adjoint) {
+            // local gradient slots of the pass
+            pass.slot0 = (int)out.slots.size();
+            for (GOp &o : gops) {
+                if (o.slot < 0) continue;
+                int loc_slot = -1;
+                for (int i = pass.slot0; i < (int)out.slots.size(); ++i)
+                    if (out.slots[i] == o.slot) loc_slot = i - pass.slot0;
+                if (loc_slot < 0) {
+                    loc_slot = (int)out.slots.size() - pass.slot0;
+                    out.slots.push_back(o.slot);
+                }
+                o.slot = loc_slot;
+            }
+            pass.nslot = (int)out.slots.size() - pass.slot0;
+            // reverse-sweep layouts over the pass's ops, last op first
+            out.rops.resize(out.ops.size());
+            pass.rseg0 = (int)out.rsegs.size();
+            std::vector<int> RB;
+            int first = pass.nops - 1, count = 0, start = pass.nops - 1;
+            auto close_r = [&](int stop) {   // ops start .. stop+1 (descending)
+                TSeg sg{};
+                sg.op0 = pass.op0 + first;
+                sg.nops = count;
+                std::vector<int> full = RB;
+                for (int j = kTileLaneBits; j < k && (int)full.size() < M; ++j)
+                    if (std::find(full.begin(), full.end(), j) == full.end()) full.push_back(j);
+                for (int i = 0; i < 8; ++i) sg.B[i] = i < M ? (int8_t)full[i] : (int8_t)-1;
+                for (int i = start; i > stop; --i) out.rops[pass.op0 + i] = decode_op(gops[i], sg.B, M);
+                out.rsegs.push_back(sg);
+            };
+            for (int i = pass.nops - 1; i >= 0; --i) {
+                const GOp &o = gops[i];
+                const int need = (o.cls != CLS_DIAG && o.tl >= kTileLaneBits) ? o.tl : -1;
+                if (need >= 0 && std::find(RB.begin(), RB.end(), need) == RB.end()) {
+                    if ((int)RB.size() < M) {
+                        RB.push_back(need);
+                    } else {
+                        close_r(i);
+                        RB.assign(1, need);
+                        first = i;
+                        count = 0;
+                        start = i;
+                    }
+                }
+                ++count;
+            }
+            close_r(-1);
+            pass.nrseg = (int)out.rsegs.size() - pass.rseg0;
+        }
         out.passes.push_back(pass);
         remaining.swap(deferred);
     }
@@ -208,174 +265,14 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
 
 namespace {
 
-// ---------------------------------------------------------------------------
-// TMA descriptor for one pass
-// ---------------------------------------------------------------------------
-struct TileDims {
-    int rank = 0;
-    int rlen[5] = {0, 0, 0, 0, 0};   // log2 box side (word bits)
-    int glen[5] = {0, 0, 0, 0, 0};   // gap bits after the run (tile-index bits of this dim)
-    int s[5] = {0, 0, 0, 0, 0};      // first word bit of the dim
-};
-
-bool make_dims(const std::vector<int> &T, int n, int wb, TileDims &d) {
-    std::vector<int> w;
-    for (int i = 0; i < wb; ++i) w.push_back(i);
-    for (int t : T) w.push_back(t + wb);
-    const int W = n + wb;
-    // runs split into chunks of at most 8 bits
-    std::vector<std::pair<int, int>> runs;   // (start, len)
-    size_t i = 0;
-    while (i < w.size()) {
-        size_t j = i;
-        while (j + 1 < w.size() && w[j + 1] == w[j] + 1) ++j;
-        int st = w[i], len = (int)(j - i + 1);
-        while (len > 0) {
-            const int l = std::min(8, len);
-            runs.push_back({st, l});
-            st += l;
-            len -= l;
-        }
-        i = j + 1;
-    }
-    if (runs.empty() || runs.size() > 5 || runs[0].first != 0) return false;
-    d.rank = (int)runs.size();
-    for (int r = 0; r < d.rank; ++r) {
-        d.s[r] = runs[r].first;
-        d.rlen[r] = runs[r].second;
-        const int next = (r + 1 < d.rank) ? runs[r + 1].first : W;
-        d.glen[r] = next - runs[r].first - runs[r].second;
-    }
-    return true;
-}
-
-bool encode_map(void *fn, CUtensorMap *map, const TileDims &d, void *base, int64_t batch, int wb) {
-    cuuint64_t dims[5];
-    cuuint64_t strides[4];
-    cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
-    uint64_t stride = 8;   // bytes of one 8-byte word
-    for (int r = 0; r < 5; ++r) {
-        if (r < d.rank) {
-            const int width = d.rlen[r] + d.glen[r];
-            uint64_t size = uint64_t(1) << width;
-            if (r == d.rank - 1) size *= (uint64_t)batch;
-            dims[r] = size;
-            box[r] = 1u << d.rlen[r];
-            if (r > 0) strides[r - 1] = stride;
-            stride <<= width;
-        } else {
-            dims[r] = 1;
-            box[r] = 1;
-            strides[r - 1] = stride;
-        }
-    }
-    (void)wb;
-    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    CUresult res = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, base, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return res == CUDA_SUCCESS;
-}
-
-// ---------------------------------------------------------------------------
-// device helpers: mbarrier and TMA
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for phase `parity` of the barrier for at most ~2 s of wall time.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (global_ns() - t0 > 2000000000ull) return false;
-    }
-}
-
-__device__ __forceinline__ void tma_load5(void *dst, const CUtensorMap *map, const int c[5], uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]),
-        "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_store5(const CUtensorMap *map, const int c[5], const void *src) {
-    asm volatile(
-        "cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(
-            reinterpret_cast<uint64_t>(map)),
-        "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(smem_u32(src))
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 struct TileKArgs {
     const TOp *ops;
     const TSeg *segs;
     int op0, nops, seg0, nseg;
     const void *coef;
-    int n, k, wb;
-    int64_t ntiles;
-    int rank;
-    int rlen[5], glen[5], s[5];
+    TileGeom g;
     int *errflag;
 };
-
-__device__ __forceinline__ void tile_coords(const TileKArgs &a, int64_t t, int c[5], uint64_t &base, int64_t &row) {
-    uint64_t rem = (uint64_t)t;
-    uint64_t word = 0;
-#pragma unroll
-    for (int r = 0; r < 5; ++r) {
-        c[r] = 0;
-        if (r < a.rank) {
-            uint64_t v;
-            if (r < a.rank - 1) {
-                v = rem & ((uint64_t(1) << a.glen[r]) - 1);
-                rem >>= a.glen[r];
-            } else {
-                v = rem;
-            }
-            const uint64_t coord = v << a.rlen[r];
-            c[r] = (int)coord;
-            word |= coord << a.s[r];
-        }
-    }
-    const uint64_t amp = word >> a.wb;
-    row = (int64_t)(amp >> a.n);
-    base = amp & ((uint64_t(1) << a.n) - 1);
-}
 
 // Threads per CTA are 2^(k - M); wide register sets (256 bytes of amplitudes
 // per thread) are limited to 256 threads so that they keep their registers.
@@ -387,7 +284,7 @@ __global__ void __launch_bounds__(tile_max_threads<R, M>(), 1)
 k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const size_t tbytes = sizeof(cx<R>) << a.k;
+    const size_t tbytes = sizeof(cx<R>) << a.g.k;
     cx<R> *buf0 = reinterpret_cast<cx<R> *>(smem);
     cx<R> *buf1 = reinterpret_cast<cx<R> *>(smem + tbytes);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * tbytes);
@@ -406,15 +303,15 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
         fence_async_smem();
     }
     __syncthreads();
-    const int64_t per = (a.ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * per;
-    const int64_t t1 = min(a.ntiles, t0 + per);
+    const int64_t t1 = min(a.g.ntiles, t0 + per);
     if (t0 >= t1) return;
     int c[5];
     uint64_t base;
     int64_t row;
     if (tid == 0) {
-        tile_coords(a, t0, c, base, row);
+        geom_coords(a.g, t0, c, base, row);
         mbar_expect_tx(&bar[0], (uint32_t)tbytes);
         tma_load5(buf0, &tmap, c, &bar[0]);
     }
@@ -428,7 +325,7 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
             int cn[5];
             uint64_t bn;
             int64_t rn;
-            tile_coords(a, t + 1, cn, bn, rn);
+            geom_coords(a.g, t + 1, cn, bn, rn);
             bulk_wait_read0();   // the other buffer's previous store has read its data
             uint64_t *nb = b ? &bar[0] : &bar[1];
             mbar_expect_tx(nb, (uint32_t)tbytes);
@@ -440,10 +337,10 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
             failed = true;
             break;
         }
-        tile_coords(a, t, c, base, row);
+        geom_coords(a.g, t, c, base, row);
         for (int si = 0; si < a.nseg; ++si) {
             const TSeg sg = ssegs[si];
-            const Layout L = make_layout(sg, M, a.k, lane, warp);
+            const Layout L = make_layout(sg, M, a.g.k, lane, warp);
             eng_load<R, M>(r, cur, L);
             for (int oi = sg.op0 - a.op0; oi < sg.op0 - a.op0 + sg.nops; ++oi) {
                 const TOp o = sops[oi];
@@ -476,8 +373,8 @@ size_t tile_smem_bytes(int k, int amp, int nops, int nseg) {
            (size_t)nops * (amp == 8 ? sizeof(Mat2<float>) : sizeof(Mat2<double>)) + 64;
 }
 
-uint64_t sched_key(const Plan &p, int k, int low, int amp, int M) {
-    uint64_t h = p.key ^ 0x9E3779B97F4A7C15ull;
+uint64_t sched_key(const Plan &p, int k, int low, int amp, int M, bool adjoint = false) {
+    uint64_t h = p.key ^ (adjoint ? 0x51ED270B27A4C3F1ull : 0x9E3779B97F4A7C15ull);
     h = (h ^ (uint64_t)M) * 1099511628211ull;
     h = (h ^ (uint64_t)k) * 1099511628211ull;
     h = (h ^ (uint64_t)low) * 1099511628211ull;
@@ -485,22 +382,6 @@ uint64_t sched_key(const Plan &p, int k, int low, int amp, int M) {
     return h;
 }
 
-bool ensure_encode_fn(TileCache &tc) {
-    if (tc.encode_fn) return true;
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-        cudaGetLastError();
-        return false;
-    }
-    tc.encode_fn = fn;
-    return true;
-}
-
-// Default tile: HBM-resident states (>= 2^25 amplitudes) take wide tiles and
-// wide register sets; L2-resident ones take narrower tiles and more warps per
-// tile so that every SM has work.
 template <typename R>
 void default_tile(int n, int &k, int &low, int &M) {
     if (n >= 25) {
@@ -525,26 +406,42 @@ const void *tile_kernel(int M) {
     }
 }
 
-TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, int amp) {
-    const uint64_t key = sched_key(p, k, low, amp, M);
+template <typename T>
+bool upload_vec(T **dst, const std::vector<T> &v) {
+    if (cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(1, v.size())) != cudaSuccess) {
+        cudaGetLastError();
+        *dst = nullptr;
+        return false;
+    }
+    if (!v.empty() && cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return false;
+    return true;
+}
+
+}  // namespace
+
+TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, int amp, bool adjoint) {
+    const uint64_t key = sched_key(p, k, low, amp, M, adjoint);
     auto it = tc.schedules.find(key);
     if (it != tc.schedules.end()) return it->second;
     TileSchedule *s = new TileSchedule();
-    if (!tile_build_schedule(p, k, low, M, amp, *s)) {
+    if (!tile_build_schedule(p, k, low, M, amp, *s, adjoint)) {
         delete s;
         return nullptr;
     }
-    if (cudaMalloc((void **)&s->d_ops, sizeof(TOp) * std::max<size_t>(1, s->ops.size())) != cudaSuccess ||
-        cudaMalloc((void **)&s->d_segs, sizeof(TSeg) * std::max<size_t>(1, s->segs.size())) != cudaSuccess) {
+    bool ok = upload_vec(&s->d_ops, s->ops) && upload_vec(&s->d_segs, s->segs);
+    if (ok && adjoint)
+        ok = upload_vec(&s->d_rops, s->rops) && upload_vec(&s->d_rsegs, s->rsegs) && upload_vec(&s->d_slots, s->slots);
+    if (!ok) {
         s->release();
         delete s;
         return nullptr;
     }
-    cudaMemcpy(s->d_ops, s->ops.data(), sizeof(TOp) * s->ops.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(s->d_segs, s->segs.data(), sizeof(TSeg) * s->segs.size(), cudaMemcpyHostToDevice);
     tc.schedules[key] = s;
     return s;
 }
+
+namespace {
 
 template <typename R>
 cudaError_t run_forward(TileCache &tc, const Plan &p, const TileSchedule &sc, const void *coef, void *state,
@@ -566,16 +463,7 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, const TileSchedule &sc, co
         a.seg0 = ps.seg0;
         a.nseg = ps.nseg;
         a.coef = coef;
-        a.n = p.n;
-        a.k = sc.k;
-        a.wb = wb;
-        a.ntiles = (int64_t)batch << (p.n - sc.k);
-        a.rank = d.rank;
-        for (int r = 0; r < 5; ++r) {
-            a.rlen[r] = d.rlen[r];
-            a.glen[r] = d.glen[r];
-            a.s[r] = d.s[r];
-        }
+        a.g = make_geom(d, p.n, sc.k, wb, batch);
         a.errflag = tc.errflag;
         const size_t smem = tile_smem_bytes(sc.k, amp, ps.nops, ps.nseg);
         const void *kfn = tile_kernel<R>(M);
@@ -584,7 +472,7 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, const TileSchedule &sc, co
         int per_sm = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem);
         per_sm = std::max(1, per_sm);
-        const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)per_sm * nsm);
+        const int64_t grid = std::min<int64_t>(a.g.ntiles, (int64_t)per_sm * nsm);
         LaunchScope ls(s, "k_tile_fwd", launches);
         switch (M) {
         case 2: k_tile_fwd<R, 2><<<(unsigned)grid, threads, smem, s>>>(map, a); break;
@@ -605,8 +493,6 @@ bool tile_supported(int n, int amp_bytes) {
     return n >= kTileLaneBits + 3 + 1 && n <= 34;
 }
 size_t tile_workspace_bytes(const Plan &, int, int) { return 0; }
-size_t tile_adjoint_part_bytes(const Plan &, int) { return 0; }
-size_t tile_expect_part_bytes(int, int, int) { return 0; }
 
 template <typename R>
 cudaError_t tile_apply(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
@@ -622,21 +508,9 @@ cudaError_t tile_apply(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tu
         low = it->second.low;
         M = it->second.M;
     }
-    TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>));
+    TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), false);
     if (!sc) return cudaErrorNotSupported;
     return run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches);
-}
-
-template <typename R>
-cudaError_t tile_expect(TileCache &, int, const std::vector<DevTerm> &, const DevTerm *, const int32_t *, int,
-                        const void *, int, double *, double *, void *, int, cudaStream_t, int64_t *) {
-    return cudaErrorNotSupported;
-}
-template <typename R>
-cudaError_t tile_adjoint(TileCache &, std::unordered_map<uint64_t, TileTune> &, const Plan &, const void *,
-                         const std::vector<DevTerm> &, int, const double *, void *, void *, int, double *,
-                         double *, double *, void *, int, cudaStream_t, int64_t *) {
-    return cudaErrorNotSupported;
 }
 
 template <typename R>
@@ -658,7 +532,7 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
         if ((1 << (k - M)) > maxt) continue;
         for (int low : {5, 7}) {
             if (low > k - 2) continue;
-            TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>));
+            TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), false);
             if (!sc) continue;
             cudaError_t err = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches);   // warm
             if (err != cudaSuccess) {
@@ -689,13 +563,6 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
 #define DQ_INST(R)                                                                                            \
     template cudaError_t tile_apply<R>(TileCache &, std::unordered_map<uint64_t, TileTune> &, const Plan &,   \
                                        const void *, void *, int, void *, int, cudaStream_t, int64_t *);     \
-    template cudaError_t tile_expect<R>(TileCache &, int, const std::vector<DevTerm> &, const DevTerm *,      \
-                                        const int32_t *, int, const void *, int, double *, double *, void *,  \
-                                        int, cudaStream_t, int64_t *);                                        \
-    template cudaError_t tile_adjoint<R>(TileCache &, std::unordered_map<uint64_t, TileTune> &, const Plan &, \
-                                         const void *, const std::vector<DevTerm> &, int, const double *,     \
-                                         void *, void *, int, double *, double *, double *, void *, int,      \
-                                         cudaStream_t, int64_t *);                                            \
     template cudaError_t tile_autotune<R>(TileCache &, std::unordered_map<uint64_t, TileTune> &, const Plan &, \
                                           const void *, void *, int, void *, int, cudaStream_t, int64_t *);
 DQ_INST(float)

@@ -1,0 +1,593 @@
+// Large-state observables and adjoint sweep on TMA-staged tiles.
+//
+// Observable passes (k_tile_obs): Pauli terms are grouped so that every
+// term's flip bits lie inside the pass's tile.  For each tile the pass adds
+// sum_l conj(psi[l ^ f]) ph(l) psi[l] to the term's expectation partial
+// (API Overview: expectation of Pauli-string observables) and, for the
+// adjoint method, lambda[l] += w c ph(l ^ f) psi[l ^ f] (lambda = sum_o w_o O_o
+// psi), writing lambda back.  Products are formed in the state precision,
+// warp sums too, and everything above a tile's warp sum is FP64.
+//
+// Reverse sweep (k_tile_adj): the passes of an adjoint schedule are visited
+// last to first; each loads a psi tile and a lambda tile, runs the pass's gates
+// in reverse on the in-register engine (gradient partial 2 Im <lambda|G|psi>
+// of every parametric gate, then U^dagger on both vectors; Sec. "Distributed
+// Simulations", adjoint differentiation) and stores both tiles.  Gradient
+// partials are kept per CTA in FP64 and written per batch row to a
+// [slot][row][cta] array that the deterministic slot reduction sums.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "dq_common.cuh"
+#include "dq_engine.cuh"
+#include "dq_plan.h"
+#include "dq_tile.h"
+#include "dq_tma.cuh"
+
+namespace dq {
+
+namespace {
+
+// One Pauli term of an observable pass, in the pass's tile coordinates.
+struct OTerm {
+    uint32_t floc;   // flip mask (local tile bits)
+    uint32_t sloc;   // sign mask (local tile bits)
+    uint64_t sout;   // sign mask outside the tile (amplitude bits)
+    int32_t nY;
+    int32_t term;    // global term index
+    int32_t obs;
+    int32_t pad;
+    double coeff;
+    double pad2;
+};
+
+struct OPass {
+    std::vector<int> T;
+    int t0 = 0, nt = 0;
+};
+
+struct ObsSchedule {
+    int n = 0, k = 0, low = 0;
+    std::vector<OPass> passes;
+    std::vector<OTerm> terms;
+    OTerm *d_terms = nullptr;
+};
+
+int dims_needed_obs(uint64_t T, int wb) {
+    uint64_t w = (T << wb) | ((uint64_t(1) << wb) - 1);
+    int dims = 0, b = 0;
+    while (w >> b) {
+        if (!((w >> b) & 1)) {
+            ++b;
+            continue;
+        }
+        int len = 0;
+        while ((w >> (b + len)) & 1) ++len;
+        dims += (len + 7) / 8;
+        b += len;
+    }
+    return dims;
+}
+
+bool build_obs_schedule(const std::vector<DevTerm> &bits, int n, int k, int low, int wb, ObsSchedule &out) {
+    out = ObsSchedule();
+    out.n = n;
+    out.k = k;
+    out.low = low;
+    const uint64_t lowmask = (uint64_t(1) << low) - 1;
+    std::vector<int> remaining(bits.size());
+    for (size_t i = 0; i < bits.size(); ++i) remaining[i] = (int)i;
+    int guard = 0;
+    while (!remaining.empty()) {
+        if (++guard > (int)bits.size() + 2) return false;
+        uint64_t T = lowmask;
+        std::vector<int> take, rest;
+        for (int i : remaining) {
+            const uint64_t nt = T | bits[i].f;
+            if (__builtin_popcountll(nt) <= k && dims_needed_obs(nt, wb) <= 5) {
+                T = nt;
+                take.push_back(i);
+            } else {
+                rest.push_back(i);
+            }
+        }
+        if (take.empty()) return false;
+        for (int b = 0; b < n && __builtin_popcountll(T) < k; ++b) {
+            if ((T >> b) & 1) continue;
+            const uint64_t nt = T | (uint64_t(1) << b);
+            if (dims_needed_obs(nt, wb) <= 5) T = nt;
+        }
+        if (__builtin_popcountll(T) != k) return false;
+        OPass ps;
+        int loc[64];
+        for (int b = 0, j = 0; b < n; ++b) {
+            loc[b] = -1;
+            if ((T >> b) & 1) {
+                ps.T.push_back(b);
+                loc[b] = j++;
+            }
+        }
+        auto compress = [&](uint64_t m) {
+            uint32_t r = 0;
+            for (int b = 0; b < n; ++b)
+                if (((m >> b) & 1) && loc[b] >= 0) r |= 1u << loc[b];
+            return r;
+        };
+        ps.t0 = (int)out.terms.size();
+        for (int i : take) {
+            const DevTerm &d = bits[i];
+            OTerm o{};
+            o.floc = compress(d.f);
+            o.sloc = compress(d.s & T);
+            o.sout = d.s & ~T;
+            o.nY = d.nY;
+            o.term = i;
+            o.obs = d.obs;
+            o.coeff = d.coeff;
+            out.terms.push_back(o);
+        }
+        ps.nt = (int)out.terms.size() - ps.t0;
+        out.passes.push_back(ps);
+        remaining.swap(rest);
+    }
+    return true;
+}
+
+template <typename R> struct AdjCfg;
+template <> struct AdjCfg<float> { static constexpr int wb = 0; };
+template <> struct AdjCfg<double> { static constexpr int wb = 1; };
+
+// Tile width for observable and adjoint passes: two vectors are resident.
+template <typename R>
+void adjoint_tile(int n, int &k, int &low, int &M) {
+    if (n >= 25) {
+        M = sizeof(R) == 4 ? 4 : 3;
+        k = sizeof(R) == 4 ? 12 : 11;
+    } else {
+        M = 3;
+        k = std::max(kLaneBits + M, std::min(11, n - 9));
+    }
+    k = std::min(k, n - 1);
+    M = std::min(M, k - kLaneBits);
+    low = std::max(kLaneBits, std::min(7, k - 3));
+}
+
+int adjoint_grid(int64_t ntiles, int nsm) { return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 2 * nsm)); }
+
+// ---------------------------------------------------------------------------
+// observable pass
+// ---------------------------------------------------------------------------
+struct ObsArgs {
+    TileGeom g;
+    const OTerm *terms;
+    int nt;
+    const double *rw;
+    int nobs;
+    int lam_mode;     // 0: no lambda, 1: lambda = contributions, 2: lambda += contributions
+    double *part;     // [term][row][cta] or null
+    int batch;
+    int *errflag;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_tile_obs(const __grid_constant__ CUtensorMap mp,
+                                                  const __grid_constant__ CUtensorMap ml, ObsArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int64_t dim = int64_t(1) << a.g.k;
+    const size_t tbytes = sizeof(cx<R>) * (size_t)dim;
+    cx<R> *bufP = reinterpret_cast<cx<R> *>(smem);
+    cx<R> *bufL = reinterpret_cast<cx<R> *>(smem + tbytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * tbytes);
+    OTerm *st = reinterpret_cast<OTerm *>(smem + 2 * tbytes + 64);
+    double *acc = reinterpret_cast<double *>(st + a.nt);            // [nt]
+    R *accw = reinterpret_cast<R *>(acc + a.nt);                     // [nw][nt]
+    for (int i = tid; i < a.nt; i += blockDim.x) {
+        st[i] = a.terms[i];
+        acc[i] = 0.0;
+    }
+    for (int i = tid; i < nw * a.nt; i += blockDim.x) accw[i] = R(0);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        fence_async_smem();
+    }
+    __syncthreads();
+    const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t1 = min(a.g.ntiles, t0 + per);
+    uint32_t phase = 0;
+    int64_t cur_row = -1;
+    bool failed = false;
+    auto flush = [&](int64_t row) {
+        if (a.part)
+            for (int j = tid; j < a.nt; j += blockDim.x) {
+                a.part[((int64_t)st[j].term * a.batch + row) * gridDim.x + blockIdx.x] = acc[j];
+                acc[j] = 0.0;
+            }
+    };
+    for (int64_t t = t0; t < t1; ++t) {
+        int c[5];
+        uint64_t base;
+        int64_t row;
+        geom_coords(a.g, t, c, base, row);
+        if (row != cur_row) {
+            if (cur_row >= 0) flush(cur_row);
+            cur_row = row;
+        }
+        if (tid == 0) {
+            mbar_expect_tx(&bar[0], (uint32_t)(a.lam_mode == 2 ? 2 * tbytes : tbytes));
+            tma_load5(bufP, &mp, c, &bar[0]);
+            if (a.lam_mode == 2) tma_load5(bufL, &ml, c, &bar[0]);
+        }
+        const bool ok = mbar_wait_bounded(&bar[0], phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (a.lam_mode == 1)
+            for (int64_t l = tid; l < dim; l += blockDim.x) bufL[l] = mk<R>(R(0), R(0));
+        const double *w = a.rw ? a.rw + row * a.nobs : nullptr;
+        for (int j = 0; j < a.nt; ++j) {
+            const OTerm o = st[j];
+            const int bpar = __popcll(base & o.sout) & 1;
+            const R wc = (R)((w ? w[o.obs] : 1.0) * o.coeff);
+            R e = R(0);
+            for (int64_t l = tid; l < dim; l += blockDim.x) {
+                const cx<R> x = bufP[l];
+                const uint32_t src = (uint32_t)l ^ o.floc;
+                const cx<R> y = bufP[src];
+                const int k4 = (o.nY + 2 * ((__popc((uint32_t)l & o.sloc) & 1) ^ bpar)) & 3;
+                const R re = y.x * x.x + y.y * x.y, im = y.x * x.y - y.y * x.x;
+                e += (k4 == 0) ? re : (k4 == 1 ? -im : (k4 == 2 ? -re : im));
+                if (a.lam_mode) {
+                    const int k5 = (o.nY + 2 * ((__popc(src & o.sloc) & 1) ^ bpar)) & 3;
+                    const R pr = (k5 == 0) ? R(1) : (k5 == 2 ? R(-1) : R(0));
+                    const R pi = (k5 == 1) ? R(1) : (k5 == 3 ? R(-1) : R(0));
+                    cx<R> lv = bufL[l];
+                    lv.x += wc * (pr * y.x - pi * y.y);
+                    lv.y += wc * (pr * y.y + pi * y.x);
+                    bufL[l] = lv;
+                }
+            }
+            e = warp_sum_t(e);
+            if (lane == 0) accw[warp * a.nt + j] += e;
+        }
+        __syncthreads();
+        for (int j = tid; j < a.nt; j += blockDim.x) {
+            double sum = 0.0;
+            for (int ww = 0; ww < nw; ++ww) {
+                sum += (double)accw[ww * a.nt + j];
+                accw[ww * a.nt + j] = R(0);
+            }
+            acc[j] += sum;
+        }
+        if (a.lam_mode) {
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tma_store5(&ml, c, bufL);
+                bulk_commit();
+                bulk_wait_read0();
+            }
+        }
+        __syncthreads();
+    }
+    if (!failed && cur_row >= 0) {
+        __syncthreads();
+        flush(cur_row);
+    }
+    if (failed && tid == 0) {
+        atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
+        mbar_wait_bounded(&bar[0], phase);
+    }
+    if (tid == 0) bulk_wait0();
+}
+
+// ---------------------------------------------------------------------------
+// reverse sweep
+// ---------------------------------------------------------------------------
+struct AdjArgs {
+    TileGeom g;
+    const EOp *ops;      // the pass's reverse decodings (op0 .. op0 + nops)
+    const ESeg *segs;    // the pass's reverse segments
+    int op0, nops, nseg;
+    const int32_t *slots;   // global slot of each local slot
+    int nslot;
+    const void *coef;
+    double *part;        // [slot][row][cta]
+    int batch;
+    int *errflag;
+};
+
+template <typename R, int M>
+constexpr int adj_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) <= 64) ? 512 : 256; }
+
+template <typename R, int M>
+__global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __grid_constant__ CUtensorMap mp,
+                                                                       const __grid_constant__ CUtensorMap ml,
+                                                                       AdjArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const size_t tbytes = sizeof(cx<R>) << a.g.k;
+    cx<R> *bufP = reinterpret_cast<cx<R> *>(smem);
+    cx<R> *bufL = reinterpret_cast<cx<R> *>(smem + tbytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * tbytes);
+    EOp *sops = reinterpret_cast<EOp *>(smem + 2 * tbytes + 64);
+    ESeg *ssegs = reinterpret_cast<ESeg *>(sops + a.nops);
+    Mat2<R> *scoef = reinterpret_cast<Mat2<R> *>(ssegs + a.nseg);
+    double *acc = reinterpret_cast<double *>(scoef + a.nops);       // [nslot]
+    R *accw = reinterpret_cast<R *>(acc + a.nslot);                  // [nw][nslot]
+    const Mat2<R> *gcoef = reinterpret_cast<const Mat2<R> *>(a.coef);
+    for (int i = tid; i < a.nops; i += blockDim.x) {
+        sops[i] = a.ops[i];
+        scoef[i] = gcoef[sops[i].coef];
+    }
+    for (int i = tid; i < a.nseg; i += blockDim.x) ssegs[i] = a.segs[i];
+    for (int i = tid; i < a.nslot; i += blockDim.x) acc[i] = 0.0;
+    for (int i = tid; i < nw * a.nslot; i += blockDim.x) accw[i] = R(0);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        fence_async_smem();
+    }
+    __syncthreads();
+    const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t1 = min(a.g.ntiles, t0 + per);
+    uint32_t phase = 0;
+    int64_t cur_row = -1;
+    bool failed = false;
+    auto flush = [&](int64_t row) {
+        for (int j = tid; j < a.nslot; j += blockDim.x) {
+            a.part[((int64_t)a.slots[j] * a.batch + row) * gridDim.x + blockIdx.x] = acc[j];
+            acc[j] = 0.0;
+        }
+    };
+    cx<R> ps[1 << M], ls[1 << M];
+    for (int64_t t = t0; t < t1; ++t) {
+        int c[5];
+        uint64_t base;
+        int64_t row;
+        geom_coords(a.g, t, c, base, row);
+        if (row != cur_row) {
+            if (cur_row >= 0) flush(cur_row);
+            cur_row = row;
+        }
+        if (tid == 0) {
+            mbar_expect_tx(&bar[0], (uint32_t)(2 * tbytes));
+            tma_load5(bufP, &mp, c, &bar[0]);
+            tma_load5(bufL, &ml, c, &bar[0]);
+        }
+        const bool ok = mbar_wait_bounded(&bar[0], phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        for (int si = 0; si < a.nseg; ++si) {
+            const ESeg sg = ssegs[si];
+            const Layout L = make_layout(sg, M, a.g.k, lane, warp);
+            eng_load<R, M>(ps, bufP, L);
+            eng_load<R, M>(ls, bufL, L);
+            for (int cc = 0; cc < sg.nops; ++cc) {
+                const int oi = sg.op0 - a.op0 - cc;
+                const EOp o = sops[oi];
+                const Mat2<R> u = o.rowstep ? gcoef[o.coef + row * o.rowstep] : scoef[oi];
+                const R gv = eng_adjoint<R, M>(ps, ls, o, dagger(u), base, L, lane);
+                if (o.slot >= 0) {
+                    const R gs = warp_sum_t(gv);
+                    if (lane == 0) accw[warp * a.nslot + o.slot] += gs;
+                }
+            }
+            eng_store<R, M>(ps, bufP, L);
+            eng_store<R, M>(ls, bufL, L);
+            __syncthreads();
+        }
+        for (int j = tid; j < a.nslot; j += blockDim.x) {
+            double sum = 0.0;
+            for (int ww = 0; ww < nw; ++ww) {
+                sum += (double)accw[ww * a.nslot + j];
+                accw[ww * a.nslot + j] = R(0);
+            }
+            acc[j] += sum;
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tma_store5(&mp, c, bufP);
+            tma_store5(&ml, c, bufL);
+            bulk_commit();
+            bulk_wait_read0();
+        }
+        __syncthreads();
+    }
+    if (!failed && cur_row >= 0) {
+        __syncthreads();
+        flush(cur_row);
+    }
+    if (failed && tid == 0) {
+        atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
+        mbar_wait_bounded(&bar[0], phase);
+    }
+    if (tid == 0) bulk_wait0();
+}
+
+uint64_t obs_key(const std::vector<DevTerm> &bits, int n, int k, int low, int amp) {
+    uint64_t h = 1469598103934665603ull ^ (uint64_t)(n * 131 + k * 7 + low + amp * 1000);
+    for (const DevTerm &t : bits) {
+        const unsigned char *b = (const unsigned char *)&t;
+        for (size_t i = 0; i < sizeof(DevTerm); ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    }
+    return h;
+}
+
+}  // namespace
+
+size_t tile_adjoint_part_bytes(const Plan &p, int batch, int nsm) {
+    return (size_t)std::max(1, p.nslots) * (size_t)std::max(1, batch) * (size_t)(2 * nsm) * sizeof(double);
+}
+
+size_t tile_expect_part_bytes(int n, int nterms, int batch, int nsm) {
+    (void)n;
+    return (size_t)std::max(1, nterms) * (size_t)std::max(1, batch) * (size_t)(2 * nsm) * sizeof(double);
+}
+
+template <typename R>
+cudaError_t tile_observe(TileCache &tc, int n, const std::vector<DevTerm> &bits, const DevTerm *d_bits,
+                         const int32_t *d_ptr, int nobs, const double *rw, const void *psi, void *lam, int batch,
+                         double *part, double *out, int nsm, cudaStream_t s, int64_t *launches) {
+    constexpr int wb = AdjCfg<R>::wb;
+    if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
+    const size_t sbytes = ((size_t)batch << n) * sizeof(cx<R>);
+    if (bits.empty()) {
+        if (lam) {
+            cudaError_t e = cudaMemsetAsync(lam, 0, sbytes, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (out) return cudaMemsetAsync(out, 0, sizeof(double) * (size_t)batch * nobs, s);
+        return cudaSuccess;
+    }
+    int k, low, M;
+    adjoint_tile<R>(n, k, low, M);
+    low = kLaneBits;   // observable passes want as many free tile bits as possible
+    const uint64_t key = obs_key(bits, n, k, low, (int)sizeof(cx<R>));
+    ObsSchedule *os = nullptr;
+    auto it = tc.obs.find(key);
+    if (it != tc.obs.end()) {
+        os = reinterpret_cast<ObsSchedule *>(it->second);
+    } else {
+        ObsSchedule *ns = new ObsSchedule();
+        if (!build_obs_schedule(bits, n, k, low, wb, *ns)) {
+            delete ns;
+            return cudaErrorNotSupported;
+        }
+        if (cudaMalloc((void **)&ns->d_terms, sizeof(OTerm) * ns->terms.size()) != cudaSuccess) {
+            cudaGetLastError();
+            delete ns;
+            return cudaErrorMemoryAllocation;
+        }
+        cudaMemcpy(ns->d_terms, ns->terms.data(), sizeof(OTerm) * ns->terms.size(), cudaMemcpyHostToDevice);
+        os = ns;
+        tc.obs[key] = ns;   // owned by the cache, released by tile_release_obs
+    }
+    const int64_t ntiles = (int64_t)batch << (n - k);
+    const int grid = adjoint_grid(ntiles, nsm);
+    const int threads = 256;
+    const int nw = threads / 32;
+    if (out) {
+        cudaError_t e = cudaMemsetAsync(part, 0, sizeof(double) * bits.size() * (size_t)batch * grid, s);
+        if (e != cudaSuccess) return e;
+    }
+    for (size_t pi = 0; pi < os->passes.size(); ++pi) {
+        const OPass &ps = os->passes[pi];
+        TileDims d;
+        if (!make_dims(ps.T, n, wb, d)) return cudaErrorInvalidValue;
+        CUtensorMap mp, ml;
+        if (!encode_map(tc.encode_fn, &mp, d, const_cast<void *>(psi), batch, wb)) return cudaErrorInvalidValue;
+        if (lam && !encode_map(tc.encode_fn, &ml, d, lam, batch, wb)) return cudaErrorInvalidValue;
+        if (!lam) ml = mp;
+        ObsArgs a;
+        a.g = make_geom(d, n, k, wb, batch);
+        a.terms = os->d_terms + ps.t0;
+        a.nt = ps.nt;
+        a.rw = rw;
+        a.nobs = nobs;
+        a.lam_mode = lam ? (pi == 0 ? 1 : 2) : 0;
+        a.part = out ? part : nullptr;
+        a.batch = batch;
+        a.errflag = tc.errflag;
+        const size_t smem = 2 * (sizeof(cx<R>) << k) + 64 + ps.nt * sizeof(OTerm) + ps.nt * sizeof(double) +
+                            (size_t)nw * ps.nt * sizeof(R) + 64;
+        cudaError_t e = cudaFuncSetAttribute(k_tile_obs<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        LaunchScope ls(s, "k_tile_obs", launches);
+        k_tile_obs<R><<<grid, threads, smem, s>>>(mp, ml, a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (out) return expect_finalize_nblk(part, d_bits, d_ptr, nobs, batch, grid, out, s, launches);
+    return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
+                         const void *coef, void *psi, void *lam, int batch, double *part, double *gp, double *gd,
+                         int nsm, cudaStream_t s, int64_t *launches) {
+    (void)tuned;
+    constexpr int wb = AdjCfg<R>::wb;
+    if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
+    int k, low, M;
+    adjoint_tile<R>(p.n, k, low, M);
+    TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), true);
+    if (!sc) return cudaErrorNotSupported;
+    const int64_t ntiles = (int64_t)batch << (p.n - k);
+    const int grid = adjoint_grid(ntiles, nsm);
+    const int threads = 1 << (k - M);
+    const int nw = threads / 32;
+    cudaError_t e = cudaMemsetAsync(part, 0, sizeof(double) * (size_t)std::max(1, p.nslots) * batch * grid, s);
+    if (e != cudaSuccess) return e;
+    for (int pi = (int)sc->passes.size() - 1; pi >= 0; --pi) {
+        const TPass &ps = sc->passes[pi];
+        TileDims d;
+        if (!make_dims(ps.T, p.n, wb, d)) return cudaErrorInvalidValue;
+        CUtensorMap mp, ml;
+        if (!encode_map(tc.encode_fn, &mp, d, psi, batch, wb) || !encode_map(tc.encode_fn, &ml, d, lam, batch, wb))
+            return cudaErrorInvalidValue;
+        AdjArgs a;
+        a.g = make_geom(d, p.n, k, wb, batch);
+        a.ops = sc->d_rops + ps.op0;
+        a.segs = sc->d_rsegs + ps.rseg0;
+        a.op0 = ps.op0;
+        a.nops = ps.nops;
+        a.nseg = ps.nrseg;
+        a.slots = sc->d_slots + ps.slot0;
+        a.nslot = ps.nslot;
+        a.coef = coef;
+        a.part = part;
+        a.batch = batch;
+        a.errflag = tc.errflag;
+        const size_t smem = 2 * (sizeof(cx<R>) << k) + 64 + (size_t)ps.nops * sizeof(EOp) +
+                            (size_t)ps.nrseg * sizeof(ESeg) + (size_t)ps.nops * sizeof(Mat2<R>) +
+                            (size_t)ps.nslot * sizeof(double) + (size_t)nw * ps.nslot * sizeof(R) + 64;
+        const void *kfn = M == 3 ? (const void *)k_tile_adj<R, 3>
+                                 : (M == 2 ? (const void *)k_tile_adj<R, 2> : (const void *)k_tile_adj<R, 4>);
+        e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        LaunchScope ls(s, "k_tile_adj", launches);
+        if (M == 3) k_tile_adj<R, 3><<<grid, threads, smem, s>>>(mp, ml, a);
+        else if (M == 2) k_tile_adj<R, 2><<<grid, threads, smem, s>>>(mp, ml, a);
+        else k_tile_adj<R, 4><<<grid, threads, smem, s>>>(mp, ml, a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return grad_reduce(p, part, batch, grid, gp, gd, s, launches);
+}
+
+#define DQ_INST(R)                                                                                               \
+    template cudaError_t tile_observe<R>(TileCache &, int, const std::vector<DevTerm> &, const DevTerm *,        \
+                                         const int32_t *, int, const double *, const void *, void *, int,        \
+                                         double *, double *, int, cudaStream_t, int64_t *);                      \
+    template cudaError_t tile_adjoint<R>(TileCache &, std::unordered_map<uint64_t, TileTune> &, const Plan &,    \
+                                         const void *, void *, void *, int, double *, double *, double *, int,   \
+                                         cudaStream_t, int64_t *);
+DQ_INST(float)
+DQ_INST(double)
+#undef DQ_INST
+
+void tile_release_obs(TileCache &tc) {
+    for (auto &kv : tc.obs) {
+        ObsSchedule *os = reinterpret_cast<ObsSchedule *>(kv.second);
+        cudaFree(os->d_terms);
+        delete os;
+    }
+    tc.obs.clear();
+}
+
+}  // namespace dq

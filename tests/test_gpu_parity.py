@@ -422,3 +422,21 @@ def test_launch_counter_counts_kernels(ctx):
     ctx.state_init(st, n)
     ctx.apply_circuit(dq.Circuit(n, gates), None, st)
     assert ctx.launch_count - c0 == 1 + 1 + n      # init, bind, one sweep per gate
+
+
+@pytest.mark.parametrize("n,batch,want", [(12, 64, {"k_rows"}),
+                                          (18, 2, {"k_tile_fwd", "k_tile_obs", "k_tile_adj"})])
+def test_fused_path_runs_the_fused_kernels(ctx, n, batch, want):
+    """The fused path must not fall back to per-gate sweeps silently."""
+    ctx.set_path(dq.PATH_FUSED)
+    gates = W.encode_layer(n) + W.hea_layers(n, 2)
+    circ = dq.Circuit(n, gates, nparams=4 * n, nfeatures=n)
+    rng = np.random.default_rng(n)
+    params = dev(rng.uniform(0, 6, 4 * n))
+    data = dev(rng.uniform(-3, 3, (batch, n)))
+    ctx.set_tracing(True)
+    ctx.forward_grad(circ, params, dq.Observables([W.obs_tfim_open(n, 0.5)]), batch, torch.complex64, data=data)
+    names = set(ctx.trace())
+    ctx.set_tracing(False)
+    assert want <= names, names
+    assert "k_sweep" not in names and "k_adj" not in names
