@@ -171,6 +171,17 @@ DQ_API dq_status dq_ctx_check(dq_ctx *ctx, void *stream);
  * accounting by callers). */
 DQ_API int64_t dq_ctx_launch_count(const dq_ctx *ctx);
 
+/* CUDA-graph replay.  With replay on, the second dq_forward_grad or
+ * dq_apply_circuit call with the same circuit structure, observables, batch,
+ * dtype, path and buffer pointers (parameters, data, weights, outputs,
+ * workspace) is captured into a CUDA graph on a stream owned by the context,
+ * and that call and later identical ones launch the graph on the caller's
+ * stream instead of issuing the kernels one by one.  Values behind the
+ * pointers (parameters, data) are read when the graph runs, so they may change
+ * between calls; pointers and shapes may not.  Capture is skipped while
+ * tracing is on.  Off by default. */
+DQ_API dq_status dq_ctx_set_graphs(dq_ctx *ctx, int on);
+
 /* Tracing (the library's profiling hook).  With tracing on, every kernel the
  * context launches is bracketed by a CUDA event pair on its stream and the
  * device time is aggregated per kernel name.  Turning tracing on or off

@@ -54,7 +54,7 @@ class dq_observables(ctypes.Structure):
 
 
 EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path", "dq_ctx_set_workspace",
-           "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_tracing",
+           "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_graphs", "dq_ctx_set_tracing",
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
            "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
            "dq_forward_grad_noalloc")
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "dq_batch_workspace_bytes": ([P, I, C, I, ctypes.POINTER(ctypes.c_size_t)], I),
         "dq_ctx_check": ([P, P], I),
         "dq_ctx_launch_count": ([P], ctypes.c_int64),
+        "dq_ctx_set_graphs": ([P, I], I),
         "dq_ctx_set_tracing": ([P, I], I),
         "dq_ctx_trace_count": ([P], I),
         "dq_ctx_trace_get": ([P, I, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64),
@@ -227,6 +228,10 @@ class Context:
 
     def check(self):
         self._check(self.lib.dq_ctx_check(self.h, _stream()), "dq_ctx_check")
+
+    def set_graphs(self, on: bool):
+        """CUDA-graph replay of repeated identical calls (see dq_ctx_set_graphs)."""
+        self._check(self.lib.dq_ctx_set_graphs(self.h, int(bool(on))), "dq_ctx_set_graphs")
 
     def set_tracing(self, on: bool):
         self._check(self.lib.dq_ctx_set_tracing(self.h, int(bool(on))), "dq_ctx_set_tracing")

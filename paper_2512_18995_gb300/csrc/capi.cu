@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -99,6 +100,20 @@ struct dq_ctx {
     Tracer tracer;
     std::vector<std::pair<std::string, std::pair<int64_t, double>>> trace_table;
     std::unordered_map<uint64_t, std::unique_ptr<RowProgram>> rowprogs;
+    // CUDA-graph replay of repeated calls
+    bool graphs_on = false;
+    cudaStream_t cap_stream = nullptr;
+    struct GraphEntry {
+        cudaGraphExec_t exec;
+        int64_t kernels;
+    };
+    std::unordered_map<uint64_t, GraphEntry> graphs;
+    std::unordered_map<uint64_t, int> graph_seen;
+    void clear_graphs() {
+        for (auto &kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+        graphs.clear();
+        graph_seen.clear();
+    }
 };
 
 namespace {
@@ -450,6 +465,69 @@ RowProgram *get_rows(dq_ctx *ctx, const Plan &p, int amp, bool grad, int nobs) {
     return rp;
 }
 
+// Run `body(stream)` through the context's graph cache.  Returns true when the
+// call was served by a graph (captured now or earlier); *st is its status.
+template <typename F>
+bool graph_run(dq_ctx *ctx, uint64_t key, cudaStream_t s, F body, dq_status *st) {
+    if (!ctx->graphs_on || ctx->tracer.on) return false;
+    key ^= (uint64_t)(uintptr_t)ctx->ws * 0x9E3779B97F4A7C15ull;
+    key ^= (uint64_t)ctx->ws_bytes * 0xC2B2AE3D27D4EB4Full;
+    key ^= (uint64_t)ctx->path * 0x165667B19E3779F9ull;
+    auto it = ctx->graphs.find(key);
+    if (it != ctx->graphs.end()) {
+        cudaError_t e = cudaGraphLaunch(it->second.exec, s);
+        if (e != cudaSuccess) {
+            *st = cuda_fail(ctx, e, "cudaGraphLaunch");
+            return true;
+        }
+        ctx->launches += it->second.kernels;
+        *st = DQ_OK;
+        return true;
+    }
+    if (ctx->graph_seen[key]++ < 1) return false;   // first sighting: run normally
+    if (ctx->graphs.size() >= 64) ctx->clear_graphs();
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int64_t before = ctx->launches;
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const dq_status bst = body(ctx->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+    const int64_t kernels = ctx->launches - before;
+    ctx->launches = before;
+    cudaGraphExec_t exec = nullptr;
+    if (bst != DQ_OK || ce != cudaSuccess || !g || cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        ctx->err.clear();
+        return false;   // run normally instead
+    }
+    cudaGraphDestroy(g);
+    ctx->graphs[key] = {exec, kernels};
+    cudaError_t e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) {
+        *st = cuda_fail(ctx, e, "cudaGraphLaunch");
+        return true;
+    }
+    ctx->launches += kernels;
+    *st = DQ_OK;
+    return true;
+}
+
+uint64_t mix_ptrs(uint64_t h, std::initializer_list<const void *> ptrs) {
+    for (const void *p : ptrs) {
+        h ^= (uint64_t)(uintptr_t)p;
+        h *= 1099511628211ull;
+        h ^= h >> 29;
+    }
+    return h;
+}
+
 // ---- templated bodies ------------------------------------------------------
 
 template <typename R>
@@ -754,6 +832,8 @@ dq_status dq_ctx_destroy(dq_ctx *ctx) {
     for (auto &kv : ctx->obs) kv.second->release();
     for (auto &kv : ctx->batches) kv.second->release();
     for (auto &kv : ctx->rowprogs) kv.second->release();
+    ctx->clear_graphs();
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     ctx->tiles.release();
     ctx->tracer.release();
     if (g_tracer == &ctx->tracer) g_tracer = nullptr;
@@ -773,10 +853,19 @@ dq_status dq_ctx_set_path(dq_ctx *ctx, int path) {
     return DQ_OK;
 }
 
+dq_status dq_ctx_set_graphs(dq_ctx *ctx, int on) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    ctx->graphs_on = on != 0;
+    if (!ctx->graphs_on) ctx->clear_graphs();
+    return DQ_OK;
+}
+
 dq_status dq_ctx_set_workspace(dq_ctx *ctx, void *ptr, size_t bytes) {
     dq_status st = check_ctx(ctx);
     if (st != DQ_OK) return st;
     if (ptr && !aligned16(ptr)) return fail(ctx, DQ_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+    ctx->clear_graphs();
     if (ctx->ws_owned && ctx->ws) {
         cudaDeviceSynchronize();
         cudaFree(ctx->ws);
@@ -922,8 +1011,14 @@ dq_status dq_apply_circuit(dq_ctx *ctx, const dq_circuit *circuit, const double 
     if (!state || !aligned16(state)) return fail(ctx, DQ_ERR_INVALID_ARG, "state must be a 16-byte aligned device pointer");
     if ((st = check_angles(ctx, *p, params, data)) != DQ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    return dtype == DQ_C64 ? apply_impl<float>(ctx, *p, params, data, state, batch, s)
-                           : apply_impl<double>(ctx, *p, params, data, state, batch, s);
+    auto body = [&](cudaStream_t ss) {
+        return dtype == DQ_C64 ? apply_impl<float>(ctx, *p, params, data, state, batch, ss)
+                               : apply_impl<double>(ctx, *p, params, data, state, batch, ss);
+    };
+    uint64_t key = mix_ptrs(p->key * 31 + (uint64_t)batch * 7 + (uint64_t)dtype, {params, data, state});
+    dq_status gst = DQ_OK;
+    if (graph_run(ctx, key, s, body, &gst)) return gst;
+    return body(s);
 }
 
 dq_status dq_expect(dq_ctx *ctx, int nqubits, const dq_observables *obs, const void *state, int batch, int dtype,
@@ -994,10 +1089,18 @@ dq_status dq_forward_grad(dq_ctx *ctx, const dq_circuit *circuit, const double *
     if (state_out && !aligned16(state_out)) return fail(ctx, DQ_ERR_INVALID_ARG, "state_out must be 16-byte aligned");
     if ((st = check_angles(ctx, *p, params, data)) != DQ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    return dtype == DQ_C64 ? forward_grad_impl<float>(ctx, *p, o, params, data, row_weights, batch, expect_out,
-                                                      grad_params, grad_data, state_out, s)
-                           : forward_grad_impl<double>(ctx, *p, o, params, data, row_weights, batch, expect_out,
-                                                       grad_params, grad_data, state_out, s);
+    auto body = [&](cudaStream_t ss) {
+        return dtype == DQ_C64 ? forward_grad_impl<float>(ctx, *p, o, params, data, row_weights, batch, expect_out,
+                                                          grad_params, grad_data, state_out, ss)
+                               : forward_grad_impl<double>(ctx, *p, o, params, data, row_weights, batch, expect_out,
+                                                           grad_params, grad_data, state_out, ss);
+    };
+    uint64_t key = mix_ptrs(p->key * 31 + (uint64_t)batch * 7 + (uint64_t)dtype,
+                            {o, params, data, row_weights, expect_out, grad_params, grad_data, state_out});
+    key ^= 0xF0F0F0F0ull;
+    dq_status gst = DQ_OK;
+    if (graph_run(ctx, key, s, body, &gst)) return gst;
+    return body(s);
 }
 
 dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit *circuits, const double *params,
@@ -1124,6 +1227,7 @@ dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch, in
     Plan *p = nullptr;
     if ((st = get_plan(ctx, circuit, 0, &p)) != DQ_OK) return st;
     if (!tile_supported(p->n, amp_bytes(dtype))) return DQ_OK;   // nothing to tune
+    ctx->clear_graphs();
     cudaStream_t s = (cudaStream_t)stream;
     const size_t need = coef_bytes(*p, batch, dtype) + 512 + tile_workspace_bytes(*p, batch, amp_bytes(dtype));
     if ((st = reserve(ctx, need)) != DQ_OK) return st;

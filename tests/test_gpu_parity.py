@@ -440,3 +440,35 @@ def test_fused_path_runs_the_fused_kernels(ctx, n, batch, want):
     ctx.set_tracing(False)
     assert want <= names, names
     assert "k_sweep" not in names and "k_adj" not in names
+
+
+@pytest.mark.parametrize("n,batch,path", [(10, 32, "fused"), (18, 1, "fused"), (9, 3, "plain")])
+def test_graph_replay_reads_current_values(ctx, n, batch, path):
+    """Replayed graphs must see parameter and data values written in place
+    between calls, and give what a fresh (non-graph) call gives."""
+    ctx.set_path(PATHS[path])
+    gates = W.encode_layer(n) + W.hea_layers(n, 2)
+    circ = dq.Circuit(n, gates, nparams=4 * n, nfeatures=n)
+    obs = dq.Observables([W.obs_tfim_open(n, 0.5)])
+    rng = np.random.default_rng(7 + n)
+    params = dev(rng.uniform(0, 6, 4 * n))
+    data = dev(rng.uniform(-3, 3, (batch, n)))
+    e = torch.empty((batch, 1), dtype=torch.float64, device="cuda")
+    gp = torch.empty(4 * n, dtype=torch.float64, device="cuda")
+    gd = torch.empty((batch, n), dtype=torch.float64, device="cuda")
+    ctx.set_graphs(True)
+    try:
+        for call in range(4):
+            params.copy_(dev(rng.uniform(0, 6, 4 * n)))
+            data.copy_(dev(rng.uniform(-3, 3, (batch, n))))
+            ctx.forward_grad(circ, params, obs, batch, torch.complex64, data=data, expect_out=e, grad_params=gp,
+                             grad_data=gd)
+            torch.cuda.synchronize()
+            e_ref, gp_ref, gd_ref = oracle.adjoint(n, gates, [W.obs_tfim_open(n, 0.5)], params.cpu().numpy(),
+                                                   data.cpu().numpy(), batch=batch)
+            assert_rel(e.cpu().numpy(), e_ref, torch.complex64, f"call {call} expectation", floor=obs_scale([W.obs_tfim_open(n, 0.5)]))
+            fl = batch * obs_scale([W.obs_tfim_open(n, 0.5)])
+            assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, f"call {call} grad params", floor=fl)
+            assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, f"call {call} grad data", floor=fl)
+    finally:
+        ctx.set_graphs(False)
