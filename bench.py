@@ -48,6 +48,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return None
+
+
 def gate_pass_bytes(n, gates, amp=8):
     """Gate-equivalent bytes: one full read+write sweep per gate."""
     return len(gates) * 2 * (1 << n) * amp
@@ -288,6 +296,7 @@ def our_arm(args, rank, world, dist):
     if not args.no_extras:
         extras["hbm_sweep"] = hbm_sweep(ctx, device, hbm_peak, peak_kind)
         extras["grads"] = batched_grads(ctx, device)
+        extras["dense_block"] = dense_block(ctx, device, hbm_peak, peak_kind)
         ctx.set_path({"auto": dq.PATH_AUTO, "plain": dq.PATH_PLAIN, "fused": dq.PATH_FUSED}[args.path])
 
     if rank == 0:
@@ -342,6 +351,39 @@ def hbm_sweep(ctx, device, hbm_peak, peak_kind, n=30, reps=3):
     torch.cuda.empty_cache()
     return {"n": n, "kernel": "k_sweep", "launches": cnt, "avg_launch_ms": per_ms, "GB/s": gbs,
             "peak": hbm_peak, "frac": gbs / hbm_peak, "peak_kind": peak_kind, "targets": targets}
+
+
+def dense_block(ctx, device, hbm_peak, peak_kind, n=30, reps=4):
+    """Tensor-core dense 64 x 64 complex block on the six lowest-order qubits
+    of an 8 GiB complex64 state: HBM GB/s and three-pass TF32 FLOP/s."""
+    import torch
+    try:
+        state = torch.empty((1, 1 << n), dtype=torch.complex64, device=device)
+    except RuntimeError:
+        return None
+    ctx.state_init(state, n)
+    U = torch.from_numpy(W.random_unitary(6, 6)).to(device)
+    ctx.apply_dense(n, U, state)
+    torch.cuda.synchronize()
+    ctx.set_tracing(True)
+    for _ in range(reps):
+        ctx.apply_dense(n, U, state)
+    tr = ctx.trace()
+    ctx.set_tracing(False)
+    cnt, tot = tr["k_dense"]
+    per_ms = tot / cnt
+    rows = 1 << (n - 6)
+    gbs = 2 * (1 << n) * 8 / (per_ms / 1e3) / 1e9
+    tflops = 3 * 2 * 128 * 128 * rows / (per_ms / 1e3) / 1e12
+    # TF32 dense peak: the measured bf16 GEMM peak times the nominal TF32/BF16 ratio (1.1 / 2.25)
+    bf16 = bf16_peak()
+    tf32_peak = bf16 * (1.1 / 2.25) if bf16 else 1900.0 * (1.1 / 2.25)
+    del state
+    torch.cuda.empty_cache()
+    return {"n": n, "kernel": "k_dense", "launches": cnt, "avg_launch_ms": per_ms, "GB/s": gbs,
+            "hbm_frac": gbs / hbm_peak, "peak_kind": peak_kind, "tflops_tf32x3": tflops,
+            "tf32_peak": tf32_peak, "tensor_frac": tflops / tf32_peak,
+            "tf32_peak_kind": "measured bf16 x nominal tf32/bf16" if bf16 else "fallback bf16 x nominal tf32/bf16"}
 
 
 def batched_grads(ctx, device, steps=5):
@@ -411,6 +453,13 @@ def profile_case(args):
         circ = dq.Circuit(n, [W.Gate("ry", (q,), angle=0.3) for q in (0, 7, 14, 21, 27)])
         for _ in range(iters):
             ctx.apply_circuit(circ, None, st)
+    elif args.profile_case == "dense":       # tensor-core dense block on a 512 MiB state
+        n = 26
+        st = torch.empty((1, 1 << n), dtype=torch.complex64, device=dev)
+        ctx.state_init(st, n)
+        U = torch.from_numpy(W.random_unitary(6, 6)).to(dev)
+        for _ in range(iters):
+            ctx.apply_dense(n, U, st)
     elif args.profile_case == "c5":          # QFT + layers, forward + adjoint, 26 qubits
         wl = W.config_c5(26)
         circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
@@ -435,7 +484,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="issue kernels one by one (no CUDA-graph replay)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--profile-case", choices=["tile", "wsv", "sweep", "c5"], default=None,
+    ap.add_argument("--profile-case", choices=["tile", "wsv", "sweep", "c5", "dense"], default=None,
                     help="run one kernel family's workload for profiling and exit")
     args = ap.parse_args()
     if args.profile_case:

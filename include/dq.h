@@ -301,6 +301,27 @@ DQ_API dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const double
                                          double *grad_params, double *grad_data, void *stream,
                                          char *err, size_t err_len);
 
+/* Dense fused block on the tensor cores.  Applies a dense 2^nw x 2^nw
+ * unitary U to the nw lowest-order qubits (wires nqubits-nw .. nqubits-1)
+ * of every row of a complex64 state, in place: amplitude index h*2^nw + j of
+ * a row becomes sum_j U[i][j] psi[h*2^nw + j] at h*2^nw + i.  This is the
+ * pure-state evolution of Sec. "Quantum Computing with Qubits" (Background)
+ * with a run of consecutive gates multiplied into one matrix; the paper
+ * itself applies gates one at a time and has no such fusion.
+ *
+ * unitary: device, complex128 row-major (interleaved re, im), 2^nw x 2^nw;
+ * index bit b of i and j is wire nqubits-1-b.  Unitarity is not checked.
+ * 1 <= nw <= 6 and nqubits >= 6; the block is applied as I (x) U on the six
+ * lowest-order qubits.  The products run on the tensor cores as three TF32
+ * passes (hi/lo splits of U and of the state) accumulated in FP32, which
+ * keeps FP32-level accuracy.  state: device, 16-byte aligned, batch rows of
+ * 2^nqubits complex64; batch * 2^(nqubits-6) < 2^31.  dtype must be DQ_C64
+ * (DQ_C128 returns DQ_ERR_UNSUPPORTED: the FP64 tensor rate of this GPU gives
+ * no fast path).  Asynchronous on `stream`; the workspace holds a 128 KiB
+ * operand image until the kernel has read it. */
+DQ_API dq_status dq_apply_dense(dq_ctx *ctx, int nqubits, int nw, const double *unitary, void *state,
+                                int batch, int dtype, void *stream);
+
 /* Time the fused-path variants (fusion width k and tile schedule) for this
  * circuit shape on `state` (device, batch rows, contents destroyed) and
  * cache the fastest for later calls with the same circuit structure.

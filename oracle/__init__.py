@@ -64,6 +64,7 @@ def _bind(path):
     lib.oracle_apply.argtypes = gate_args + [I, I, P]
     lib.oracle_expect.argtypes = [I, P, P, P, P, I, I, P, P]
     lib.oracle_adjoint.argtypes = gate_args + [I, P, P, P, P, I, P, P, P, P]
+    lib.oracle_apply_dense.argtypes = [I, I, P, I, P]
     return lib
 
 
@@ -175,6 +176,15 @@ def adjoint(n, gates, observables, params=None, data=None, batch=1, params_per_r
     lib.oracle_adjoint(*args, int(batch), _ptr(o.coeff), _ptr(o.x), _ptr(o.z), _ptr(o.offsets),
                        o.nobs, _ptr(rw), _ptr(exp), _ptr(gp), _ptr(gd))
     return exp, gp, gd
+
+
+def apply_dense(n, nw, unitary, states, lib=None):
+    """(I (x) U) on the nw lowest-order wires of every row; returns a copy."""
+    lib = lib or _load()
+    u = np.ascontiguousarray(unitary, dtype=np.complex128).reshape(1 << nw, 1 << nw)
+    st = np.array(states, dtype=np.complex128, copy=True).reshape(-1, 1 << n)
+    lib.oracle_apply_dense(int(n), int(nw), _ptr(u), st.shape[0], _ptr(st))
+    return st
 
 
 def load_library(path: str):

@@ -22,6 +22,10 @@
  *     with rx(-h dt), rzz(-2 J dt)): rotations are R_P(t) = exp(-i t P / 2).
  *   - Sec. "Distributed Quantum Fourier Transform": controlled phase
  *     CP(phi) = diag(1, 1, 1, e^{i phi}), Hadamard, SWAP.
+ *   - Dense blocks (oracle_apply_dense): the same evolution with a group of
+ *     consecutive gates written as one matrix on the lowest-order wires; the
+ *     paper applies gates one at a time, so this is the plain definition of
+ *     a matrix acting on a subset of wires.
  *
  * Readings where the paper is silent (also listed in the design notes):
  *   - wire 0 is the most significant bit of the amplitude index:
@@ -404,4 +408,36 @@ void oracle_adjoint(int n, int ngates, const int *kind, const int *w0, const int
     }
     (void)gp_rows;
     free(gp_row);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense matrix on the lowest-order wires.                                   */
+/* ------------------------------------------------------------------------ */
+
+/* psi <- (I (x) U) psi for every row, U a 2^nw x 2^nw matrix (row-major,
+ * interleaved re/im) on the nw lowest-order wires n-nw .. n-1.  With wire 0 as
+ * the most significant index bit, those wires are the low nw bits, so each
+ * row splits into 2^(n-nw) contiguous groups of 2^nw amplitudes and U
+ * multiplies each group as a vector: y_i = sum_j U_ij x_j. */
+void oracle_apply_dense(int n, int nw, const double *u, int batch, double *states)
+{
+    const int64_t bw = (int64_t)1 << nw;
+    const int64_t groups = (int64_t)batch << (n - nw);
+    const cplx *U = (const cplx *)u;
+    cplx *st = (cplx *)states;
+#pragma omp parallel
+    {
+        cplx *y = (cplx *)malloc((size_t)bw * sizeof(cplx));
+#pragma omp for schedule(static)
+        for (int64_t v = 0; v < groups; ++v) {
+            cplx *x = st + v * bw;
+            for (int64_t i = 0; i < bw; ++i) {
+                cplx acc = 0;
+                for (int64_t j = 0; j < bw; ++j) acc += U[i * bw + j] * x[j];
+                y[i] = acc;
+            }
+            memcpy(x, y, (size_t)bw * sizeof(cplx));
+        }
+        free(y);
+    }
 }

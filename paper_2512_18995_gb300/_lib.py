@@ -57,7 +57,7 @@ EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path"
            "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_graphs", "dq_ctx_set_tracing",
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
            "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
-           "dq_forward_grad_noalloc")
+           "dq_forward_grad_noalloc", "dq_apply_dense")
 
 _lib = None
 
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH):
         "dq_batch_forward_grad": ([P, I, C, P, ctypes.POINTER(ctypes.c_int64), O, I, P, P, P], I),
         "dq_plan_autotune": ([P, C, I, I, P, P], I),
         "dq_forward_grad_noalloc": ([C, P, I, P, O, P, I, I, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t], I),
+        "dq_apply_dense": ([P, I, I, P, P, I, I, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -281,6 +282,19 @@ class Context:
         self.ensure_workspace(circuit, None, batch, dt)
         self._check(self.lib.dq_apply_circuit(self.h, circuit.ref(), _ptr(params), int(params_per_row), _ptr(data),
                                               _ptr(state), int(batch), dt, _stream()), "dq_apply_circuit")
+
+    def apply_dense(self, nqubits: int, unitary: torch.Tensor, state: torch.Tensor):
+        """Dense 2^nw x 2^nw unitary (complex128, on the device) on the nw
+        lowest-order qubits of every row of a complex64 state, in place, on
+        the tensor cores."""
+        nw = int(unitary.shape[-1]).bit_length() - 1
+        if unitary.dtype != torch.complex128 or tuple(unitary.shape) != (1 << nw, 1 << nw):
+            raise ValueError("unitary must be a complex128 tensor of shape (2^nw, 2^nw)")
+        u = unitary.contiguous()
+        batch = state.numel() >> nqubits
+        self.ensure_workspace(None, None, batch, dtype_code(state.dtype), need_bytes=1 << 20)
+        self._check(self.lib.dq_apply_dense(self.h, int(nqubits), nw, _ptr(u), _ptr(state), int(batch),
+                                            dtype_code(state.dtype), _stream()), "dq_apply_dense")
 
     def expect(self, nqubits: int, obs: Observables, state: torch.Tensor,
                out: Optional[torch.Tensor] = None) -> torch.Tensor:

@@ -15,6 +15,7 @@
 
 #include "dq.h"
 #include "dq_common.cuh"
+#include "dq_dense.h"
 #include "dq_plan.h"
 #include "dq_rows.h"
 #include "dq_tile.h"
@@ -1215,6 +1216,29 @@ dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit *circui
                                   bd->nmax, bd->maxparams, expect_out, grad_params, scratch, counter, ctx->nsm,
                                   ctx->smem_optin, s, &ctx->launches),
                 "batch");
+    return DQ_OK;
+}
+
+dq_status dq_apply_dense(dq_ctx *ctx, int nqubits, int nw, const double *unitary, void *state, int batch, int dtype,
+                         void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if ((st = check_n(ctx, nqubits)) != DQ_OK) return st;
+    if (dtype != DQ_C64) return fail(ctx, DQ_ERR_UNSUPPORTED, "dense blocks run on complex64 states only");
+    if (nw < 1 || nw > kDenseBits) return fail(ctx, DQ_ERR_INVALID_ARG, "nw must be in [1, %d]", kDenseBits);
+    if (nqubits < kDenseBits)
+        return fail(ctx, DQ_ERR_UNSUPPORTED, "dense blocks need at least %d qubits", kDenseBits);
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    if (batch == 0) return DQ_OK;
+    if (!unitary || !aligned16(unitary)) return fail(ctx, DQ_ERR_INVALID_ARG, "unitary must be a 16-byte aligned device pointer");
+    if (!state || !aligned16(state)) return fail(ctx, DQ_ERR_INVALID_ARG, "state must be a 16-byte aligned device pointer");
+    if (!dense_supported(nqubits, batch))
+        return fail(ctx, DQ_ERR_UNSUPPORTED, "batch * 2^(nqubits-%d) must stay below 2^31", kDenseBits);
+    if ((st = reserve(ctx, dense_image_bytes())) != DQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    DQ_CUDA(dense_prepare(unitary, nw, ctx->ws, s, &ctx->launches), "dense_prepare");
+    DQ_CUDA(dense_apply(ctx->tiles, ctx->ws, state, nqubits, batch, ctx->nsm, s, &ctx->launches), "dense_apply");
     return DQ_OK;
 }
 

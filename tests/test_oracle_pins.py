@@ -121,6 +121,13 @@ def pin_failures(oracle, lib=None):
         fm = oracle.expect(n, oracle.run(n, gates, params - e, lib=lib), obs, lib=lib)[0, 0]
         fd[p] = (fp - fm) / (2 * h)
     check("adjoint-fd", np.allclose(gp, fd, atol=1e-8))
+    # dense block on the low wires = I (x) U as a Kronecker product
+    n, nw = 5, 3
+    U = W.random_unitary(nw, 11)
+    st = rng.standard_normal((2, 1 << n)) + 1j * rng.standard_normal((2, 1 << n))
+    got = oracle.apply_dense(n, nw, U, st, lib=lib)
+    ref = st @ np.kron(np.eye(1 << (n - nw)), U).T
+    check("dense-kron", np.allclose(got, ref, atol=1e-12))
     return bad
 
 
@@ -317,7 +324,53 @@ def test_distributed_example_four_qubits(oracle_mod):
 # ---------------------------------------------------------------------------
 # planted mistakes: each mutant of the oracle must fail at least one pin
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,nw", [(3, 1), (5, 3), (7, 6), (6, 6)])
+def test_dense_block_is_kronecker_product(oracle_mod, n, nw):
+    """(I (x) U) psi with the block on the low wires, against numpy.kron."""
+    rng = np.random.default_rng(n * 10 + nw)
+    U = W.random_unitary(nw, 100 + nw)
+    assert np.allclose(U.conj().T @ U, np.eye(1 << nw), atol=1e-12)
+    st = rng.standard_normal((3, 1 << n)) + 1j * rng.standard_normal((3, 1 << n))
+    got = oracle_mod.apply_dense(n, nw, U, st)
+    ref = st @ np.kron(np.eye(1 << (n - nw)), U).T
+    np.testing.assert_allclose(got, ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("nw", [1, 2, 4])
+def test_dense_dft_block_on_basis_states(oracle_mod, nw):
+    """The DFT matrix on the low wires maps |h, x> to (1/sqrt N) sum_y w^{xy} |h, y>
+    with w = e^{2 pi i / N} (closed form), leaving the high wires h alone."""
+    n = nw + 2
+    N = 1 << nw
+    F = np.exp(2j * np.pi * np.outer(np.arange(N), np.arange(N)) / N) / math.sqrt(N)
+    for h in range(4):
+        for x in range(N):
+            st = np.zeros(1 << n, complex)
+            st[h * N + x] = 1.0
+            got = oracle_mod.apply_dense(n, nw, F, st)[0]
+            ref = np.zeros(1 << n, complex)
+            ref[h * N:(h + 1) * N] = np.exp(2j * np.pi * x * np.arange(N) / N) / math.sqrt(N)
+            np.testing.assert_allclose(got, ref, atol=1e-13)
+
+
+def test_dense_block_of_gates_equals_gate_sequence(oracle_mod):
+    """A group of gates on the low wires, multiplied into one matrix by dense
+    Kronecker products, acts like the gates applied one by one."""
+    n, nw = 6, 3
+    rng = np.random.default_rng(3)
+    low = list(range(n - nw, n))
+    gates = [Gate("h", (low[0],)), Gate("ry", (low[1],), angle=0.4), Gate("cnot", (low[1], low[2])),
+             Gate("cp", (low[2], low[0]), angle=1.1), Gate("rx", (low[2],), angle=-0.8),
+             Gate("crz", (low[0], low[1]), angle=0.3), Gate("swap", (low[0], low[2]))]
+    U = D.circuit_operator(nw, [Gate(g.kind, tuple(w - (n - nw) for w in g.wires), angle=g.angle)
+                                for g in gates], np.zeros(1))
+    st = rng.standard_normal((2, 1 << n)) + 1j * rng.standard_normal((2, 1 << n))
+    np.testing.assert_allclose(oracle_mod.apply_dense(n, nw, U, st), oracle_mod.apply(n, gates, st), atol=1e-12)
+
+
 MUTANTS = {
+    "dense-transposed": ("for (int64_t j = 0; j < bw; ++j) acc += U[i * bw + j] * x[j];",
+                         "for (int64_t j = 0; j < bw; ++j) acc += U[j * bw + i] * x[j];"),
     "rx-sign": ("case O_CRX:  m[0] = c;  m[1] = -I * s; m[2] = -I * s;",
                 "case O_CRX:  m[0] = c;  m[1] = I * s; m[2] = I * s;"),
     "ry-transposed": ("case O_CRY:  m[0] = c;  m[1] = -s;  m[2] = s;",

@@ -96,6 +96,15 @@ def uniform_array(seed: int, count: int, lo: float, hi: float) -> np.ndarray:
 # --------------------------------------------------------------------------
 # circuit builders (gate lists only)
 # --------------------------------------------------------------------------
+def random_unitary(nw: int, seed: int) -> np.ndarray:
+    """A 2^nw x 2^nw unitary: Q of the QR factorisation of a matrix whose
+    entries have real and imaginary parts uniform in [-1, 1)."""
+    d = 1 << nw
+    v = uniform_array(seed, 2 * d * d, -1.0, 1.0)
+    q, _ = np.linalg.qr((v[0::2] + 1j * v[1::2]).reshape(d, d))
+    return np.ascontiguousarray(q)
+
+
 def hea_layers(n: int, layers: int, first_param: int = 0,
                ring: Optional[Sequence[Sequence[int]]] = None) -> List[Gate]:
     """Hardware-efficient ansatz: per layer RY on every wire, RZ on every wire,
