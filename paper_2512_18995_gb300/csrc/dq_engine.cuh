@@ -23,18 +23,21 @@ namespace dq {
 
 constexpr int kLaneBits = 5;
 
-// Handlers: pair updates on register position P (REAL, GEN, ANTI), diagonal
-// factors on register position P, lane-bit updates, and a diagonal factor
-// that is uniform for the thread.
+// Handlers: pair updates on register position P (uncontrolled REAL and DIAG
+// take straight-line paths; controlled ones and GEN/ANTI take branch-free
+// selects on the control mask), lane-bit updates, and a diagonal factor that
+// is uniform for the thread.
 enum Handler : int16_t {
-    H_REAL = 0,     // + P
+    H_REAL = 0,     // + P, uncontrolled
     H_GEN = 5,      // + P
     H_ANTI = 10,    // + P
-    H_DIAG = 15,    // + P
-    H_LREAL = 20,
-    H_LGEN = 21,
-    H_LANTI = 22,
-    H_DUNI = 23,
+    H_DIAG = 15,    // + P, uncontrolled
+    H_CREAL = 20,   // + P, controlled
+    H_CDIAG = 25,   // + P, controlled
+    H_LREAL = 30,
+    H_LGEN = 31,
+    H_LANTI = 32,
+    H_DUNI = 33,
 };
 
 // One operation decoded for one register layout.  32 bytes.
@@ -97,10 +100,11 @@ inline EOp decode_op(const GOp &g, const int8_t *B, int M) {
             o.carg = (int8_t)g.cg;
         }
     }
+    const bool ctrl = g.cg >= 0;
     if (g.cls == CLS_DIAG) {
         const int pt = g.tl >= 0 ? pos(g.tl) : -1;
         if (pt >= 0) {
-            o.h = (int16_t)(H_DIAG + pt);
+            o.h = (int16_t)((ctrl ? H_CDIAG : H_DIAG) + pt);
         } else {
             o.h = H_DUNI;
             if (g.tl >= 0) {
@@ -119,7 +123,8 @@ inline EOp decode_op(const GOp &g, const int8_t *B, int M) {
         return o;
     }
     const int p = pos(g.tl);   // the planners guarantee p >= 0
-    o.h = (int16_t)((g.cls == CLS_ANTI ? H_ANTI : (g.cls == CLS_REAL ? H_REAL : H_GEN)) + (p < 0 ? 0 : p));
+    const int base = g.cls == CLS_ANTI ? H_ANTI : (g.cls == CLS_REAL ? (ctrl ? H_CREAL : H_REAL) : H_GEN);
+    o.h = (int16_t)(base + (p < 0 ? 0 : p));
     return o;
 }
 
@@ -185,23 +190,45 @@ __device__ __forceinline__ uint32_t op_cmask(const EOp &o, const Layout &L, uint
 // ---------------------------------------------------------------------------
 // forward application
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T sel(bool c, T x, T y) { return c ? x : y; }
+
+// Uncontrolled pair update on register position P.
 template <typename R, int M, int P, int CLS>
-__device__ __forceinline__ void pairs_at(cx<R> (&a)[1 << M], const Mat2<R> &u, uint32_t cm) {
-    const bool all = cm == ~0u;
+__device__ __forceinline__ void pairs_at(cx<R> (&a)[1 << M], const Mat2<R> &u) {
 #pragma unroll
     for (int e0 = 0; e0 < (1 << M); ++e0) {
         if (e0 & (1 << P)) continue;
-        if (!all && !((cm >> e0) & 1)) continue;
         apply2<R, CLS>(u, a[e0], a[e0 | (1 << P)]);
     }
 }
 
-template <typename R, int M, int P>
-__device__ __forceinline__ void diag_at(cx<R> (&a)[1 << M], const Mat2<R> &u, uint32_t cm) {
-    const bool all = cm == ~0u;
+// Pair update on the elements whose control bit (mask cm) is set: both
+// results are formed and selected, so lanes never diverge.
+template <typename R, int M, int P, int CLS>
+__device__ __forceinline__ void pairs_sel(cx<R> (&a)[1 << M], const Mat2<R> &u, uint32_t cm) {
 #pragma unroll
-    for (int e = 0; e < (1 << M); ++e)
-        if (all || ((cm >> e) & 1)) a[e] = cmul(((e >> P) & 1) ? u.m[3] : u.m[0], a[e]);
+    for (int e0 = 0; e0 < (1 << M); ++e0) {
+        if (e0 & (1 << P)) continue;
+        const int e1 = e0 | (1 << P);
+        const bool c = (cm >> e0) & 1;
+        cx<R> b0 = a[e0], b1 = a[e1];
+        apply2<R, CLS>(u, b0, b1);
+        a[e0] = sel(c, b0, a[e0]);
+        a[e1] = sel(c, b1, a[e1]);
+    }
+}
+
+template <typename R, int M, int P>
+__device__ __forceinline__ void diag_at(cx<R> (&a)[1 << M], const Mat2<R> &u) {
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) a[e] = cmul(((e >> P) & 1) ? u.m[3] : u.m[0], a[e]);
+}
+
+template <typename R, int M, int P>
+__device__ __forceinline__ void diag_sel(cx<R> (&a)[1 << M], const Mat2<R> &u, uint32_t cm) {
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) a[e] = sel((cm >> e) & 1, cmul(((e >> P) & 1) ? u.m[3] : u.m[0], a[e]), a[e]);
 }
 
 template <typename R, int M, int CLS>
@@ -210,14 +237,14 @@ __device__ __forceinline__ void lane_at(cx<R> (&a)[1 << M], const Mat2<R> &u, in
     const cx<R> cs = hi ? u.m[3] : u.m[0];
     const cx<R> cp = hi ? u.m[2] : u.m[1];
     const int m = 1 << j;
-    const bool all = cm == ~0u;
 #pragma unroll
     for (int e = 0; e < (1 << M); ++e) {
         const cx<R> p = shfl_xor_cx(a[e], m);
-        if (!all && !((cm >> e) & 1)) continue;
-        if (CLS == CLS_ANTI) a[e] = p;
-        else if (CLS == CLS_REAL) a[e] = mk<R>(cs.x * a[e].x + cp.x * p.x, cs.x * a[e].y + cp.x * p.y);
-        else a[e] = cadd(cmul(cs, a[e]), cmul(cp, p));
+        cx<R> r;
+        if (CLS == CLS_ANTI) r = p;
+        else if (CLS == CLS_REAL) r = mk<R>(cs.x * a[e].x + cp.x * p.x, cs.x * a[e].y + cp.x * p.y);
+        else r = cadd(cmul(cs, a[e]), cmul(cp, p));
+        a[e] = sel((cm >> e) & 1, r, a[e]);
     }
 }
 
@@ -226,37 +253,46 @@ __device__ __forceinline__ void diag_uni(cx<R> (&a)[1 << M], const Mat2<R> &u, c
                                          uint64_t base, uint32_t cm) {
     const int t = o.tmode == 1 ? (int)((L.tb >> o.targ) & 1) : (int)((base >> o.targ) & 1);
     const cx<R> f = t ? u.m[3] : u.m[0];
-    const bool all = cm == ~0u;
 #pragma unroll
-    for (int e = 0; e < (1 << M); ++e)
-        if (all || ((cm >> e) & 1)) a[e] = cmul(f, a[e]);
+    for (int e = 0; e < (1 << M); ++e) a[e] = sel((cm >> e) & 1, cmul(f, a[e]), a[e]);
 }
 
 #define DQ_ENG_P(MACRO) MACRO(0) MACRO(1) MACRO(2) MACRO(3) MACRO(4)
 
 // Apply one op (u already daggered by the caller when un-applying).
+// Uncontrolled REAL and DIAG ops run straight-line code; the others take the
+// control mask as selects, so every lane runs the same instructions and the
+// lane handlers' full-mask shuffles stay convergent, and a warp whose
+// controls are all off skips the op (a warp-uniform vote).
 template <typename R, int M>
 __device__ __forceinline__ void eng_apply(cx<R> (&a)[1 << M], const EOp &o, const Mat2<R> &u, uint64_t base,
                                           const Layout &L, int lane) {
+    if (o.h < H_GEN) {
+        switch (o.h) {
+#define DQ_CASE(P) \
+        case H_REAL + P: if (P < M) pairs_at<R, M, (P < M ? P : 0), CLS_REAL>(a, u); break;
+        DQ_ENG_P(DQ_CASE)
+#undef DQ_CASE
+        }
+        return;
+    }
+    if (o.h >= H_DIAG && o.h < H_CREAL) {
+        switch (o.h) {
+#define DQ_CASE(P) \
+        case H_DIAG + P: if (P < M) diag_at<R, M, (P < M ? P : 0)>(a, u); break;
+        DQ_ENG_P(DQ_CASE)
+#undef DQ_CASE
+        }
+        return;
+    }
     const uint32_t cm = op_cmask(o, L, base);
-    // A control on a thread bit can differ between lanes: leave only when the
-    // whole warp has nothing to do, so lane operations keep every lane in
-    // their full-mask shuffles.
     if (__all_sync(0xffffffffu, cm == 0)) return;
     switch (o.h) {
-#define DQ_CASE(P)                                                                         \
-    case H_REAL + P:                                                                       \
-        if (P < M) pairs_at<R, M, (P < M ? P : 0), CLS_REAL>(a, u, cm);                    \
-        break;                                                                             \
-    case H_GEN + P:                                                                        \
-        if (P < M) pairs_at<R, M, (P < M ? P : 0), CLS_GENERAL>(a, u, cm);                 \
-        break;                                                                             \
-    case H_ANTI + P:                                                                       \
-        if (P < M) pairs_at<R, M, (P < M ? P : 0), CLS_ANTI>(a, u, cm);                    \
-        break;                                                                             \
-    case H_DIAG + P:                                                                       \
-        if (P < M) diag_at<R, M, (P < M ? P : 0)>(a, u, cm);                               \
-        break;
+#define DQ_CASE(P)                                                                                  \
+    case H_GEN + P: if (P < M) pairs_sel<R, M, (P < M ? P : 0), CLS_GENERAL>(a, u, cm); break;      \
+    case H_ANTI + P: if (P < M) pairs_sel<R, M, (P < M ? P : 0), CLS_ANTI>(a, u, cm); break;        \
+    case H_CREAL + P: if (P < M) pairs_sel<R, M, (P < M ? P : 0), CLS_REAL>(a, u, cm); break;       \
+    case H_CDIAG + P: if (P < M) diag_sel<R, M, (P < M ? P : 0)>(a, u, cm); break;
         DQ_ENG_P(DQ_CASE)
 #undef DQ_CASE
     case H_LREAL: lane_at<R, M, CLS_REAL>(a, u, o.targ, lane, cm); break;
@@ -270,19 +306,48 @@ __device__ __forceinline__ void eng_apply(cx<R> (&a)[1 << M], const EOp &o, cons
 // adjoint step: gradient partial 2 Im <lam|G|psi> (after the gate), then
 // un-apply U^dagger on both register sets.  Returns this thread's partial.
 // ---------------------------------------------------------------------------
-template <typename R, int M, int P, int CLS>
-__device__ __forceinline__ R adj_pairs_at(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud, uint32_t cm,
-                                          int kind, bool grad) {
+// 2 Im <l|G|p> on one amplitude pair for the parametric kinds of a class:
+// REAL: RY/CRY (G = Y/2), GENERAL: RX/CRX (G = X/2).
+template <typename R, int CLS>
+__device__ __forceinline__ R grad_cls(cx<R> l0, cx<R> l1, cx<R> p0, cx<R> p1) {
+    if (CLS == CLS_REAL) return -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
+    if (CLS == CLS_GENERAL) return (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
+    return R(0);
+}
+
+// Uncontrolled pair update with optional gradient (GRAD compile-time).
+template <typename R, int M, int P, int CLS, bool GRAD>
+__device__ __forceinline__ R adj_pairs_at(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud) {
     R g = R(0);
-    const bool all = cm == ~0u;
 #pragma unroll
     for (int e0 = 0; e0 < (1 << M); ++e0) {
         if (e0 & (1 << P)) continue;
-        if (!all && !((cm >> e0) & 1)) continue;
         const int e1 = e0 | (1 << P);
-        if (grad) g += grad_pair<R>(kind, ls[e0], ls[e1], ps[e0], ps[e1]);
+        if (GRAD) g += grad_cls<R, CLS>(ls[e0], ls[e1], ps[e0], ps[e1]);
         apply2<R, CLS>(ud, ps[e0], ps[e1]);
         apply2<R, CLS>(ud, ls[e0], ls[e1]);
+    }
+    return g;
+}
+
+// Controlled (or GEN/ANTI) pair update: selects on the control mask.
+template <typename R, int M, int P, int CLS, bool GRAD>
+__device__ __forceinline__ R adj_pairs_sel(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud,
+                                           uint32_t cm) {
+    R g = R(0);
+#pragma unroll
+    for (int e0 = 0; e0 < (1 << M); ++e0) {
+        if (e0 & (1 << P)) continue;
+        const int e1 = e0 | (1 << P);
+        const bool c = (cm >> e0) & 1;
+        if (GRAD) g += c ? grad_cls<R, CLS>(ls[e0], ls[e1], ps[e0], ps[e1]) : R(0);
+        cx<R> p0 = ps[e0], p1 = ps[e1], l0 = ls[e0], l1 = ls[e1];
+        apply2<R, CLS>(ud, p0, p1);
+        apply2<R, CLS>(ud, l0, l1);
+        ps[e0] = sel(c, p0, ps[e0]);
+        ps[e1] = sel(c, p1, ps[e1]);
+        ls[e0] = sel(c, l0, ls[e0]);
+        ls[e1] = sel(c, l1, ls[e1]);
     }
     return g;
 }
@@ -294,17 +359,14 @@ __device__ __forceinline__ void diag_weights(int kind, R &w0, R &w1) {
     w1 = (kind == DQ_CP) ? R(-2) : R(-1);
 }
 
-template <typename R, int M, int P>
-__device__ __forceinline__ R adj_diag_at(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud, uint32_t cm,
-                                         int kind, bool grad) {
+template <typename R, int M, int P, bool GRAD>
+__device__ __forceinline__ R adj_diag_at(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud, int kind) {
     R g = R(0), w0, w1;
     diag_weights<R>(kind, w0, w1);
-    const bool all = cm == ~0u;
 #pragma unroll
     for (int e = 0; e < (1 << M); ++e) {
-        if (!all && !((cm >> e) & 1)) continue;
         const bool t = (e >> P) & 1;
-        if (grad) g += (t ? w1 : w0) * (ls[e].x * ps[e].y - ls[e].y * ps[e].x);
+        if (GRAD) g += (t ? w1 : w0) * (ls[e].x * ps[e].y - ls[e].y * ps[e].x);
         const cx<R> f = t ? ud.m[3] : ud.m[0];
         ps[e] = cmul(f, ps[e]);
         ls[e] = cmul(f, ls[e]);
@@ -312,77 +374,120 @@ __device__ __forceinline__ R adj_diag_at(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M
     return g;
 }
 
-template <typename R, int M>
+template <typename R, int M, int P, bool GRAD>
+__device__ __forceinline__ R adj_diag_sel(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud, int kind,
+                                          uint32_t cm) {
+    R g = R(0), w0, w1;
+    diag_weights<R>(kind, w0, w1);
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) {
+        const bool c = (cm >> e) & 1;
+        const bool t = (e >> P) & 1;
+        if (GRAD) g += c ? (t ? w1 : w0) * (ls[e].x * ps[e].y - ls[e].y * ps[e].x) : R(0);
+        const cx<R> f = t ? ud.m[3] : ud.m[0];
+        ps[e] = sel(c, cmul(f, ps[e]), ps[e]);
+        ls[e] = sel(c, cmul(f, ls[e]), ls[e]);
+    }
+    return g;
+}
+
+template <typename R, int M, bool GRAD>
 __device__ __forceinline__ R adj_diag_uni(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud, const EOp &o,
-                                          const Layout &L, uint64_t base, uint32_t cm, bool grad) {
+                                          const Layout &L, uint64_t base, uint32_t cm) {
     R g = R(0), w0, w1;
     diag_weights<R>(o.kind, w0, w1);
     const int t = o.tmode == 1 ? (int)((L.tb >> o.targ) & 1) : (int)((base >> o.targ) & 1);
     const cx<R> f = t ? ud.m[3] : ud.m[0];
     const R w = t ? w1 : w0;
-    const bool all = cm == ~0u;
 #pragma unroll
     for (int e = 0; e < (1 << M); ++e) {
-        if (!all && !((cm >> e) & 1)) continue;
-        if (grad) g += w * (ls[e].x * ps[e].y - ls[e].y * ps[e].x);
-        ps[e] = cmul(f, ps[e]);
-        ls[e] = cmul(f, ls[e]);
+        const bool c = (cm >> e) & 1;
+        if (GRAD) g += c ? w * (ls[e].x * ps[e].y - ls[e].y * ps[e].x) : R(0);
+        ps[e] = sel(c, cmul(f, ps[e]), ps[e]);
+        ls[e] = sel(c, cmul(f, ls[e]), ls[e]);
     }
     return g;
 }
 
-template <typename R, int M, int CLS>
+template <typename R, int M, int CLS, bool GRAD>
 __device__ __forceinline__ R adj_lane_at(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &ud, int j, int lane,
-                                         uint32_t cm, int kind, bool grad) {
+                                         uint32_t cm) {
     R g = R(0);
     const int m = 1 << j;
     const bool hi = (lane >> j) & 1;
     const cx<R> cs = hi ? ud.m[3] : ud.m[0];
     const cx<R> cp = hi ? ud.m[2] : ud.m[1];
-    const bool all = cm == ~0u;
 #pragma unroll
     for (int e = 0; e < (1 << M); ++e) {
         const cx<R> pp = shfl_xor_cx(ps[e], m);
         const cx<R> lp = shfl_xor_cx(ls[e], m);
-        if (!all && !((cm >> e) & 1)) continue;
-        if (grad && !hi) g += grad_pair<R>(kind, ls[e], lp, ps[e], pp);
+        const bool c = (cm >> e) & 1;
+        if (GRAD) g += (c && !hi) ? grad_cls<R, CLS>(ls[e], lp, ps[e], pp) : R(0);
+        cx<R> rp, rl;
         if (CLS == CLS_ANTI) {
-            ps[e] = pp;
-            ls[e] = lp;
+            rp = pp;
+            rl = lp;
         } else if (CLS == CLS_REAL) {
-            ps[e] = mk<R>(cs.x * ps[e].x + cp.x * pp.x, cs.x * ps[e].y + cp.x * pp.y);
-            ls[e] = mk<R>(cs.x * ls[e].x + cp.x * lp.x, cs.x * ls[e].y + cp.x * lp.y);
+            rp = mk<R>(cs.x * ps[e].x + cp.x * pp.x, cs.x * ps[e].y + cp.x * pp.y);
+            rl = mk<R>(cs.x * ls[e].x + cp.x * lp.x, cs.x * ls[e].y + cp.x * lp.y);
         } else {
-            ps[e] = cadd(cmul(cs, ps[e]), cmul(cp, pp));
-            ls[e] = cadd(cmul(cs, ls[e]), cmul(cp, lp));
+            rp = cadd(cmul(cs, ps[e]), cmul(cp, pp));
+            rl = cadd(cmul(cs, ls[e]), cmul(cp, lp));
         }
+        ps[e] = sel(c, rp, ps[e]);
+        ls[e] = sel(c, rl, ls[e]);
     }
     return g;
 }
 
+template <typename R, int M, bool GRAD>
+__device__ __forceinline__ R eng_adjoint_g(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const EOp &o, const Mat2<R> &ud,
+                                           uint64_t base, const Layout &L, int lane) {
+    if (o.h < H_GEN) {
+        switch (o.h) {
+#define DQ_CASE(P) \
+        case H_REAL + P: return P < M ? adj_pairs_at<R, M, (P < M ? P : 0), CLS_REAL, GRAD>(ps, ls, ud) : R(0);
+        DQ_ENG_P(DQ_CASE)
+#undef DQ_CASE
+        }
+        return R(0);
+    }
+    if (o.h >= H_DIAG && o.h < H_CREAL) {
+        switch (o.h) {
+#define DQ_CASE(P) \
+        case H_DIAG + P: return P < M ? adj_diag_at<R, M, (P < M ? P : 0), GRAD>(ps, ls, ud, o.kind) : R(0);
+        DQ_ENG_P(DQ_CASE)
+#undef DQ_CASE
+        }
+        return R(0);
+    }
+    const uint32_t cm = op_cmask(o, L, base);
+    if (__all_sync(0xffffffffu, cm == 0)) return R(0);   // warp-uniform skip (see eng_apply)
+    switch (o.h) {
+#define DQ_CASE(P)                                                                                              \
+    case H_GEN + P:                                                                                             \
+        return P < M ? adj_pairs_sel<R, M, (P < M ? P : 0), CLS_GENERAL, GRAD>(ps, ls, ud, cm) : R(0);          \
+    case H_ANTI + P:                                                                                            \
+        return P < M ? adj_pairs_sel<R, M, (P < M ? P : 0), CLS_ANTI, false>(ps, ls, ud, cm) : R(0);            \
+    case H_CREAL + P:                                                                                           \
+        return P < M ? adj_pairs_sel<R, M, (P < M ? P : 0), CLS_REAL, GRAD>(ps, ls, ud, cm) : R(0);             \
+    case H_CDIAG + P:                                                                                           \
+        return P < M ? adj_diag_sel<R, M, (P < M ? P : 0), GRAD>(ps, ls, ud, o.kind, cm) : R(0);
+        DQ_ENG_P(DQ_CASE)
+#undef DQ_CASE
+    case H_LREAL: return adj_lane_at<R, M, CLS_REAL, GRAD>(ps, ls, ud, o.targ, lane, cm);
+    case H_LGEN: return adj_lane_at<R, M, CLS_GENERAL, GRAD>(ps, ls, ud, o.targ, lane, cm);
+    case H_LANTI: return adj_lane_at<R, M, CLS_ANTI, false>(ps, ls, ud, o.targ, lane, cm);
+    default: return adj_diag_uni<R, M, GRAD>(ps, ls, ud, o, L, base, cm);
+    }
+}
+
+// One reverse step; the gradient partial is formed only for ops with a slot.
 template <typename R, int M>
 __device__ __forceinline__ R eng_adjoint(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const EOp &o, const Mat2<R> &ud,
                                          uint64_t base, const Layout &L, int lane) {
-    const bool grad = o.slot >= 0;
-    const uint32_t cm = op_cmask(o, L, base);
-    if (__all_sync(0xffffffffu, cm == 0)) return R(0);   // warp-uniform exit (see eng_apply)
-    switch (o.h) {
-#define DQ_CASE(P)                                                                                       \
-    case H_REAL + P:                                                                                     \
-        return P < M ? adj_pairs_at<R, M, (P < M ? P : 0), CLS_REAL>(ps, ls, ud, cm, o.kind, grad) : R(0);    \
-    case H_GEN + P:                                                                                      \
-        return P < M ? adj_pairs_at<R, M, (P < M ? P : 0), CLS_GENERAL>(ps, ls, ud, cm, o.kind, grad) : R(0); \
-    case H_ANTI + P:                                                                                     \
-        return P < M ? adj_pairs_at<R, M, (P < M ? P : 0), CLS_ANTI>(ps, ls, ud, cm, o.kind, grad) : R(0);    \
-    case H_DIAG + P:                                                                                     \
-        return P < M ? adj_diag_at<R, M, (P < M ? P : 0)>(ps, ls, ud, cm, o.kind, grad) : R(0);
-        DQ_ENG_P(DQ_CASE)
-#undef DQ_CASE
-    case H_LREAL: return adj_lane_at<R, M, CLS_REAL>(ps, ls, ud, o.targ, lane, cm, o.kind, grad);
-    case H_LGEN: return adj_lane_at<R, M, CLS_GENERAL>(ps, ls, ud, o.targ, lane, cm, o.kind, grad);
-    case H_LANTI: return adj_lane_at<R, M, CLS_ANTI>(ps, ls, ud, o.targ, lane, cm, o.kind, grad);
-    default: return adj_diag_uni<R, M>(ps, ls, ud, o, L, base, cm, grad);
-    }
+    return o.slot >= 0 ? eng_adjoint_g<R, M, true>(ps, ls, o, ud, base, L, lane)
+                       : eng_adjoint_g<R, M, false>(ps, ls, o, ud, base, L, lane);
 }
 
 // FP32 (or FP64) warp sum.

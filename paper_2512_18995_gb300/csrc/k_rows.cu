@@ -175,7 +175,7 @@ template <typename R, int M>
 constexpr int rows_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) <= 64) ? 512 : 256; }
 
 template <typename R, int M>
-__global__ void __launch_bounds__(rows_max_threads<R, M>()) k_rows(RowArgs a) {
+__global__ void __launch_bounds__(rows_max_threads<R, M>(), sizeof(R) == 4 ? 2 : 1) k_rows(RowArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int n = a.n;

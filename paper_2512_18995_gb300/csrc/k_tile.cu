@@ -278,9 +278,13 @@ struct TileKArgs {
 // per thread) are limited to 256 threads so that they keep their registers.
 template <typename R, int M>
 constexpr int tile_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) >= 256) ? 256 : 512; }
+// Narrow register sets (<= 64 bytes of amplitudes per thread) are held to 64
+// registers, so that four 256-thread tiles fit on an SM.
+template <typename R, int M>
+constexpr int tile_min_blocks() { return ((1 << M) * (int)sizeof(cx<R>) <= 64) ? 2 : 1; }
 
 template <typename R, int M>
-__global__ void __launch_bounds__(tile_max_threads<R, M>(), 1)
+__global__ void __launch_bounds__(tile_max_threads<R, M>(), tile_min_blocks<R, M>())
 k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
