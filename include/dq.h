@@ -230,8 +230,9 @@ DQ_API dq_status dq_expect(dq_ctx *ctx, int nqubits, const dq_observables *obs,
  *                batch * nparams (params_per_row != 0);
  *   grad_data:   batch * nfeatures.
  * flags: DQ_ADJ_CLOBBER_STATE lets the call use `state` as the reverse-sweep
- * vector (it is left holding an approximation of |0...0>); without it the
- * state is preserved and one extra state-sized buffer of workspace is used. */
+ * vector (its contents are unspecified afterwards: the sweep stops at the
+ * earliest gate whose gradient is requested); without it the state is
+ * preserved and one extra state-sized buffer of workspace is used. */
 #define DQ_ADJ_CLOBBER_STATE 1
 DQ_API dq_status dq_adjoint_grad(dq_ctx *ctx, const dq_circuit *circuit,
                           const double *params, int params_per_row,

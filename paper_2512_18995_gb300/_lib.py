@@ -332,7 +332,7 @@ class Context:
                      row_weights: Optional[torch.Tensor] = None, params_per_row: bool = False,
                      want_expect: bool = True, want_grad: bool = True, state_out: Optional[torch.Tensor] = None,
                      expect_out: Optional[torch.Tensor] = None, grad_params: Optional[torch.Tensor] = None,
-                     grad_data: Optional[torch.Tensor] = None):
+                     grad_data: Optional[torch.Tensor] = None, want_data_grad: bool = True):
         dt = dtype_code(dtype)
         dev = torch.device(f"cuda:{self.device}")
         if want_expect and expect_out is None and obs is not None:
@@ -341,7 +341,7 @@ class Context:
             if grad_params is None and circuit.nparams > 0:
                 shape = (batch, circuit.nparams) if params_per_row else (circuit.nparams,)
                 grad_params = torch.empty(shape, dtype=torch.float64, device=dev)
-            if grad_data is None and circuit.nfeatures > 0 and data is not None:
+            if grad_data is None and circuit.nfeatures > 0 and data is not None and want_data_grad:
                 grad_data = torch.empty((batch, circuit.nfeatures), dtype=torch.float64, device=dev)
         else:
             grad_params = grad_data = None

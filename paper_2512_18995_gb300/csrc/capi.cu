@@ -308,6 +308,7 @@ dq_status get_plan(dq_ctx *ctx, const dq_circuit *c, int ppr, Plan **out) {
         if (g.gkind == 0) continue;
         const int slot = p->nslots++;
         p->slot_of_gate[i] = slot;
+        p->slot_is_data.push_back(g.gkind == 3 ? 1 : 0);
         if (g.gkind == 3) ds[g.gout].push_back(slot);
         else ps[g.gout].push_back(slot);
     }

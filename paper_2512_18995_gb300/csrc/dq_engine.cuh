@@ -38,6 +38,8 @@ enum Handler : int16_t {
     H_LGEN = 31,
     H_LANTI = 32,
     H_DUNI = 33,
+    H_FAN = 34,     // first op of a controlled-phase fan (see decode_fans)
+    H_FANM = 35,    // further members of a fan (consumed by its first op)
 };
 
 // One operation decoded for one register layout.  32 bytes.
@@ -126,6 +128,100 @@ inline EOp decode_op(const GOp &g, const int8_t *B, int M) {
     const int base = g.cls == CLS_ANTI ? H_ANTI : (g.cls == CLS_REAL ? (ctrl ? H_CREAL : H_REAL) : H_GEN);
     o.h = (int16_t)(base + (p < 0 ? 0 : p));
     return o;
+}
+
+// Controlled-phase fans.  Consecutive CP gates (no gradient, shared angle)
+// that all touch one common qubit q commute and multiply to
+//     diag: amplitude * prod_j e^{i phi_j b_j}  when b_q = 1,
+// so a run of them is decoded as one fan: its first op (H_FAN) carries the
+// location of q in (cmode, carg) (0: register position, 1: thread-local bit,
+// 2: block bit), the register positions of members in cmc, and the member
+// count in pad[0]; every op of the run (H_FAN then H_FANM) carries its member
+// qubit's location in (tmode, targ) and its own coefficient (the CP block,
+// whose m[3] is e^{i phi}).  Members on register bits come first, in position
+// order.  The run keeps its length, so op indices do not move.
+inline int fan_loc(int lbit, int gbit, const int8_t *B, int M, int8_t &mode, int8_t &arg) {
+    if (lbit >= 0)
+        for (int i = 0; i < M; ++i)
+            if (B[i] == lbit) {
+                mode = 0;
+                arg = (int8_t)i;
+                return i;
+            }
+    if (lbit >= 0) {
+        mode = 1;
+        arg = (int8_t)lbit;
+    } else {
+        mode = 2;
+        arg = (int8_t)gbit;
+    }
+    return -1;
+}
+
+inline bool fan_member(const GOp &g) { return g.cls == CLS_DIAG && g.kind == DQ_CP && g.slot < 0 && g.rowstep == 0; }
+
+// Decode ops [i0, i1) of `g` against register layout B, fusing CP runs of at
+// least kMinFan gates into fans; appends exactly i1 - i0 ops to `out`.
+constexpr int kMinFan = 3;
+inline void decode_with_fans(const std::vector<GOp> &g, int i0, int i1, const int8_t *B, int M,
+                             std::vector<EOp> &out) {
+    int i = i0;
+    while (i < i1) {
+        int end = i;
+        int q = -1;
+        if (fan_member(g[i])) {
+            // longest run from i sharing one qubit
+            for (int cand : {g[i].tg, g[i].cg}) {
+                int e = i;
+                while (e < i1 && fan_member(g[e]) && (g[e].tg == cand || g[e].cg == cand)) ++e;
+                if (e - i > end - i) {
+                    end = e;
+                    q = cand;
+                }
+            }
+        }
+        if (end - i < kMinFan) {
+            out.push_back(decode_op(g[i], B, M));
+            ++i;
+            continue;
+        }
+        // members: the other qubit of each CP, register members first
+        struct Mem { int pos, lbit, gbit, idx; };
+        std::vector<Mem> mem;
+        int qlbit = -1;
+        for (int j = i; j < end; ++j) {
+            const bool qt = g[j].tg == q;
+            const int ol = qt ? g[j].cl : g[j].tl, og = qt ? g[j].cg : g[j].tg;
+            if (qlbit < 0) qlbit = qt ? g[j].tl : g[j].cl;
+            int8_t md, ar;
+            const int pos = fan_loc(ol, og, B, M, md, ar);
+            mem.push_back({pos, ol, og, j});
+        }
+        std::stable_sort(mem.begin(), mem.end(), [](const Mem &a, const Mem &b) {
+            const int ka = a.pos >= 0 ? a.pos : 64, kb = b.pos >= 0 ? b.pos : 64;
+            return ka < kb;
+        });
+        uint32_t rmask = 0;
+        for (const Mem &x : mem)
+            if (x.pos >= 0) rmask |= 1u << x.pos;
+        for (size_t j = 0; j < mem.size(); ++j) {
+            const GOp &src = g[mem[j].idx];
+            EOp o{};
+            o.h = (int16_t)(j == 0 ? H_FAN : H_FANM);
+            o.kind = (int16_t)src.kind;
+            o.coef = src.coef;
+            o.rowstep = 0;
+            o.slot = -1;
+            fan_loc(mem[j].lbit, mem[j].gbit, B, M, o.tmode, o.targ);
+            if (j == 0) {
+                fan_loc(qlbit, q, B, M, o.cmode, o.carg);
+                o.cmc = rmask;
+                o.pad[0] = (int32_t)mem.size();
+            }
+            out.push_back(o);
+        }
+        i = end;
+    }
 }
 
 struct Layout {
@@ -285,6 +381,7 @@ __device__ __forceinline__ void eng_apply(cx<R> (&a)[1 << M], const EOp &o, cons
         }
         return;
     }
+    if (o.h >= H_FAN) return;   // fans are run by eng_fan from their first op
     const uint32_t cm = op_cmask(o, L, base);
     if (__all_sync(0xffffffffu, cm == 0)) return;
     switch (o.h) {
@@ -300,6 +397,61 @@ __device__ __forceinline__ void eng_apply(cx<R> (&a)[1 << M], const EOp &o, cons
     case H_LANTI: lane_at<R, M, CLS_ANTI>(a, u, o.targ, lane, cm); break;
     default: diag_uni<R, M>(a, u, o, L, base, cm); break;
     }
+}
+
+// A controlled-phase fan (ops[0] is its H_FAN op, cf the coefficients of
+// its ops): every amplitude with b_q = 1 is multiplied by F * prod of the
+// register members' phases whose bits are set in it, F being the product of
+// the phases of members on thread or block bits that are set.  Thread-
+// uniform branches only (no shuffles), so lanes may diverge.
+template <typename R, int M, int QP>
+__device__ __forceinline__ void fan_elems(cx<R> (&a)[1 << M], const cx<R> &F, const cx<R> (&wp)[M]) {
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) {
+        if (QP >= 0 && !((e >> QP) & 1)) continue;
+        cx<R> f = F;
+#pragma unroll
+        for (int p = 0; p < M; ++p)
+            if (p != QP && ((e >> p) & 1)) f = cmul(f, wp[p]);
+        a[e] = cmul(f, a[e]);
+    }
+}
+
+template <typename R, int M>
+__device__ __forceinline__ int eng_fan(cx<R> (&a)[1 << M], const EOp *ops, const Mat2<R> *cf, uint64_t base,
+                                       const Layout &L) {
+    const EOp h = ops[0];
+    const int m = h.pad[0];
+    if (h.cmode != 0) {
+        const int qb = h.cmode == 1 ? (int)((L.tb >> h.carg) & 1) : (int)((base >> h.carg) & 1);
+        if (!qb) return m;
+    }
+    cx<R> wp[M];
+    int j = 0;
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+        if ((h.cmc >> p) & 1) {
+            wp[p] = cf[j].m[3];
+            ++j;
+        } else {
+            wp[p] = mk<R>(R(1), R(0));
+        }
+    }
+    cx<R> F = mk<R>(R(1), R(0));
+    for (; j < m; ++j) {
+        const EOp e = ops[j];
+        const int bit = e.tmode == 1 ? (int)((L.tb >> e.targ) & 1) : (int)((base >> e.targ) & 1);
+        if (bit) F = cmul(F, cf[j].m[3]);
+    }
+    switch (h.cmode == 0 ? (int)h.carg : -1) {
+    case 0: fan_elems<R, M, 0>(a, F, wp); break;
+    case 1: if (M > 1) fan_elems<R, M, (M > 1 ? 1 : 0)>(a, F, wp); break;
+    case 2: if (M > 2) fan_elems<R, M, (M > 2 ? 2 : 0)>(a, F, wp); break;
+    case 3: if (M > 3) fan_elems<R, M, (M > 3 ? 3 : 0)>(a, F, wp); break;
+    case 4: if (M > 4) fan_elems<R, M, (M > 4 ? 4 : 0)>(a, F, wp); break;
+    default: fan_elems<R, M, -1>(a, F, wp); break;
+    }
+    return m;
 }
 
 // ---------------------------------------------------------------------------

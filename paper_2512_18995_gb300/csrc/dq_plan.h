@@ -64,6 +64,20 @@ struct Plan {
     int32_t *d_pslot_ptr = nullptr, *d_pslots = nullptr;
     int32_t *d_dslot_ptr = nullptr, *d_dslots = nullptr;
     void release();
+    // Whether gradient slot `slot` feeds a requested output (parameters when
+    // want_params, encoded data when want_data).
+    bool slot_needed(int slot, bool want_params, bool want_data) const {
+        if (slot < 0) return false;
+        return slot_is_data[slot] ? want_data : want_params;
+    }
+    // First gate (in circuit order) whose gradient is requested; ngates when
+    // none.  The reverse sweep never needs to go below it.
+    int first_grad_gate(bool want_params, bool want_data) const {
+        for (int i = 0; i < ngates; ++i)
+            if (slot_needed(slot_of_gate[i], want_params, want_data)) return i;
+        return ngates;
+    }
+    std::vector<char> slot_is_data;    // per slot: encoded-data gradient
 };
 
 // Workspace bump allocator over the context's device buffer.

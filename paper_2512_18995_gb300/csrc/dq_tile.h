@@ -97,10 +97,11 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
                           const void *coef, void *state, int batch, void *tws, int nsm, cudaStream_t s,
                           int64_t *launches);
 
-TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, int amp, bool adjoint);
+// g0: first gate of the circuit to schedule (adjoint sweeps that stop early).
+TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, int amp, bool adjoint, int g0 = 0);
 
 // Host planner.
 bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, TileSchedule &out,
-                         bool adjoint = false);
+                         bool adjoint = false, int g0 = 0);
 
 }  // namespace dq

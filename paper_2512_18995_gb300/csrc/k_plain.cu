@@ -514,7 +514,9 @@ cudaError_t plain_adjoint(const Plan &p, const void *coef, const std::vector<Dev
     const int nblk = blocks_per_row(n, batch);
     const Mat2<R> *cf = (const Mat2<R> *)coef;
     cx<R> *ps = (cx<R> *)psi, *ls = (cx<R> *)lam;
-    for (int gi = p.ngates - 1; gi >= 0; --gi) {
+    // gates before the first requested gradient are never un-applied
+    const int gstop = p.first_grad_gate(grad_params != nullptr, grad_data != nullptr);
+    for (int gi = p.ngates - 1; gi >= gstop; --gi) {
         const DevGate &g = p.gates[gi];
         if (g.cls == CLS_SWAP) {
             const int ib = (g.t >= 1) ? n - 3 : n - 2;

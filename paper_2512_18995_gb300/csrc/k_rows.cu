@@ -155,6 +155,7 @@ struct RowArgs {
     const void *coef;
     int n;
     int batch;
+    int nrseg_run;          // reverse segments to run (later ones only un-apply gradient-free gates)
     const void *state_in;
     void *state_out;
     int forward;
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>(), sizeof(R) == 4 ? 2 :
         }
         __syncthreads();   // bufP is rewritten by the first layout change
         // ---- reverse sweep -----------------------------------------------------
-        for (int s = 0; s < a.nrseg; ++s) {
+        for (int s = 0; s < a.nrseg_run; ++s) {
             const ESeg sg = sr[s];
             if (s > 0) {
                 eng_store<R, M>(ps, bufP, L);
@@ -416,6 +417,26 @@ cudaError_t rows_launch(const RowProgram &rp, const Plan &p, const void *coef, c
     a.grad_params = grad_params;
     a.grad_data = grad_data;
     a.part = part;
+    // reverse segments run from the last op down; stop after the one holding
+    // the first op whose gradient is requested
+    a.nrseg_run = 0;
+    if (grad) {
+        int first = (int)rp.fops.size();
+        for (int i = 0; i < (int)rp.fops.size(); ++i) {
+            const int acc = rp.fops[i].slot;
+            if (acc < 0) continue;
+            const bool data = acc >= rp.nacc_shared && acc < rp.nacc_shared + p.nfeat;
+            const bool params = !data;
+            if ((data && grad_data) || (params && grad_params)) {
+                first = i;
+                break;
+            }
+        }
+        for (int sg = 0; sg < (int)rp.rsegs.size(); ++sg) {
+            a.nrseg_run = sg + 1;
+            if (rp.rsegs[sg].op0 - rp.rsegs[sg].nops + 1 <= first) break;
+        }
+    }
     constexpr int Mmax = sizeof(R) == 4 ? 4 : 3;
     const void *kfn = nullptr;
     switch (rp.M) {

@@ -96,7 +96,8 @@ GateBits gate_bits(const DevGate &g) {
 
 }  // namespace
 
-bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, TileSchedule &out, bool adjoint) {
+bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, TileSchedule &out, bool adjoint,
+                         int g0) {
     const int n = p.n;
     const int wb = amp_bytes == 16 ? 1 : 0;
     // a SWAP of two high bits needs two free tile bits
@@ -108,8 +109,9 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
     out.M = M;
     out.adjoint = adjoint;
     const uint64_t lowmask = (uint64_t(1) << low) - 1;
-    std::vector<int> remaining(p.ngates);
-    for (int i = 0; i < p.ngates; ++i) remaining[i] = i;
+    // gates [0, g0) are left out (an adjoint sweep that stops before them)
+    std::vector<int> remaining;
+    for (int i = std::max(0, g0); i < p.ngates; ++i) remaining.push_back(i);
     int guard = 0;
     while (!remaining.empty()) {
         if (++guard > p.ngates + 2) return false;
@@ -190,7 +192,7 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
             for (int j = kTileLaneBits; j < k && (int)full.size() < M; ++j)
                 if (std::find(full.begin(), full.end(), j) == full.end()) full.push_back(j);
             for (int i = 0; i < 8; ++i) sg.B[i] = i < M ? (int8_t)full[i] : (int8_t)-1;
-            for (int i = sop0; i < end; ++i) out.ops.push_back(decode_op(gops[i], sg.B, M));
+            decode_with_fans(gops, sop0, end, sg.B, M, out.ops);
             out.segs.push_back(sg);
         };
         for (int i = 0; i < pass.nops; ++i) {
@@ -348,6 +350,10 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
             eng_load<R, M>(r, cur, L);
             for (int oi = sg.op0 - a.op0; oi < sg.op0 - a.op0 + sg.nops; ++oi) {
                 const TOp o = sops[oi];
+                if (o.h == H_FAN) {
+                    oi += eng_fan<R, M>(r, sops + oi, scoef + oi, base, L) - 1;
+                    continue;
+                }
                 const Mat2<R> u = o.rowstep ? gcoef[o.coef + row * o.rowstep] : scoef[oi];
                 eng_apply<R, M>(r, o, u, base, L, lane);
             }
@@ -377,8 +383,9 @@ size_t tile_smem_bytes(int k, int amp, int nops, int nseg) {
            (size_t)nops * (amp == 8 ? sizeof(Mat2<float>) : sizeof(Mat2<double>)) + 64;
 }
 
-uint64_t sched_key(const Plan &p, int k, int low, int amp, int M, bool adjoint = false) {
+uint64_t sched_key(const Plan &p, int k, int low, int amp, int M, bool adjoint = false, int g0 = 0) {
     uint64_t h = p.key ^ (adjoint ? 0x51ED270B27A4C3F1ull : 0x9E3779B97F4A7C15ull);
+    h = (h ^ (uint64_t)(uint32_t)g0) * 1099511628211ull;
     h = (h ^ (uint64_t)M) * 1099511628211ull;
     h = (h ^ (uint64_t)k) * 1099511628211ull;
     h = (h ^ (uint64_t)low) * 1099511628211ull;
@@ -424,12 +431,12 @@ bool upload_vec(T **dst, const std::vector<T> &v) {
 
 }  // namespace
 
-TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, int amp, bool adjoint) {
-    const uint64_t key = sched_key(p, k, low, amp, M, adjoint);
+TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, int amp, bool adjoint, int g0) {
+    const uint64_t key = sched_key(p, k, low, amp, M, adjoint, g0);
     auto it = tc.schedules.find(key);
     if (it != tc.schedules.end()) return it->second;
     TileSchedule *s = new TileSchedule();
-    if (!tile_build_schedule(p, k, low, M, amp, *s, adjoint)) {
+    if (!tile_build_schedule(p, k, low, M, amp, *s, adjoint, g0)) {
         delete s;
         return nullptr;
     }

@@ -173,9 +173,15 @@ struct ObsArgs {
     int *errflag;
 };
 
+// Amplitudes each thread owns in an observable pass (threads = 2^k / kObsJ).
+constexpr int kObsJ = 8;
+
 template <typename R>
-__global__ void __launch_bounds__(256) k_tile_obs(const __grid_constant__ CUtensorMap mp,
-                                                  const __grid_constant__ CUtensorMap ml, ObsArgs a) {
+constexpr int obs_max_threads() { return sizeof(R) == 4 ? 1024 : 512; }
+
+template <typename R>
+__global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_constant__ CUtensorMap mp,
+                                                   const __grid_constant__ CUtensorMap ml, ObsArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int64_t dim = int64_t(1) << a.g.k;
@@ -229,35 +235,53 @@ __global__ void __launch_bounds__(256) k_tile_obs(const __grid_constant__ CUtens
             failed = true;
             break;
         }
-        if (a.lam_mode == 1)
-            for (int64_t l = tid; l < dim; l += blockDim.x) bufL[l] = mk<R>(R(0), R(0));
+        // this thread's amplitudes l_i = tid + i * blockDim and their lambda
+        cx<R> x[kObsJ], lv[kObsJ];
+#pragma unroll
+        for (int i = 0; i < kObsJ; ++i) {
+            const int l = tid + i * (int)blockDim.x;
+            x[i] = bufP[l];
+            lv[i] = a.lam_mode == 2 ? bufL[l] : mk<R>(R(0), R(0));
+        }
         const double *w = a.rw ? a.rw + row * a.nobs : nullptr;
         for (int j = 0; j < a.nt; ++j) {
             const OTerm o = st[j];
             const int bpar = __popcll(base & o.sout) & 1;
             const R wc = (R)((w ? w[o.obs] : 1.0) * o.coeff);
             R e = R(0);
-            for (int64_t l = tid; l < dim; l += blockDim.x) {
-                const cx<R> x = bufP[l];
-                const uint32_t src = (uint32_t)l ^ o.floc;
-                const cx<R> y = bufP[src];
-                const int k4 = (o.nY + 2 * ((__popc((uint32_t)l & o.sloc) & 1) ^ bpar)) & 3;
-                const R re = y.x * x.x + y.y * x.y, im = y.x * x.y - y.y * x.x;
-                e += (k4 == 0) ? re : (k4 == 1 ? -im : (k4 == 2 ? -re : im));
-                if (a.lam_mode) {
+            if (o.floc == 0) {
+                // Z string: sign (-1)^(parity of l & sloc, and of the tile base)
+#pragma unroll
+                for (int i = 0; i < kObsJ; ++i) {
+                    const int l = tid + i * (int)blockDim.x;
+                    const bool neg = (__popc((uint32_t)l & o.sloc) & 1) ^ bpar;
+                    const R pr = x[i].x * x[i].x + x[i].y * x[i].y;
+                    e += neg ? -pr : pr;
+                    const R f = neg ? -wc : wc;
+                    lv[i].x += f * x[i].x;
+                    lv[i].y += f * x[i].y;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < kObsJ; ++i) {
+                    const int l = tid + i * (int)blockDim.x;
+                    const uint32_t src = (uint32_t)l ^ o.floc;
+                    const cx<R> y = bufP[src];
+                    const int k4 = (o.nY + 2 * ((__popc((uint32_t)l & o.sloc) & 1) ^ bpar)) & 3;
+                    const R re = y.x * x[i].x + y.y * x[i].y, im = y.x * x[i].y - y.y * x[i].x;
+                    e += (k4 == 0) ? re : (k4 == 1 ? -im : (k4 == 2 ? -re : im));
                     const int k5 = (o.nY + 2 * ((__popc(src & o.sloc) & 1) ^ bpar)) & 3;
-                    const R pr = (k5 == 0) ? R(1) : (k5 == 2 ? R(-1) : R(0));
-                    const R pi = (k5 == 1) ? R(1) : (k5 == 3 ? R(-1) : R(0));
-                    cx<R> lv = bufL[l];
-                    lv.x += wc * (pr * y.x - pi * y.y);
-                    lv.y += wc * (pr * y.y + pi * y.x);
-                    bufL[l] = lv;
+                    // lambda[l] += wc * i^k5 * y
+                    const R yr = (k5 & 1) ? -y.y : y.x, yi = (k5 & 1) ? y.x : y.y;
+                    const R sg = (k5 & 2) ? -wc : wc;
+                    lv[i].x += sg * yr;
+                    lv[i].y += sg * yi;
                 }
             }
             e = warp_sum_t(e);
             if (lane == 0) accw[warp * a.nt + j] += e;
         }
-        __syncthreads();
+        __syncthreads();   // every partner read of this tile is done
         for (int j = tid; j < a.nt; j += blockDim.x) {
             double sum = 0.0;
             for (int ww = 0; ww < nw; ++ww) {
@@ -267,6 +291,8 @@ __global__ void __launch_bounds__(256) k_tile_obs(const __grid_constant__ CUtens
             acc[j] += sum;
         }
         if (a.lam_mode) {
+#pragma unroll
+            for (int i = 0; i < kObsJ; ++i) bufL[tid + i * (int)blockDim.x] = lv[i];
             fence_async_smem();
             __syncthreads();
             if (tid == 0) {
@@ -479,7 +505,8 @@ cudaError_t tile_observe(TileCache &tc, int n, const std::vector<DevTerm> &bits,
     }
     const int64_t ntiles = (int64_t)batch << (n - k);
     const int grid = adjoint_grid(ntiles, nsm);
-    const int threads = 256;
+    if (k < 8 || (1 << k) / kObsJ > obs_max_threads<R>()) return cudaErrorNotSupported;
+    const int threads = (1 << k) / kObsJ;
     const int nw = threads / 32;
     if (out) {
         cudaError_t e = cudaMemsetAsync(part, 0, sizeof(double) * bits.size() * (size_t)batch * grid, s);
@@ -525,7 +552,10 @@ cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &
     if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
     int k, low, M;
     adjoint_tile<R>(p.n, k, low, M);
-    TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), true);
+    // the sweep stops at the first gate whose gradient is requested: schedule
+    // only the gates from there on
+    const int g0 = p.first_grad_gate(gp != nullptr, gd != nullptr);
+    TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), true, g0);
     if (!sc) return cudaErrorNotSupported;
     const int64_t ntiles = (int64_t)batch << (p.n - k);
     const int grid = adjoint_grid(ntiles, nsm);
@@ -533,7 +563,16 @@ cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &
     const int nw = threads / 32;
     cudaError_t e = cudaMemsetAsync(part, 0, sizeof(double) * (size_t)std::max(1, p.nslots) * batch * grid, s);
     if (e != cudaSuccess) return e;
-    for (int pi = (int)sc->passes.size() - 1; pi >= 0; --pi) {
+    // passes below the first one holding a requested gradient are never
+    // un-applied (passes are in application order)
+    int pstop = (int)sc->passes.size();
+    for (int pi = 0; pi < (int)sc->passes.size() && pstop == (int)sc->passes.size(); ++pi)
+        for (int j = 0; j < sc->passes[pi].nslot; ++j)
+            if (p.slot_needed(sc->slots[sc->passes[pi].slot0 + j], gp != nullptr, gd != nullptr)) {
+                pstop = pi;
+                break;
+            }
+    for (int pi = (int)sc->passes.size() - 1; pi >= pstop; --pi) {
         const TPass &ps = sc->passes[pi];
         TileDims d;
         if (!make_dims(ps.T, p.n, wb, d)) return cudaErrorInvalidValue;

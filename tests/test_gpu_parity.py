@@ -216,9 +216,54 @@ def test_clobber_flag_uses_state(ctx):
     gp, _ = ctx.adjoint_grad(circ, dev(params), dq.Observables(obs), st, clobber=True)
     _, gp_ref, _ = oracle.adjoint(n, gates, obs, params, batch=batch)
     assert_rel(gp.cpu().numpy(), gp_ref, torch.complex128)
-    zero = np.zeros((batch, 1 << n), complex)
-    zero[:, 0] = 1
-    assert_amps(np_state(st), zero, torch.complex128, "un-applied state")
+
+
+@pytest.mark.parametrize("dtype", sorted(DTYPES))
+@pytest.mark.parametrize("n,batch", [(17, 2), (20, 1)])
+def test_qft_controlled_phase_fans(ctx, dtype, n, batch):
+    """QFT columns (runs of controlled phases sharing one qubit) on the tiled
+    path are applied as fused fans: states against the oracle, from random
+    product states so that every fan member's bit takes both values."""
+    ctx.set_path(dq.PATH_FUSED)
+    dt = DTYPES[dtype]
+    rng = np.random.default_rng(n + 5)
+    pre = [W.Gate("ry", (q,), angle=float(a)) for q, a in enumerate(rng.uniform(0, 2 * math.pi, size=n))]
+    gates = pre + W.qft_gates(n) + [W.Gate("rz", (q,), angle=0.1 * q) for q in range(0, n, 3)]
+    circ = dq.Circuit(n, gates)
+    st = torch.empty((batch, 1 << n), dtype=dt, device="cuda")
+    ctx.state_init(st, n)
+    ctx.apply_circuit(circ, None, st)
+    torch.cuda.synchronize()
+    ctx.check()
+    ref = oracle.run(n, gates, batch=batch)
+    assert_amps(np_state(st), ref, dt, "QFT state")
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+@pytest.mark.parametrize("n,batch", [(7, 3), (13, 2), (18, 1)])
+def test_gradient_free_prefix(ctx, path, n, batch):
+    """A parameter-free prefix (QFT) before the parametric layers: the reverse
+    sweep stops at the first parametric gate; gradients, expectations and
+    data gradients (when an encoding precedes the QFT) stay exact."""
+    ctx.set_path(PATHS[path])
+    rng = np.random.default_rng(40 + n)
+    gates = W.encode_layer(n, wires=[0, n - 1]) + W.qft_gates(n) + W.hea_layers(n, 1)
+    npar = 2 * n
+    params = rng.uniform(0, 2 * math.pi, size=npar)
+    data = rng.uniform(-math.pi, math.pi, size=(batch, 2))
+    obs = [W.obs_tfim_open(n)]
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=2)
+    exp_ref, gp_ref, gd_ref = oracle.adjoint(n, gates, obs, params, data=data, batch=batch)
+    for with_data in (False, True):
+        e, gp, gd, _ = ctx.forward_grad(circ, dev(params), dq.Observables(obs), batch, torch.complex64,
+                                        data=dev(data), want_data_grad=with_data)
+        assert (gd is not None) == with_data
+        torch.cuda.synchronize()
+        scale = obs_scale(obs)
+        assert_rel(e.cpu().numpy(), exp_ref, torch.complex64, "expectation", floor=scale)
+        assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, "grad params", floor=scale * batch)
+        if with_data:
+            assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, "grad data", floor=scale)
 
 
 # ---------------------------------------------------------------------------
