@@ -156,7 +156,12 @@ void adjoint_tile(int n, int &k, int &low, int &M) {
     low = std::max(kLaneBits, std::min(7, k - 3));
 }
 
-int adjoint_grid(int64_t ntiles, int nsm) { return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 2 * nsm)); }
+// Persistent grid: two CTAs per SM, one when the two tiles of a CTA (psi and
+// lambda, 2^k amplitudes each) take more than half of shared memory.
+int adjoint_grid(int64_t ntiles, int nsm, int k, int amp) {
+    const int per_sm = ((size_t)2 * amp << k) > 100 * 1024 ? 1 : 2;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)per_sm * nsm));
+}
 
 // ---------------------------------------------------------------------------
 // observable pass
@@ -504,7 +509,7 @@ cudaError_t tile_observe(TileCache &tc, int n, const std::vector<DevTerm> &bits,
         tc.obs[key] = ns;   // owned by the cache, released by tile_release_obs
     }
     const int64_t ntiles = (int64_t)batch << (n - k);
-    const int grid = adjoint_grid(ntiles, nsm);
+    const int grid = adjoint_grid(ntiles, nsm, k, (int)sizeof(cx<R>));
     if (k < 8 || (1 << k) / kObsJ > obs_max_threads<R>()) return cudaErrorNotSupported;
     const int threads = (1 << k) / kObsJ;
     const int nw = threads / 32;
@@ -558,7 +563,7 @@ cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &
     TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), true, g0);
     if (!sc) return cudaErrorNotSupported;
     const int64_t ntiles = (int64_t)batch << (p.n - k);
-    const int grid = adjoint_grid(ntiles, nsm);
+    const int grid = adjoint_grid(ntiles, nsm, k, (int)sizeof(cx<R>));
     const int threads = 1 << (k - M);
     const int nw = threads / 32;
     cudaError_t e = cudaMemsetAsync(part, 0, sizeof(double) * (size_t)std::max(1, p.nslots) * batch * grid, s);
