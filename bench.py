@@ -297,6 +297,7 @@ def our_arm(args, rank, world, dist):
         extras["hbm_sweep"] = hbm_sweep(ctx, device, hbm_peak, peak_kind)
         extras["grads"] = batched_grads(ctx, device)
         extras["dense_block"] = dense_block(ctx, device, hbm_peak, peak_kind)
+        extras["uneven_batch"] = uneven_batch(ctx, device)
         ctx.set_path({"auto": dq.PATH_AUTO, "plain": dq.PATH_PLAIN, "fused": dq.PATH_FUSED}[args.path])
 
     if rank == 0:
@@ -384,6 +385,36 @@ def dense_block(ctx, device, hbm_peak, peak_kind, n=30, reps=4):
             "hbm_frac": gbs / hbm_peak, "peak_kind": peak_kind, "tflops_tf32x3": tflops,
             "tf32_peak": tf32_peak, "tensor_frac": tflops / tf32_peak,
             "tf32_peak_kind": "measured bf16 x nominal tf32/bf16" if bf16 else "fallback bf16 x nominal tf32/bf16"}
+
+
+def uneven_batch(ctx, device, steps=3):
+    """1024 circuits of 8..16 qubits and depth 10..40 (own parameters each):
+    expectations and per-circuit adjoint gradients, the persistent uneven-
+    batch kernel vs the per-gate path run circuit after circuit."""
+    import torch
+    import paper_2512_18995_gb300 as dq
+    circs = W.config_c4(1024)
+    dcs = [dq.Circuit(n, g, nparams=len(a)) for n, g, a in circs]
+    params = torch.tensor(np.concatenate([a for _, _, a in circs]), device=device)
+    obs = dq.Observables([W.obs_zz01_x0()])
+    out = {}
+    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+        ctx.set_path(path)
+        ctx.batch_forward_grad(dcs, params, obs, torch.complex64)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            ctx.batch_forward_grad(dcs, params, obs, torch.complex64)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out[name] = {"ms_per_step": ms, "circuits_per_s": len(circs) / (ms / 1e3)}
+    ctx.set_path(dq.PATH_AUTO)
+    out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
+    out["workload"] = "c4_uneven1024_c64"
+    return out
 
 
 def batched_grads(ctx, device, steps=5):

@@ -159,7 +159,8 @@ DQ_API dq_status dq_workspace_bytes(dq_ctx *ctx, const dq_circuit *circuit,
                              size_t *out);
 
 /* Bytes of workspace that dq_batch_forward_grad needs for these circuits
- * and dtype, written to *out. */
+ * and dtype under the context's current path (observables of up to 256
+ * terms), written to *out. */
 DQ_API dq_status dq_batch_workspace_bytes(dq_ctx *ctx, int ncirc, const dq_circuit *circuits,
                                           int dtype, size_t *out);
 
@@ -260,7 +261,9 @@ DQ_API dq_status dq_forward_grad(dq_ctx *ctx, const dq_circuit *circuit,
  * parameters at params[param_offsets[c] ...]; param_offsets: host, ncirc + 1
  * entries.  expect_out: device FP64 ncirc * nobs.  grad_params: device FP64
  * laid out like params (may be NULL for forward only).  The observable must
- * act on wires below every circuit's qubit count. */
+ * act on wires below every circuit's qubit count.  Under DQ_PATH_PLAIN the
+ * circuits run one after another on the per-gate path (the baseline of the
+ * persistent kernel). */
 DQ_API dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit *circuits,
                                 const double *params, const int64_t *param_offsets,
                                 const dq_observables *obs, int dtype,

@@ -983,7 +983,24 @@ dq_status dq_batch_workspace_bytes(dq_ctx *ctx, int ncirc, const dq_circuit *cir
     a.take(mat * (size_t)(ngates + 1));
     a.take(batch_scratch_bytes(nmax, amp_bytes(dtype), ctx->nsm, ctx->smem_optin));
     a.take(256);
-    *out = a.used;
+    size_t need = a.used;
+    if (ctx->path == DQ_PATH_PLAIN) {
+        // one circuit at a time on the per-gate path (observables of up to
+        // 256 terms)
+        for (int c = 0; c < ncirc; ++c) {
+            Plan *p = nullptr;
+            if ((st = get_plan(ctx, &circuits[c], 0, &p)) != DQ_OK) return st;
+            const size_t sb = ((size_t)1 << p->n) * amp_bytes(dtype);
+            Arena b;
+            b.measuring = true;
+            b.take(coef_bytes(*p, 1, dtype));
+            b.take(2 * sb);
+            b.take(plain_adjoint_part_bytes(*p, 1));
+            b.take(plain_expect_part_bytes(p->n, 256, 1));
+            need = std::max(need, b.used);
+        }
+    }
+    *out = need;
     return DQ_OK;
 }
 
@@ -1136,6 +1153,26 @@ dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit *circui
     const int64_t ptotal = param_offsets[ncirc];
     if (ptotal > 0 && !params) return fail(ctx, DQ_ERR_INVALID_ARG, "params is NULL");
     if (ptotal >= (int64_t(1) << 31)) return fail(ctx, DQ_ERR_INVALID_ARG, "too many parameters");
+    cudaStream_t s0 = (cudaStream_t)stream;
+    if (ctx->path == DQ_PATH_PLAIN) {
+        // the per-gate path, circuit after circuit (the baseline for the
+        // persistent kernel below)
+        for (int c = 0; c < ncirc; ++c) {
+            Plan *pc = nullptr;
+            if ((st = get_plan(ctx, &circuits[c], 0, &pc)) != DQ_OK) return st;
+            ObsDev *oc = nullptr;
+            if ((st = get_obs(ctx, obs, circuits[c].nqubits, &oc)) != DQ_OK) return st;
+            const double *pp = params ? params + param_offsets[c] : nullptr;
+            double *gpc = (grad_params && circuits[c].nparams > 0) ? grad_params + param_offsets[c] : nullptr;
+            double *eo = expect_out + (size_t)c * oc->nobs;
+            st = dtype == DQ_C64 ? forward_grad_impl<float>(ctx, *pc, oc, pp, nullptr, nullptr, 1, eo, gpc, nullptr,
+                                                            nullptr, s0)
+                                 : forward_grad_impl<double>(ctx, *pc, oc, pp, nullptr, nullptr, 1, eo, gpc, nullptr,
+                                                             nullptr, s0);
+            if (st != DQ_OK) return st;
+        }
+        return DQ_OK;
+    }
     BatchDev *bd = nullptr;
     std::vector<BindGate> allbind;
     auto it = ctx->batches.find(h);

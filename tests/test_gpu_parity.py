@@ -309,7 +309,9 @@ def test_config_c3_qml_batch(ctx, path):
     assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, "grad data")
 
 
-def test_config_c4_uneven_batch(ctx):
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_config_c4_uneven_batch(ctx, path):
+    ctx.set_path(PATHS[path])
     circs = W.config_c4(1024)
     obs = [W.obs_zz01_x0()]
     dcs = [dq.Circuit(n, g, nparams=len(a)) for n, g, a in circs]
