@@ -8,6 +8,7 @@
 // bits, so every TMA box row is a contiguous run of memory.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -49,6 +50,21 @@ struct TileSchedule {
     TOp *d_ops = nullptr, *d_rops = nullptr;
     TSeg *d_segs = nullptr, *d_rsegs = nullptr;
     int32_t *d_slots = nullptr;
+    // Launch data of the forward passes for the last state buffer seen (TMA
+    // descriptors, shared memory, grid), so repeated calls on one buffer do
+    // no host-side encoding or occupancy queries.
+    struct Launch {
+        CUtensorMap map;
+        size_t smem;
+        int grid;
+    };
+    std::vector<Launch> fwd_launch;
+    const void *fwd_state = nullptr;
+    int fwd_batch = -1;
+    // the same for the reverse passes (psi and lambda descriptors)
+    std::vector<CUtensorMap> adj_psi, adj_lam;
+    const void *adj_p = nullptr, *adj_l = nullptr;
+    int adj_batch = -1;
     void release();
 };
 
@@ -66,6 +82,7 @@ struct TileCache {
     int *errflag = nullptr;             // device error flag of the owning context
     std::unordered_map<uint64_t, TileSchedule *> schedules;
     std::unordered_map<uint64_t, void *> obs;   // observable-pass schedules
+    std::unordered_map<const void *, size_t> smem_set;   // dynamic shared memory limit set per kernel
     void release();
 };
 

@@ -255,10 +255,10 @@ __global__ void k_expect_finalize(const double *__restrict__ part, const DevTerm
     const int row = blockIdx.x / nobs, o = blockIdx.x % nobs;
     const int k0 = obs_ptr[o], k1 = obs_ptr[o + 1];
     double acc = 0.0;
-    const int64_t cnt = (int64_t)(k1 - k0) * nblk;
-    for (int64_t i = threadIdx.x; i < cnt; i += kThreads) {
-        const int k = k0 + (int)(i / nblk), blk = (int)(i % nblk);
-        acc += terms[k].coeff * part[((int64_t)k * nbatch + row) * nblk + blk];
+    for (int k = k0; k < k1; ++k) {
+        const double c = terms[k].coeff;
+        const double *pk = part + ((int64_t)k * nbatch + row) * nblk;
+        for (int blk = threadIdx.x; blk < nblk; blk += kThreads) acc += c * pk[blk];
     }
     const double s = block_sum<kThreads>(acc, red);
     if (threadIdx.x == 0) out[(int64_t)row * nobs + o] = s;

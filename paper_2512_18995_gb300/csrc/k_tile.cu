@@ -298,29 +298,31 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
     TSeg *ssegs = reinterpret_cast<TSeg *>(sops + a.nops);
     Mat2<R> *scoef = reinterpret_cast<Mat2<R> *>(ssegs + a.nseg);
     const Mat2<R> *gcoef = reinterpret_cast<const Mat2<R> *>(a.coef);
-    for (int i = tid; i < a.nops; i += blockDim.x) {
-        sops[i] = a.ops[a.op0 + i];
-        scoef[i] = gcoef[sops[i].coef];
-    }
-    for (int i = tid; i < a.nseg; i += blockDim.x) ssegs[i] = a.segs[a.seg0 + i];
+    const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t1 = min(a.g.ntiles, t0 + per);
+    int c[5];
+    uint64_t base;
+    int64_t row;
+    // the first tile's copy overlaps the staging of the pass's ops
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_async_smem();
+        if (t0 < t1) {
+            geom_coords(a.g, t0, c, base, row);
+            mbar_expect_tx(&bar[0], (uint32_t)tbytes);
+            tma_load5(buf0, &tmap, c, &bar[0]);
+        }
     }
+    for (int i = tid; i < a.nops; i += blockDim.x) {
+        const TOp o = a.ops[a.op0 + i];
+        sops[i] = o;
+        scoef[i] = gcoef[o.coef];
+    }
+    for (int i = tid; i < a.nseg; i += blockDim.x) ssegs[i] = a.segs[a.seg0 + i];
     __syncthreads();
-    const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * per;
-    const int64_t t1 = min(a.g.ntiles, t0 + per);
     if (t0 >= t1) return;
-    int c[5];
-    uint64_t base;
-    int64_t row;
-    if (tid == 0) {
-        geom_coords(a.g, t0, c, base, row);
-        mbar_expect_tx(&bar[0], (uint32_t)tbytes);
-        tma_load5(buf0, &tmap, c, &bar[0]);
-    }
     uint32_t phase0 = 0, phase1 = 0;
     cx<R> r[1 << M];
     bool failed = false;
@@ -455,17 +457,48 @@ TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, 
 namespace {
 
 template <typename R>
-cudaError_t run_forward(TileCache &tc, const Plan &p, const TileSchedule &sc, const void *coef, void *state,
+cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const void *coef, void *state,
                         int batch, int nsm, cudaStream_t s, int64_t *launches) {
     const int M = sc.M;
     constexpr int wb = TileCfg<R>::wb;
     const int amp = (int)sizeof(cx<R>);
     const int threads = 1 << (sc.k - M);
-    for (const TPass &ps : sc.passes) {
+    const void *kfn = tile_kernel<R>(M);
+    if (sc.fwd_state != state || sc.fwd_batch != batch || sc.fwd_launch.size() != sc.passes.size()) {
+        // encode every pass once for this buffer
+        sc.fwd_launch.assign(sc.passes.size(), TileSchedule::Launch{});
+        sc.fwd_state = nullptr;
+        size_t smax = 0;
+        for (size_t i = 0; i < sc.passes.size(); ++i) {
+            const TPass &ps = sc.passes[i];
+            TileDims d;
+            if (!make_dims(ps.T, p.n, wb, d)) return cudaErrorInvalidValue;
+            TileSchedule::Launch &L = sc.fwd_launch[i];
+            if (!encode_map(tc.encode_fn, &L.map, d, state, batch, wb)) return cudaErrorInvalidValue;
+            L.smem = tile_smem_bytes(sc.k, amp, ps.nops, ps.nseg);
+            smax = std::max(smax, L.smem);
+        }
+        if (tc.smem_set[kfn] < smax) {
+            cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+            if (e != cudaSuccess) return e;
+            tc.smem_set[kfn] = smax;
+        }
+        for (size_t i = 0; i < sc.passes.size(); ++i) {
+            TileSchedule::Launch &L = sc.fwd_launch[i];
+            int per_sm = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, L.smem);
+            per_sm = std::max(1, per_sm);
+            const int64_t ntiles = (int64_t)batch << (p.n - sc.k);
+            L.grid = (int)std::min<int64_t>(ntiles, (int64_t)per_sm * nsm);
+        }
+        sc.fwd_state = state;
+        sc.fwd_batch = batch;
+    }
+    for (size_t i = 0; i < sc.passes.size(); ++i) {
+        const TPass &ps = sc.passes[i];
+        const TileSchedule::Launch &L = sc.fwd_launch[i];
         TileDims d;
         if (!make_dims(ps.T, p.n, wb, d)) return cudaErrorInvalidValue;
-        CUtensorMap map;
-        if (!encode_map(tc.encode_fn, &map, d, state, batch, wb)) return cudaErrorInvalidValue;
         TileKArgs a;
         a.ops = sc.d_ops;
         a.segs = sc.d_segs;
@@ -476,22 +509,14 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, const TileSchedule &sc, co
         a.coef = coef;
         a.g = make_geom(d, p.n, sc.k, wb, batch);
         a.errflag = tc.errflag;
-        const size_t smem = tile_smem_bytes(sc.k, amp, ps.nops, ps.nseg);
-        const void *kfn = tile_kernel<R>(M);
-        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem);
-        per_sm = std::max(1, per_sm);
-        const int64_t grid = std::min<int64_t>(a.g.ntiles, (int64_t)per_sm * nsm);
         LaunchScope ls(s, "k_tile_fwd", launches);
         switch (M) {
-        case 2: k_tile_fwd<R, 2><<<(unsigned)grid, threads, smem, s>>>(map, a); break;
-        case 3: k_tile_fwd<R, 3><<<(unsigned)grid, threads, smem, s>>>(map, a); break;
-        case 4: k_tile_fwd<R, 4><<<(unsigned)grid, threads, smem, s>>>(map, a); break;
-        default: k_tile_fwd<R, (TileCfg<R>::Mmax)><<<(unsigned)grid, threads, smem, s>>>(map, a); break;
+        case 2: k_tile_fwd<R, 2><<<(unsigned)L.grid, threads, L.smem, s>>>(L.map, a); break;
+        case 3: k_tile_fwd<R, 3><<<(unsigned)L.grid, threads, L.smem, s>>>(L.map, a); break;
+        case 4: k_tile_fwd<R, 4><<<(unsigned)L.grid, threads, L.smem, s>>>(L.map, a); break;
+        default: k_tile_fwd<R, (TileCfg<R>::Mmax)><<<(unsigned)L.grid, threads, L.smem, s>>>(L.map, a); break;
         }
-        e = cudaGetLastError();
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -354,21 +354,32 @@ __global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __gr
     double *acc = reinterpret_cast<double *>(scoef + a.nops);       // [nslot]
     R *accw = reinterpret_cast<R *>(acc + a.nslot);                  // [nw][nslot]
     const Mat2<R> *gcoef = reinterpret_cast<const Mat2<R> *>(a.coef);
+    const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t1 = min(a.g.ntiles, t0 + per);
+    // the first tile's copies overlap the staging of the pass's ops
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        fence_async_smem();
+        if (t0 < t1) {
+            int c[5];
+            uint64_t base;
+            int64_t row;
+            geom_coords(a.g, t0, c, base, row);
+            mbar_expect_tx(&bar[0], (uint32_t)(2 * tbytes));
+            tma_load5(bufP, &mp, c, &bar[0]);
+            tma_load5(bufL, &ml, c, &bar[0]);
+        }
+    }
     for (int i = tid; i < a.nops; i += blockDim.x) {
-        sops[i] = a.ops[i];
-        scoef[i] = gcoef[sops[i].coef];
+        const EOp o = a.ops[i];
+        sops[i] = o;
+        scoef[i] = gcoef[o.coef];
     }
     for (int i = tid; i < a.nseg; i += blockDim.x) ssegs[i] = a.segs[i];
     for (int i = tid; i < a.nslot; i += blockDim.x) acc[i] = 0.0;
     for (int i = tid; i < nw * a.nslot; i += blockDim.x) accw[i] = R(0);
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        fence_async_smem();
-    }
     __syncthreads();
-    const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * per;
-    const int64_t t1 = min(a.g.ntiles, t0 + per);
     uint32_t phase = 0;
     int64_t cur_row = -1;
     bool failed = false;
@@ -388,7 +399,7 @@ __global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __gr
             if (cur_row >= 0) flush(cur_row);
             cur_row = row;
         }
-        if (tid == 0) {
+        if (tid == 0 && t > t0) {
             mbar_expect_tx(&bar[0], (uint32_t)(2 * tbytes));
             tma_load5(bufP, &mp, c, &bar[0]);
             tma_load5(bufL, &ml, c, &bar[0]);
@@ -537,11 +548,15 @@ cudaError_t tile_observe(TileCache &tc, int n, const std::vector<DevTerm> &bits,
         a.errflag = tc.errflag;
         const size_t smem = 2 * (sizeof(cx<R>) << k) + 64 + ps.nt * sizeof(OTerm) + ps.nt * sizeof(double) +
                             (size_t)nw * ps.nt * sizeof(R) + 64;
-        cudaError_t e = cudaFuncSetAttribute(k_tile_obs<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        const void *ofn = (const void *)k_tile_obs<R>;
+        if (tc.smem_set[ofn] < smem) {
+            cudaError_t e = cudaFuncSetAttribute(ofn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            tc.smem_set[ofn] = smem;
+        }
         LaunchScope ls(s, "k_tile_obs", launches);
         k_tile_obs<R><<<grid, threads, smem, s>>>(mp, ml, a);
-        e = cudaGetLastError();
+        const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (out) return expect_finalize_nblk(part, d_bits, d_ptr, nobs, batch, grid, out, s, launches);
@@ -577,13 +592,30 @@ cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &
                 pstop = pi;
                 break;
             }
+    if (sc->adj_p != psi || sc->adj_l != lam || sc->adj_batch != batch ||
+        sc->adj_psi.size() != sc->passes.size()) {
+        // encode every pass once for these buffers
+        sc->adj_psi.assign(sc->passes.size(), CUtensorMap{});
+        sc->adj_lam.assign(sc->passes.size(), CUtensorMap{});
+        sc->adj_p = nullptr;
+        for (size_t pi = 0; pi < sc->passes.size(); ++pi) {
+            TileDims d;
+            if (!make_dims(sc->passes[pi].T, p.n, wb, d)) return cudaErrorInvalidValue;
+            if (!encode_map(tc.encode_fn, &sc->adj_psi[pi], d, psi, batch, wb) ||
+                !encode_map(tc.encode_fn, &sc->adj_lam[pi], d, lam, batch, wb))
+                return cudaErrorInvalidValue;
+        }
+        sc->adj_p = psi;
+        sc->adj_l = lam;
+        sc->adj_batch = batch;
+    }
+    const void *kfn = M == 3 ? (const void *)k_tile_adj<R, 3>
+                             : (M == 2 ? (const void *)k_tile_adj<R, 2> : (const void *)k_tile_adj<R, 4>);
     for (int pi = (int)sc->passes.size() - 1; pi >= pstop; --pi) {
         const TPass &ps = sc->passes[pi];
         TileDims d;
         if (!make_dims(ps.T, p.n, wb, d)) return cudaErrorInvalidValue;
-        CUtensorMap mp, ml;
-        if (!encode_map(tc.encode_fn, &mp, d, psi, batch, wb) || !encode_map(tc.encode_fn, &ml, d, lam, batch, wb))
-            return cudaErrorInvalidValue;
+        const CUtensorMap &mp = sc->adj_psi[pi], &ml = sc->adj_lam[pi];
         AdjArgs a;
         a.g = make_geom(d, p.n, k, wb, batch);
         a.ops = sc->d_rops + ps.op0;
@@ -600,10 +632,11 @@ cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &
         const size_t smem = 2 * (sizeof(cx<R>) << k) + 64 + (size_t)ps.nops * sizeof(EOp) +
                             (size_t)ps.nrseg * sizeof(ESeg) + (size_t)ps.nops * sizeof(Mat2<R>) +
                             (size_t)ps.nslot * sizeof(double) + (size_t)nw * ps.nslot * sizeof(R) + 64;
-        const void *kfn = M == 3 ? (const void *)k_tile_adj<R, 3>
-                                 : (M == 2 ? (const void *)k_tile_adj<R, 2> : (const void *)k_tile_adj<R, 4>);
-        e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        if (tc.smem_set[kfn] < smem) {
+            e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            tc.smem_set[kfn] = smem;
+        }
         LaunchScope ls(s, "k_tile_adj", launches);
         if (M == 3) k_tile_adj<R, 3><<<grid, threads, smem, s>>>(mp, ml, a);
         else if (M == 2) k_tile_adj<R, 2><<<grid, threads, smem, s>>>(mp, ml, a);
