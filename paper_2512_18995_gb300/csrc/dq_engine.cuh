@@ -224,6 +224,42 @@ inline void decode_with_fans(const std::vector<GOp> &g, int i0, int i1, const in
     }
 }
 
+// Rotation pairs.  An uncontrolled REAL op (RY, H) whose next op on the same
+// target is an uncontrolled DIAG op (RZ, Z, S) commutes that op up to itself
+// (the ops in between act on other qubits).  In the reverse sweep the two run
+// as one register sweep that un-applies both and forms both gradients.
+// pair_real_diag reorders `ops` so that every such partner directly follows
+// its head and returns the head flags; the reverse decoders then mark the
+// DIAG op (pad[1] = 1; it runs first there) when both ops share a register
+// layout and decode to matching handlers.
+inline std::vector<char> pair_real_diag(std::vector<GOp> &ops, int i0 = 0, int i1 = -1) {
+    if (i1 < 0) i1 = (int)ops.size();
+    std::vector<char> head(ops.size(), 0);
+    for (int i = i0; i < i1; ++i) {
+        const GOp a = ops[i];
+        if (a.cls != CLS_REAL || a.cg >= 0 || a.tl < 0) continue;
+        for (int j = i + 1; j < i1; ++j) {
+            const GOp &b = ops[j];
+            if (b.tg != a.tg && b.cg != a.tg) continue;
+            if (b.cls == CLS_DIAG && b.cg < 0 && b.tg == a.tg) {
+                const GOp moved = b;
+                for (int k = j; k > i + 1; --k) ops[k] = ops[k - 1];
+                ops[i + 1] = moved;
+                head[i] = 1;
+            }
+            break;
+        }
+    }
+    return head;
+}
+
+inline bool pair_handlers_match(const EOp &real, const EOp &diag) {
+    if (real.h >= H_REAL && real.h < H_REAL + 5) return diag.h == H_DIAG + (real.h - H_REAL);
+    if (real.h == H_LREAL) return diag.h == H_DUNI && diag.tmode == 1 && diag.targ == real.targ && diag.cmode == 0 &&
+                                  diag.cmc == ~0u;
+    return false;
+}
+
 struct Layout {
     uint32_t tb;     // this thread's local index with register bits zero
     uint32_t off[8]; // local offset of register bit i
@@ -640,6 +676,88 @@ __device__ __forceinline__ R eng_adjoint(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M
                                          uint64_t base, const Layout &L, int lane) {
     return o.slot >= 0 ? eng_adjoint_g<R, M, true>(ps, ls, o, ud, base, L, lane)
                        : eng_adjoint_g<R, M, false>(ps, ls, o, ud, base, L, lane);
+}
+
+// ---------------------------------------------------------------------------
+// rotation pairs in the reverse sweep (see pair_real_diag)
+// ---------------------------------------------------------------------------
+// Reverse: un-apply the DIAG op d (daggered matrix dd, generator by kind) and
+// then the REAL op r (daggered rr) on one pair sweep; gd / gr receive the
+// gradient partials 2 Im <lambda|G|psi> of each (taken after its own gate).
+template <typename R, int M, int P, bool GRAD>
+__device__ __forceinline__ void adj_pair_reg(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &dd,
+                                             const Mat2<R> &rr, int dkind, R &gd, R &gr) {
+    R w0, w1;
+    diag_weights<R>(dkind, w0, w1);
+#pragma unroll
+    for (int e0 = 0; e0 < (1 << M); ++e0) {
+        if (e0 & (1 << P)) continue;
+        const int e1 = e0 | (1 << P);
+        cx<R> p0 = ps[e0], p1 = ps[e1], l0 = ls[e0], l1 = ls[e1];
+        if (GRAD) gd += w0 * (l0.x * p0.y - l0.y * p0.x) + w1 * (l1.x * p1.y - l1.y * p1.x);
+        p0 = cmul(dd.m[0], p0);
+        p1 = cmul(dd.m[3], p1);
+        l0 = cmul(dd.m[0], l0);
+        l1 = cmul(dd.m[3], l1);
+        if (GRAD) gr += grad_cls<R, CLS_REAL>(l0, l1, p0, p1);
+        apply2<R, CLS_REAL>(rr, p0, p1);
+        apply2<R, CLS_REAL>(rr, l0, l1);
+        ps[e0] = p0;
+        ps[e1] = p1;
+        ls[e0] = l0;
+        ls[e1] = l1;
+    }
+}
+
+template <typename R, int M, bool GRAD>
+__device__ __forceinline__ void adj_pair_lane(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const Mat2<R> &dd,
+                                              const Mat2<R> &rr, int dkind, int j, int lane, R &gd, R &gr) {
+    R w0, w1;
+    diag_weights<R>(dkind, w0, w1);
+    const int m = 1 << j;
+    const bool hi = (lane >> j) & 1;
+    const cx<R> f = hi ? dd.m[3] : dd.m[0];
+    const R w = hi ? w1 : w0;
+    const R cs = hi ? rr.m[3].x : rr.m[0].x;
+    const R cp = hi ? rr.m[2].x : rr.m[1].x;
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) {
+        cx<R> p = ps[e], l = ls[e];
+        if (GRAD) gd += w * (l.x * p.y - l.y * p.x);
+        p = cmul(f, p);
+        l = cmul(f, l);
+        const cx<R> pp = shfl_xor_cx(p, m);
+        const cx<R> lp = shfl_xor_cx(l, m);
+        if (GRAD && !hi) gr += grad_cls<R, CLS_REAL>(l, lp, p, pp);
+        ps[e] = mk<R>(cs * p.x + cp * pp.x, cs * p.y + cp * pp.y);
+        ls[e] = mk<R>(cs * l.x + cp * lp.x, cs * l.y + cp * lp.y);
+    }
+}
+
+template <typename R, int M>
+__device__ __forceinline__ void eng_adjoint_pair(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const EOp &d,
+                                                 const Mat2<R> &dd, const EOp &r, const Mat2<R> &rr, int lane,
+                                                 R &gd, R &gr) {
+    gd = R(0);
+    gr = R(0);
+    const bool grad = d.slot >= 0 || r.slot >= 0;
+    if (r.h == H_LREAL) {
+        if (grad) adj_pair_lane<R, M, true>(ps, ls, dd, rr, d.kind, r.targ, lane, gd, gr);
+        else adj_pair_lane<R, M, false>(ps, ls, dd, rr, d.kind, r.targ, lane, gd, gr);
+        return;
+    }
+    switch (r.h - H_REAL) {
+#define DQ_CASE(P)                                                                                      \
+    case P:                                                                                             \
+        if (P < M) {                                                                                    \
+            if (grad) adj_pair_reg<R, M, (P < M ? P : 0), true>(ps, ls, dd, rr, d.kind, gd, gr);        \
+            else adj_pair_reg<R, M, (P < M ? P : 0), false>(ps, ls, dd, rr, d.kind, gd, gr);            \
+        }                                                                                               \
+        break;
+        DQ_ENG_P(DQ_CASE)
+#undef DQ_CASE
+    default: break;
+    }
 }
 
 // FP32 (or FP64) warp sum.

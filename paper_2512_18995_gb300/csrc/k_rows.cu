@@ -134,6 +134,7 @@ bool rows_build_program(const Plan &p, int M, RowProgram &out) {
             push(g.cls, g.t, g.c, acc_of(g));
         }
     }
+    const std::vector<char> head = pair_real_diag(ops);
     std::vector<int> fwd(ops.size()), rev(ops.size());
     for (size_t i = 0; i < ops.size(); ++i) {
         fwd[i] = (int)i;
@@ -141,6 +142,15 @@ bool rows_build_program(const Plan &p, int M, RowProgram &out) {
     }
     build_segments(ops, fwd, M, n, out.fsegs, out.fops);
     build_segments(ops, rev, M, n, out.rsegs, out.rops);
+    // rotation pairs whose two ops share a reverse layout run as one op there
+    // (forward, the folded product costs as much as the two ops)
+    std::vector<int> rseg(ops.size(), -1);
+    for (size_t s = 0; s < out.rsegs.size(); ++s)
+        for (int i = out.rsegs[s].op0; i > out.rsegs[s].op0 - out.rsegs[s].nops; --i) rseg[i] = (int)s;
+    for (size_t i = 0; i + 1 < ops.size(); ++i) {
+        if (!head[i]) continue;
+        if (rseg[i] == rseg[i + 1] && pair_handlers_match(out.rops[i], out.rops[i + 1])) out.rops[i + 1].pad[1] = 1;
+    }
     return true;
 }
 
@@ -320,6 +330,22 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>(), sizeof(R) == 4 ? 2 :
                 const int oi = sg.op0 - c;
                 const EOp o = srops[oi];
                 const Mat2<R> u = o.rowstep ? gcoef[o.coef + (int64_t)row * o.rowstep] : scoef[oi];
+                if (o.pad[1]) {   // rotation pair: this DIAG op, then the REAL op before it
+                    const EOp o2 = srops[oi - 1];
+                    const Mat2<R> u2 = o2.rowstep ? gcoef[o2.coef + (int64_t)row * o2.rowstep] : scoef[oi - 1];
+                    R gd, gr;
+                    eng_adjoint_pair<R, M>(ps, ls, o, dagger(u), o2, dagger(u2), lane, gd, gr);
+                    if (o.slot >= 0) {
+                        const R gs = warp_sum_t(gd);
+                        if (lane == 0) accw[warp * nacc + o.slot] += gs;
+                    }
+                    if (o2.slot >= 0) {
+                        const R gs = warp_sum_t(gr);
+                        if (lane == 0) accw[warp * nacc + o2.slot] += gs;
+                    }
+                    ++c;
+                    continue;
+                }
                 const R g = eng_adjoint<R, M>(ps, ls, o, dagger(u), 0, L, lane);
                 if (o.slot >= 0) {
                     // this row's partial over the warp's amplitude pairs

@@ -180,6 +180,7 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
             }
         }
         pass.nops = (int)gops.size();
+        const std::vector<char> head = pair_real_diag(gops);
         // register layouts, then decode every op against its layout
         pass.seg0 = (int)out.segs.size();
         std::vector<int> B;
@@ -209,6 +210,7 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
         }
         close_seg(pass.nops);
         pass.nseg = (int)out.segs.size() - pass.seg0;
+
         if (adjoint) {
             // local gradient slots of the pass
             pass.slot0 = (int)out.slots.size();
@@ -258,6 +260,14 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
             }
             close_r(-1);
             pass.nrseg = (int)out.rsegs.size() - pass.rseg0;
+            std::vector<int> rseg(gops.size(), -1);
+            for (int sgi = pass.rseg0; sgi < pass.rseg0 + pass.nrseg; ++sgi)
+                for (int i = out.rsegs[sgi].op0; i > out.rsegs[sgi].op0 - out.rsegs[sgi].nops; --i)
+                    rseg[i - pass.op0] = sgi;
+            for (int i = 0; i + 1 < pass.nops; ++i)
+                if (head[i] && rseg[i] == rseg[i + 1] &&
+                    pair_handlers_match(out.rops[pass.op0 + i], out.rops[pass.op0 + i + 1]))
+                    out.rops[pass.op0 + i + 1].pad[1] = 1;
         }
         out.passes.push_back(pass);
         remaining.swap(deferred);

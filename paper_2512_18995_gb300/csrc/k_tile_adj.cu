@@ -419,6 +419,22 @@ __global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __gr
                 const int oi = sg.op0 - a.op0 - cc;
                 const EOp o = sops[oi];
                 const Mat2<R> u = o.rowstep ? gcoef[o.coef + row * o.rowstep] : scoef[oi];
+                if (o.pad[1]) {   // rotation pair: this DIAG op, then the REAL op before it
+                    const EOp o2 = sops[oi - 1];
+                    const Mat2<R> u2 = o2.rowstep ? gcoef[o2.coef + row * o2.rowstep] : scoef[oi - 1];
+                    R gd, gr;
+                    eng_adjoint_pair<R, M>(ps, ls, o, dagger(u), o2, dagger(u2), lane, gd, gr);
+                    if (o.slot >= 0) {
+                        const R gs = warp_sum_t(gd);
+                        if (lane == 0) accw[warp * a.nslot + o.slot] += gs;
+                    }
+                    if (o2.slot >= 0) {
+                        const R gs = warp_sum_t(gr);
+                        if (lane == 0) accw[warp * a.nslot + o2.slot] += gs;
+                    }
+                    ++cc;
+                    continue;
+                }
                 const R gv = eng_adjoint<R, M>(ps, ls, o, dagger(u), base, L, lane);
                 if (o.slot >= 0) {
                     const R gs = warp_sum_t(gv);
