@@ -151,6 +151,21 @@ def oracle_rate(wl, budget_s, max_steps=None):
     return rate, steps, dt, oracle.num_threads()
 
 
+def max_over_ranks(ms, world, dist, device):
+    """The job's time: the slowest replica's (all ranks receive it)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, bytes_step, steps, ms):
+    """Whole-job gate-equivalent GB/s: every replica moves bytes_step per step."""
+    return world * bytes_step * steps / (ms / 1e3) / 1e9
+
+
 def reference_arm(args, rank, world):
     """The oracle on the host cores, as the reference arm."""
     if rank != 0:
@@ -242,13 +257,9 @@ def our_arm(args, rank, world, dist):
             ends[i].record()
         barrier()
     launches = ctx.launch_count - launches0
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, dist, device)
     bytes_step = gate_pass_bytes(n, wl.gates)
-    value = world * bytes_step * args.steps / (ms / 1e3) / 1e9
+    value = job_value(world, bytes_step, args.steps, ms)
     clocks = clk.summary()
 
     # per-kernel device time (a traced repetition of the same timed steps)
