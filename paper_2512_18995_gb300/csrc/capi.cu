@@ -752,7 +752,18 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     void *tws = tile ? w.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>))) : nullptr;
     DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
     DQ_CUDA(plain_init_zero<R>(psi, p.n, batch, s, &ctx->launches), "init");
-    if (tile) {
+    bool done_obs = false, done_grad = false;
+    if (tile && o && eo && !grad) {
+        // diagonal observables measured by the last forward pass itself
+        cudaError_t e = tile_apply_expect<R>(ctx->tiles, ctx->tuned, p, coef, psi, batch, o->bits, o->d_bits,
+                                             o->d_ptr, o->nobs, epart, eo, ctx->nsm, s, &ctx->launches);
+        if (e == cudaSuccess) done_obs = true;
+        else if (e != cudaErrorNotSupported) DQ_CUDA(e, "tiled apply with expectations");
+        else cudaGetLastError();
+    }
+    if (done_obs) {
+        // evolution and expectations done
+    } else if (tile) {
         cudaError_t e = tile_apply<R>(ctx->tiles, ctx->tuned, p, coef, psi, batch, tws, ctx->nsm, s, &ctx->launches);
         if (e == cudaErrorNotSupported) {   // no schedule for this shape: per-gate sweeps
             cudaGetLastError();
@@ -762,8 +773,7 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     } else {
         DQ_CUDA(plain_apply<R>(p, coef, psi, batch, 0, s, &ctx->launches), "plain apply");
     }
-    bool done_obs = false, done_grad = false;
-    if (tile && o && (eo || grad)) {
+    if (tile && o && (eo || grad) && !done_obs) {
         // expectations and lambda in one set of observable passes
         cudaError_t e = tile_observe<R>(ctx->tiles, p.n, o->bits, o->d_bits, o->d_ptr, o->nobs, rw, psi,
                                         grad ? lam : nullptr, batch, epart, eo, ctx->nsm, s, &ctx->launches);

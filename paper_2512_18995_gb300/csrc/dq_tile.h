@@ -109,6 +109,15 @@ template <typename R>
 cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
                          const void *coef, void *psi, void *lam, int batch, double *part, double *gp, double *gd,
                          int nsm, cudaStream_t s, int64_t *launches);
+// Forward passes with the diagonal observables (Z strings only) measured on
+// the last pass's tiles, then the FP64 finalisation into out[row][obs].
+// part: [term][row][cta] workspace of tile_expect_part_bytes.  Returns
+// cudaErrorNotSupported when a term is not diagonal.
+template <typename R>
+cudaError_t tile_apply_expect(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
+                              const void *coef, void *state, int batch, const std::vector<DevTerm> &bits,
+                              const DevTerm *d_bits, const int32_t *d_ptr, int nobs, double *part, double *out,
+                              int nsm, cudaStream_t s, int64_t *launches);
 template <typename R>
 cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
                           const void *coef, void *state, int batch, void *tws, int nsm, cudaStream_t s,

@@ -254,12 +254,22 @@ __global__ void k_expect_finalize(const double *__restrict__ part, const DevTerm
     __shared__ double red[kThreads / 32];
     const int row = blockIdx.x / nobs, o = blockIdx.x % nobs;
     const int k0 = obs_ptr[o], k1 = obs_ptr[o + 1];
-    double acc = 0.0;
-    for (int k = k0; k < k1; ++k) {
-        const double c = terms[k].coeff;
-        const double *pk = part + ((int64_t)k * nbatch + row) * nblk;
-        for (int blk = threadIdx.x; blk < nblk; blk += kThreads) acc += c * pk[blk];
+    // (term, block) items, four independent loads in flight per thread
+    const int cnt = (k1 - k0) * nblk;
+    auto item = [&](int i) {
+        const int k = k0 + i / nblk, blk = i - (k - k0) * nblk;
+        return terms[k].coeff * part[((int64_t)k * nbatch + row) * nblk + blk];
+    };
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int i = threadIdx.x;
+    for (; i + 3 * kThreads < cnt; i += 4 * kThreads) {
+        a0 += item(i);
+        a1 += item(i + kThreads);
+        a2 += item(i + 2 * kThreads);
+        a3 += item(i + 3 * kThreads);
     }
+    for (; i < cnt; i += kThreads) a0 += item(i);
+    const double acc = (a0 + a1) + (a2 + a3);
     const double s = block_sum<kThreads>(acc, red);
     if (threadIdx.x == 0) out[(int64_t)row * nobs + o] = s;
 }

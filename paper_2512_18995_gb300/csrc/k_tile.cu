@@ -277,6 +277,16 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
 
 namespace {
 
+// Diagonal observables measured on the last pass's tiles (Z strings): the
+// pass's tile bits map each term's sign mask to tile-local and block parts.
+struct TileEpi {
+    const DevTerm *terms;   // device, all terms diagonal
+    int nterms;
+    double *part;           // [term][row][cta]
+    int batch;
+    int8_t T[16];           // tile bit -> amplitude bit
+};
+
 struct TileKArgs {
     const TOp *ops;
     const TSeg *segs;
@@ -284,6 +294,13 @@ struct TileKArgs {
     const void *coef;
     TileGeom g;
     int *errflag;
+    TileEpi epi;            // epi.nterms == 0: none
+};
+
+struct ETerm {
+    uint32_t sloc;
+    uint32_t pad;
+    uint64_t sout;
 };
 
 // Threads per CTA are 2^(k - M); wide register sets (256 bytes of amplitudes
@@ -307,6 +324,10 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
     TOp *sops = reinterpret_cast<TOp *>(smem + 2 * tbytes + 64);
     TSeg *ssegs = reinterpret_cast<TSeg *>(sops + a.nops);
     Mat2<R> *scoef = reinterpret_cast<Mat2<R> *>(ssegs + a.nseg);
+    const int nte = a.epi.nterms, nw = blockDim.x >> 5;
+    ETerm *sterm = reinterpret_cast<ETerm *>(scoef + a.nops);     // [nte]
+    double *eacc = reinterpret_cast<double *>(sterm + nte);         // [nte]
+    R *eaccw = reinterpret_cast<R *>(eacc + nte);                   // [nw][nte]
     const Mat2<R> *gcoef = reinterpret_cast<const Mat2<R> *>(a.coef);
     const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * per;
@@ -331,8 +352,29 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
         scoef[i] = gcoef[o.coef];
     }
     for (int i = tid; i < a.nseg; i += blockDim.x) ssegs[i] = a.segs[a.seg0 + i];
+    for (int j = tid; j < nte; j += blockDim.x) {
+        const uint64_t sm = a.epi.terms[j].s;
+        ETerm e{};
+        uint64_t in = 0;
+        for (int i = 0; i < a.g.k; ++i)
+            if ((sm >> a.epi.T[i]) & 1) {
+                e.sloc |= 1u << i;
+                in |= uint64_t(1) << a.epi.T[i];
+            }
+        e.sout = sm & ~in;
+        sterm[j] = e;
+        eacc[j] = 0.0;
+    }
+    for (int i = tid; i < nw * nte; i += blockDim.x) eaccw[i] = R(0);
     __syncthreads();
     if (t0 >= t1) return;
+    int64_t erow = -1;
+    auto eflush = [&](int64_t rr) {
+        for (int j = tid; j < nte; j += blockDim.x) {
+            a.epi.part[((int64_t)j * a.epi.batch + rr) * gridDim.x + blockIdx.x] = eacc[j];
+            eacc[j] = 0.0;
+        }
+    };
     uint32_t phase0 = 0, phase1 = 0;
     cx<R> r[1 << M];
     bool failed = false;
@@ -380,6 +422,39 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
             tma_store5(&tmap, c, cur);
             bulk_commit();
         }
+        if (nte) {
+            // diagonal observables of the final tile (read-only, beside the store)
+            if (row != erow) {
+                if (erow >= 0) eflush(erow);
+                erow = row;
+            }
+            const int dim = 1 << a.g.k;
+            for (int j = 0; j < nte; ++j) {
+                const ETerm et = sterm[j];
+                const int bpar = __popcll(base & et.sout) & 1;
+                R e = R(0);
+                for (int l = tid; l < dim; l += blockDim.x) {
+                    const cx<R> x = cur[l];
+                    const R pr = x.x * x.x + x.y * x.y;
+                    e += ((__popc((uint32_t)l & et.sloc) & 1) ^ bpar) ? -pr : pr;
+                }
+                e = warp_sum_t(e);
+                if (lane == 0) eaccw[warp * nte + j] += e;
+            }
+            __syncthreads();
+            for (int j = tid; j < nte; j += blockDim.x) {
+                double sum = 0.0;
+                for (int ww = 0; ww < nw; ++ww) {
+                    sum += (double)eaccw[ww * nte + j];
+                    eaccw[ww * nte + j] = R(0);
+                }
+                eacc[j] += sum;
+            }
+        }
+    }
+    if (nte && !failed && erow >= 0) {
+        __syncthreads();
+        eflush(erow);
     }
     if (failed && tid == 0) {
         atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
@@ -390,9 +465,10 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
     if (tid == 0) bulk_wait0();
 }
 
-size_t tile_smem_bytes(int k, int amp, int nops, int nseg) {
+size_t tile_smem_bytes(int k, int amp, int nops, int nseg, int nterms = 0, int threads = 0) {
     return 2 * ((size_t)amp << k) + 64 + (size_t)nops * sizeof(TOp) + (size_t)nseg * sizeof(TSeg) +
-           (size_t)nops * (amp == 8 ? sizeof(Mat2<float>) : sizeof(Mat2<double>)) + 64;
+           (size_t)nops * (amp == 8 ? sizeof(Mat2<float>) : sizeof(Mat2<double>)) +
+           (size_t)nterms * (sizeof(ETerm) + sizeof(double) + (size_t)(threads / 32) * (amp == 8 ? 4 : 8)) + 64;
 }
 
 uint64_t sched_key(const Plan &p, int k, int low, int amp, int M, bool adjoint = false, int g0 = 0) {
@@ -468,7 +544,8 @@ namespace {
 
 template <typename R>
 cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const void *coef, void *state,
-                        int batch, int nsm, cudaStream_t s, int64_t *launches) {
+                        int batch, int nsm, cudaStream_t s, int64_t *launches, const TileEpi *epi = nullptr,
+                        int *epi_grid = nullptr) {
     const int M = sc.M;
     constexpr int wb = TileCfg<R>::wb;
     const int amp = (int)sizeof(cx<R>);
@@ -510,6 +587,22 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
         TileDims d;
         if (!make_dims(ps.T, p.n, wb, d)) return cudaErrorInvalidValue;
         TileKArgs a;
+        a.epi = TileEpi{};
+        size_t smem = L.smem;
+        int grid = L.grid;
+        if (epi && i + 1 == sc.passes.size()) {
+            // the last pass also measures the diagonal observables
+            a.epi = *epi;
+            for (int j = 0; j < 16; ++j) a.epi.T[j] = (int8_t)(j < (int)ps.T.size() ? ps.T[j] : 0);
+            smem = tile_smem_bytes(sc.k, amp, ps.nops, ps.nseg, epi->nterms, threads);
+            if (tc.smem_set[kfn] < smem) {
+                cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                tc.smem_set[kfn] = smem;
+            }
+            grid = std::min(grid, 4 * nsm);   // the partials hold at most 4 CTAs per SM
+            if (epi_grid) *epi_grid = grid;
+        }
         a.ops = sc.d_ops;
         a.segs = sc.d_segs;
         a.op0 = ps.op0;
@@ -521,10 +614,10 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
         a.errflag = tc.errflag;
         LaunchScope ls(s, "k_tile_fwd", launches);
         switch (M) {
-        case 2: k_tile_fwd<R, 2><<<(unsigned)L.grid, threads, L.smem, s>>>(L.map, a); break;
-        case 3: k_tile_fwd<R, 3><<<(unsigned)L.grid, threads, L.smem, s>>>(L.map, a); break;
-        case 4: k_tile_fwd<R, 4><<<(unsigned)L.grid, threads, L.smem, s>>>(L.map, a); break;
-        default: k_tile_fwd<R, (TileCfg<R>::Mmax)><<<(unsigned)L.grid, threads, L.smem, s>>>(L.map, a); break;
+        case 2: k_tile_fwd<R, 2><<<(unsigned)grid, threads, smem, s>>>(L.map, a); break;
+        case 3: k_tile_fwd<R, 3><<<(unsigned)grid, threads, smem, s>>>(L.map, a); break;
+        case 4: k_tile_fwd<R, 4><<<(unsigned)grid, threads, smem, s>>>(L.map, a); break;
+        default: k_tile_fwd<R, (TileCfg<R>::Mmax)><<<(unsigned)grid, threads, smem, s>>>(L.map, a); break;
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -557,6 +650,40 @@ cudaError_t tile_apply(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tu
     TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), false);
     if (!sc) return cudaErrorNotSupported;
     return run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches);
+}
+
+template <typename R>
+cudaError_t tile_apply_expect(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
+                              const void *coef, void *state, int batch, const std::vector<DevTerm> &bits,
+                              const DevTerm *d_bits, const int32_t *d_ptr, int nobs, double *part, double *out,
+                              int nsm, cudaStream_t s, int64_t *launches) {
+    if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
+    for (const DevTerm &t : bits)
+        if (t.f != 0 || t.nY != 0) return cudaErrorNotSupported;   // diagonal terms only
+    if (bits.empty() || bits.size() > 64) return cudaErrorNotSupported;
+    int k, low, M;
+    default_tile<R>(p.n, k, low, M);
+    auto it = tuned.find(p.key ^ (sizeof(R) == 8 ? 1ull : 0ull));
+    if (it != tuned.end() && it->second.k) {
+        k = it->second.k;
+        low = it->second.low;
+        M = it->second.M;
+    }
+    TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), false);
+    if (!sc || sc->passes.empty()) return cudaErrorNotSupported;
+    const int nsm4 = 4 * nsm;
+    cudaError_t e = cudaMemsetAsync(part, 0, sizeof(double) * bits.size() * (size_t)batch * nsm4, s);
+    if (e != cudaSuccess) return e;
+    TileEpi epi{};
+    epi.terms = d_bits;
+    epi.nterms = (int)bits.size();
+    epi.part = part;
+    epi.batch = batch;
+    int grid = 0;
+    e = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches, &epi, &grid);
+    if (e != cudaSuccess) return e;
+    if (grid < 1 || grid > nsm4) return cudaErrorInvalidValue;
+    return expect_finalize_nblk(part, d_bits, d_ptr, nobs, batch, grid, out, s, launches);
 }
 
 template <typename R>
@@ -610,7 +737,11 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
     template cudaError_t tile_apply<R>(TileCache &, std::unordered_map<uint64_t, TileTune> &, const Plan &,   \
                                        const void *, void *, int, void *, int, cudaStream_t, int64_t *);     \
     template cudaError_t tile_autotune<R>(TileCache &, std::unordered_map<uint64_t, TileTune> &, const Plan &, \
-                                          const void *, void *, int, void *, int, cudaStream_t, int64_t *);
+                                          const void *, void *, int, void *, int, cudaStream_t, int64_t *);      \
+    template cudaError_t tile_apply_expect<R>(TileCache &, std::unordered_map<uint64_t, TileTune> &,             \
+                                              const Plan &, const void *, void *, int,                         \
+                                              const std::vector<DevTerm> &, const DevTerm *, const int32_t *,  \
+                                              int, double *, double *, int, cudaStream_t, int64_t *);
 DQ_INST(float)
 DQ_INST(double)
 #undef DQ_INST

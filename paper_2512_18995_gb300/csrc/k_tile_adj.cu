@@ -494,7 +494,9 @@ size_t tile_adjoint_part_bytes(const Plan &p, int batch, int nsm) {
 
 size_t tile_expect_part_bytes(int n, int nterms, int batch, int nsm) {
     (void)n;
-    return (size_t)std::max(1, nterms) * (size_t)std::max(1, batch) * (size_t)(2 * nsm) * sizeof(double);
+    // [term][row][cta]: observable passes use up to 2 CTAs per SM, the forward
+    // epilogue (diagonal observables) up to 4
+    return (size_t)std::max(1, nterms) * (size_t)std::max(1, batch) * (size_t)(4 * nsm) * sizeof(double);
 }
 
 template <typename R>

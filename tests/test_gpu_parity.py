@@ -239,6 +239,31 @@ def test_qft_controlled_phase_fans(ctx, dtype, n, batch):
     assert_amps(np_state(st), ref, dt, "QFT state")
 
 
+@pytest.mark.parametrize("dtype", sorted(DTYPES))
+@pytest.mark.parametrize("n,batch", [(17, 3), (20, 1)])
+def test_diagonal_observables_in_last_forward_pass(ctx, dtype, n, batch):
+    """Z-string observables measured by the last tiled forward pass (no
+    separate observable pass), several observables and rows; a set with an
+    X term takes the observable passes instead and must agree too."""
+    ctx.set_path(dq.PATH_FUSED)
+    dt = DTYPES[dtype]
+    rng = np.random.default_rng(60 + n)
+    gates = W.encode_layer(n) + W.hea_layers(n, 2)
+    npar = 4 * n
+    params = rng.uniform(0, 2 * math.pi, size=npar)
+    data = rng.uniform(-math.pi, math.pi, size=(batch, n))
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=n)
+    diag = [W.obs_sum_z(n), W.obs_z(0), [W.pauli_term(0.7, {1: "Z", n - 1: "Z"}), W.pauli_term(-0.2, {3: "Z"})]]
+    mixed = diag + [W.obs_zz01_x0()]
+    for obs in (diag, mixed):
+        ref = oracle.expect(n, oracle.run(n, gates, params, data, batch=batch), obs)
+        e, _, _, _ = ctx.forward_grad(circ, dev(params), dq.Observables(obs), batch, dt, data=dev(data),
+                                      want_grad=False)
+        torch.cuda.synchronize()
+        ctx.check()
+        assert_rel(e.cpu().numpy(), ref, dt, "expectations", floor=obs_scale(obs))
+
+
 @pytest.mark.parametrize("path", sorted(PATHS))
 @pytest.mark.parametrize("n,batch", [(7, 3), (13, 2), (18, 1)])
 def test_gradient_free_prefix(ctx, path, n, batch):
