@@ -179,14 +179,18 @@ DQ_API int64_t dq_ctx_launch_count(const dq_ctx *ctx);
  * and that call and later identical ones launch the graph on the caller's
  * stream instead of issuing the kernels one by one.  Values behind the
  * pointers (parameters, data) are read when the graph runs, so they may change
- * between calls; pointers and shapes may not.  Capture is skipped while
- * tracing is on.  Off by default. */
+ * between calls; pointers and shapes may not.  With tracing on, calls use
+ * their own traced graphs (see dq_ctx_set_tracing).  Off by default. */
 DQ_API dq_status dq_ctx_set_graphs(dq_ctx *ctx, int on);
 
 /* Tracing (the library's profiling hook).  With tracing on, every kernel the
  * context launches is bracketed by a CUDA event pair on its stream and the
- * device time is aggregated per kernel name.  Turning tracing on or off
- * clears the records.  dq_ctx_trace_count synchronises the device, then
+ * device time is aggregated per kernel name.  With graph replay on, the
+ * event pairs are captured into the graph as event-record nodes, and every
+ * replay of a traced graph synchronises the caller's stream and adds the
+ * graph's per-kernel times (device time inside the graph, no host launch
+ * gaps).  Turning tracing on or off clears the records and the captured
+ * graphs.  dq_ctx_trace_count synchronises the device, then
  * returns the number of distinct kernel names recorded (or -1 on error);
  * dq_ctx_trace_get copies entry i's name (NUL-terminated, truncated to
  * name_len) and writes its launch count and total device milliseconds. */

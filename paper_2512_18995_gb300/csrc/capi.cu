@@ -107,11 +107,18 @@ struct dq_ctx {
     struct GraphEntry {
         cudaGraphExec_t exec;
         int64_t kernels;
+        std::vector<Tracer::Rec> trace;   // event records captured with tracing on
     };
     std::unordered_map<uint64_t, GraphEntry> graphs;
     std::unordered_map<uint64_t, int> graph_seen;
     void clear_graphs() {
-        for (auto &kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+        for (auto &kv : graphs) {
+            cudaGraphExecDestroy(kv.second.exec);
+            for (auto &r : kv.second.trace) {
+                cudaEventDestroy(r.a);
+                cudaEventDestroy(r.b);
+            }
+        }
         graphs.clear();
         graph_seen.clear();
     }
@@ -469,12 +476,27 @@ RowProgram *get_rows(dq_ctx *ctx, const Plan &p, int amp, bool grad, int nobs) {
 
 // Run `body(stream)` through the context's graph cache.  Returns true when the
 // call was served by a graph (captured now or earlier); *st is its status.
+// With tracing on, a replay is followed by a synchronisation and the
+// graph's own event records are added to the tracer (per-kernel device time
+// inside the graph, without host launch gaps).
+void graph_trace(dq_ctx *ctx, const dq_ctx::GraphEntry &g, cudaStream_t s) {
+    if (g.trace.empty() || cudaStreamSynchronize(s) != cudaSuccess) return;
+    for (const auto &r : g.trace) {
+        float ms = 0.f;
+        if (r.name < (int)ctx->tracer.acc.size() && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            ctx->tracer.acc[r.name].first += 1;
+            ctx->tracer.acc[r.name].second += ms;
+        }
+    }
+}
+
 template <typename F>
 bool graph_run(dq_ctx *ctx, uint64_t key, cudaStream_t s, F body, dq_status *st) {
-    if (!ctx->graphs_on || ctx->tracer.on) return false;
+    if (!ctx->graphs_on) return false;
     key ^= (uint64_t)(uintptr_t)ctx->ws * 0x9E3779B97F4A7C15ull;
     key ^= (uint64_t)ctx->ws_bytes * 0xC2B2AE3D27D4EB4Full;
     key ^= (uint64_t)ctx->path * 0x165667B19E3779F9ull;
+    if (ctx->tracer.on) key ^= 0x7A3C5E0F1B2D4C6Bull;
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
         cudaError_t e = cudaGraphLaunch(it->second.exec, s);
@@ -483,6 +505,7 @@ bool graph_run(dq_ctx *ctx, uint64_t key, cudaStream_t s, F body, dq_status *st)
             return true;
         }
         ctx->launches += it->second.kernels;
+        if (ctx->tracer.on) graph_trace(ctx, it->second, s);
         *st = DQ_OK;
         return true;
     }
@@ -493,6 +516,7 @@ bool graph_run(dq_ctx *ctx, uint64_t key, cudaStream_t s, F body, dq_status *st)
         return false;
     }
     const int64_t before = ctx->launches;
+    const size_t r0 = ctx->tracer.recs.size();
     if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -502,20 +526,29 @@ bool graph_run(dq_ctx *ctx, uint64_t key, cudaStream_t s, F body, dq_status *st)
     const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
     const int64_t kernels = ctx->launches - before;
     ctx->launches = before;
+    // the event records of the capture belong to the graph
+    std::vector<Tracer::Rec> trace(ctx->tracer.recs.begin() + (std::ptrdiff_t)r0, ctx->tracer.recs.end());
+    ctx->tracer.recs.resize(r0);
     cudaGraphExec_t exec = nullptr;
     if (bst != DQ_OK || ce != cudaSuccess || !g || cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
+        for (auto &r : trace) {
+            ctx->tracer.pool.push_back(r.a);
+            ctx->tracer.pool.push_back(r.b);
+        }
         cudaGetLastError();
         ctx->err.clear();
         return false;   // run normally instead
     }
     cudaGraphDestroy(g);
-    ctx->graphs[key] = {exec, kernels};
+    auto &entry = ctx->graphs[key];
+    entry = {exec, kernels, std::move(trace)};
     cudaError_t e = cudaGraphLaunch(exec, s);
     if (e != cudaSuccess) {
         *st = cuda_fail(ctx, e, "cudaGraphLaunch");
         return true;
     }
+    if (ctx->tracer.on) graph_trace(ctx, entry, s);
     ctx->launches += kernels;
     *st = DQ_OK;
     return true;
@@ -900,7 +933,9 @@ dq_status dq_ctx_set_tracing(dq_ctx *ctx, int on) {
     }
     ctx->tracer.recs.clear();
     ctx->tracer.names.clear();
+    ctx->tracer.acc.clear();
     ctx->trace_table.clear();
+    ctx->clear_graphs();   // traced graphs refer to the cleared names
     ctx->tracer.on = on != 0;
     return DQ_OK;
 }
@@ -909,6 +944,7 @@ int dq_ctx_trace_count(dq_ctx *ctx) {
     if (check_ctx(ctx) != DQ_OK) return -1;
     if (cudaDeviceSynchronize() != cudaSuccess) return -1;
     std::vector<std::pair<int64_t, double>> agg(ctx->tracer.names.size(), {0, 0.0});
+    for (size_t i = 0; i < agg.size() && i < ctx->tracer.acc.size(); ++i) agg[i] = ctx->tracer.acc[i];
     for (auto &r : ctx->tracer.recs) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {

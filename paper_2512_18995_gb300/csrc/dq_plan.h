@@ -103,6 +103,8 @@ struct Tracer {
     struct Rec { int name; cudaEvent_t a, b; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
+    // launches and milliseconds per name accumulated from replayed CUDA graphs
+    std::vector<std::pair<int64_t, double>> acc;
     cudaEvent_t get_event();
     int name_id(const char *n);
     void release();

@@ -22,6 +22,7 @@ int Tracer::name_id(const char *n) {
     for (size_t i = 0; i < names.size(); ++i)
         if (names[i] == n) return (int)i;
     names.emplace_back(n);
+    acc.emplace_back(0, 0.0);
     return (int)names.size() - 1;
 }
 
@@ -34,6 +35,17 @@ void Tracer::release() {
     recs.clear();
     pool.clear();
     names.clear();
+    acc.clear();
+}
+
+// Inside a stream capture the event records become nodes of the graph
+// (recorded at every replay); outside they are ordinary stream records.
+static void record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
 }
 
 LaunchScope::LaunchScope(cudaStream_t st, const char *name, int64_t *c) : s(st), counter(c) {
@@ -43,7 +55,7 @@ LaunchScope::LaunchScope(cudaStream_t st, const char *name, int64_t *c) : s(st),
         r.name = t->name_id(name);
         r.a = t->get_event();
         r.b = t->get_event();
-        cudaEventRecord(r.a, s);
+        record(r.a, s);
         t->recs.push_back(r);
         rec = (int)t->recs.size() - 1;
     }
@@ -52,7 +64,7 @@ LaunchScope::LaunchScope(cudaStream_t st, const char *name, int64_t *c) : s(st),
 LaunchScope::~LaunchScope() {
     if (counter) ++*counter;
     Tracer *t = g_tracer;
-    if (rec >= 0 && t) cudaEventRecord(t->recs[rec].b, s);
+    if (rec >= 0 && t) record(t->recs[rec].b, s);
 }
 
 }  // namespace dq

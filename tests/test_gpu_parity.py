@@ -544,3 +544,39 @@ def test_graph_replay_reads_current_values(ctx, n, batch, path):
             assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, f"call {call} grad data", floor=fl)
     finally:
         ctx.set_graphs(False)
+
+
+def test_tracing_inside_replayed_graphs(ctx):
+    """With graph replay and tracing both on, every call's kernels are
+    counted once (first call issued directly, later ones from the traced
+    graph) with positive device times, and results stay exact."""
+    ctx.set_path(dq.PATH_FUSED)
+    n = 18
+    rng = np.random.default_rng(18)
+    gates = W.hea_layers(n, 2)
+    params = rng.uniform(0, 2 * math.pi, size=4 * n)
+    obs = [W.obs_sum_z(n)]
+    circ = dq.Circuit(n, gates, nparams=4 * n)
+    o = dq.Observables(obs)
+    p = dev(params)
+    e = torch.empty((1, 1), dtype=torch.float64, device="cuda")
+    st = torch.empty((1, 1 << n), dtype=torch.complex64, device="cuda")
+    ref = oracle.expect(n, oracle.run(n, gates, params), obs)
+    ctx.set_graphs(True)
+    try:
+        ctx.forward_grad(circ, p, o, 1, torch.complex64, want_grad=False, state_out=st, expect_out=e)
+        torch.cuda.synchronize()
+        per_call = ctx.launch_count
+        ctx.set_tracing(True)
+        l0 = ctx.launch_count
+        for _ in range(5):
+            ctx.forward_grad(circ, p, o, 1, torch.complex64, want_grad=False, state_out=st, expect_out=e)
+        tr = ctx.trace()
+        per_call = (ctx.launch_count - l0) // 5
+        ctx.set_tracing(False)
+    finally:
+        ctx.set_graphs(False)
+    assert per_call > 0
+    assert sum(c for c, _ in tr.values()) == 5 * per_call
+    assert all(ms > 0 for _, ms in tr.values())
+    assert_rel(e.cpu().numpy(), ref, torch.complex64, "expectation", floor=obs_scale(obs))
