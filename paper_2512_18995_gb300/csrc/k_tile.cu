@@ -699,7 +699,7 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
     cudaEventCreate(&e1);
     Tracer *saved = g_tracer;
     g_tracer = nullptr;
-    for (int M = 3; M <= TileCfg<R>::Mmax; ++M)
+    for (int M = 2; M <= TileCfg<R>::Mmax; ++M)
     for (int k = kTileLaneBits + M; k <= std::min(p.n - 1, sizeof(R) == 4 ? 13 : 12); ++k) {
         const int maxt = ((1 << M) * (int)sizeof(cx<R>) >= 256) ? 256 : 512;
         if ((1 << (k - M)) > maxt) continue;

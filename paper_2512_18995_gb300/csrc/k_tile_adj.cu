@@ -266,6 +266,16 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
                     lv[i].x += f * x[i].x;
                     lv[i].y += f * x[i].y;
                 }
+            } else if (o.sloc == 0 && o.sout == 0 && o.nY == 0) {
+                // X string: <x|X|x> terms Re(conj(y) x), lambda += wc y
+#pragma unroll
+                for (int i = 0; i < kObsJ; ++i) {
+                    const int l = tid + i * (int)blockDim.x;
+                    const cx<R> y = bufP[(uint32_t)l ^ o.floc];
+                    e += y.x * x[i].x + y.y * x[i].y;
+                    lv[i].x += wc * y.x;
+                    lv[i].y += wc * y.y;
+                }
             } else {
 #pragma unroll
                 for (int i = 0; i < kObsJ; ++i) {
