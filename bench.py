@@ -319,6 +319,7 @@ def our_arm(args, rank, world, dist):
         extras["grads"] = batched_grads(ctx, device)
         extras["dense_block"] = dense_block(ctx, device, hbm_peak, peak_kind)
         extras["uneven_batch"] = uneven_batch(ctx, device)
+        extras["qft_tfim30"] = qft_tfim30(ctx, device)
         ctx.set_path({"auto": dq.PATH_AUTO, "plain": dq.PATH_PLAIN, "fused": dq.PATH_FUSED}[args.path])
 
     if rank == 0:
@@ -406,6 +407,41 @@ def dense_block(ctx, device, hbm_peak, peak_kind, n=30, reps=4):
             "hbm_frac": gbs / hbm_peak, "peak_kind": peak_kind, "tflops_tf32x3": tflops,
             "tf32_peak": tf32_peak, "tensor_frac": tflops / tf32_peak,
             "tf32_peak_kind": "measured bf16 x nominal tf32/bf16" if bf16 else "fallback bf16 x nominal tf32/bf16"}
+
+
+def qft_tfim30(ctx, device):
+    """30 qubits (8 GiB complex64 per vector): QFT then 10 RY/RZ + CNOT-ring
+    layers (600 parameters), open-chain TFIM energy and all 600 gradients,
+    the fused path vs the per-gate path (one warm-up and one timed call each)."""
+    import torch
+    import paper_2512_18995_gb300 as dq
+    wl = W.config_c5(30)
+    circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
+    obs = dq.Observables(wl.observables)
+    params = torch.tensor(wl.params, device=device)
+    out = {}
+    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+        ctx.set_path(path)
+        try:
+            ctx.forward_grad(circ, params, obs, 1, torch.complex64)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.forward_grad(circ, params, obs, 1, torch.complex64)
+            b.record()
+            torch.cuda.synchronize()
+        except RuntimeError as exc:   # not enough device memory
+            ctx.set_path(dq.PATH_AUTO)
+            return {"skipped": str(exc)[:120]}
+        ms = a.elapsed_time(b)
+        out[name] = {"ms_per_step": ms, "grads_per_s": wl.nparams / (ms / 1e3)}
+    ctx.set_path(dq.PATH_AUTO)
+    ctx.release_workspace()
+    torch.cuda.empty_cache()
+    out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
+    out["workload"] = "c5_qft_tfim30_c64"
+    return out
 
 
 def uneven_batch(ctx, device, steps=3):

@@ -252,6 +252,12 @@ class Context:
             out[buf.value.decode()] = (int(cnt.value), float(ms.value))
         return out
 
+    def release_workspace(self):
+        """Detach and free the workspace tensor (the next call allocates again)."""
+        torch.cuda.synchronize(self.device)
+        self._check(self.lib.dq_ctx_set_workspace(self.h, None, 0), "dq_ctx_set_workspace")
+        self._ws = None
+
     def ensure_workspace(self, circuit: Optional[Circuit], obs: Optional[Observables], batch: int, dtype: int,
                          need_bytes: Optional[int] = None):
         if need_bytes is None:
