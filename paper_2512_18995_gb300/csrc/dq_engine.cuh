@@ -17,6 +17,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <unordered_map>
+#include <vector>
+
 #include "dq_common.cuh"
 
 namespace dq {
@@ -222,6 +226,75 @@ inline void decode_with_fans(const std::vector<GOp> &g, int i0, int i1, const in
         }
         i = end;
     }
+}
+
+// Reorders ops into another valid order that changes the register layout
+// less often.  Two ops must keep their order when they share a qubit on which
+// at least one of them is not diagonal (a control acts diagonally on its
+// qubit; DIAG ops on every qubit they touch).  List scheduling: among the
+// ops whose predecessors are done, run those that need no new register bit
+// (diagonal, lane-bit or already-resident targets) first, in circuit order;
+// otherwise take the earliest ready op, adding its bit while fewer than M
+// are held, else starting a new layout with it.
+inline void schedule_for_layouts(std::vector<GOp> &ops, int M, int lane_bits) {
+    const int n = (int)ops.size();
+    if (n < 3 || M < 1) return;
+    std::vector<std::vector<int>> succ(n);
+    std::vector<int> indeg(n, 0);
+    std::unordered_map<int, int> last_nd;                 // qubit -> last op not diagonal on it
+    std::unordered_map<int, std::vector<int>> diag_since; // qubit -> diagonal ops since then
+    auto edge = [&](int a, int b) {
+        succ[a].push_back(b);
+        ++indeg[b];
+    };
+    for (int j = 0; j < n; ++j) {
+        const GOp &o = ops[j];
+        int qs[2] = {o.tg, o.cg};
+        bool nd[2] = {o.cls != CLS_DIAG, false};
+        for (int t = 0; t < 2; ++t) {
+            const int q = qs[t];
+            if (q < 0) continue;
+            auto it = last_nd.find(q);
+            if (it != last_nd.end()) edge(it->second, j);
+            if (nd[t]) {
+                for (int d : diag_since[q]) edge(d, j);
+                diag_since[q].clear();
+                last_nd[q] = j;
+            } else {
+                diag_since[q].push_back(j);
+            }
+        }
+    }
+    auto need = [&](const GOp &o) { return (o.cls != CLS_DIAG && o.tl >= lane_bits) ? o.tl : -1; };
+    std::vector<int> ready, order;
+    for (int j = 0; j < n; ++j)
+        if (!indeg[j]) ready.push_back(j);
+    std::vector<int> B;
+    order.reserve(n);
+    while (!ready.empty()) {
+        std::sort(ready.begin(), ready.end());
+        int pick = -1;
+        for (int j : ready) {
+            const int b = need(ops[j]);
+            if (b < 0 || std::find(B.begin(), B.end(), b) != B.end()) {
+                pick = j;
+                break;
+            }
+        }
+        if (pick < 0) {
+            pick = ready.front();
+            if ((int)B.size() >= M) B.clear();
+            B.push_back(need(ops[pick]));
+        }
+        ready.erase(std::find(ready.begin(), ready.end(), pick));
+        order.push_back(pick);
+        for (int k : succ[pick])
+            if (--indeg[k] == 0) ready.push_back(k);
+    }
+    if ((int)order.size() != n) return;   // (cannot happen: the graph follows circuit order)
+    std::vector<GOp> out(n);
+    for (int i = 0; i < n; ++i) out[i] = ops[order[i]];
+    ops.swap(out);
 }
 
 // Rotation pairs.  An uncontrolled REAL op (RY, H) whose next op on the same

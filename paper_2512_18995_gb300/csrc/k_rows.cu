@@ -134,6 +134,7 @@ bool rows_build_program(const Plan &p, int M, RowProgram &out) {
             push(g.cls, g.t, g.c, acc_of(g));
         }
     }
+    schedule_for_layouts(ops, M, kLaneBits);
     const std::vector<char> head = pair_real_diag(ops);
     std::vector<int> fwd(ops.size()), rev(ops.size());
     for (size_t i = 0; i < ops.size(); ++i) {

@@ -180,6 +180,7 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
             }
         }
         pass.nops = (int)gops.size();
+        schedule_for_layouts(gops, M, kTileLaneBits);
         const std::vector<char> head = pair_real_diag(gops);
         // register layouts, then decode every op against its layout
         pass.seg0 = (int)out.segs.size();
