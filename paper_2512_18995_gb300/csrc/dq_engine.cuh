@@ -282,9 +282,28 @@ inline void schedule_for_layouts(std::vector<GOp> &ops, int M, int lane_bits) {
             }
         }
         if (pick < 0) {
-            pick = ready.front();
-            if ((int)B.size() >= M) B.clear();
-            B.push_back(need(ops[pick]));
+            // a new bit: the one most ready ops need (earliest on ties); a full
+            // set starts over with the most needed bits
+            std::vector<std::pair<int, int>> cnt;   // (bit, count) in first-need order
+            for (int j : ready) {
+                const int b = need(ops[j]);
+                auto it = std::find_if(cnt.begin(), cnt.end(), [&](const std::pair<int, int> &x) { return x.first == b; });
+                if (it == cnt.end()) cnt.push_back({b, 1});
+                else ++it->second;
+            }
+            std::stable_sort(cnt.begin(), cnt.end(),
+                             [](const std::pair<int, int> &a, const std::pair<int, int> &b) { return a.second > b.second; });
+            if ((int)B.size() >= M) {
+                B.clear();
+                for (size_t i = 0; i < cnt.size() && (int)B.size() < M; ++i) B.push_back(cnt[i].first);
+            } else {
+                B.push_back(cnt[0].first);
+            }
+            for (int j : ready)
+                if (need(ops[j]) == cnt[0].first) {
+                    pick = j;
+                    break;
+                }
         }
         ready.erase(std::find(ready.begin(), ready.end(), pick));
         order.push_back(pick);
