@@ -336,23 +336,24 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
     int c[5];
     uint64_t base;
     int64_t row;
-    // the first tile's copy overlaps the staging of the pass's ops
+    // The pass's program (uploaded at planning time) is staged before waiting
+    // for the previous kernel of the stream (programmatic dependent launch:
+    // this prologue overlaps that kernel's tail); the state and the bound
+    // coefficients are read only after the wait.
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_async_smem();
-        if (t0 < t1) {
-            geom_coords(a.g, t0, c, base, row);
-            mbar_expect_tx(&bar[0], (uint32_t)tbytes);
-            tma_load5(buf0, &tmap, c, &bar[0]);
-        }
     }
-    for (int i = tid; i < a.nops; i += blockDim.x) {
-        const TOp o = a.ops[a.op0 + i];
-        sops[i] = o;
-        scoef[i] = gcoef[o.coef];
-    }
+    for (int i = tid; i < a.nops; i += blockDim.x) sops[i] = a.ops[a.op0 + i];
     for (int i = tid; i < a.nseg; i += blockDim.x) ssegs[i] = a.segs[a.seg0 + i];
+    grid_dep_wait();
+    if (tid == 0 && t0 < t1) {
+        geom_coords(a.g, t0, c, base, row);
+        mbar_expect_tx(&bar[0], (uint32_t)tbytes);
+        tma_load5(buf0, &tmap, c, &bar[0]);
+    }
+    for (int i = tid; i < a.nops; i += blockDim.x) scoef[i] = gcoef[sops[i].coef];
     for (int j = tid; j < nte; j += blockDim.x) {
         const uint64_t sm = a.epi.terms[j].s;
         ETerm e{};
@@ -453,6 +454,7 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
             }
         }
     }
+    grid_dep_launch();   // the next kernel of the stream may start its prologue
     if (nte && !failed && erow >= 0) {
         __syncthreads();
         eflush(erow);
@@ -614,13 +616,24 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
         a.g = make_geom(d, p.n, sc.k, wb, batch);
         a.errflag = tc.errflag;
         LaunchScope ls(s, "k_tile_fwd", launches);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e;
         switch (M) {
-        case 2: k_tile_fwd<R, 2><<<(unsigned)grid, threads, smem, s>>>(L.map, a); break;
-        case 3: k_tile_fwd<R, 3><<<(unsigned)grid, threads, smem, s>>>(L.map, a); break;
-        case 4: k_tile_fwd<R, 4><<<(unsigned)grid, threads, smem, s>>>(L.map, a); break;
-        default: k_tile_fwd<R, (TileCfg<R>::Mmax)><<<(unsigned)grid, threads, smem, s>>>(L.map, a); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 2>, L.map, a); break;
+        case 3: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 3>, L.map, a); break;
+        case 4: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 4>, L.map, a); break;
+        default: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, (TileCfg<R>::Mmax)>, L.map, a); break;
         }
-        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
