@@ -217,7 +217,17 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>(), sizeof(R) == 4 ? 2 :
     __syncthreads();
 
     cx<R> ps[1 << M], ls[1 << M];
+    // ops whose coefficients depend on the row (per-row parameters, encoded
+    // features) have their block refreshed in the shared table for every row,
+    // so every op reads its coefficients from shared memory
+    bool any_row = false;
+    for (int i = 0; i < a.nops; ++i) any_row |= sops[i].rowstep != 0;
     for (int row = blockIdx.x; row < a.batch; row += gridDim.x) {
+        if (any_row) {
+            for (int i = tid; i < a.nops; i += blockDim.x)
+                if (sops[i].rowstep) scoef[i] = gcoef[sops[i].coef + (int64_t)row * sops[i].rowstep];
+            __syncthreads();
+        }
         // ---- state preparation ------------------------------------------------
         Layout L = make_layout(sf[0], M, n, lane, warp);
         if (a.state_in) {
@@ -241,7 +251,7 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>(), sizeof(R) == 4 ? 2 :
                 }
                 for (int oi = sg.op0; oi < sg.op0 + sg.nops; ++oi) {
                     const EOp o = sops[oi];
-                    const Mat2<R> u = o.rowstep ? gcoef[o.coef + (int64_t)row * o.rowstep] : scoef[oi];
+                    const Mat2<R> u = scoef[oi];
                     eng_apply<R, M>(ps, o, u, 0, L, lane);
                 }
             }
@@ -330,10 +340,10 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>(), sizeof(R) == 4 ? 2 :
             for (int c = 0; c < sg.nops; ++c) {
                 const int oi = sg.op0 - c;
                 const EOp o = srops[oi];
-                const Mat2<R> u = o.rowstep ? gcoef[o.coef + (int64_t)row * o.rowstep] : scoef[oi];
+                const Mat2<R> u = scoef[oi];
                 if (o.pad[1]) {   // rotation pair: this DIAG op, then the REAL op before it
                     const EOp o2 = srops[oi - 1];
-                    const Mat2<R> u2 = o2.rowstep ? gcoef[o2.coef + (int64_t)row * o2.rowstep] : scoef[oi - 1];
+                    const Mat2<R> u2 = scoef[oi - 1];
                     R gd, gr;
                     eng_adjoint_pair<R, M>(ps, ls, o, dagger(u), o2, dagger(u2), lane, gd, gr);
                     if (o.slot >= 0) {

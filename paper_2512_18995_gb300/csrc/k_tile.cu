@@ -295,6 +295,7 @@ struct TileKArgs {
     const void *coef;
     TileGeom g;
     int *errflag;
+    int any_row;            // some op's coefficients depend on the batch row
     TileEpi epi;            // epi.nterms == 0: none
 };
 
@@ -378,6 +379,7 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
         }
     };
     uint32_t phase0 = 0, phase1 = 0;
+    int64_t crow = 0;   // the table holds row 0's coefficient blocks
     cx<R> r[1 << M];
     bool failed = false;
     for (int64_t t = t0, i = 0; t < t1; ++t, ++i) {
@@ -400,6 +402,13 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
             break;
         }
         geom_coords(a.g, t, c, base, row);
+        if (a.any_row && row != crow) {
+            // row-dependent coefficient blocks of this tile's row into the table
+            for (int i = tid; i < a.nops; i += blockDim.x)
+                if (sops[i].rowstep) scoef[i] = gcoef[sops[i].coef + row * sops[i].rowstep];
+            __syncthreads();
+            crow = row;
+        }
         for (int si = 0; si < a.nseg; ++si) {
             const TSeg sg = ssegs[si];
             const Layout L = make_layout(sg, M, a.g.k, lane, warp);
@@ -410,8 +419,7 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
                     oi += eng_fan<R, M>(r, sops + oi, scoef + oi, base, L) - 1;
                     continue;
                 }
-                const Mat2<R> u = o.rowstep ? gcoef[o.coef + row * o.rowstep] : scoef[oi];
-                eng_apply<R, M>(r, o, u, base, L, lane);
+                eng_apply<R, M>(r, o, scoef[oi], base, L, lane);
             }
             // each thread writes back exactly the addresses it read in this
             // layout; the barrier orders them before the next layout's reads
@@ -615,6 +623,8 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
         a.coef = coef;
         a.g = make_geom(d, p.n, sc.k, wb, batch);
         a.errflag = tc.errflag;
+        a.any_row = 0;
+        for (int j = ps.op0; j < ps.op0 + ps.nops; ++j) a.any_row |= sc.ops[j].rowstep != 0;
         LaunchScope ls(s, "k_tile_fwd", launches);
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];

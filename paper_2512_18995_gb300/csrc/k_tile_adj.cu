@@ -343,6 +343,7 @@ struct AdjArgs {
     double *part;        // [slot][row][cta]
     int batch;
     int *errflag;
+    int any_row;       // some op's coefficients depend on the batch row
 };
 
 template <typename R, int M>
@@ -400,6 +401,7 @@ __global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __gr
         }
     };
     cx<R> ps[1 << M], ls[1 << M];
+    int64_t crow = 0;   // the table holds row 0's coefficient blocks
     for (int64_t t = t0; t < t1; ++t) {
         int c[5];
         uint64_t base;
@@ -408,6 +410,14 @@ __global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __gr
         if (row != cur_row) {
             if (cur_row >= 0) flush(cur_row);
             cur_row = row;
+        }
+        if (a.any_row && row != crow) {
+            // row-dependent coefficient blocks of this tile's row into the table
+            __syncthreads();
+            for (int i = tid; i < a.nops; i += blockDim.x)
+                if (sops[i].rowstep) scoef[i] = gcoef[sops[i].coef + row * sops[i].rowstep];
+            __syncthreads();
+            crow = row;
         }
         if (tid == 0 && t > t0) {
             mbar_expect_tx(&bar[0], (uint32_t)(2 * tbytes));
@@ -428,10 +438,10 @@ __global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __gr
             for (int cc = 0; cc < sg.nops; ++cc) {
                 const int oi = sg.op0 - a.op0 - cc;
                 const EOp o = sops[oi];
-                const Mat2<R> u = o.rowstep ? gcoef[o.coef + row * o.rowstep] : scoef[oi];
+                const Mat2<R> u = scoef[oi];
                 if (o.pad[1]) {   // rotation pair: this DIAG op, then the REAL op before it
                     const EOp o2 = sops[oi - 1];
-                    const Mat2<R> u2 = o2.rowstep ? gcoef[o2.coef + row * o2.rowstep] : scoef[oi - 1];
+                    const Mat2<R> u2 = scoef[oi - 1];
                     R gd, gr;
                     eng_adjoint_pair<R, M>(ps, ls, o, dagger(u), o2, dagger(u2), lane, gd, gr);
                     if (o.slot >= 0) {
@@ -657,6 +667,8 @@ cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &
         a.part = part;
         a.batch = batch;
         a.errflag = tc.errflag;
+        a.any_row = 0;
+        for (int j = ps.op0; j < ps.op0 + ps.nops; ++j) a.any_row |= sc->rops[j].rowstep != 0;
         const size_t smem = 2 * (sizeof(cx<R>) << k) + 64 + (size_t)ps.nops * sizeof(EOp) +
                             (size_t)ps.nrseg * sizeof(ESeg) + (size_t)ps.nops * sizeof(Mat2<R>) +
                             (size_t)ps.nslot * sizeof(double) + (size_t)nw * ps.nslot * sizeof(R) + 64;

@@ -169,7 +169,7 @@ def test_expectations(ctx, path, dtype, n, batch):
 @pytest.mark.parametrize("path", sorted(PATHS))
 @pytest.mark.parametrize("dtype", sorted(DTYPES))
 @pytest.mark.parametrize("ppr", [False, True])
-@pytest.mark.parametrize("n,batch", [(1, 2), (4, 3), (9, 17), (12, 5), (15, 2)])
+@pytest.mark.parametrize("n,batch", [(1, 2), (4, 3), (9, 17), (12, 5), (15, 2), (18, 3)])
 def test_adjoint_gradients(ctx, path, dtype, ppr, n, batch):
     ctx.set_path(PATHS[path])
     dt = DTYPES[dtype]
