@@ -495,8 +495,8 @@ uint64_t sched_key(const Plan &p, int k, int low, int amp, int M, bool adjoint =
 template <typename R>
 void default_tile(int n, int &k, int &low, int &M) {
     if (n >= 25) {
-        M = sizeof(R) == 4 ? 5 : 4;
-        k = sizeof(R) == 4 ? 13 : 12;
+        M = 4;
+        k = sizeof(R) == 4 ? 12 : 12;
     } else {
         M = 3;
         k = std::max(kTileLaneBits + M, std::min(11, n - 9));
