@@ -72,14 +72,37 @@ typedef enum dq_status {
 
 typedef enum dq_dtype { DQ_C64 = 0, DQ_C128 = 1 } dq_dtype;
 
-/* Gate kinds.  One-qubit kinds use wires[0] as the target.  Controlled kinds
- * use wires[0] as the control and wires[1] as the target.  SWAP exchanges
- * wires[0] and wires[1].  Parametric kinds: RX RY RZ CP CRX CRY CRZ. */
+/* Gate kinds.
+ *   One-qubit kinds (H X Y Z S RX RY RZ P U3) act on wires[0].
+ *   Controlled kinds (CNOT CZ CP CRX CRY CRZ) take wires[0] as the control and
+ *   wires[1] as the target.
+ *   SWAP, RXX, RYY and RZZ act on wires[0] and wires[1] (symmetric).
+ *   CCX (Toffoli, the two-control X) takes wires[0] and wires[1] as controls
+ *   and wires[2] as the target.
+ * Wires of a gate must be distinct; unused entries of `wires` are ignored.
+ *
+ * Parametric kinds: RX RY RZ CP CRX CRY CRZ P RXX RYY RZZ (one angle t) and U3
+ * (three angles).  Definitions beyond the rotations of the conventions above:
+ *   P(t)     = diag(1, e^{it}), the phase shift.
+ *   R_PP(t)  = exp(-i t P(x)P / 2) for PP in {XX, YY, ZZ} (the two-qubit
+ *              rotations of the paper's QCNN and Trotterised-TFIM examples,
+ *              Sec. "Quantum Machine Learning" and "Simulation of Large
+ *              Quantum Systems with MPS").
+ *   U3(theta, phi, lam) = [[cos(theta/2), -e^{i lam} sin(theta/2)],
+ *                          [e^{i phi} sin(theta/2), e^{i(phi+lam)} cos(theta/2)]]
+ *              (the general one-qubit gate of the paper's QNN example, whose
+ *              action on |0> is the Bloch form of Sec. "Quantum Computing with
+ *              Qubits").  Its three angles are params[param_idx + 0, 1, 2]
+ *              (theta, phi, lam), or data[row, data_idx + 0, 1, 2]; a U3 with
+ *              neither index set is rejected (DQ_ERR_INVALID_ARG).
+ * The library lowers RXX, RYY, RZZ, U3 and CCX to exact products of the other
+ * kinds before planning (gradients of their angles are exact as well). */
 typedef enum dq_gate_kind {
     DQ_H = 0, DQ_X, DQ_Y, DQ_Z, DQ_S,
     DQ_RX, DQ_RY, DQ_RZ,
     DQ_CNOT, DQ_CZ, DQ_CP, DQ_SWAP,
     DQ_CRX, DQ_CRY, DQ_CRZ,
+    DQ_P, DQ_U3, DQ_RXX, DQ_RYY, DQ_RZZ, DQ_CCX,
     DQ_NUM_GATE_KINDS
 } dq_gate_kind;
 
@@ -95,12 +118,11 @@ typedef enum dq_path { DQ_PATH_AUTO = 0, DQ_PATH_PLAIN = 1, DQ_PATH_FUSED = 2 } 
 
 typedef struct dq_gate {
     int32_t kind;        /* dq_gate_kind */
-    int32_t wires[2];    /* see dq_gate_kind; wires[1] unused for 1-qubit kinds */
+    int32_t wires[3];    /* see dq_gate_kind */
     int32_t param_idx;   /* >= 0: trainable parameter index, else -1 */
     int32_t data_idx;    /* >= 0: encoded feature index, else -1 */
-    int32_t reserved;    /* must be 0 */
     double angle;        /* fixed angle when param_idx < 0 and data_idx < 0 */
-} dq_gate;
+} dq_gate;              /* 32 bytes */
 
 typedef struct dq_circuit {
     int32_t nqubits;       /* 1 .. 34 */

@@ -32,7 +32,8 @@ _default = None
 # The oracle's own gate codes (order of the enum in oracle.c).
 _KIND = {k: i for i, k in enumerate(
     ["h", "x", "y", "z", "s", "rx", "ry", "rz",
-     "cnot", "cz", "cp", "swap", "crx", "cry", "crz"])}
+     "cnot", "cz", "cp", "swap", "crx", "cry", "crz",
+     "p", "u3", "rxx", "ryy", "rzz", "ccx"])}
 
 
 def compile_source(src: str, out: str) -> str:
@@ -59,7 +60,7 @@ def _bind(path):
     I = ctypes.c_int
     lib.oracle_num_threads.restype = I
     lib.oracle_gate_block.argtypes = [I, ctypes.c_double, P]
-    gate_args = [I, I, P, P, P, P, P, P, P, I, I, P, I]
+    gate_args = [I, I, P, P, P, P, P, P, P, P, I, I, P, I]
     lib.oracle_run.argtypes = gate_args + [I, P]
     lib.oracle_apply.argtypes = gate_args + [I, I, P]
     lib.oracle_expect.argtypes = [I, P, P, P, P, I, I, P, P]
@@ -94,6 +95,7 @@ class _Gates:
         self.kind = np.array([_KIND[x.kind] for x in g] or [0], dtype=np.int32)
         self.w0 = np.array([x.wires[0] for x in g] or [0], dtype=np.int32)
         self.w1 = np.array([x.wires[1] if len(x.wires) > 1 else -1 for x in g] or [0], dtype=np.int32)
+        self.w2 = np.array([x.wires[2] if len(x.wires) > 2 else -1 for x in g] or [0], dtype=np.int32)
         self.pidx = np.array([x.param for x in g] or [0], dtype=np.int32)
         self.didx = np.array([x.data for x in g] or [0], dtype=np.int32)
         self.angle = np.array([x.angle for x in g] or [0.0], dtype=np.float64)
@@ -107,7 +109,7 @@ class _Gates:
         else:
             nfeat = 0
         self._keep = (params, data)
-        return [n, self.count, _ptr(self.kind), _ptr(self.w0), _ptr(self.w1), _ptr(self.pidx),
+        return [n, self.count, _ptr(self.kind), _ptr(self.w0), _ptr(self.w1), _ptr(self.w2), _ptr(self.pidx),
                 _ptr(self.didx), _ptr(self.angle), _ptr(params), int(nparams),
                 int(bool(params_per_row)), _ptr(data), int(nfeat)]
 
@@ -166,7 +168,7 @@ def adjoint(n, gates, observables, params=None, data=None, batch=1, params_per_r
     g = _Gates(gates)
     o = _Obs(observables)
     args = g.args(n, params, params_per_row, data)
-    nparams, nfeat = args[9], args[12]
+    nparams, nfeat = args[10], args[13]
     exp = np.empty((batch, o.nobs), dtype=np.float64)
     gp = np.zeros((batch, nparams) if params_per_row else (nparams,), dtype=np.float64)
     gd = np.zeros((batch, nfeat), dtype=np.float64) if nfeat else None

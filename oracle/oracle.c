@@ -22,6 +22,11 @@
  *     with rx(-h dt), rzz(-2 J dt)): rotations are R_P(t) = exp(-i t P / 2).
  *   - Sec. "Distributed Quantum Fourier Transform": controlled phase
  *     CP(phi) = diag(1, 1, 1, e^{i phi}), Hadamard, SWAP.
+ *   - Sec. "Quantum Machine Learning" (QNN, QCNN examples) and the Trotterised
+ *     TFIM: the general one-qubit gate u3, the two-qubit rotations rxx, ryy,
+ *     rzz (R_PP(t) = exp(-i t P(x)P / 2), the same exp(-i t G / 2) form),
+ *     controlled RY with an encoded angle.  The phase shift P(t) = diag(1,
+ *     e^{it}) and the Toffoli gate CCX complete the gate set.
  *   - Dense blocks (oracle_apply_dense): the same evolution with a group of
  *     consecutive gates written as one matrix on the lowest-order wires; the
  *     paper applies gates one at a time, so this is the plain definition of
@@ -32,6 +37,10 @@
  *       index = sum_q b_q 2^(n-1-q).
  *   - RZ(t) = diag(e^{-i t/2}, e^{i t/2}) (the exp(-i t Z / 2) form).
  *   - a Pauli term carries bit q of xmask/zmask for wire q; both bits = Y.
+ *   - U3(theta, phi, lam) = [[cos(theta/2), -e^{i lam} sin(theta/2)],
+ *     [e^{i phi} sin(theta/2), e^{i(phi+lam)} cos(theta/2)]] (the usual u3
+ *     matrix; its first column is the Bloch form of the Background section),
+ *     with its three angles in consecutive parameter (or feature) slots.
  *
  * Parity: pinned (closed forms, brute-force dense products, parameter-shift
  * and finite differences in the test-suite).
@@ -53,6 +62,7 @@ enum {
     O_RX, O_RY, O_RZ,
     O_CNOT, O_CZ, O_CP, O_SWAP,
     O_CRX, O_CRY, O_CRZ,
+    O_P, O_U3, O_RXX, O_RYY, O_RZZ, O_CCX,
     O_NKINDS
 };
 
@@ -92,6 +102,7 @@ static void target_matrix(int kind, double t, cplx m[4])
     case O_RZ:
     case O_CRZ:  m[0] = c - I * s; m[1] = 0; m[2] = 0; m[3] = c + I * s; break;
     case O_CP:   m[0] = 1;  m[1] = 0;   m[2] = 0;  m[3] = cexp(I * t); break;
+    case O_P:    m[0] = 1;  m[1] = 0;   m[2] = 0;  m[3] = cexp(I * t); break;
     default:     m[0] = 1;  m[1] = 0;   m[2] = 0;  m[3] = 1;   break;
     }
 }
@@ -107,6 +118,7 @@ static void generator_matrix(int kind, cplx g[4])
     case O_RY: case O_CRY: g[1] = -0.5 * I;  g[2] = 0.5 * I;  break;  /* Y/2 */
     case O_RZ: case O_CRZ: g[0] = 0.5;       g[3] = -0.5;     break;  /* Z/2 */
     case O_CP:             g[3] = -1.0;                        break;  /* CP = exp(i t |11><11|) */
+    case O_P:              g[3] = -1.0;                        break;  /* P = exp(i t |1><1|) */
     default: break;
     }
 }
@@ -114,7 +126,31 @@ static void generator_matrix(int kind, cplx g[4])
 static int is_parametric(int kind)
 {
     return kind == O_RX || kind == O_RY || kind == O_RZ || kind == O_CP ||
-           kind == O_CRX || kind == O_CRY || kind == O_CRZ;
+           kind == O_CRX || kind == O_CRY || kind == O_CRZ || kind == O_P ||
+           kind == O_U3 || kind == O_RXX || kind == O_RYY || kind == O_RZZ;
+}
+
+/* Number of consecutive angle slots a gate reads (U3: theta, phi, lam). */
+static int angle_span(int kind) { return kind == O_U3 ? 3 : 1; }
+
+/* U3(theta, phi, lam) and its partial derivatives, written out from the
+ * matrix definition:
+ *   U  = [[ch, -e^{i lam} sh], [e^{i phi} sh, e^{i(phi+lam)} ch]]
+ *   dU/dtheta = 1/2 [[-sh, -e^{i lam} ch], [e^{i phi} ch, -e^{i(phi+lam)} sh]]
+ *   dU/dphi   = [[0, 0], [i e^{i phi} sh, i e^{i(phi+lam)} ch]]
+ *   dU/dlam   = [[0, -i e^{i lam} sh], [0, i e^{i(phi+lam)} ch]]
+ * with ch = cos(theta/2), sh = sin(theta/2).  which = 0 gives U, 1..3 the
+ * derivative in theta, phi, lam. */
+static void u3_matrix(const double t3[3], int which, cplx m[4])
+{
+    const double ch = cos(t3[0] / 2.0), sh = sin(t3[0] / 2.0);
+    const cplx ep = cexp(I * t3[1]), el = cexp(I * t3[2]), epl = cexp(I * (t3[1] + t3[2]));
+    switch (which) {
+    case 0: m[0] = ch;        m[1] = -el * sh;      m[2] = ep * sh;      m[3] = epl * ch;       break;
+    case 1: m[0] = -0.5 * sh; m[1] = -0.5 * el * ch; m[2] = 0.5 * ep * ch; m[3] = -0.5 * epl * sh; break;
+    case 2: m[0] = 0;         m[1] = 0;             m[2] = I * ep * sh;  m[3] = I * epl * ch;   break;
+    default: m[0] = 0;        m[1] = -I * el * sh;  m[2] = 0;            m[3] = I * epl * ch;   break;
+    }
 }
 
 static int is_controlled(int kind)
@@ -122,6 +158,8 @@ static int is_controlled(int kind)
     return kind == O_CNOT || kind == O_CZ || kind == O_CP ||
            kind == O_CRX || kind == O_CRY || kind == O_CRZ;
 }
+
+static int is_pauli_pair(int kind) { return kind == O_RXX || kind == O_RYY || kind == O_RZZ; }
 
 /* Bit position of wire q: wire 0 is the most significant bit. */
 static inline int bitpos(int n, int q) { return n - 1 - q; }
@@ -164,55 +202,21 @@ static void apply_swap(int n, cplx *psi, int qa, int qb)
     }
 }
 
-/* Angle of gate g for batch row `row`. */
-static double gate_angle(int g, const int *pidx, const int *didx, const double *angle,
-                         const double *params, int nparams, int params_per_row,
-                         const double *data, int nfeat, int row)
-{
-    if (pidx[g] >= 0)
-        return params_per_row ? params[(int64_t)row * nparams + pidx[g]] : params[pidx[g]];
-    if (didx[g] >= 0)
-        return data[(int64_t)row * nfeat + didx[g]];
-    return angle[g];
-}
-
-static void conj_transpose(const cplx m[4], cplx d[4])
-{
-    d[0] = conj(m[0]); d[1] = conj(m[2]); d[2] = conj(m[1]); d[3] = conj(m[3]);
-}
-
-/* Apply gate g (or its inverse when `dagger`). */
-static void apply_gate(int n, cplx *psi, int kind, int w0, int w1, double t, int dagger)
-{
-    if (kind == O_SWAP) {
-        apply_swap(n, psi, w0, w1);
-        return;
-    }
-    cplx m[4], d[4];
-    target_matrix(kind, t, m);
-    if (dagger) {
-        conj_transpose(m, d);
-        memcpy(m, d, sizeof(m));
-    }
-    if (is_controlled(kind))
-        apply_block(n, psi, w1, w0, m);
-    else
-        apply_block(n, psi, w0, -1, m);
-}
-
-/* Single-row forward run from |0...0>. */
-static void run_row(int n, int ngates, const int *kind, const int *w0, const int *w1,
-                    const int *pidx, const int *didx, const double *angle,
-                    const double *params, int nparams, int params_per_row,
-                    const double *data, int nfeat, int row, cplx *psi)
+/* Apply X on the target wire of the amplitudes whose two control wires are
+ * both |1> (Toffoli). */
+static void apply_ccx(int n, cplx *psi, int c0, int c1, int target)
 {
     const int64_t dim = (int64_t)1 << n;
-    for (int64_t i = 0; i < dim; ++i) psi[i] = 0;
-    psi[0] = 1;
-    for (int g = 0; g < ngates; ++g) {
-        const double t = gate_angle(g, pidx, didx, angle, params, nparams, params_per_row,
-                                    data, nfeat, row);
-        apply_gate(n, psi, kind[g], w0[g], w1[g], t, 0);
+    const int64_t b0 = (int64_t)1 << bitpos(n, c0);
+    const int64_t b1 = (int64_t)1 << bitpos(n, c1);
+    const int64_t tb = (int64_t)1 << bitpos(n, target);
+#pragma omp parallel for schedule(static) if (dim >= (1 << 16))
+    for (int64_t i = 0; i < dim; ++i) {
+        if ((i & tb) || !(i & b0) || !(i & b1)) continue;
+        const int64_t j = i | tb;
+        const cplx a = psi[i];
+        psi[i] = psi[j];
+        psi[j] = a;
     }
 }
 
@@ -226,6 +230,98 @@ static void apply_pauli(int n, cplx *v, uint64_t xmask, uint64_t zmask)
         cplx m[4];
         target_matrix(kind, 0.0, m);
         apply_block(n, v, q, -1, m);
+    }
+}
+
+/* The two-qubit Pauli string P(x)P of kind RXX / RYY / RZZ on wires a, b, as
+ * (xmask, zmask) by wire. */
+static void pauli_pair_masks(int kind, int a, int b, uint64_t *xm, uint64_t *zm)
+{
+    const uint64_t w = ((uint64_t)1 << a) | ((uint64_t)1 << b);
+    *xm = (kind == O_RXX || kind == O_RYY) ? w : 0;
+    *zm = (kind == O_RZZ || kind == O_RYY) ? w : 0;
+}
+
+/* psi <- exp(-i t S / 2) psi = cos(t/2) psi - i sin(t/2) S psi for a Pauli
+ * string S (S^2 = I), with S psi formed on a copy. */
+static void apply_pauli_rotation(int n, cplx *psi, uint64_t xm, uint64_t zm, double t)
+{
+    const int64_t dim = (int64_t)1 << n;
+    cplx *sp = (cplx *)malloc((size_t)dim * sizeof(cplx));
+    memcpy(sp, psi, (size_t)dim * sizeof(cplx));
+    apply_pauli(n, sp, xm, zm);
+    const double c = cos(t / 2.0), sn = sin(t / 2.0);
+    for (int64_t i = 0; i < dim; ++i) psi[i] = c * psi[i] - I * sn * sp[i];
+    free(sp);
+}
+
+/* Angles of gate g for batch row `row`: t3[k] for k < angle_span(kind),
+ * from consecutive parameter or feature slots, else the fixed angle. */
+static void gate_angles(int g, int kind, const int *pidx, const int *didx, const double *angle,
+                        const double *params, int nparams, int params_per_row,
+                        const double *data, int nfeat, int row, double t3[3])
+{
+    t3[0] = t3[1] = t3[2] = 0.0;
+    for (int k = 0; k < angle_span(kind); ++k) {
+        if (pidx[g] >= 0)
+            t3[k] = params_per_row ? params[(int64_t)row * nparams + pidx[g] + k] : params[pidx[g] + k];
+        else if (didx[g] >= 0)
+            t3[k] = data[(int64_t)row * nfeat + didx[g] + k];
+        else
+            t3[k] = angle[g];
+    }
+}
+
+static void conj_transpose(const cplx m[4], cplx d[4])
+{
+    d[0] = conj(m[0]); d[1] = conj(m[2]); d[2] = conj(m[1]); d[3] = conj(m[3]);
+}
+
+/* Apply gate g (or its inverse when `dagger`); t3 holds its angles. */
+static void apply_gate(int n, cplx *psi, int kind, int w0, int w1, int w2, const double t3[3], int dagger)
+{
+    if (kind == O_SWAP) {
+        apply_swap(n, psi, w0, w1);
+        return;
+    }
+    if (kind == O_CCX) {
+        apply_ccx(n, psi, w0, w1, w2);
+        return;
+    }
+    if (is_pauli_pair(kind)) {
+        uint64_t xm, zm;
+        pauli_pair_masks(kind, w0, w1, &xm, &zm);
+        apply_pauli_rotation(n, psi, xm, zm, dagger ? -t3[0] : t3[0]);
+        return;
+    }
+    cplx m[4], d[4];
+    if (kind == O_U3)
+        u3_matrix(t3, 0, m);
+    else
+        target_matrix(kind, t3[0], m);
+    if (dagger) {
+        conj_transpose(m, d);
+        memcpy(m, d, sizeof(m));
+    }
+    if (is_controlled(kind))
+        apply_block(n, psi, w1, w0, m);
+    else
+        apply_block(n, psi, w0, -1, m);
+}
+
+/* Single-row forward run from |0...0>. */
+static void run_row(int n, int ngates, const int *kind, const int *w0, const int *w1, const int *w2,
+                    const int *pidx, const int *didx, const double *angle,
+                    const double *params, int nparams, int params_per_row,
+                    const double *data, int nfeat, int row, cplx *psi)
+{
+    const int64_t dim = (int64_t)1 << n;
+    for (int64_t i = 0; i < dim; ++i) psi[i] = 0;
+    psi[0] = 1;
+    for (int g = 0; g < ngates; ++g) {
+        double t3[3];
+        gate_angles(g, kind[g], pidx, didx, angle, params, nparams, params_per_row, data, nfeat, row, t3);
+        apply_gate(n, psi, kind[g], w0[g], w1[g], w2[g], t3, 0);
     }
 }
 
@@ -251,7 +347,7 @@ void oracle_gate_block(int kind, double t, double *out8)
 
 /* Apply a gate list to `batch` given states in place (used for unitarity and
  * dense-matrix checks, where the input is not |0...0>). */
-void oracle_apply(int n, int ngates, const int *kind, const int *w0, const int *w1,
+void oracle_apply(int n, int ngates, const int *kind, const int *w0, const int *w1, const int *w2,
                   const int *pidx, const int *didx, const double *angle,
                   const double *params, int nparams, int params_per_row,
                   const double *data, int nfeat, int batch, int dagger, double *states_ri)
@@ -261,24 +357,17 @@ void oracle_apply(int n, int ngates, const int *kind, const int *w0, const int *
 #pragma omp parallel for schedule(dynamic, 1) if (batch > 1)
     for (int r = 0; r < batch; ++r) {
         cplx *psi = states + (int64_t)r * dim;
-        if (!dagger) {
-            for (int g = 0; g < ngates; ++g) {
-                const double t = gate_angle(g, pidx, didx, angle, params, nparams,
-                                            params_per_row, data, nfeat, r);
-                apply_gate(n, psi, kind[g], w0[g], w1[g], t, 0);
-            }
-        } else {
-            for (int g = ngates - 1; g >= 0; --g) {
-                const double t = gate_angle(g, pidx, didx, angle, params, nparams,
-                                            params_per_row, data, nfeat, r);
-                apply_gate(n, psi, kind[g], w0[g], w1[g], t, 1);
-            }
+        for (int step = 0; step < ngates; ++step) {
+            const int g = dagger ? ngates - 1 - step : step;
+            double t3[3];
+            gate_angles(g, kind[g], pidx, didx, angle, params, nparams, params_per_row, data, nfeat, r, t3);
+            apply_gate(n, psi, kind[g], w0[g], w1[g], w2[g], t3, dagger);
         }
     }
 }
 
 /* |psi_row> = U_G ... U_1 |0...0> for every batch row. */
-void oracle_run(int n, int ngates, const int *kind, const int *w0, const int *w1,
+void oracle_run(int n, int ngates, const int *kind, const int *w0, const int *w1, const int *w2,
                 const int *pidx, const int *didx, const double *angle,
                 const double *params, int nparams, int params_per_row,
                 const double *data, int nfeat, int batch, double *states_ri)
@@ -287,7 +376,7 @@ void oracle_run(int n, int ngates, const int *kind, const int *w0, const int *w1
     cplx *states = (cplx *)states_ri;
 #pragma omp parallel for schedule(dynamic, 1) if (batch > 1)
     for (int r = 0; r < batch; ++r)
-        run_row(n, ngates, kind, w0, w1, pidx, didx, angle, params, nparams,
+        run_row(n, ngates, kind, w0, w1, w2, pidx, didx, angle, params, nparams,
                 params_per_row, data, nfeat, r, states + (int64_t)r * dim);
 }
 
@@ -324,13 +413,15 @@ void oracle_expect(int n, const double *coeff, const uint64_t *xmask, const uint
  *   for j = G .. 1:
  *       if gate j has an angle t_j = exp(-i t G_j):
  *           dL/dt_j += 2 Im <lambda | G_j | psi>
+ *       (U3, whose angles enter otherwise: dL/dt_k += 2 Re <lambda| dU/dt_k
+ *        U^dagger psi>, the same derivative before the generator is factored)
  *       psi <- U_j^dagger psi,  lambda <- U_j^dagger lambda
  *
  * The derivative is routed to the trainable parameter (summed over rows when
  * params are shared, per row when params_per_row) or to the encoded feature
  * (per row).  expect_out (batch x nobs) receives E.
  */
-void oracle_adjoint(int n, int ngates, const int *kind, const int *w0, const int *w1,
+void oracle_adjoint(int n, int ngates, const int *kind, const int *w0, const int *w1, const int *w2,
                     const int *pidx, const int *didx, const double *angle,
                     const double *params, int nparams, int params_per_row,
                     const double *data, int nfeat, int batch,
@@ -347,9 +438,10 @@ void oracle_adjoint(int n, int ngates, const int *kind, const int *w0, const int
         cplx *psi = (cplx *)malloc((size_t)dim * sizeof(cplx));
         cplx *lam = (cplx *)calloc((size_t)dim, sizeof(cplx));
         cplx *tmp = (cplx *)malloc((size_t)dim * sizeof(cplx));
+        cplx *tmp2 = (cplx *)malloc((size_t)dim * sizeof(cplx));
         double *gp = gp_row + (int64_t)r * (nparams > 0 ? nparams : 1);
 
-        run_row(n, ngates, kind, w0, w1, pidx, didx, angle, params, nparams,
+        run_row(n, ngates, kind, w0, w1, w2, pidx, didx, angle, params, nparams,
                 params_per_row, data, nfeat, r, psi);
 
         /* expectations and lambda = sum_o w_o O_o psi */
@@ -368,31 +460,56 @@ void oracle_adjoint(int n, int ngates, const int *kind, const int *w0, const int
             for (int f = 0; f < nfeat; ++f) grad_data[(int64_t)r * nfeat + f] = 0.0;
 
         for (int g = ngates - 1; g >= 0; --g) {
-            const double t = gate_angle(g, pidx, didx, angle, params, nparams,
-                                        params_per_row, data, nfeat, r);
-            if (is_parametric(kind[g]) && (pidx[g] >= 0 || didx[g] >= 0)) {
-                cplx gm[4];
-                generator_matrix(kind[g], gm);
+            double t3[3];
+            gate_angles(g, kind[g], pidx, didx, angle, params, nparams, params_per_row, data, nfeat, r, t3);
+            const int trainable = is_parametric(kind[g]) && (pidx[g] >= 0 || didx[g] >= 0);
+            if (trainable && kind[g] == O_U3) {
+                /* U3 is not of the exp(-i t G) form in each angle: take
+                 * dL/dt_k = 2 Re <lambda| (dU/dt_k) psi_before> with
+                 * psi_before = U^dagger psi. */
                 memcpy(tmp, psi, (size_t)dim * sizeof(cplx));
-                if (is_controlled(kind[g])) {
-                    /* generator lives on the control=|1> subspace */
-                    const int64_t cb = (int64_t)1 << bitpos(n, w0[g]);
-                    for (int64_t i = 0; i < dim; ++i)
-                        if (!(i & cb)) tmp[i] = 0;
-                    apply_block(n, tmp, w1[g], w0[g], gm);
+                apply_gate(n, tmp, O_U3, w0[g], -1, -1, t3, 1);
+                for (int k = 0; k < 3; ++k) {
+                    cplx dm[4];
+                    u3_matrix(t3, k + 1, dm);
+                    memcpy(tmp2, tmp, (size_t)dim * sizeof(cplx));
+                    apply_block(n, tmp2, w0[g], -1, dm);
+                    const double dk = 2.0 * creal(inner(dim, lam, tmp2));
+                    if (pidx[g] >= 0) gp[pidx[g] + k] += dk;
+                    else if (grad_data) grad_data[(int64_t)r * nfeat + didx[g] + k] += dk;
+                }
+            } else if (trainable) {
+                memcpy(tmp, psi, (size_t)dim * sizeof(cplx));
+                if (is_pauli_pair(kind[g])) {
+                    /* R_S(t) = exp(-i t S / 2): generator S / 2 */
+                    uint64_t xm, zm;
+                    pauli_pair_masks(kind[g], w0[g], w1[g], &xm, &zm);
+                    apply_pauli(n, tmp, xm, zm);
+                    for (int64_t i = 0; i < dim; ++i) tmp[i] *= 0.5;
                 } else {
-                    apply_block(n, tmp, w0[g], -1, gm);
+                    cplx gm[4];
+                    generator_matrix(kind[g], gm);
+                    if (is_controlled(kind[g])) {
+                        /* generator lives on the control=|1> subspace */
+                        const int64_t cb = (int64_t)1 << bitpos(n, w0[g]);
+                        for (int64_t i = 0; i < dim; ++i)
+                            if (!(i & cb)) tmp[i] = 0;
+                        apply_block(n, tmp, w1[g], w0[g], gm);
+                    } else {
+                        apply_block(n, tmp, w0[g], -1, gm);
+                    }
                 }
                 const double d = 2.0 * cimag(inner(dim, lam, tmp));
                 if (pidx[g] >= 0) gp[pidx[g]] += d;
                 else if (grad_data) grad_data[(int64_t)r * nfeat + didx[g]] += d;
             }
-            apply_gate(n, psi, kind[g], w0[g], w1[g], t, 1);
-            apply_gate(n, lam, kind[g], w0[g], w1[g], t, 1);
+            apply_gate(n, psi, kind[g], w0[g], w1[g], w2[g], t3, 1);
+            apply_gate(n, lam, kind[g], w0[g], w1[g], w2[g], t3, 1);
         }
         free(psi);
         free(lam);
         free(tmp);
+        free(tmp2);
     }
 
     if (grad_params && nparams > 0) {

@@ -25,7 +25,10 @@ PATH_AUTO, PATH_PLAIN, PATH_FUSED = 0, 1, 2
 ADJ_CLOBBER_STATE = 1
 
 KIND = {k: i for i, k in enumerate(
-    ["h", "x", "y", "z", "s", "rx", "ry", "rz", "cnot", "cz", "cp", "swap", "crx", "cry", "crz"])}
+    ["h", "x", "y", "z", "s", "rx", "ry", "rz", "cnot", "cz", "cp", "swap", "crx", "cry", "crz",
+     "p", "u3", "rxx", "ryy", "rzz", "ccx"])}
+# consecutive angle slots a gate reads from params / data (U3: theta, phi, lam)
+ANGLE_SPAN = {"u3": 3}
 
 
 class DQError(RuntimeError):
@@ -35,8 +38,8 @@ class DQError(RuntimeError):
 
 
 class dq_gate(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("wires", ctypes.c_int32 * 2), ("param_idx", ctypes.c_int32),
-                ("data_idx", ctypes.c_int32), ("reserved", ctypes.c_int32), ("angle", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int32), ("wires", ctypes.c_int32 * 3), ("param_idx", ctypes.c_int32),
+                ("data_idx", ctypes.c_int32), ("angle", ctypes.c_double)]
 
 
 class dq_circuit(ctypes.Structure):
@@ -140,14 +143,16 @@ class Circuit:
             kind, wires, param, data, angle = (g.kind, g.wires, g.param, g.data, g.angle) \
                 if hasattr(g, "kind") else tuple(g)
             arr[i].kind = KIND[kind] if isinstance(kind, str) else int(kind)
-            arr[i].wires[0] = int(wires[0])
-            arr[i].wires[1] = int(wires[1]) if len(wires) > 1 else -1
+            for j in range(3):
+                arr[i].wires[j] = int(wires[j]) if len(wires) > j else -1
             arr[i].param_idx = int(param)
             arr[i].data_idx = int(data)
-            arr[i].reserved = 0
             arr[i].angle = float(angle)
-            maxp = max(maxp, int(param))
-            maxd = max(maxd, int(data))
+            span = ANGLE_SPAN.get(kind, 1) if isinstance(kind, str) else (3 if int(kind) == KIND["u3"] else 1)
+            if int(param) >= 0:
+                maxp = max(maxp, int(param) + span - 1)
+            if int(data) >= 0:
+                maxd = max(maxd, int(data) + span - 1)
         self.nqubits = int(nqubits)
         self.ngates = len(gl)
         self.nparams = int(nparams) if nparams is not None else maxp + 1

@@ -180,7 +180,122 @@ dq_status upload(dq_ctx *ctx, T **dst, const T *src, size_t count) {
     return DQ_OK;
 }
 
-// Validate a circuit and translate it to bit-space gates.
+// A gate after lowering: one of the kinds the kernels implement (wire space).
+struct Prim {
+    int kind, w0, w1, pidx, didx;
+    double angle;
+};
+
+// Number of kernel-level gates that gate kind `k` lowers to.
+int lowered_size(int k) {
+    switch (k) {
+    case DQ_RZZ: case DQ_U3: return 3;
+    case DQ_RXX: case DQ_RYY: case DQ_CCX: return 7;
+    default: return 1;
+    }
+}
+
+int lowered_count(const dq_circuit &c) {
+    int64_t total = 0;
+    if (c.gates)
+        for (int i = 0; i < c.ngates; ++i) {
+            const int k = c.gates[i].kind;
+            total += (k >= 0 && k < DQ_NUM_GATE_KINDS) ? lowered_size(k) : 1;
+        }
+    return (int)std::min<int64_t>(total, INT32_MAX);
+}
+
+// Validate API gate i of circuit c and append its kernel-level gates to
+// `out`.  The composite kinds become exact products of the others (operators
+// written right to left, appended in circuit order):
+//   RZZ(t) = CNOT(a,b) RZ_b(t) CNOT(a,b): after the CNOT, Z on b carries Z_a Z_b.
+//   RXX(t) = (H (x) H) RZZ(t) (H (x) H), since H Z H = X.
+//   RYY(t) = (V (x) V) RZZ(t) (V^dag (x) V^dag), V = RX(-pi/2), since V Z V^dag = Y.
+//   U3(theta, phi, lam) = P(phi) RY(theta) P(lam) (multiply out the 2x2 blocks).
+//   CCX(c0, c1; t) = H_t CCZ H_t with CCZ = CP_{c0,t}(pi/2) CNOT(c0,c1)
+//       CP_{c1,t}(-pi/2) CNOT(c0,c1) CP_{c1,t}(pi/2): the phases sum to
+//       (pi/2) b_t (b_c1 - (b_c0 xor b_c1) + b_c0) = pi b_t b_c0 b_c1.
+// A lowered rotation keeps its angle source, so the adjoint sweep's gradient
+// for it is the gradient of the composite gate's angle.
+dq_status lower_gate(dq_ctx *ctx, const dq_circuit *c, int i, std::vector<Prim> &out) {
+    const dq_gate &g = c->gates[i];
+    const int n = c->nqubits;
+    if (g.kind < 0 || g.kind >= DQ_NUM_GATE_KINDS)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: unknown kind %d", i, g.kind);
+    const int k = g.kind;
+    const int nw = k == DQ_CCX ? 3 : ((kind_controlled(k) || k == DQ_SWAP || k == DQ_RXX || k == DQ_RYY ||
+                                       k == DQ_RZZ) ? 2 : 1);
+    for (int j = 0; j < nw; ++j) {
+        if (g.wires[j] < 0 || g.wires[j] >= n)
+            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: wire %d outside [0, %d)", i, g.wires[j], n);
+        for (int l = 0; l < j; ++l)
+            if (g.wires[l] == g.wires[j])
+                return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: wires %d and %d coincide (%d)", i, l, j, g.wires[j]);
+    }
+    const bool par = kind_parametric(k) || k == DQ_U3 || k == DQ_RXX || k == DQ_RYY || k == DQ_RZZ;
+    if (!par && (g.param_idx >= 0 || g.data_idx >= 0))
+        return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: kind %d takes no angle", i, k);
+    if (g.param_idx >= 0 && g.data_idx >= 0)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: both param_idx and data_idx set", i);
+    const int span = k == DQ_U3 ? 3 : 1;
+    if (g.param_idx >= 0 && g.param_idx + span > c->nparams)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: param_idx %d (+%d) >= nparams %d", i, g.param_idx, span - 1,
+                    c->nparams);
+    if (g.data_idx >= 0 && g.data_idx + span > c->nfeatures)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: data_idx %d (+%d) >= nfeatures %d", i, g.data_idx, span - 1,
+                    c->nfeatures);
+    if (k == DQ_U3 && g.param_idx < 0 && g.data_idx < 0)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: U3 takes its angles from params or data", i);
+    const int a = g.wires[0], b = g.wires[1];
+    auto fixed = [&](int kind, int w0, int w1, double t) { out.push_back(Prim{kind, w0, w1, -1, -1, t}); };
+    auto angled = [&](int kind, int w0, int w1, int off) {
+        out.push_back(Prim{kind, w0, w1, g.param_idx >= 0 ? g.param_idx + off : -1,
+                           g.data_idx >= 0 ? g.data_idx + off : -1, g.angle});
+    };
+    const double h = 1.5707963267948966;   // pi / 2
+    switch (k) {
+    case DQ_RZZ:
+        fixed(DQ_CNOT, a, b, 0);
+        angled(DQ_RZ, b, -1, 0);
+        fixed(DQ_CNOT, a, b, 0);
+        break;
+    case DQ_RXX:
+    case DQ_RYY: {
+        const int fk = k == DQ_RXX ? DQ_H : DQ_RX;
+        fixed(fk, a, -1, h);
+        fixed(fk, b, -1, h);
+        fixed(DQ_CNOT, a, b, 0);
+        angled(DQ_RZ, b, -1, 0);
+        fixed(DQ_CNOT, a, b, 0);
+        fixed(fk, a, -1, -h);
+        fixed(fk, b, -1, -h);
+        break;
+    }
+    case DQ_U3:
+        angled(DQ_P, a, -1, 2);
+        angled(DQ_RY, a, -1, 0);
+        angled(DQ_P, a, -1, 1);
+        break;
+    case DQ_CCX: {
+        const int t = g.wires[2];
+        fixed(DQ_H, t, -1, 0);
+        fixed(DQ_CP, b, t, h);
+        fixed(DQ_CNOT, a, b, 0);
+        fixed(DQ_CP, b, t, -h);
+        fixed(DQ_CNOT, a, b, 0);
+        fixed(DQ_CP, a, t, h);
+        fixed(DQ_H, t, -1, 0);
+        break;
+    }
+    default:
+        out.push_back(Prim{k, a, nw > 1 ? b : -1, g.param_idx, g.data_idx, g.angle});
+        break;
+    }
+    return DQ_OK;
+}
+
+// Validate a circuit, lower it and translate it to bit-space gates (appended
+// to dg / bg).
 dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<DevGate> &dg,
                         std::vector<BindGate> &bg, int param_base, int *ncoef_shared, int *ncoef_rows,
                         bool batch_mode) {
@@ -191,58 +306,43 @@ dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<D
     if (c->ngates > 0 && !c->gates) return fail(ctx, DQ_ERR_INVALID_ARG, "gates is NULL");
     if (c->nparams < 0 || c->nfeatures < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "negative nparams/nfeatures");
     const int n = c->nqubits;
+    std::vector<Prim> prims;
+    prims.reserve((size_t)lowered_count(*c));
+    for (int i = 0; i < c->ngates; ++i) {
+        if ((st = lower_gate(ctx, c, i, prims)) != DQ_OK) return st;
+        if (batch_mode && c->gates[i].data_idx >= 0)
+            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: encoded data is not supported in uneven batches", i);
+    }
     // First pass: count per-row coefficient slots (their row stride).
     int nrows = 0, nshared = 0;
-    for (int i = 0; i < c->ngates; ++i) {
-        const dq_gate &g = c->gates[i];
-        const bool rowwise = (g.data_idx >= 0) || (g.param_idx >= 0 && ppr);
+    for (const Prim &g : prims) {
+        const bool rowwise = (g.didx >= 0) || (g.pidx >= 0 && ppr);
         if (rowwise) ++nrows; else ++nshared;
     }
+    const size_t first = dg.size();
     int ks = *ncoef_shared, kr = 0;
-    for (int i = 0; i < c->ngates; ++i) {
-        const dq_gate &g = c->gates[i];
-        if (g.kind < 0 || g.kind >= DQ_NUM_GATE_KINDS)
-            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: unknown kind %d", i, g.kind);
-        if (g.reserved != 0) return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: reserved field must be 0", i);
+    for (const Prim &g : prims) {
         const bool two = kind_controlled(g.kind) || g.kind == DQ_SWAP;
-        if (g.wires[0] < 0 || g.wires[0] >= n)
-            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: wire %d outside [0, %d)", i, g.wires[0], n);
-        if (two) {
-            if (g.wires[1] < 0 || g.wires[1] >= n)
-                return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: wire %d outside [0, %d)", i, g.wires[1], n);
-            if (g.wires[1] == g.wires[0])
-                return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: control and target coincide", i);
-        }
         const bool par = kind_parametric(g.kind);
-        if (!par && (g.param_idx >= 0 || g.data_idx >= 0))
-            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: kind %d takes no angle", i, g.kind);
-        if (g.param_idx >= 0 && g.data_idx >= 0)
-            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: both param_idx and data_idx set", i);
-        if (g.param_idx >= c->nparams)
-            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: param_idx %d >= nparams %d", i, g.param_idx, c->nparams);
-        if (g.data_idx >= c->nfeatures)
-            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: data_idx %d >= nfeatures %d", i, g.data_idx, c->nfeatures);
-        if (batch_mode && g.data_idx >= 0)
-            return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: encoded data is not supported in uneven batches", i);
         DevGate d{};
         d.kind = g.kind;
         d.cls = gate_class(g.kind);
         if (g.kind == DQ_SWAP) {
-            const int a = n - 1 - g.wires[0], b = n - 1 - g.wires[1];
+            const int a = n - 1 - g.w0, b = n - 1 - g.w1;
             d.t = std::min(a, b);
             d.c = std::max(a, b);
         } else if (two) {
-            d.c = n - 1 - g.wires[0];
-            d.t = n - 1 - g.wires[1];
+            d.c = n - 1 - g.w0;
+            d.t = n - 1 - g.w1;
         } else {
-            d.t = n - 1 - g.wires[0];
+            d.t = n - 1 - g.w0;
             d.c = -1;
         }
-        const bool rowwise = (g.data_idx >= 0) || (g.param_idx >= 0 && ppr);
+        const bool rowwise = (g.didx >= 0) || (g.pidx >= 0 && ppr);
         BindGate b{};
         b.kind = g.kind;
-        b.pidx = g.param_idx >= 0 ? g.param_idx + param_base : -1;
-        b.didx = g.data_idx;
+        b.pidx = g.pidx >= 0 ? g.pidx + param_base : -1;
+        b.didx = g.didx;
         b.angle = g.angle;
         if (rowwise) {
             d.coef = *ncoef_shared + nshared + kr;   // placeholder, fixed below
@@ -256,12 +356,12 @@ dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<D
         }
         d.gkind = 0;
         d.gout = -1;
-        if (par && g.param_idx >= 0) {
+        if (par && g.pidx >= 0) {
             d.gkind = ppr || batch_mode ? 2 : 1;
-            d.gout = g.param_idx;
-        } else if (par && g.data_idx >= 0) {
+            d.gout = g.pidx;
+        } else if (par && g.didx >= 0) {
             d.gkind = 3;
-            d.gout = g.data_idx;
+            d.gout = g.didx;
         }
         b.coef = d.coef;
         dg.push_back(d);
@@ -270,7 +370,7 @@ dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<D
     // Row-wise slots start after every shared slot: [shared...][row 0: k..][row 1: k..]...
     const int shared_end = ks;
     int k = 0;
-    for (size_t i = dg.size() - c->ngates; i < dg.size(); ++i) {
+    for (size_t i = first; i < dg.size(); ++i) {
         if (dg[i].rowstep) {
             dg[i].coef = shared_end + k;
             bg[i].coef = shared_end + k;
@@ -301,7 +401,7 @@ dq_status get_plan(dq_ctx *ctx, const dq_circuit *c, int ppr, Plan **out) {
     if (st != DQ_OK) return st;
     p->key = h;
     p->n = c->nqubits;
-    p->ngates = c->ngates;
+    p->ngates = (int)p->gates.size();
     p->nparams = c->nparams;
     p->nfeat = c->nfeatures;
     p->ppr = ppr;
@@ -1021,7 +1121,7 @@ dq_status dq_batch_workspace_bytes(dq_ctx *ctx, int ncirc, const dq_circuit *cir
     for (int c = 0; c < ncirc; ++c) {
         if ((st = check_n(ctx, circuits[c].nqubits)) != DQ_OK) return st;
         nmax = std::max(nmax, circuits[c].nqubits);
-        ngates += std::max(0, circuits[c].ngates);
+        ngates += lowered_count(circuits[c]);
     }
     const size_t mat = dtype == DQ_C128 ? sizeof(Mat2<double>) : sizeof(Mat2<float>);
     Arena a;
@@ -1236,12 +1336,12 @@ dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit *circui
             BatchCirc x{};
             x.n = circuits[c].nqubits;
             x.gate0 = (int)allg.size();
-            x.ngates = circuits[c].ngates;
             x.param0 = (int)param_offsets[c];
             x.nparams = circuits[c].nparams;
             int ncr = 0;
             st = compile_gates(ctx, &circuits[c], 0, allg, allbind, (int)param_offsets[c], &ncoef, &ncr, true);
             if (st != DQ_OK) return fail(ctx, st, "circuit %d: %s", c, ctx->err.c_str());
+            x.ngates = (int)allg.size() - x.gate0;
             bc[c] = x;
             nmax = std::max(nmax, x.n);
             maxp = std::max(maxp, x.nparams);
@@ -1469,7 +1569,7 @@ extern "C" dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const do
 
     Plan p;
     p.n = n;
-    p.ngates = circuit->ngates;
+    p.ngates = (int)gates.size();
     p.nparams = circuit->nparams;
     p.nfeat = circuit->nfeatures;
     p.ppr = ppr;

@@ -46,7 +46,7 @@ enum GateClass : int {
 __host__ __device__ inline int gate_class(int kind) {
     switch (kind) {
     case DQ_H: case DQ_RY: case DQ_CRY: return CLS_REAL;
-    case DQ_Z: case DQ_S: case DQ_RZ: case DQ_CZ: case DQ_CP: case DQ_CRZ: return CLS_DIAG;
+    case DQ_Z: case DQ_S: case DQ_RZ: case DQ_CZ: case DQ_CP: case DQ_CRZ: case DQ_P: return CLS_DIAG;
     case DQ_X: case DQ_CNOT: return CLS_ANTI;
     case DQ_SWAP: return CLS_SWAP;
     default: return CLS_GENERAL;   // Y, RX, CRX
@@ -57,16 +57,19 @@ __host__ __device__ inline bool kind_controlled(int k) {
     return k == DQ_CNOT || k == DQ_CZ || k == DQ_CP || k == DQ_CRX || k == DQ_CRY || k == DQ_CRZ;
 }
 __host__ __device__ inline bool kind_parametric(int k) {
-    return k == DQ_RX || k == DQ_RY || k == DQ_RZ || k == DQ_CP || k == DQ_CRX || k == DQ_CRY || k == DQ_CRZ;
+    return k == DQ_RX || k == DQ_RY || k == DQ_RZ || k == DQ_CP || k == DQ_CRX || k == DQ_CRY || k == DQ_CRZ ||
+           k == DQ_P;
 }
 
 // Target block of `kind` at angle t, evaluated in double and rounded to R.
-// R_P(t) = cos(t/2) I - i sin(t/2) P;  CP(t): diag(1, e^{i t}).
+// R_P(t) = cos(t/2) I - i sin(t/2) P;  CP(t) and P(t): diag(1, e^{i t}).
+// Only the kinds that reach the kernels (everything but the composite kinds
+// U3, RXX, RYY, RZZ and CCX, which are lowered first).
 template <typename R>
 __host__ __device__ inline Mat2<R> gate_matrix(int kind, double t) {
     double c = 1.0, s = 0.0;
     if (kind_parametric(kind)) {
-        const double h = (kind == DQ_CP) ? t : 0.5 * t;
+        const double h = (kind == DQ_CP || kind == DQ_P) ? t : 0.5 * t;
 #ifdef __CUDA_ARCH__
         sincos(h, &s, &c);
 #else
@@ -84,7 +87,7 @@ __host__ __device__ inline Mat2<R> gate_matrix(int kind, double t) {
     case DQ_RX: case DQ_CRX: a[0] = c; a[3] = -s; a[5] = -s; a[6] = c; break;
     case DQ_RY: case DQ_CRY: a[0] = c; a[2] = -s; a[4] = s; a[6] = c; break;
     case DQ_RZ: case DQ_CRZ: a[0] = c; a[1] = -s; a[6] = c; a[7] = s; break;
-    case DQ_CP: a[6] = c; a[7] = s; break;
+    case DQ_CP: case DQ_P: a[6] = c; a[7] = s; break;
     default: break;
     }
     Mat2<R> m;
@@ -134,8 +137,8 @@ __device__ __forceinline__ void apply2_rt(int cls, const Mat2<R>& u, cx<R>& a0, 
 
 // Contribution of one target pair to dL/dt = 2 Im <lambda| G |psi>, where
 // U(t) = exp(-i t G) and (l0, l1), (p0, p1) are the pair's amplitudes after
-// the gate.  G is P/2 for R_P (restricted to control = |1>) and -|11><11| for
-// CP; the factor 2 is folded in.
+// the gate.  G is P/2 for R_P (restricted to control = |1>), -|11><11| for
+// CP and -|1><1| for P; the factor 2 is folded in.
 template <typename R>
 __device__ __forceinline__ R grad_pair(int kind, cx<R> l0, cx<R> l1, cx<R> p0, cx<R> p1) {
     switch (kind) {
@@ -145,7 +148,7 @@ __device__ __forceinline__ R grad_pair(int kind, cx<R> l0, cx<R> l1, cx<R> p0, c
         return -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
     case DQ_RZ: case DQ_CRZ:   // Im(conj(l0) p0 - conj(l1) p1)
         return (l0.x * p0.y - l0.y * p0.x) - (l1.x * p1.y - l1.y * p1.x);
-    case DQ_CP:                // 2 Im(conj(l1) (-p1))
+    case DQ_CP: case DQ_P:     // 2 Im(conj(l1) (-p1))
         return (R)(-2) * (l1.x * p1.y - l1.y * p1.x);
     default:
         return (R)0;

@@ -632,11 +632,12 @@ __device__ __forceinline__ R adj_pairs_sel(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 <<
     return g;
 }
 
-// Diagonal generator weights: RZ/CRZ +1 on target 0, -1 on target 1; CP 0 / -2.
+// Diagonal generator weights: RZ/CRZ +1 on target 0, -1 on target 1; CP and P 0 / -2.
 template <typename R>
 __device__ __forceinline__ void diag_weights(int kind, R &w0, R &w1) {
-    w0 = (kind == DQ_CP) ? R(0) : R(1);
-    w1 = (kind == DQ_CP) ? R(-2) : R(-1);
+    const bool ph = kind == DQ_CP || kind == DQ_P;
+    w0 = ph ? R(0) : R(1);
+    w1 = ph ? R(-2) : R(-1);
 }
 
 template <typename R, int M, int P, bool GRAD>

@@ -33,7 +33,19 @@ def rotation(P, theta):
     return expm(-0.5j * theta * P)
 
 
+def u3_euler(theta, phi, lam):
+    """U3 by the Z-Y-Z Euler decomposition of a one-qubit unitary (Nielsen &
+    Chuang, Theorem 4.1): e^{i(phi+lam)/2} R_Z(phi) R_Y(theta) R_Z(lam), the
+    global phase chosen so that the (0, 0) entry cos(theta/2) is real."""
+    return np.exp(0.5j * (phi + lam)) * rotation(Z, phi) @ rotation(Y, theta) @ rotation(Z, lam)
+
+
 def one_qubit(kind, theta):
+    if kind == "u3":
+        return u3_euler(*theta)
+    if kind == "p":
+        # phase shift = exp(i t |1><1|)
+        return expm(1j * theta * P1)
     if kind == "h":
         return (X + Z) / np.sqrt(2.0)
     if kind == "x":
@@ -51,7 +63,14 @@ def gate_operator(n, kind, wires, theta):
     """Dense operator of one gate on n qubits."""
     if len(wires) == 1:
         return embed(n, {wires[0]: one_qubit(kind, theta)})
+    if kind == "ccx":
+        c0, c1, t = wires
+        # identity off the |11> control subspace, X on it
+        return embed(n, {}) - embed(n, {c0: P1, c1: P1}) + embed(n, {c0: P1, c1: P1, t: X})
     a, b = wires
+    if kind in ("rxx", "ryy", "rzz"):
+        P = {"rxx": X, "ryy": Y, "rzz": Z}[kind]
+        return expm(-0.5j * theta * embed(n, {a: P, b: P}))
     if kind == "swap":
         # SWAP = (II + XX + YY + ZZ) / 2
         return 0.5 * (embed(n, {}) + embed(n, {a: X, b: X}) + embed(n, {a: Y, b: Y})
@@ -68,6 +87,11 @@ def gate_operator(n, kind, wires, theta):
 
 
 def angle_of(g, params, data_row):
+    """The gate's angle (U3: the tuple theta, phi, lam from consecutive slots)."""
+    if g.kind == "u3":
+        if g.param >= 0:
+            return tuple(float(params[g.param + k]) for k in range(3))
+        return tuple(float(data_row[g.data + k]) for k in range(3))
     if g.param >= 0:
         return float(params[g.param])
     if g.data >= 0:

@@ -36,26 +36,29 @@ def ctx():
 
 
 def random_gates(n, depth, rng, nfeat=0, kinds=None):
+    """Random gates over every kind (U3 reads three consecutive parameter or
+    feature slots and never takes a fixed angle)."""
     kinds = kinds or W.GATE_KINDS
     gates, npar = [], 0
     while len(gates) < depth:
         k = kinds[rng.integers(len(kinds))]
-        if k in W.TWO_QUBIT:
-            if n < 2:
+        if k in W.TWO_QUBIT or k in W.THREE_QUBIT:
+            nw = 3 if k in W.THREE_QUBIT else 2
+            if n < nw:
                 continue
-            a, b = rng.choice(n, size=2, replace=False)
-            wires = (int(a), int(b))
+            wires = tuple(int(w) for w in rng.choice(n, size=nw, replace=False))
         else:
             wires = (int(rng.integers(n)),)
+        span = W.ANGLE_SPAN.get(k, 1)
         if k in W.PARAMETRIC:
             u = rng.random()
-            if nfeat and u < 0.25:
-                gates.append(W.Gate(k, wires, data=int(rng.integers(nfeat))))
-            elif u < 0.35:
+            if nfeat >= span and u < 0.25:
+                gates.append(W.Gate(k, wires, data=int(rng.integers(nfeat - span + 1))))
+            elif span == 1 and u < 0.35:
                 gates.append(W.Gate(k, wires, angle=float(rng.uniform(-4, 4))))
             else:
                 gates.append(W.Gate(k, wires, param=npar))
-                npar += 1
+                npar += span
         else:
             gates.append(W.Gate(k, wires))
     return gates, max(npar, 1)
@@ -76,8 +79,15 @@ def edge_gates(n):
         for a, b in sorted(pairs):
             for k in ("cnot", "cz", "swap"):
                 g.append(W.Gate(k, (a, b)))
-            for k in ("cp", "crx", "cry", "crz"):
+            for k in ("cp", "crx", "cry", "crz", "rxx", "ryy", "rzz"):
                 g.append(W.Gate(k, (a, b), angle=1.1 + 0.1 * a))
+    for q in sorted({hi, lo, n // 2}):
+        g.append(W.Gate("p", (q,), angle=0.6 - q))
+    if n >= 3:
+        mid = n // 2 if n // 2 not in (hi, lo) else 1
+        for c0, c1, t in ((hi, lo, mid), (lo, mid, hi), (mid, hi, lo), (n - 3, n - 2, n - 1), (2, 1, 0)):
+            g.append(W.Gate("h", (t,)))
+            g.append(W.Gate("ccx", (c0, c1, t)))
     return g
 
 
@@ -441,7 +451,8 @@ def test_empty_and_degenerate(ctx):
 
 
 @pytest.mark.parametrize("bad", ["wire", "same", "kind", "param", "data_missing", "fixed_angle_param",
-                                 "reserved", "dtype", "null_state", "misaligned"])
+                                 "u3_fixed", "u3_span", "ccx_same", "ccx_wire", "dtype", "null_state",
+                                 "misaligned"])
 def test_invalid_arguments_are_rejected(ctx, bad):
     n = 4
     st = torch.empty((1, 16), dtype=torch.complex64, device="cuda")
@@ -466,9 +477,16 @@ def test_invalid_arguments_are_rejected(ctx, bad):
     elif bad == "fixed_angle_param":
         gates = [W.Gate("h", (0,), param=0)]
         circ_kw = {"nparams": 1}
+    elif bad == "u3_fixed":
+        gates = [W.Gate("u3", (0,), angle=0.5)]
+    elif bad == "u3_span":
+        gates = [W.Gate("u3", (0,), param=0)]
+        circ_kw = {"nparams": 2}
+    elif bad == "ccx_same":
+        gates = [W.Gate("ccx", (0, 2, 0))]
+    elif bad == "ccx_wire":
+        gates = [W.Gate("ccx", (0, 1, 4))]
     circ = dq.Circuit(n, gates, **circ_kw)
-    if bad == "reserved":
-        circ._arr[0].reserved = 3
     with pytest.raises(dq.DQError) as ei:
         if bad == "dtype":
             ctx.lib.dq_state_init(ctx.h, n, 1, 7, st.data_ptr(), None) and ctx._check(7 and 1, "x")

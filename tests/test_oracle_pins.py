@@ -27,27 +27,29 @@ RNG = np.random.default_rng(1234)
 
 
 def random_gates(n, depth, rng, nparams_box, data_features=0, kinds=None):
-    """Random gate list over every kind; parameters each used once."""
+    """Random gate list over every kind; parameters each used once (U3 takes
+    three consecutive slots and never a fixed angle)."""
     kinds = kinds or W.GATE_KINDS
     gates = []
     np_ = 0
     for _ in range(depth):
         k = kinds[rng.integers(len(kinds))]
-        if k in W.TWO_QUBIT:
-            if n < 2:
+        if k in W.TWO_QUBIT or k in W.THREE_QUBIT:
+            nw = 3 if k in W.THREE_QUBIT else 2
+            if n < nw:
                 continue
-            a, b = rng.choice(n, size=2, replace=False)
-            wires = (int(a), int(b))
+            wires = tuple(int(w) for w in rng.choice(n, size=nw, replace=False))
         else:
             wires = (int(rng.integers(n)),)
+        span = W.ANGLE_SPAN.get(k, 1)
         if k in W.PARAMETRIC:
-            if data_features and rng.random() < 0.3:
-                gates.append(Gate(k, wires, data=int(rng.integers(data_features))))
-            elif rng.random() < 0.15:
+            if data_features >= span and rng.random() < 0.3:
+                gates.append(Gate(k, wires, data=int(rng.integers(data_features - span + 1))))
+            elif span == 1 and rng.random() < 0.15:
                 gates.append(Gate(k, wires, angle=float(rng.uniform(-4, 4))))
             else:
                 gates.append(Gate(k, wires, param=np_))
-                np_ += 1
+                np_ += span
         else:
             gates.append(Gate(k, wires))
     nparams_box.append(np_)
@@ -121,6 +123,33 @@ def pin_failures(oracle, lib=None):
         fm = oracle.expect(n, oracle.run(n, gates, params - e, lib=lib), obs, lib=lib)[0, 0]
         fd[p] = (fp - fm) / (2 * h)
     check("adjoint-fd", np.allclose(gp, fd, atol=1e-8))
+    # U3 against the Z-Y-Z Euler form; RXX/RYY/RZZ against expm; CCX truth table
+    for th, ph, la in ((0.3, -1.2, 2.1), (2.5, 0.4, -0.9)):
+        got = oracle.apply(1, [Gate("u3", (0,), param=0)], np.eye(2), np.array([th, ph, la]), lib=lib)
+        check("u3-euler", np.allclose(got.T, D.u3_euler(th, ph, la), atol=1e-14))
+    for kind in ("rxx", "ryy", "rzz"):
+        got = oracle.apply(3, [Gate(kind, (2, 0), angle=0.9)], np.eye(8), lib=lib)
+        check(f"pair-{kind}", np.allclose(got.T, D.gate_operator(3, kind, (2, 0), 0.9), atol=1e-14))
+    got = oracle.apply(3, [Gate("ccx", (2, 0, 1))], np.eye(8), lib=lib)
+    check("ccx", np.allclose(got.T, D.gate_operator(3, "ccx", (2, 0, 1), 0.0), atol=1e-15))
+    # adjoint gradient vs central differences for the wider gate set, with
+    # encoded U3 angles (grad_data)
+    n = 3
+    box = []
+    gates = random_gates(n, 24, rng, box, data_features=3, kinds=("h", "p", "u3", "rxx", "ryy", "rzz", "ccx",
+                                                                     "cnot", "ry"))
+    params = rng.uniform(-3, 3, size=max(box[0], 1))
+    data = rng.uniform(-3, 3, size=(1, 3))
+    obs = [[(1.0, 0b011, 0b001), (0.5, 0b100, 0), (0.8, 0, 0b110)]]
+    _, gp, gd = oracle.adjoint(n, gates, obs, params, data, lib=lib)
+
+    def f(pv, dv):
+        return oracle.expect(n, oracle.run(n, gates, pv, dv, lib=lib), obs, lib=lib)[0, 0]
+
+    h = 1e-5
+    fd = np.array([(f(params + h * e, data) - f(params - h * e, data)) / (2 * h) for e in np.eye(params.size)])
+    fdd = np.array([(f(params, data + h * e) - f(params, data - h * e)) / (2 * h) for e in np.eye(3)])
+    check("adjoint-fd-wide", np.allclose(gp, fd, atol=1e-8) and np.allclose(gd[0], fdd, atol=1e-8))
     # dense block on the low wires = I (x) U as a Kronecker product
     n, nw = 5, 3
     U = W.random_unitary(nw, 11)
@@ -322,6 +351,124 @@ def test_distributed_example_four_qubits(oracle_mod):
 
 
 # ---------------------------------------------------------------------------
+# the wider gate set: P, U3, RXX / RYY / RZZ, CCX
+# ---------------------------------------------------------------------------
+def _u3(oracle_mod, th, ph, la):
+    return oracle_mod.apply(1, [Gate("u3", (0,), param=0)], np.eye(2), np.array([th, ph, la])).T
+
+
+def test_u3_special_cases_and_bloch_column(oracle_mod):
+    """U3(t, 0, 0) = RY(t); U3(t, -pi/2, pi/2) = RX(t); U3(0, 0, l) = P(l) =
+    diag(1, e^{il}); U3|0> = cos(t/2)|0> + e^{i phi} sin(t/2)|1> (the Bloch
+    form of the Background section); U3 is unitary."""
+    for t in np.linspace(-5, 5, 11):
+        np.testing.assert_allclose(_u3(oracle_mod, t, 0, 0), D.rotation(D.Y, t), atol=1e-14)
+        np.testing.assert_allclose(_u3(oracle_mod, t, -math.pi / 2, math.pi / 2), D.rotation(D.X, t), atol=1e-14)
+        np.testing.assert_allclose(_u3(oracle_mod, 0, 0, t), np.diag([1, np.exp(1j * t)]), atol=1e-14)
+        ph, la = 0.37 * t + 0.2, -0.6 * t
+        U = _u3(oracle_mod, t, ph, la)
+        np.testing.assert_allclose(U[:, 0], [math.cos(t / 2), np.exp(1j * ph) * math.sin(t / 2)], atol=1e-14)
+        np.testing.assert_allclose(U.conj().T @ U, np.eye(2), atol=1e-14)
+        np.testing.assert_allclose(U, D.u3_euler(t, ph, la), atol=1e-14)
+
+
+def test_phase_shift_special_cases(oracle_mod):
+    """P(pi/2) = S, P(pi) = Z, P(t) = e^{it/2} RZ(t)."""
+    basis = np.eye(2)
+    S = oracle_mod.apply(1, [Gate("p", (0,), angle=math.pi / 2)], basis).T
+    Zm = oracle_mod.apply(1, [Gate("p", (0,), angle=math.pi)], basis).T
+    np.testing.assert_allclose(S, D.one_qubit("s", 0), atol=1e-15)
+    np.testing.assert_allclose(Zm, D.Z, atol=1e-15)
+    for t in (-2.2, 0.4, 3.0):
+        Pm = oracle_mod.apply(1, [Gate("p", (0,), angle=t)], basis).T
+        np.testing.assert_allclose(Pm, np.exp(0.5j * t) * D.rotation(D.Z, t), atol=1e-14)
+
+
+@pytest.mark.parametrize("kind", ["rxx", "ryy", "rzz"])
+def test_two_qubit_rotations_match_expm(oracle_mod, kind):
+    """R_PP(t) = exp(-i t P(x)P / 2) on every ordered wire pair of 4 qubits."""
+    n = 4
+    for a in range(n):
+        for b in range(n):
+            if a == b:
+                continue
+            t = 0.3 + a - 0.7 * b
+            got = oracle_mod.apply(n, [Gate(kind, (a, b), angle=t)], np.eye(1 << n)).T
+            np.testing.assert_allclose(got, D.gate_operator(n, kind, (a, b), t), atol=1e-13)
+
+
+def test_rzz_phases_by_parity(oracle_mod):
+    """RZZ(t)|b> = e^{-it/2}|b> when the two bits agree, e^{+it/2}|b> otherwise
+    (Z(x)Z has eigenvalue +1 on equal bits)."""
+    n, t = 3, 1.3
+    got = oracle_mod.apply(n, [Gate("rzz", (0, 2), angle=t)], np.eye(1 << n)).T
+    for i in range(1 << n):
+        same = ((i >> 2) & 1) == (i & 1)
+        assert abs(got[i, i] - np.exp(-0.5j * t if same else 0.5j * t)) < 1e-15
+    assert np.allclose(got - np.diag(np.diag(got)), 0)
+
+
+def test_ccx_truth_table(oracle_mod):
+    """CCX flips the target exactly when both controls are 1, for every
+    assignment of the three roles to wires of a 4-qubit register."""
+    n = 4
+    import itertools
+    for c0, c1, t in itertools.permutations(range(n), 3):
+        got = oracle_mod.apply(n, [Gate("ccx", (c0, c1, t))], np.eye(1 << n)).T
+        for i in range(1 << n):
+            bits = [(i >> (n - 1 - q)) & 1 for q in range(n)]
+            j = i ^ (1 << (n - 1 - t)) if bits[c0] and bits[c1] else i
+            assert got[j, i] == 1 and abs(got[:, i]).sum() == 1
+
+
+def test_two_qubit_rotations_parameter_shift(oracle_mod):
+    """The two-term shift rule is exact for R_PP(t) = exp(-i t P(x)P/2) (the
+    generator P(x)P/2 has eigenvalues +-1/2)."""
+    n = 4
+    rng = np.random.default_rng(17)
+    box = []
+    gates = random_gates(n, 30, rng, box, kinds=("h", "rxx", "ryy", "rzz", "cnot", "ccx"))
+    gates = [g if g.param >= 0 or g.kind not in W.PARAMETRIC else g._replace(angle=0.4) for g in gates]
+    params = rng.uniform(0, 2 * math.pi, size=box[0])
+    obs = [W.obs_tfim_open(n, 0.5)]
+    _, gp, _ = oracle_mod.adjoint(n, gates, obs, params)
+    for p in range(params.size):
+        e = np.zeros_like(params)
+        e[p] = math.pi / 2
+        fp = oracle_mod.expect(n, oracle_mod.run(n, gates, params + e), obs)[0, 0]
+        fm = oracle_mod.expect(n, oracle_mod.run(n, gates, params - e), obs)[0, 0]
+        assert abs(gp[p] - 0.5 * (fp - fm)) < 1e-12
+
+
+def test_u3_gradients_finite_differences(oracle_mod):
+    """Adjoint gradients of U3 angles (trainable and encoded, per row) against
+    central differences."""
+    n, batch = 3, 2
+    gates = [Gate("u3", (0,), param=0), Gate("u3", (1,), data=0), Gate("cnot", (0, 2)),
+             Gate("u3", (2,), param=3), Gate("ccx", (0, 1, 2)), Gate("u3", (1,), param=6),
+             Gate("rxx", (1, 2), data=3)]
+    rng = np.random.default_rng(4)
+    params = rng.uniform(-3, 3, size=9)
+    data = rng.uniform(-3, 3, size=(batch, 4))
+    obs = [[(1.0, 0b001, 0b011), (0.6, 0b110, 0)]]
+    _, gp, gd = oracle_mod.adjoint(n, gates, obs, params, data, batch=batch)
+
+    def loss(pv, dv):
+        return oracle_mod.expect(n, oracle_mod.run(n, gates, pv, dv, batch=batch), obs).sum()
+
+    h = 1e-6
+    for i in range(params.size):
+        e = np.zeros(params.size)
+        e[i] = h
+        assert abs(gp[i] - (loss(params + e, data) - loss(params - e, data)) / (2 * h)) < 1e-7
+    for i in range(data.size):
+        e = np.zeros(data.size)
+        e[i] = h
+        dp, dm = (data.reshape(-1) + e).reshape(data.shape), (data.reshape(-1) - e).reshape(data.shape)
+        assert abs(gd.reshape(-1)[i] - (loss(params, dp) - loss(params, dm)) / (2 * h)) < 1e-7
+
+
+# ---------------------------------------------------------------------------
 # planted mistakes: each mutant of the oracle must fail at least one pin
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("n,nw", [(3, 1), (5, 3), (7, 6), (6, 6)])
@@ -391,6 +538,18 @@ MUTANTS = {
                      "            psi[j] = psi[i];\n"),
     "hadamard-sign": ("case O_H:    m[0] = r;  m[1] = r;   m[2] = r;  m[3] = -r;",
                       "case O_H:    m[0] = r;  m[1] = r;   m[2] = r;  m[3] = r;"),
+    "u3-phi-lam-swapped": ("case 0: m[0] = ch;        m[1] = -el * sh;      m[2] = ep * sh;",
+                           "case 0: m[0] = ch;        m[1] = -ep * sh;      m[2] = el * sh;"),
+    "u3-dphi-dropped-phase": ("case 2: m[0] = 0;         m[1] = 0;             m[2] = I * ep * sh;",
+                              "case 2: m[0] = 0;         m[1] = 0;             m[2] = ep * sh;"),
+    "phase-shift-sign": ("case O_P:    m[0] = 1;  m[1] = 0;   m[2] = 0;  m[3] = cexp(I * t);",
+                         "case O_P:    m[0] = 1;  m[1] = 0;   m[2] = 0;  m[3] = cexp(-I * t);"),
+    "ryy-as-rxx": ("*zm = (kind == O_RZZ || kind == O_RYY) ? w : 0;",
+                   "*zm = (kind == O_RZZ) ? w : 0;"),
+    "pair-generator-unhalved": ("for (int64_t i = 0; i < dim; ++i) tmp[i] *= 0.5;",
+                                "for (int64_t i = 0; i < dim; ++i) tmp[i] *= 1.0;"),
+    "ccx-one-control": ("if ((i & tb) || !(i & b0) || !(i & b1)) continue;",
+                        "if ((i & tb) || !(i & b0)) continue;"),
 }
 
 

@@ -11,10 +11,13 @@ notes):
 
 * A gate is ``Gate(kind, wires, param, data, angle)``.  ``kind`` is one of
   :data:`GATE_KINDS`; ``wires`` is ``(target,)`` for one-qubit gates,
-  ``(control, target)`` for controlled gates and ``(a, b)`` for SWAP.  The
-  rotation angle is ``params[param]`` when ``param >= 0``, else
+  ``(control, target)`` for controlled gates, ``(a, b)`` for SWAP and the
+  two-qubit rotations RXX/RYY/RZZ, and ``(control0, control1, target)`` for
+  CCX.  The rotation angle is ``params[param]`` when ``param >= 0``, else
   ``data[row, data]`` when ``data >= 0`` (an encoded input feature, the
   ``encode=True`` gates of the paper's qubit API), else the fixed ``angle``.
+  U3 reads its three angles (theta, phi, lam) from ``params[param + 0..2]``
+  or ``data[row, data + 0..2]``.
 * A Pauli term is ``(coeff, xmask, zmask)`` with bit ``q`` of a mask
   referring to wire ``q``; a wire with both bits set carries ``Y``.  An
   observable is a list of terms whose weighted sum is measured.
@@ -35,10 +38,14 @@ GATE_KINDS = (
     "rx", "ry", "rz",
     "cnot", "cz", "cp", "swap",
     "crx", "cry", "crz",
+    "p", "u3", "rxx", "ryy", "rzz", "ccx",
 )
-ONE_QUBIT = {"h", "x", "y", "z", "s", "rx", "ry", "rz"}
-TWO_QUBIT = {"cnot", "cz", "cp", "swap", "crx", "cry", "crz"}
-PARAMETRIC = {"rx", "ry", "rz", "cp", "crx", "cry", "crz"}
+ONE_QUBIT = {"h", "x", "y", "z", "s", "rx", "ry", "rz", "p", "u3"}
+TWO_QUBIT = {"cnot", "cz", "cp", "swap", "crx", "cry", "crz", "rxx", "ryy", "rzz"}
+THREE_QUBIT = {"ccx"}
+PARAMETRIC = {"rx", "ry", "rz", "cp", "crx", "cry", "crz", "p", "u3", "rxx", "ryy", "rzz"}
+# consecutive parameter / feature slots a gate reads (U3: theta, phi, lam)
+ANGLE_SPAN = {"u3": 3}
 
 MASK64 = (1 << 64) - 1
 BASE_SEED = 0x2512_18995
@@ -155,6 +162,79 @@ def qft_gates(n: int, swaps: bool = True) -> List[Gate]:
     return gates
 
 
+def qcnn_gates(n: int = 12) -> Tuple[List[Gate], int, int]:
+    """The QCNN of the paper's Quantum Machine Learning section, as a gate
+    list: features are angle-encoded by RY on the active wires, each
+    convolution puts RXX then RYY on neighbouring pairs (0,1), (2,3), ...,
+    each pooling applies CRY with control 2i+1 and target 2i, halving the
+    active wires 12 -> 6 -> 3; the last stage convolves (0,1), (1,2) and pools
+    with CRY(1 -> 0), CRY(2 -> 0).  Every RXX/RYY/CRY owns a parameter.
+    Returns (gates, nparams, nfeatures)."""
+    gates: List[Gate] = []
+    npar = nfeat = 0
+
+    def encode(m):
+        nonlocal nfeat
+        for q in range(m):
+            gates.append(Gate("ry", (q,), data=nfeat))
+            nfeat += 1
+
+    def pair(kind, a, b):
+        nonlocal npar
+        gates.append(Gate(kind, (a, b), param=npar))
+        npar += 1
+
+    m = n
+    encode(m)
+    while m > 3:
+        for i in range(0, m - 1, 2):
+            pair("rxx", i, i + 1)
+            pair("ryy", i, i + 1)
+        for i in range(m // 2):
+            pair("cry", 2 * i + 1, 2 * i)
+        m //= 2
+        encode(m)
+    for i in range(m - 1):
+        pair("rxx", i, i + 1)
+        pair("ryy", i, i + 1)
+    for c in range(1, m):
+        pair("cry", c, 0)
+    return gates, npar, nfeat
+
+
+def qnn_u3_gates(residual: bool) -> Tuple[int, List[Gate], int, int, List[List[Term]]]:
+    """The small data re-uploading QNNs of the paper's Quantum Machine Learning
+    section.  Plain: one qubit, U3, RY(x), U3, measured in Z.  Residual: two
+    qubits, RY on wire 0 and U3 on wire 1, an encoded RY(x) on wire 1
+    controlled by wire 0, then RY and U3 again; observables Z_1 and Z_0 Z_1.
+    Returns (n, gates, nparams, nfeatures, observables)."""
+    if not residual:
+        g = [Gate("u3", (0,), param=0), Gate("ry", (0,), data=0), Gate("u3", (0,), param=3)]
+        return 1, g, 6, 1, [obs_z(0)]
+    g = [Gate("ry", (0,), param=0), Gate("u3", (1,), param=1), Gate("cry", (0, 1), data=0),
+         Gate("ry", (0,), param=4), Gate("u3", (1,), param=5)]
+    return 2, g, 8, 1, [obs_z(1), [pauli_term(1.0, {0: "Z", 1: "Z"})]]
+
+
+def tfim_trotter_gates(n: int, steps: int, J: float = 1.0, h: float = 1.2, dt: float = 0.1,
+                       periodic: bool = True) -> List[Gate]:
+    """Second-order (Strang) Trotterisation of H = -J sum Z_i Z_{i+1} - h sum X_i
+    on a chain: per step exp(-i H_x dt/2) exp(-i H_zz dt) exp(-i H_x dt/2),
+    i.e. RX(-h dt) on every wire, RZZ(-2 J dt) on the even bonds, the odd
+    bonds and (periodic) the bond (n-1, 0), then RX(-h dt) again
+    (RX(t) = exp(-i t X / 2), RZZ(t) = exp(-i t Z Z / 2)).  Fixed angles."""
+    gates: List[Gate] = []
+    for _ in range(steps):
+        gates += [Gate("rx", (q,), angle=-h * dt) for q in range(n)]
+        for start in (0, 1):
+            for i in range(start, n - 1, 2):
+                gates.append(Gate("rzz", (i, i + 1), angle=-2.0 * J * dt))
+        if periodic and n > 2:
+            gates.append(Gate("rzz", (n - 1, 0), angle=-2.0 * J * dt))
+        gates += [Gate("rx", (q,), angle=-h * dt) for q in range(n)]
+    return gates
+
+
 def random_circuit(seed: int, nmin: int = 8, nmax: int = 16, dmin: int = 10, dmax: int = 40,
                    kinds: Sequence[str] = ("h", "rx", "ry", "rz", "cnot", "cz")):
     """One circuit of the uneven batch: returns (n, gates, angles).
@@ -162,8 +242,9 @@ def random_circuit(seed: int, nmin: int = 8, nmax: int = 16, dmin: int = 10, dma
     Draw order from one splitmix64 stream: n ~ U{nmin..nmax}, depth ~
     U{dmin..dmax}; then per gate: kind ~ U(kinds); a one-qubit target ~ U{0..n-1}
     or an ordered pair of distinct wires (control first, then target drawn from
-    the remaining n-1 wires); for rotations an angle ~ U[0, 2pi).  Each rotation
-    owns one parameter (its own index), so gradients are per circuit.
+    the remaining n-1 wires), or three distinct wires drawn the same way; for
+    rotations an angle ~ U[0, 2pi) per angle slot.  Each rotation owns its
+    parameters (its own indices), so gradients are per circuit.
     """
     rng = SplitMix64(seed)
     n = rng.integer(nmin, nmax)
@@ -178,11 +259,21 @@ def random_circuit(seed: int, nmin: int = 8, nmax: int = 16, dmin: int = 10, dma
             if t >= c:
                 t += 1
             wires = (c, t)
+        elif kind in THREE_QUBIT:
+            picked: List[int] = []
+            for k in range(3):
+                w = rng.integer(0, n - 1 - k)
+                for p in sorted(picked):
+                    if w >= p:
+                        w += 1
+                picked.append(w)
+            wires = tuple(picked)
         else:
             wires = (rng.integer(0, n - 1),)
         if kind in PARAMETRIC:
             gates.append(Gate(kind, wires, param=len(angles)))
-            angles.append(rng.uniform_range(0.0, 2.0 * math.pi))
+            for _ in range(ANGLE_SPAN.get(kind, 1)):
+                angles.append(rng.uniform_range(0.0, 2.0 * math.pi))
         else:
             gates.append(Gate(kind, wires))
     return n, gates, np.asarray(angles, dtype=np.float64)
