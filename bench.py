@@ -320,6 +320,9 @@ def our_arm(args, rank, world, dist):
         extras["dense_block"] = dense_block(ctx, device, hbm_peak, peak_kind)
         extras["uneven_batch"] = uneven_batch(ctx, device)
         extras["qft_tfim30"] = qft_tfim30(ctx, device)
+        extras["qcnn"] = qcnn_batch(ctx, device)
+        extras["trotter30"] = trotter30(ctx, device)
+        extras["sample30"] = sample30(ctx, device, hbm_peak, peak_kind)
         ctx.set_path({"auto": dq.PATH_AUTO, "plain": dq.PATH_PLAIN, "fused": dq.PATH_FUSED}[args.path])
 
     if rank == 0:
@@ -441,6 +444,109 @@ def qft_tfim30(ctx, device):
     torch.cuda.empty_cache()
     out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
     out["workload"] = "c5_qft_tfim30_c64"
+    return out
+
+
+def trotter30(ctx, device, steps=5):
+    """Trotterised TFIM quench on 30 qubits (8 GiB complex64): `steps`
+    second-order Trotter steps (RX half steps and RZZ on every bond of the
+    periodic chain, fixed angles) from |0...0>, then <H>; fused path vs
+    per-gate path.  Gate-equivalent bandwidth counts one read and one write
+    of the state per gate of the circuit as written (RZZ counted once)."""
+    import torch
+    import paper_2512_18995_gb300 as dq
+    n = 30
+    gates = W.tfim_trotter_gates(n, steps)
+    circ = dq.Circuit(n, gates, nparams=0)
+    H = dq.Observables([[W.pauli_term(-1.0, {i: "Z", (i + 1) % n: "Z"}) for i in range(n)]
+                        + [W.pauli_term(-1.2, {i: "X"}) for i in range(n)]])
+    out = {}
+    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+        ctx.set_path(path)
+        try:
+            ctx.forward_grad(circ, None, H, 1, torch.complex64, want_grad=False)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.forward_grad(circ, None, H, 1, torch.complex64, want_grad=False)
+            b.record()
+            torch.cuda.synchronize()
+        except RuntimeError as exc:   # not enough device memory
+            ctx.set_path(dq.PATH_AUTO)
+            return {"skipped": str(exc)[:120]}
+        ms = a.elapsed_time(b)
+        out[name] = {"ms_per_step": ms,
+                     "gate_equiv_GBps": len(gates) * 2 * (8 << n) / (ms / 1e3) / 1e9}
+    ctx.set_path(dq.PATH_AUTO)
+    ctx.release_workspace()
+    torch.cuda.empty_cache()
+    out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
+    out["workload"] = f"tfim_trotter30_{steps}steps_c64"
+    out["gates"] = len(gates)
+    return out
+
+
+def sample30(ctx, device, hbm_peak, peak_kind, n=30, shots=1 << 20, reps=3):
+    """2^20 shots from a 30-qubit complex64 state (8 GiB): one streaming pass
+    for the cumulative sums, then per shot a search over group prefixes, a
+    scan of up to 1024 chunk sums and of one 256-amplitude chunk.  Algorithmic
+    HBM bytes: the state once plus 2 KiB of amplitudes per shot."""
+    import torch
+    try:
+        gen = torch.Generator(device=device).manual_seed(30)
+        st = torch.randn((1, 1 << n), dtype=torch.complex64, device=device, generator=gen)
+        out = torch.empty((1, shots), dtype=torch.int64, device=device)
+        ctx.sample(n, st, shots, seed=1, out=out)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for r in range(reps):
+            ctx.sample(n, st, shots, seed=2 + r, out=out)
+        b.record()
+        torch.cuda.synchronize()
+    except RuntimeError as exc:
+        return {"skipped": str(exc)[:120]}
+    ms = a.elapsed_time(b) / reps
+    nbytes = (8 << n) + shots * 256 * 8
+    del st, out
+    ctx.release_workspace()
+    torch.cuda.empty_cache()
+    return {"workload": "sample_30q_1Mshots_c64", "ms_per_call": ms, "shots_per_s": shots / (ms / 1e3),
+            "GBps": nbytes / (ms / 1e3) / 1e9, "frac": nbytes / (ms / 1e3) / 1e9 / hbm_peak,
+            "peak_kind": peak_kind}
+
+
+def qcnn_batch(ctx, device, batch=4096, steps=5):
+    """The 12-qubit QCNN (RY encodings, RXX/RYY convolutions, CRY pooling; 33
+    parameters, 21 features per row) on 4096 rows: <Z_0>, gradients with
+    respect to the parameters and to every feature; fused vs per-gate path."""
+    import torch
+    import paper_2512_18995_gb300 as dq
+    gates, npar, nfeat = W.qcnn_gates(12)
+    circ = dq.Circuit(12, gates, nparams=npar, nfeatures=nfeat)
+    obs = dq.Observables([W.obs_z(0)])
+    params = torch.tensor(W.uniform_array(71, npar, 0.0, 2 * np.pi), device=device)
+    data = torch.tensor(W.uniform_array(72, batch * nfeat, -np.pi, np.pi).reshape(batch, nfeat), device=device)
+    out = {}
+    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+        ctx.set_path(path)
+        for _ in range(2):
+            ctx.forward_grad(circ, params, obs, batch, torch.complex64, data=data)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            ctx.forward_grad(circ, params, obs, batch, torch.complex64, data=data)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out[name] = {"ms_per_step": ms, "grads_per_s": batch * (npar + nfeat) / (ms / 1e3)}
+    ctx.set_path(dq.PATH_AUTO)
+    out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
+    out["workload"] = "qcnn12x4096_c64"
     return out
 
 

@@ -352,6 +352,32 @@ DQ_API dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const double
 DQ_API dq_status dq_apply_dense(dq_ctx *ctx, int nqubits, int nw, const double *unitary, void *state,
                                 int batch, int dtype, void *stream);
 
+/* Shot sampling (API Overview: measure(shots, wires) -- outcomes drawn with
+ * the Born probabilities |psi_i|^2 of the current state).  For row r and shot
+ * s, with u = the uniform of that shot in [0, 1), the outcome is the smallest
+ * basis index i with u * Z < p_0 + ... + p_i, p_i = |psi_r[i]|^2 and Z the
+ * row's total probability (inversion of the cumulative distribution; Z
+ * absorbs the rounding of the norm).  Outcomes of zero probability are never
+ * drawn.  A target within rounding of a cumulative boundary may select either
+ * neighbour; both are valid outcomes for it.
+ *   state:     device, batch rows of 2^nqubits amplitudes of `dtype`, read only.
+ *   uniforms:  device FP64, batch * shots values in [0, 1), row-major; or
+ *              NULL, in which case shot k = r * shots + s uses output k of the
+ *              splitmix64 stream seeded with `seed` (Steele, Lea & Flood,
+ *              OOPSLA 2014), mapped to [0, 1) by its top 53 bits.
+ *   wire_mask: 0 for the full basis index; otherwise bit q selects wire q and
+ *              the outcome packs the selected wires' bits, the lowest selected
+ *              wire in the most significant position (the marginal outcome of
+ *              those wires).  Bits at or above nqubits are invalid.
+ *   out:       device int64, batch * shots outcomes.
+ * Uses sample_workspace_bytes of workspace (dq_sample_workspace_bytes); the
+ * state is streamed once, then each shot reads 2^8 amplitudes and up to 2^10
+ * partial sums.  A row of zeros returns 2^nqubits - 1. */
+DQ_API dq_status dq_sample_workspace_bytes(dq_ctx *ctx, int nqubits, int batch, size_t *out);
+DQ_API dq_status dq_sample(dq_ctx *ctx, int nqubits, const void *state, int batch, int dtype,
+                           int64_t shots, const double *uniforms, uint64_t seed,
+                           uint64_t wire_mask, int64_t *out, void *stream);
+
 /* Time the fused-path variants (fusion width k and tile schedule) for this
  * circuit shape on `state` (device, batch rows, contents destroyed) and
  * cache the fastest for later calls with the same circuit structure.

@@ -66,6 +66,7 @@ def _bind(path):
     lib.oracle_expect.argtypes = [I, P, P, P, P, I, I, P, P]
     lib.oracle_adjoint.argtypes = gate_args + [I, P, P, P, P, I, P, P, P, P]
     lib.oracle_apply_dense.argtypes = [I, I, P, I, P]
+    lib.oracle_sample.argtypes = [I, I, P, ctypes.c_int64, P, ctypes.c_uint64, P]
     return lib
 
 
@@ -187,6 +188,21 @@ def apply_dense(n, nw, unitary, states, lib=None):
     st = np.array(states, dtype=np.complex128, copy=True).reshape(-1, 1 << n)
     lib.oracle_apply_dense(int(n), int(nw), _ptr(u), st.shape[0], _ptr(st))
     return st
+
+
+def sample(n, states, uniforms, wires=None, lib=None):
+    """(batch, shots) int64 outcomes from |psi|^2 by inversion of the
+    cumulative distribution, one per uniform in ``uniforms`` (batch, shots);
+    ``wires``: packed bits of those wires (lowest wire most significant)."""
+    lib = lib or _load()
+    st = np.ascontiguousarray(states, dtype=np.complex128).reshape(-1, 1 << n)
+    u = np.ascontiguousarray(uniforms, dtype=np.float64).reshape(st.shape[0], -1)
+    mask = 0
+    for q in (wires or []):
+        mask |= 1 << int(q)
+    out = np.empty(u.shape, dtype=np.int64)
+    lib.oracle_sample(int(n), st.shape[0], _ptr(st), int(u.shape[1]), _ptr(u), ctypes.c_uint64(mask), _ptr(out))
+    return out
 
 
 def load_library(path: str):

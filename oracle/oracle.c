@@ -528,6 +528,59 @@ void oracle_adjoint(int n, int ngates, const int *kind, const int *w0, const int
 }
 
 /* ------------------------------------------------------------------------ */
+/* Shot sampling.                                                            */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Outcomes of `shots` measurements of every row in the computational basis
+ * (API Overview: measure(shots, wires)), by inversion of the cumulative
+ * distribution (Devroye, "Non-Uniform Random Variate Generation", 1986,
+ * Sec. III.2, the search done by bisection): with p_i = |psi_i|^2, C(i) = p_0 + ... +
+ * p_i in index order and Z = C(2^n - 1), shot s returns the smallest i with
+ * u_s * Z < C(i); when rounding leaves no such i it returns the last i with
+ * p_i > 0.  wire_mask != 0 packs the bits of the selected wires of that
+ * index, the lowest selected wire first (most significant).
+ */
+void oracle_sample(int n, int batch, const double *states_ri, int64_t shots, const double *uniforms,
+                   uint64_t wire_mask, int64_t *out)
+{
+    const int64_t dim = (int64_t)1 << n;
+    const cplx *states = (const cplx *)states_ri;
+#pragma omp parallel for schedule(dynamic, 1) if (batch > 1)
+    for (int r = 0; r < batch; ++r) {
+        const cplx *psi = states + (int64_t)r * dim;
+        double *cum = (double *)malloc((size_t)dim * sizeof(double));
+        double run = 0.0;
+        int64_t last_nz = dim - 1;
+        for (int64_t i = 0; i < dim; ++i) {
+            const double p = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
+            run += p;
+            cum[i] = run;
+            if (p > 0.0) last_nz = i;
+        }
+        for (int64_t s = 0; s < shots; ++s) {
+            const double target = uniforms[(int64_t)r * shots + s] * cum[dim - 1];
+            /* smallest i with target < C(i): bisection on the non-decreasing C */
+            int64_t lo = 0, hi = dim;
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (target < cum[mid]) hi = mid;
+                else lo = mid + 1;
+            }
+            const int64_t idx = lo < dim ? lo : last_nz;
+            int64_t o = idx;
+            if (wire_mask) {
+                o = 0;
+                for (int q = 0; q < n; ++q)
+                    if ((wire_mask >> q) & 1) o = (o << 1) | ((idx >> bitpos(n, q)) & 1);
+            }
+            out[(int64_t)r * shots + s] = o;
+        }
+        free(cum);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Dense matrix on the lowest-order wires.                                   */
 /* ------------------------------------------------------------------------ */
 

@@ -60,7 +60,7 @@ EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path"
            "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_graphs", "dq_ctx_set_tracing",
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
            "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
-           "dq_forward_grad_noalloc", "dq_apply_dense")
+           "dq_forward_grad_noalloc", "dq_apply_dense", "dq_sample_workspace_bytes", "dq_sample")
 
 _lib = None
 
@@ -101,6 +101,8 @@ def load_library(path: str = LIB_PATH):
         "dq_plan_autotune": ([P, C, I, I, P, P], I),
         "dq_forward_grad_noalloc": ([C, P, I, P, O, P, I, I, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t], I),
         "dq_apply_dense": ([P, I, I, P, P, I, I, P], I),
+        "dq_sample_workspace_bytes": ([P, I, I, ctypes.POINTER(ctypes.c_size_t)], I),
+        "dq_sample": ([P, I, P, I, I, ctypes.c_int64, P, ctypes.c_uint64, ctypes.c_uint64, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -306,6 +308,35 @@ class Context:
         self.ensure_workspace(None, None, batch, dtype_code(state.dtype), need_bytes=1 << 20)
         self._check(self.lib.dq_apply_dense(self.h, int(nqubits), nw, _ptr(u), _ptr(state), int(batch),
                                             dtype_code(state.dtype), _stream()), "dq_apply_dense")
+
+    def sample(self, nqubits: int, state: torch.Tensor, shots: int, uniforms: Optional[torch.Tensor] = None,
+               seed: int = 0, wires: Optional[Sequence[int]] = None,
+               out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Outcomes (batch, shots) int64 drawn from |psi|^2 of every row:
+        basis indices, or the packed bits of ``wires`` (first listed wire =
+        most significant; the wires are taken in increasing order).
+        ``uniforms`` (FP64 (batch, shots) on the device, in [0, 1)) or, when
+        None, the splitmix64 stream of ``seed`` drives the draws."""
+        batch = state.numel() >> nqubits
+        mask = 0
+        if wires is not None:
+            for q in wires:
+                mask |= 1 << int(q)
+        if out is None:
+            out = torch.empty((batch, int(shots)), dtype=torch.int64, device=state.device)
+        need = ctypes.c_size_t(0)
+        self._check(self.lib.dq_sample_workspace_bytes(self.h, int(nqubits), int(batch), ctypes.byref(need)),
+                    "dq_sample_workspace_bytes")
+        self.ensure_workspace(None, None, batch, dtype_code(state.dtype), need_bytes=need.value)
+        u = None
+        if uniforms is not None:
+            u = uniforms.to(torch.float64).contiguous()
+            if u.numel() != batch * int(shots):
+                raise ValueError("uniforms must hold batch * shots values")
+        self._check(self.lib.dq_sample(self.h, int(nqubits), _ptr(state), int(batch), dtype_code(state.dtype),
+                                       int(shots), _ptr(u), ctypes.c_uint64(int(seed) & (2 ** 64 - 1)),
+                                       ctypes.c_uint64(mask), _ptr(out), _stream()), "dq_sample")
+        return out
 
     def expect(self, nqubits: int, obs: Observables, state: torch.Tensor,
                out: Optional[torch.Tensor] = None) -> torch.Tensor:

@@ -16,6 +16,7 @@
 #include "dq.h"
 #include "dq_common.cuh"
 #include "dq_dense.h"
+#include "dq_sample.h"
 #include "dq_plan.h"
 #include "dq_rows.h"
 #include "dq_tile.h"
@@ -1205,6 +1206,45 @@ dq_status dq_expect(dq_ctx *ctx, int nqubits, const dq_observables *obs, const v
     }
     return dtype == DQ_C64 ? expect_impl<float>(ctx, nqubits, *o, state, batch, out, s)
                            : expect_impl<double>(ctx, nqubits, *o, state, batch, out, s);
+}
+
+dq_status dq_sample_workspace_bytes(dq_ctx *ctx, int nqubits, int batch, size_t *out) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_n(ctx, nqubits)) != DQ_OK) return st;
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    if (!out) return fail(ctx, DQ_ERR_INVALID_ARG, "out is NULL");
+    *out = sample_workspace_bytes(nqubits, std::max(batch, 1));
+    return DQ_OK;
+}
+
+dq_status dq_sample(dq_ctx *ctx, int nqubits, const void *state, int batch, int dtype, int64_t shots,
+                    const double *uniforms, uint64_t seed, uint64_t wire_mask, int64_t *out, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if ((st = check_n(ctx, nqubits)) != DQ_OK) return st;
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    if (shots < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "shots < 0");
+    if (nqubits < 64 && (wire_mask >> nqubits) != 0)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "wire_mask selects a wire >= %d", nqubits);
+    if (batch == 0 || shots == 0) return DQ_OK;
+    if ((int64_t)batch * shots >= (int64_t(1) << 62)) return fail(ctx, DQ_ERR_INVALID_ARG, "too many shots");
+    if (!state || !aligned16(state)) return fail(ctx, DQ_ERR_INVALID_ARG, "state must be a 16-byte aligned device pointer");
+    if (!out || ((uintptr_t)out & 7)) return fail(ctx, DQ_ERR_INVALID_ARG, "out must be an 8-byte aligned device pointer");
+    if (uniforms && ((uintptr_t)uniforms & 7))
+        return fail(ctx, DQ_ERR_INVALID_ARG, "uniforms must be 8-byte aligned");
+    if ((st = reserve(ctx, sample_workspace_bytes(nqubits, batch))) != DQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == DQ_C64)
+        DQ_CUDA(sample_run<float>(state, nqubits, batch, shots, uniforms, seed, wire_mask, out, ctx->ws, ctx->nsm, s,
+                                  &ctx->launches),
+                "sample");
+    else
+        DQ_CUDA(sample_run<double>(state, nqubits, batch, shots, uniforms, seed, wire_mask, out, ctx->ws, ctx->nsm,
+                                   s, &ctx->launches),
+                "sample");
+    return DQ_OK;
 }
 
 dq_status dq_adjoint_grad(dq_ctx *ctx, const dq_circuit *circuit, const double *params, int params_per_row,

@@ -150,6 +150,16 @@ def pin_failures(oracle, lib=None):
     fd = np.array([(f(params + h * e, data) - f(params - h * e, data)) / (2 * h) for e in np.eye(params.size)])
     fdd = np.array([(f(params, data + h * e) - f(params, data - h * e)) / (2 * h) for e in np.eye(3)])
     check("adjoint-fd-wide", np.allclose(gp, fd, atol=1e-8) and np.allclose(gd[0], fdd, atol=1e-8))
+    # sampling: inversion of the cumulative distribution, marginal packing
+    n = 4
+    st = rng.normal(size=(1, 16)) + 1j * rng.normal(size=(1, 16))
+    st[0, 5] = 0
+    c = np.cumsum(st[0].real ** 2 + st[0].imag ** 2)
+    u = np.concatenate([rng.random(200), c[:8] / c[-1]])[None]   # includes exact boundaries
+    got = oracle.sample(n, st, u, lib=lib)
+    check("sample", (got[0] == np.searchsorted(c, u[0] * c[-1], side="right")).all())
+    got2 = oracle.sample(n, st, u, wires=[2, 0], lib=lib)
+    check("sample-marginal", (got2 == ((((got >> 3) & 1) << 1) | ((got >> 1) & 1))).all())
     # dense block on the low wires = I (x) U as a Kronecker product
     n, nw = 5, 3
     U = W.random_unitary(nw, 11)
@@ -550,6 +560,9 @@ MUTANTS = {
                                 "for (int64_t i = 0; i < dim; ++i) tmp[i] *= 1.0;"),
     "ccx-one-control": ("if ((i & tb) || !(i & b0) || !(i & b1)) continue;",
                         "if ((i & tb) || !(i & b0)) continue;"),
+    "sample-inclusive-bound": ("if (target < cum[mid]) hi = mid;", "if (target <= cum[mid]) hi = mid;"),
+    "sample-marginal-lsb-first": ("if ((wire_mask >> q) & 1) o = (o << 1) | ((idx >> bitpos(n, q)) & 1);",
+                                  "if ((wire_mask >> q) & 1) o |= ((idx >> bitpos(n, q)) & 1) << q;"),
 }
 
 
@@ -569,3 +582,68 @@ def test_pins_reject_planted_mistake(oracle_mod, name):
         assert pin_failures(oracle_mod, lib=lib), f"mutant {name} passed every pin"
     finally:
         shutil.rmtree(tmpdir, ignore_errors=True)
+
+
+# ---------------------------------------------------------------------------
+# shot sampling
+# ---------------------------------------------------------------------------
+def test_sampling_basis_state_is_deterministic(oracle_mod):
+    """A basis state |x> yields x on every shot, whatever the uniforms."""
+    n = 5
+    for x in (0, 7, 31):
+        st = np.zeros((1, 1 << n), complex)
+        st[0, x] = 1j
+        u = np.linspace(0, 1, 50, endpoint=False)[None]
+        assert (oracle_mod.sample(n, st, u) == x).all()
+
+
+def test_sampling_inverts_the_cumulative_distribution(oracle_mod):
+    """Against numpy's cumulative sum and search: smallest i with u Z < C(i);
+    zero-probability outcomes never appear."""
+    rng = np.random.default_rng(9)
+    n = 7
+    st = rng.normal(size=(3, 1 << n)) + 1j * rng.normal(size=(3, 1 << n))
+    st[:, ::3] = 0                         # a third of the outcomes impossible
+    u = rng.random((3, 400))
+    got = oracle_mod.sample(n, st, u)
+    for r in range(3):
+        c = np.cumsum(st[r].real ** 2 + st[r].imag ** 2)
+        ref = np.searchsorted(c, u[r] * c[-1], side="right")
+        assert (got[r] == ref).all()
+        assert (got[r] % 3 != 0).all()
+
+
+def test_sampling_frequencies_match_born_rule(oracle_mod):
+    """Empirical frequencies of 200k shots of a 4-qubit state pass a
+    chi-square test against |psi|^2 (fixed seed, 0.1% level)."""
+    from scipy.stats import chi2
+    rng = np.random.default_rng(3)
+    n = 4
+    st = rng.normal(size=(1, 16)) + 1j * rng.normal(size=(1, 16))
+    st /= np.linalg.norm(st)
+    p = np.abs(st[0]) ** 2
+    shots = 200_000
+    u = W.uniform_array(77, shots, 0.0, 1.0)[None]
+    counts = np.bincount(oracle_mod.sample(n, st, u)[0], minlength=16)
+    stat = float(np.sum((counts - shots * p) ** 2 / (shots * p)))
+    assert stat < chi2.ppf(0.999, 15)
+
+
+def test_sampling_marginal_wires(oracle_mod):
+    """The packed outcome of a wire subset is the projection of the full
+    outcome (first selected wire most significant), and for a product state
+    the marginal of one wire follows that wire's own probabilities."""
+    rng = np.random.default_rng(5)
+    n = 6
+    st = rng.normal(size=(2, 1 << n)) + 1j * rng.normal(size=(2, 1 << n))
+    u = rng.random((2, 300))
+    full = oracle_mod.sample(n, st, u)
+    part = oracle_mod.sample(n, st, u, wires=[4, 1, 2])
+    proj = (((full >> (n - 1 - 1)) & 1) << 2) | (((full >> (n - 1 - 2)) & 1) << 1) | ((full >> (n - 1 - 4)) & 1)
+    assert (part == proj).all()
+    # product state RY(t)|0> on wire 3 (others |0>): P(1) = sin^2(t/2)
+    t = 1.1
+    prod = oracle_mod.run(n, [Gate("ry", (3,), angle=t)])
+    uu = W.uniform_array(5, 100_000, 0.0, 1.0)[None]
+    ones = oracle_mod.sample(n, prod, uu, wires=[3]).mean()
+    assert abs(ones - math.sin(t / 2) ** 2) < 5 * math.sqrt(0.25 / 100_000)
