@@ -510,12 +510,16 @@ def sample30(ctx, device, hbm_peak, peak_kind, n=30, shots=1 << 20, reps=3):
         return {"skipped": str(exc)[:120]}
     ms = a.elapsed_time(b) / reps
     nbytes = (8 << n) + shots * 256 * 8
+    ctx.set_tracing(True)
+    ctx.sample(n, st, shots, seed=9, out=out)
+    kernels = {k: round(v[1], 3) for k, v in ctx.trace().items()}
+    ctx.set_tracing(False)
     del st, out
     ctx.release_workspace()
     torch.cuda.empty_cache()
     return {"workload": "sample_30q_1Mshots_c64", "ms_per_call": ms, "shots_per_s": shots / (ms / 1e3),
             "GBps": nbytes / (ms / 1e3) / 1e9, "frac": nbytes / (ms / 1e3) / 1e9 / hbm_peak,
-            "peak_kind": peak_kind}
+            "peak_kind": peak_kind, "kernel_ms": kernels}
 
 
 def qcnn_batch(ctx, device, batch=4096, steps=5):

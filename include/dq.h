@@ -352,6 +352,33 @@ DQ_API dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const double
 DQ_API dq_status dq_apply_dense(dq_ctx *ctx, int nqubits, int nw, const double *unitary, void *state,
                                 int batch, int dtype, void *stream);
 
+/* Hessian of L = sum_row sum_o w[row, o] <psi_row| O_o |psi_row> with respect
+ * to the shared trainable parameters (the second derivatives of the paper's
+ * gradient-and-Hessian benchmark, Sec. "Benchmarks").  Every angle slot of a
+ * gate with a trainable parameter is an occurrence; row v of the occurrence
+ * Hessian comes from adjoint gradients at shifted angles -- the two-term rule
+ * [g(t + pi/2) - g(t - pi/2)] / 2 for generators with eigenvalue gap 1 (RX RY
+ * RZ P CP RXX RYY RZZ and the three angles of U3) and the four-term rule for
+ * the controlled rotations CRX CRY CRZ -- and parameters used by several
+ * gates sum their occurrences.  Both rules are exact, so the result equals
+ * the analytic Hessian up to rounding.  All shifted points (times the data
+ * rows) run as one batch through the fused forward + adjoint path with
+ * per-row parameters, in chunks of occurrences whose shifted rows' states
+ * (psi and lambda per row on the tiled path) fit in max_bytes (0: a quarter
+ * of the free device memory); a chunk holds at least one occurrence.
+ *   params: device FP64, nparams (shared).  data: device FP64 batch *
+ *   nfeatures or NULL (encoded inputs are held fixed).  row_weights: device
+ *   FP64 batch * nobs or NULL (ones).  batch >= 1 (1 without data).
+ *   hess: device FP64 nparams x nparams, row p = d/dtheta_p of the gradient
+ *   (symmetric up to rounding), overwritten.  grad: device FP64 nparams (the
+ *   gradient at params) or NULL.
+ * The row tables and per-row gradients live in context-owned device memory
+ * (freed by dq_ctx_destroy); the fused path's scratch is the workspace. */
+DQ_API dq_status dq_hessian(dq_ctx *ctx, const dq_circuit *circuit, const double *params,
+                            const double *data, const dq_observables *obs, const double *row_weights,
+                            int batch, int dtype, size_t max_bytes, double *hess, double *grad,
+                            void *stream);
+
 /* Shot sampling (API Overview: measure(shots, wires) -- outcomes drawn with
  * the Born probabilities |psi_i|^2 of the current state).  For row r and shot
  * s, with u = the uniform of that shot in [0, 1), the outcome is the smallest

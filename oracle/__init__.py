@@ -66,6 +66,7 @@ def _bind(path):
     lib.oracle_expect.argtypes = [I, P, P, P, P, I, I, P, P]
     lib.oracle_adjoint.argtypes = gate_args + [I, P, P, P, P, I, P, P, P, P]
     lib.oracle_apply_dense.argtypes = [I, I, P, I, P]
+    lib.oracle_hessian.argtypes = [I, I, P, P, P, P, P, P, P, P, I, P, I, I, P, P, P, P, I, P, P]
     lib.oracle_sample.argtypes = [I, I, P, ctypes.c_int64, P, ctypes.c_uint64, P]
     return lib
 
@@ -188,6 +189,31 @@ def apply_dense(n, nw, unitary, states, lib=None):
     st = np.array(states, dtype=np.complex128, copy=True).reshape(-1, 1 << n)
     lib.oracle_apply_dense(int(n), int(nw), _ptr(u), st.shape[0], _ptr(st))
     return st
+
+
+def hessian(n, gates, observables, params, data=None, batch=1, row_weights=None, lib=None):
+    """(nparams, nparams) Hessian of sum_row sum_o w[row, o] E[row, o] with
+    respect to the shared parameters, by the product rule (one forward run
+    per pair of parameter occurrences -- small cases only)."""
+    lib = lib or _load()
+    g = _Gates(gates)
+    o = _Obs(observables)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    nparams = params.size
+    if data is not None:
+        data = np.ascontiguousarray(data, dtype=np.float64).reshape(batch, -1)
+        nfeat = data.shape[1]
+    else:
+        nfeat = 0
+    rw = None
+    if row_weights is not None:
+        rw = np.ascontiguousarray(row_weights, dtype=np.float64).reshape(batch, o.nobs)
+    out = np.zeros((nparams, nparams), dtype=np.float64)
+    lib.oracle_hessian(int(n), g.count, _ptr(g.kind), _ptr(g.w0), _ptr(g.w1), _ptr(g.w2), _ptr(g.pidx),
+                       _ptr(g.didx), _ptr(g.angle), _ptr(params), int(nparams), _ptr(data), int(nfeat),
+                       int(batch), _ptr(o.coeff), _ptr(o.x), _ptr(o.z), _ptr(o.offsets), o.nobs, _ptr(rw),
+                       _ptr(out))
+    return out
 
 
 def sample(n, states, uniforms, wires=None, lib=None):

@@ -528,6 +528,182 @@ void oracle_adjoint(int n, int ngates, const int *kind, const int *w0, const int
 }
 
 /* ------------------------------------------------------------------------ */
+/* Hessian.                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Second partial derivatives of U3 (which = 0, 1, 2 for theta, phi, lam),
+ * from the matrix definition: every entry is a product of one of
+ * cos(theta/2), sin(theta/2) with a phase e^{i(a phi + b lam)}, so each
+ * derivative multiplies it by the matching factor (-sin/2 <-> cos/2 for
+ * theta, i a for phi, i b for lam). */
+static void u3_second(const double t3[3], int wa, int wb, cplx m[4])
+{
+    const double ch = cos(t3[0] / 2.0), sh = sin(t3[0] / 2.0);
+    /* entry e: trig part T_e(theta) and phase exponents (a_e, b_e) */
+    const double ca[4] = {0, 0, 1, 1}, cb[4] = {0, 1, 0, 1};
+    const double sgn[4] = {1, -1, 1, 1};
+    const int usesin[4] = {0, 1, 1, 0};
+    for (int e = 0; e < 4; ++e) {
+        /* trig part and its theta derivatives: f, f', f'' */
+        const double f0 = usesin[e] ? sh : ch;
+        const double f1 = usesin[e] ? 0.5 * ch : -0.5 * sh;
+        const double f2 = -0.25 * f0;
+        int nth = (wa == 0) + (wb == 0);
+        const double trig = nth == 0 ? f0 : (nth == 1 ? f1 : f2);
+        cplx fac = 1.0;
+        if (wa == 1) fac *= I * ca[e];
+        if (wa == 2) fac *= I * cb[e];
+        if (wb == 1) fac *= I * ca[e];
+        if (wb == 2) fac *= I * cb[e];
+        m[e] = sgn[e] * trig * fac * cexp(I * (ca[e] * t3[1] + cb[e] * t3[2]));
+    }
+}
+
+/* v <- G v for the generator G of gate kind (U(t) = exp(-i t G)); controlled
+ * kinds: G acts on the control = |1> subspace only. */
+static void apply_generator(int n, cplx *v, int kind, int w0, int w1)
+{
+    const int64_t dim = (int64_t)1 << n;
+    if (is_pauli_pair(kind)) {
+        uint64_t xm, zm;
+        pauli_pair_masks(kind, w0, w1, &xm, &zm);
+        apply_pauli(n, v, xm, zm);
+        for (int64_t i = 0; i < dim; ++i) v[i] *= 0.5;
+        return;
+    }
+    cplx gm[4];
+    generator_matrix(kind, gm);
+    if (is_controlled(kind)) {
+        const int64_t cb = (int64_t)1 << bitpos(n, w0);
+        for (int64_t i = 0; i < dim; ++i)
+            if (!(i & cb)) v[i] = 0;
+        apply_block(n, v, w1, w0, gm);
+    } else {
+        apply_block(n, v, w0, -1, gm);
+    }
+}
+
+/* Apply gate g to v, differentiated with respect to angle slots: nd = 0
+ * (the gate), 1 (d/dt_ka) or 2 (d^2/dt_ka dt_kb).  For exp(-i t G):
+ * dU = -i G U, d^2U = -G^2 U; U3 uses its derivative matrices. */
+static void apply_gate_diff(int n, cplx *v, int kind, int w0, int w1, int w2, const double t3[3], int nd,
+                            int ka, int kb)
+{
+    const int64_t dim = (int64_t)1 << n;
+    if (nd == 0) {
+        apply_gate(n, v, kind, w0, w1, w2, t3, 0);
+        return;
+    }
+    if (kind == O_U3) {
+        cplx m[4];
+        if (nd == 1) u3_matrix(t3, ka + 1, m);
+        else u3_second(t3, ka, kb, m);
+        apply_block(n, v, w0, -1, m);
+        return;
+    }
+    apply_gate(n, v, kind, w0, w1, w2, t3, 0);
+    apply_generator(n, v, kind, w0, w1);
+    if (nd == 2) apply_generator(n, v, kind, w0, w1);
+    const cplx f = nd == 1 ? -I : -1.0;
+    for (int64_t i = 0; i < dim; ++i) v[i] *= f;
+}
+
+/*
+ * Hessian of L = sum_row sum_o w[row, o] <psi_row| O_o |psi_row> with respect
+ * to the shared trainable parameters (the second derivatives of the paper's
+ * gradient-and-Hessian benchmark), by the product rule on the circuit:
+ * with O = sum_o w_o O_o, psi_a the final state with occurrence a's gate
+ * differentiated in its angle, and psi_ab the state with both differentiated
+ * (a second derivative when a and b are angles of the same gate),
+ *     d^2 L / dt_a dt_b = 2 Re( <psi_ab|O|psi> + <psi_a|O|psi_b> ).
+ * An occurrence is one angle slot of one gate with a trainable parameter;
+ * parameters used several times collect their occurrences' sums.
+ * hess: nparams x nparams, overwritten.  Every pair costs a forward run
+ * (plain and slow by construction).
+ */
+void oracle_hessian(int n, int ngates, const int *kind, const int *w0, const int *w1, const int *w2,
+                    const int *pidx, const int *didx, const double *angle,
+                    const double *params, int nparams, const double *data, int nfeat, int batch,
+                    const double *coeff, const uint64_t *xmask, const uint64_t *zmask,
+                    const int *term_offsets, int nobs, const double *row_weights, double *hess)
+{
+    const int64_t dim = (int64_t)1 << n;
+    /* occurrences (gate, angle slot) */
+    int nocc = 0;
+    for (int g = 0; g < ngates; ++g)
+        if (is_parametric(kind[g]) && pidx[g] >= 0) nocc += angle_span(kind[g]);
+    int *og = (int *)malloc(sizeof(int) * (nocc + 1)), *ok = (int *)malloc(sizeof(int) * (nocc + 1));
+    for (int g = 0, a = 0; g < ngates; ++g)
+        if (is_parametric(kind[g]) && pidx[g] >= 0)
+            for (int k = 0; k < angle_span(kind[g]); ++k, ++a) { og[a] = g; ok[a] = k; }
+    double *acc = (double *)calloc((size_t)nparams * (nparams > 0 ? nparams : 1) + 1, sizeof(double));
+
+    for (int r = 0; r < batch; ++r) {
+        /* the states: psi, psi_a, and per pair psi_ab */
+        cplx *psi = (cplx *)malloc((size_t)dim * sizeof(cplx));
+        cplx *Opsi = (cplx *)calloc((size_t)dim, sizeof(cplx));
+        cplx *tmp = (cplx *)malloc((size_t)dim * sizeof(cplx));
+        cplx *pa = (cplx *)malloc((size_t)dim * (nocc + 1) * sizeof(cplx));
+        cplx *Opa = (cplx *)calloc((size_t)dim * (nocc + 1), sizeof(cplx));
+        /* run the circuit with occurrence sets differentiated */
+        #define RUN_DIFF(out_, a_, b_)                                                                      \
+            do {                                                                                           \
+                for (int64_t i = 0; i < dim; ++i) (out_)[i] = 0;                                           \
+                (out_)[0] = 1;                                                                             \
+                for (int g = 0; g < ngates; ++g) {                                                         \
+                    double t3[3];                                                                          \
+                    gate_angles(g, kind[g], pidx, didx, angle, params, nparams, 0, data, nfeat, r, t3);    \
+                    int nd = 0, ka = 0, kb = 0;                                                            \
+                    if ((a_) >= 0 && og[(a_)] == g) { nd++; ka = ok[(a_)]; }                               \
+                    if ((b_) >= 0 && og[(b_)] == g) { if (nd) kb = ok[(b_)]; else ka = ok[(b_)]; nd++; }  \
+                    apply_gate_diff(n, (out_), kind[g], w0[g], w1[g], w2[g], t3, nd, ka, kb);              \
+                }                                                                                          \
+            } while (0)
+        /* O applied to a state: sum_o w_o sum_k c_k P_k */
+        #define APPLY_O(dst_, src_)                                                                        \
+            do {                                                                                           \
+                for (int64_t i = 0; i < dim; ++i) (dst_)[i] = 0;                                           \
+                for (int o = 0; o < nobs; ++o) {                                                           \
+                    const double w = row_weights ? row_weights[(int64_t)r * nobs + o] : 1.0;               \
+                    for (int k = term_offsets[o]; k < term_offsets[o + 1]; ++k) {                          \
+                        memcpy(tmp, (src_), (size_t)dim * sizeof(cplx));                                   \
+                        apply_pauli(n, tmp, xmask[k], zmask[k]);                                           \
+                        for (int64_t i = 0; i < dim; ++i) (dst_)[i] += w * coeff[k] * tmp[i];              \
+                    }                                                                                      \
+                }                                                                                          \
+            } while (0)
+        RUN_DIFF(psi, -1, -1);
+        APPLY_O(Opsi, psi);
+        for (int a = 0; a < nocc; ++a) {
+            RUN_DIFF(pa + (int64_t)a * dim, a, -1);
+            APPLY_O(Opa + (int64_t)a * dim, pa + (int64_t)a * dim);
+        }
+        cplx *pab = (cplx *)malloc((size_t)dim * sizeof(cplx));
+        for (int a = 0; a < nocc; ++a)
+            for (int b = a; b < nocc; ++b) {
+                RUN_DIFF(pab, a, b);
+                const double h = 2.0 * creal(inner(dim, pab, Opsi) + inner(dim, pa + (int64_t)a * dim,
+                                                                        Opa + (int64_t)b * dim));
+                const int p = pidx[og[a]] + ok[a], q = pidx[og[b]] + ok[b];
+                acc[(int64_t)p * nparams + q] += h;
+                if (a != b) acc[(int64_t)q * nparams + p] += h;
+            }
+        #undef RUN_DIFF
+        #undef APPLY_O
+        free(pab);
+        free(psi);
+        free(Opsi);
+        free(tmp);
+        free(pa);
+        free(Opa);
+    }
+    memcpy(hess, acc, sizeof(double) * (size_t)nparams * nparams);
+    free(acc);
+    free(og);
+    free(ok);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Shot sampling.                                                            */
 /* ------------------------------------------------------------------------ */
 

@@ -60,7 +60,8 @@ EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path"
            "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_graphs", "dq_ctx_set_tracing",
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
            "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
-           "dq_forward_grad_noalloc", "dq_apply_dense", "dq_sample_workspace_bytes", "dq_sample")
+           "dq_forward_grad_noalloc", "dq_apply_dense", "dq_sample_workspace_bytes", "dq_sample",
+           "dq_hessian")
 
 _lib = None
 
@@ -102,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         "dq_forward_grad_noalloc": ([C, P, I, P, O, P, I, I, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t], I),
         "dq_apply_dense": ([P, I, I, P, P, I, I, P], I),
         "dq_sample_workspace_bytes": ([P, I, I, ctypes.POINTER(ctypes.c_size_t)], I),
+        "dq_hessian": ([P, C, P, P, O, P, I, I, ctypes.c_size_t, P, P, P], I),
         "dq_sample": ([P, I, P, I, I, ctypes.c_int64, P, ctypes.c_uint64, ctypes.c_uint64, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -308,6 +310,25 @@ class Context:
         self.ensure_workspace(None, None, batch, dtype_code(state.dtype), need_bytes=1 << 20)
         self._check(self.lib.dq_apply_dense(self.h, int(nqubits), nw, _ptr(u), _ptr(state), int(batch),
                                             dtype_code(state.dtype), _stream()), "dq_apply_dense")
+
+    def hessian(self, circuit: Circuit, params: torch.Tensor, obs: Observables, data: Optional[torch.Tensor] = None,
+                row_weights: Optional[torch.Tensor] = None, dtype: torch.dtype = torch.complex64,
+                want_grad: bool = True, max_bytes: int = 0):
+        """(hess (nparams, nparams), grad (nparams,) or None) of the weighted
+        sum of expectations over the data rows (batch = data rows, or 1).
+        ``max_bytes`` bounds the shifted rows' state memory per chunk (0: a
+        quarter of the free device memory)."""
+        batch = int(data.shape[0]) if data is not None else 1
+        dev = torch.device(f"cuda:{self.device}")
+        P = circuit.nparams
+        hess = torch.empty((P, P), dtype=torch.float64, device=dev)
+        grad = torch.empty((P,), dtype=torch.float64, device=dev) if want_grad else None
+        self._check(self.lib.dq_hessian(self.h, circuit.ref(), _ptr(params.to(torch.float64).contiguous()),
+                                        _ptr(data.to(torch.float64).contiguous() if data is not None else None),
+                                        obs.ref(), _ptr(row_weights), batch, dtype_code(dtype),
+                                        ctypes.c_size_t(int(max_bytes)), _ptr(hess),
+                                        _ptr(grad), _stream()), "dq_hessian")
+        return hess, grad
 
     def sample(self, nqubits: int, state: torch.Tensor, shots: int, uniforms: Optional[torch.Tensor] = None,
                seed: int = 0, wires: Optional[Sequence[int]] = None,

@@ -16,6 +16,7 @@
 #include "dq.h"
 #include "dq_common.cuh"
 #include "dq_dense.h"
+#include "dq_hessian.h"
 #include "dq_sample.h"
 #include "dq_plan.h"
 #include "dq_rows.h"
@@ -112,6 +113,9 @@ struct dq_ctx {
     };
     std::unordered_map<uint64_t, GraphEntry> graphs;
     std::unordered_map<uint64_t, int> graph_seen;
+    // row tables and per-row gradients of dq_hessian (context-owned)
+    char *hbuf = nullptr;
+    size_t hbuf_bytes = 0;
     void clear_graphs() {
         for (auto &kv : graphs) {
             cudaGraphExecDestroy(kv.second.exec);
@@ -984,6 +988,7 @@ dq_status dq_ctx_destroy(dq_ctx *ctx) {
     ctx->tracer.release();
     if (g_tracer == &ctx->tracer) g_tracer = nullptr;
     if (ctx->ws_owned) cudaFree(ctx->ws);
+    if (ctx->hbuf) cudaFree(ctx->hbuf);
     cudaFree(ctx->d_flag);
     delete ctx;
     return DQ_OK;
@@ -1206,6 +1211,181 @@ dq_status dq_expect(dq_ctx *ctx, int nqubits, const dq_observables *obs, const v
     }
     return dtype == DQ_C64 ? expect_impl<float>(ctx, nqubits, *o, state, batch, out, s)
                            : expect_impl<double>(ctx, nqubits, *o, state, batch, out, s);
+}
+
+// ---- Hessian (shift rules on adjoint gradients, see k_hessian.cu) ---------
+dq_status dq_hessian(dq_ctx *ctx, const dq_circuit *circuit, const double *params, const double *data,
+                     const dq_observables *obs, const double *row_weights, int batch, int dtype, size_t max_bytes,
+                     double *hess, double *grad, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (batch < 1) return fail(ctx, DQ_ERR_INVALID_ARG, "batch must be >= 1");
+    if (!hess) return fail(ctx, DQ_ERR_INVALID_ARG, "hess is NULL");
+    Plan *p = nullptr;
+    if ((st = get_plan(ctx, circuit, 0, &p)) != DQ_OK) return st;
+    ObsDev *o = nullptr;
+    if (!obs) return fail(ctx, DQ_ERR_INVALID_ARG, "observables are NULL");
+    if ((st = get_obs(ctx, obs, p->n, &o)) != DQ_OK) return st;
+    if ((st = check_angles(ctx, *p, params, data)) != DQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int P = circuit->nparams;
+    if (P == 0) return DQ_OK;
+    // occurrences: every angle slot of a gate with a trainable parameter
+    std::vector<dq_gate> vg(circuit->gates, circuit->gates + circuit->ngates);
+    std::vector<int32_t> occ;
+    std::vector<char> four;
+    for (dq_gate &g : vg) {
+        if (g.param_idx < 0) continue;
+        const int span = g.kind == DQ_U3 ? 3 : 1;
+        const int v0 = (int)occ.size();
+        for (int k = 0; k < span; ++k) {
+            occ.push_back(g.param_idx + k);
+            four.push_back(g.kind == DQ_CRX || g.kind == DQ_CRY || g.kind == DQ_CRZ);
+        }
+        g.param_idx = v0;
+    }
+    const int V = (int)occ.size();
+    if (V == 0) {
+        DQ_CUDA(cudaMemsetAsync(hess, 0, sizeof(double) * (size_t)P * P, s), "memset");
+    } else {
+        dq_circuit vc = *circuit;
+        vc.gates = vg.data();
+        vc.nparams = V;
+        Plan *pv = nullptr;
+        if ((st = get_plan(ctx, &vc, 1, &pv)) != DQ_OK) return st;
+        // shift rows, grouped by occurrence
+        const double h = 1.5707963267948966, r2 = 1.4142135623730951;
+        const double c1 = (r2 + 1.0) / (4.0 * r2), c2 = (r2 - 1.0) / (4.0 * r2);
+        std::vector<int32_t> sv, vrow0(V), nshift(V);
+        std::vector<double> sh, coef;
+        for (int v = 0; v < V; ++v) {
+            vrow0[v] = (int32_t)sv.size();
+            auto add = [&](double d, double c) {
+                sv.push_back(v);
+                sh.push_back(d);
+                coef.push_back(c);
+            };
+            if (four[v]) {
+                add(h, c1); add(-h, -c1); add(3 * h, -c2); add(-3 * h, c2);
+            } else {
+                add(h, 0.5); add(-h, -0.5);
+            }
+            nshift[v] = (int32_t)sv.size() - vrow0[v];
+        }
+        const int J = (int)sv.size();
+        // occurrence lists per parameter (CSR)
+        std::vector<int32_t> optr(P + 1, 0), oidx(V);
+        for (int v = 0; v < V; ++v) ++optr[occ[v] + 1];
+        for (int q = 0; q < P; ++q) optr[q + 1] += optr[q];
+        {
+            std::vector<int32_t> fill(optr.begin(), optr.end() - 1);
+            for (int v = 0; v < V; ++v) oidx[fill[occ[v]]++] = v;
+        }
+        // chunk of occurrences per batched call: the rows' states (psi and
+        // lambda on the tiled path) within a quarter of the free memory
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const size_t amp = dtype == DQ_C128 ? 16 : 8;
+        const size_t per_row = 2 * (amp << p->n) + sizeof(double) * (size_t)(2 * V + p->nfeat + o->nobs) + 512;
+        const size_t budget = max_bytes ? max_bytes : std::max<size_t>(free_b / 4, (size_t)1 << 28);
+        int64_t rows_cap = (int64_t)(budget / per_row);
+        rows_cap = std::min<int64_t>(rows_cap, (int64_t)1 << 30);
+        // tables: occ, shift rows, vrow0/nshift, CSR, H~, then per-chunk rows
+        int vchunk = V;
+        while (vchunk > 1) {
+            int64_t rows = 0;
+            for (int v = 0; v < vchunk; ++v) rows += (int64_t)nshift[v] * batch;   // upper bound by first chunk
+            if (rows <= rows_cap) break;
+            vchunk = (vchunk + 1) / 2;
+        }
+        int maxJ = 0;
+        for (int v0 = 0; v0 < V; v0 += vchunk) {
+            int j = 0;
+            for (int v = v0; v < std::min(V, v0 + vchunk); ++v) j += nshift[v];
+            maxJ = std::max(maxJ, j);
+        }
+        const int64_t Rmax = (int64_t)maxJ * batch;
+        if (Rmax >= ((int64_t)1 << 31)) return fail(ctx, DQ_ERR_UNSUPPORTED, "too many shifted rows");
+        Arena a;
+        a.measuring = true;
+        auto layout = [&](Arena &ar, void **ptrs) {
+            ptrs[0] = ar.take(sizeof(int32_t) * V);                 // occ
+            ptrs[1] = ar.take(sizeof(int32_t) * J);                 // shift_v
+            ptrs[2] = ar.take(sizeof(double) * J);                  // shift
+            ptrs[3] = ar.take(sizeof(double) * J);                  // coef
+            ptrs[4] = ar.take(sizeof(int32_t) * V);                 // vrow0
+            ptrs[5] = ar.take(sizeof(int32_t) * V);                 // nshift
+            ptrs[6] = ar.take(sizeof(int32_t) * (P + 1));           // optr
+            ptrs[7] = ar.take(sizeof(int32_t) * V);                 // oidx
+            ptrs[8] = ar.take(sizeof(double) * (size_t)V * V);      // H~
+            ptrs[9] = ar.take(sizeof(double) * (size_t)Rmax * V);   // row params
+            ptrs[10] = ar.take(sizeof(double) * (size_t)Rmax * std::max(1, p->nfeat));
+            ptrs[11] = ar.take(sizeof(double) * (size_t)Rmax * o->nobs);
+            ptrs[12] = ar.take(sizeof(double) * (size_t)Rmax * V);  // per-row gradients
+        };
+        void *ptr[13];
+        layout(a, ptr);
+        if (a.used > ctx->hbuf_bytes) {
+            cudaStreamSynchronize(s);
+            if (ctx->hbuf) cudaFree(ctx->hbuf);
+            ctx->hbuf = nullptr;
+            ctx->hbuf_bytes = 0;
+            cudaError_t e = cudaMalloc((void **)&ctx->hbuf, a.used);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, DQ_ERR_OOM, "cannot allocate %zu bytes for the Hessian's row tables", a.used);
+            }
+            ctx->hbuf_bytes = a.used;
+        }
+        Arena w;
+        w.base = ctx->hbuf;
+        w.cap = ctx->hbuf_bytes;
+        layout(w, ptr);
+        int32_t *d_occ = (int32_t *)ptr[0], *d_sv = (int32_t *)ptr[1], *d_vrow0 = (int32_t *)ptr[4],
+                *d_nshift = (int32_t *)ptr[5], *d_optr = (int32_t *)ptr[6], *d_oidx = (int32_t *)ptr[7];
+        double *d_sh = (double *)ptr[2], *d_coef = (double *)ptr[3], *d_Ht = (double *)ptr[8],
+               *d_prow = (double *)ptr[9], *d_drow = (double *)ptr[10], *d_wrow = (double *)ptr[11],
+               *d_G = (double *)ptr[12];
+        auto up = [&](void *dst, const void *src, size_t bytes) {
+            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+        };
+        DQ_CUDA(up(d_occ, occ.data(), sizeof(int32_t) * V), "hessian tables");
+        DQ_CUDA(up(d_sv, sv.data(), sizeof(int32_t) * J), "hessian tables");
+        DQ_CUDA(up(d_sh, sh.data(), sizeof(double) * J), "hessian tables");
+        DQ_CUDA(up(d_coef, coef.data(), sizeof(double) * J), "hessian tables");
+        DQ_CUDA(up(d_vrow0, vrow0.data(), sizeof(int32_t) * V), "hessian tables");
+        DQ_CUDA(up(d_nshift, nshift.data(), sizeof(int32_t) * V), "hessian tables");
+        DQ_CUDA(up(d_optr, optr.data(), sizeof(int32_t) * (P + 1)), "hessian tables");
+        DQ_CUDA(up(d_oidx, oidx.data(), sizeof(int32_t) * V), "hessian tables");
+        for (int v0 = 0; v0 < V; v0 += vchunk) {
+            const int v1 = std::min(V, v0 + vchunk);
+            const int j0 = vrow0[v0], jn = (v1 < V ? vrow0[v1] : J) - j0;
+            const int R = jn * batch;
+            DQ_CUDA(hess_rows(params, d_occ, V, d_sv + j0, d_sh + j0, jn, batch, data, p->nfeat, row_weights,
+                              o->nobs, d_prow, d_drow, d_wrow, ctx->nsm, s, &ctx->launches),
+                    "hessian rows");
+            st = dtype == DQ_C64 ? forward_grad_impl<float>(ctx, *pv, o, d_prow, data ? d_drow : nullptr,
+                                                            row_weights ? d_wrow : nullptr, R, nullptr, d_G,
+                                                            nullptr, nullptr, s)
+                                 : forward_grad_impl<double>(ctx, *pv, o, d_prow, data ? d_drow : nullptr,
+                                                             row_weights ? d_wrow : nullptr, R, nullptr, d_G,
+                                                             nullptr, nullptr, s);
+            if (st != DQ_OK) return st;
+            DQ_CUDA(hess_combine(d_G, d_vrow0 + v0, d_nshift + v0, d_coef, j0, v1 - v0, v0, batch, V, d_Ht, s,
+                                 &ctx->launches),
+                    "hessian combine");
+        }
+        DQ_CUDA(hess_fold(d_Ht, d_optr, d_oidx, P, V, hess, s, &ctx->launches), "hessian fold");
+    }
+    if (grad) {
+        st = dtype == DQ_C64 ? forward_grad_impl<float>(ctx, *p, o, params, data, row_weights, batch, nullptr, grad,
+                                                        nullptr, nullptr, s)
+                             : forward_grad_impl<double>(ctx, *p, o, params, data, row_weights, batch, nullptr, grad,
+                                                         nullptr, nullptr, s);
+        if (st != DQ_OK) return st;
+    }
+    return DQ_OK;
 }
 
 dq_status dq_sample_workspace_bytes(dq_ctx *ctx, int nqubits, int batch, size_t *out) {

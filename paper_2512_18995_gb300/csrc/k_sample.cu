@@ -10,17 +10,30 @@
 // Layout of the cumulative sums: a row of 2^n amplitudes is cut into chunks
 // of 2^c amplitudes (c = min(8, n)) and the chunks into groups of 2^g chunks
 // (g = min(10, n - c)).  k_chunk_sums streams the state once (one CTA per
-// group, a warp per chunk) and writes every chunk's probability and every
-// group's total, each summed in a fixed order; k_group_scan forms each row's
-// exclusive prefix over its groups and the row total Z.  k_draw then gives
-// each shot one warp: a 32-way search over the group prefixes, a scan of the
-// group's chunk sums, and a scan of the chunk's amplitudes -- 2^c amplitudes
-// and 2^g chunk sums per shot, the latter usually from L2.
+// group, a warp per chunk) and writes, per group, the inclusive prefix sums
+// of its chunks' probabilities and the group total, each added in a fixed
+// order; k_group_scan forms each row's inclusive prefix over its groups (the
+// last entry is the row total Z).  k_draw then gives each shot one warp: a
+// 32-way search over the group prefixes, another over the group's chunk
+// prefixes, and a scan of the chunk's 2^c amplitudes (eight per lane, one
+// round of loads) -- a handful of dependent memory rounds per shot.
 //
-// Scans inside k_draw add in a different order than k_chunk_sums did, so a
-// target within rounding of a group or chunk boundary can run past the last
-// element of the chosen group or chunk; the draw then takes the last element
-// with non-zero probability there, which is a valid outcome for that target.
+// Precision: GB300's FP64 rate is a small fraction of its FP32 rate, and
+// per-amplitude FP64 arithmetic (conversion, squares, adds) would cost more
+// than streaming the state.  For complex64 states each amplitude's
+// probability and the per-lane and per-warp sums are therefore kept as
+// unevaluated float pairs (hi + lo) built with error-free transformations
+// (TwoSum and the FMA residual of a product, Dekker 1971 / Knuth TAOCP 4.2.2),
+// about 44 bits of precision, and converted to FP64 once per chunk; only the
+// prefix sums above the chunk level are FP64.  Probabilities below the
+// smallest FP32 subnormal count as zero.  Complex128 states use FP64
+// throughout.
+//
+// The prefixes of different levels are added separately, so a target within
+// rounding of a boundary can run past the end of the chosen group or chunk;
+// the search then takes the first group (chunk) at which the prefix reaches
+// the total, and the amplitude scan the last amplitude with non-zero
+// probability of the chunk: a valid outcome for that target either way.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -35,55 +48,130 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-template <typename R>
-__device__ __forceinline__ double born(cx<R> a) {
-    return (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+// Unevaluated float pair hi + lo (|lo| <= ulp(hi) / 2 after normalisation).
+struct FF {
+    float hi, lo;
+};
+
+// s + e = a + b exactly (Knuth's TwoSum; the _rn intrinsics keep the compiler
+// from contracting or reassociating the steps).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
+__device__ __forceinline__ FF ff_norm(float s, float e) {
+    const float h = __fadd_rn(s, e);
+    return FF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return ff_norm(s, e);
+}
+
+// Accumulator of probabilities: FF for complex64 amplitudes, double for
+// complex128.
+template <typename R> struct Acc;
+template <> struct Acc<float> {
+    using T = FF;
+    static __device__ __forceinline__ T zero() { return FF{0.f, 0.f}; }
+    // |a|^2 = x^2 + y^2: each square split exactly into float + FMA residual
+    static __device__ __forceinline__ T prob(float2 a) {
+        const float h1 = __fmul_rn(a.x, a.x), l1 = __fmaf_rn(a.x, a.x, -h1);
+        const float h2 = __fmul_rn(a.y, a.y), l2 = __fmaf_rn(a.y, a.y, -h2);
+        float s, e;
+        two_sum(h1, h2, s, e);
+        return ff_norm(s, __fadd_rn(e, __fadd_rn(l1, l2)));
+    }
+    static __device__ __forceinline__ T add(T a, T b) { return ff_add(a, b); }
+    static __device__ __forceinline__ T shfl_up(T a, int o) {
+        return FF{__shfl_up_sync(0xffffffffu, a.hi, o), __shfl_up_sync(0xffffffffu, a.lo, o)};
+    }
+    static __device__ __forceinline__ T shfl_xor(T a, int o) {
+        return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+    }
+    static __device__ __forceinline__ T shfl(T a, int l) {
+        return FF{__shfl_sync(0xffffffffu, a.hi, l), __shfl_sync(0xffffffffu, a.lo, l)};
+    }
+    static __device__ __forceinline__ double value(T a) { return (double)a.hi + (double)a.lo; }
+    static __device__ __forceinline__ bool positive(T a) { return a.hi > 0.f; }
+};
+template <> struct Acc<double> {
+    using T = double;
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ T prob(double2 a) { return a.x * a.x + a.y * a.y; }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T shfl_up(T a, int o) { return __shfl_up_sync(0xffffffffu, a, o); }
+    static __device__ __forceinline__ T shfl_xor(T a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+    static __device__ __forceinline__ T shfl(T a, int l) { return __shfl_sync(0xffffffffu, a, l); }
+    static __device__ __forceinline__ double value(T a) { return a; }
+    static __device__ __forceinline__ bool positive(T a) { return a > 0.0; }
+};
+
 // One CTA per group: warp w sums chunks w, w + 8, ... of the group (lanes
-// stride over the chunk's amplitudes), then the CTA adds the warps' partial
-// totals in warp order.
+// stride over the chunk's amplitudes) into shared memory; the CTA then forms
+// the inclusive prefix over the group's chunks (thread t adds its run of
+// consecutive chunks in order, then the runs are scanned) and the total.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_chunk_sums(const cx<R> *__restrict__ st, SampleGeom G,
-                                                         double *__restrict__ chunk, double *__restrict__ group) {
-    __shared__ double wsum[kWarps];
+                                                         double *__restrict__ cpre, double *__restrict__ group) {
+    __shared__ double sums[1024];
+    __shared__ double part[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t grp = blockIdx.x;                     // row * ngroups + group
     const int L = 1 << G.c, K = 1 << G.g;
     const int64_t ch0 = grp << G.g;
-    double acc = 0.0;
+    using A = Acc<R>;
     for (int k = warp; k < K; k += kWarps) {
         const cx<R> *p = st + ((ch0 + k) << G.c);
-        double s = 0.0;
+        typename A::T s = A::zero();
 #pragma unroll 8
-        for (int i = lane; i < L; i += 32) s += born<R>(p[i]);
-        s = warp_sum(s);
-        if (lane == 0) chunk[ch0 + k] = s;
-        acc += s;
+        for (int i = lane; i < L; i += 32) s = A::add(s, A::prob(p[i]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl_xor(s, o));
+        if (lane == 0) sums[k] = A::value(s);
     }
-    if (lane == 0) wsum[warp] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kWarps; ++w) t += wsum[w];
-        group[grp] = t;
+    // run of consecutive chunks per thread (K <= 1024, 256 threads)
+    const int per = (K + kThreads - 1) / kThreads;
+    const int b = min(K, (int)threadIdx.x * per), e = min(K, b + per);
+    double loc = 0.0;
+    for (int k = b; k < e; ++k) loc += sums[k];
+    double incl = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
+    if (lane == 31) part[warp] = incl;
+    __syncthreads();
+    double off = 0.0;
+    for (int w = 0; w < warp; ++w) off += part[w];
+    double run = off + incl - loc;
+    for (int k = b; k < e; ++k) {
+        run += sums[k];
+        cpre[ch0 + k] = run;
+    }
+    if (e == K && b < e) group[grp] = run;
 }
 
-// One CTA per row: exclusive prefix of the row's group totals, then the row
-// total at index ngroups.  pre has ngroups + 1 entries per row.
+// One CTA per row: inclusive prefix of the row's group totals (the last
+// entry is the row total Z).
 __global__ void __launch_bounds__(1024) k_group_scan(const double *__restrict__ group, int64_t ngroups,
-                                                     double *__restrict__ pre) {
+                                                     double *__restrict__ gpre) {
     __shared__ double part[32];
     const int64_t row = blockIdx.x;
     const double *in = group + row * ngroups;
-    double *out = pre + row * (ngroups + 1);
+    double *out = gpre + row * ngroups;
     const int T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t per = (ngroups + T - 1) / T;
     const int64_t b = min(ngroups, (int64_t)t * per), e = min(ngroups, b + per);
     double loc = 0.0;
     for (int64_t k = b; k < e; ++k) loc += in[k];
-    // exclusive scan of loc over the block
     double incl = loc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -92,23 +180,12 @@ __global__ void __launch_bounds__(1024) k_group_scan(const double *__restrict__ 
     }
     if (lane == 31) part[warp] = incl;
     __syncthreads();
-    if (warp == 0) {
-        const int nw = T >> 5;
-        double v = lane < nw ? part[lane] : 0.0;
-        double x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane < nw) part[lane] = x - v;            // exclusive warp offsets
-        if (lane == nw - 1) out[ngroups] = x;         // row total Z
-    }
-    __syncthreads();
-    double run = part[warp] + incl - loc;
+    double off = 0.0;
+    for (int w = 0; w < warp; ++w) off += part[w];
+    double run = off + incl - loc;
     for (int64_t k = b; k < e; ++k) {
-        out[k] = run;
         run += in[k];
+        out[k] = run;
     }
 }
 
@@ -122,38 +199,32 @@ __device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t k) {
     return (double)(z >> 11) * (1.0 / 9007199254740992.0);
 }
 
-// Warp search for the first element whose running sum exceeds `target`:
-// values are read 32 at a time (value j * 32 + lane in round j), scanned
-// across the warp and added to the running base.  Returns the element index,
-// or -1 when the sum of all `count` values does not exceed target; `last_nz`
-// receives the last element with a positive value (or -1).  `before`
-// receives the running sum in front of the returned element.
-template <typename F>
-__device__ __forceinline__ int warp_find(F value, int count, double target, int lane, int &last_nz,
-                                         double &before) {
-    double base = 0.0;
-    last_nz = -1;
-    for (int j0 = 0; j0 < count; j0 += 32) {
-        const int i = j0 + lane;
-        const double v = i < count ? value(i) : 0.0;
-        double incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+// First index i in [0, count) with pre[i] > x (strict) or >= x (!strict),
+// for non-decreasing pre; count when there is none.  32-way search by the
+// whole warp: every round probes 32 evenly spaced positions.
+__device__ __forceinline__ int64_t warp_first(const double *__restrict__ pre, int64_t count, double x, bool strict,
+                                              int lane) {
+    int64_t lo = 0, hi = count;    // answer in [lo, hi]; hi == count: none found yet
+    while (lo < hi) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t probe = lo + (int64_t)lane * step;
+        bool t = false;
+        if (probe < hi) {
+            const double v = pre[probe];
+            t = strict ? (v > x) : (v >= x);
         }
-        const uint32_t hit = __ballot_sync(0xffffffffu, i < count && base + incl > target);
-        const uint32_t nz = __ballot_sync(0xffffffffu, v > 0.0);
-        if (nz) last_nz = j0 + 31 - __clz(nz);
-        if (hit) {
-            const int l = __ffs(hit) - 1;
-            before = base + __shfl_sync(0xffffffffu, incl - v, l);
-            return j0 + l;
+        const uint32_t m = __ballot_sync(0xffffffffu, t);
+        const uint32_t valid = __ballot_sync(0xffffffffu, probe < hi);
+        if (m) {
+            const int f = __ffs(m) - 1;
+            hi = lo + (int64_t)f * step;
+            lo = f > 0 ? lo + (int64_t)(f - 1) * step + 1 : lo;
+        } else {
+            const int last = 31 - __clz(valid);
+            lo = lo + (int64_t)last * step + 1;
         }
-        base += __shfl_sync(0xffffffffu, incl, 31);
     }
-    before = base;
-    return -1;
+    return lo;
 }
 
 // Packed outcome of the wires in `wmask` (bit q = wire q), the lowest
@@ -166,9 +237,11 @@ __device__ __forceinline__ int64_t pack_outcome(uint64_t idx, int n, uint64_t wm
     return (int64_t)r;
 }
 
+constexpr int kAmpPerLane = 8;   // 2^8 amplitudes per chunk over 32 lanes
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_draw(const cx<R> *__restrict__ st, SampleGeom G,
-                                                   const double *__restrict__ chunk, const double *__restrict__ pre,
+                                                   const double *__restrict__ cpre, const double *__restrict__ gpre,
                                                    int64_t shots, const double *__restrict__ uniforms, uint64_t seed,
                                                    uint64_t wmask, int64_t *__restrict__ out) {
     const int lane = threadIdx.x & 31;
@@ -176,40 +249,80 @@ __global__ void __launch_bounds__(kThreads) k_draw(const cx<R> *__restrict__ st,
     const int64_t total = (int64_t)G.batch * shots;
     const int64_t ngroups = G.ngroups;
     const int K = 1 << G.g, L = 1 << G.c;
+    const int per = L >= 32 * kAmpPerLane ? kAmpPerLane : (L + 31) / 32;   // amplitudes per lane (L <= 256)
     for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < total; k += nwarps) {
         const int64_t row = k / shots;
         const double u = uniforms ? uniforms[k] : splitmix_uniform(seed, (uint64_t)k);
-        const double *gp = pre + row * (ngroups + 1);
-        const double target = u * gp[ngroups];
-        // group: largest index with prefix <= target (32-way search)
-        int64_t lo = 0, hi = ngroups;                  // answer in [lo, hi)
-        while (hi - lo > 1) {
-            const int64_t step = (hi - lo + 31) / 32;
-            const int64_t probe = lo + (int64_t)lane * step;
-            const bool le = probe < hi && gp[probe] <= target;
-            const uint32_t m = __ballot_sync(0xffffffffu, le);
-            const int l = 31 - __clz(m | 1u);          // last lane with prefix <= target (lane 0 always)
-            lo = lo + (int64_t)l * step;
-            hi = min(hi, lo + step);
+        const double *gp = gpre + row * ngroups;
+        const double z = gp[ngroups - 1];
+        if (!(z > 0.0)) {   // a row without probability: the last index, as documented
+            if (lane == 0) out[k] = pack_outcome((uint64_t(1) << G.n) - 1, G.n, wmask);
+            continue;
         }
-        const int64_t grp = row * ngroups + lo;
-        const double gtarget = target - gp[lo];
-        const double *cs = chunk + (grp << G.g);
-        int cnz;
-        double cbefore;
-        int ci = warp_find([&](int i) { return cs[i]; }, K, gtarget, lane, cnz, cbefore);
-        if (ci < 0) {
-            ci = cnz >= 0 ? cnz : K - 1;
-            cbefore = 0.0;
-            for (int i = 0; i < ci; ++i) cbefore += cs[i];
-        }
-        const int64_t c0 = ((grp << G.g) + ci) << G.c;
+        const double target = u * z;
+        // group: first inclusive prefix above the target, else the first at the total
+        int64_t g = warp_first(gp, ngroups, target, true, lane);
+        if (g == ngroups) g = warp_first(gp, ngroups, z, false, lane);
+        if (g == ngroups) g = ngroups - 1;
+        const double tg = target - (g > 0 ? gp[g - 1] : 0.0);
+        const int64_t grp = row * ngroups + g;
+        const double *cp = cpre + (grp << G.g);
+        int64_t ch = warp_first(cp, K, tg, true, lane);
+        if (ch == K) ch = warp_first(cp, K, cp[K - 1], false, lane);
+        if (ch == K) ch = K - 1;
+        const double ta = tg - (ch > 0 ? cp[ch - 1] : 0.0);
+        // amplitudes: lane l holds [l * per, l * per + per) of the chunk
+        const int64_t c0 = ((grp << G.g) + ch) << G.c;
         const cx<R> *amp = st + c0;
-        int anz;
-        double abefore;
-        int ai = warp_find([&](int i) { return born<R>(amp[i]); }, L, gtarget - cbefore, lane, anz, abefore);
-        if (ai < 0) ai = anz >= 0 ? anz : L - 1;
-        if (lane == 0) out[k] = pack_outcome((uint64_t)(c0 - (row << G.n)) + (uint64_t)ai, G.n, wmask);
+        using A = Acc<R>;
+        typename A::T pr[kAmpPerLane];
+        typename A::T mine = A::zero();
+#pragma unroll
+        for (int j = 0; j < kAmpPerLane; ++j) {
+            const int i = lane * per + j;
+            pr[j] = (j < per && i < L) ? A::prob(amp[i]) : A::zero();
+            mine = A::add(mine, pr[j]);
+        }
+        // inclusive scan of the lanes' sums (lane order = index order)
+        typename A::T incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const typename A::T y = A::shfl_up(incl, o);
+            if (lane >= o) incl = A::add(incl, y);
+        }
+        const double incl_d = A::value(incl);
+        const double excl_d = incl_d - A::value(mine);
+        const uint32_t hit = __ballot_sync(0xffffffffu, incl_d > ta);
+        const uint32_t nz = __ballot_sync(0xffffffffu, A::positive(mine));
+        int a;
+        if (hit) {
+            const int l = __ffs(hit) - 1;
+            // walk lane l's run in order, starting from the sum of the lanes before it
+            const double base = __shfl_sync(0xffffffffu, excl_d, l);
+            typename A::T run = A::zero();
+            int pick = -1, lastnz = -1;
+#pragma unroll
+            for (int j = 0; j < kAmpPerLane; ++j) {
+                if (lane == l && j < per) {
+                    run = A::add(run, pr[j]);
+                    if (A::positive(pr[j])) lastnz = j;
+                    if (pick < 0 && base + A::value(run) > ta) pick = j;
+                }
+            }
+            pick = __shfl_sync(0xffffffffu, pick >= 0 ? pick : lastnz, l);
+            a = l * per + (pick >= 0 ? pick : per - 1);
+        } else {
+            // rounding ran past the chunk: its last amplitude with non-zero probability
+            const int l = nz ? 31 - __clz(nz) : 31;
+            int lastnz = -1;
+#pragma unroll
+            for (int j = 0; j < kAmpPerLane; ++j)
+                if (lane == l && j < per && A::positive(pr[j])) lastnz = j;
+            lastnz = __shfl_sync(0xffffffffu, lastnz, l);
+            a = l * per + (lastnz >= 0 ? lastnz : per - 1);
+        }
+        if (a >= L) a = L - 1;
+        if (lane == 0) out[k] = pack_outcome((uint64_t)(c0 - (row << G.n)) + (uint64_t)a, G.n, wmask);
     }
 }
 
@@ -229,8 +342,7 @@ size_t sample_workspace_bytes(int n, int batch) {
     const SampleGeom G = sample_geom(n, batch);
     const size_t nch = (size_t)batch << (n - G.c);
     const size_t ng = (size_t)batch * (size_t)G.ngroups;
-    const size_t pre = (size_t)batch * (size_t)(G.ngroups + 1);
-    return (nch + ng + pre) * sizeof(double) + 3 * 256;
+    return (nch + 2 * ng) * sizeof(double) + 3 * 256;
 }
 
 template <typename R>
@@ -243,25 +355,25 @@ cudaError_t sample_run(const void *state, int n, int batch, int64_t shots, const
         w += (bytes + 255) & ~size_t(255);
         return p;
     };
-    double *chunk = (double *)take(((size_t)batch << (n - G.c)) * sizeof(double));
+    double *cpre = (double *)take(((size_t)batch << (n - G.c)) * sizeof(double));
     double *group = (double *)take((size_t)batch * (size_t)G.ngroups * sizeof(double));
-    double *pre = (double *)take((size_t)batch * (size_t)(G.ngroups + 1) * sizeof(double));
+    double *gpre = (double *)take((size_t)batch * (size_t)G.ngroups * sizeof(double));
     const cx<R> *st = (const cx<R> *)state;
     {
         LaunchScope ls(s, "k_chunk_sums", launches);
-        k_chunk_sums<R><<<(unsigned)((int64_t)batch * G.ngroups), kThreads, 0, s>>>(st, G, chunk, group);
+        k_chunk_sums<R><<<(unsigned)((int64_t)batch * G.ngroups), kThreads, 0, s>>>(st, G, cpre, group);
     }
     {
         LaunchScope ls(s, "k_group_scan", launches);
         const int t = G.ngroups >= 1024 ? 1024 : (G.ngroups >= 256 ? 256 : 32);
-        k_group_scan<<<batch, t, 0, s>>>(group, G.ngroups, pre);
+        k_group_scan<<<batch, t, 0, s>>>(group, G.ngroups, gpre);
     }
     const int64_t total = (int64_t)batch * shots;
     const int64_t want = (total + kWarps - 1) / kWarps;
-    const int64_t cap = (int64_t)nsm * 16;
+    const int64_t cap = (int64_t)nsm * 32;
     {
         LaunchScope ls(s, "k_draw", launches);
-        k_draw<R><<<(unsigned)(want < cap ? want : cap), kThreads, 0, s>>>(st, G, chunk, pre, shots, uniforms,
+        k_draw<R><<<(unsigned)(want < cap ? want : cap), kThreads, 0, s>>>(st, G, cpre, gpre, shots, uniforms,
                                                                            seed, wmask, out);
     }
     return cudaGetLastError();

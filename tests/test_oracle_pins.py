@@ -150,6 +150,19 @@ def pin_failures(oracle, lib=None):
     fd = np.array([(f(params + h * e, data) - f(params - h * e, data)) / (2 * h) for e in np.eye(params.size)])
     fdd = np.array([(f(params, data + h * e) - f(params, data - h * e)) / (2 * h) for e in np.eye(3)])
     check("adjoint-fd-wide", np.allclose(gp, fd, atol=1e-8) and np.allclose(gd[0], fdd, atol=1e-8))
+    # Hessian against gradient differences (closed form pair, U3 same-gate terms)
+    gates = [Gate("rx", (0,), param=0), Gate("ry", (0,), param=1), Gate("u3", (1,), param=2),
+             Gate("cnot", (0, 1)), Gate("u3", (0,), param=5)]
+    params = np.array([0.3, 1.2, -0.7, 0.4, 2.2, 0.9, -1.1, 0.5])
+    obs = [[(1.0, 0b01, 0b11), (0.6, 0b10, 0b00)]]
+    H = oracle.hessian(2, gates, obs, params, lib=lib)
+    fdH = np.zeros_like(H)
+    for j in range(params.size):
+        e = np.zeros(params.size)
+        e[j] = 1e-5
+        fdH[j] = (oracle.adjoint(2, gates, obs, params + e, lib=lib)[1]
+                  - oracle.adjoint(2, gates, obs, params - e, lib=lib)[1]) / 2e-5
+    check("hessian-fd", np.allclose(H, fdH, atol=1e-7))
     # sampling: inversion of the cumulative distribution, marginal packing
     n = 4
     st = rng.normal(size=(1, 16)) + 1j * rng.normal(size=(1, 16))
@@ -560,6 +573,9 @@ MUTANTS = {
                                 "for (int64_t i = 0; i < dim; ++i) tmp[i] *= 1.0;"),
     "ccx-one-control": ("if ((i & tb) || !(i & b0) || !(i & b1)) continue;",
                         "if ((i & tb) || !(i & b0)) continue;"),
+    "hessian-cross-term-dropped": ("const double h = 2.0 * creal(inner(dim, pab, Opsi) + inner(dim, pa + (int64_t)a * dim,",
+                                   "const double h = 2.0 * creal(inner(dim, pab, Opsi) + 0.0 * inner(dim, pa + (int64_t)a * dim,"),
+    "u3-second-theta-sign": ("const double f2 = -0.25 * f0;", "const double f2 = 0.25 * f0;"),
     "sample-inclusive-bound": ("if (target < cum[mid]) hi = mid;", "if (target <= cum[mid]) hi = mid;"),
     "sample-marginal-lsb-first": ("if ((wire_mask >> q) & 1) o = (o << 1) | ((idx >> bitpos(n, q)) & 1);",
                                   "if ((wire_mask >> q) & 1) o |= ((idx >> bitpos(n, q)) & 1) << q;"),
@@ -647,3 +663,44 @@ def test_sampling_marginal_wires(oracle_mod):
     uu = W.uniform_array(5, 100_000, 0.0, 1.0)[None]
     ones = oracle_mod.sample(n, prod, uu, wires=[3]).mean()
     assert abs(ones - math.sin(t / 2) ** 2) < 5 * math.sqrt(0.25 / 100_000)
+
+
+# ---------------------------------------------------------------------------
+# Hessian (product rule)
+# ---------------------------------------------------------------------------
+def test_hessian_closed_form_two_rotations(oracle_mod):
+    """<Z> of RY(b) RX(a)|0> is cos(a) cos(b): its Hessian in (a, b) is
+    [[-cos a cos b, sin a sin b], [sin a sin b, -cos a cos b]]."""
+    gates = [Gate("rx", (0,), param=0), Gate("ry", (0,), param=1)]
+    for a, b in ((0.3, 1.2), (-2.0, 0.7), (2.9, -1.4)):
+        H = oracle_mod.hessian(1, gates, [W.obs_z(0)], np.array([a, b]))
+        ref = np.array([[-math.cos(a) * math.cos(b), math.sin(a) * math.sin(b)],
+                        [math.sin(a) * math.sin(b), -math.cos(a) * math.cos(b)]])
+        np.testing.assert_allclose(H, ref, atol=1e-14)
+
+
+@pytest.mark.parametrize("kinds", [("h", "rx", "ry", "rz", "cnot", "cp", "p", "rzz"),
+                                   ("h", "crx", "cry", "crz", "cnot", "u3", "rxx", "ryy", "ccx")])
+def test_hessian_matches_gradient_differences(oracle_mod, kinds):
+    """Against central differences of the (pinned) adjoint gradient, with a
+    parameter shared by two gates, encoded data, two rows and row weights;
+    the Hessian is symmetric."""
+    n, batch = 3, 2
+    rng = np.random.default_rng(len(kinds))
+    box = []
+    gates = random_gates(n, 16, rng, box, data_features=3, kinds=kinds)
+    npar = max(box[0], 1)
+    gates.append(Gate("rx", (1,), param=0))       # parameter 0 used twice
+    params = rng.uniform(-3, 3, size=npar)
+    data = rng.uniform(-3, 3, size=(batch, 3))
+    obs = [[(1.0, 0b011, 0b001), (0.5, 0b100, 0)], [(0.7, 0, 0b110)]]
+    w = rng.normal(size=(batch, 2))
+    H = oracle_mod.hessian(n, gates, obs, params, data, batch=batch, row_weights=w)
+    h = 1e-5
+    for j in range(npar):
+        e = np.zeros(npar)
+        e[j] = h
+        gp = oracle_mod.adjoint(n, gates, obs, params + e, data, batch=batch, row_weights=w)[1]
+        gm = oracle_mod.adjoint(n, gates, obs, params - e, data, batch=batch, row_weights=w)[1]
+        np.testing.assert_allclose(H[j], (gp - gm) / (2 * h), atol=2e-7)
+    np.testing.assert_allclose(H, H.T, atol=1e-12)
