@@ -323,6 +323,7 @@ def our_arm(args, rank, world, dist):
         extras["qcnn"] = qcnn_batch(ctx, device)
         extras["trotter30"] = trotter30(ctx, device)
         extras["sample30"] = sample30(ctx, device, hbm_peak, peak_kind)
+        extras["hessian"] = hessian_hea(ctx, device)
         ctx.set_path({"auto": dq.PATH_AUTO, "plain": dq.PATH_PLAIN, "fused": dq.PATH_FUSED}[args.path])
 
     if rank == 0:
@@ -522,6 +523,55 @@ def sample30(ctx, device, hbm_peak, peak_kind, n=30, shots=1 << 20, reps=3):
             "peak_kind": peak_kind, "kernel_ms": kernels}
 
 
+def hessian_workload(n=22, layers=2):
+    """The layered ansatz of the gradient-and-Hessian benchmark at 22 qubits:
+    2 layers of RY/RZ + CNOT ring (88 parameters), <sum_i Z_i>."""
+    g = W.hea_layers(n, layers)
+    p = W.uniform_array(W._seed(22), 2 * n * layers, 0.0, 2 * np.pi)
+    return W.Workload(f"hessian_hea{n}x{layers}_c64", n, "c64", 1, g, p.size, p, False, 0, None,
+                      [W.obs_sum_z(n)], True, False)
+
+
+def hessian_hea(ctx, device):
+    """Full 88 x 88 Hessian of <sum Z> for the 22-qubit, 2-layer ansatz: 176
+    shifted points of the fused forward + adjoint as one batch, vs the same
+    on the per-gate path."""
+    import torch
+    import paper_2512_18995_gb300 as dq
+    wl = hessian_workload()
+    circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
+    obs = dq.Observables(wl.observables)
+    params = torch.tensor(wl.params, device=device)
+    out = {}
+    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+        ctx.set_path(path)
+        try:
+            ctx.hessian(circ, params, obs, want_grad=False)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.hessian(circ, params, obs, want_grad=False)
+            b.record()
+            torch.cuda.synchronize()
+        except RuntimeError as exc:
+            ctx.set_path(dq.PATH_AUTO)
+            return {"skipped": str(exc)[:120]}
+        ms = a.elapsed_time(b)
+        out[name] = {"ms_per_hessian": ms, "entries_per_s": wl.nparams ** 2 / (ms / 1e3)}
+        if name == "fused":
+            ctx.set_tracing(True)
+            ctx.hessian(circ, params, obs, want_grad=False)
+            out[name]["kernel_ms"] = {k: [v[0], round(v[1], 3)] for k, v in ctx.trace().items()}
+            ctx.set_tracing(False)
+    ctx.set_path(dq.PATH_AUTO)
+    ctx.release_workspace()
+    torch.cuda.empty_cache()
+    out["speedup"] = out["plain"]["ms_per_hessian"] / out["fused"]["ms_per_hessian"]
+    out["workload"] = wl.name
+    return out
+
+
 def qcnn_batch(ctx, device, batch=4096, steps=5):
     """The 12-qubit QCNN (RY encodings, RXX/RYY convolutions, CRY pooling; 33
     parameters, 21 features per row) on 4096 rows: <Z_0>, gradients with
@@ -665,6 +715,20 @@ def profile_case(args):
         params = torch.tensor(wl.params, device=dev)
         for _ in range(iters):
             ctx.forward_grad(circ, params, obs, 1, torch.complex64)
+    elif args.profile_case == "sample":      # 2^18 shots from a 26-qubit state (512 MiB)
+        n = 26
+        gen = torch.Generator(device=dev).manual_seed(26)
+        st = torch.randn((1, 1 << n), dtype=torch.complex64, device=dev, generator=gen)
+        out = torch.empty((1, 1 << 18), dtype=torch.int64, device=dev)
+        for i in range(iters):
+            ctx.sample(n, st, 1 << 18, seed=i, out=out)
+    elif args.profile_case == "hessian":     # 22-qubit, 2-layer ansatz Hessian (88 parameters)
+        wl = hessian_workload()
+        circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
+        obs = dq.Observables(wl.observables)
+        params = torch.tensor(wl.params, device=dev)
+        for _ in range(iters):
+            ctx.hessian(circ, params, obs, want_grad=False)
     torch.cuda.synchronize()
     print(f"profile case {args.profile_case}: {iters} iterations in {time.perf_counter() - t0:.3f} s, "
           f"{ctx.launch_count} launches", flush=True)
@@ -682,7 +746,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="issue kernels one by one (no CUDA-graph replay)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--profile-case", choices=["tile", "wsv", "sweep", "c5", "dense"], default=None,
+    ap.add_argument("--profile-case", choices=["tile", "wsv", "sweep", "c5", "dense", "sample", "hessian"], default=None,
                     help="run one kernel family's workload for profiling and exit")
     args = ap.parse_args()
     if args.profile_case:

@@ -9,25 +9,25 @@
 //
 // Layout of the cumulative sums: a row of 2^n amplitudes is cut into chunks
 // of 2^c amplitudes (c = min(8, n)) and the chunks into groups of 2^g chunks
-// (g = min(10, n - c)).  k_chunk_sums streams the state once (one CTA per
-// group, a warp per chunk) and writes, per group, the inclusive prefix sums
-// of its chunks' probabilities and the group total, each added in a fixed
-// order; k_group_scan forms each row's inclusive prefix over its groups (the
-// last entry is the row total Z).  k_draw then gives each shot one warp: a
-// 32-way search over the group prefixes, another over the group's chunk
-// prefixes, and a scan of the chunk's 2^c amplitudes (eight per lane, one
-// round of loads) -- a handful of dependent memory rounds per shot.
+// (g chosen so that a row has min(1024, 2^(n-c)) or more groups, g <= 10).
+// k_chunk_sums streams the state once (one CTA per group, a warp per chunk)
+// and writes, per group, the inclusive prefix sums of its chunks'
+// probabilities and the group total, each added in a fixed order;
+// k_group_scan forms each row's inclusive prefix over its groups (the last
+// entry is the row total Z).  k_draw then gives each shot one warp: a 32-way
+// search over the group prefixes, another over the group's chunk prefixes,
+// and a scan of the chunk's 2^c amplitudes (eight per lane, one round of
+// loads) -- a handful of dependent memory rounds per shot.
 //
 // Precision: GB300's FP64 rate is a small fraction of its FP32 rate, and
-// per-amplitude FP64 arithmetic (conversion, squares, adds) would cost more
-// than streaming the state.  For complex64 states each amplitude's
-// probability and the per-lane and per-warp sums are therefore kept as
-// unevaluated float pairs (hi + lo) built with error-free transformations
-// (TwoSum and the FMA residual of a product, Dekker 1971 / Knuth TAOCP 4.2.2),
-// about 44 bits of precision, and converted to FP64 once per chunk; only the
-// prefix sums above the chunk level are FP64.  Probabilities below the
-// smallest FP32 subnormal count as zero.  Complex128 states use FP64
-// throughout.
+// per-amplitude (or per-shot, per-comparison) FP64 instructions would cost
+// more than the memory traffic.  For complex64 states every probability,
+// partial sum, prefix and comparison is therefore an unevaluated float pair
+// hi + lo built with error-free transformations (TwoSum and the FMA residual
+// of a product: Dekker 1971; Knuth, TAOCP vol. 2, 4.2.2), about 44 bits of
+// precision; a shot converts only its uniform from FP64.  Probabilities
+// below the smallest FP32 subnormal count as zero.  Complex128 states use
+// FP64 throughout.
 //
 // The prefixes of different levels are added separately, so a target within
 // rounding of a boundary can run past the end of the chosen group or chunk;
@@ -48,13 +48,14 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-// Unevaluated float pair hi + lo (|lo| <= ulp(hi) / 2 after normalisation).
+// Unevaluated float pair hi + lo, normalised (hi = fl(hi + lo)), so that
+// pairs compare lexicographically.
 struct FF {
     float hi, lo;
 };
 
-// s + e = a + b exactly (Knuth's TwoSum; the _rn intrinsics keep the compiler
-// from contracting or reassociating the steps).
+// s + e = a + b exactly (TwoSum; the _rn intrinsics keep the compiler from
+// contracting or reassociating the steps).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = __fadd_rn(a, b);
     const float bp = __fsub_rn(s, a);
@@ -73,8 +74,8 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
     return ff_norm(s, e);
 }
 
-// Accumulator of probabilities: FF for complex64 amplitudes, double for
-// complex128.
+// Probability accumulator and prefix type: float pairs for complex64
+// amplitudes, double for complex128.
 template <typename R> struct Acc;
 template <> struct Acc<float> {
     using T = FF;
@@ -88,6 +89,20 @@ template <> struct Acc<float> {
         return ff_norm(s, __fadd_rn(e, __fadd_rn(l1, l2)));
     }
     static __device__ __forceinline__ T add(T a, T b) { return ff_add(a, b); }
+    static __device__ __forceinline__ T sub(T a, T b) { return ff_add(a, FF{-b.hi, -b.lo}); }
+    static __device__ __forceinline__ bool gt(T a, T b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+    static __device__ __forceinline__ bool ge(T a, T b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
+    static __device__ __forceinline__ bool positive(T a) { return a.hi > 0.f; }
+    // u (FP64, in [0, 1)) times z, as a pair: u split into two floats, then
+    // the products with the FMA residual of the leading one
+    static __device__ __forceinline__ T scale(double u, T z) {
+        const float uh = __double2float_rn(u);
+        const float ul = __double2float_rn(u - (double)uh);
+        const float p = __fmul_rn(uh, z.hi);
+        float e = __fmaf_rn(uh, z.hi, -p);
+        e = __fadd_rn(e, __fadd_rn(__fmul_rn(uh, z.lo), __fmul_rn(ul, z.hi)));
+        return ff_norm(p, e);
+    }
     static __device__ __forceinline__ T shfl_up(T a, int o) {
         return FF{__shfl_up_sync(0xffffffffu, a.hi, o), __shfl_up_sync(0xffffffffu, a.lo, o)};
     }
@@ -97,20 +112,42 @@ template <> struct Acc<float> {
     static __device__ __forceinline__ T shfl(T a, int l) {
         return FF{__shfl_sync(0xffffffffu, a.hi, l), __shfl_sync(0xffffffffu, a.lo, l)};
     }
-    static __device__ __forceinline__ double value(T a) { return (double)a.hi + (double)a.lo; }
-    static __device__ __forceinline__ bool positive(T a) { return a.hi > 0.f; }
 };
 template <> struct Acc<double> {
     using T = double;
     static __device__ __forceinline__ T zero() { return 0.0; }
     static __device__ __forceinline__ T prob(double2 a) { return a.x * a.x + a.y * a.y; }
     static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+    static __device__ __forceinline__ bool gt(T a, T b) { return a > b; }
+    static __device__ __forceinline__ bool ge(T a, T b) { return a >= b; }
+    static __device__ __forceinline__ bool positive(T a) { return a > 0.0; }
+    static __device__ __forceinline__ T scale(double u, T z) { return u * z; }
     static __device__ __forceinline__ T shfl_up(T a, int o) { return __shfl_up_sync(0xffffffffu, a, o); }
     static __device__ __forceinline__ T shfl_xor(T a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
     static __device__ __forceinline__ T shfl(T a, int l) { return __shfl_sync(0xffffffffu, a, l); }
-    static __device__ __forceinline__ double value(T a) { return a; }
-    static __device__ __forceinline__ bool positive(T a) { return a > 0.0; }
 };
+
+// Exclusive prefix of `loc` over the block (threads in order; lanes are
+// scanned within a warp, warps' totals added in warp order); part holds one
+// entry per warp.
+template <typename A>
+__device__ __forceinline__ typename A::T block_excl(typename A::T loc, typename A::T *part) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    typename A::T incl = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const typename A::T y = A::shfl_up(incl, o);
+        if (lane >= o) incl = A::add(y, incl);
+    }
+    if (lane == 31) part[warp] = incl;
+    __syncthreads();
+    typename A::T off = A::zero();
+    for (int w = 0; w < warp; ++w) off = A::add(off, part[w]);
+    typename A::T before = A::shfl_up(incl, 1);
+    if (lane == 0) before = A::zero();
+    return A::add(off, before);
+}
 
 // One CTA per group: warp w sums chunks w, w + 8, ... of the group (lanes
 // stride over the chunk's amplitudes) into shared memory; the CTA then forms
@@ -118,42 +155,34 @@ template <> struct Acc<double> {
 // consecutive chunks in order, then the runs are scanned) and the total.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_chunk_sums(const cx<R> *__restrict__ st, SampleGeom G,
-                                                         double *__restrict__ cpre, double *__restrict__ group) {
-    __shared__ double sums[1024];
-    __shared__ double part[kWarps];
+                                                         typename Acc<R>::T *__restrict__ cpre,
+                                                         typename Acc<R>::T *__restrict__ group) {
+    using A = Acc<R>;
+    using T = typename A::T;
+    __shared__ T sums[1024];
+    __shared__ T part[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t grp = blockIdx.x;                     // row * ngroups + group
     const int L = 1 << G.c, K = 1 << G.g;
     const int64_t ch0 = grp << G.g;
-    using A = Acc<R>;
     for (int k = warp; k < K; k += kWarps) {
         const cx<R> *p = st + ((ch0 + k) << G.c);
-        typename A::T s = A::zero();
+        T s = A::zero();
 #pragma unroll 8
         for (int i = lane; i < L; i += 32) s = A::add(s, A::prob(p[i]));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl_xor(s, o));
-        if (lane == 0) sums[k] = A::value(s);
+        if (lane == 0) sums[k] = s;
     }
     __syncthreads();
     // run of consecutive chunks per thread (K <= 1024, 256 threads)
     const int per = (K + kThreads - 1) / kThreads;
     const int b = min(K, (int)threadIdx.x * per), e = min(K, b + per);
-    double loc = 0.0;
-    for (int k = b; k < e; ++k) loc += sums[k];
-    double incl = loc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) part[warp] = incl;
-    __syncthreads();
-    double off = 0.0;
-    for (int w = 0; w < warp; ++w) off += part[w];
-    double run = off + incl - loc;
+    T loc = A::zero();
+    for (int k = b; k < e; ++k) loc = A::add(loc, sums[k]);
+    T run = block_excl<A>(loc, part);
     for (int k = b; k < e; ++k) {
-        run += sums[k];
+        run = A::add(run, sums[k]);
         cpre[ch0 + k] = run;
     }
     if (e == K && b < e) group[grp] = run;
@@ -161,30 +190,23 @@ __global__ void __launch_bounds__(kThreads) k_chunk_sums(const cx<R> *__restrict
 
 // One CTA per row: inclusive prefix of the row's group totals (the last
 // entry is the row total Z).
-__global__ void __launch_bounds__(1024) k_group_scan(const double *__restrict__ group, int64_t ngroups,
-                                                     double *__restrict__ gpre) {
-    __shared__ double part[32];
+template <typename R>
+__global__ void __launch_bounds__(1024) k_group_scan(const typename Acc<R>::T *__restrict__ group, int64_t ngroups,
+                                                     typename Acc<R>::T *__restrict__ gpre) {
+    using A = Acc<R>;
+    using T = typename A::T;
+    __shared__ T part[32];
     const int64_t row = blockIdx.x;
-    const double *in = group + row * ngroups;
-    double *out = gpre + row * ngroups;
-    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t per = (ngroups + T - 1) / T;
-    const int64_t b = min(ngroups, (int64_t)t * per), e = min(ngroups, b + per);
-    double loc = 0.0;
-    for (int64_t k = b; k < e; ++k) loc += in[k];
-    double incl = loc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) part[warp] = incl;
-    __syncthreads();
-    double off = 0.0;
-    for (int w = 0; w < warp; ++w) off += part[w];
-    double run = off + incl - loc;
+    const T *in = group + row * ngroups;
+    T *out = gpre + row * ngroups;
+    const int nt = blockDim.x;
+    const int64_t per = (ngroups + nt - 1) / nt;
+    const int64_t b = min(ngroups, (int64_t)threadIdx.x * per), e = min(ngroups, b + per);
+    T loc = A::zero();
+    for (int64_t k = b; k < e; ++k) loc = A::add(loc, in[k]);
+    T run = block_excl<A>(loc, part);
     for (int64_t k = b; k < e; ++k) {
-        run += in[k];
+        run = A::add(run, in[k]);
         out[k] = run;
     }
 }
@@ -202,16 +224,17 @@ __device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t k) {
 // First index i in [0, count) with pre[i] > x (strict) or >= x (!strict),
 // for non-decreasing pre; count when there is none.  32-way search by the
 // whole warp: every round probes 32 evenly spaced positions.
-__device__ __forceinline__ int64_t warp_first(const double *__restrict__ pre, int64_t count, double x, bool strict,
-                                              int lane) {
+template <typename A>
+__device__ __forceinline__ int64_t warp_first(const typename A::T *__restrict__ pre, int64_t count,
+                                              typename A::T x, bool strict, int lane) {
     int64_t lo = 0, hi = count;    // answer in [lo, hi]; hi == count: none found yet
     while (lo < hi) {
         const int64_t step = (hi - lo + 31) / 32;
         const int64_t probe = lo + (int64_t)lane * step;
         bool t = false;
         if (probe < hi) {
-            const double v = pre[probe];
-            t = strict ? (v > x) : (v >= x);
+            const typename A::T v = pre[probe];
+            t = strict ? A::gt(v, x) : A::ge(v, x);
         }
         const uint32_t m = __ballot_sync(0xffffffffu, t);
         const uint32_t valid = __ballot_sync(0xffffffffu, probe < hi);
@@ -241,9 +264,12 @@ constexpr int kAmpPerLane = 8;   // 2^8 amplitudes per chunk over 32 lanes
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_draw(const cx<R> *__restrict__ st, SampleGeom G,
-                                                   const double *__restrict__ cpre, const double *__restrict__ gpre,
-                                                   int64_t shots, const double *__restrict__ uniforms, uint64_t seed,
-                                                   uint64_t wmask, int64_t *__restrict__ out) {
+                                                   const typename Acc<R>::T *__restrict__ cpre,
+                                                   const typename Acc<R>::T *__restrict__ gpre, int64_t shots,
+                                                   const double *__restrict__ uniforms, uint64_t seed, uint64_t wmask,
+                                                   int64_t *__restrict__ out) {
+    using A = Acc<R>;
+    using T = typename A::T;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t total = (int64_t)G.batch * shots;
@@ -251,32 +277,31 @@ __global__ void __launch_bounds__(kThreads) k_draw(const cx<R> *__restrict__ st,
     const int K = 1 << G.g, L = 1 << G.c;
     const int per = L >= 32 * kAmpPerLane ? kAmpPerLane : (L + 31) / 32;   // amplitudes per lane (L <= 256)
     for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < total; k += nwarps) {
-        const int64_t row = k / shots;
+        const int64_t row = G.batch == 1 ? 0 : k / shots;
         const double u = uniforms ? uniforms[k] : splitmix_uniform(seed, (uint64_t)k);
-        const double *gp = gpre + row * ngroups;
-        const double z = gp[ngroups - 1];
-        if (!(z > 0.0)) {   // a row without probability: the last index, as documented
+        const T *gp = gpre + row * ngroups;
+        const T z = gp[ngroups - 1];
+        if (!A::positive(z)) {   // a row without probability: the last index, as documented
             if (lane == 0) out[k] = pack_outcome((uint64_t(1) << G.n) - 1, G.n, wmask);
             continue;
         }
-        const double target = u * z;
+        const T target = A::scale(u, z);
         // group: first inclusive prefix above the target, else the first at the total
-        int64_t g = warp_first(gp, ngroups, target, true, lane);
-        if (g == ngroups) g = warp_first(gp, ngroups, z, false, lane);
+        int64_t g = warp_first<A>(gp, ngroups, target, true, lane);
+        if (g == ngroups) g = warp_first<A>(gp, ngroups, z, false, lane);
         if (g == ngroups) g = ngroups - 1;
-        const double tg = target - (g > 0 ? gp[g - 1] : 0.0);
+        const T tg = g > 0 ? A::sub(target, gp[g - 1]) : target;
         const int64_t grp = row * ngroups + g;
-        const double *cp = cpre + (grp << G.g);
-        int64_t ch = warp_first(cp, K, tg, true, lane);
-        if (ch == K) ch = warp_first(cp, K, cp[K - 1], false, lane);
+        const T *cp = cpre + (grp << G.g);
+        int64_t ch = warp_first<A>(cp, K, tg, true, lane);
+        if (ch == K) ch = warp_first<A>(cp, K, cp[K - 1], false, lane);
         if (ch == K) ch = K - 1;
-        const double ta = tg - (ch > 0 ? cp[ch - 1] : 0.0);
+        const T ta = ch > 0 ? A::sub(tg, cp[ch - 1]) : tg;
         // amplitudes: lane l holds [l * per, l * per + per) of the chunk
         const int64_t c0 = ((grp << G.g) + ch) << G.c;
         const cx<R> *amp = st + c0;
-        using A = Acc<R>;
-        typename A::T pr[kAmpPerLane];
-        typename A::T mine = A::zero();
+        T pr[kAmpPerLane];
+        T mine = A::zero();
 #pragma unroll
         for (int j = 0; j < kAmpPerLane; ++j) {
             const int i = lane * per + j;
@@ -284,29 +309,28 @@ __global__ void __launch_bounds__(kThreads) k_draw(const cx<R> *__restrict__ st,
             mine = A::add(mine, pr[j]);
         }
         // inclusive scan of the lanes' sums (lane order = index order)
-        typename A::T incl = mine;
+        T incl = mine;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const typename A::T y = A::shfl_up(incl, o);
-            if (lane >= o) incl = A::add(incl, y);
+            const T y = A::shfl_up(incl, o);
+            if (lane >= o) incl = A::add(y, incl);
         }
-        const double incl_d = A::value(incl);
-        const double excl_d = incl_d - A::value(mine);
-        const uint32_t hit = __ballot_sync(0xffffffffu, incl_d > ta);
+        T before = A::shfl_up(incl, 1);
+        if (lane == 0) before = A::zero();
+        const uint32_t hit = __ballot_sync(0xffffffffu, A::gt(incl, ta));
         const uint32_t nz = __ballot_sync(0xffffffffu, A::positive(mine));
         int a;
         if (hit) {
             const int l = __ffs(hit) - 1;
             // walk lane l's run in order, starting from the sum of the lanes before it
-            const double base = __shfl_sync(0xffffffffu, excl_d, l);
-            typename A::T run = A::zero();
+            T run = A::shfl(before, l);
             int pick = -1, lastnz = -1;
 #pragma unroll
             for (int j = 0; j < kAmpPerLane; ++j) {
                 if (lane == l && j < per) {
                     run = A::add(run, pr[j]);
                     if (A::positive(pr[j])) lastnz = j;
-                    if (pick < 0 && base + A::value(run) > ta) pick = j;
+                    if (pick < 0 && A::gt(run, ta)) pick = j;
                 }
             }
             pick = __shfl_sync(0xffffffffu, pick >= 0 ? pick : lastnz, l);
@@ -333,8 +357,9 @@ SampleGeom sample_geom(int n, int batch) {
     G.n = n;
     G.batch = batch;
     G.c = n < 8 ? n : 8;
-    G.g = (n - G.c) < 10 ? (n - G.c) : 10;
-    G.ngroups = (int64_t)1 << (n - G.c - G.g);
+    const int rest = n - G.c;                 // chunk-index bits of a row
+    G.g = rest <= 10 ? 0 : (rest - 10 < 10 ? rest - 10 : 10);
+    G.ngroups = (int64_t)1 << (rest - G.g);
     return G;
 }
 
@@ -342,12 +367,14 @@ size_t sample_workspace_bytes(int n, int batch) {
     const SampleGeom G = sample_geom(n, batch);
     const size_t nch = (size_t)batch << (n - G.c);
     const size_t ng = (size_t)batch * (size_t)G.ngroups;
-    return (nch + 2 * ng) * sizeof(double) + 3 * 256;
+    return (nch + 2 * ng) * 8 + 3 * 256;      // 8-byte prefixes (float pair or double)
 }
 
 template <typename R>
 cudaError_t sample_run(const void *state, int n, int batch, int64_t shots, const double *uniforms, uint64_t seed,
                        uint64_t wmask, int64_t *out, void *ws, int nsm, cudaStream_t s, int64_t *launches) {
+    using T = typename Acc<R>::T;
+    static_assert(sizeof(T) == 8, "prefix entries are 8 bytes");
     const SampleGeom G = sample_geom(n, batch);
     char *w = (char *)ws;
     auto take = [&](size_t bytes) {
@@ -355,9 +382,9 @@ cudaError_t sample_run(const void *state, int n, int batch, int64_t shots, const
         w += (bytes + 255) & ~size_t(255);
         return p;
     };
-    double *cpre = (double *)take(((size_t)batch << (n - G.c)) * sizeof(double));
-    double *group = (double *)take((size_t)batch * (size_t)G.ngroups * sizeof(double));
-    double *gpre = (double *)take((size_t)batch * (size_t)G.ngroups * sizeof(double));
+    T *cpre = (T *)take(((size_t)batch << (n - G.c)) * sizeof(T));
+    T *group = (T *)take((size_t)batch * (size_t)G.ngroups * sizeof(T));
+    T *gpre = (T *)take((size_t)batch * (size_t)G.ngroups * sizeof(T));
     const cx<R> *st = (const cx<R> *)state;
     {
         LaunchScope ls(s, "k_chunk_sums", launches);
@@ -366,7 +393,7 @@ cudaError_t sample_run(const void *state, int n, int batch, int64_t shots, const
     {
         LaunchScope ls(s, "k_group_scan", launches);
         const int t = G.ngroups >= 1024 ? 1024 : (G.ngroups >= 256 ? 256 : 32);
-        k_group_scan<<<batch, t, 0, s>>>(group, G.ngroups, gpre);
+        k_group_scan<R><<<batch, t, 0, s>>>(group, G.ngroups, gpre);
     }
     const int64_t total = (int64_t)batch * shots;
     const int64_t want = (total + kWarps - 1) / kWarps;
