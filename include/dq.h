@@ -96,13 +96,23 @@ typedef enum dq_dtype { DQ_C64 = 0, DQ_C128 = 1 } dq_dtype;
  *              (theta, phi, lam), or data[row, data_idx + 0, 1, 2]; a U3 with
  *              neither index set is rejected (DQ_ERR_INVALID_ARG).
  * The library lowers RXX, RYY, RZZ, U3 and CCX to exact products of the other
- * kinds before planning (gradients of their angles are exact as well). */
+ * kinds before planning (gradients of their angles are exact as well).
+ *
+ * Noise channels (the "single-qubit noise channels" of the API Overview) act
+ * on wires[0] with the probability p in `angle` (fixed; param_idx and
+ * data_idx must be -1), and are accepted only by dq_density_forward:
+ *   DQ_BITFLIP       rho -> (1-p) rho + p X rho X
+ *   DQ_PHASEFLIP     rho -> (1-p) rho + p Z rho Z
+ *   DQ_DEPOLARIZING  rho -> (1-p) rho + p/3 (X rho X + Y rho Y + Z rho Z), p <= 3/4
+ *   DQ_AMPDAMP       Kraus operators [[1, 0], [0, sqrt(1-p)]], [[0, sqrt(p)], [0, 0]]
+ *                    (amplitude damping with decay probability p). */
 typedef enum dq_gate_kind {
     DQ_H = 0, DQ_X, DQ_Y, DQ_Z, DQ_S,
     DQ_RX, DQ_RY, DQ_RZ,
     DQ_CNOT, DQ_CZ, DQ_CP, DQ_SWAP,
     DQ_CRX, DQ_CRY, DQ_CRZ,
     DQ_P, DQ_U3, DQ_RXX, DQ_RYY, DQ_RZZ, DQ_CCX,
+    DQ_BITFLIP, DQ_PHASEFLIP, DQ_DEPOLARIZING, DQ_AMPDAMP,
     DQ_NUM_GATE_KINDS
 } dq_gate_kind;
 
@@ -351,6 +361,29 @@ DQ_API dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const double
  * operand image until the kernel has read it. */
 DQ_API dq_status dq_apply_dense(dq_ctx *ctx, int nqubits, int nw, const double *unitary, void *state,
                                 int batch, int dtype, void *stream);
+
+/* Mixed-state evolution (Sec. "Quantum Computing with Qubits", Background:
+ * rho_n = U_n ... U_1 rho_0 U_1^dagger ... U_n^dagger, with the noise channels
+ * of dq_gate_kind applied as Kraus maps) from rho_0 = |0...0><0...0| for
+ * every row, then out[row * nobs + o] = sum_k c_k Re Tr(P_k rho_row).
+ * rho is kept vectorised row-major -- entry (i, j) of row r at
+ * r * 4^n + i * 2^n + j -- so that it is a 2n-qubit "state" whose first n
+ * wires carry i and last n wires carry j: a gate U on wire q becomes U on wire
+ * q and conj(U) on wire q + n, and a channel on wire q a non-unitary map on
+ * the pair (q, q + n) (lowered to two-qubit products of kernel gates and one
+ * non-unitary one-qubit matrix).  The fused and plain paths then run it like
+ * a 2n-qubit circuit.  nqubits <= 17.  params/data as in dq_apply_circuit
+ * (shared parameters only).  expect_out: device FP64 batch * nobs, or NULL.
+ * rho_out: device, batch * 4^n amplitudes of `dtype` (16-byte aligned), or
+ * NULL (then context-owned device memory holds rho).  No gradients. */
+/* Workspace bytes dq_density_forward needs for this circuit, batch and
+ * dtype under the context's current path (the vectorised matrices
+ * themselves are rho_out or context-owned). */
+DQ_API dq_status dq_density_workspace_bytes(dq_ctx *ctx, const dq_circuit *circuit, int batch, int dtype,
+                                            size_t *out);
+DQ_API dq_status dq_density_forward(dq_ctx *ctx, const dq_circuit *circuit, const double *params,
+                                    const double *data, const dq_observables *obs, int batch, int dtype,
+                                    double *expect_out, void *rho_out, void *stream);
 
 /* Hessian of L = sum_row sum_o w[row, o] <psi_row| O_o |psi_row> with respect
  * to the shared trainable parameters (the second derivatives of the paper's

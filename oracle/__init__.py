@@ -33,7 +33,7 @@ _default = None
 _KIND = {k: i for i, k in enumerate(
     ["h", "x", "y", "z", "s", "rx", "ry", "rz",
      "cnot", "cz", "cp", "swap", "crx", "cry", "crz",
-     "p", "u3", "rxx", "ryy", "rzz", "ccx"])}
+     "p", "u3", "rxx", "ryy", "rzz", "ccx", "bitflip", "phaseflip", "depolarizing", "ampdamp"])}
 
 
 def compile_source(src: str, out: str) -> str:
@@ -67,6 +67,7 @@ def _bind(path):
     lib.oracle_adjoint.argtypes = gate_args + [I, P, P, P, P, I, P, P, P, P]
     lib.oracle_apply_dense.argtypes = [I, I, P, I, P]
     lib.oracle_hessian.argtypes = [I, I, P, P, P, P, P, P, P, P, I, P, I, I, P, P, P, P, I, P, P]
+    lib.oracle_density.argtypes = [I, I, P, P, P, P, P, P, P, P, I, P, I, I, P, P, P, P, I, P, P]
     lib.oracle_sample.argtypes = [I, I, P, ctypes.c_int64, P, ctypes.c_uint64, P]
     return lib
 
@@ -214,6 +215,27 @@ def hessian(n, gates, observables, params, data=None, batch=1, row_weights=None,
                        int(batch), _ptr(o.coeff), _ptr(o.x), _ptr(o.z), _ptr(o.offsets), o.nobs, _ptr(rw),
                        _ptr(out))
     return out
+
+
+def density(n, gates, observables=None, params=None, data=None, batch=1, lib=None):
+    """Mixed-state evolution from |0><0| (gates and noise channels):
+    (expectations (batch, nobs) or None, rho (batch, 2**n, 2**n) complex128)."""
+    lib = lib or _load()
+    g = _Gates(gates)
+    params = np.ascontiguousarray(params, dtype=np.float64) if params is not None else np.zeros(1)
+    if data is not None:
+        data = np.ascontiguousarray(data, dtype=np.float64).reshape(batch, -1)
+        nfeat = data.shape[1]
+    else:
+        nfeat = 0
+    o = _Obs(observables or [])
+    exp = np.empty((batch, o.nobs), dtype=np.float64) if observables else None
+    rho = np.empty((batch, 1 << n, 1 << n), dtype=np.complex128)
+    lib.oracle_density(int(n), g.count, _ptr(g.kind), _ptr(g.w0), _ptr(g.w1), _ptr(g.w2), _ptr(g.pidx),
+                       _ptr(g.didx), _ptr(g.angle), _ptr(params), int(params.size), _ptr(data), int(nfeat),
+                       int(batch), _ptr(o.coeff), _ptr(o.x), _ptr(o.z), _ptr(o.offsets), o.nobs, _ptr(exp),
+                       _ptr(rho))
+    return exp, rho
 
 
 def sample(n, states, uniforms, wires=None, lib=None):

@@ -63,6 +63,7 @@ enum {
     O_CNOT, O_CZ, O_CP, O_SWAP,
     O_CRX, O_CRY, O_CRZ,
     O_P, O_U3, O_RXX, O_RYY, O_RZZ, O_CCX,
+    O_BITFLIP, O_PHASEFLIP, O_DEPOLARIZING, O_AMPDAMP,
     O_NKINDS
 };
 
@@ -701,6 +702,146 @@ void oracle_hessian(int n, int ngates, const int *kind, const int *w0, const int
     free(acc);
     free(og);
     free(ok);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Density matrices and noise channels.                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Kraus operators {K_k} (sum_k K_k^dagger K_k = I) of the single-qubit
+ * channels, with probability p:
+ *   bit flip:      sqrt(1-p) I, sqrt(p) X
+ *   phase flip:    sqrt(1-p) I, sqrt(p) Z
+ *   depolarizing:  sqrt(1-p) I, sqrt(p/3) X, sqrt(p/3) Y, sqrt(p/3) Z
+ *   amplitude damping: [[1, 0], [0, sqrt(1-p)]], [[0, sqrt(p)], [0, 0]]
+ * Returns the number of operators. */
+static int kraus_ops(int kind, double p, cplx K[4][4])
+{
+    cplx I2[4] = {1, 0, 0, 1}, X[4] = {0, 1, 1, 0}, Y[4] = {0, -I, I, 0}, Z[4] = {1, 0, 0, -1};
+    const double a = sqrt(1.0 - p);
+    int nk = 0;
+    switch (kind) {
+    case O_BITFLIP:
+        for (int e = 0; e < 4; ++e) { K[0][e] = a * I2[e]; K[1][e] = sqrt(p) * X[e]; }
+        nk = 2;
+        break;
+    case O_PHASEFLIP:
+        for (int e = 0; e < 4; ++e) { K[0][e] = a * I2[e]; K[1][e] = sqrt(p) * Z[e]; }
+        nk = 2;
+        break;
+    case O_DEPOLARIZING: {
+        const double b = sqrt(p / 3.0);
+        for (int e = 0; e < 4; ++e) {
+            K[0][e] = a * I2[e]; K[1][e] = b * X[e]; K[2][e] = b * Y[e]; K[3][e] = b * Z[e];
+        }
+        nk = 4;
+        break;
+    }
+    default: /* amplitude damping */
+        K[0][0] = 1; K[0][1] = 0; K[0][2] = 0; K[0][3] = a;
+        K[1][0] = 0; K[1][1] = sqrt(p); K[1][2] = 0; K[1][3] = 0;
+        nk = 2;
+        break;
+    }
+    return nk;
+}
+
+static int is_noise(int kind)
+{
+    return kind == O_BITFLIP || kind == O_PHASEFLIP || kind == O_DEPOLARIZING || kind == O_AMPDAMP;
+}
+
+/* Operator applied from the left to every column of the dim x dim row-major
+ * matrix m: op(v) acts on a column vector in place. */
+typedef struct { int kind, w0, w1, w2; const double *t3; const cplx *blk; int dagger; } OracleOp;
+
+static void op_apply(int n, cplx *v, const OracleOp *op)
+{
+    if (op->blk) apply_block(n, v, op->w0, -1, op->blk);
+    else apply_gate(n, v, op->kind, op->w0, op->w1, op->w2, op->t3, op->dagger);
+}
+
+/* m <- A m A^dagger: A on every column, then conj(A) on every row (the rows
+ * of m A^dagger are conj(A) applied to the rows of m; conj(A) v is formed as
+ * conj(A conj(v))). */
+static void sandwich(int n, cplx *m, const OracleOp *op, cplx *col)
+{
+    const int64_t dim = (int64_t)1 << n;
+    for (int64_t j = 0; j < dim; ++j) {
+        for (int64_t i = 0; i < dim; ++i) col[i] = m[i * dim + j];
+        op_apply(n, col, op);
+        for (int64_t i = 0; i < dim; ++i) m[i * dim + j] = col[i];
+    }
+    for (int64_t i = 0; i < dim; ++i) {
+        cplx *row = m + i * dim;
+        for (int64_t j = 0; j < dim; ++j) col[j] = conj(row[j]);
+        op_apply(n, col, op);
+        for (int64_t j = 0; j < dim; ++j) row[j] = conj(col[j]);
+    }
+}
+
+/*
+ * Mixed-state evolution rho_n = U_n ... U_1 rho_0 U_1^dagger ... U_n^dagger
+ * (Sec. "Quantum Computing with Qubits", Background) from rho_0 = |0><0|,
+ * with noise channels applied as rho -> sum_k K_k rho K_k^dagger, for every
+ * batch row; then expect_out[row * nobs + o] = sum_k c_k Re Tr(P_k rho)
+ * (Tr(P rho) = sum_i (P rho)_ii with P applied to every column).  rho_out
+ * (batch x 2^n x 2^n, row-major, may be NULL) receives the matrices.
+ */
+void oracle_density(int n, int ngates, const int *kind, const int *w0, const int *w1, const int *w2,
+                    const int *pidx, const int *didx, const double *angle,
+                    const double *params, int nparams, const double *data, int nfeat, int batch,
+                    const double *coeff, const uint64_t *xmask, const uint64_t *zmask,
+                    const int *term_offsets, int nobs, double *expect_out, double *rho_out)
+{
+    const int64_t dim = (int64_t)1 << n;
+#pragma omp parallel for schedule(dynamic, 1) if (batch > 1)
+    for (int r = 0; r < batch; ++r) {
+        cplx *rho = (cplx *)calloc((size_t)(dim * dim), sizeof(cplx));
+        cplx *acc = (cplx *)malloc((size_t)(dim * dim) * sizeof(cplx));
+        cplx *tmp = (cplx *)malloc((size_t)(dim * dim) * sizeof(cplx));
+        cplx *col = (cplx *)malloc((size_t)dim * sizeof(cplx));
+        rho[0] = 1;
+        for (int g = 0; g < ngates; ++g) {
+            if (is_noise(kind[g])) {
+                cplx K[4][4];
+                const int nk = kraus_ops(kind[g], angle[g], K);
+                for (int64_t i = 0; i < dim * dim; ++i) acc[i] = 0;
+                for (int k = 0; k < nk; ++k) {
+                    memcpy(tmp, rho, (size_t)(dim * dim) * sizeof(cplx));
+                    OracleOp op = {0, w0[g], -1, -1, NULL, K[k], 0};
+                    sandwich(n, tmp, &op, col);
+                    for (int64_t i = 0; i < dim * dim; ++i) acc[i] += tmp[i];
+                }
+                memcpy(rho, acc, (size_t)(dim * dim) * sizeof(cplx));
+            } else {
+                double t3[3];
+                gate_angles(g, kind[g], pidx, didx, angle, params, nparams, 0, data, nfeat, r, t3);
+                OracleOp op = {kind[g], w0[g], w1[g], w2[g], t3, NULL, 0};
+                sandwich(n, rho, &op, col);
+            }
+        }
+        if (expect_out) {
+            for (int o = 0; o < nobs; ++o) {
+                double e = 0.0;
+                for (int k = term_offsets[o]; k < term_offsets[o + 1]; ++k) {
+                    double tr = 0.0;
+                    for (int64_t j = 0; j < dim; ++j) {
+                        for (int64_t i = 0; i < dim; ++i) col[i] = rho[i * dim + j];
+                        apply_pauli(n, col, xmask[k], zmask[k]);
+                        tr += creal(col[j]);
+                    }
+                    e += coeff[k] * tr;
+                }
+                expect_out[(int64_t)r * nobs + o] = e;
+            }
+        }
+        if (rho_out) memcpy(rho_out + (int64_t)r * dim * dim * 2, rho, (size_t)(dim * dim) * sizeof(cplx));
+        free(rho);
+        free(acc);
+        free(tmp);
+        free(col);
+    }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -26,7 +26,7 @@ ADJ_CLOBBER_STATE = 1
 
 KIND = {k: i for i, k in enumerate(
     ["h", "x", "y", "z", "s", "rx", "ry", "rz", "cnot", "cz", "cp", "swap", "crx", "cry", "crz",
-     "p", "u3", "rxx", "ryy", "rzz", "ccx"])}
+     "p", "u3", "rxx", "ryy", "rzz", "ccx", "bitflip", "phaseflip", "depolarizing", "ampdamp"])}
 # consecutive angle slots a gate reads from params / data (U3: theta, phi, lam)
 ANGLE_SPAN = {"u3": 3}
 
@@ -61,7 +61,7 @@ EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path"
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
            "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
            "dq_forward_grad_noalloc", "dq_apply_dense", "dq_sample_workspace_bytes", "dq_sample",
-           "dq_hessian")
+           "dq_hessian", "dq_density_workspace_bytes", "dq_density_forward")
 
 _lib = None
 
@@ -104,6 +104,8 @@ def load_library(path: str = LIB_PATH):
         "dq_apply_dense": ([P, I, I, P, P, I, I, P], I),
         "dq_sample_workspace_bytes": ([P, I, I, ctypes.POINTER(ctypes.c_size_t)], I),
         "dq_hessian": ([P, C, P, P, O, P, I, I, ctypes.c_size_t, P, P, P], I),
+        "dq_density_forward": ([P, C, P, P, O, I, I, P, P, P], I),
+        "dq_density_workspace_bytes": ([P, C, I, I, ctypes.POINTER(ctypes.c_size_t)], I),
         "dq_sample": ([P, I, P, I, I, ctypes.c_int64, P, ctypes.c_uint64, ctypes.c_uint64, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -310,6 +312,27 @@ class Context:
         self.ensure_workspace(None, None, batch, dtype_code(state.dtype), need_bytes=1 << 20)
         self._check(self.lib.dq_apply_dense(self.h, int(nqubits), nw, _ptr(u), _ptr(state), int(batch),
                                             dtype_code(state.dtype), _stream()), "dq_apply_dense")
+
+    def density_forward(self, circuit: Circuit, params: Optional[torch.Tensor], obs: Optional[Observables],
+                        batch: int = 1, dtype: torch.dtype = torch.complex64, data: Optional[torch.Tensor] = None,
+                        want_rho: bool = False, rho: Optional[torch.Tensor] = None):
+        """Mixed-state evolution from |0><0| with the circuit's gates and
+        noise channels: (expectations (batch, nobs) FP64 or None, rho
+        (batch, 2^n, 2^n) or None)."""
+        n = circuit.nqubits
+        dev = torch.device(f"cuda:{self.device}")
+        if want_rho and rho is None:
+            rho = torch.empty((batch, 1 << n, 1 << n), dtype=dtype, device=dev)
+        expect = torch.empty((batch, obs.nobs), dtype=torch.float64, device=dev) if obs is not None else None
+        need = ctypes.c_size_t(0)
+        self._check(self.lib.dq_density_workspace_bytes(self.h, circuit.ref(), int(batch), dtype_code(dtype),
+                                                        ctypes.byref(need)), "dq_density_workspace_bytes")
+        self.ensure_workspace(None, None, int(batch), dtype_code(dtype), need_bytes=need.value)
+        self._check(self.lib.dq_density_forward(self.h, circuit.ref(), _ptr(params), _ptr(data),
+                                                obs.ref() if obs is not None else None, int(batch),
+                                                dtype_code(dtype), _ptr(expect), _ptr(rho), _stream()),
+                    "dq_density_forward")
+        return expect, rho
 
     def hessian(self, circuit: Circuit, params: torch.Tensor, obs: Observables, data: Optional[torch.Tensor] = None,
                 row_weights: Optional[torch.Tensor] = None, dtype: torch.dtype = torch.complex64,

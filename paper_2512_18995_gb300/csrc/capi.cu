@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +18,7 @@
 #include "dq.h"
 #include "dq_common.cuh"
 #include "dq_dense.h"
+#include "dq_density.h"
 #include "dq_hessian.h"
 #include "dq_sample.h"
 #include "dq_plan.h"
@@ -75,6 +78,8 @@ uint64_t fnv(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
 void Plan::release() {
     cudaFree(d_gates);
     cudaFree(d_bind);
+    cudaFree(d_fixed);
+    d_fixed = nullptr;
     cudaFree(d_pslot_ptr);
     cudaFree(d_pslots);
     cudaFree(d_dslot_ptr);
@@ -116,6 +121,9 @@ struct dq_ctx {
     // row tables and per-row gradients of dq_hessian (context-owned)
     char *hbuf = nullptr;
     size_t hbuf_bytes = 0;
+    // vectorised density matrices of dq_density_forward when the caller passes none
+    char *dbuf = nullptr;
+    size_t dbuf_bytes = 0;
     void clear_graphs() {
         for (auto &kv : graphs) {
             cudaGraphExecDestroy(kv.second.exec);
@@ -189,13 +197,21 @@ dq_status upload(dq_ctx *ctx, T **dst, const T *src, size_t count) {
 struct Prim {
     int kind, w0, w1, pidx, didx;
     double angle;
+    int conj = 0;     // bind the complex conjugate of the block
+    int fixed = -1;   // kKindFixed / kKindCFixed: index of the block in the fixed table
+    int cls = -1;     // class of a fixed block (else from the kind)
 };
+
+bool kind_noise(int k) { return k == DQ_BITFLIP || k == DQ_PHASEFLIP || k == DQ_DEPOLARIZING || k == DQ_AMPDAMP; }
 
 // Number of kernel-level gates that gate kind `k` lowers to.
 int lowered_size(int k) {
     switch (k) {
     case DQ_RZZ: case DQ_U3: return 3;
     case DQ_RXX: case DQ_RYY: case DQ_CCX: return 7;
+    case DQ_BITFLIP: case DQ_PHASEFLIP: return 3;
+    case DQ_DEPOLARIZING: return 13;
+    case DQ_AMPDAMP: return 7;
     default: return 1;
     }
 }
@@ -228,6 +244,8 @@ dq_status lower_gate(dq_ctx *ctx, const dq_circuit *c, int i, std::vector<Prim> 
     if (g.kind < 0 || g.kind >= DQ_NUM_GATE_KINDS)
         return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: unknown kind %d", i, g.kind);
     const int k = g.kind;
+    if (kind_noise(k))
+        return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: noise channels need the density-matrix entry point", i);
     const int nw = k == DQ_CCX ? 3 : ((kind_controlled(k) || k == DQ_SWAP || k == DQ_RXX || k == DQ_RYY ||
                                        k == DQ_RZZ) ? 2 : 1);
     for (int j = 0; j < nw; ++j) {
@@ -299,22 +317,127 @@ dq_status lower_gate(dq_ctx *ctx, const dq_circuit *c, int i, std::vector<Prim> 
     return DQ_OK;
 }
 
+// Density-matrix lowering of API gate i on the vectorised rho (2n wires:
+// wire q carries the row index bit of wire q, wire q + n the column index
+// bit).  A unitary gate U becomes its pure lowering on the wires q and its
+// complex conjugate on the wires q + n (vec(U rho U^dagger) = (U (x) conj U)
+// vec(rho) for the row-major vectorisation).  A channel on wire q becomes
+// its superoperator on (a, b) = (q, q + n), written as exact products:
+//   bit flip   (1-p) I + p X_a X_b = CNOT(a,b) [(1-p) I + p X]_a CNOT(a,b)
+//              (CNOT(a,b) maps X_a to X_a X_b);
+//   phase flip (1-p) I + p Z_a Z_b = CNOT(a,b) diag(1, 1-2p)_b CNOT(a,b)
+//              (CNOT(a,b) maps Z_b to Z_a Z_b);
+//   Y flip     (1-p) I + p Y_a conj(Y)_b = (1-p) I - p Y_a Y_b
+//              = (S (x) S) CNOT(a,b) [(1-p) I - p X]_a CNOT(a,b) (S^dag (x) S^dag)
+//              (S X S^dag = Y);
+//   depolarizing p: X, Y and Z flips of probability r with r (1 - r) = p/3
+//              (their composition is the Pauli channel with p/3 on each of
+//              X, Y, Z and 1 - p on the identity);
+//   amplitude damping g: K0 (x) K0 + K1 (x) K1 = D T with T = I + g |00><11|
+//              = CNOT(a,b) X_b C_b([[1, g], [0, 1]])_a X_b CNOT(a,b) and
+//              D = diag(1, sqrt(1-g))_a diag(1, sqrt(1-g))_b.
+dq_status lower_gate_density(dq_ctx *ctx, const dq_circuit *c, int i, std::vector<Prim> &out,
+                             std::vector<std::array<double, 8>> &fixed) {
+    const dq_gate &g = c->gates[i];
+    const int n = c->nqubits;
+    if (g.kind < 0 || g.kind >= DQ_NUM_GATE_KINDS)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: unknown kind %d", i, g.kind);
+    if (!kind_noise(g.kind)) {
+        std::vector<Prim> pure;
+        dq_status st = lower_gate(ctx, c, i, pure);
+        if (st != DQ_OK) return st;
+        for (const Prim &p : pure) {
+            out.push_back(p);
+            Prim q = p;
+            q.w0 += n;
+            if (q.w1 >= 0) q.w1 += n;
+            q.conj = 1;
+            out.push_back(q);
+        }
+        return DQ_OK;
+    }
+    if (g.wires[0] < 0 || g.wires[0] >= n)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: wire %d outside [0, %d)", i, g.wires[0], n);
+    if (g.param_idx >= 0 || g.data_idx >= 0)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: a noise channel takes a fixed probability in angle", i);
+    const double p = g.angle;
+    const double pmax = g.kind == DQ_DEPOLARIZING ? 0.75 : 1.0;
+    if (!(p >= 0.0 && p <= pmax))
+        return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: probability %g outside [0, %g]", i, p, pmax);
+    const int a = g.wires[0], b = g.wires[0] + n;
+    auto gate = [&](int kind, int w0, int w1, double t) { out.push_back(Prim{kind, w0, w1, -1, -1, t}); };
+    auto block = [&](int w, int ctrl, int cls, double m0, double m1, double m2, double m3) {
+        fixed.push_back({m0, 0, m1, 0, m2, 0, m3, 0});
+        Prim q{ctrl >= 0 ? kKindCFixed : kKindFixed, ctrl >= 0 ? ctrl : w, ctrl >= 0 ? w : -1, -1, -1, 0.0};
+        q.fixed = (int)fixed.size() - 1;
+        q.cls = cls;
+        out.push_back(q);
+    };
+    const double h = 1.5707963267948966;
+    auto xflip = [&](double r) {
+        gate(DQ_CNOT, a, b, 0);
+        block(a, -1, CLS_REAL, 1 - r, r, r, 1 - r);
+        gate(DQ_CNOT, a, b, 0);
+    };
+    auto zflip = [&](double r) {
+        gate(DQ_CNOT, a, b, 0);
+        block(b, -1, CLS_DIAG, 1, 0, 0, 1 - 2 * r);
+        gate(DQ_CNOT, a, b, 0);
+    };
+    auto yflip = [&](double r) {
+        gate(DQ_P, a, -1, -h);
+        gate(DQ_P, b, -1, -h);
+        gate(DQ_CNOT, a, b, 0);
+        block(a, -1, CLS_REAL, 1 - r, -r, -r, 1 - r);
+        gate(DQ_CNOT, a, b, 0);
+        gate(DQ_S, a, -1, 0);
+        gate(DQ_S, b, -1, 0);
+    };
+    switch (g.kind) {
+    case DQ_BITFLIP: xflip(p); break;
+    case DQ_PHASEFLIP: zflip(p); break;
+    case DQ_DEPOLARIZING: {
+        const double r = 0.5 * (1.0 - std::sqrt(std::max(0.0, 1.0 - 4.0 * p / 3.0)));
+        xflip(r);
+        yflip(r);
+        zflip(r);
+        break;
+    }
+    default: {   // amplitude damping
+        const double sq = std::sqrt(1.0 - p);
+        gate(DQ_CNOT, a, b, 0);
+        gate(DQ_X, b, -1, 0);
+        block(a, b, CLS_REAL, 1, p, 0, 1);
+        gate(DQ_X, b, -1, 0);
+        gate(DQ_CNOT, a, b, 0);
+        block(a, -1, CLS_DIAG, 1, 0, 0, sq);
+        block(b, -1, CLS_DIAG, 1, 0, 0, sq);
+        break;
+    }
+    }
+    return DQ_OK;
+}
+
 // Validate a circuit, lower it and translate it to bit-space gates (appended
 // to dg / bg).
 dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<DevGate> &dg,
                         std::vector<BindGate> &bg, int param_base, int *ncoef_shared, int *ncoef_rows,
-                        bool batch_mode) {
+                        bool batch_mode, std::vector<std::array<double, 8>> *fixed = nullptr) {
     if (!c) return fail(ctx, DQ_ERR_INVALID_ARG, "circuit is NULL");
     dq_status st = check_n(ctx, c->nqubits);
     if (st != DQ_OK) return st;
+    const bool density = fixed != nullptr;
+    if (density && c->nqubits > 17)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "density matrices support up to 17 qubits (got %d)", c->nqubits);
     if (c->ngates < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "ngates < 0");
     if (c->ngates > 0 && !c->gates) return fail(ctx, DQ_ERR_INVALID_ARG, "gates is NULL");
     if (c->nparams < 0 || c->nfeatures < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "negative nparams/nfeatures");
-    const int n = c->nqubits;
+    const int n = density ? 2 * c->nqubits : c->nqubits;
     std::vector<Prim> prims;
-    prims.reserve((size_t)lowered_count(*c));
+    prims.reserve((size_t)lowered_count(*c) * (density ? 2 : 1));
     for (int i = 0; i < c->ngates; ++i) {
-        if ((st = lower_gate(ctx, c, i, prims)) != DQ_OK) return st;
+        st = density ? lower_gate_density(ctx, c, i, prims, *fixed) : lower_gate(ctx, c, i, prims);
+        if (st != DQ_OK) return st;
         if (batch_mode && c->gates[i].data_idx >= 0)
             return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: encoded data is not supported in uneven batches", i);
     }
@@ -327,11 +450,11 @@ dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<D
     const size_t first = dg.size();
     int ks = *ncoef_shared, kr = 0;
     for (const Prim &g : prims) {
-        const bool two = kind_controlled(g.kind) || g.kind == DQ_SWAP;
-        const bool par = kind_parametric(g.kind);
+        const bool two = kind_controlled(g.kind) || g.kind == DQ_SWAP || g.kind == kKindCFixed;
+        const bool par = kind_parametric(g.kind) && !density;
         DevGate d{};
         d.kind = g.kind;
-        d.cls = gate_class(g.kind);
+        d.cls = g.cls >= 0 ? g.cls : gate_class(g.kind);
         if (g.kind == DQ_SWAP) {
             const int a = n - 1 - g.w0, b = n - 1 - g.w1;
             d.t = std::min(a, b);
@@ -349,6 +472,7 @@ dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<D
         b.pidx = g.pidx >= 0 ? g.pidx + param_base : -1;
         b.didx = g.didx;
         b.angle = g.angle;
+        b.aux = (g.conj ? 1 : 0) | ((g.fixed + 1) << 1);
         if (rowwise) {
             d.coef = *ncoef_shared + nshared + kr;   // placeholder, fixed below
             d.rowstep = nrows;
@@ -387,9 +511,10 @@ dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<D
     return DQ_OK;
 }
 
-dq_status get_plan(dq_ctx *ctx, const dq_circuit *c, int ppr, Plan **out) {
+dq_status get_plan(dq_ctx *ctx, const dq_circuit *c, int ppr, Plan **out, bool density = false) {
     if (!c) return fail(ctx, DQ_ERR_INVALID_ARG, "circuit is NULL");
     uint64_t h = fnv(&c->nqubits, sizeof(int32_t));
+    if (density) h = fnv("density", 7, h);
     h = fnv(&c->nparams, sizeof(int32_t), h);
     h = fnv(&c->nfeatures, sizeof(int32_t), h);
     h = fnv(&ppr, sizeof(int), h);
@@ -402,10 +527,14 @@ dq_status get_plan(dq_ctx *ctx, const dq_circuit *c, int ppr, Plan **out) {
     }
     std::unique_ptr<Plan> p(new Plan());
     int ncs = 0, ncr = 0;
-    dq_status st = compile_gates(ctx, c, ppr, p->gates, p->bind, 0, &ncs, &ncr, false);
+    std::vector<std::array<double, 8>> fixed;
+    dq_status st = compile_gates(ctx, c, ppr, p->gates, p->bind, 0, &ncs, &ncr, false, density ? &fixed : nullptr);
     if (st != DQ_OK) return st;
     p->key = h;
-    p->n = c->nqubits;
+    p->n = density ? 2 * c->nqubits : c->nqubits;
+    if (!fixed.empty()) {
+        if ((st = upload(ctx, (std::array<double, 8> **)&p->d_fixed, fixed.data(), fixed.size())) != DQ_OK) return st;
+    }
     p->ngates = (int)p->gates.size();
     p->nparams = c->nparams;
     p->nfeat = c->nfeatures;
@@ -989,6 +1118,7 @@ dq_status dq_ctx_destroy(dq_ctx *ctx) {
     if (g_tracer == &ctx->tracer) g_tracer = nullptr;
     if (ctx->ws_owned) cudaFree(ctx->ws);
     if (ctx->hbuf) cudaFree(ctx->hbuf);
+    if (ctx->dbuf) cudaFree(ctx->dbuf);
     cudaFree(ctx->d_flag);
     delete ctx;
     return DQ_OK;
@@ -1116,6 +1246,22 @@ dq_status dq_workspace_bytes(dq_ctx *ctx, const dq_circuit *circuit, const dq_ob
     return DQ_OK;
 }
 
+dq_status dq_density_workspace_bytes(dq_ctx *ctx, const dq_circuit *circuit, int batch, int dtype, size_t *out) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if (!out) return fail(ctx, DQ_ERR_INVALID_ARG, "out is NULL");
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    Plan *p = nullptr;
+    if ((st = get_plan(ctx, circuit, 0, &p, true)) != DQ_OK) return st;
+    Arena a;
+    a.measuring = true;
+    a.take(coef_bytes(*p, batch, dtype));
+    a.take(tile_workspace_bytes(*p, batch, amp_bytes(dtype)));
+    *out = a.used;
+    return DQ_OK;
+}
+
 dq_status dq_batch_workspace_bytes(dq_ctx *ctx, int ncirc, const dq_circuit *circuits, int dtype, size_t *out) {
     dq_status st = check_ctx(ctx);
     if (st != DQ_OK) return st;
@@ -1211,6 +1357,61 @@ dq_status dq_expect(dq_ctx *ctx, int nqubits, const dq_observables *obs, const v
     }
     return dtype == DQ_C64 ? expect_impl<float>(ctx, nqubits, *o, state, batch, out, s)
                            : expect_impl<double>(ctx, nqubits, *o, state, batch, out, s);
+}
+
+// ---- density matrices (see dq_density_forward in dq.h) ----------------------
+dq_status dq_density_forward(dq_ctx *ctx, const dq_circuit *circuit, const double *params, const double *data,
+                             const dq_observables *obs, int batch, int dtype, double *expect_out, void *rho_out,
+                             void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    Plan *p = nullptr;
+    if ((st = get_plan(ctx, circuit, 0, &p, true)) != DQ_OK) return st;
+    const int n = circuit->nqubits;
+    ObsDev *o = nullptr;
+    if (obs) {
+        if ((st = get_obs(ctx, obs, n, &o)) != DQ_OK) return st;
+    } else if (expect_out) {
+        return fail(ctx, DQ_ERR_INVALID_ARG, "expectations need observables");
+    }
+    if (batch == 0) return DQ_OK;
+    if (rho_out && !aligned16(rho_out)) return fail(ctx, DQ_ERR_INVALID_ARG, "rho_out must be 16-byte aligned");
+    if ((st = check_angles(ctx, *p, params, data)) != DQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = ((size_t)batch << (2 * n)) * (size_t)amp_bytes(dtype);
+    void *rho = rho_out;
+    if (!rho) {
+        if (bytes > ctx->dbuf_bytes) {
+            cudaStreamSynchronize(s);
+            if (ctx->dbuf) cudaFree(ctx->dbuf);
+            ctx->dbuf = nullptr;
+            ctx->dbuf_bytes = 0;
+            cudaError_t e = cudaMalloc((void **)&ctx->dbuf, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, DQ_ERR_OOM, "cannot allocate %zu bytes for the density matrices", bytes);
+            }
+            ctx->dbuf_bytes = bytes;
+        }
+        rho = ctx->dbuf;
+    }
+    if (dtype == DQ_C64) {
+        DQ_CUDA(plain_init_zero<float>(rho, p->n, batch, s, &ctx->launches), "density init");
+        if (p->ngates > 0 && (st = apply_impl<float>(ctx, *p, params, data, rho, batch, s)) != DQ_OK) return st;
+        if (o && expect_out)
+            DQ_CUDA(density_expect<float>(rho, n, o->d_bits, o->d_ptr, o->nobs, batch, expect_out, s, &ctx->launches),
+                    "density expect");
+    } else {
+        DQ_CUDA(plain_init_zero<double>(rho, p->n, batch, s, &ctx->launches), "density init");
+        if (p->ngates > 0 && (st = apply_impl<double>(ctx, *p, params, data, rho, batch, s)) != DQ_OK) return st;
+        if (o && expect_out)
+            DQ_CUDA(density_expect<double>(rho, n, o->d_bits, o->d_ptr, o->nobs, batch, expect_out, s,
+                                           &ctx->launches),
+                    "density expect");
+    }
+    return DQ_OK;
 }
 
 // ---- Hessian (shift rules on adjoint gradients, see k_hessian.cu) ---------

@@ -11,6 +11,8 @@
 
 namespace dq {
 
+template <typename R> struct Mat2;
+
 // Gate as the kernels see it (bit positions, not wires).  32 bytes.
 struct DevGate {
     int32_t kind;       // dq_gate_kind
@@ -30,9 +32,15 @@ struct BindGate {
     int32_t didx;       // data feature index
     int32_t coef;       // output slot (row 0)
     int32_t rowstep;    // row stride of the output slot (0: shared angle)
-    int32_t pad;
+    int32_t aux;        // bit 0: store the complex conjugate of the block;
+                        // bits 1..: 1 + index of a fixed block in the plan's table (0: none)
     double angle;
 };
+
+// Internal kernel-level kinds (never in the public enum): a fixed 2x2 block
+// from the plan's table, uncontrolled or controlled (c = control bit).
+constexpr int kKindFixed = 64;
+constexpr int kKindCFixed = 65;
 
 // One Pauli term in bit space.
 struct DevTerm {
@@ -57,6 +65,7 @@ struct Plan {
     int ncoef_rows = 0;                // gates with rowstep 1
     DevGate *d_gates = nullptr;
     BindGate *d_bind = nullptr;
+    Mat2<double> *d_fixed = nullptr;   // fixed (possibly non-unitary) blocks, referenced by BindGate.aux
     // Gradient slots: one per gate with a trainable/encoded angle.
     int nslots = 0;
     std::vector<int> slot_of_gate;     // -1 or slot id

@@ -77,15 +77,24 @@ __device__ __forceinline__ uint64_t unit_of(const UnitMap &m, uint64_t j) {
 template <typename R>
 __global__ void k_bind(const BindGate *__restrict__ g, int ngates, const double *__restrict__ params,
                        int nparams, int ppr, const double *__restrict__ data, int nfeat,
-                       int batch, Mat2<R> *__restrict__ coef) {
+                       int batch, const Mat2<double> *__restrict__ fixed, Mat2<R> *__restrict__ coef) {
     for (int gi = blockIdx.y; gi < ngates; gi += gridDim.y) {
         const BindGate bg = g[gi];
         const int rows = bg.rowstep ? batch : 1;
         for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
-            double t = bg.angle;
-            if (bg.pidx >= 0) t = ppr ? params[(int64_t)r * nparams + bg.pidx] : params[bg.pidx];
-            else if (bg.didx >= 0) t = data[(int64_t)r * nfeat + bg.didx];
-            coef[bg.coef + (int64_t)r * bg.rowstep] = gate_matrix<R>(bg.kind, t);
+            Mat2<R> m;
+            if (bg.aux >> 1) {   // a fixed block from the plan's table
+                const Mat2<double> &f = fixed[(bg.aux >> 1) - 1];
+                for (int i = 0; i < 4; ++i) m.m[i] = mk<R>((R)f.m[i].x, (R)f.m[i].y);
+            } else {
+                double t = bg.angle;
+                if (bg.pidx >= 0) t = ppr ? params[(int64_t)r * nparams + bg.pidx] : params[bg.pidx];
+                else if (bg.didx >= 0) t = data[(int64_t)r * nfeat + bg.didx];
+                m = gate_matrix<R>(bg.kind, t);
+            }
+            if (bg.aux & 1)
+                for (int i = 0; i < 4; ++i) m.m[i] = cconj(m.m[i]);
+            coef[bg.coef + (int64_t)r * bg.rowstep] = m;
         }
     }
 }
@@ -417,7 +426,7 @@ cudaError_t plain_bind(const Plan &p, const double *params, const double *data, 
     const int rows = p.ncoef_rows ? batch : 1;
     dim3 grid((unsigned)std::min<int64_t>(cdiv(rows, 128), 64), (unsigned)std::min(p.ngates, 65535));
     LaunchScope ls(s, "k_bind", launches);
-    k_bind<R><<<grid, 128, 0, s>>>(p.d_bind, p.ngates, params, p.nparams, p.ppr, data, p.nfeat, batch,
+    k_bind<R><<<grid, 128, 0, s>>>(p.d_bind, p.ngates, params, p.nparams, p.ppr, data, p.nfeat, batch, p.d_fixed,
                                    (Mat2<R> *)coef);
     return cudaGetLastError();
 }

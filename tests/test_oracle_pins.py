@@ -163,6 +163,20 @@ def pin_failures(oracle, lib=None):
         fdH[j] = (oracle.adjoint(2, gates, obs, params + e, lib=lib)[1]
                   - oracle.adjoint(2, gates, obs, params - e, lib=lib)[1]) / 2e-5
     check("hessian-fd", np.allclose(H, fdH, atol=1e-7))
+    # density matrices: pure circuits give |psi><psi|; channel closed forms
+    gates = [Gate("h", (0,)), Gate("ry", (1,), angle=0.7), Gate("cnot", (0, 1)), Gate("u3", (1,), param=0)]
+    params = np.array([0.4, -1.2, 0.8])
+    _, rho = oracle.density(2, gates, None, params, lib=lib)
+    psi = oracle.run(2, gates, params, lib=lib)[0]
+    check("density-pure", np.allclose(rho[0], np.outer(psi, psi.conj()), atol=1e-13))
+    _, r = oracle.density(1, [Gate("bitflip", (0,), angle=0.3)], lib=lib)
+    check("bitflip", np.allclose(r[0], np.diag([0.7, 0.3]), atol=1e-15))
+    _, r = oracle.density(1, [Gate("x", (0,)), Gate("ampdamp", (0,), angle=0.3)], lib=lib)
+    _, r2 = oracle.density(1, [Gate("h", (0,)), Gate("ampdamp", (0,), angle=0.3)], lib=lib)
+    check("ampdamp", np.allclose(r[0], np.diag([0.3, 0.7]), atol=1e-15)
+          and abs(r2[0][0, 1] - math.sqrt(0.7) / 2) < 1e-15)
+    _, r = oracle.density(1, [Gate("h", (0,)), Gate("depolarizing", (0,), angle=0.3)], lib=lib)
+    check("depolarizing", abs(np.real(r[0][0, 1]) - 0.5 * (1 - 0.4)) < 1e-15)
     # sampling: inversion of the cumulative distribution, marginal packing
     n = 4
     st = rng.normal(size=(1, 16)) + 1j * rng.normal(size=(1, 16))
@@ -576,6 +590,13 @@ MUTANTS = {
     "hessian-cross-term-dropped": ("const double h = 2.0 * creal(inner(dim, pab, Opsi) + inner(dim, pa + (int64_t)a * dim,",
                                    "const double h = 2.0 * creal(inner(dim, pab, Opsi) + 0.0 * inner(dim, pa + (int64_t)a * dim,"),
     "u3-second-theta-sign": ("const double f2 = -0.25 * f0;", "const double f2 = 0.25 * f0;"),
+    "bitflip-as-phaseflip": ("for (int e = 0; e < 4; ++e) { K[0][e] = a * I2[e]; K[1][e] = sqrt(p) * X[e]; }",
+                             "for (int e = 0; e < 4; ++e) { K[0][e] = a * I2[e]; K[1][e] = sqrt(p) * Z[e]; }"),
+    "depolarizing-p-over-4": ("const double b = sqrt(p / 3.0);", "const double b = sqrt(p / 4.0);"),
+    "damping-no-sqrt": ("K[0][0] = 1; K[0][1] = 0; K[0][2] = 0; K[0][3] = a;",
+                        "K[0][0] = 1; K[0][1] = 0; K[0][2] = 0; K[0][3] = 1.0 - p;"),
+    "density-rows-unconjugated": ("for (int64_t j = 0; j < dim; ++j) row[j] = conj(col[j]);",
+                                  "for (int64_t j = 0; j < dim; ++j) row[j] = col[j];"),
     "sample-inclusive-bound": ("if (target < cum[mid]) hi = mid;", "if (target <= cum[mid]) hi = mid;"),
     "sample-marginal-lsb-first": ("if ((wire_mask >> q) & 1) o = (o << 1) | ((idx >> bitpos(n, q)) & 1);",
                                   "if ((wire_mask >> q) & 1) o |= ((idx >> bitpos(n, q)) & 1) << q;"),
@@ -704,3 +725,77 @@ def test_hessian_matches_gradient_differences(oracle_mod, kinds):
         gm = oracle_mod.adjoint(n, gates, obs, params - e, data, batch=batch, row_weights=w)[1]
         np.testing.assert_allclose(H[j], (gp - gm) / (2 * h), atol=2e-7)
     np.testing.assert_allclose(H, H.T, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# density matrices and noise channels
+# ---------------------------------------------------------------------------
+def bloch(rho):
+    """(<X>, <Y>, <Z>) of a one-qubit density matrix."""
+    return np.array([np.real(np.trace(D.X @ rho)), np.real(np.trace(D.Y @ rho)), np.real(np.trace(D.Z @ rho))])
+
+
+def test_density_of_pure_circuits_is_the_outer_product(oracle_mod):
+    """Without channels rho = |psi><psi| of the (pinned) state-vector oracle,
+    and Tr(P rho) = <psi|P|psi>, for random circuits over every gate kind."""
+    rng = np.random.default_rng(31)
+    for n in (1, 2, 3, 4):
+        box = []
+        gates = random_gates(n, 10 * n + 6, rng, box, data_features=3)
+        params = rng.uniform(-3, 3, size=max(box[0], 1))
+        data = rng.uniform(-3, 3, size=(2, 3))
+        obs = [W.obs_tfim_open(n, 0.5) if n > 1 else W.obs_z(0), [(0.7, (1 << n) - 1, 1)]]
+        exp, rho = oracle_mod.density(n, gates, obs, params, data, batch=2)
+        psi = oracle_mod.run(n, gates, params, data, batch=2)
+        for r in range(2):
+            np.testing.assert_allclose(rho[r], np.outer(psi[r], psi[r].conj()), atol=1e-13)
+        np.testing.assert_allclose(exp, oracle_mod.expect(n, psi, obs), atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [0.0, 0.13, 0.5, 0.9])
+def test_channels_closed_forms(oracle_mod, p):
+    """Textbook actions (Nielsen & Chuang, Sec. 8.3): bit flip on |0> gives
+    diag(1-p, p); phase flip on |+> scales the coherence by 1-2p; amplitude
+    damping on |1> gives diag(p, 1-p) and on |+> coherence sqrt(1-p)/2;
+    depolarizing (p <= 3/4) shrinks the Bloch vector by 1 - 4p/3."""
+    G = Gate
+    _, r = oracle_mod.density(1, [G("bitflip", (0,), angle=p)])
+    np.testing.assert_allclose(r[0], np.diag([1 - p, p]), atol=1e-15)
+    _, r = oracle_mod.density(1, [G("h", (0,)), G("phaseflip", (0,), angle=p)])
+    np.testing.assert_allclose(r[0], 0.5 * np.array([[1, 1 - 2 * p], [1 - 2 * p, 1]]), atol=1e-15)
+    _, r = oracle_mod.density(1, [G("x", (0,)), G("ampdamp", (0,), angle=p)])
+    np.testing.assert_allclose(r[0], np.diag([p, 1 - p]), atol=1e-15)
+    _, r = oracle_mod.density(1, [G("h", (0,)), G("ampdamp", (0,), angle=p)])
+    ref = np.array([[(1 + p) / 2, math.sqrt(1 - p) / 2], [math.sqrt(1 - p) / 2, (1 - p) / 2]])
+    np.testing.assert_allclose(r[0], ref, atol=1e-15)
+    if p <= 0.75:
+        prep = [G("ry", (0,), angle=1.1), G("rz", (0,), angle=-0.6)]
+        _, r0 = oracle_mod.density(1, prep)
+        _, r1 = oracle_mod.density(1, prep + [G("depolarizing", (0,), angle=p)])
+        np.testing.assert_allclose(bloch(r1[0]), (1 - 4 * p / 3) * bloch(r0[0]), atol=1e-14)
+
+
+def test_noisy_circuits_stay_density_matrices(oracle_mod):
+    """Random circuits with channels on every qubit: trace 1, Hermitian,
+    positive semidefinite; the depolarizing channel at p = 3/4 leaves the
+    maximally mixed state on its qubit (partial trace = I/2)."""
+    rng = np.random.default_rng(8)
+    n = 3
+    gates = []
+    for _ in range(30):
+        k = ("h", "ry", "cnot", "rxx", "bitflip", "phaseflip", "depolarizing", "ampdamp")[rng.integers(8)]
+        if k in W.NOISE_KINDS:
+            gates.append(Gate(k, (int(rng.integers(n)),), angle=float(rng.uniform(0, 0.75))))
+        elif k in ("cnot", "rxx"):
+            a, b = rng.choice(n, size=2, replace=False)
+            gates.append(Gate(k, (int(a), int(b)), angle=float(rng.uniform(-3, 3))))
+        else:
+            gates.append(Gate(k, (int(rng.integers(n)),), angle=float(rng.uniform(-3, 3))))
+    _, r = oracle_mod.density(n, gates)
+    rho = r[0]
+    assert abs(np.trace(rho) - 1) < 1e-13
+    np.testing.assert_allclose(rho, rho.conj().T, atol=1e-14)
+    assert np.linalg.eigvalsh(rho).min() > -1e-13
+    _, r = oracle_mod.density(n, gates + [Gate("depolarizing", (1,), angle=0.75)])
+    red = np.einsum("ajbj->ab", r[0].reshape(2, 2, 2, 2, 2, 2).transpose(1, 0, 2, 4, 3, 5).reshape(2, 4, 2, 4))
+    np.testing.assert_allclose(red, np.eye(2) / 2, atol=1e-14)

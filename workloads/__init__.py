@@ -46,6 +46,9 @@ THREE_QUBIT = {"ccx"}
 PARAMETRIC = {"rx", "ry", "rz", "cp", "crx", "cry", "crz", "p", "u3", "rxx", "ryy", "rzz"}
 # consecutive parameter / feature slots a gate reads (U3: theta, phi, lam)
 ANGLE_SPAN = {"u3": 3}
+# single-qubit noise channels (density-matrix circuits only); the probability
+# is the gate's fixed `angle`
+NOISE_KINDS = ("bitflip", "phaseflip", "depolarizing", "ampdamp")
 
 MASK64 = (1 << 64) - 1
 BASE_SEED = 0x2512_18995
