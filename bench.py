@@ -324,6 +324,7 @@ def our_arm(args, rank, world, dist):
         extras["trotter30"] = trotter30(ctx, device)
         extras["sample30"] = sample30(ctx, device, hbm_peak, peak_kind)
         extras["hessian"] = hessian_hea(ctx, device)
+        extras["density"] = density_noisy(ctx, device)
         ctx.set_path({"auto": dq.PATH_AUTO, "plain": dq.PATH_PLAIN, "fused": dq.PATH_FUSED}[args.path])
 
     if rank == 0:
@@ -569,6 +570,49 @@ def hessian_hea(ctx, device):
     torch.cuda.empty_cache()
     out["speedup"] = out["plain"]["ms_per_hessian"] / out["fused"]["ms_per_hessian"]
     out["workload"] = wl.name
+    return out
+
+
+def density_gates(n=13, layers=4, p=0.01):
+    """Layered ansatz (RY, RZ, CNOT ring) with a depolarizing channel of
+    probability p on every qubit after each layer."""
+    g = []
+    for l in range(layers):
+        g += W.hea_layers(n, 1, first_param=2 * n * l)
+        g += [W.Gate("depolarizing", (q,), angle=p) for q in range(n)]
+    return g
+
+
+def density_noisy(ctx, device, n=13, layers=4):
+    """Noisy 13-qubit circuit as a density matrix (a 26-qubit vectorised
+    register, 512 MiB complex64): forward evolution and <sum Z>, fused vs
+    per-gate path."""
+    import torch
+    import paper_2512_18995_gb300 as dq
+    gates = density_gates(n, layers)
+    circ = dq.Circuit(n, gates, nparams=2 * n * layers)
+    obs = dq.Observables([W.obs_sum_z(n)])
+    params = torch.tensor(W.uniform_array(W._seed(13), 2 * n * layers, 0.0, 2 * np.pi), device=device)
+    out = {}
+    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+        ctx.set_path(path)
+        try:
+            ctx.density_forward(circ, params, obs, 1, torch.complex64)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.density_forward(circ, params, obs, 1, torch.complex64)
+            b.record()
+            torch.cuda.synchronize()
+        except RuntimeError as exc:
+            ctx.set_path(dq.PATH_AUTO)
+            return {"skipped": str(exc)[:120]}
+        out[name] = {"ms_per_step": a.elapsed_time(b)}
+    ctx.set_path(dq.PATH_AUTO)
+    out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
+    out["workload"] = f"density_hea{n}x{layers}_depolarizing_c64"
+    out["gates"] = len(gates)
     return out
 
 
