@@ -344,6 +344,10 @@ class Context:
         batch = int(data.shape[0]) if data is not None else 1
         dev = torch.device(f"cuda:{self.device}")
         P = circuit.nparams
+        # the shifted rows' scratch is sized inside the call: let the context
+        # grow its own workspace instead of an attached tensor
+        if self._ws is not None:
+            self.release_workspace()
         hess = torch.empty((P, P), dtype=torch.float64, device=dev)
         grad = torch.empty((P,), dtype=torch.float64, device=dev) if want_grad else None
         self._check(self.lib.dq_hessian(self.h, circuit.ref(), _ptr(params.to(torch.float64).contiguous()),

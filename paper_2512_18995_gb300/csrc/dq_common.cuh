@@ -40,8 +40,12 @@ enum GateClass : int {
     CLS_REAL = 1,      // real 2x2 (H, RY, CRY)
     CLS_DIAG = 2,      // diagonal (Z, S, RZ, CZ, CP, CRZ)
     CLS_ANTI = 3,      // X / CNOT: exchange
-    CLS_SWAP = 4       // SWAP of two qubits
+    CLS_SWAP = 4,      // SWAP of two qubits
+    CLS_PDIAG = 5      // diagonal in the parity of two bits (fused CNOT, diagonal, CNOT; fused engines only)
 };
+
+// Classes that act diagonally on every bit they touch.
+__host__ __device__ inline bool cls_diagonal(int cls) { return cls == CLS_DIAG || cls == CLS_PDIAG; }
 
 __host__ __device__ inline int gate_class(int kind) {
     switch (kind) {

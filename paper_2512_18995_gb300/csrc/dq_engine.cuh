@@ -44,7 +44,21 @@ enum Handler : int16_t {
     H_DUNI = 33,
     H_FAN = 34,     // first op of a controlled-phase fan (see decode_fans)
     H_FANM = 35,    // further members of a fan (consumed by its first op)
+    H_PDIAG = 36,   // parity-diagonal op (see parity_triple)
 };
+
+// Parity-diagonal ops.  CNOT(c -> t), a diagonal D = diag(d0, d1) on t,
+// CNOT(c -> t) is the diagonal op that multiplies an amplitude by d0 when
+// its bits t and c are equal and by d1 when they differ (the CNOT maps bit t
+// to t xor c for D and back), with D's generator and gradient slot.  The
+// fused planners replace such triples (RZZ, the inner part of RXX and RYY,
+// phase-flip superoperators of density circuits) by one op that needs no
+// tile or register bit; GOp carries t in (tl, tg) and c in (cl, cg).
+template <typename G>
+inline bool parity_triple(const G &a, const G &b, const G &c) {
+    return a.kind == DQ_CNOT && c.kind == DQ_CNOT && a.t == c.t && a.c == c.c && a.c >= 0 && b.cls == CLS_DIAG &&
+           b.c < 0 && b.t == a.t;
+}
 
 // One operation decoded for one register layout.  32 bytes.
 struct EOp {
@@ -105,6 +119,25 @@ inline EOp decode_op(const GOp &g, const int8_t *B, int M) {
             o.cmode = 2;
             o.carg = (int8_t)g.cg;
         }
+    }
+    if (g.cls == CLS_PDIAG) {
+        // a non-register bit's location: thread-local (mode 1) or block (mode 2)
+        auto where = [&](int lbit, int gbit, int8_t &mode, int8_t &arg) {
+            if (lbit >= 0) {
+                mode = 1;
+                arg = (int8_t)lbit;
+            } else {
+                mode = 2;
+                arg = (int8_t)gbit;
+            }
+        };
+        const int pt = g.tl >= 0 ? pos(g.tl) : -1, pc = g.cl >= 0 ? pos(g.cl) : -1;
+        // cmc: element mask of the register part of the parity (used in reverse)
+        o.cmc = (pt >= 0 ? regmask_h[pt] : 0u) ^ (pc >= 0 ? regmask_h[pc] : 0u);
+        o.h = H_PDIAG;
+        if (pt < 0) where(g.tl, g.tg, o.tmode, o.targ);
+        if (pc < 0) where(g.cl, g.cg, o.cmode, o.carg);
+        return o;
     }
     const bool ctrl = g.cg >= 0;
     if (g.cls == CLS_DIAG) {
@@ -250,7 +283,7 @@ inline void schedule_for_layouts(std::vector<GOp> &ops, int M, int lane_bits) {
     for (int j = 0; j < n; ++j) {
         const GOp &o = ops[j];
         int qs[2] = {o.tg, o.cg};
-        bool nd[2] = {o.cls != CLS_DIAG, false};
+        bool nd[2] = {!cls_diagonal(o.cls), false};
         for (int t = 0; t < 2; ++t) {
             const int q = qs[t];
             if (q < 0) continue;
@@ -265,7 +298,7 @@ inline void schedule_for_layouts(std::vector<GOp> &ops, int M, int lane_bits) {
             }
         }
     }
-    auto need = [&](const GOp &o) { return (o.cls != CLS_DIAG && o.tl >= lane_bits) ? o.tl : -1; };
+    auto need = [&](const GOp &o) { return (!cls_diagonal(o.cls) && o.tl >= lane_bits) ? o.tl : -1; };
     std::vector<int> ready, order;
     for (int j = 0; j < n; ++j)
         if (!indeg[j]) ready.push_back(j);
@@ -481,6 +514,25 @@ __device__ __forceinline__ void diag_uni(cx<R> (&a)[1 << M], const Mat2<R> &u, c
     for (int e = 0; e < (1 << M); ++e) a[e] = sel((cm >> e) & 1, cmul(f, a[e]), a[e]);
 }
 
+// Parity-diagonal ops (see parity_triple).  uni_bit reads a thread-uniform
+// bit (mode 1: thread-local index bit, mode 2: block base bit).
+__device__ __forceinline__ int uni_bit(int mode, int arg, const Layout &L, uint64_t base) {
+    return mode == 1 ? (int)((L.tb >> arg) & 1) : (int)((base >> arg) & 1);
+}
+
+// Forward parity-diagonal op: the element mask cmc holds the register part
+// of the parity (set at decode), (tmode, targ) and (cmode, carg) the bits
+// that are thread-uniform (mode 0: none).  One compact body for every
+// placement of the two bits (code size matters more than the selects).
+template <typename R, int M>
+__device__ __forceinline__ void eng_pdiag(cx<R> (&a)[1 << M], const EOp &o, const Mat2<R> &u, uint64_t base,
+                                          const Layout &L) {
+    const int upar = (o.tmode ? uni_bit(o.tmode, o.targ, L, base) : 0) ^ (o.cmode ? uni_bit(o.cmode, o.carg, L, base) : 0);
+    const cx<R> fe = upar ? u.m[3] : u.m[0], fo = upar ? u.m[0] : u.m[3];
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) a[e] = cmul(((o.cmc >> e) & 1) ? fo : fe, a[e]);
+}
+
 #define DQ_ENG_P(MACRO) MACRO(0) MACRO(1) MACRO(2) MACRO(3) MACRO(4)
 
 // Apply one op (u already daggered by the caller when un-applying).
@@ -488,7 +540,9 @@ __device__ __forceinline__ void diag_uni(cx<R> (&a)[1 << M], const Mat2<R> &u, c
 // control mask as selects, so every lane runs the same instructions and the
 // lane handlers' full-mask shuffles stay convergent, and a warp whose
 // controls are all off skips the op (a warp-uniform vote).
-template <typename R, int M>
+// PD: the kernel's programs may hold parity-diagonal ops (kernels are
+// compiled with and without them, to keep the common code small).
+template <typename R, int M, bool PD = false>
 __device__ __forceinline__ void eng_apply(cx<R> (&a)[1 << M], const EOp &o, const Mat2<R> &u, uint64_t base,
                                           const Layout &L, int lane) {
     if (o.h < H_GEN) {
@@ -507,6 +561,10 @@ __device__ __forceinline__ void eng_apply(cx<R> (&a)[1 << M], const EOp &o, cons
         DQ_ENG_P(DQ_CASE)
 #undef DQ_CASE
         }
+        return;
+    }
+    if (PD && o.h == H_PDIAG) {
+        eng_pdiag<R, M>(a, o, u, base, L);
         return;
     }
     if (o.h >= H_FAN) return;   // fans are run by eng_fan from their first op
@@ -721,7 +779,31 @@ __device__ __forceinline__ R adj_lane_at(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M
     return g;
 }
 
+// Reverse parity-diagonal op: gradient partial with the generator's weight
+// for the amplitude's parity (taken after the gate), then un-apply.  The
+// register part of the parity is the element mask cmc (set at decode), the
+// thread-uniform part comes from the (tmode, targ) and (cmode, carg) bits
+// that are not register bits (mode 0: none).
 template <typename R, int M, bool GRAD>
+__device__ __forceinline__ R adj_pdiag(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const EOp &o, const Mat2<R> &ud,
+                                       uint64_t base, const Layout &L) {
+    const int upar = (o.tmode ? uni_bit(o.tmode, o.targ, L, base) : 0) ^ (o.cmode ? uni_bit(o.cmode, o.carg, L, base) : 0);
+    R g = R(0), w0, w1;
+    diag_weights<R>(o.kind, w0, w1);
+    const cx<R> fe = upar ? ud.m[3] : ud.m[0], fo = upar ? ud.m[0] : ud.m[3];
+    const R we = upar ? w1 : w0, wo = upar ? w0 : w1;
+#pragma unroll
+    for (int e = 0; e < (1 << M); ++e) {
+        const bool odd = (o.cmc >> e) & 1;
+        if (GRAD) g += (odd ? wo : we) * (ls[e].x * ps[e].y - ls[e].y * ps[e].x);
+        const cx<R> f = odd ? fo : fe;
+        ps[e] = cmul(f, ps[e]);
+        ls[e] = cmul(f, ls[e]);
+    }
+    return g;
+}
+
+template <typename R, int M, bool GRAD, bool PD>
 __device__ __forceinline__ R eng_adjoint_g(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const EOp &o, const Mat2<R> &ud,
                                            uint64_t base, const Layout &L, int lane) {
     if (o.h < H_GEN) {
@@ -742,6 +824,7 @@ __device__ __forceinline__ R eng_adjoint_g(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 <<
         }
         return R(0);
     }
+    if (PD && o.h == H_PDIAG) return adj_pdiag<R, M, GRAD>(ps, ls, o, ud, base, L);
     const uint32_t cm = op_cmask(o, L, base);
     if (__all_sync(0xffffffffu, cm == 0)) return R(0);   // warp-uniform skip (see eng_apply)
     switch (o.h) {
@@ -764,11 +847,13 @@ __device__ __forceinline__ R eng_adjoint_g(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 <<
 }
 
 // One reverse step; the gradient partial is formed only for ops with a slot.
-template <typename R, int M>
+// PD: the kernel's reverse programs may hold parity-diagonal ops (compiled in
+// only where they can occur, to keep the other kernels' code small).
+template <typename R, int M, bool PD>
 __device__ __forceinline__ R eng_adjoint(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], const EOp &o, const Mat2<R> &ud,
                                          uint64_t base, const Layout &L, int lane) {
-    return o.slot >= 0 ? eng_adjoint_g<R, M, true>(ps, ls, o, ud, base, L, lane)
-                       : eng_adjoint_g<R, M, false>(ps, ls, o, ud, base, L, lane);
+    return o.slot >= 0 ? eng_adjoint_g<R, M, true, PD>(ps, ls, o, ud, base, L, lane)
+                       : eng_adjoint_g<R, M, false, PD>(ps, ls, o, ud, base, L, lane);
 }
 
 // ---------------------------------------------------------------------------

@@ -17,6 +17,7 @@ namespace dq {
 struct RowProgram {
     int n = 0, M = 0;
     int nacc_shared = 0, nacc_row = 0;
+    bool pdiag = false;            // holds parity-diagonal ops
     std::vector<EOp> fops, rops;   // op i decoded for its forward / reverse layout
     std::vector<ESeg> fsegs, rsegs;
     EOp *d_fops = nullptr, *d_rops = nullptr;

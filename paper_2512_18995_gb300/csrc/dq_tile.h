@@ -34,6 +34,7 @@ struct TPass {
     int op0 = 0, nops = 0;    // into the schedule's op array
     int rseg0 = 0, nrseg = 0; // reverse-sweep layouts (adjoint schedules)
     int slot0 = 0, nslot = 0; // gradient slots of the pass (adjoint schedules)
+    bool pdiag = false;       // holds parity-diagonal ops
 };
 
 // Passes of fused gates.  Adjoint schedules also carry, per pass, the ops

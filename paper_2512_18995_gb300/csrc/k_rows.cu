@@ -58,7 +58,7 @@ void build_segments(const std::vector<GOp> &ops, const std::vector<int> &order, 
     };
     for (size_t idx = 0; idx < order.size(); ++idx) {
         const GOp &o = ops[order[idx]];
-        const int need = (o.cls != CLS_DIAG && o.tl >= kLaneBits) ? o.tl : -1;
+        const int need = (!cls_diagonal(o.cls) && o.tl >= kLaneBits) ? o.tl : -1;
         if (need >= 0 && std::find(B.begin(), B.end(), need) == B.end()) {
             if ((int)B.size() < M) {
                 B.push_back(need);
@@ -113,6 +113,22 @@ bool rows_build_program(const Plan &p, int M, RowProgram &out) {
     std::vector<GOp> ops;
     for (int gi = 0; gi < p.ngates; ++gi) {
         const DevGate &g = p.gates[gi];
+        if (gi + 2 < p.ngates && parity_triple(g, p.gates[gi + 1], p.gates[gi + 2])) {
+            // CNOT, diagonal, CNOT: one parity-diagonal op with the diagonal's slot
+            const DevGate &d = p.gates[gi + 1];
+            GOp o{};
+            o.cls = CLS_PDIAG;
+            o.tl = o.tg = g.t;
+            o.cl = o.cg = g.c;
+            o.kind = d.kind;
+            o.coef = d.coef;
+            o.rowstep = d.rowstep;
+            o.slot = acc_of(d);
+            ops.push_back(o);
+            out.pdiag = true;
+            gi += 2;
+            continue;
+        }
         auto push = [&](int cls, int t, int c, int slot) {
             GOp o{};
             o.cls = cls;
@@ -186,7 +202,7 @@ __device__ __forceinline__ uint64_t wire_bits(uint64_t m, int n) { return m ? (_
 template <typename R, int M>
 constexpr int rows_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) <= 64) ? 512 : 256; }
 
-template <typename R, int M>
+template <typename R, int M, bool PD>
 __global__ void __launch_bounds__(rows_max_threads<R, M>(), sizeof(R) == 4 ? 2 : 1) k_rows(RowArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -252,7 +268,7 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>(), sizeof(R) == 4 ? 2 :
                 for (int oi = sg.op0; oi < sg.op0 + sg.nops; ++oi) {
                     const EOp o = sops[oi];
                     const Mat2<R> u = scoef[oi];
-                    eng_apply<R, M>(ps, o, u, 0, L, lane);
+                    eng_apply<R, M, PD>(ps, o, u, 0, L, lane);
                 }
             }
         }
@@ -357,7 +373,7 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>(), sizeof(R) == 4 ? 2 :
                     ++c;
                     continue;
                 }
-                const R g = eng_adjoint<R, M>(ps, ls, o, dagger(u), 0, L, lane);
+                const R g = eng_adjoint<R, M, PD>(ps, ls, o, dagger(u), 0, L, lane);
                 if (o.slot >= 0) {
                     // this row's partial over the warp's amplitude pairs
                     const R gs = warp_sum_t(g);
@@ -476,10 +492,11 @@ cudaError_t rows_launch(const RowProgram &rp, const Plan &p, const void *coef, c
     }
     constexpr int Mmax = sizeof(R) == 4 ? 4 : 3;
     const void *kfn = nullptr;
+    const bool pd = rp.pdiag;
     switch (rp.M) {
-    case 2: kfn = (const void *)k_rows<R, 2>; break;
-    case 3: kfn = (const void *)k_rows<R, 3>; break;
-    default: kfn = (const void *)k_rows<R, Mmax>; break;
+    case 2: kfn = pd ? (const void *)k_rows<R, 2, true> : (const void *)k_rows<R, 2, false>; break;
+    case 3: kfn = pd ? (const void *)k_rows<R, 3, true> : (const void *)k_rows<R, 3, false>; break;
+    default: kfn = pd ? (const void *)k_rows<R, Mmax, true> : (const void *)k_rows<R, Mmax, false>; break;
     }
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -489,10 +506,15 @@ cudaError_t rows_launch(const RowProgram &rp, const Plan &p, const void *coef, c
     const int grid = std::max(1, std::min(batch, std::min(per_sm, 4) * nsm));
     {
         LaunchScope ls(s, "k_rows", launches);
-        switch (rp.M) {
-        case 2: k_rows<R, 2><<<grid, threads, smem, s>>>(a); break;
-        case 3: k_rows<R, 3><<<grid, threads, smem, s>>>(a); break;
-        default: k_rows<R, Mmax><<<grid, threads, smem, s>>>(a); break;
+        switch (rp.M * 2 + (pd ? 1 : 0)) {
+        case 4: k_rows<R, 2, false><<<grid, threads, smem, s>>>(a); break;
+        case 5: k_rows<R, 2, true><<<grid, threads, smem, s>>>(a); break;
+        case 6: k_rows<R, 3, false><<<grid, threads, smem, s>>>(a); break;
+        case 7: k_rows<R, 3, true><<<grid, threads, smem, s>>>(a); break;
+        default:
+            if (pd) k_rows<R, Mmax, true><<<grid, threads, smem, s>>>(a);
+            else k_rows<R, Mmax, false><<<grid, threads, smem, s>>>(a);
+            break;
         }
     }
     e = cudaGetLastError();

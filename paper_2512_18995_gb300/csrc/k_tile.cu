@@ -80,6 +80,12 @@ struct GateBits {
     uint64_t D;   // bits acted on diagonally (controls, diagonal targets)
 };
 
+// A schedulable item: one gate, or a CNOT-diagonal-CNOT triple run as one
+// parity-diagonal op (acts diagonally on both of its bits).
+struct Item {
+    int g, len;
+};
+
 GateBits gate_bits(const DevGate &g) {
     GateBits gb{0, 0};
     if (g.cls == CLS_SWAP) {
@@ -109,30 +115,49 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
     out.M = M;
     out.adjoint = adjoint;
     const uint64_t lowmask = (uint64_t(1) << low) - 1;
-    // gates [0, g0) are left out (an adjoint sweep that stops before them)
+    // gates [0, g0) are left out (an adjoint sweep that stops before them);
+    // on forward passes parity triples become single items (the reverse
+    // kernel keeps them as three ops, which keeps its code smaller)
+    std::vector<Item> items;
+    for (int i = std::max(0, g0); i < p.ngates;) {
+        if (!adjoint && i + 2 < p.ngates && parity_triple(p.gates[i], p.gates[i + 1], p.gates[i + 2])) {
+            items.push_back({i, 3});
+            i += 3;
+        } else {
+            items.push_back({i, 1});
+            ++i;
+        }
+    }
+    auto item_bits = [&](const Item &it) {
+        if (it.len == 3) {
+            const DevGate &c = p.gates[it.g];
+            return GateBits{0, (uint64_t(1) << c.t) | (uint64_t(1) << c.c)};
+        }
+        return gate_bits(p.gates[it.g]);
+    };
     std::vector<int> remaining;
-    for (int i = std::max(0, g0); i < p.ngates; ++i) remaining.push_back(i);
+    for (int i = 0; i < (int)items.size(); ++i) remaining.push_back(i);
     int guard = 0;
     while (!remaining.empty()) {
         if (++guard > p.ngates + 2) return false;
         uint64_t T = lowmask, bnd = 0, bany = 0;
         std::vector<int> sched, deferred;
         int nops = 0;
-        for (int gi : remaining) {
-            const DevGate &g = p.gates[gi];
-            const GateBits gb = gate_bits(g);
-            const int cost = g.cls == CLS_SWAP ? 3 : 1;
+        for (int ii : remaining) {
+            const DevGate &g = p.gates[items[ii].g];
+            const GateBits gb = item_bits(items[ii]);
+            const int cost = (items[ii].len == 1 && g.cls == CLS_SWAP) ? 3 : 1;
             bool ok = !(gb.N & bany) && !(gb.D & bnd) && nops + cost <= kTileMaxOps;
             if (ok) {
                 const uint64_t nt = T | gb.N;
                 if (popc64(nt) <= k && dims_needed(nt, wb) <= 5) {
                     T = nt;
-                    sched.push_back(gi);
+                    sched.push_back(ii);
                     nops += cost;
                     continue;
                 }
             }
-            deferred.push_back(gi);
+            deferred.push_back(ii);
             bnd |= gb.N;
             bany |= gb.N | gb.D;
         }
@@ -168,7 +193,16 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
             o.slot = slot;
             gops.push_back(o);
         };
-        for (int gi : sched) {
+        for (int ii : sched) {
+            const Item &it = items[ii];
+            if (it.len == 3) {
+                const DevGate &c = p.gates[it.g], &d = p.gates[it.g + 1];
+                const int slot = it.g + 1 < (int)p.slot_of_gate.size() ? p.slot_of_gate[it.g + 1] : -1;
+                push_op(CLS_PDIAG, c.t, c.c, d, slot);
+                pass.pdiag = true;
+                continue;
+            }
+            const int gi = it.g;
             const DevGate &g = p.gates[gi];
             const int slot = gi < (int)p.slot_of_gate.size() ? p.slot_of_gate[gi] : -1;
             if (g.cls == CLS_SWAP) {
@@ -199,7 +233,7 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
         };
         for (int i = 0; i < pass.nops; ++i) {
             const GOp &o = gops[i];
-            const int need = (o.cls != CLS_DIAG && o.tl >= kTileLaneBits) ? o.tl : -1;
+            const int need = (!cls_diagonal(o.cls) && o.tl >= kTileLaneBits) ? o.tl : -1;
             if (need < 0 || std::find(B.begin(), B.end(), need) != B.end()) continue;
             if ((int)B.size() < M) {
                 B.push_back(need);
@@ -245,7 +279,7 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
             };
             for (int i = pass.nops - 1; i >= 0; --i) {
                 const GOp &o = gops[i];
-                const int need = (o.cls != CLS_DIAG && o.tl >= kTileLaneBits) ? o.tl : -1;
+                const int need = (!cls_diagonal(o.cls) && o.tl >= kTileLaneBits) ? o.tl : -1;
                 if (need >= 0 && std::find(RB.begin(), RB.end(), need) == RB.end()) {
                     if ((int)RB.size() < M) {
                         RB.push_back(need);
@@ -314,7 +348,7 @@ constexpr int tile_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) >= 256)
 template <typename R, int M>
 constexpr int tile_min_blocks() { return ((1 << M) * (int)sizeof(cx<R>) <= 64) ? 2 : 1; }
 
-template <typename R, int M>
+template <typename R, int M, bool PD>
 __global__ void __launch_bounds__(tile_max_threads<R, M>(), tile_min_blocks<R, M>())
 k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -419,7 +453,7 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
                     oi += eng_fan<R, M>(r, sops + oi, scoef + oi, base, L) - 1;
                     continue;
                 }
-                eng_apply<R, M>(r, o, scoef[oi], base, L, lane);
+                eng_apply<R, M, PD>(r, o, scoef[oi], base, L, lane);
             }
             // each thread writes back exactly the addresses it read in this
             // layout; the barrier orders them before the next layout's reads
@@ -507,12 +541,14 @@ void default_tile(int n, int &k, int &low, int &M) {
 }
 
 template <typename R>
-const void *tile_kernel(int M) {
+const void *tile_kernel(int M, bool pd) {
     switch (M) {
-    case 2: return (const void *)k_tile_fwd<R, 2>;
-    case 3: return (const void *)k_tile_fwd<R, 3>;
-    case 4: return (const void *)k_tile_fwd<R, 4>;
-    default: return (const void *)k_tile_fwd<R, (TileCfg<R>::Mmax)>;
+    case 2: return pd ? (const void *)k_tile_fwd<R, 2, true> : (const void *)k_tile_fwd<R, 2, false>;
+    case 3: return pd ? (const void *)k_tile_fwd<R, 3, true> : (const void *)k_tile_fwd<R, 3, false>;
+    case 4: return pd ? (const void *)k_tile_fwd<R, 4, true> : (const void *)k_tile_fwd<R, 4, false>;
+    default:
+        return pd ? (const void *)k_tile_fwd<R, (TileCfg<R>::Mmax), true>
+                  : (const void *)k_tile_fwd<R, (TileCfg<R>::Mmax), false>;
     }
 }
 
@@ -561,12 +597,10 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
     constexpr int wb = TileCfg<R>::wb;
     const int amp = (int)sizeof(cx<R>);
     const int threads = 1 << (sc.k - M);
-    const void *kfn = tile_kernel<R>(M);
     if (sc.fwd_state != state || sc.fwd_batch != batch || sc.fwd_launch.size() != sc.passes.size()) {
         // encode every pass once for this buffer
         sc.fwd_launch.assign(sc.passes.size(), TileSchedule::Launch{});
         sc.fwd_state = nullptr;
-        size_t smax = 0;
         for (size_t i = 0; i < sc.passes.size(); ++i) {
             const TPass &ps = sc.passes[i];
             TileDims d;
@@ -574,15 +608,16 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
             TileSchedule::Launch &L = sc.fwd_launch[i];
             if (!encode_map(tc.encode_fn, &L.map, d, state, batch, wb)) return cudaErrorInvalidValue;
             L.smem = tile_smem_bytes(sc.k, amp, ps.nops, ps.nseg);
-            smax = std::max(smax, L.smem);
-        }
-        if (tc.smem_set[kfn] < smax) {
-            cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-            if (e != cudaSuccess) return e;
-            tc.smem_set[kfn] = smax;
+            const void *kfn = tile_kernel<R>(M, ps.pdiag);
+            if (tc.smem_set[kfn] < L.smem) {
+                cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+                if (e != cudaSuccess) return e;
+                tc.smem_set[kfn] = L.smem;
+            }
         }
         for (size_t i = 0; i < sc.passes.size(); ++i) {
             TileSchedule::Launch &L = sc.fwd_launch[i];
+            const void *kfn = tile_kernel<R>(M, sc.passes[i].pdiag);
             int per_sm = 1;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, L.smem);
             per_sm = std::max(1, per_sm);
@@ -601,6 +636,7 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
         a.epi = TileEpi{};
         size_t smem = L.smem;
         int grid = L.grid;
+        const void *kfn = tile_kernel<R>(M, ps.pdiag);
         if (epi && i + 1 == sc.passes.size()) {
             // the last pass also measures the diagonal observables
             a.epi = *epi;
@@ -637,11 +673,18 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         cudaError_t e;
-        switch (M) {
-        case 2: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 2>, L.map, a); break;
-        case 3: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 3>, L.map, a); break;
-        case 4: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 4>, L.map, a); break;
-        default: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, (TileCfg<R>::Mmax)>, L.map, a); break;
+        const bool pd = ps.pdiag;
+        switch (M * 2 + (pd ? 1 : 0)) {
+        case 4: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 2, false>, L.map, a); break;
+        case 5: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 2, true>, L.map, a); break;
+        case 6: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 3, false>, L.map, a); break;
+        case 7: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 3, true>, L.map, a); break;
+        case 8: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 4, false>, L.map, a); break;
+        case 9: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 4, true>, L.map, a); break;
+        default:
+            e = pd ? cudaLaunchKernelEx(&cfg, k_tile_fwd<R, (TileCfg<R>::Mmax), true>, L.map, a)
+                   : cudaLaunchKernelEx(&cfg, k_tile_fwd<R, (TileCfg<R>::Mmax), false>, L.map, a);
+            break;
         }
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;

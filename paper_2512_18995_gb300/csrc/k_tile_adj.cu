@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __gr
                     ++cc;
                     continue;
                 }
-                const R gv = eng_adjoint<R, M>(ps, ls, o, dagger(u), base, L, lane);
+                const R gv = eng_adjoint<R, M, false>(ps, ls, o, dagger(u), base, L, lane);
                 if (o.slot >= 0) {
                     const R gs = warp_sum_t(gv);
                     if (lane == 0) accw[warp * a.nslot + o.slot] += gs;
