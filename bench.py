@@ -613,6 +613,29 @@ def density_noisy(ctx, device, n=13, layers=4):
     out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
     out["workload"] = f"density_hea{n}x{layers}_depolarizing_c64"
     out["gates"] = len(gates)
+    # gradients of the same kind of circuit at 10 qubits, 2 layers (40 parameters,
+    # 80 shifted density rows of 2^20 amplitudes)
+    ng, lg = 10, 2
+    gg = density_gates(ng, lg)
+    cg = dq.Circuit(ng, gg, nparams=2 * ng * lg)
+    og = dq.Observables([W.obs_sum_z(ng)])
+    pg = torch.tensor(W.uniform_array(W._seed(10), 2 * ng * lg, 0.0, 2 * np.pi), device=device)
+    grad = {}
+    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+        ctx.set_path(path)
+        ctx.density_grad(cg, pg, og, dtype=torch.complex64)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.density_grad(cg, pg, og, dtype=torch.complex64)
+        b.record()
+        torch.cuda.synchronize()
+        grad[name] = {"ms_per_gradient": a.elapsed_time(b)}
+    ctx.set_path(dq.PATH_AUTO)
+    grad["speedup"] = grad["plain"]["ms_per_gradient"] / grad["fused"]["ms_per_gradient"]
+    grad["workload"] = f"density_grad_hea{ng}x{lg}_depolarizing_c64"
+    out["grad"] = grad
     return out
 
 

@@ -385,6 +385,26 @@ DQ_API dq_status dq_density_forward(dq_ctx *ctx, const dq_circuit *circuit, cons
                                     const double *data, const dq_observables *obs, int batch, int dtype,
                                     double *expect_out, void *rho_out, void *stream);
 
+/* Gradient of L = sum_row sum_o w[row, o] Re Tr(O_o rho_row) for a density
+ * circuit (gates and noise channels, as in dq_density_forward) with respect
+ * to the shared trainable parameters.  The adjoint sweep of the pure-state
+ * path does not apply (channels have no inverse), so every angle occurrence
+ * is differentiated by exact shift rules on the expectation itself: the
+ * expectation is a trigonometric polynomial in each gate angle whatever the
+ * channels around the gate, with the frequencies of the pure case (two-term
+ * rule for eigenvalue gap 1, four-term rule for the controlled rotations).
+ * All shifted points times the data rows run as one batch of per-row
+ * parameters through the density path, chunked so that their vectorised
+ * matrices fit in max_bytes (0: a quarter of the free device memory).
+ *   expect_out: device FP64 batch * nobs (the unshifted expectations) or NULL.
+ *   grad_params: device FP64 nparams or NULL.  row_weights as in
+ *   dq_adjoint_grad.  Encoded inputs are held fixed.  Scratch lives in
+ *   context-owned device memory. */
+DQ_API dq_status dq_density_grad(dq_ctx *ctx, const dq_circuit *circuit, const double *params,
+                                 const double *data, const dq_observables *obs, const double *row_weights,
+                                 int batch, int dtype, size_t max_bytes, double *expect_out,
+                                 double *grad_params, void *stream);
+
 /* Hessian of L = sum_row sum_o w[row, o] <psi_row| O_o |psi_row> with respect
  * to the shared trainable parameters (the second derivatives of the paper's
  * gradient-and-Hessian benchmark, Sec. "Benchmarks").  Every angle slot of a

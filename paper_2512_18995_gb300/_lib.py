@@ -61,7 +61,8 @@ EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path"
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
            "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
            "dq_forward_grad_noalloc", "dq_apply_dense", "dq_sample_workspace_bytes", "dq_sample",
-           "dq_hessian", "dq_density_workspace_bytes", "dq_density_forward")
+           "dq_hessian", "dq_density_workspace_bytes", "dq_density_forward",
+           "dq_density_grad")
 
 _lib = None
 
@@ -106,6 +107,7 @@ def load_library(path: str = LIB_PATH):
         "dq_hessian": ([P, C, P, P, O, P, I, I, ctypes.c_size_t, P, P, P], I),
         "dq_density_forward": ([P, C, P, P, O, I, I, P, P, P], I),
         "dq_density_workspace_bytes": ([P, C, I, I, ctypes.POINTER(ctypes.c_size_t)], I),
+        "dq_density_grad": ([P, C, P, P, O, P, I, I, ctypes.c_size_t, P, P, P], I),
         "dq_sample": ([P, I, P, I, I, ctypes.c_int64, P, ctypes.c_uint64, ctypes.c_uint64, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -333,6 +335,24 @@ class Context:
                                                 dtype_code(dtype), _ptr(expect), _ptr(rho), _stream()),
                     "dq_density_forward")
         return expect, rho
+
+    def density_grad(self, circuit: Circuit, params: torch.Tensor, obs: Observables,
+                     data: Optional[torch.Tensor] = None, row_weights: Optional[torch.Tensor] = None,
+                     dtype: torch.dtype = torch.complex64, max_bytes: int = 0):
+        """(expectations (batch, nobs), gradient (nparams,)) of a density
+        circuit's weighted expectation sum, by exact shift rules."""
+        batch = int(data.shape[0]) if data is not None else 1
+        dev = torch.device(f"cuda:{self.device}")
+        expect = torch.empty((batch, obs.nobs), dtype=torch.float64, device=dev)
+        grad = torch.empty((circuit.nparams,), dtype=torch.float64, device=dev)
+        if self._ws is not None:   # scratch is sized inside the call
+            self.release_workspace()
+        self._check(self.lib.dq_density_grad(self.h, circuit.ref(), _ptr(params.to(torch.float64).contiguous()),
+                                             _ptr(data.to(torch.float64).contiguous() if data is not None else None),
+                                             obs.ref(), _ptr(row_weights), batch, dtype_code(dtype),
+                                             ctypes.c_size_t(int(max_bytes)), _ptr(expect), _ptr(grad), _stream()),
+                    "dq_density_grad")
+        return expect, grad
 
     def hessian(self, circuit: Circuit, params: torch.Tensor, obs: Observables, data: Optional[torch.Tensor] = None,
                 row_weights: Optional[torch.Tensor] = None, dtype: torch.dtype = torch.complex64,

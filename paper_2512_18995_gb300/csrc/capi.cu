@@ -1359,7 +1359,124 @@ dq_status dq_expect(dq_ctx *ctx, int nqubits, const dq_observables *obs, const v
                            : expect_impl<double>(ctx, nqubits, *o, state, batch, out, s);
 }
 
+}  // extern "C"
+
+namespace {
+
+// ---- shift rules (see k_hessian.cu) ----------------------------------------
+// Every angle slot of a gate with a trainable parameter is an occurrence with
+// its own virtual parameter; its shift rows (angle offset, weight) give the
+// derivative of anything trigonometric in that angle: the two-term rule for
+// generators with eigenvalue gap 1, the four-term rule for the controlled
+// rotations (gaps 1/2 and 1).
+struct ShiftPlan {
+    std::vector<dq_gate> vg;             // gates with param_idx renumbered to occurrences
+    std::vector<int32_t> occ;            // occurrence -> parameter
+    std::vector<int32_t> sv, vrow0, nshift;
+    std::vector<double> sh, coef;        // per shift row: angle offset, weight
+    std::vector<int32_t> optr, oidx;     // parameter -> occurrences (CSR)
+    int V = 0, J = 0;
+};
+
+ShiftPlan make_shift_plan(const dq_circuit &c) {
+    ShiftPlan sp;
+    sp.vg.assign(c.gates, c.gates + c.ngates);
+    std::vector<char> four;
+    for (dq_gate &g : sp.vg) {
+        if (g.param_idx < 0) continue;
+        const int span = g.kind == DQ_U3 ? 3 : 1;
+        const int v0 = (int)sp.occ.size();
+        for (int k = 0; k < span; ++k) {
+            sp.occ.push_back(g.param_idx + k);
+            four.push_back(g.kind == DQ_CRX || g.kind == DQ_CRY || g.kind == DQ_CRZ);
+        }
+        g.param_idx = v0;
+    }
+    sp.V = (int)sp.occ.size();
+    const double h = 1.5707963267948966, r2 = 1.4142135623730951;
+    const double c1 = (r2 + 1.0) / (4.0 * r2), c2 = (r2 - 1.0) / (4.0 * r2);
+    sp.vrow0.resize(sp.V);
+    sp.nshift.resize(sp.V);
+    for (int v = 0; v < sp.V; ++v) {
+        sp.vrow0[v] = (int32_t)sp.sv.size();
+        auto add = [&](double d, double w) {
+            sp.sv.push_back(v);
+            sp.sh.push_back(d);
+            sp.coef.push_back(w);
+        };
+        if (four[v]) {
+            add(h, c1); add(-h, -c1); add(3 * h, -c2); add(-3 * h, c2);
+        } else {
+            add(h, 0.5); add(-h, -0.5);
+        }
+        sp.nshift[v] = (int32_t)sp.sv.size() - sp.vrow0[v];
+    }
+    sp.J = (int)sp.sv.size();
+    const int P = c.nparams;
+    sp.optr.assign(P + 1, 0);
+    sp.oidx.resize(sp.V);
+    for (int v = 0; v < sp.V; ++v) ++sp.optr[sp.occ[v] + 1];
+    for (int q = 0; q < P; ++q) sp.optr[q + 1] += sp.optr[q];
+    std::vector<int32_t> fill(sp.optr.begin(), sp.optr.end() - 1);
+    for (int v = 0; v < sp.V; ++v) sp.oidx[fill[sp.occ[v]]++] = v;
+    return sp;
+}
+
+// Largest number of leading occurrences per chunk whose shifted rows (times
+// the data rows) fit rows_cap rows; at least one.
+int shift_chunk(const ShiftPlan &sp, int batch, int64_t rows_cap) {
+    int vchunk = sp.V;
+    while (vchunk > 1) {
+        int64_t rows = 0;
+        for (int v = 0; v < vchunk; ++v) rows += (int64_t)sp.nshift[v] * batch;
+        if (rows <= rows_cap) break;
+        vchunk = (vchunk + 1) / 2;
+    }
+    return vchunk;
+}
+
+// Context-owned device buffer of at least `bytes` (grown after the stream is idle).
+dq_status grow_buffer(dq_ctx *ctx, char **buf, size_t *have, size_t bytes, cudaStream_t s, const char *what) {
+    if (bytes <= *have) return DQ_OK;
+    cudaStreamSynchronize(s);
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (cudaMalloc((void **)buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, DQ_ERR_OOM, "cannot allocate %zu bytes for %s", bytes, what);
+    }
+    *have = bytes;
+    return DQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 // ---- density matrices (see dq_density_forward in dq.h) ----------------------
+}  // extern "C"
+
+namespace {
+
+// rho <- the density circuit applied to |0><0| for `rows` rows, then the
+// expectations (when out is not NULL).
+template <typename R>
+dq_status density_run(dq_ctx *ctx, Plan &p, ObsDev *o, const double *params, const double *data, int rows,
+                      double *out, void *rho, cudaStream_t s) {
+    DQ_CUDA(plain_init_zero<R>(rho, p.n, rows, s, &ctx->launches), "density init");
+    dq_status st = DQ_OK;
+    if (p.ngates > 0 && (st = apply_impl<R>(ctx, p, params, data, rho, rows, s)) != DQ_OK) return st;
+    if (o && out)
+        DQ_CUDA(density_expect<R>(rho, p.n / 2, o->d_bits, o->d_ptr, o->nobs, rows, out, s, &ctx->launches),
+                "density expect");
+    return DQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 dq_status dq_density_forward(dq_ctx *ctx, const dq_circuit *circuit, const double *params, const double *data,
                              const dq_observables *obs, int batch, int dtype, double *expect_out, void *rho_out,
                              void *stream) {
@@ -1397,20 +1514,116 @@ dq_status dq_density_forward(dq_ctx *ctx, const dq_circuit *circuit, const doubl
         }
         rho = ctx->dbuf;
     }
-    if (dtype == DQ_C64) {
-        DQ_CUDA(plain_init_zero<float>(rho, p->n, batch, s, &ctx->launches), "density init");
-        if (p->ngates > 0 && (st = apply_impl<float>(ctx, *p, params, data, rho, batch, s)) != DQ_OK) return st;
-        if (o && expect_out)
-            DQ_CUDA(density_expect<float>(rho, n, o->d_bits, o->d_ptr, o->nobs, batch, expect_out, s, &ctx->launches),
-                    "density expect");
-    } else {
-        DQ_CUDA(plain_init_zero<double>(rho, p->n, batch, s, &ctx->launches), "density init");
-        if (p->ngates > 0 && (st = apply_impl<double>(ctx, *p, params, data, rho, batch, s)) != DQ_OK) return st;
-        if (o && expect_out)
-            DQ_CUDA(density_expect<double>(rho, n, o->d_bits, o->d_ptr, o->nobs, batch, expect_out, s,
-                                           &ctx->launches),
-                    "density expect");
+    return dtype == DQ_C64 ? density_run<float>(ctx, *p, o, params, data, batch, expect_out, rho, s)
+                           : density_run<double>(ctx, *p, o, params, data, batch, expect_out, rho, s);
+}
+
+dq_status dq_density_grad(dq_ctx *ctx, const dq_circuit *circuit, const double *params, const double *data,
+                          const dq_observables *obs, const double *row_weights, int batch, int dtype,
+                          size_t max_bytes, double *expect_out, double *grad_params, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (batch < 1) return fail(ctx, DQ_ERR_INVALID_ARG, "batch must be >= 1");
+    if (!obs) return fail(ctx, DQ_ERR_INVALID_ARG, "observables are NULL");
+    Plan *p = nullptr;
+    if ((st = get_plan(ctx, circuit, 0, &p, true)) != DQ_OK) return st;
+    const int n = circuit->nqubits;
+    ObsDev *o = nullptr;
+    if ((st = get_obs(ctx, obs, n, &o)) != DQ_OK) return st;
+    if ((st = check_angles(ctx, *p, params, data)) != DQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t amp = (size_t)amp_bytes(dtype);
+    if (expect_out) {
+        if ((st = grow_buffer(ctx, &ctx->dbuf, &ctx->dbuf_bytes, ((size_t)batch << (2 * n)) * amp, s,
+                              "the density matrices")) != DQ_OK)
+            return st;
+        st = dtype == DQ_C64 ? density_run<float>(ctx, *p, o, params, data, batch, expect_out, ctx->dbuf, s)
+                             : density_run<double>(ctx, *p, o, params, data, batch, expect_out, ctx->dbuf, s);
+        if (st != DQ_OK) return st;
     }
+    const int P = circuit->nparams;
+    if (!grad_params || P == 0) return DQ_OK;
+    const ShiftPlan sp = make_shift_plan(*circuit);
+    if (sp.V == 0) {
+        DQ_CUDA(cudaMemsetAsync(grad_params, 0, sizeof(double) * (size_t)P, s), "memset");
+        return DQ_OK;
+    }
+    dq_circuit vc = *circuit;
+    vc.gates = sp.vg.data();
+    vc.nparams = sp.V;
+    Plan *pv = nullptr;
+    if ((st = get_plan(ctx, &vc, 1, &pv, true)) != DQ_OK) return st;
+    // shifted rows per chunk: their density matrices within the memory bound
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t per_row = (amp << (2 * n)) + sizeof(double) * (size_t)(sp.V + p->nfeat + o->nobs) + 512;
+    const size_t budget = max_bytes ? max_bytes : std::max<size_t>(free_b / 4, (size_t)1 << 28);
+    const int vchunk = shift_chunk(sp, batch, std::max<int64_t>(1, (int64_t)(budget / per_row)));
+    int maxJ = 0;
+    for (int v0 = 0; v0 < sp.V; v0 += vchunk) {
+        int j = 0;
+        for (int v = v0; v < std::min(sp.V, v0 + vchunk); ++v) j += sp.nshift[v];
+        maxJ = std::max(maxJ, j);
+    }
+    const int64_t Rmax = (int64_t)maxJ * batch;
+    if (Rmax >= ((int64_t)1 << 31)) return fail(ctx, DQ_ERR_UNSUPPORTED, "too many shifted rows");
+    Arena a;
+    a.measuring = true;
+    auto layout = [&](Arena &ar, void **ptrs) {
+        ptrs[0] = ar.take(sizeof(int32_t) * sp.V);                             // occ
+        ptrs[1] = ar.take(sizeof(int32_t) * sp.J);                             // shift_v
+        ptrs[2] = ar.take(sizeof(double) * sp.J);                              // shift
+        ptrs[3] = ar.take(sizeof(double) * sp.J);                              // coef
+        ptrs[4] = ar.take(sizeof(int32_t) * sp.V);                             // vrow0
+        ptrs[5] = ar.take(sizeof(int32_t) * sp.V);                             // nshift
+        ptrs[6] = ar.take(sizeof(int32_t) * (P + 1));                          // optr
+        ptrs[7] = ar.take(sizeof(int32_t) * sp.V);                             // oidx
+        ptrs[8] = ar.take(sizeof(double) * sp.V);                              // per-occurrence gradient
+        ptrs[9] = ar.take(sizeof(double) * (size_t)Rmax * sp.V);               // row params
+        ptrs[10] = ar.take(sizeof(double) * (size_t)Rmax * std::max(1, p->nfeat));
+        ptrs[11] = ar.take(sizeof(double) * (size_t)Rmax * o->nobs);           // row expectations
+        ptrs[12] = ar.take(((size_t)Rmax << (2 * n)) * amp);                   // row density matrices
+    };
+    void *ptr[13];
+    layout(a, ptr);
+    if ((st = grow_buffer(ctx, &ctx->hbuf, &ctx->hbuf_bytes, a.used, s, "the shifted density rows")) != DQ_OK)
+        return st;
+    Arena w;
+    w.base = ctx->hbuf;
+    w.cap = ctx->hbuf_bytes;
+    layout(w, ptr);
+    int32_t *d_occ = (int32_t *)ptr[0], *d_sv = (int32_t *)ptr[1], *d_vrow0 = (int32_t *)ptr[4],
+            *d_nshift = (int32_t *)ptr[5], *d_optr = (int32_t *)ptr[6], *d_oidx = (int32_t *)ptr[7];
+    double *d_sh = (double *)ptr[2], *d_coef = (double *)ptr[3], *d_gv = (double *)ptr[8], *d_prow = (double *)ptr[9],
+           *d_drow = (double *)ptr[10], *d_E = (double *)ptr[11];
+    void *d_rho = ptr[12];
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    DQ_CUDA(up(d_occ, sp.occ.data(), sizeof(int32_t) * sp.V), "shift tables");
+    DQ_CUDA(up(d_sv, sp.sv.data(), sizeof(int32_t) * sp.J), "shift tables");
+    DQ_CUDA(up(d_sh, sp.sh.data(), sizeof(double) * sp.J), "shift tables");
+    DQ_CUDA(up(d_coef, sp.coef.data(), sizeof(double) * sp.J), "shift tables");
+    DQ_CUDA(up(d_vrow0, sp.vrow0.data(), sizeof(int32_t) * sp.V), "shift tables");
+    DQ_CUDA(up(d_nshift, sp.nshift.data(), sizeof(int32_t) * sp.V), "shift tables");
+    DQ_CUDA(up(d_optr, sp.optr.data(), sizeof(int32_t) * (P + 1)), "shift tables");
+    DQ_CUDA(up(d_oidx, sp.oidx.data(), sizeof(int32_t) * sp.V), "shift tables");
+    for (int v0 = 0; v0 < sp.V; v0 += vchunk) {
+        const int v1 = std::min(sp.V, v0 + vchunk);
+        const int j0 = sp.vrow0[v0], jn = (v1 < sp.V ? sp.vrow0[v1] : sp.J) - j0;
+        const int R = jn * batch;
+        DQ_CUDA(hess_rows(params, d_occ, sp.V, d_sv + j0, d_sh + j0, jn, batch, data, p->nfeat, nullptr, o->nobs,
+                          d_prow, d_drow, nullptr, ctx->nsm, s, &ctx->launches),
+                "shifted rows");
+        st = dtype == DQ_C64 ? density_run<float>(ctx, *pv, o, d_prow, data ? d_drow : nullptr, R, d_E, d_rho, s)
+                             : density_run<double>(ctx, *pv, o, d_prow, data ? d_drow : nullptr, R, d_E, d_rho, s);
+        if (st != DQ_OK) return st;
+        DQ_CUDA(shift_combine(d_E, row_weights, d_vrow0 + v0, d_nshift + v0, d_coef, j0, v1 - v0, v0, batch,
+                              o->nobs, d_gv, s, &ctx->launches),
+                "shift combine");
+    }
+    DQ_CUDA(shift_fold(d_gv, d_optr, d_oidx, P, grad_params, s, &ctx->launches), "gradient fold");
     return DQ_OK;
 }
 

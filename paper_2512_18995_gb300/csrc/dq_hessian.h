@@ -14,4 +14,14 @@ cudaError_t hess_combine(const double *G, const int32_t *vrow0, const int32_t *n
 cudaError_t hess_fold(const double *Ht, const int32_t *optr, const int32_t *oidx, int P, int V, double *H,
                       cudaStream_t s, int64_t *launches);
 
+// Gradients of expectations by shift rules (density circuits):
+// g[v0 + vl] = sum_s coef[j_s] sum_r sum_o w[r][o] E[((j_s - j0) * batch + r) * nobs + o]
+// over the shift rows j_s of local occurrence vl (w = NULL: ones).
+cudaError_t shift_combine(const double *E, const double *w, const int32_t *vrow0, const int32_t *nshift,
+                          const double *coef, int j0, int nv, int v0, int batch, int nobs, double *g, cudaStream_t s,
+                          int64_t *launches);
+// grad[p] = sum over occurrences v of p of g[v].
+cudaError_t shift_fold(const double *g, const int32_t *optr, const int32_t *oidx, int P, double *grad, cudaStream_t s,
+                       int64_t *launches);
+
 }  // namespace dq

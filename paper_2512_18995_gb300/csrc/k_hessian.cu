@@ -94,6 +94,36 @@ k_hess_fold(const double *__restrict__ Ht, const int32_t *__restrict__ optr, con
     H[i] = acc;
 }
 
+// Expectation-level shift rules: one thread per local occurrence (the rows
+// and observables are summed in a fixed order).
+__global__ void __launch_bounds__(kThreads)
+k_shift_combine(const double *__restrict__ E, const double *__restrict__ w, const int32_t *__restrict__ vrow0,
+                const int32_t *__restrict__ nshift, const double *__restrict__ coef, int j0, int nv, int v0, int batch,
+                int nobs, double *__restrict__ g) {
+    const int vl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (vl >= nv) return;
+    double acc = 0.0;
+    for (int s = 0; s < nshift[vl]; ++s) {
+        const int j = vrow0[vl] + s;
+        double sum = 0.0;
+        for (int r = 0; r < batch; ++r)
+            for (int o = 0; o < nobs; ++o)
+                sum += (w ? w[(int64_t)r * nobs + o] : 1.0) * E[((int64_t)(j - j0) * batch + r) * nobs + o];
+        acc += coef[j] * sum;
+    }
+    g[v0 + vl] = acc;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_shift_fold(const double *__restrict__ g, const int32_t *__restrict__ optr, const int32_t *__restrict__ oidx, int P,
+             double *__restrict__ grad) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    double acc = 0.0;
+    for (int a = optr[p]; a < optr[p + 1]; ++a) acc += g[oidx[a]];
+    grad[p] = acc;
+}
+
 unsigned blocks_for(int64_t work, int nsm) {
     const int64_t b = (work + kThreads - 1) / kThreads;
     const int64_t cap = (int64_t)nsm * 32;
@@ -127,6 +157,22 @@ cudaError_t hess_fold(const double *Ht, const int32_t *optr, const int32_t *oidx
     const int64_t work = (int64_t)P * P;
     LaunchScope ls(s, "k_hess_fold", launches);
     k_hess_fold<<<(unsigned)((work + kThreads - 1) / kThreads), kThreads, 0, s>>>(Ht, optr, oidx, P, V, H);
+    return cudaGetLastError();
+}
+
+cudaError_t shift_combine(const double *E, const double *w, const int32_t *vrow0, const int32_t *nshift,
+                          const double *coef, int j0, int nv, int v0, int batch, int nobs, double *g, cudaStream_t s,
+                          int64_t *launches) {
+    LaunchScope ls(s, "k_shift_combine", launches);
+    k_shift_combine<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(E, w, vrow0, nshift, coef, j0, nv,
+                                                                                   v0, batch, nobs, g);
+    return cudaGetLastError();
+}
+
+cudaError_t shift_fold(const double *g, const int32_t *optr, const int32_t *oidx, int P, double *grad, cudaStream_t s,
+                       int64_t *launches) {
+    LaunchScope ls(s, "k_shift_fold", launches);
+    k_shift_fold<<<(unsigned)((P + kThreads - 1) / kThreads), kThreads, 0, s>>>(g, optr, oidx, P, grad);
     return cudaGetLastError();
 }
 

@@ -111,3 +111,55 @@ def test_density_rejects_bad_arguments(ctx):
                             dev(np.array([0.1])), None)
     with pytest.raises(dq.DQError, match="17"):
         ctx.density_forward(dq.Circuit(18, [W.Gate("h", (0,))]), None, None)
+
+
+def fd_density_grad(n, gates, obs, params, data, w, h=1e-5):
+    """Central differences of the oracle's weighted expectation sum."""
+    def loss(pv):
+        e, _ = oracle.density(n, gates, obs, pv, data, batch=data.shape[0])
+        return float(np.sum(w * e))
+    g = np.zeros(params.size)
+    for i in range(params.size):
+        d = np.zeros(params.size)
+        d[i] = h
+        g[i] = (loss(params + d) - loss(params - d)) / (2 * h)
+    return g
+
+
+@pytest.mark.parametrize("dtype", sorted(DTYPES))
+@pytest.mark.parametrize("n,batch,depth", [(1, 2, 12), (3, 2, 30), (4, 3, 36), (6, 1, 40)])
+def test_density_gradients_match_finite_differences(ctx, dtype, n, batch, depth):
+    """Shift-rule gradients of noisy circuits (every parametric kind,
+    including the four-term controlled rotations, U3 and shared parameters)
+    against central differences of the oracle."""
+    ctx.set_path(dq.PATH_AUTO)
+    dt = DTYPES[dtype]
+    rng = np.random.default_rng(2300 + 5 * n + batch)
+    gates, npar = noisy_gates(n, depth, rng, nfeat=3)
+    if npar > 1:
+        gates.append(W.Gate("rx", (0,), param=0))   # parameter 0 used twice
+    params = rng.uniform(-3, 3, size=npar)
+    data = rng.uniform(-3, 3, size=(batch, 3))
+    obs = [W.obs_tfim_open(n, 0.5) if n > 1 else W.obs_z(0), [(0.6, (1 << n) - 1, 1)]]
+    w = rng.normal(size=(batch, 2))
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=3)
+    e, g = ctx.density_grad(circ, dev(params), dq.Observables(obs), data=dev(data), row_weights=dev(w), dtype=dt)
+    e_ref, _ = oracle.density(n, gates, obs, params, data, batch=batch)
+    g_ref = fd_density_grad(n, gates, obs, params, data, w)
+    assert_rel(e.cpu().numpy(), e_ref, dt, "expectations", floor=obs_scale(obs))
+    scale = float(np.abs(w).max(axis=1).sum()) * obs_scale(obs)
+    err = np.max(np.abs(g.cpu().numpy() - g_ref)) / scale
+    assert err <= (1e-4 if dt == torch.complex64 else 1e-8), f"gradient error {err:.3e} (relative to {scale:.3f})"
+
+
+def test_density_gradients_in_chunks(ctx):
+    """A memory bound of one occurrence per batched call gives the same gradient."""
+    n = 5
+    rng = np.random.default_rng(9)
+    gates, npar = noisy_gates(n, 40, rng, nfeat=0)
+    params = rng.uniform(-3, 3, size=npar)
+    obs = [W.obs_tfim_open(n, 0.5)]
+    circ = dq.Circuit(n, gates, nparams=npar)
+    _, g1 = ctx.density_grad(circ, dev(params), dq.Observables(obs), dtype=torch.complex128)
+    _, g2 = ctx.density_grad(circ, dev(params), dq.Observables(obs), dtype=torch.complex128, max_bytes=1 << 12)
+    torch.testing.assert_close(g1, g2, atol=1e-12, rtol=0)
