@@ -1500,18 +1500,8 @@ dq_status dq_density_forward(dq_ctx *ctx, const dq_circuit *circuit, const doubl
     const size_t bytes = ((size_t)batch << (2 * n)) * (size_t)amp_bytes(dtype);
     void *rho = rho_out;
     if (!rho) {
-        if (bytes > ctx->dbuf_bytes) {
-            cudaStreamSynchronize(s);
-            if (ctx->dbuf) cudaFree(ctx->dbuf);
-            ctx->dbuf = nullptr;
-            ctx->dbuf_bytes = 0;
-            cudaError_t e = cudaMalloc((void **)&ctx->dbuf, bytes);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                return fail(ctx, DQ_ERR_OOM, "cannot allocate %zu bytes for the density matrices", bytes);
-            }
-            ctx->dbuf_bytes = bytes;
-        }
+        if ((st = grow_buffer(ctx, &ctx->dbuf, &ctx->dbuf_bytes, bytes, s, "the density matrices")) != DQ_OK)
+            return st;
         rho = ctx->dbuf;
     }
     return dtype == DQ_C64 ? density_run<float>(ctx, *p, o, params, data, batch, expect_out, rho, s)
@@ -1645,57 +1635,20 @@ dq_status dq_hessian(dq_ctx *ctx, const dq_circuit *circuit, const double *param
     cudaStream_t s = (cudaStream_t)stream;
     const int P = circuit->nparams;
     if (P == 0) return DQ_OK;
-    // occurrences: every angle slot of a gate with a trainable parameter
-    std::vector<dq_gate> vg(circuit->gates, circuit->gates + circuit->ngates);
-    std::vector<int32_t> occ;
-    std::vector<char> four;
-    for (dq_gate &g : vg) {
-        if (g.param_idx < 0) continue;
-        const int span = g.kind == DQ_U3 ? 3 : 1;
-        const int v0 = (int)occ.size();
-        for (int k = 0; k < span; ++k) {
-            occ.push_back(g.param_idx + k);
-            four.push_back(g.kind == DQ_CRX || g.kind == DQ_CRY || g.kind == DQ_CRZ);
-        }
-        g.param_idx = v0;
-    }
-    const int V = (int)occ.size();
+    const ShiftPlan sp = make_shift_plan(*circuit);
+    const int V = sp.V;
     if (V == 0) {
         DQ_CUDA(cudaMemsetAsync(hess, 0, sizeof(double) * (size_t)P * P, s), "memset");
     } else {
         dq_circuit vc = *circuit;
-        vc.gates = vg.data();
+        vc.gates = sp.vg.data();
         vc.nparams = V;
         Plan *pv = nullptr;
         if ((st = get_plan(ctx, &vc, 1, &pv)) != DQ_OK) return st;
-        // shift rows, grouped by occurrence
-        const double h = 1.5707963267948966, r2 = 1.4142135623730951;
-        const double c1 = (r2 + 1.0) / (4.0 * r2), c2 = (r2 - 1.0) / (4.0 * r2);
-        std::vector<int32_t> sv, vrow0(V), nshift(V);
-        std::vector<double> sh, coef;
-        for (int v = 0; v < V; ++v) {
-            vrow0[v] = (int32_t)sv.size();
-            auto add = [&](double d, double c) {
-                sv.push_back(v);
-                sh.push_back(d);
-                coef.push_back(c);
-            };
-            if (four[v]) {
-                add(h, c1); add(-h, -c1); add(3 * h, -c2); add(-3 * h, c2);
-            } else {
-                add(h, 0.5); add(-h, -0.5);
-            }
-            nshift[v] = (int32_t)sv.size() - vrow0[v];
-        }
-        const int J = (int)sv.size();
-        // occurrence lists per parameter (CSR)
-        std::vector<int32_t> optr(P + 1, 0), oidx(V);
-        for (int v = 0; v < V; ++v) ++optr[occ[v] + 1];
-        for (int q = 0; q < P; ++q) optr[q + 1] += optr[q];
-        {
-            std::vector<int32_t> fill(optr.begin(), optr.end() - 1);
-            for (int v = 0; v < V; ++v) oidx[fill[occ[v]]++] = v;
-        }
+        const std::vector<int32_t> &occ = sp.occ, &sv = sp.sv, &vrow0 = sp.vrow0, &nshift = sp.nshift,
+                                   &optr = sp.optr, &oidx = sp.oidx;
+        const std::vector<double> &sh = sp.sh, &coef = sp.coef;
+        const int J = sp.J;
         // chunk of occurrences per batched call: the rows' states (psi and
         // lambda on the tiled path) within a quarter of the free memory
         size_t free_b = 0, total_b = 0;
@@ -1706,13 +1659,7 @@ dq_status dq_hessian(dq_ctx *ctx, const dq_circuit *circuit, const double *param
         int64_t rows_cap = (int64_t)(budget / per_row);
         rows_cap = std::min<int64_t>(rows_cap, (int64_t)1 << 30);
         // tables: occ, shift rows, vrow0/nshift, CSR, H~, then per-chunk rows
-        int vchunk = V;
-        while (vchunk > 1) {
-            int64_t rows = 0;
-            for (int v = 0; v < vchunk; ++v) rows += (int64_t)nshift[v] * batch;   // upper bound by first chunk
-            if (rows <= rows_cap) break;
-            vchunk = (vchunk + 1) / 2;
-        }
+        const int vchunk = shift_chunk(sp, batch, rows_cap);
         int maxJ = 0;
         for (int v0 = 0; v0 < V; v0 += vchunk) {
             int j = 0;
@@ -1740,18 +1687,8 @@ dq_status dq_hessian(dq_ctx *ctx, const dq_circuit *circuit, const double *param
         };
         void *ptr[13];
         layout(a, ptr);
-        if (a.used > ctx->hbuf_bytes) {
-            cudaStreamSynchronize(s);
-            if (ctx->hbuf) cudaFree(ctx->hbuf);
-            ctx->hbuf = nullptr;
-            ctx->hbuf_bytes = 0;
-            cudaError_t e = cudaMalloc((void **)&ctx->hbuf, a.used);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                return fail(ctx, DQ_ERR_OOM, "cannot allocate %zu bytes for the Hessian's row tables", a.used);
-            }
-            ctx->hbuf_bytes = a.used;
-        }
+        if ((st = grow_buffer(ctx, &ctx->hbuf, &ctx->hbuf_bytes, a.used, s, "the Hessian's row tables")) != DQ_OK)
+            return st;
         Arena w;
         w.base = ctx->hbuf;
         w.cap = ctx->hbuf_bytes;
