@@ -14,7 +14,9 @@ Typical use::
 """
 from ._lib import (ADJ_CLOBBER_STATE, DQ_C64, DQ_C128, PATH_AUTO, PATH_FUSED, PATH_PLAIN, Circuit, Context,
                    DQError, Observables, load_library)
-from .autograd import expectation, ExpectationFunction
+from .autograd import (DensityExpectationFunction, ExpectationFunction, density_expectation, expectation,
+                       measure)
 
 __all__ = ["Circuit", "Context", "DQError", "Observables", "expectation", "ExpectationFunction",
+           "density_expectation", "DensityExpectationFunction", "measure",
            "load_library", "PATH_AUTO", "PATH_PLAIN", "PATH_FUSED", "DQ_C64", "DQ_C128", "ADJ_CLOBBER_STATE"]

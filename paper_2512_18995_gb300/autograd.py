@@ -95,3 +95,60 @@ def expectation(circuit: Circuit, params: Optional[torch.Tensor], obs: Observabl
     if data is not None and data.dtype != torch.float64:
         data = data.to(torch.float64)
     return ExpectationFunction.apply(params, data, circuit, obs, context, dtype, params_per_row, memory_budget)
+
+
+class DensityExpectationFunction(torch.autograd.Function):
+    """Expectations Re Tr(O rho) of a noisy (density-matrix) circuit; backward
+    runs the exact shift rules of dq_density_grad with the upstream gradient
+    as per-row observable weights (shared parameters only)."""
+
+    @staticmethod
+    def forward(fctx, params, data, circuit: Circuit, obs: Observables, context: Context, dtype):
+        batch = data.shape[0] if data is not None else 1
+        exp, _ = context.density_forward(circuit, params, obs, batch, dtype, data=data)
+        fctx.circuit, fctx.obs, fctx.context, fctx.dtype = circuit, obs, context, dtype
+        fctx.save_for_backward(params, data)
+        return exp
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        params, data = fctx.saved_tensors
+        grad_params = None
+        if fctx.needs_input_grad[0]:
+            _, grad_params = fctx.context.density_grad(fctx.circuit, params, fctx.obs, data=data,
+                                                       row_weights=grad_out.contiguous().to(torch.float64),
+                                                       dtype=fctx.dtype)
+        return grad_params, None, None, None, None, None
+
+
+def density_expectation(circuit: Circuit, params: torch.Tensor, obs: Observables,
+                        data: Optional[torch.Tensor] = None, dtype: torch.dtype = torch.complex64,
+                        context: Optional[Context] = None) -> torch.Tensor:
+    """Differentiable (with respect to ``params``) expectations (batch, nobs)
+    of a circuit with noise channels, simulated as density matrices."""
+    context = context or default_context()
+    if params.dtype != torch.float64:
+        params = params.to(torch.float64)
+    if data is not None and data.dtype != torch.float64:
+        data = data.to(torch.float64)
+    return DensityExpectationFunction.apply(params, data, circuit, obs, context, dtype)
+
+
+def measure(state: torch.Tensor, nqubits: int, shots: int, wires=None, seed: int = 0,
+            context: Optional[Context] = None):
+    """Shot counts of a batch of states (the API overview's measure(shots,
+    wires)): a list (one per row) of {bitstring: count}, bitstrings over
+    ``wires`` (all wires by default) in increasing wire order, the lowest wire
+    leftmost (as in the full basis bitstring)."""
+    context = context or default_context()
+    ws = list(range(nqubits)) if wires is None else sorted(int(w) for w in wires)
+    out = context.sample(nqubits, state, shots, seed=seed, wires=None if wires is None else ws)
+    width = len(ws)
+    counts = []
+    for row in out.cpu().tolist():
+        d = {}
+        for v in row:
+            key = format(v, f"0{width}b")
+            d[key] = d.get(key, 0) + 1
+        counts.append(dict(sorted(d.items())))
+    return counts

@@ -163,3 +163,20 @@ def test_density_gradients_in_chunks(ctx):
     _, g1 = ctx.density_grad(circ, dev(params), dq.Observables(obs), dtype=torch.complex128)
     _, g2 = ctx.density_grad(circ, dev(params), dq.Observables(obs), dtype=torch.complex128, max_bytes=1 << 12)
     torch.testing.assert_close(g1, g2, atol=1e-12, rtol=0)
+
+
+def test_density_autograd(ctx):
+    """density_expectation through torch autograd: d(sum w * E)/dparams equals
+    dq_density_grad with the same weights."""
+    n, batch = 4, 3
+    rng = np.random.default_rng(12)
+    gates, npar = noisy_gates(n, 30, rng, nfeat=2)
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=2)
+    obs = dq.Observables([W.obs_tfim_open(n, 0.5)])
+    p = torch.tensor(rng.uniform(-3, 3, size=npar), device="cuda", requires_grad=True)
+    x = dev(rng.uniform(-3, 3, size=(batch, 2)))
+    w = dev(rng.normal(size=(batch, 1)))
+    e = dq.density_expectation(circ, p, obs, data=x, dtype=torch.complex128, context=ctx)
+    (e * w).sum().backward()
+    _, g = ctx.density_grad(circ, p.detach(), obs, data=x, row_weights=w, dtype=torch.complex128)
+    torch.testing.assert_close(p.grad, g, atol=1e-12, rtol=0)

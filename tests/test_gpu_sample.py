@@ -161,3 +161,18 @@ def test_sampling_rejects_bad_arguments(ctx):
         ctx.sample(4, t, 10, wires=[4])
     with pytest.raises(ValueError):
         ctx.sample(4, t, 10, uniforms=torch.zeros(3, dtype=torch.float64, device="cuda"))
+
+
+def test_measure_counts(ctx):
+    """measure() returns bitstring counts whose total is the shot count and
+    whose keys follow the selected wires (first listed wire leftmost)."""
+    n = 3
+    st = torch.zeros((1, 8), dtype=torch.complex64, device="cuda")
+    st[0, 0b101] = 1.0
+    c = dq.measure(st, n, 100, context=ctx)[0]
+    assert c == {"101": 100}
+    c = dq.measure(st, n, 50, wires=[2, 0], context=ctx)[0]
+    assert c == {"11": 50}
+    st2 = torch.full((1, 8), 8 ** -0.5, dtype=torch.complex64, device="cuda")
+    c = dq.measure(st2, n, 4000, seed=3, context=ctx)[0]
+    assert sum(c.values()) == 4000 and len(c) == 8
