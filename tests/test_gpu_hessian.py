@@ -124,3 +124,32 @@ def test_hessian_without_trainable_occurrences(ctx):
     circ = dq.Circuit(3, [W.Gate("h", (0,)), W.Gate("rx", (1,), angle=0.3)], nparams=2)
     H, g = ctx.hessian(circ, dev(np.array([0.1, 0.2])), dq.Observables([W.obs_z(1)]))
     assert torch.count_nonzero(H) == 0 and torch.count_nonzero(g) == 0
+
+
+def test_hessian_full_size_properties(ctx):
+    """20 qubits (beyond the oracle's product rule): the Hessian is symmetric
+    and each row matches central differences of the library's own adjoint
+    gradient (complex128; the gradient itself is checked against the oracle
+    elsewhere)."""
+    ctx.set_path(dq.PATH_AUTO)
+    n = 20
+    gates = W.hea_layers(n, 1)[:2 * n] + [W.Gate("rzz", (0, 7), param=2 * n), W.Gate("cry", (3, 11), param=2 * n + 1),
+                                         W.Gate("u3", (5,), param=2 * n + 2)] + W.hea_layers(n, 1)[2 * n:]
+    npar = 2 * n + 5
+    rng = np.random.default_rng(20)
+    params = rng.uniform(-3, 3, size=npar)
+    obs = [W.obs_tfim_open(n, 0.5)]
+    circ = dq.Circuit(n, gates, nparams=npar)
+    dobs = dq.Observables(obs)
+    H, g = ctx.hessian(circ, dev(params), dobs, dtype=torch.complex128)
+    H = H.cpu().numpy()
+    scale = obs_scale(obs)
+    assert np.max(np.abs(H - H.T)) <= 1e-10 * scale
+    h = 1e-5
+    for j in (0, n, 2 * n, 2 * n + 1, 2 * n + 3):
+        e = np.zeros(npar)
+        e[j] = h
+        _, gp, _, _ = ctx.forward_grad(circ, dev(params + e), dobs, 1, torch.complex128)
+        _, gm, _, _ = ctx.forward_grad(circ, dev(params - e), dobs, 1, torch.complex128)
+        fd = (gp - gm).cpu().numpy() / (2 * h)
+        assert np.max(np.abs(H[j] - fd)) <= 1e-6 * scale, j
