@@ -205,7 +205,7 @@ def test_trotter_full_size_paths_agree(ctx):
     a, b = out["fused"][0], out["plain"][0]
     idx = torch.randint(0, 1 << n, (4096,), generator=torch.Generator().manual_seed(26)).cuda()
     assert float((a[0, idx] - b[0, idx]).abs().max()) <= 1e-5
-    assert abs(float(torch.linalg.vector_norm(a.double())) - 1.0) <= 1e-4
+    assert abs(float(torch.linalg.vector_norm(a.to(torch.complex128))) - 1.0) <= 1e-4
     assert abs(out["fused"][1][0, 0] - out["plain"][1][0, 0]) <= 1e-4 * 2 * n * 1.2
     del out, a, b
     torch.cuda.empty_cache()
