@@ -465,6 +465,12 @@ DQ_API dq_status dq_sample(dq_ctx *ctx, int nqubits, const void *state, int batc
 DQ_API dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch,
                            int dtype, void *state, void *stream);
 
+/* The fused forward configuration dq_plan_autotune chose for this circuit
+ * structure and dtype: tile qubits *k, always-resident low bits *low and
+ * register bits per thread *M (all 0 when the circuit was not tuned and the
+ * size-based default applies). */
+DQ_API dq_status dq_plan_tuned(dq_ctx *ctx, const dq_circuit *circuit, int dtype, int *k, int *low, int *M);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,7 +62,7 @@ EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path"
            "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
            "dq_forward_grad_noalloc", "dq_apply_dense", "dq_sample_workspace_bytes", "dq_sample",
            "dq_hessian", "dq_density_workspace_bytes", "dq_density_forward",
-           "dq_density_grad")
+           "dq_density_grad", "dq_plan_tuned")
 
 _lib = None
 
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         "dq_density_forward": ([P, C, P, P, O, I, I, P, P, P], I),
         "dq_density_workspace_bytes": ([P, C, I, I, ctypes.POINTER(ctypes.c_size_t)], I),
         "dq_density_grad": ([P, C, P, P, O, P, I, I, ctypes.c_size_t, P, P, P], I),
+        "dq_plan_tuned": ([P, C, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "dq_sample": ([P, I, P, I, I, ctypes.c_int64, P, ctypes.c_uint64, ctypes.c_uint64, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -489,6 +490,13 @@ class Context:
                                                    _ptr(expect_out), _ptr(grad_params), _stream()),
                     "dq_batch_forward_grad")
         return expect_out, grad_params
+
+    def plan_tuned(self, circuit: Circuit, dtype: torch.dtype = torch.complex64):
+        """(k, low, M) chosen by plan_autotune for this circuit, or zeros."""
+        k, low, m = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self.lib.dq_plan_tuned(self.h, circuit.ref(), dtype_code(dtype), ctypes.byref(k),
+                                           ctypes.byref(low), ctypes.byref(m)), "dq_plan_tuned")
+        return k.value, low.value, m.value
 
     def plan_autotune(self, circuit: Circuit, state: torch.Tensor):
         batch = state.numel() >> circuit.nqubits

@@ -1997,6 +1997,23 @@ dq_status dq_apply_dense(dq_ctx *ctx, int nqubits, int nw, const double *unitary
     return DQ_OK;
 }
 
+dq_status dq_plan_tuned(dq_ctx *ctx, const dq_circuit *circuit, int dtype, int *k, int *low, int *M) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (!k || !low || !M) return fail(ctx, DQ_ERR_INVALID_ARG, "output pointers are NULL");
+    Plan *p = nullptr;
+    if ((st = get_plan(ctx, circuit, 0, &p)) != DQ_OK) return st;
+    *k = *low = *M = 0;
+    auto it = ctx->tuned.find(p->key ^ (dtype == DQ_C128 ? 1ull : 0ull));
+    if (it != ctx->tuned.end()) {
+        *k = it->second.k;
+        *low = it->second.low;
+        *M = it->second.M;
+    }
+    return DQ_OK;
+}
+
 dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch, int dtype, void *state, void *stream) {
     dq_status st = check_ctx(ctx);
     if (st != DQ_OK) return st;
