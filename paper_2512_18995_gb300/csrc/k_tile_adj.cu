@@ -154,10 +154,16 @@ void adjoint_tile(int n, int &k, int &low, int &M) {
     k = std::min(k, n - 1);
     M = std::min(M, k - kLaneBits);
     low = std::max(kLaneBits, std::min(7, k - 3));
-    // large complex64 states: only the lane bits always resident, which
-    // leaves more tile bits to the passes (measured on the 30-qubit QFT +
-    // ansatz reverse sweep: 40 passes / 655 ms against 54 / 739 ms)
-    if (n >= 25 && sizeof(R) == 4) low = kLaneBits;
+    // complex64 states of 20 qubits or more: 12-qubit tiles, four register
+    // bits and only the lane bits always resident, which leaves more tile
+    // bits to the passes (measured on the 30-qubit QFT + ansatz reverse sweep:
+    // 40 passes / 655 ms against 54 / 739 ms; on the 22-qubit Hessian batch
+    // together with the forward default: 114 ms against 175 ms)
+    if (n >= 20 && sizeof(R) == 4) {
+        k = std::min(12, n - 1);
+        M = 4;
+        low = kLaneBits;
+    }
 }
 
 // Persistent grid: two CTAs per SM, one when the two tiles of a CTA (psi and
