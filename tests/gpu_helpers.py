@@ -6,7 +6,7 @@ import torch
 
 import workloads as W
 
-# Tolerances (BASELINE targets): amplitudes max-abs 1e-5 (c64) / 1e-12
+# Tolerances of the parity bar: amplitudes max-abs 1e-5 (c64) / 1e-12
 # (c128); expectations and gradients 1e-4 relative (c64) / 1e-12 (c128),
 # relative to max(|ref|, max-norm of the reference vector, floor).  The floor
 # is the natural scale of the quantity (sum of |coefficients| for an
