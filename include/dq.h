@@ -471,6 +471,80 @@ DQ_API dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int ba
  * size-based default applies). */
 DQ_API dq_status dq_plan_tuned(dq_ctx *ctx, const dq_circuit *circuit, int dtype, int *k, int *low, int *M);
 
+/* ---- host-side plan inspection (no context, no GPU) ----------------------
+ * These calls run only the host code that the compute calls run before any
+ * launch -- argument validation, lowering to kernel-level gates, the tile
+ * planner and the shift-rule tables -- and touch no device, so a caller can
+ * see what a circuit becomes without a GPU.  They take no context: failures
+ * return a status only (no message). */
+
+/* One kernel-level operation of a lowered circuit.
+ *   kind:  a kernel-level dq_gate_kind (H X Y Z S RX RY RZ P CNOT CZ CP SWAP
+ *          CRX CRY CRZ), or DQ_LOWERED_BLOCK / DQ_LOWERED_CBLOCK for the
+ *          fixed 2x2 matrix `block` (not unitary in the channels of density
+ *          circuits), uncontrolled or applied to wires[1] when wires[0] is |1>.
+ *   wires: one-wire ops use wires[0] (wires[1] = -1); controlled ops are
+ *          (control, target); SWAP is the pair.  Density circuits number the
+ *          2n wires of the vectorised rho (wire q + n carries column bit q).
+ *   param_idx, data_idx, angle: the angle source as in dq_gate; U3's three
+ *          angles become the ops P(lam), RY(theta), P(phi), applied in that
+ *          order, with param_idx (or data_idx) + 2, + 0, + 1.
+ *   conj:  1 when the op's matrix is replaced by its complex conjugate (the
+ *          column-wire copy of a gate in a density circuit).
+ *   block: DQ_LOWERED_BLOCK / CBLOCK only: row-major 2x2 as (re, im) pairs. */
+#define DQ_LOWERED_BLOCK 64
+#define DQ_LOWERED_CBLOCK 65
+typedef struct dq_lowered_op {
+    int32_t kind;
+    int32_t wires[2];
+    int32_t param_idx;
+    int32_t data_idx;
+    int32_t conj;
+    double angle;
+    double block[8];
+} dq_lowered_op;      /* 96 bytes */
+
+/* Validate `circuit` exactly as the compute calls do and lower it: pure
+ * circuits (density = 0) to the ops that dq_apply_circuit runs, density
+ * circuits (density = 1, noise channels allowed, nqubits <= 17) to the ops
+ * that dq_density_forward runs on the 2n-qubit vectorised rho.  The composite
+ * gates become exact products (the product of the ops, first op applied
+ * first, equals the circuit's operator; for a density circuit it equals the
+ * superoperator on row-major vec(rho)).  *count receives the number of ops.
+ * ops may be NULL (count only); otherwise it holds `capacity` entries and a
+ * capacity below *count returns DQ_ERR_INVALID_ARG with nothing written. */
+DQ_API dq_status dq_lower_circuit(const dq_circuit *circuit, int density, dq_lowered_op *ops, int capacity,
+                                  int *count);
+
+/* The fused-path tile schedule of the pure circuit's lowered ops (numbered as
+ * by dq_lower_circuit) for tile qubits k, always-resident low bits `low` and
+ * register bits per thread M: forward passes (adjoint = 0) or the passes of
+ * the adjoint sweep (adjoint = 1).  Pass p holds ops order[pass_start[p] ..
+ * pass_start[p+1]) in forward order and acts on tiles of the amplitude bits
+ * set in tile_bits[p] (bit b = wire nqubits-1-b); the forward direction runs
+ * the passes and their ops first to last, the adjoint sweep un-applies them
+ * last to first.  op_flags[i] (may be NULL) gets bit 0 when op order[i] is
+ * part of a CNOT-diagonal-CNOT triple run as one parity-diagonal op (it then
+ * needs no tile bit).  Every array holds `capacity` >= op count entries
+ * (pass_start one more).  Returns DQ_ERR_UNSUPPORTED when no schedule exists
+ * for these values (for instance k > nqubits), the number of passes in
+ * *npasses otherwise. */
+DQ_API dq_status dq_tile_schedule(const dq_circuit *circuit, int dtype, int k, int low, int M, int adjoint,
+                                  int capacity, int32_t *order, int32_t *pass_start, uint64_t *tile_bits,
+                                  int32_t *op_flags, int *npasses);
+
+/* The shift rules that dq_hessian and dq_density_grad apply.  Occurrence v
+ * (each angle of each gate with a trainable parameter, in gate order; U3
+ * gives three, theta phi lam) belongs to parameter occ_param[v], and
+ * d f / d t_v = sum_{j in [row0[v], row0[v+1])} weight[j] f(t_v + shift[j])
+ * for every f trigonometric in that angle (two rows for eigenvalue gap 1,
+ * four for CRX CRY CRZ).  occ_param and row0 hold cap_occ entries (row0 one
+ * more), shift and weight cap_rows; *nocc and *nrows receive the counts, and
+ * too small a capacity returns DQ_ERR_INVALID_ARG with nothing written (NULL
+ * arrays: counts only). */
+DQ_API dq_status dq_shift_rules(const dq_circuit *circuit, int cap_occ, int cap_rows, int32_t *occ_param,
+                                int32_t *row0, double *shift, double *weight, int *nocc, int *nrows);
+
 #ifdef __cplusplus
 }
 #endif

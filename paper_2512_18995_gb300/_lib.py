@@ -56,13 +56,24 @@ class dq_observables(ctypes.Structure):
                 ("terms", ctypes.POINTER(dq_pauli_term))]
 
 
+# kernel-level kinds of lowered circuits beyond the public ones (dq_lowered_op)
+LOWERED_BLOCK, LOWERED_CBLOCK = 64, 65
+KIND_NAME = {**{i: k for k, i in KIND.items()}, LOWERED_BLOCK: "block", LOWERED_CBLOCK: "cblock"}
+
+
+class dq_lowered_op(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("wires", ctypes.c_int32 * 2), ("param_idx", ctypes.c_int32),
+                ("data_idx", ctypes.c_int32), ("conj", ctypes.c_int32), ("angle", ctypes.c_double),
+                ("block", ctypes.c_double * 8)]
+
+
 EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path", "dq_ctx_set_workspace",
            "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_graphs", "dq_ctx_set_tracing",
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
            "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
            "dq_forward_grad_noalloc", "dq_apply_dense", "dq_sample_workspace_bytes", "dq_sample",
            "dq_hessian", "dq_density_workspace_bytes", "dq_density_forward",
-           "dq_density_grad", "dq_plan_tuned")
+           "dq_density_grad", "dq_plan_tuned", "dq_lower_circuit", "dq_tile_schedule", "dq_shift_rules")
 
 _lib = None
 
@@ -110,6 +121,11 @@ def load_library(path: str = LIB_PATH):
         "dq_density_grad": ([P, C, P, P, O, P, I, I, ctypes.c_size_t, P, P, P], I),
         "dq_plan_tuned": ([P, C, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "dq_sample": ([P, I, P, I, I, ctypes.c_int64, P, ctypes.c_uint64, ctypes.c_uint64, P, P], I),
+        "dq_lower_circuit": ([C, I, ctypes.POINTER(dq_lowered_op), I, ctypes.POINTER(I)], I),
+        "dq_tile_schedule": ([C, I, I, I, I, I, I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(I)], I),
+        "dq_shift_rules": ([C, I, I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), D, D,
+                            ctypes.POINTER(I), ctypes.POINTER(I)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -196,6 +212,76 @@ class Observables:
 
     def ref(self):
         return ctypes.byref(self.c)
+
+
+# ---------------------------------------------------------------------------
+# host-side plan inspection (no context, no GPU)
+# ---------------------------------------------------------------------------
+def _inspect_check(st: int, what: str):
+    if st != DQ_OK:
+        raise DQError(st, f"{what}: the circuit or arguments were rejected")
+
+
+def lower_circuit(circuit: Circuit, density: bool = False) -> List[dict]:
+    """The kernel-level ops the library runs for ``circuit`` (dq_lower_circuit):
+    dicts with ``kind`` (name; "block"/"cblock" for fixed 2x2 blocks),
+    ``wires``, ``param``, ``data``, ``angle``, ``conj`` and ``block`` (2x2
+    complex, fixed blocks only)."""
+    lib = load_library()
+    cnt = ctypes.c_int(0)
+    _inspect_check(lib.dq_lower_circuit(circuit.ref(), int(bool(density)), None, 0, ctypes.byref(cnt)),
+                   "dq_lower_circuit")
+    arr = (dq_lowered_op * max(1, cnt.value))()
+    _inspect_check(lib.dq_lower_circuit(circuit.ref(), int(bool(density)), arr, cnt.value, ctypes.byref(cnt)),
+                   "dq_lower_circuit")
+    out = []
+    for o in arr[:cnt.value]:
+        w = tuple(int(x) for x in o.wires if x >= 0)
+        b = None
+        if o.kind in (LOWERED_BLOCK, LOWERED_CBLOCK):
+            v = list(o.block)
+            b = [[complex(v[0], v[1]), complex(v[2], v[3])], [complex(v[4], v[5]), complex(v[6], v[7])]]
+        out.append({"kind": KIND_NAME[o.kind], "wires": w, "param": o.param_idx, "data": o.data_idx,
+                    "angle": o.angle, "conj": bool(o.conj), "block": b})
+    return out
+
+
+def tile_schedule(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64,
+                  adjoint: bool = False) -> List[Tuple[int, List[int], List[bool]]]:
+    """The fused path's tile passes for ``circuit`` (dq_tile_schedule): a list
+    of (tile amplitude-bit mask, lowered-op indices in forward order,
+    parity-triple flags), or DQError(DQ_ERR_UNSUPPORTED) if no schedule
+    exists for (k, low, M)."""
+    lib = load_library()
+    cnt = ctypes.c_int(0)
+    _inspect_check(lib.dq_lower_circuit(circuit.ref(), 0, None, 0, ctypes.byref(cnt)), "dq_lower_circuit")
+    cap = max(1, cnt.value)
+    order = (ctypes.c_int32 * cap)()
+    start = (ctypes.c_int32 * (cap + 1))()
+    bits = (ctypes.c_uint64 * cap)()
+    flags = (ctypes.c_int32 * cap)()
+    npass = ctypes.c_int(0)
+    _inspect_check(lib.dq_tile_schedule(circuit.ref(), int(dtype), int(k), int(low), int(M), int(bool(adjoint)),
+                                        cap, order, start, bits, flags, ctypes.byref(npass)), "dq_tile_schedule")
+    return [(int(bits[p]), [int(x) for x in order[start[p]:start[p + 1]]],
+             [bool(x) for x in flags[start[p]:start[p + 1]]]) for p in range(npass.value)]
+
+
+def shift_rules(circuit: Circuit):
+    """The shift rules of dq_hessian / dq_density_grad (dq_shift_rules):
+    (occurrence -> parameter, row offsets per occurrence (+1 entry), shifts,
+    weights) as Python lists."""
+    lib = load_library()
+    nv, nj = ctypes.c_int(0), ctypes.c_int(0)
+    _inspect_check(lib.dq_shift_rules(circuit.ref(), 0, 0, None, None, None, None, ctypes.byref(nv),
+                                      ctypes.byref(nj)), "dq_shift_rules")
+    occ = (ctypes.c_int32 * max(1, nv.value))()
+    row0 = (ctypes.c_int32 * (nv.value + 1))()
+    sh = (ctypes.c_double * max(1, nj.value))()
+    wt = (ctypes.c_double * max(1, nj.value))()
+    _inspect_check(lib.dq_shift_rules(circuit.ref(), nv.value, nj.value, occ, row0, sh, wt, ctypes.byref(nv),
+                                      ctypes.byref(nj)), "dq_shift_rules")
+    return (list(occ[:nv.value]), list(row0[:nv.value + 1]), list(sh[:nj.value]), list(wt[:nj.value]))
 
 
 # ---------------------------------------------------------------------------

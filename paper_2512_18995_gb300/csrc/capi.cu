@@ -418,11 +418,10 @@ dq_status lower_gate_density(dq_ctx *ctx, const dq_circuit *c, int i, std::vecto
     return DQ_OK;
 }
 
-// Validate a circuit, lower it and translate it to bit-space gates (appended
-// to dg / bg).
-dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<DevGate> &dg,
-                        std::vector<BindGate> &bg, int param_base, int *ncoef_shared, int *ncoef_rows,
-                        bool batch_mode, std::vector<std::array<double, 8>> *fixed = nullptr) {
+// Validate a circuit and lower every gate (density: on the vectorised rho,
+// with the fixed blocks appended to *fixed).
+dq_status lower_circuit(dq_ctx *ctx, const dq_circuit *c, bool batch_mode, std::vector<Prim> &prims,
+                        std::vector<std::array<double, 8>> *fixed) {
     if (!c) return fail(ctx, DQ_ERR_INVALID_ARG, "circuit is NULL");
     dq_status st = check_n(ctx, c->nqubits);
     if (st != DQ_OK) return st;
@@ -432,8 +431,6 @@ dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<D
     if (c->ngates < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "ngates < 0");
     if (c->ngates > 0 && !c->gates) return fail(ctx, DQ_ERR_INVALID_ARG, "gates is NULL");
     if (c->nparams < 0 || c->nfeatures < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "negative nparams/nfeatures");
-    const int n = density ? 2 * c->nqubits : c->nqubits;
-    std::vector<Prim> prims;
     prims.reserve((size_t)lowered_count(*c) * (density ? 2 : 1));
     for (int i = 0; i < c->ngates; ++i) {
         st = density ? lower_gate_density(ctx, c, i, prims, *fixed) : lower_gate(ctx, c, i, prims);
@@ -441,6 +438,19 @@ dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<D
         if (batch_mode && c->gates[i].data_idx >= 0)
             return fail(ctx, DQ_ERR_INVALID_ARG, "gate %d: encoded data is not supported in uneven batches", i);
     }
+    return DQ_OK;
+}
+
+// Validate a circuit, lower it and translate it to bit-space gates (appended
+// to dg / bg).
+dq_status compile_gates(dq_ctx *ctx, const dq_circuit *c, int ppr, std::vector<DevGate> &dg,
+                        std::vector<BindGate> &bg, int param_base, int *ncoef_shared, int *ncoef_rows,
+                        bool batch_mode, std::vector<std::array<double, 8>> *fixed = nullptr) {
+    std::vector<Prim> prims;
+    dq_status st = lower_circuit(ctx, c, batch_mode, prims, fixed);
+    if (st != DQ_OK) return st;
+    const bool density = fixed != nullptr;
+    const int n = density ? 2 * c->nqubits : c->nqubits;
     // First pass: count per-row coefficient slots (their row stride).
     int nrows = 0, nshared = 0;
     for (const Prim &g : prims) {
@@ -1422,14 +1432,18 @@ ShiftPlan make_shift_plan(const dq_circuit &c) {
     return sp;
 }
 
-// Largest number of leading occurrences per chunk whose shifted rows (times
-// the data rows) fit rows_cap rows; at least one.
+// Occurrences per chunk (halved from all of them) such that every chunk's
+// shifted rows (times the data rows) fit rows_cap rows; at least one.
 int shift_chunk(const ShiftPlan &sp, int batch, int64_t rows_cap) {
     int vchunk = sp.V;
     while (vchunk > 1) {
-        int64_t rows = 0;
-        for (int v = 0; v < vchunk; ++v) rows += (int64_t)sp.nshift[v] * batch;
-        if (rows <= rows_cap) break;
+        int64_t worst = 0;
+        for (int v0 = 0; v0 < sp.V; v0 += vchunk) {
+            int64_t rows = 0;
+            for (int v = v0; v < std::min(sp.V, v0 + vchunk); ++v) rows += (int64_t)sp.nshift[v] * batch;
+            worst = std::max(worst, rows);
+        }
+        if (worst <= rows_cap) break;
         vchunk = (vchunk + 1) / 2;
     }
     return vchunk;
@@ -2048,6 +2062,99 @@ dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch, in
     cudaStreamSynchronize(s);
     cudaFree(zeros);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+    return DQ_OK;
+}
+
+// ---- host-side plan inspection (no context, no device) ---------------------
+static_assert(kKindFixed == DQ_LOWERED_BLOCK && kKindCFixed == DQ_LOWERED_CBLOCK, "lowered block kinds");
+static_assert(sizeof(dq_lowered_op) == 96, "dq_lowered_op layout");
+
+dq_status dq_lower_circuit(const dq_circuit *circuit, int density, dq_lowered_op *ops, int capacity, int *count) {
+    if (!count || (density != 0 && density != 1)) return DQ_ERR_INVALID_ARG;
+    std::vector<Prim> prims;
+    std::vector<std::array<double, 8>> fixed;
+    const dq_status st = lower_circuit(nullptr, circuit, false, prims, density ? &fixed : nullptr);
+    if (st != DQ_OK) return st;
+    *count = (int)prims.size();
+    if (!ops) return DQ_OK;
+    if (capacity < (int)prims.size()) return DQ_ERR_INVALID_ARG;
+    for (size_t i = 0; i < prims.size(); ++i) {
+        const Prim &q = prims[i];
+        dq_lowered_op o{};
+        o.kind = q.kind;
+        o.wires[0] = q.w0;
+        o.wires[1] = q.w1;
+        o.param_idx = q.pidx;
+        o.data_idx = q.didx;
+        o.conj = q.conj;
+        o.angle = q.angle;
+        if (q.fixed >= 0)
+            for (int j = 0; j < 8; ++j) o.block[j] = fixed[q.fixed][j];
+        ops[i] = o;
+    }
+    return DQ_OK;
+}
+
+dq_status dq_tile_schedule(const dq_circuit *circuit, int dtype, int k, int low, int M, int adjoint, int capacity,
+                           int32_t *order, int32_t *pass_start, uint64_t *tile_bits, int32_t *op_flags,
+                           int *npasses) {
+    if (!order || !pass_start || !tile_bits || !npasses) return DQ_ERR_INVALID_ARG;
+    if (dtype != DQ_C64 && dtype != DQ_C128) return DQ_ERR_INVALID_ARG;
+    Plan p;
+    int ncs = 0, ncr = 0;
+    const dq_status st = compile_gates(nullptr, circuit, 0, p.gates, p.bind, 0, &ncs, &ncr, false);
+    if (st != DQ_OK) return st;
+    p.n = circuit->nqubits;
+    p.ngates = (int)p.gates.size();
+    if (capacity < p.ngates) return DQ_ERR_INVALID_ARG;
+    const int amp = amp_bytes(dtype);
+    if (M < 2 || M > (dtype == DQ_C64 ? 5 : 4) || k > kTileMaxK || !tile_supported(p.n, amp))
+        return DQ_ERR_UNSUPPORTED;
+    TileSchedule sc;
+    if (!tile_build_schedule(p, k, low, M, amp, sc, adjoint != 0)) return DQ_ERR_UNSUPPORTED;
+    int pos = 0;
+    for (size_t q = 0; q < sc.passes.size(); ++q) {
+        const TPass &ps = sc.passes[q];
+        pass_start[q] = pos;
+        uint64_t T = 0;
+        for (int b : ps.T) T |= uint64_t(1) << b;
+        tile_bits[q] = T;
+        for (size_t j = 0; j < ps.gates.size() && pos < capacity; ++j, ++pos) {
+            order[pos] = ps.gates[j];
+            if (op_flags) op_flags[pos] = ps.fused[j] ? 1 : 0;
+        }
+    }
+    pass_start[sc.passes.size()] = pos;
+    *npasses = (int)sc.passes.size();
+    return DQ_OK;
+}
+
+dq_status dq_shift_rules(const dq_circuit *circuit, int cap_occ, int cap_rows, int32_t *occ_param, int32_t *row0,
+                         double *shift, double *weight, int *nocc, int *nrows) {
+    if (!nocc || !nrows) return DQ_ERR_INVALID_ARG;
+    // validate as the entry point that takes the circuit would: the density
+    // path when it holds a noise channel, else the pure path
+    bool noisy = false;
+    if (circuit && circuit->gates)
+        for (int i = 0; i < circuit->ngates; ++i) noisy = noisy || kind_noise(circuit->gates[i].kind);
+    std::vector<Prim> prims;
+    std::vector<std::array<double, 8>> fixed;
+    const dq_status st = lower_circuit(nullptr, circuit, false, prims, noisy ? &fixed : nullptr);
+    if (st != DQ_OK) return st;
+    const ShiftPlan sp = make_shift_plan(*circuit);
+    *nocc = sp.V;
+    *nrows = sp.J;
+    if (!occ_param && !row0 && !shift && !weight) return DQ_OK;
+    if (!occ_param || !row0 || !shift || !weight || cap_occ < sp.V || cap_rows < sp.J) return DQ_ERR_INVALID_ARG;
+    for (int v = 0; v < sp.V; ++v) {
+        occ_param[v] = sp.occ[v];
+        row0[v] = sp.vrow0[v];
+    }
+    row0[sp.V] = sp.J;
+    for (int j = 0; j < sp.J; ++j) {
+        shift[j] = sp.sh[j];
+        weight[j] = sp.coef[j];
+    }
     return DQ_OK;
 }
 

@@ -35,6 +35,8 @@ struct TPass {
     int rseg0 = 0, nrseg = 0; // reverse-sweep layouts (adjoint schedules)
     int slot0 = 0, nslot = 0; // gradient slots of the pass (adjoint schedules)
     bool pdiag = false;       // holds parity-diagonal ops
+    std::vector<int> gates;   // plan gates of the pass in execution order (host inspection)
+    std::vector<char> fused;  // per entry of gates: part of a parity-diagonal triple
 };
 
 // Passes of fused gates.  Adjoint schedules also carry, per pass, the ops

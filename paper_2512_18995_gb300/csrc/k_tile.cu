@@ -195,6 +195,10 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
         };
         for (int ii : sched) {
             const Item &it = items[ii];
+            for (int j = 0; j < it.len; ++j) {
+                pass.gates.push_back(it.g + j);
+                pass.fused.push_back(it.len == 3);
+            }
             if (it.len == 3) {
                 const DevGate &c = p.gates[it.g], &d = p.gates[it.g + 1];
                 const int slot = it.g + 1 < (int)p.slot_of_gate.size() ? p.slot_of_gate[it.g + 1] : -1;

@@ -63,6 +63,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(dq_pauli_term), sizeof(dq_observables),
          offsetof(dq_observables, term_offsets), offsetof(dq_observables, terms));
   printf("%d %d %d %d\n", (int)DQ_CRZ, (int)DQ_SWAP, (int)DQ_NUM_GATE_KINDS, (int)DQ_ERR_TIMEOUT);
+  printf("%zu %zu %zu %zu %d %d\n", sizeof(dq_lowered_op), offsetof(dq_lowered_op, conj),
+         offsetof(dq_lowered_op, angle), offsetof(dq_lowered_op, block), DQ_LOWERED_BLOCK, DQ_LOWERED_CBLOCK);
   return 0;
 }
 '''
@@ -80,6 +82,9 @@ int main(void) {
                  _lib.dq_observables.term_offsets.offset, _lib.dq_observables.terms.offset]
     k = list(map(int, lines[2].split()))
     assert k == [_lib.KIND["crz"], _lib.KIND["swap"], len(_lib.KIND), 5]
+    lo = list(map(int, lines[3].split()))
+    assert lo == [ctypes.sizeof(_lib.dq_lowered_op), _lib.dq_lowered_op.conj.offset, _lib.dq_lowered_op.angle.offset,
+                  _lib.dq_lowered_op.block.offset, _lib.LOWERED_BLOCK, _lib.LOWERED_CBLOCK]
 
 
 def test_context_creation_fails_cleanly_without_device(libdq):
