@@ -152,6 +152,64 @@ def dtype_code(dt: torch.dtype) -> int:
 
 
 # ---------------------------------------------------------------------------
+# tensor checks: the library receives bare device pointers and cannot see a
+# buffer's device, type or size, so the binding checks them before a call
+# ---------------------------------------------------------------------------
+def _bad(msg: str):
+    raise DQError(1, msg)
+
+
+def _on_device(t, what: str, device: Optional[int]):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        _bad(f"{what} must be a CUDA tensor")
+    if device is not None and t.device.index != device:
+        _bad(f"{what} is on cuda:{t.device.index}, the context on cuda:{device}")
+
+
+def _f64_in(t: Optional[torch.Tensor], count: int, what: str, device: Optional[int]):
+    """An FP64 input of which the call reads `count` values, converted to
+    float64 and made contiguous (no-ops, same pointer, for tensors that
+    already are); host tensors and short ones are rejected."""
+    if t is None:
+        return None
+    _on_device(t, what, device)
+    if t.dtype != torch.float64:
+        t = t.to(torch.float64)
+    t = t.contiguous()
+    if t.numel() < count:
+        _bad(f"{what} holds {t.numel()} values; the call reads {count}")
+    return t
+
+
+def _out(t: Optional[torch.Tensor], count: int, dtype: torch.dtype, what: str, device: Optional[int]):
+    """A caller-supplied output buffer: `dtype`, contiguous, >= count values."""
+    if t is None:
+        return None
+    _on_device(t, what, device)
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() < count:
+        _bad(f"{what} must be a contiguous {dtype} tensor of at least {count} values")
+    return t
+
+
+def _state_rows(t: torch.Tensor, nqubits: int, what: str, device: Optional[int]) -> int:
+    """Rows of a state batch tensor (contiguous complex rows of 2^nqubits)."""
+    _on_device(t, what, device)
+    dtype_code(t.dtype)
+    if not t.is_contiguous():
+        _bad(f"{what} must be contiguous")
+    if 1 <= nqubits <= 34 and t.numel() % (1 << nqubits):
+        _bad(f"{what} holds {t.numel()} amplitudes, not rows of 2^{nqubits}")
+    return t.numel() >> nqubits if 0 <= nqubits < 63 else 0
+
+
+def _angles(circuit, params, data, batch: int, params_per_row: bool, device: Optional[int]):
+    """params and data of a call, checked against what the circuit reads."""
+    params = _f64_in(params, circuit.nparams * (batch if params_per_row else 1), "params", device)
+    data = _f64_in(data, batch * circuit.nfeatures, "data", device)
+    return params, data
+
+
+# ---------------------------------------------------------------------------
 # circuit and observable descriptions
 # ---------------------------------------------------------------------------
 class Circuit:
@@ -377,14 +435,15 @@ class Context:
 
     # ---- hot path --------------------------------------------------------
     def state_init(self, state: torch.Tensor, nqubits: int):
-        batch = state.numel() >> nqubits
+        batch = _state_rows(state, nqubits, "state", self.device)
         self._check(self.lib.dq_state_init(self.h, int(nqubits), int(batch), dtype_code(state.dtype), _ptr(state),
                                            _stream()), "dq_state_init")
 
     def apply_circuit(self, circuit: Circuit, params: Optional[torch.Tensor], state: torch.Tensor,
                       data: Optional[torch.Tensor] = None, params_per_row: bool = False):
-        batch = state.numel() >> circuit.nqubits
+        batch = _state_rows(state, circuit.nqubits, "state", self.device)
         dt = dtype_code(state.dtype)
+        params, data = _angles(circuit, params, data, batch, params_per_row, self.device)
         self.ensure_workspace(circuit, None, batch, dt)
         self._check(self.lib.dq_apply_circuit(self.h, circuit.ref(), _ptr(params), int(params_per_row), _ptr(data),
                                               _ptr(state), int(batch), dt, _stream()), "dq_apply_circuit")
@@ -396,8 +455,9 @@ class Context:
         nw = int(unitary.shape[-1]).bit_length() - 1
         if unitary.dtype != torch.complex128 or tuple(unitary.shape) != (1 << nw, 1 << nw):
             raise ValueError("unitary must be a complex128 tensor of shape (2^nw, 2^nw)")
+        _on_device(unitary, "unitary", self.device)
         u = unitary.contiguous()
-        batch = state.numel() >> nqubits
+        batch = _state_rows(state, nqubits, "state", self.device)
         self.ensure_workspace(None, None, batch, dtype_code(state.dtype), need_bytes=1 << 20)
         self._check(self.lib.dq_apply_dense(self.h, int(nqubits), nw, _ptr(u), _ptr(state), int(batch),
                                             dtype_code(state.dtype), _stream()), "dq_apply_dense")
@@ -410,6 +470,9 @@ class Context:
         (batch, 2^n, 2^n) or None)."""
         n = circuit.nqubits
         dev = torch.device(f"cuda:{self.device}")
+        params, data = _angles(circuit, params, data, batch, False, self.device)
+        if rho is not None:
+            rho = _out(rho, batch << (2 * n) if 1 <= n <= 17 else 0, dtype, "rho", self.device)
         if want_rho and rho is None:
             rho = torch.empty((batch, 1 << n, 1 << n), dtype=dtype, device=dev)
         expect = torch.empty((batch, obs.nobs), dtype=torch.float64, device=dev) if obs is not None else None
@@ -430,12 +493,13 @@ class Context:
         circuit's weighted expectation sum, by exact shift rules."""
         batch = int(data.shape[0]) if data is not None else 1
         dev = torch.device(f"cuda:{self.device}")
+        params, data = _angles(circuit, params, data, batch, False, self.device)
+        row_weights = _f64_in(row_weights, batch * obs.nobs, "row_weights", self.device)
         expect = torch.empty((batch, obs.nobs), dtype=torch.float64, device=dev)
         grad = torch.empty((circuit.nparams,), dtype=torch.float64, device=dev)
         if self._ws is not None:   # scratch is sized inside the call
             self.release_workspace()
-        self._check(self.lib.dq_density_grad(self.h, circuit.ref(), _ptr(params.to(torch.float64).contiguous()),
-                                             _ptr(data.to(torch.float64).contiguous() if data is not None else None),
+        self._check(self.lib.dq_density_grad(self.h, circuit.ref(), _ptr(params), _ptr(data),
                                              obs.ref(), _ptr(row_weights), batch, dtype_code(dtype),
                                              ctypes.c_size_t(int(max_bytes)), _ptr(expect), _ptr(grad), _stream()),
                     "dq_density_grad")
@@ -451,14 +515,15 @@ class Context:
         batch = int(data.shape[0]) if data is not None else 1
         dev = torch.device(f"cuda:{self.device}")
         P = circuit.nparams
+        params, data = _angles(circuit, params, data, batch, False, self.device)
+        row_weights = _f64_in(row_weights, batch * obs.nobs, "row_weights", self.device)
         # the shifted rows' scratch is sized inside the call: let the context
         # grow its own workspace instead of an attached tensor
         if self._ws is not None:
             self.release_workspace()
         hess = torch.empty((P, P), dtype=torch.float64, device=dev)
         grad = torch.empty((P,), dtype=torch.float64, device=dev) if want_grad else None
-        self._check(self.lib.dq_hessian(self.h, circuit.ref(), _ptr(params.to(torch.float64).contiguous()),
-                                        _ptr(data.to(torch.float64).contiguous() if data is not None else None),
+        self._check(self.lib.dq_hessian(self.h, circuit.ref(), _ptr(params), _ptr(data),
                                         obs.ref(), _ptr(row_weights), batch, dtype_code(dtype),
                                         ctypes.c_size_t(int(max_bytes)), _ptr(hess),
                                         _ptr(grad), _stream()), "dq_hessian")
@@ -472,22 +537,24 @@ class Context:
         most significant; the wires are taken in increasing order).
         ``uniforms`` (FP64 (batch, shots) on the device, in [0, 1)) or, when
         None, the splitmix64 stream of ``seed`` drives the draws."""
-        batch = state.numel() >> nqubits
+        batch = _state_rows(state, nqubits, "state", self.device)
         mask = 0
         if wires is not None:
             for q in wires:
                 mask |= 1 << int(q)
         if out is None:
             out = torch.empty((batch, int(shots)), dtype=torch.int64, device=state.device)
+        else:
+            out = _out(out, batch * int(shots), torch.int64, "out", self.device)
         need = ctypes.c_size_t(0)
         self._check(self.lib.dq_sample_workspace_bytes(self.h, int(nqubits), int(batch), ctypes.byref(need)),
                     "dq_sample_workspace_bytes")
         self.ensure_workspace(None, None, batch, dtype_code(state.dtype), need_bytes=need.value)
         u = None
         if uniforms is not None:
-            u = uniforms.to(torch.float64).contiguous()
-            if u.numel() != batch * int(shots):
+            if uniforms.numel() != batch * int(shots):
                 raise ValueError("uniforms must hold batch * shots values")
+            u = _f64_in(uniforms, batch * int(shots), "uniforms", self.device)
         self._check(self.lib.dq_sample(self.h, int(nqubits), _ptr(state), int(batch), dtype_code(state.dtype),
                                        int(shots), _ptr(u), ctypes.c_uint64(int(seed) & (2 ** 64 - 1)),
                                        ctypes.c_uint64(mask), _ptr(out), _stream()), "dq_sample")
@@ -495,10 +562,12 @@ class Context:
 
     def expect(self, nqubits: int, obs: Observables, state: torch.Tensor,
                out: Optional[torch.Tensor] = None) -> torch.Tensor:
-        batch = state.numel() >> nqubits
+        batch = _state_rows(state, nqubits, "state", self.device)
         dt = dtype_code(state.dtype)
         if out is None:
             out = torch.empty((batch, obs.nobs), dtype=torch.float64, device=state.device)
+        else:
+            out = _out(out, batch * obs.nobs, torch.float64, "out", self.device)
         self.ensure_workspace(Circuit(nqubits, []), obs, batch, dt)
         self._check(self.lib.dq_expect(self.h, int(nqubits), obs.ref(), _ptr(state), int(batch), dt, _ptr(out),
                                        _stream()), "dq_expect")
@@ -509,9 +578,14 @@ class Context:
                      row_weights: Optional[torch.Tensor] = None, params_per_row: bool = False,
                      clobber: bool = False, grad_params: Optional[torch.Tensor] = None,
                      grad_data: Optional[torch.Tensor] = None):
-        batch = state.numel() >> circuit.nqubits
+        batch = _state_rows(state, circuit.nqubits, "state", self.device)
         dt = dtype_code(state.dtype)
         dev = state.device
+        params, data = _angles(circuit, params, data, batch, params_per_row, self.device)
+        row_weights = _f64_in(row_weights, batch * obs.nobs, "row_weights", self.device)
+        grad_params = _out(grad_params, circuit.nparams * (batch if params_per_row else 1), torch.float64,
+                           "grad_params", self.device)
+        grad_data = _out(grad_data, batch * circuit.nfeatures, torch.float64, "grad_data", self.device)
         if grad_params is None and circuit.nparams > 0:
             shape = (batch, circuit.nparams) if params_per_row else (circuit.nparams,)
             grad_params = torch.empty(shape, dtype=torch.float64, device=dev)
@@ -532,6 +606,16 @@ class Context:
                      grad_data: Optional[torch.Tensor] = None, want_data_grad: bool = True):
         dt = dtype_code(dtype)
         dev = torch.device(f"cuda:{self.device}")
+        params, data = _angles(circuit, params, data, batch, params_per_row, self.device)
+        nobs = obs.nobs if obs is not None else 0
+        row_weights = _f64_in(row_weights, batch * nobs, "row_weights", self.device)
+        expect_out = _out(expect_out, batch * nobs, torch.float64, "expect_out", self.device)
+        grad_params = _out(grad_params, circuit.nparams * (batch if params_per_row else 1), torch.float64,
+                           "grad_params", self.device)
+        grad_data = _out(grad_data, batch * circuit.nfeatures, torch.float64, "grad_data", self.device)
+        if state_out is not None:
+            n = circuit.nqubits
+            state_out = _out(state_out, batch << n if 1 <= n <= 34 else 0, dtype, "state_out", self.device)
         if want_expect and expect_out is None and obs is not None:
             expect_out = torch.empty((batch, obs.nobs), dtype=torch.float64, device=dev)
         if want_grad:
@@ -559,6 +643,9 @@ class Context:
             arr[i] = c.c
             offs[i + 1] = offs[i] + c.nparams
         dev = torch.device(f"cuda:{self.device}")
+        params = _f64_in(params, int(offs[nc]), "params", self.device)
+        expect_out = _out(expect_out, nc * obs.nobs, torch.float64, "expect_out", self.device)
+        grad_params = _out(grad_params, int(offs[nc]), torch.float64, "grad_params", self.device)
         if expect_out is None:
             expect_out = torch.empty((nc, obs.nobs), dtype=torch.float64, device=dev)
         if want_grad and grad_params is None:
@@ -585,7 +672,7 @@ class Context:
         return k.value, low.value, m.value
 
     def plan_autotune(self, circuit: Circuit, state: torch.Tensor):
-        batch = state.numel() >> circuit.nqubits
+        batch = _state_rows(state, circuit.nqubits, "state", self.device)
         dt = dtype_code(state.dtype)
         self.ensure_workspace(circuit, None, batch, dt)
         self._check(self.lib.dq_plan_autotune(self.h, circuit.ref(), int(batch), dt, _ptr(state), _stream()),
@@ -602,6 +689,12 @@ def forward_grad_noalloc(circuit: Circuit, params: Optional[torch.Tensor], obs: 
     Output tensors are supplied by the caller (allocated here if None)."""
     lib = load_library()
     dev = torch.device("cuda", torch.cuda.current_device())
+    params, data = _angles(circuit, params, data, batch, params_per_row, dev.index)
+    row_weights = _f64_in(row_weights, batch * obs.nobs, "row_weights", dev.index)
+    expect_out = _out(expect_out, batch * obs.nobs, torch.float64, "expect_out", dev.index)
+    grad_params = _out(grad_params, circuit.nparams * (batch if params_per_row else 1), torch.float64,
+                       "grad_params", dev.index)
+    grad_data = _out(grad_data, batch * circuit.nfeatures, torch.float64, "grad_data", dev.index)
     if expect_out is None:
         expect_out = torch.empty((batch, obs.nobs), dtype=torch.float64, device=dev)
     if grad_params is None and circuit.nparams > 0:

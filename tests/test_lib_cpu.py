@@ -149,3 +149,51 @@ def test_uneven_batch_generator():
             if len(g.wires) == 2:
                 assert g.wires[0] != g.wires[1]
         assert len(angles) == sum(g.param >= 0 for g in gates)
+
+
+# ---------------------------------------------------------------------------
+# tensor checks of the binding (the library sees bare device pointers)
+# ---------------------------------------------------------------------------
+def test_binding_rejects_host_tensors():
+    import torch
+    from paper_2512_18995_gb300 import _lib
+    for call in (lambda: _lib._f64_in(torch.zeros(4, dtype=torch.float64), 4, "params", None),
+                 lambda: _lib._out(torch.zeros(4, dtype=torch.float64), 4, torch.float64, "out", None),
+                 lambda: _lib._state_rows(torch.zeros((1, 8), dtype=torch.complex64), 3, "state", None)):
+        with pytest.raises(_lib.DQError) as e:
+            call()
+        assert e.value.status == 1 and "CUDA tensor" in str(e.value)
+
+
+def test_binding_tensor_checks(monkeypatch):
+    """Conversion, size, type and layout checks (device check bypassed so
+    that host tensors stand in for device ones)."""
+    import torch
+    from paper_2512_18995_gb300 import _lib
+    monkeypatch.setattr(_lib, "_on_device", lambda t, what, device: None)
+    t = torch.arange(6, dtype=torch.float64)
+    assert _lib._f64_in(t, 6, "params", None) is t                 # already right: same tensor
+    f = _lib._f64_in(torch.arange(6, dtype=torch.float32)[::2], 3, "params", None)
+    assert f.dtype == torch.float64 and f.is_contiguous() and f.tolist() == [0.0, 2.0, 4.0]
+    with pytest.raises(_lib.DQError):
+        _lib._f64_in(t, 7, "params", None)
+    assert _lib._f64_in(None, 5, "params", None) is None
+    assert _lib._out(t, 6, torch.float64, "out", None) is t
+    for bad in (t.float(), t[::2], t[:5]):
+        with pytest.raises(_lib.DQError):
+            _lib._out(bad, 6, torch.float64, "out", None)
+    st = torch.zeros((3, 16), dtype=torch.complex64)
+    assert _lib._state_rows(st, 4, "state", None) == 3
+    with pytest.raises(_lib.DQError):
+        _lib._state_rows(torch.zeros(24, dtype=torch.complex64), 4, "state", None)
+    with pytest.raises(_lib.DQError):
+        _lib._state_rows(torch.zeros((16, 3), dtype=torch.complex64).t(), 4, "state", None)
+    with pytest.raises(TypeError):
+        _lib._state_rows(torch.zeros((1, 16), dtype=torch.float32), 4, "state", None)
+    c = _lib.Circuit(2, [W.Gate("rx", (0,), param=1), W.Gate("ry", (1,), data=0)])
+    p, d = _lib._angles(c, torch.zeros(4), torch.zeros((2, 1)), 2, True, None)
+    assert p.dtype == d.dtype == torch.float64
+    with pytest.raises(_lib.DQError):
+        _lib._angles(c, torch.zeros(3), None, 2, True, None)      # per-row: 2 rows x 2 params
+    with pytest.raises(_lib.DQError):
+        _lib._angles(c, torch.zeros(2), torch.zeros(1), 2, False, None)   # 2 rows x 1 feature
