@@ -519,19 +519,34 @@ DQ_API dq_status dq_lower_circuit(const dq_circuit *circuit, int density, dq_low
 /* The fused-path tile schedule of the pure circuit's lowered ops (numbered as
  * by dq_lower_circuit) for tile qubits k, always-resident low bits `low` and
  * register bits per thread M: forward passes (adjoint = 0) or the passes of
- * the adjoint sweep (adjoint = 1).  Pass p holds ops order[pass_start[p] ..
- * pass_start[p+1]) in forward order and acts on tiles of the amplitude bits
- * set in tile_bits[p] (bit b = wire nqubits-1-b); the forward direction runs
- * the passes and their ops first to last, the adjoint sweep un-applies them
- * last to first.  op_flags[i] (may be NULL) gets bit 0 when op order[i] is
- * part of a CNOT-diagonal-CNOT triple run as one parity-diagonal op (it then
- * needs no tile bit).  Every array holds `capacity` >= op count entries
- * (pass_start one more).  Returns DQ_ERR_UNSUPPORTED when no schedule exists
+ * the adjoint sweep (adjoint = 1).  Pass p acts on tiles of the amplitude
+ * bits set in tile_bits[p] (bit b = wire nqubits-1-b) and runs the entries
+ * order[pass_start[p] .. pass_start[p+1]) in its execution order (the
+ * planner regroups commuting ops to save register-layout changes); the
+ * adjoint sweep un-applies the passes and their entries last to first.
+ * Entry i names a lowered op, with op_flags[i] (may be NULL): bit 0 when the
+ * op is one of a CNOT-diagonal-CNOT triple run as one parity-diagonal op
+ * (listed as its three ops; it needs no tile bit); bit 1 when the entry is
+ * one of the three CNOTs that a SWAP of wires a < b runs as -- the first and
+ * third with control b and target a, the second with control a and target
+ * b.  So there are at most three entries per op.  Every array holds
+ * `capacity` entries (pass_start one more); too few return
+ * DQ_ERR_INVALID_ARG.  Returns DQ_ERR_UNSUPPORTED when no schedule exists
  * for these values (for instance k > nqubits), the number of passes in
  * *npasses otherwise. */
 DQ_API dq_status dq_tile_schedule(const dq_circuit *circuit, int dtype, int k, int low, int M, int adjoint,
                                   int capacity, int32_t *order, int32_t *pass_start, uint64_t *tile_bits,
                                   int32_t *op_flags, int *npasses);
+
+/* The program of the whole-row kernel (the fused path for rows of up to 16
+ * qubits held on chip) for the pure circuit's lowered ops: M register bits
+ * per thread (0: the kernel's own choice for this size and dtype, written to
+ * *M_used).  The entries order[0 .. *count) and op_flags are as in
+ * dq_tile_schedule for a single pass: the forward sweep runs them first to
+ * last, the adjoint sweep last to first.  Returns DQ_ERR_UNSUPPORTED when the
+ * rows do not fit the kernel. */
+DQ_API dq_status dq_row_program(const dq_circuit *circuit, int dtype, int M, int capacity, int32_t *order,
+                                int32_t *op_flags, int *count, int *M_used);
 
 /* The shift rules that dq_hessian and dq_density_grad apply.  Occurrence v
  * (each angle of each gate with a trainable parameter, in gate order; U3

@@ -73,7 +73,8 @@ EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path"
            "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
            "dq_forward_grad_noalloc", "dq_apply_dense", "dq_sample_workspace_bytes", "dq_sample",
            "dq_hessian", "dq_density_workspace_bytes", "dq_density_forward",
-           "dq_density_grad", "dq_plan_tuned", "dq_lower_circuit", "dq_tile_schedule", "dq_shift_rules")
+           "dq_density_grad", "dq_plan_tuned", "dq_lower_circuit", "dq_tile_schedule", "dq_row_program",
+           "dq_shift_rules")
 
 _lib = None
 
@@ -124,6 +125,8 @@ def load_library(path: str = LIB_PATH):
         "dq_lower_circuit": ([C, I, ctypes.POINTER(dq_lowered_op), I, ctypes.POINTER(I)], I),
         "dq_tile_schedule": ([C, I, I, I, I, I, I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(I)], I),
+        "dq_row_program": ([C, I, I, I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "dq_shift_rules": ([C, I, I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), D, D,
                             ctypes.POINTER(I), ctypes.POINTER(I)], I),
     }
@@ -304,16 +307,20 @@ def lower_circuit(circuit: Circuit, density: bool = False) -> List[dict]:
     return out
 
 
+# entry flags of dq_tile_schedule / dq_row_program
+FLAG_PARITY_TRIPLE, FLAG_SWAP_CNOT = 1, 2
+
+
 def tile_schedule(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64,
-                  adjoint: bool = False) -> List[Tuple[int, List[int], List[bool]]]:
+                  adjoint: bool = False) -> List[Tuple[int, List[int], List[int]]]:
     """The fused path's tile passes for ``circuit`` (dq_tile_schedule): a list
-    of (tile amplitude-bit mask, lowered-op indices in forward order,
-    parity-triple flags), or DQError(DQ_ERR_UNSUPPORTED) if no schedule
-    exists for (k, low, M)."""
+    of (tile amplitude-bit mask, lowered-op index of every entry in execution
+    order, entry flags FLAG_PARITY_TRIPLE / FLAG_SWAP_CNOT), or
+    DQError(DQ_ERR_UNSUPPORTED) if no schedule exists for (k, low, M)."""
     lib = load_library()
     cnt = ctypes.c_int(0)
     _inspect_check(lib.dq_lower_circuit(circuit.ref(), 0, None, 0, ctypes.byref(cnt)), "dq_lower_circuit")
-    cap = max(1, cnt.value)
+    cap = max(1, 3 * cnt.value)
     order = (ctypes.c_int32 * cap)()
     start = (ctypes.c_int32 * (cap + 1))()
     bits = (ctypes.c_uint64 * cap)()
@@ -322,7 +329,23 @@ def tile_schedule(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C6
     _inspect_check(lib.dq_tile_schedule(circuit.ref(), int(dtype), int(k), int(low), int(M), int(bool(adjoint)),
                                         cap, order, start, bits, flags, ctypes.byref(npass)), "dq_tile_schedule")
     return [(int(bits[p]), [int(x) for x in order[start[p]:start[p + 1]]],
-             [bool(x) for x in flags[start[p]:start[p + 1]]]) for p in range(npass.value)]
+             [int(x) for x in flags[start[p]:start[p + 1]]]) for p in range(npass.value)]
+
+
+def row_program(circuit: Circuit, M: int = 0, dtype: int = DQ_C64) -> Tuple[int, List[int], List[int]]:
+    """The whole-row kernel's program for ``circuit`` (dq_row_program):
+    (register bits used, lowered-op index of every entry in execution order,
+    entry flags as in tile_schedule)."""
+    lib = load_library()
+    cnt = ctypes.c_int(0)
+    _inspect_check(lib.dq_lower_circuit(circuit.ref(), 0, None, 0, ctypes.byref(cnt)), "dq_lower_circuit")
+    cap = max(1, 3 * cnt.value)
+    order = (ctypes.c_int32 * cap)()
+    flags = (ctypes.c_int32 * cap)()
+    m = ctypes.c_int(0)
+    _inspect_check(lib.dq_row_program(circuit.ref(), int(dtype), int(M), cap, order, flags, ctypes.byref(cnt),
+                                      ctypes.byref(m)), "dq_row_program")
+    return m.value, [int(x) for x in order[:cnt.value]], [int(x) for x in flags[:cnt.value]]
 
 
 def shift_rules(circuit: Circuit):

@@ -2106,12 +2106,14 @@ dq_status dq_tile_schedule(const dq_circuit *circuit, int dtype, int k, int low,
     if (st != DQ_OK) return st;
     p.n = circuit->nqubits;
     p.ngates = (int)p.gates.size();
-    if (capacity < p.ngates) return DQ_ERR_INVALID_ARG;
     const int amp = amp_bytes(dtype);
     if (M < 2 || M > (dtype == DQ_C64 ? 5 : 4) || k > kTileMaxK || !tile_supported(p.n, amp))
         return DQ_ERR_UNSUPPORTED;
     TileSchedule sc;
     if (!tile_build_schedule(p, k, low, M, amp, sc, adjoint != 0)) return DQ_ERR_UNSUPPORTED;
+    size_t entries = 0;
+    for (const TPass &ps : sc.passes) entries += ps.gates.size();
+    if ((size_t)capacity < entries || (size_t)capacity < sc.passes.size()) return DQ_ERR_INVALID_ARG;
     int pos = 0;
     for (size_t q = 0; q < sc.passes.size(); ++q) {
         const TPass &ps = sc.passes[q];
@@ -2119,13 +2121,39 @@ dq_status dq_tile_schedule(const dq_circuit *circuit, int dtype, int k, int low,
         uint64_t T = 0;
         for (int b : ps.T) T |= uint64_t(1) << b;
         tile_bits[q] = T;
-        for (size_t j = 0; j < ps.gates.size() && pos < capacity; ++j, ++pos) {
+        for (size_t j = 0; j < ps.gates.size(); ++j, ++pos) {
             order[pos] = ps.gates[j];
-            if (op_flags) op_flags[pos] = ps.fused[j] ? 1 : 0;
+            if (op_flags) op_flags[pos] = ps.flags[j];
         }
     }
     pass_start[sc.passes.size()] = pos;
     *npasses = (int)sc.passes.size();
+    return DQ_OK;
+}
+
+dq_status dq_row_program(const dq_circuit *circuit, int dtype, int M, int capacity, int32_t *order,
+                         int32_t *op_flags, int *count, int *M_used) {
+    if (!order || !count || !M_used) return DQ_ERR_INVALID_ARG;
+    if (dtype != DQ_C64 && dtype != DQ_C128) return DQ_ERR_INVALID_ARG;
+    Plan p;
+    int ncs = 0, ncr = 0;
+    const dq_status st = compile_gates(nullptr, circuit, 0, p.gates, p.bind, 0, &ncs, &ncr, false);
+    if (st != DQ_OK) return st;
+    p.n = circuit->nqubits;
+    p.ngates = (int)p.gates.size();
+    p.nparams = circuit->nparams;
+    p.nfeat = circuit->nfeatures;
+    const int m = M ? M : rows_pick_M(p.n, amp_bytes(dtype));
+    if (m < 2 || m > (dtype == DQ_C64 ? 4 : 3)) return DQ_ERR_UNSUPPORTED;
+    RowProgram rp;
+    if (!rows_build_program(p, m, rp)) return DQ_ERR_UNSUPPORTED;
+    if ((size_t)capacity < rp.gates.size()) return DQ_ERR_INVALID_ARG;
+    for (size_t i = 0; i < rp.gates.size(); ++i) {
+        order[i] = rp.gates[i];
+        if (op_flags) op_flags[i] = rp.flags[i];
+    }
+    *count = (int)rp.gates.size();
+    *M_used = m;
     return DQ_OK;
 }
 

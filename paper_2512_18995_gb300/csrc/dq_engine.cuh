@@ -83,6 +83,7 @@ struct GOp {
     int cl;          // control local bit or -1
     int cg;          // control global bit or -1 (none)
     int kind, coef, rowstep, slot;
+    int gi;          // plan gate it comes from (a parity triple: its first CNOT; host inspection)
 };
 
 // A run of operations executed with one register layout.
@@ -376,6 +377,26 @@ inline std::vector<char> pair_real_diag(std::vector<GOp> &ops, int i0 = 0, int i
         }
     }
     return head;
+}
+
+// Host inspection: the plan gate of every op in `ops` order, flagged (bit 0:
+// one gate of a parity-diagonal triple, which is listed as its three gates;
+// bit 1: one of the three CNOTs a SWAP runs as).  `gates` holds the plan's
+// gates (their class tells SWAPs apart).
+template <typename Gates>
+inline void record_order(const std::vector<GOp> &ops, const Gates &gates, std::vector<int> &order,
+                         std::vector<char> &flags) {
+    for (const GOp &o : ops) {
+        if (o.cls == CLS_PDIAG) {
+            for (int j = 0; j < 3; ++j) {
+                order.push_back(o.gi + j);
+                flags.push_back(1);
+            }
+            continue;
+        }
+        order.push_back(o.gi);
+        flags.push_back(gates[o.gi].cls == CLS_SWAP ? 2 : 0);
+    }
 }
 
 inline bool pair_handlers_match(const EOp &real, const EOp &diag) {

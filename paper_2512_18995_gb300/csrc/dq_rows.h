@@ -11,20 +11,25 @@
 
 namespace dq {
 
-// Engine program for whole rows of one circuit: ops in gate order (SWAP as
-// three CNOTs), register layouts for the forward and the reverse sweep.
+// Engine program for whole rows of one circuit: ops in an execution order
+// that keeps every pair of non-commuting ops in gate order (SWAP as three
+// CNOTs), register layouts for the forward and the reverse sweep.
 // Reverse segments list their first (highest) op in op0 and run downwards.
 struct RowProgram {
     int n = 0, M = 0;
     int nacc_shared = 0, nacc_row = 0;
     bool pdiag = false;            // holds parity-diagonal ops
     std::vector<EOp> fops, rops;   // op i decoded for its forward / reverse layout
+    std::vector<int> gates;        // host inspection: plan gate per executed op (see record_order)
+    std::vector<char> flags;
     std::vector<ESeg> fsegs, rsegs;
     EOp *d_fops = nullptr, *d_rops = nullptr;
     ESeg *d_fsegs = nullptr, *d_rsegs = nullptr;
     void release();
 };
 
+// Register bits the whole-row kernel uses for an n-qubit row (0: the row
+// does not fit the kernel).
 int rows_pick_M(int n, int amp_bytes);
 bool rows_build_program(const Plan &p, int M, RowProgram &out);
 size_t rows_smem_bytes(const RowProgram &rp, int amp, bool grad, int nobs, int threads);

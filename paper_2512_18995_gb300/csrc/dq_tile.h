@@ -35,8 +35,11 @@ struct TPass {
     int rseg0 = 0, nrseg = 0; // reverse-sweep layouts (adjoint schedules)
     int slot0 = 0, nslot = 0; // gradient slots of the pass (adjoint schedules)
     bool pdiag = false;       // holds parity-diagonal ops
-    std::vector<int> gates;   // plan gates of the pass in execution order (host inspection)
-    std::vector<char> fused;  // per entry of gates: part of a parity-diagonal triple
+    // Host inspection: the plan gate of every executed op in forward order,
+    // with flags (bit 0: one gate of a parity-diagonal triple, listed as its
+    // three gates; bit 1: one of the three CNOTs a SWAP runs as).
+    std::vector<int> gates;
+    std::vector<char> flags;
 };
 
 // Passes of fused gates.  Adjoint schedules also carry, per pass, the ops

@@ -117,6 +117,7 @@ bool rows_build_program(const Plan &p, int M, RowProgram &out) {
             // CNOT, diagonal, CNOT: one parity-diagonal op with the diagonal's slot
             const DevGate &d = p.gates[gi + 1];
             GOp o{};
+            o.gi = gi;
             o.cls = CLS_PDIAG;
             o.tl = o.tg = g.t;
             o.cl = o.cg = g.c;
@@ -131,6 +132,7 @@ bool rows_build_program(const Plan &p, int M, RowProgram &out) {
         }
         auto push = [&](int cls, int t, int c, int slot) {
             GOp o{};
+            o.gi = gi;
             o.cls = cls;
             o.tl = t;
             o.tg = t;
@@ -152,6 +154,7 @@ bool rows_build_program(const Plan &p, int M, RowProgram &out) {
     }
     schedule_for_layouts(ops, M, kLaneBits);
     const std::vector<char> head = pair_real_diag(ops);
+    record_order(ops, p.gates, out.gates, out.flags);
     std::vector<int> fwd(ops.size()), rev(ops.size());
     for (size_t i = 0; i < ops.size(); ++i) {
         fwd[i] = (int)i;

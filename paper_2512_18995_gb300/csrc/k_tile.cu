@@ -180,8 +180,9 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
         }
         pass.op0 = (int)out.ops.size();
         std::vector<GOp> gops;
-        auto push_op = [&](int cls, int tb, int cb, const DevGate &g, int slot) {
+        auto push_op = [&](int cls, int tb, int cb, const DevGate &g, int slot, int gi) {
             GOp o{};
+            o.gi = gi;
             o.cls = cls;
             o.tl = loc[tb];
             o.tg = tb;
@@ -195,14 +196,10 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
         };
         for (int ii : sched) {
             const Item &it = items[ii];
-            for (int j = 0; j < it.len; ++j) {
-                pass.gates.push_back(it.g + j);
-                pass.fused.push_back(it.len == 3);
-            }
             if (it.len == 3) {
                 const DevGate &c = p.gates[it.g], &d = p.gates[it.g + 1];
                 const int slot = it.g + 1 < (int)p.slot_of_gate.size() ? p.slot_of_gate[it.g + 1] : -1;
-                push_op(CLS_PDIAG, c.t, c.c, d, slot);
+                push_op(CLS_PDIAG, c.t, c.c, d, slot, it.g);
                 pass.pdiag = true;
                 continue;
             }
@@ -210,16 +207,17 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
             const DevGate &g = p.gates[gi];
             const int slot = gi < (int)p.slot_of_gate.size() ? p.slot_of_gate[gi] : -1;
             if (g.cls == CLS_SWAP) {
-                push_op(CLS_ANTI, g.c, g.t, g, -1);
-                push_op(CLS_ANTI, g.t, g.c, g, -1);
-                push_op(CLS_ANTI, g.c, g.t, g, -1);
+                push_op(CLS_ANTI, g.c, g.t, g, -1, gi);
+                push_op(CLS_ANTI, g.t, g.c, g, -1, gi);
+                push_op(CLS_ANTI, g.c, g.t, g, -1, gi);
             } else {
-                push_op(g.cls, g.t, g.c, g, slot);
+                push_op(g.cls, g.t, g.c, g, slot, gi);
             }
         }
         pass.nops = (int)gops.size();
         schedule_for_layouts(gops, M, kTileLaneBits);
         const std::vector<char> head = pair_real_diag(gops);
+        record_order(gops, p.gates, pass.gates, pass.flags);
         // register layouts, then decode every op against its layout
         pass.seg0 = (int)out.segs.size();
         std::vector<int> B;

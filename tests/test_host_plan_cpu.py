@@ -270,17 +270,68 @@ def tma_dims(T, wb):
 SCHEDULES = [(9, 8, 5, 3), (10, 8, 6, 3), (10, 10, 7, 2), (11, 9, 5, 4), (12, 10, 7, 5), (12, 12, 5, 4)]
 
 
+def swap_part(op, k):
+    """The k-th of the three CNOTs a SWAP of wires a < b runs as."""
+    a, b = sorted(op["wires"])
+    wires = (b, a) if k in (0, 2) else (a, b)
+    return {"kind": "cnot", "wires": wires, "param": -1, "data": -1, "angle": 0.0, "conj": False}
+
+
+def check_entries(ops, idx, flags):
+    """Every op once (a SWAP as its three CNOTs); parity triples listed as
+    CNOT, diagonal, CNOT on one pair; returns the ops to apply in order."""
+    seq, seen = [], {}
+    j = 0
+    while j < len(idx):
+        i, f = idx[j], flags[j]
+        if f & 1:
+            a, d, e = (ops[x] for x in idx[j:j + 3])
+            assert flags[j:j + 3] == [1, 1, 1] and idx[j + 1] == i + 1 and idx[j + 2] == i + 2
+            assert a["kind"] == e["kind"] == "cnot" and a["wires"] == e["wires"]
+            assert d["kind"] in DIAGONAL and d["wires"] == (a["wires"][1],)
+            seq += [a, d, e]
+            for x in idx[j:j + 3]:
+                seen[x] = seen.get(x, 0) + 1
+            j += 3
+            continue
+        if f & 2:
+            assert ops[i]["kind"] == "swap"
+            seq.append(swap_part(ops[i], seen.get(i, 0)))
+        else:
+            assert ops[i]["kind"] != "swap"
+            seq.append(ops[i])
+        seen[i] = seen.get(i, 0) + 1
+        j += 1
+    assert sorted(seen) == list(range(len(ops)))
+    for i, cnt in seen.items():
+        assert cnt == (3 if ops[i]["kind"] == "swap" else 1), (i, ops[i], cnt)
+    return seq
+
+
+def assert_same_evolution(n, ops, seq, params, data_row):
+    s0 = np.zeros((1, 1 << n), dtype=complex)
+    s0[0, 0] = 1.0
+    for q in range(n):
+        s0 = apply_op(s0, n, {"kind": "h", "wires": (q,), "param": -1, "data": -1, "angle": 0.0, "conj": False})
+    a, b = s0.copy(), s0.copy()
+    for op in ops:
+        a = apply_op(a, n, op, params, data_row)
+    for op in seq:
+        b = apply_op(b, n, op, params, data_row)
+    np.testing.assert_allclose(b, a, atol=1e-12)
+
+
 @pytest.mark.parametrize("n,k,low,M", SCHEDULES)
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_tile_schedule_is_an_exact_reordering(L, n, k, low, M, adjoint):
     """Every lowered op runs exactly once; each pass's tile has k bits,
     contains the resident low bits and every bit its ops act on
     non-diagonally (parity triples act diagonally), fits five TMA box
-    dimensions; and the schedule's order gives the same state as circuit
+    dimensions; and the execution order -- passes regrouped, ops within a
+    pass reordered for register layouts -- gives the same state as circuit
     order."""
     rng = np.random.default_rng(n * 100 + k * 10 + M)
-    kinds = W.GATE_KINDS
-    gates, P = random_circuit(n, 60, rng, kinds, data_features=2)
+    gates, P = random_circuit(n, 60, rng, W.GATE_KINDS, data_features=2)
     params = rng.uniform(-4, 4, size=max(P, 1))
     data_row = rng.uniform(-4, 4, size=2)
     c = L.Circuit(n, gates, nparams=max(P, 1), nfeatures=2)
@@ -291,40 +342,21 @@ def test_tile_schedule_is_an_exact_reordering(L, n, k, low, M, adjoint):
                 L.tile_schedule(c, k, low, M, dtype=dtype, adjoint=adjoint)
             continue
         passes = L.tile_schedule(c, k, low, M, dtype=dtype, adjoint=adjoint)
-        seen = [i for _, idx, _ in passes for i in idx]
-        assert sorted(seen) == list(range(len(ops)))
-        for T, idx, fused in passes:
+        idx = [i for _, ix, _ in passes for i in ix]
+        flags = [f for _, _, fl in passes for f in fl]
+        seq = check_entries(ops, idx, flags)
+        for T, ix, fl in passes:
             assert bin(T).count("1") == k
             assert T & ((1 << low) - 1) == (1 << low) - 1
             assert tma_dims(T, wb) <= 5
             if adjoint:
-                assert not any(fused)
-            for j, (i, f) in enumerate(zip(idx, fused)):
-                if f:
+                assert not any(f & 1 for f in fl)
+            for i, f in zip(ix, fl):
+                if f & 1:
                     continue
                 for b in nondiagonal_bits(ops[i], n):
                     assert (T >> b) & 1, (i, ops[i], b, bin(T))
-            # fused triples are CNOT, diagonal, CNOT on one pair
-            j = 0
-            while j < len(idx):
-                if fused[j]:
-                    a, d, e = (ops[x] for x in idx[j:j + 3])
-                    assert a["kind"] == e["kind"] == "cnot" and a["wires"] == e["wires"]
-                    assert d["kind"] in DIAGONAL and d["wires"] == (a["wires"][1],)
-                    j += 3
-                else:
-                    j += 1
-        if dtype == L.DQ_C64:
-            s0 = np.zeros((1, 1 << n), dtype=complex)
-            s0[0, 0] = 1.0
-            s0 = apply_op(s0, n, {"kind": "h", "wires": (0,), "param": -1, "data": -1, "angle": 0.0,
-                                  "conj": False})
-            a, b = s0.copy(), s0.copy()
-            for op in ops:
-                a = apply_op(a, n, op, params, data_row)
-            for i in seen:
-                b = apply_op(b, n, ops[i], params, data_row)
-            np.testing.assert_allclose(b, a, atol=1e-12)
+        assert_same_evolution(n, ops, seq, params, data_row)
 
 
 def test_tile_schedule_fuses_parity_triples_on_forward_passes(L):
@@ -332,9 +364,46 @@ def test_tile_schedule_fuses_parity_triples_on_forward_passes(L):
     gates = [Gate("rzz", (q, (q + 3) % n), param=q) for q in range(n)]
     c = L.Circuit(n, gates)
     fwd = L.tile_schedule(c, 9, 5, 4)
-    assert all(f for _, _, fl in fwd for f in fl)
+    assert all(f == L.FLAG_PARITY_TRIPLE for _, _, fl in fwd for f in fl)
     rev = L.tile_schedule(c, 9, 5, 4, adjoint=True)
     assert not any(f for _, _, fl in rev for f in fl)
+
+
+@pytest.mark.parametrize("n", [7, 9, 12, 14, 16])
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_row_program_is_an_exact_reordering(L, n, dtype):
+    """The whole-row kernel's single pass: every op once, parity triples
+    fused, and its execution order gives the circuit's state.  (The kernel
+    itself takes rows of up to 12 qubits for complex64 and 11 for
+    complex128; larger n only exercise the planner with an explicit register
+    width.)"""
+    rng = np.random.default_rng(700 + n + 50 * dtype)
+    gates, P = random_circuit(n, 70, rng, W.GATE_KINDS, data_features=2)
+    params = rng.uniform(-4, 4, size=max(P, 1))
+    data_row = rng.uniform(-4, 4, size=2)
+    c = L.Circuit(n, gates, nparams=max(P, 1), nfeatures=2)
+    ops = L.lower_circuit(c)
+    for M in ([0, 2, 3, 4] if dtype == 0 else [0, 2, 3]):
+        if M and n < 5 + M:
+            continue
+        if M == 0 and n > (12 if dtype == 0 else 11):    # rows of 2^12 c64 / 2^11 c128 at most
+            with pytest.raises(L.DQError) as e:
+                L.row_program(c, M, dtype=dtype)
+            assert e.value.status == 2
+            continue
+        m, idx, flags = L.row_program(c, M, dtype=dtype)
+        assert m == M or (M == 0 and 2 <= m <= 4 - dtype)
+        seq = check_entries(ops, idx, flags)
+        if n <= 12:
+            assert_same_evolution(n, ops, seq, params, data_row)
+
+
+def test_row_program_rejects_rows_that_do_not_fit(L):
+    # 17 qubits; 6 < 5 lane bits + 3 register bits; 5 register bits (c64); 4 (c128)
+    for n, M, dtype in ((17, 0, 0), (6, 3, 0), (9, 5, 0), (9, 4, 1)):
+        with pytest.raises(L.DQError) as e:
+            L.row_program(L.Circuit(n, [Gate("h", (0,))]), M, dtype=dtype)
+        assert e.value.status == 2
 
 
 @pytest.mark.parametrize("n,k,low,M,dtype", [(10, 11, 5, 3, 0), (10, 9, 5, 6, 0), (10, 9, 5, 5, 1),
