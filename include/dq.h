@@ -119,7 +119,10 @@ typedef enum dq_gate_kind {
 /* Which implementation runs the circuit.
  *   DQ_PATH_PLAIN: one kernel launch per gate (and per adjoint step), each a
  *                  full sweep over the batch -- the paper's gate-by-gate
- *                  evolution, kept as the baseline.
+ *                  evolution, kept as the baseline.  Its expectation and
+ *                  adjoint kernels take one grid row per batch row, so they
+ *                  accept at most 65535 rows per call (more return
+ *                  DQ_ERR_CUDA, invalid configuration).
  *   DQ_PATH_FUSED: whole states in shared memory for small n, otherwise
  *                  k-qubit tiles staged in shared memory by TMA with many
  *                  gates applied per HBM pass.
