@@ -33,7 +33,10 @@ def _rank_main(rank, world, port, out):
         ms_local = 10.0 + 3.0 * rank          # rank 1 is the slow replica
         ms = bench.max_over_ranks(ms_local, world, dist, torch.device("cpu"))
         value = bench.job_value(world, 1 << 20, 5, ms)
-        out[rank] = (ms, value)
+        # only rank 1 saw a throttled clock: both ranks measure again
+        again = bench.any_rank(rank == 1, world, dist, torch.device("cpu"))
+        neither = bench.any_rank(False, world, dist, torch.device("cpu"))
+        out[rank] = (ms, value, again, neither)
     finally:
         dist.destroy_process_group()
 
@@ -48,9 +51,10 @@ def test_two_replicas_take_the_slowest_time():
         res = dict(out)
     assert sorted(res) == [0, 1]
     for r in (0, 1):
-        ms, value = res[r]
+        ms, value, again, neither = res[r]
         assert ms == pytest.approx(13.0)                                   # max over ranks
         assert value == pytest.approx(world * (1 << 20) * 5 / 13e-3 / 1e9)  # all ranks' bytes / slowest time
+        assert again is True and neither is False
 
 
 def test_single_rank_is_its_own_time():
@@ -71,3 +75,16 @@ def test_reference_arm_prints_on_rank_zero_only():
     with redirect_stdout(buf):
         bench.reference_arm(Args, rank=1, world=2)   # returns at once, no work
     assert buf.getvalue() == ""
+
+
+def test_throttle_rule():
+    sys.path.insert(0, ROOT)
+    import bench
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert not bench.throttled(ok)
+    assert not bench.throttled({**ok, "sm_mhz": 1800.0, "reasons": ["sw_power_cap"]})   # power cap: kept
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.throttled({**ok, "reasons": [r]})
+    assert bench.throttled({**ok, "sm_mhz": 1200.0})                  # far below max, no reason: a lock
+    assert not bench.throttled({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
+    assert bench.any_rank(True, 1, None, None) and not bench.any_rank(False, 1, None, None)
