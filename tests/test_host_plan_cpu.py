@@ -160,13 +160,15 @@ def test_lowered_channel_equals_kraus_superoperator(L, kind, p):
     np.testing.assert_allclose(got, ref, atol=1e-14)
 
 
-@pytest.mark.parametrize("seed", [5, 6])
+@pytest.mark.parametrize("seed", [5, 6, 7])
 def test_lowered_density_circuit_matches_the_oracle(L, oracle_mod, seed):
-    """Gates and channels on 3 qubits: the lowered 6-wire ops applied to
-    vec(|0><0|) give the oracle's density matrix."""
+    """Gates (trainable, encoded and fixed angles) and channels on 3 qubits:
+    the lowered 6-wire ops applied to vec(|0><0|) give the oracle's density
+    matrix."""
     n = 3
     rng = np.random.default_rng(seed)
-    gates, P = random_circuit(n, 16, rng, W.GATE_KINDS)
+    gates, P = random_circuit(n, 16, rng, W.GATE_KINDS, data_features=3)
+    data = rng.uniform(-3, 3, size=(1, 3))
     noisy = []
     for i, g in enumerate(gates):
         noisy.append(g)
@@ -174,12 +176,12 @@ def test_lowered_density_circuit_matches_the_oracle(L, oracle_mod, seed):
             noisy.append(Gate(W.NOISE_KINDS[(i // 2) % 4], (int(rng.integers(n)),),
                               angle=float(rng.uniform(0.02, 0.4))))
     params = rng.uniform(-4, 4, size=max(P, 1))
-    ops = L.lower_circuit(L.Circuit(n, noisy, nparams=max(P, 1)), density=True)
+    ops = L.lower_circuit(L.Circuit(n, noisy, nparams=max(P, 1), nfeatures=3), density=True)
     v = np.zeros((1, 1 << (2 * n)), dtype=complex)
     v[0, 0] = 1.0
     for op in ops:
-        v = apply_op(v, 2 * n, op, params)
-    _, rho = oracle_mod.density(n, noisy, None, params)
+        v = apply_op(v, 2 * n, op, params, data[0])
+    _, rho = oracle_mod.density(n, noisy, None, params, data)
     np.testing.assert_allclose(v[0], rho[0].reshape(-1), atol=1e-12)
 
 
