@@ -470,3 +470,28 @@ def test_shift_rule_table_accepts_noisy_circuits(L):
     with pytest.raises(L.DQError):
         L.shift_rules(L.Circuit(2, [Gate("depolarizing", (1,), angle=0.9)]))
     assert L.shift_rules(L.Circuit(2, [Gate("h", (0,))])) == ([], [0], [], [])
+
+
+def test_inspection_calls_reject_null_arguments(L):
+    import ctypes
+    lib = L.load_library()
+    c = L.Circuit(9, [Gate("h", (0,))])
+    n = ctypes.c_int(0)
+    i32 = (ctypes.c_int32 * 8)()
+    u64 = (ctypes.c_uint64 * 8)()
+    assert lib.dq_lower_circuit(None, 0, None, 0, ctypes.byref(n)) == 1
+    assert lib.dq_lower_circuit(c.ref(), 0, None, 0, None) == 1
+    assert lib.dq_lower_circuit(c.ref(), 2, None, 0, ctypes.byref(n)) == 1           # density flag 0 or 1
+    assert lib.dq_tile_schedule(None, 0, 8, 5, 3, 0, 8, i32, i32, u64, None, ctypes.byref(n)) == 1
+    assert lib.dq_tile_schedule(c.ref(), 0, 8, 5, 3, 0, 8, None, i32, u64, None, ctypes.byref(n)) == 1
+    assert lib.dq_tile_schedule(c.ref(), 5, 8, 5, 3, 0, 8, i32, i32, u64, None, ctypes.byref(n)) == 1  # dtype
+    m = ctypes.c_int(0)
+    assert lib.dq_row_program(None, 0, 0, 8, i32, None, ctypes.byref(n), ctypes.byref(m)) == 1
+    assert lib.dq_row_program(c.ref(), 0, 0, 8, i32, None, None, ctypes.byref(m)) == 1
+    assert lib.dq_shift_rules(None, 0, 0, None, None, None, None, ctypes.byref(n), ctypes.byref(m)) == 1
+    assert lib.dq_shift_rules(c.ref(), 0, 0, None, None, None, None, None, ctypes.byref(m)) == 1
+    # too small an output array: rejected with nothing written
+    ops = (L.dq_lowered_op * 1)()
+    c3 = L.Circuit(3, [Gate("ccx", (0, 1, 2))])
+    assert lib.dq_lower_circuit(c3.ref(), 0, ops, 1, ctypes.byref(n)) == 1 and n.value == 7
+    assert ops[0].param_idx == 0 and ops[0].data_idx == 0     # untouched (a written op holds -1 there)
