@@ -197,3 +197,11 @@ def test_binding_tensor_checks(monkeypatch):
         _lib._angles(c, torch.zeros(3), None, 2, True, None)      # per-row: 2 rows x 2 params
     with pytest.raises(_lib.DQError):
         _lib._angles(c, torch.zeros(2), torch.zeros(1), 2, False, None)   # 2 rows x 1 feature
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without libdq.so the binding refuses to load."""
+    from paper_2512_18995_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        _lib.load_library(str(tmp_path / "libdq.so"))
