@@ -205,3 +205,19 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(ImportError, match="no CPU fallback"):
         _lib.load_library(str(tmp_path / "libdq.so"))
+
+
+def test_product_never_touches_the_oracle():
+    """The library and its binding share nothing with the oracle: no import,
+    include, path or symbol of it anywhere in the package."""
+    pkg = os.path.join(ROOT, "paper_2512_18995_gb300")
+    hits = []
+    for d, _, files in os.walk(pkg):
+        if "_build" in d or "__pycache__" in d:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                text = open(os.path.join(d, f), encoding="utf-8").read()
+                if re.search(r"\boracle\b", text):
+                    hits.append(os.path.relpath(os.path.join(d, f), ROOT))
+    assert not hits, hits
