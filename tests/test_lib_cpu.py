@@ -221,3 +221,13 @@ def test_product_never_touches_the_oracle():
                 if re.search(r"\boracle\b", text):
                     hits.append(os.path.relpath(os.path.join(d, f), ROOT))
     assert not hits, hits
+
+
+def test_oracle_shares_nothing_with_the_library():
+    """The oracle includes only the C standard library and OpenMP and imports
+    neither the package nor its headers."""
+    src = open(os.path.join(ROOT, "oracle", "oracle.c"), encoding="utf-8").read()
+    includes = set(re.findall(r"#include\s*[<\"]([^>\"]+)[>\"]", src))
+    assert includes <= {"complex.h", "math.h", "stdint.h", "stdlib.h", "string.h", "omp.h"}, includes
+    py = open(os.path.join(ROOT, "oracle", "__init__.py"), encoding="utf-8").read()
+    assert "paper_2512_18995_gb300" not in py and "dq.h" not in py and "libdq" not in py
