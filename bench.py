@@ -174,6 +174,31 @@ def oracle_rate(wl, budget_s, max_steps=None):
     return rate, steps, dt, oracle.num_threads()
 
 
+def oracle_rate_single_thread(budget_s=4.0):
+    """The same gate-equivalent GB/s of the oracle on one host core: a child
+    process with OpenMP held to one thread times a prefix of the workload's
+    gates (a quarter of them) as many times as fit the budget."""
+    code = (
+        "import json, time, oracle, workloads as W\n"
+        "from bench import gate_pass_bytes\n"
+        "oracle.build()\n"
+        "wl = W.config_c2()\n"
+        "gates = wl.gates[:len(wl.gates) // 4]\n"
+        "t0 = time.perf_counter(); oracle.run(wl.n, gates, wl.params); per = time.perf_counter() - t0\n"
+        f"reps = max(1, int({budget_s} / max(per, 1e-6)))\n"
+        "t0 = time.perf_counter()\n"
+        "for _ in range(reps): oracle.run(wl.n, gates, wl.params)\n"
+        "dt = time.perf_counter() - t0\n"
+        "print(json.dumps({'value': gate_pass_bytes(wl.n, gates) * reps / dt / 1e9, 'cores': oracle.num_threads(),"
+        " 'sample': f'{reps} x the first {len(gates)} of {len(wl.gates)} gates in {dt:.1f} s'}))\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], cwd=os.path.dirname(os.path.abspath(__file__)), env=env,
+                         capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        return {"unavailable": out.stderr.strip().splitlines()[-1][:160] if out.stderr.strip() else "failed"}
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def max_over_ranks(ms, world, dist, device):
     """The job's time: the slowest replica's (all ranks receive it)."""
     if world <= 1:
@@ -363,7 +388,8 @@ def our_arm(args, rank, world, dist):
         if world == 1 and not args.no_cpu:
             rate, steps, dt, cores = oracle_rate(wl, budget_s=args.cpu_budget)
             cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"{steps} full steps (480-gate forward + <sum Z>) in {dt:.1f} s"}
+                   "sample": f"{steps} full steps (480-gate forward + <sum Z>) in {dt:.1f} s",
+                   "single_thread": oracle_rate_single_thread()}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

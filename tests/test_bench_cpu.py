@@ -34,3 +34,10 @@ def test_reference_arm_prints_the_contract_line():
 
 def test_reference_arm_other_ranks_print_nothing():
     assert run_reference({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_single_thread_oracle_rate():
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.oracle_rate_single_thread(budget_s=1.0)
+    assert r["cores"] == 1 and r["value"] > 0 and "of 480 gates" in r["sample"], r
