@@ -323,11 +323,17 @@ DQ_API dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit 
  * DQ_ERR_UNSUPPORTED otherwise.  Its scratch (gate tables, bound gate
  * coefficients, Pauli terms and per-CTA gradient partials) is a fixed
  * static device array of DQ_NOALLOC_SCRATCH_BYTES bytes that every GPU that
- * loads the library holds until the process exits; a call needing more
- * returns DQ_ERR_UNSUPPORTED with the required size in `err`.
+ * loads the library's device code holds until the process exits; a call
+ * needing more returns DQ_ERR_UNSUPPORTED with the required size in `err`.
  *
  * The first call on each device looks up that array's device address (with
- * that device current), so make that first call before any stream capture.
+ * that device current).  Under CUDA's lazy module loading (the default) that
+ * lookup is also what loads the device code and reserves the array on the
+ * device, so make the first call at start-up, before the caller's own
+ * allocator takes the rest of the memory and before any stream capture.
+ * The call uploads its gate and term tables from host buffers of its own on
+ * `stream`; on a stream that is capturing it returns DQ_ERR_UNSUPPORTED
+ * before doing anything.
  * All calls on a device share the one array and it keeps the last call's
  * contents, so two calls whose work overlaps on the GPU (different streams,
  * or host threads) race: serialise them, e.g. on one stream.

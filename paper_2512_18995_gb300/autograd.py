@@ -8,7 +8,9 @@ are kept from the forward pass and the backward pass only runs the reverse
 sweep; otherwise nothing but the inputs is kept and the backward pass
 recomputes the forward states (dq_forward_grad) before sweeping back.  Small
 states take the fused on-chip path, which always recomputes (it is cheaper
-than storing).
+than storing).  The kept states are consumed by the first backward pass (the
+sweep runs on them in place); a further backward through the same graph
+recomputes.
 """
 from __future__ import annotations
 
@@ -61,7 +63,12 @@ class ExpectationFunction(torch.autograd.Function):
         params, data, state = fctx.saved_tensors
         w = grad_out.detach().to(torch.float64).contiguous()
         ctx = fctx.context
-        if state is not None:
+        if state is not None and not getattr(fctx, "state_swept", False):
+            # The reverse sweep un-applies the circuit on the kept states in
+            # place (no copy).  The library writes through a raw pointer, so
+            # torch does not see the change: remember it, and let a second
+            # backward through the same graph (retain_graph=True) recompute.
+            fctx.state_swept = True
             gp, gd = ctx.adjoint_grad(fctx.circuit, params, fctx.obs, state, data=data, row_weights=w,
                                       params_per_row=fctx.ppr, clobber=True)
         else:

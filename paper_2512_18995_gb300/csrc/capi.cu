@@ -2240,10 +2240,9 @@ extern "C" dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const do
     if (dtype != DQ_C64 && dtype != DQ_C128) return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "unknown dtype");
     if (batch < 0) return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "batch < 0");
     if (!circuit) return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "circuit is NULL");
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(err, err_len, DQ_ERR_CUDA, "no current device");
-    // Validate and translate with a throw-away context-free helper context
-    // (only its error string is used; nothing is allocated on the device).
+    // Validate and translate with a throw-away helper context (only its error
+    // string is used; nothing touches the device before every argument has
+    // been checked).
     dq_ctx scratch_ctx;
     std::vector<DevGate> gates;
     std::vector<BindGate> bind;
@@ -2259,6 +2258,8 @@ extern "C" dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const do
         if (obs->nobs < 1 || !obs->term_offsets || obs->term_offsets[0] != 0)
             return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "malformed observables");
         nobs = obs->nobs;
+        if (obs->term_offsets[nobs] > 0 && !obs->terms)
+            return noalloc_fail(err, err_len, DQ_ERR_INVALID_ARG, "terms is NULL");
         const uint64_t allowed = (uint64_t(1) << n) - 1;
         for (int o = 0; o < nobs; ++o) {
             if (obs->term_offsets[o + 1] < obs->term_offsets[o])
@@ -2290,6 +2291,20 @@ extern "C" dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const do
     if (grad_params && circuit->nparams == 0) grad_params = nullptr;
     if (grad_data && circuit->nfeatures == 0) grad_data = nullptr;
 
+    // Host-side validation is done; from here on the device is involved.
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(err, err_len, DQ_ERR_CUDA, "no current device");
+    // The gate and term tables are uploaded from this call's own host
+    // buffers, which are gone once it returns; a captured copy would read
+    // them again at every replay.  So a capturing stream is refused.
+    {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess)
+            return noalloc_fail(err, err_len, DQ_ERR_CUDA, "cannot query the stream's capture status");
+        if (cap != cudaStreamCaptureStatusNone)
+            return noalloc_fail(err, err_len, DQ_ERR_UNSUPPORTED,
+                                "the stream is capturing; this entry point uploads per-call host tables");
+    }
     Plan p;
     p.n = n;
     p.ngates = (int)gates.size();
@@ -2344,8 +2359,13 @@ extern "C" dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const do
         cudaMemcpyAsync(d_terms, wterms.data(), sizeof(DevTerm) * wterms.size(), cudaMemcpyHostToDevice, s) !=
             cudaSuccess)
         return noalloc_fail(err, err_len, DQ_ERR_CUDA, "copying terms: %s", cudaGetErrorString(cudaGetLastError()));
-    Tracer *saved = g_tracer;
-    g_tracer = nullptr;
+    // No context, so no tracing: the tracer pointer is thread-local, and it is
+    // cleared for this thread's launches only and put back on every return.
+    struct TracerOff {
+        Tracer *saved = g_tracer;
+        TracerOff() { g_tracer = nullptr; }
+        ~TracerOff() { g_tracer = saved; }
+    } tracer_off;
     int64_t launches = 0;
     cudaError_t e = cudaSuccess;
     if (dtype == DQ_C64) {
@@ -2359,7 +2379,6 @@ extern "C" dq_status dq_forward_grad_noalloc(const dq_circuit *circuit, const do
             e = wsv_launch<double>(p, coef, nullptr, 1, d_terms, (int)wterms.size(), nobs, row_weights, batch,
                                    nullptr, expect_out, grad_params, grad_data, part, nsm, s, &launches);
     }
-    g_tracer = saved;
     if (e != cudaSuccess) return noalloc_fail(err, err_len, DQ_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
     return DQ_OK;
 }

@@ -30,6 +30,23 @@ template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
 template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
 template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
 
+// Re(conj(l) p) and Im(conj(l) p) with each product rounded on its own (no
+// FMA contraction).  Sums of the form a*b - c*d then vanish exactly whenever
+// the two products are equal: the imaginary part of conj(p) p, or the
+// per-term cancellation of a generator's expectation when lambda is a real
+// multiple of psi element by element (a diagonal observable).  A contracted
+// fma(a, b, -(c*d)) would leave one product's rounding error behind in every
+// such term, which a gradient or expectation that is exactly zero does not
+// survive in single precision.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+template <typename C> __device__ __forceinline__ auto re_conj_mul(C l, C p) -> decltype(l.x) {
+    return mul_rn(l.x, p.x) + mul_rn(l.y, p.y);
+}
+template <typename C> __device__ __forceinline__ auto im_conj_mul(C l, C p) -> decltype(l.x) {
+    return mul_rn(l.x, p.y) - mul_rn(l.y, p.x);
+}
+
 // 2x2 block acting on the target qubit (applied on control = |1> for
 // controlled kinds).  m[0] m[1] / m[2] m[3] row-major.
 template <typename R> struct Mat2 { cx<R> m[4]; };
@@ -147,13 +164,13 @@ template <typename R>
 __device__ __forceinline__ R grad_pair(int kind, cx<R> l0, cx<R> l1, cx<R> p0, cx<R> p1) {
     switch (kind) {
     case DQ_RX: case DQ_CRX:   // Im(conj(l0) p1 + conj(l1) p0)
-        return (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
+        return im_conj_mul(l0, p1) + im_conj_mul(l1, p0);
     case DQ_RY: case DQ_CRY:   // Im(-i conj(l0) p1 + i conj(l1) p0) = -Re(conj(l0) p1) + Re(conj(l1) p0)
-        return -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
+        return re_conj_mul(l1, p0) - re_conj_mul(l0, p1);
     case DQ_RZ: case DQ_CRZ:   // Im(conj(l0) p0 - conj(l1) p1)
-        return (l0.x * p0.y - l0.y * p0.x) - (l1.x * p1.y - l1.y * p1.x);
+        return im_conj_mul(l0, p0) - im_conj_mul(l1, p1);
     case DQ_CP: case DQ_P:     // 2 Im(conj(l1) (-p1))
-        return (R)(-2) * (l1.x * p1.y - l1.y * p1.x);
+        return (R)(-2) * im_conj_mul(l1, p1);
     default:
         return (R)0;
     }

@@ -669,8 +669,8 @@ __device__ __forceinline__ int eng_fan(cx<R> (&a)[1 << M], const EOp *ops, const
 // REAL: RY/CRY (G = Y/2), GENERAL: RX/CRX (G = X/2).
 template <typename R, int CLS>
 __device__ __forceinline__ R grad_cls(cx<R> l0, cx<R> l1, cx<R> p0, cx<R> p1) {
-    if (CLS == CLS_REAL) return -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
-    if (CLS == CLS_GENERAL) return (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
+    if (CLS == CLS_REAL) return re_conj_mul(l1, p0) - re_conj_mul(l0, p1);
+    if (CLS == CLS_GENERAL) return im_conj_mul(l0, p1) + im_conj_mul(l1, p0);
     return R(0);
 }
 
@@ -726,7 +726,7 @@ __device__ __forceinline__ R adj_diag_at(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M
 #pragma unroll
     for (int e = 0; e < (1 << M); ++e) {
         const bool t = (e >> P) & 1;
-        if (GRAD) g += (t ? w1 : w0) * (ls[e].x * ps[e].y - ls[e].y * ps[e].x);
+        if (GRAD) g += (t ? w1 : w0) * im_conj_mul(ls[e], ps[e]);
         const cx<R> f = t ? ud.m[3] : ud.m[0];
         ps[e] = cmul(f, ps[e]);
         ls[e] = cmul(f, ls[e]);
@@ -743,7 +743,7 @@ __device__ __forceinline__ R adj_diag_sel(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << 
     for (int e = 0; e < (1 << M); ++e) {
         const bool c = (cm >> e) & 1;
         const bool t = (e >> P) & 1;
-        if (GRAD) g += c ? (t ? w1 : w0) * (ls[e].x * ps[e].y - ls[e].y * ps[e].x) : R(0);
+        if (GRAD) g += c ? (t ? w1 : w0) * im_conj_mul(ls[e], ps[e]) : R(0);
         const cx<R> f = t ? ud.m[3] : ud.m[0];
         ps[e] = sel(c, cmul(f, ps[e]), ps[e]);
         ls[e] = sel(c, cmul(f, ls[e]), ls[e]);
@@ -762,7 +762,7 @@ __device__ __forceinline__ R adj_diag_uni(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << 
 #pragma unroll
     for (int e = 0; e < (1 << M); ++e) {
         const bool c = (cm >> e) & 1;
-        if (GRAD) g += c ? w * (ls[e].x * ps[e].y - ls[e].y * ps[e].x) : R(0);
+        if (GRAD) g += c ? w * im_conj_mul(ls[e], ps[e]) : R(0);
         ps[e] = sel(c, cmul(f, ps[e]), ps[e]);
         ls[e] = sel(c, cmul(f, ls[e]), ls[e]);
     }
@@ -816,7 +816,7 @@ __device__ __forceinline__ R adj_pdiag(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M],
 #pragma unroll
     for (int e = 0; e < (1 << M); ++e) {
         const bool odd = (o.cmc >> e) & 1;
-        if (GRAD) g += (odd ? wo : we) * (ls[e].x * ps[e].y - ls[e].y * ps[e].x);
+        if (GRAD) g += (odd ? wo : we) * im_conj_mul(ls[e], ps[e]);
         const cx<R> f = odd ? fo : fe;
         ps[e] = cmul(f, ps[e]);
         ls[e] = cmul(f, ls[e]);
@@ -893,7 +893,7 @@ __device__ __forceinline__ void adj_pair_reg(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 
         if (e0 & (1 << P)) continue;
         const int e1 = e0 | (1 << P);
         cx<R> p0 = ps[e0], p1 = ps[e1], l0 = ls[e0], l1 = ls[e1];
-        if (GRAD) gd += w0 * (l0.x * p0.y - l0.y * p0.x) + w1 * (l1.x * p1.y - l1.y * p1.x);
+        if (GRAD) gd += w0 * im_conj_mul(l0, p0) + w1 * im_conj_mul(l1, p1);
         p0 = cmul(dd.m[0], p0);
         p1 = cmul(dd.m[3], p1);
         l0 = cmul(dd.m[0], l0);
@@ -922,7 +922,7 @@ __device__ __forceinline__ void adj_pair_lane(cx<R> (&ps)[1 << M], cx<R> (&ls)[1
 #pragma unroll
     for (int e = 0; e < (1 << M); ++e) {
         cx<R> p = ps[e], l = ls[e];
-        if (GRAD) gd += w * (l.x * p.y - l.y * p.x);
+        if (GRAD) gd += w * im_conj_mul(l, p);
         p = cmul(f, p);
         l = cmul(f, l);
         const cx<R> pp = shfl_xor_cx(p, m);

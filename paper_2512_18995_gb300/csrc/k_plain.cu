@@ -226,8 +226,8 @@ k_expect(const cx<R> *__restrict__ st, int n, uint64_t f, int lf, TermPack tp, i
         if (f) {
             b = insert0(b, lf);
             const cx<R> x = rp[b], y = rp[b ^ f];     // z = conj(psi_{b^f}) psi_b
-            re = y.x * x.x + y.y * x.y;
-            im = y.x * x.y - y.y * x.x;
+            re = re_conj_mul(y, x);
+            im = im_conj_mul(y, x);
         } else {
             const cx<R> x = rp[b];
             re = x.x * x.x + x.y * x.y;

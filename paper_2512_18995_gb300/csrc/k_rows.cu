@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(rows_max_threads<R, M>(), sizeof(R) == 4 ? 2 :
                 } else {
                     for (int64_t b = tid; b < dim; b += blockDim.x) {
                         const cx<R> x = bufP[b], y = bufP[b ^ f];
-                        const R re = y.x * x.x + y.y * x.y, im = y.x * x.y - y.y * x.x;
+                        const R re = re_conj_mul(y, x), im = im_conj_mul(y, x);
                         const int ph = (t.nY + 2 * parity64((uint64_t)b & sm)) & 3;
                         v += (ph == 0) ? re : (ph == 1 ? -im : (ph == 2 ? -re : im));
                     }

@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
                     const uint32_t src = (uint32_t)l ^ o.floc;
                     const cx<R> y = bufP[src];
                     const int k4 = (o.nY + 2 * ((__popc((uint32_t)l & o.sloc) & 1) ^ bpar)) & 3;
-                    const R re = y.x * x[i].x + y.y * x[i].y, im = y.x * x[i].y - y.y * x[i].x;
+                    const R re = re_conj_mul(y, x[i]), im = im_conj_mul(y, x[i]);
                     e += (k4 == 0) ? re : (k4 == 1 ? -im : (k4 == 2 ? -re : im));
                     const int k5 = (o.nY + 2 * ((__popc(src & o.sloc) & 1) ^ bpar)) & 3;
                     // lambda[l] += wc * i^k5 * y

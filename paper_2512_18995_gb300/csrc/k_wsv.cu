@@ -130,7 +130,7 @@ __device__ __forceinline__ R vec_term(const cx<R> *psi, int n, uint64_t f, uint6
         for (int64_t j = tid; j < items; j += nt) {
             const uint64_t b = insert0((uint64_t)j, lf);
             const cx<R> x = psi[b], y = psi[b ^ f];
-            const R re = y.x * x.x + y.y * x.y, im = y.x * x.y - y.y * x.x;
+            const R re = re_conj_mul(y, x), im = im_conj_mul(y, x);
             const int ph = (nY + 2 * parity64(b & s)) & 3;
             const R v = (ph == 0) ? re : (ph == 1 ? -im : (ph == 2 ? -re : im));
             acc += R(2) * v;

@@ -45,7 +45,7 @@ def test_c2_autotuned_graph_replay_matches_oracle():
             ctx.check()
             assert_amps(np_state(state), ref, torch.complex64, f"step {step}: state")
             assert_rel(expect.cpu().numpy(), e_ref, torch.complex64, f"step {step}: <sum Z>",
-                       floor=obs_scale(wl.observables))
+                       zero_scale=obs_scale(wl.observables))
     finally:
         ctx.set_graphs(False)
         ctx.close()

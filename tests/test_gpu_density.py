@@ -78,7 +78,7 @@ def test_density_matches_oracle(ctx, path, dtype, n, batch, depth):
     e, rho = ctx.density_forward(circ, dev(params), dq.Observables(obs), batch, dt, data=dev(data), want_rho=True)
     e_ref, rho_ref = oracle.density(n, gates, obs, params, data, batch=batch)
     assert_amps(rho.cpu().numpy().astype(np.complex128), rho_ref, dt, "rho")
-    assert_rel(e.cpu().numpy(), e_ref, dt, "expectations", floor=obs_scale(obs))
+    assert_rel(e.cpu().numpy(), e_ref, dt, "expectations", zero_scale=obs_scale(obs))
 
 
 def test_noiseless_density_equals_outer_product(ctx):
@@ -146,7 +146,7 @@ def test_density_gradients_match_finite_differences(ctx, dtype, n, batch, depth)
     e, g = ctx.density_grad(circ, dev(params), dq.Observables(obs), data=dev(data), row_weights=dev(w), dtype=dt)
     e_ref, _ = oracle.density(n, gates, obs, params, data, batch=batch)
     g_ref = fd_density_grad(n, gates, obs, params, data, w)
-    assert_rel(e.cpu().numpy(), e_ref, dt, "expectations", floor=obs_scale(obs))
+    assert_rel(e.cpu().numpy(), e_ref, dt, "expectations", zero_scale=obs_scale(obs))
     scale = float(np.abs(w).max(axis=1).sum()) * obs_scale(obs)
     err = np.max(np.abs(g.cpu().numpy() - g_ref)) / scale
     assert err <= (1e-4 if dt == torch.complex64 else 1e-8), f"gradient error {err:.3e} (relative to {scale:.3f})"

@@ -60,7 +60,7 @@ def hess_gates(n, depth, rng, nfeat):
     return gates, max(npar, 1)
 
 
-def hfloor(obs, w):
+def hscale(obs, w):
     return obs_scale(obs) * (float(np.abs(w).sum()) if w is not None else 1.0)
 
 
@@ -80,8 +80,8 @@ def test_hessian_matches_product_rule(ctx, path, dtype, n, batch, depth):
     H, g = ctx.hessian(circ, dev(params), dq.Observables(obs), data=dev(data), row_weights=dev(w), dtype=dt)
     Href = oracle.hessian(n, gates, obs, params, data, batch=batch, row_weights=w)
     _, gref, _ = oracle.adjoint(n, gates, obs, params, data, batch=batch, row_weights=w)
-    assert_rel(H.cpu().numpy(), Href, dt, "hessian", floor=hfloor(obs, w))
-    assert_rel(g.cpu().numpy(), gref, dt, "gradient", floor=hfloor(obs, w))
+    assert_rel(H.cpu().numpy(), Href, dt, "hessian", zero_scale=hscale(obs, w))
+    assert_rel(g.cpu().numpy(), gref, dt, "gradient", zero_scale=hscale(obs, w))
 
 
 def test_hessian_in_chunks(ctx):
@@ -99,8 +99,8 @@ def test_hessian_in_chunks(ctx):
     H2, _ = ctx.hessian(circ, dev(params), dq.Observables(obs), data=dev(data), dtype=torch.complex128,
                         max_bytes=1 << 16)
     Href = oracle.hessian(n, gates, obs, params, data, batch=batch)
-    assert_rel(H1.cpu().numpy(), Href, torch.complex128, "hessian", floor=obs_scale(obs) * batch)
-    assert_rel(H2.cpu().numpy(), Href, torch.complex128, "hessian (chunked)", floor=obs_scale(obs) * batch)
+    assert_rel(H1.cpu().numpy(), Href, torch.complex128, "hessian", zero_scale=obs_scale(obs) * batch)
+    assert_rel(H2.cpu().numpy(), Href, torch.complex128, "hessian (chunked)", zero_scale=obs_scale(obs) * batch)
 
 
 @pytest.mark.parametrize("dtype", sorted(DTYPES))
@@ -116,7 +116,7 @@ def test_hessian_qnn_u3(ctx, dtype):
     circ = dq.Circuit(n, gates, nparams=npar, nfeatures=nfeat)
     H, _ = ctx.hessian(circ, dev(params), dq.Observables(obs), data=dev(data), dtype=dt, want_grad=False)
     Href = oracle.hessian(n, gates, obs, params, data, batch=batch)
-    assert_rel(H.cpu().numpy(), Href, dt, "hessian", floor=float(batch * len(obs)))
+    assert_rel(H.cpu().numpy(), Href, dt, "hessian", zero_scale=float(batch * len(obs)))
 
 
 def test_hessian_without_trainable_occurrences(ctx):

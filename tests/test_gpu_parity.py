@@ -170,7 +170,7 @@ def test_expectations(ctx, path, dtype, n, batch):
     st = torch.as_tensor(psi, dtype=dt, device="cuda").contiguous()
     got = ctx.expect(n, dq.Observables(obs), st).cpu().numpy()
     ref = oracle.expect(n, np_state(st), obs)
-    assert_rel(got, ref, dt, "expectations", floor=obs_scale(obs))
+    assert_rel(got, ref, dt, "expectations", zero_scale=obs_scale(obs))
 
 
 # ---------------------------------------------------------------------------
@@ -201,15 +201,15 @@ def test_adjoint_gradients(ctx, path, dtype, ppr, n, batch):
     assert torch.equal(st, keep), "state must be preserved without the clobber flag"
     e_ref, gp_ref, gd_ref = oracle.adjoint(n, gates, obs, params, data, batch=batch, params_per_row=ppr,
                                            row_weights=w)
-    gfloor = float(np.abs(w).max(axis=1).sum()) * obs_scale(obs)
-    assert_rel(gp.cpu().numpy(), gp_ref, dt, "grad params", floor=gfloor)
-    assert_rel(gd.cpu().numpy(), gd_ref, dt, "grad data", floor=gfloor)
+    gscale = float(np.abs(w).max(axis=1).sum()) * obs_scale(obs)
+    assert_rel(gp.cpu().numpy(), gp_ref, dt, "grad params", zero_scale=gscale)
+    assert_rel(gd.cpu().numpy(), gd_ref, dt, "grad data", zero_scale=gscale)
     # the one-call path gives the same expectations and gradients
     e2, gp2, gd2, _ = ctx.forward_grad(circ, dev(params), dobs, batch, dt, data=dev(data), row_weights=dev(w),
                                        params_per_row=ppr)
-    assert_rel(e2.cpu().numpy(), e_ref, dt, "expectations (forward_grad)", floor=obs_scale(obs))
-    assert_rel(gp2.cpu().numpy(), gp_ref, dt, "grad params (forward_grad)", floor=gfloor)
-    assert_rel(gd2.cpu().numpy(), gd_ref, dt, "grad data (forward_grad)", floor=gfloor)
+    assert_rel(e2.cpu().numpy(), e_ref, dt, "expectations (forward_grad)", zero_scale=obs_scale(obs))
+    assert_rel(gp2.cpu().numpy(), gp_ref, dt, "grad params (forward_grad)", zero_scale=gscale)
+    assert_rel(gd2.cpu().numpy(), gd_ref, dt, "grad data (forward_grad)", zero_scale=gscale)
 
 
 def test_clobber_flag_uses_state(ctx):
@@ -271,7 +271,7 @@ def test_diagonal_observables_in_last_forward_pass(ctx, dtype, n, batch):
                                       want_grad=False)
         torch.cuda.synchronize()
         ctx.check()
-        assert_rel(e.cpu().numpy(), ref, dt, "expectations", floor=obs_scale(obs))
+        assert_rel(e.cpu().numpy(), ref, dt, "expectations", zero_scale=obs_scale(obs))
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
@@ -295,10 +295,10 @@ def test_gradient_free_prefix(ctx, path, n, batch):
         assert (gd is not None) == with_data
         torch.cuda.synchronize()
         scale = obs_scale(obs)
-        assert_rel(e.cpu().numpy(), exp_ref, torch.complex64, "expectation", floor=scale)
-        assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, "grad params", floor=scale * batch)
+        assert_rel(e.cpu().numpy(), exp_ref, torch.complex64, "expectation", zero_scale=scale)
+        assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, "grad params", zero_scale=scale * batch)
         if with_data:
-            assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, "grad data", floor=scale)
+            assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, "grad data", zero_scale=scale)
 
 
 # ---------------------------------------------------------------------------
@@ -357,11 +357,15 @@ def test_config_c4_uneven_batch(ctx, path):
     gp = gp.cpu().numpy()
     # sampled circuits: every 16th plus every 16-qubit one
     pick = sorted(set(range(0, 1024, 16)) | {i for i, c in enumerate(circs) if c[0] == 16})
+    # the expectations of the sampled circuits form one result vector; each
+    # circuit's gradient is judged on its own largest element
+    e_ref = []
     for i in pick:
         n, g, a = circs[i]
         er, gr, _ = oracle.adjoint(n, g, obs, a)
-        assert_rel(e[i], er[0], torch.complex64, f"circuit {i} expectation", floor=obs_scale(obs))
-        assert_rel(gp[offs[i]:offs[i + 1]], gr, torch.complex64, f"circuit {i} gradient", floor=obs_scale(obs))
+        e_ref.append(er[0, 0])
+        assert_rel(gp[offs[i]:offs[i + 1]], gr, torch.complex64, f"circuit {i} gradient", zero_scale=obs_scale(obs))
+    assert_rel(e[pick], e_ref, torch.complex64, "sampled circuits' expectations", zero_scale=obs_scale(obs))
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
@@ -428,6 +432,32 @@ def test_autograd_function(ctx, n, budget):
     assert_rel(e.detach().cpu().numpy(), e_ref, torch.complex64)
     assert_rel(params.grad.cpu().numpy(), gp_ref, torch.complex64)
     assert_rel(data.grad.cpu().numpy(), gd_ref, torch.complex64)
+
+
+@pytest.mark.parametrize("n", [10, 15])
+def test_autograd_backward_twice(ctx, n):
+    """retain_graph=True and a second backward: the kept forward states are
+    swept in place by the first backward, so the second must recompute and
+    give the same gradients (both against the oracle)."""
+    ctx.set_path(dq.PATH_AUTO)
+    rng = np.random.default_rng(100 + n)
+    batch = 4
+    gates = W.encode_layer(n) + W.hea_layers(n, 2)
+    npar = 4 * n
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=n)
+    obs = [W.obs_tfim_open(n, 0.5)]
+    params = torch.tensor(rng.uniform(0, 6, npar), device="cuda", requires_grad=True)
+    data = torch.tensor(rng.uniform(-3, 3, (batch, n)), device="cuda", requires_grad=True)
+    wts = torch.tensor(rng.normal(size=(batch, 1)), device="cuda")
+    e = dq.expectation(circ, params, dq.Observables(obs), data=data, context=ctx, memory_budget=1 << 40)
+    loss = (e * wts).sum()
+    _, gp_ref, gd_ref = oracle.adjoint(n, gates, obs, params.detach().cpu().numpy(), data.detach().cpu().numpy(),
+                                       batch=batch, row_weights=wts.cpu().numpy())
+    gscale = float(wts.abs().sum()) * obs_scale(obs)
+    for k in range(2):
+        gp, gd = torch.autograd.grad(loss, (params, data), retain_graph=True)
+        assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, f"backward {k}: grad params", zero_scale=gscale)
+        assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, f"backward {k}: grad data", zero_scale=gscale)
 
 
 # ---------------------------------------------------------------------------
@@ -556,10 +586,10 @@ def test_graph_replay_reads_current_values(ctx, n, batch, path):
             torch.cuda.synchronize()
             e_ref, gp_ref, gd_ref = oracle.adjoint(n, gates, [W.obs_tfim_open(n, 0.5)], params.cpu().numpy(),
                                                    data.cpu().numpy(), batch=batch)
-            assert_rel(e.cpu().numpy(), e_ref, torch.complex64, f"call {call} expectation", floor=obs_scale([W.obs_tfim_open(n, 0.5)]))
+            assert_rel(e.cpu().numpy(), e_ref, torch.complex64, f"call {call} expectation", zero_scale=obs_scale([W.obs_tfim_open(n, 0.5)]))
             fl = batch * obs_scale([W.obs_tfim_open(n, 0.5)])
-            assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, f"call {call} grad params", floor=fl)
-            assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, f"call {call} grad data", floor=fl)
+            assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, f"call {call} grad params", zero_scale=fl)
+            assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, f"call {call} grad data", zero_scale=fl)
     finally:
         ctx.set_graphs(False)
 
@@ -597,4 +627,4 @@ def test_tracing_inside_replayed_graphs(ctx):
     assert per_call > 0
     assert sum(c for c, _ in tr.values()) == 5 * per_call
     assert all(ms > 0 for _, ms in tr.values())
-    assert_rel(e.cpu().numpy(), ref, torch.complex64, "expectation", floor=obs_scale(obs))
+    assert_rel(e.cpu().numpy(), ref, torch.complex64, "expectation", zero_scale=obs_scale(obs))

@@ -104,6 +104,34 @@ def test_null_context_is_rejected(libdq):
     assert st == 1   # DQ_ERR_INVALID_ARG
 
 
+
+def test_noalloc_entry_point_checks_arguments_before_the_device(libdq):
+    """dq_forward_grad_noalloc validates every host argument before it
+    touches the device, so these rejections need no GPU."""
+    from paper_2512_18995_gb300 import _lib
+    err = ctypes.create_string_buffer(128)
+    c = _lib.Circuit(3, [W.Gate("ry", (0,), param=0), W.Gate("rx", (1,), data=0)], nparams=1, nfeatures=1)
+    obs = _lib.Observables([W.obs_z(0)])
+    fake = ctypes.c_void_p(0x1000)     # never dereferenced: the calls fail first
+
+    def call(circ=c, params=fake, data=fake, o=obs, batch=2, dtype=0):
+        return libdq.dq_forward_grad_noalloc(circ.ref() if circ is not None else None, params, 0, data,
+                                             o.ref() if o is not None else None, None, batch, dtype,
+                                             fake, None, None, None, err, 128)
+
+    assert call(circ=None) == 1 and b"circuit" in err.value
+    assert call(dtype=7) == 1 and b"dtype" in err.value
+    assert call(batch=-1) == 1
+    assert call(params=None) == 1 and b"params" in err.value
+    assert call(data=None) == 1 and b"data" in err.value
+    assert call(o=None) == 1 and b"observables" in err.value
+    bad = _lib.Observables([W.obs_z(0)])
+    bad.c.terms = ctypes.POINTER(_lib.dq_pauli_term)()        # NULL terms behind one term offset
+    assert call(o=bad) == 1 and b"terms is NULL" in err.value
+    wide = _lib.Observables([W.obs_z(5)])                     # a wire beyond the circuit
+    assert call(o=wide) == 1 and b"wire" in err.value
+    assert call(circ=_lib.Circuit(3, [W.Gate("h", (3,))])) == 1
+
 # ---------------------------------------------------------------------------
 # input generators
 # ---------------------------------------------------------------------------
