@@ -181,6 +181,37 @@ DQ_API const char *dq_last_error(const dq_ctx *ctx);
 /* Select the implementation (dq_path) used by later calls. */
 DQ_API dq_status dq_ctx_set_path(dq_ctx *ctx, int path);
 
+/* Context options (dq_ctx_set_option).
+ *
+ * DQ_OPT_MULTIPASS (default 1): on the fused path, run every forward tile
+ *   pass of a state whose rows together hold at most 32 MiB (it stays in L2
+ *   between passes) in one persistent launch, the passes separated by a grid
+ *   barrier whose wait is bounded like every other device-side wait; 0 runs
+ *   one launch per pass.  Results are identical either way.
+ * DQ_OPT_WAIT_LIMIT_US (default 2000000): the limit, in microseconds (1 ..
+ *   60000000), of every device-side bounded wait of the context's kernels (a
+ *   TMA copy's or a tensor-core product's completion barrier, the multi-pass
+ *   grid barrier).  A wait that runs out sets the context's device error
+ *   flag; the kernel then waits (with the same limit) for its own copies in
+ *   flight, frees what it holds and returns, and the next dq_ctx_check
+ *   returns DQ_ERR_TIMEOUT.  Setting it synchronises the device.
+ * DQ_OPT_DENSE_BLOCKS (default 2): on forward-only calls of the fused path
+ *   (dq_apply_circuit, dq_forward_grad without gradients) for complex64
+ *   states of more than 6 qubits, runs of at least 8 consecutive gates on the
+ *   six lowest-order qubits (wires nqubits-6 .. nqubits-1, angles shared by
+ *   all rows) are multiplied into one 64 x 64 unitary on the device (FP64
+ *   products of the bound gate blocks) and applied by the tensor-core kernel
+ *   of dq_apply_dense; gates on the other wires that commute with a run
+ *   (disjoint wires) move past it, the rest run as tile passes.  0: never;
+ *   1: whenever the circuit has such a run; 2: when dq_plan_autotune measured
+ *   the blocks faster for this circuit.  Gradient calls always run gate by
+ *   gate (the adjoint sweep needs every gate's generator). */
+enum dq_option { DQ_OPT_MULTIPASS = 1, DQ_OPT_WAIT_LIMIT_US = 2, DQ_OPT_DENSE_BLOCKS = 3 };
+
+/* Set a context option; DQ_ERR_INVALID_ARG for an unknown option or value.
+ * Captured graphs of the context are dropped (the next calls capture anew). */
+DQ_API dq_status dq_ctx_set_option(dq_ctx *ctx, int option, int64_t value);
+
 /* Attach caller-owned device memory of `bytes` bytes (16-byte aligned) as the
  * workspace; ptr == NULL detaches it.  The memory must stay valid while calls
  * that use it are in flight. */
@@ -202,6 +233,16 @@ DQ_API dq_status dq_batch_workspace_bytes(dq_ctx *ctx, int ncirc, const dq_circu
 /* Synchronise `stream` and report device-side failures recorded by earlier
  * calls (DQ_ERR_TIMEOUT for a bounded wait that gave up), then clear them. */
 DQ_API dq_status dq_ctx_check(dq_ctx *ctx, void *stream);
+
+/* Failure-detection self-test (no counterpart in the paper): launches on
+ * `stream` one kernel whose bounded wait runs out on purpose -- it waits on
+ * an mbarrier that nothing arrives on and that no copy targets, so nothing
+ * is in flight -- and records the timeout in the context's device error
+ * flag the way a kernel whose copy never landed would.  After it, with the
+ * wait limit lowered by DQ_OPT_WAIT_LIMIT_US to keep the test short,
+ * dq_ctx_check returns DQ_ERR_TIMEOUT and clears the flag; the context stays
+ * usable. */
+DQ_API dq_status dq_selftest_wait_expiry(dq_ctx *ctx, void *stream);
 
 /* Number of kernels this context has launched since creation (for launch
  * accounting by callers). */
@@ -261,6 +302,17 @@ DQ_API dq_status dq_expect(dq_ctx *ctx, int nqubits, const dq_observables *obs,
                     const void *state, int batch, int dtype, double *out,
                     void *stream);
 
+/* Squared norm <psi|psi> of every row of `state` (batch rows of 2^nqubits
+ * amplitudes, device) into out[batch] (device, FP64): |psi_i|^2 in the
+ * state's precision, summed in runs of eight in that precision and in FP64
+ * above that, the per-block partials of a row added in a fixed order.  With
+ * a normalised initial state this is the drift of the norm that rounding in
+ * the state's precision accumulated over the gates (the paper's evolution is
+ * unitary: Sec. "Quantum Computing with Qubits", Background).  Uses the
+ * context workspace; asynchronous on `stream`. */
+DQ_API dq_status dq_state_norm(dq_ctx *ctx, int nqubits, const void *state, int batch, int dtype,
+                               double *out, void *stream);
+
 /* Adjoint differentiation (Sec. "Distributed Simulations", adjoint method)
  * of L = sum_row sum_o w[row, o] <psi_row| O_o |psi_row>, where state holds
  * the final states psi_row produced by dq_apply_circuit with the same
@@ -308,6 +360,22 @@ DQ_API dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit 
                                 const dq_observables *obs, int dtype,
                                 double *expect_out, double *grad_params,
                                 void *stream);
+
+/* Autotuner of the uneven-batch launch (the benchmark spec's batched encoded-input
+ * circuits of uneven qubit counts and depths; the API Overview batches
+ * encode=True circuits).  Runs dq_batch_forward_grad with every candidate
+ * launch configuration -- the largest qubit count kept in shared memory
+ * (10, 11, 12; larger circuits work in per-CTA L2 scratch), threads per
+ * circuit (128, 256, 512), CTAs per SM (2, 4, 8) -- on the caller's own
+ * inputs, keeps the fastest for this batch structure and dtype (later
+ * dq_batch_forward_grad calls of the same structure use it), and leaves the
+ * outputs as that configuration computes them.  choice (host, may be NULL)
+ * receives {qubits in shared memory, threads, CTAs per SM}.  Synchronises
+ * the stream; arguments as dq_batch_forward_grad. */
+DQ_API dq_status dq_batch_autotune(dq_ctx *ctx, int ncirc, const dq_circuit *circuits,
+                                   const double *params, const int64_t *param_offsets,
+                                   const dq_observables *obs, int dtype, double *expect_out,
+                                   double *grad_params, int *choice, void *stream);
 
 /* Allocation-free variant of dq_forward_grad, for callers that must not
  * allocate device memory at call time -- for example a serving loop that

@@ -22,6 +22,7 @@ STATUS = {0: "DQ_OK", 1: "DQ_ERR_INVALID_ARG", 2: "DQ_ERR_UNSUPPORTED", 3: "DQ_E
           4: "DQ_ERR_CUDA", 5: "DQ_ERR_TIMEOUT"}
 DQ_C64, DQ_C128 = 0, 1
 PATH_AUTO, PATH_PLAIN, PATH_FUSED = 0, 1, 2
+OPT_MULTIPASS, OPT_WAIT_LIMIT_US, OPT_DENSE_BLOCKS = 1, 2, 3
 ADJ_CLOBBER_STATE = 1
 
 KIND = {k: i for i, k in enumerate(
@@ -67,7 +68,9 @@ class dq_lowered_op(ctypes.Structure):
                 ("block", ctypes.c_double * 8)]
 
 
-EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path", "dq_ctx_set_workspace",
+EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path", "dq_ctx_set_option",
+           "dq_state_norm", "dq_selftest_wait_expiry", "dq_batch_autotune",
+           "dq_ctx_set_workspace",
            "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_graphs", "dq_ctx_set_tracing",
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
            "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
@@ -96,6 +99,11 @@ def load_library(path: str = LIB_PATH):
         "dq_ctx_destroy": ([P], I),
         "dq_last_error": ([P], ctypes.c_char_p),
         "dq_ctx_set_path": ([P, I], I),
+        "dq_ctx_set_option": ([P, I, ctypes.c_int64], I),
+        "dq_state_norm": ([P, I, P, I, I, P, P], I),
+        "dq_batch_autotune": ([P, I, C, P, ctypes.POINTER(ctypes.c_int64), O, I, P, P,
+                               ctypes.POINTER(ctypes.c_int), P], I),
+        "dq_selftest_wait_expiry": ([P, P], I),
         "dq_ctx_set_workspace": ([P, P, ctypes.c_size_t], I),
         "dq_workspace_bytes": ([P, C, O, I, I, ctypes.POINTER(ctypes.c_size_t)], I),
         "dq_batch_workspace_bytes": ([P, I, C, I, ctypes.POINTER(ctypes.c_size_t)], I),
@@ -404,6 +412,25 @@ class Context:
         self._check(self.lib.dq_ctx_set_path(self.h, int(path)), "dq_ctx_set_path")
         self.path = int(path)
 
+    def set_option(self, option: int, value: int):
+        """dq_ctx_set_option (OPT_MULTIPASS, OPT_WAIT_LIMIT_US, OPT_DENSE_BLOCKS)."""
+        self._check(self.lib.dq_ctx_set_option(self.h, int(option), int(value)), "dq_ctx_set_option")
+
+    def selftest_wait_expiry(self):
+        """dq_selftest_wait_expiry: one bounded wait runs out on purpose; the
+        next check() raises DQError(DQ_ERR_TIMEOUT)."""
+        self._check(self.lib.dq_selftest_wait_expiry(self.h, _stream()), "dq_selftest_wait_expiry")
+
+    def state_norm(self, state: torch.Tensor, nqubits: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """<psi|psi> of every row (FP64 accumulation), shape (batch,)."""
+        batch = _state_rows(state, nqubits, "state", self.device)
+        out = _out(out, batch, torch.float64, "out", self.device)
+        if out is None:
+            out = torch.empty(batch, dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(self.lib.dq_state_norm(self.h, int(nqubits), _ptr(state), int(batch), dtype_code(state.dtype),
+                                           _ptr(out), _stream()), "dq_state_norm")
+        return out
+
     @property
     def launch_count(self) -> int:
         return int(self.lib.dq_ctx_launch_count(self.h))
@@ -656,9 +683,18 @@ class Context:
                                              _ptr(state_out), _stream()), "dq_forward_grad")
         return expect_out, grad_params, grad_data, state_out
 
+    def batch_autotune(self, circuits: Sequence[Circuit], params: torch.Tensor, obs: Observables,
+                       dtype: torch.dtype = torch.complex64):
+        """dq_batch_autotune: tune the uneven-batch launch for this batch;
+        returns (qubits in shared memory, threads per circuit, CTAs per SM)."""
+        choice = (ctypes.c_int * 3)()
+        self.batch_forward_grad(circuits, params, obs, dtype, _tune_choice=choice)
+        return tuple(int(x) for x in choice)
+
     def batch_forward_grad(self, circuits: Sequence[Circuit], params: torch.Tensor, obs: Observables,
                            dtype: torch.dtype = torch.complex64, want_grad: bool = True,
-                           expect_out: Optional[torch.Tensor] = None, grad_params: Optional[torch.Tensor] = None):
+                           expect_out: Optional[torch.Tensor] = None, grad_params: Optional[torch.Tensor] = None,
+                           _tune_choice=None):
         nc = len(circuits)
         arr = (dq_circuit * max(1, nc))()
         offs = (ctypes.c_int64 * (nc + 1))()
@@ -681,10 +717,16 @@ class Context:
                                                       dtype_code(dtype), ctypes.byref(need)),
                     "dq_batch_workspace_bytes")
         self.ensure_workspace(None, None, 0, dtype_code(dtype), need_bytes=need.value)
-        self._check(self.lib.dq_batch_forward_grad(self.h, nc, ctypes.cast(arr, ctypes.POINTER(dq_circuit)),
+        if _tune_choice is not None:
+            self._check(self.lib.dq_batch_autotune(self.h, nc, ctypes.cast(arr, ctypes.POINTER(dq_circuit)),
                                                    _ptr(params), offs, obs.ref(), dtype_code(dtype),
-                                                   _ptr(expect_out), _ptr(grad_params), _stream()),
-                    "dq_batch_forward_grad")
+                                                   _ptr(expect_out), _ptr(grad_params), _tune_choice, _stream()),
+                        "dq_batch_autotune")
+        else:
+            self._check(self.lib.dq_batch_forward_grad(self.h, nc, ctypes.cast(arr, ctypes.POINTER(dq_circuit)),
+                                                       _ptr(params), offs, obs.ref(), dtype_code(dtype),
+                                                       _ptr(expect_out), _ptr(grad_params), _stream()),
+                        "dq_batch_forward_grad")
         return expect_out, grad_params
 
     def plan_tuned(self, circuit: Circuit, dtype: torch.dtype = torch.complex64):

@@ -48,6 +48,8 @@ struct ObsDev {
 
 struct BatchDev {
     int ncirc = 0, nmax = 0, maxparams = 0, ngates = 0;
+    BatchTune tune[2];          // autotuned launch choices (complex64, complex128)
+    bool tuned[2] = {false, false};
     BatchCirc *d_circ = nullptr;
     int32_t *d_order = nullptr;
     DevGate *d_gates = nullptr;
@@ -89,6 +91,24 @@ void Plan::release() {
     d_pslot_ptr = d_pslots = d_dslot_ptr = d_dslots = nullptr;
 }
 
+// Forward segmentation of a circuit for the dense-block path: tile segments
+// (each its own plan over a subset of the gates, scheduled into tile passes)
+// alternating with runs of gates on the six lowest-order bits, each applied
+// as one 64 x 64 tensor-core block.
+struct DensePlan {
+    std::vector<int> seg_dense;                 // per segment: 1 dense run, 0 tile segment
+    std::vector<std::unique_ptr<Plan>> sub;     // tile segments' plans (null for dense runs)
+    std::vector<DevGate *> d_run;               // dense runs' gates on the device (null for tile segments)
+    std::vector<int> run_len;
+    int nruns = 0;
+    void release() {
+        for (auto &q : sub)
+            if (q) q->release();
+        for (DevGate *d : d_run) cudaFree(d);
+        d_run.clear();
+    }
+};
+
 struct dq_ctx {
     int device = 0;
     int nsm = 0;
@@ -108,6 +128,8 @@ struct dq_ctx {
     Tracer tracer;
     std::vector<std::pair<std::string, std::pair<int64_t, double>>> trace_table;
     std::unordered_map<uint64_t, std::unique_ptr<RowProgram>> rowprogs;
+    std::unordered_map<uint64_t, std::unique_ptr<DensePlan>> dense_plans;
+    int dense_mode = 2;   // DQ_OPT_DENSE_BLOCKS
     // CUDA-graph replay of repeated calls
     bool graphs_on = false;
     cudaStream_t cap_stream = nullptr;
@@ -807,6 +829,147 @@ uint64_t mix_ptrs(uint64_t h, std::initializer_list<const void *> ptrs) {
     return h;
 }
 
+// ---- dense blocks chosen by the planner -------------------------------------
+
+bool dense_eligible(const DevGate &g) {
+    if (g.rowstep != 0 || g.t < 0) return false;   // one block for every row: shared angles only
+    return g.t < kDenseBits && g.c < kDenseBits;
+}
+bool touches_low_bits(const DevGate &g) {
+    return (g.t >= 0 && g.t < kDenseBits) || (g.c >= 0 && g.c < kDenseBits);
+}
+
+// Segments of the forward circuit: runs of at least kDenseMinRun gates on
+// bits 0..5 become dense blocks.  A gate on high bits only commutes with the
+// run (disjoint bits), so it is moved past it into the next tile segment; a
+// gate that touches a low bit but cannot join the run (it also acts on a
+// high bit, or its angle depends on the row) ends the run.  The resulting
+// order is an exact reordering of the circuit.
+dq_status get_dense_plan(dq_ctx *ctx, const Plan &p, DensePlan **out) {
+    *out = nullptr;
+    auto it = ctx->dense_plans.find(p.key);
+    if (it != ctx->dense_plans.end()) {
+        *out = it->second.get();
+        return DQ_OK;
+    }
+    std::vector<std::pair<int, std::vector<int>>> segs;
+    std::vector<int> normal, run, deferred;
+    auto flush = [&]() {
+        if ((int)run.size() >= kDenseMinRun) {
+            if (!normal.empty()) segs.push_back({0, normal});
+            segs.push_back({1, run});
+            normal = deferred;
+        } else {
+            std::vector<int> merged = run;
+            merged.insert(merged.end(), deferred.begin(), deferred.end());
+            std::sort(merged.begin(), merged.end());
+            normal.insert(normal.end(), merged.begin(), merged.end());
+        }
+        run.clear();
+        deferred.clear();
+    };
+    for (int i = 0; i < p.ngates; ++i) {
+        const DevGate &g = p.gates[i];
+        if (dense_eligible(g)) {
+            run.push_back(i);
+        } else if (!run.empty() && !touches_low_bits(g)) {
+            deferred.push_back(i);
+        } else {
+            flush();
+            normal.push_back(i);
+        }
+    }
+    flush();
+    if (!normal.empty()) segs.push_back({0, normal});
+    std::unique_ptr<DensePlan> dp(new DensePlan());
+    dq_status st;
+    for (size_t k = 0; k < segs.size(); ++k) {
+        const std::vector<int> &idx = segs[k].second;
+        std::vector<DevGate> gs;
+        for (int i : idx) gs.push_back(p.gates[i]);
+        dp->seg_dense.push_back(segs[k].first);
+        if (segs[k].first) {
+            DevGate *d = nullptr;
+            if ((st = upload(ctx, &d, gs.data(), gs.size())) != DQ_OK) {
+                dp->release();
+                return st;
+            }
+            dp->d_run.push_back(d);
+            dp->run_len.push_back((int)gs.size());
+            dp->sub.emplace_back(nullptr);
+            ++dp->nruns;
+        } else {
+            std::unique_ptr<Plan> q(new Plan());
+            q->key = (p.key * 1099511628211ull) ^ (0xD3A5E00000000000ull + k);
+            q->n = p.n;
+            q->nparams = p.nparams;
+            q->nfeat = p.nfeat;
+            q->ppr = p.ppr;
+            q->ncoef_shared = p.ncoef_shared;
+            q->ncoef_rows = p.ncoef_rows;
+            q->gates = gs;
+            q->ngates = (int)gs.size();
+            q->slot_of_gate.assign(gs.size(), -1);
+            if ((st = upload(ctx, &q->d_gates, gs.data(), gs.size())) != DQ_OK) {
+                dp->release();
+                return st;
+            }
+            dp->sub.push_back(std::move(q));
+            dp->d_run.push_back(nullptr);
+            dp->run_len.push_back(0);
+        }
+    }
+    *out = dp.get();
+    ctx->dense_plans.emplace(p.key, std::move(dp));
+    return DQ_OK;
+}
+
+// Whether this forward call runs dense blocks: complex64 tile path, a
+// circuit with at least one dense run, and DQ_OPT_DENSE_BLOCKS on (1) or on
+// automatic (2) with the autotuner having measured the blocks faster.
+bool dense_wanted(dq_ctx *ctx, const Plan &p, int amp, int batch, DensePlan **dp) {
+    *dp = nullptr;
+    if (amp != 8 || ctx->dense_mode == 0 || p.n <= kDenseBits || !dense_supported(p.n, batch)) return false;
+    if (ctx->dense_mode == 2) {
+        auto it = ctx->tuned.find(p.key);
+        if (it == ctx->tuned.end() || it->second.dense != 1) return false;
+    }
+    if (get_dense_plan(ctx, p, dp) != DQ_OK) {
+        cudaGetLastError();
+        return false;
+    }
+    return (*dp)->nruns > 0;
+}
+
+constexpr size_t kDenseUnitaryBytes = 64 * 64 * 16;
+
+// Forward evolution through the segments; ubuf holds one composed unitary,
+// image its tensor-core operand image.
+template <typename R>
+cudaError_t dense_forward(dq_ctx *ctx, const Plan &p, DensePlan &dp, const void *coef, void *state, int batch,
+                          void *tws, void *ubuf, void *image, cudaStream_t s) {
+    auto tuned = ctx->tuned.find(p.key ^ (sizeof(R) == 8 ? 1ull : 0ull));
+    for (size_t k = 0; k < dp.seg_dense.size(); ++k) {
+        cudaError_t e;
+        if (dp.seg_dense[k]) {
+            e = dense_compose<R>(dp.d_run[k], dp.run_len[k], coef, ubuf, s, &ctx->launches);
+            if (e == cudaSuccess) e = dense_prepare(ubuf, kDenseBits, image, s, &ctx->launches);
+            if (e == cudaSuccess) e = dense_apply(ctx->tiles, image, state, p.n, batch, ctx->nsm, s, &ctx->launches);
+        } else {
+            const Plan &q = *dp.sub[k];
+            // tile segments run with the circuit's tuned tile shape
+            if (tuned != ctx->tuned.end()) ctx->tuned[q.key ^ (sizeof(R) == 8 ? 1ull : 0ull)] = tuned->second;
+            e = tile_apply<R>(ctx->tiles, ctx->tuned, q, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+            if (e == cudaErrorNotSupported) {
+                cudaGetLastError();
+                e = plain_apply<R>(q, coef, state, batch, 0, s, &ctx->launches);
+            }
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // ---- templated bodies ------------------------------------------------------
 
 template <typename R>
@@ -815,10 +978,16 @@ dq_status apply_impl(dq_ctx *ctx, Plan &p, const double *params, const double *d
     RowProgram *rp = use_fused(ctx) ? get_rows(ctx, p, (int)sizeof(cx<R>), false, 1) : nullptr;
     const bool small = rp || (use_fused(ctx) && wsv_supported(p.n, (int)sizeof(cx<R>), false, ctx->smem_optin, wsv_doubles(p, 1)));
     const bool tile = use_fused(ctx) && !small && tile_supported(p.n, (int)sizeof(cx<R>));
+    DensePlan *dp = nullptr;
+    const bool dense = tile && dense_wanted(ctx, p, (int)sizeof(cx<R>), batch, &dp);
     Arena a;
     a.measuring = true;
     a.take(coef_bytes(p, batch, sizeof(R) == 8 ? DQ_C128 : DQ_C64));
     if (tile) a.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>)));
+    if (dense) {
+        a.take(kDenseUnitaryBytes);
+        a.take(dense_image_bytes());
+    }
     dq_status st = reserve(ctx, a.used);
     if (st != DQ_OK) return st;
     Arena w;
@@ -836,7 +1005,14 @@ dq_status apply_impl(dq_ctx *ctx, Plan &p, const double *params, const double *d
                 "fused apply");
     } else if (tile) {
         void *tws = w.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>)));
-        cudaError_t e = tile_apply<R>(ctx->tiles, ctx->tuned, p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+        cudaError_t e;
+        if (dense) {
+            void *ubuf = w.take(kDenseUnitaryBytes);
+            void *image = w.take(dense_image_bytes());
+            e = dense_forward<R>(ctx, p, *dp, coef, state, batch, tws, ubuf, image, s);
+        } else {
+            e = tile_apply<R>(ctx->tiles, ctx->tuned, p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+        }
         if (e == cudaErrorNotSupported) {   // no schedule for this shape: per-gate sweeps
             cudaGetLastError();
             e = plain_apply<R>(p, coef, state, batch, 0, s, &ctx->launches);
@@ -1009,6 +1185,13 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     if (o) a.take(std::max(plain_expect_part_bytes(p.n, (int)o->bits.size(), batch),
                            tile_expect_part_bytes(p.n, (int)o->bits.size(), batch, ctx->nsm)));
     if (tile) a.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>)));
+    // dense blocks on forward-only calls (the reverse sweep runs gate by gate)
+    DensePlan *dp = nullptr;
+    const bool dense = tile && !grad && dense_wanted(ctx, p, (int)sizeof(cx<R>), batch, &dp);
+    if (dense) {
+        a.take(kDenseUnitaryBytes);
+        a.take(dense_image_bytes());
+    }
     dq_status st = reserve(ctx, a.used);
     if (st != DQ_OK) return st;
     Arena w;
@@ -1027,10 +1210,12 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     if (o) epart = (double *)w.take(std::max(plain_expect_part_bytes(p.n, (int)o->bits.size(), batch),
                                              tile_expect_part_bytes(p.n, (int)o->bits.size(), batch, ctx->nsm)));
     void *tws = tile ? w.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>))) : nullptr;
+    void *ubuf = dense ? w.take(kDenseUnitaryBytes) : nullptr;
+    void *image = dense ? w.take(dense_image_bytes()) : nullptr;
     DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
     DQ_CUDA(plain_init_zero<R>(psi, p.n, batch, s, &ctx->launches), "init");
     bool done_obs = false, done_grad = false;
-    if (tile && o && eo && !grad) {
+    if (tile && o && eo && !grad && !dense) {
         // diagonal observables measured by the last forward pass itself
         cudaError_t e = tile_apply_expect<R>(ctx->tiles, ctx->tuned, p, coef, psi, batch, o->bits, o->d_bits,
                                              o->d_ptr, o->nobs, epart, eo, ctx->nsm, s, &ctx->launches);
@@ -1040,6 +1225,8 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     }
     if (done_obs) {
         // evolution and expectations done
+    } else if (dense) {
+        DQ_CUDA(dense_forward<R>(ctx, p, *dp, coef, psi, batch, tws, ubuf, image, s), "dense-block apply");
     } else if (tile) {
         cudaError_t e = tile_apply<R>(ctx->tiles, ctx->tuned, p, coef, psi, batch, tws, ctx->nsm, s, &ctx->launches);
         if (e == cudaErrorNotSupported) {   // no schedule for this shape: per-gate sweeps
@@ -1108,7 +1295,12 @@ dq_status dq_ctx_create(dq_ctx **out, int device) {
     c->smem_optin = prop.sharedMemPerBlockOptin;
     if (cudaMalloc((void **)&c->d_flag, 256) != cudaSuccess) return DQ_ERR_OOM;
     if (cudaMemset(c->d_flag, 0, 256) != cudaSuccess) return DQ_ERR_CUDA;
+    const unsigned long long lim = kDefaultWaitNs;
+    if (cudaMemcpy(reinterpret_cast<char *>(c->d_flag) + kFlagWaitLimitOffset, &lim, sizeof(lim),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return DQ_ERR_CUDA;
     c->tiles.errflag = c->d_flag;
+    c->tiles.gridbar = reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(c->d_flag) + kFlagGridBarOffset);
     *out = c.release();
     return DQ_OK;
 }
@@ -1121,6 +1313,7 @@ dq_status dq_ctx_destroy(dq_ctx *ctx) {
     for (auto &kv : ctx->obs) kv.second->release();
     for (auto &kv : ctx->batches) kv.second->release();
     for (auto &kv : ctx->rowprogs) kv.second->release();
+    for (auto &kv : ctx->dense_plans) kv.second->release();
     ctx->clear_graphs();
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     ctx->tiles.release();
@@ -1141,6 +1334,36 @@ dq_status dq_ctx_set_path(dq_ctx *ctx, int path) {
     if (path != DQ_PATH_AUTO && path != DQ_PATH_PLAIN && path != DQ_PATH_FUSED)
         return fail(ctx, DQ_ERR_INVALID_ARG, "unknown path %d", path);
     ctx->path = path;
+    return DQ_OK;
+}
+
+dq_status dq_ctx_set_option(dq_ctx *ctx, int option, int64_t value) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    switch (option) {
+    case DQ_OPT_MULTIPASS:
+        if (value != 0 && value != 1) return fail(ctx, DQ_ERR_INVALID_ARG, "DQ_OPT_MULTIPASS takes 0 or 1");
+        ctx->tiles.multi_on = value != 0;
+        break;
+    case DQ_OPT_DENSE_BLOCKS:
+        if (value < 0 || value > 2) return fail(ctx, DQ_ERR_INVALID_ARG, "DQ_OPT_DENSE_BLOCKS takes 0, 1 or 2");
+        ctx->dense_mode = (int)value;
+        break;
+    case DQ_OPT_WAIT_LIMIT_US: {
+        if (value < 1 || value > 60000000)
+            return fail(ctx, DQ_ERR_INVALID_ARG, "DQ_OPT_WAIT_LIMIT_US takes 1 .. 60000000");
+        const unsigned long long ns = (unsigned long long)value * 1000ull;
+        // ordered after every launch already issued on any stream of the context's device
+        DQ_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+        DQ_CUDA(cudaMemcpy(reinterpret_cast<char *>(ctx->d_flag) + kFlagWaitLimitOffset, &ns, sizeof(ns),
+                           cudaMemcpyHostToDevice),
+                "set the wait limit");
+        break;
+    }
+    default:
+        return fail(ctx, DQ_ERR_INVALID_ARG, "unknown option %d", option);
+    }
+    ctx->clear_graphs();
     return DQ_OK;
 }
 
@@ -1225,8 +1448,37 @@ dq_status dq_ctx_check(dq_ctx *ctx, void *stream) {
     if (flag != DEVERR_NONE) {
         cudaMemset(ctx->d_flag, 0, sizeof(int));
         if (flag == DEVERR_TIMEOUT) return fail(ctx, DQ_ERR_TIMEOUT, "a device-side bounded wait gave up");
+        if (flag == DEVERR_BOUNDS)
+            return fail(ctx, DQ_ERR_CUDA, "a device-side bounds check found an index outside its buffer");
         return fail(ctx, DQ_ERR_CUDA, "device-side check failed (code %d)", flag);
     }
+    return DQ_OK;
+}
+
+dq_status dq_selftest_wait_expiry(dq_ctx *ctx, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    DQ_CUDA(selftest_wait_expiry(ctx->d_flag, (cudaStream_t)stream, &ctx->launches), "k_wait_expiry");
+    return DQ_OK;
+}
+
+dq_status dq_state_norm(dq_ctx *ctx, int nqubits, const void *state, int batch, int dtype, double *out,
+                        void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (nqubits < 0 || nqubits > 34) return fail(ctx, DQ_ERR_INVALID_ARG, "nqubits %d outside 0..34", nqubits);
+    if (batch < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "batch < 0");
+    if (batch == 0) return DQ_OK;
+    if (!state || !out) return fail(ctx, DQ_ERR_INVALID_ARG, "state or out is NULL");
+    if (!aligned16(state)) return fail(ctx, DQ_ERR_INVALID_ARG, "state is not 16-byte aligned");
+    if ((st = reserve(ctx, norm_part_bytes(nqubits, batch))) != DQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *part = reinterpret_cast<double *>(ctx->ws);
+    if (dtype == DQ_C64)
+        DQ_CUDA(state_norm<float>(state, nqubits, batch, part, out, s, &ctx->launches), "norm");
+    else
+        DQ_CUDA(state_norm<double>(state, nqubits, batch, part, out, s, &ctx->launches), "norm");
     return DQ_OK;
 }
 
@@ -1853,14 +2105,16 @@ dq_status dq_forward_grad(dq_ctx *ctx, const dq_circuit *circuit, const double *
     return body(s);
 }
 
-dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit *circuits, const double *params,
-                                const int64_t *param_offsets, const dq_observables *obs, int dtype,
-                                double *expect_out, double *grad_params, void *stream) {
-    dq_status st = check_ctx(ctx);
-    if (st != DQ_OK) return st;
-    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
-    if (ncirc < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "ncirc < 0");
-    if (ncirc == 0) return DQ_OK;
+}  // extern "C"
+
+namespace {
+
+// Validation of an uneven batch and the hash of its structure (circuits,
+// parameter spans).
+dq_status batch_check(dq_ctx *ctx, int ncirc, const dq_circuit *circuits, const double *params,
+                      const int64_t *param_offsets, const dq_observables *obs, const double *expect_out,
+                      uint64_t *hash, ObsDev **o) {
+    dq_status st;
     if (!circuits || !param_offsets) return fail(ctx, DQ_ERR_INVALID_ARG, "circuits/param_offsets is NULL");
     if (!expect_out) return fail(ctx, DQ_ERR_INVALID_ARG, "expect_out is NULL");
     int nmin = 64;
@@ -1878,12 +2132,122 @@ dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit *circui
             h = fnv(circuits[c].gates, sizeof(dq_gate) * circuits[c].ngates, h);
     }
     h = fnv(param_offsets, sizeof(int64_t) * (ncirc + 1), h);
-    ObsDev *o = nullptr;
-    if ((st = get_obs(ctx, obs, nmin, &o)) != DQ_OK) return st;
+    if ((st = get_obs(ctx, obs, nmin, o)) != DQ_OK) return st;
     if (param_offsets[0] != 0) return fail(ctx, DQ_ERR_INVALID_ARG, "param_offsets[0] must be 0");
     const int64_t ptotal = param_offsets[ncirc];
     if (ptotal > 0 && !params) return fail(ctx, DQ_ERR_INVALID_ARG, "params is NULL");
     if (ptotal >= (int64_t(1) << 31)) return fail(ctx, DQ_ERR_INVALID_ARG, "too many parameters");
+    *hash = h;
+    return DQ_OK;
+}
+
+// The batch's device tables (gates, bind records, circuit records ordered by
+// cost, largest first), cached per structure hash.
+dq_status batch_tables(dq_ctx *ctx, uint64_t h, int ncirc, const dq_circuit *circuits, const int64_t *param_offsets,
+                       BatchDev **out) {
+    auto it = ctx->batches.find(h);
+    if (it != ctx->batches.end()) {
+        *out = it->second.get();
+        return DQ_OK;
+    }
+    dq_status st;
+    std::unique_ptr<BatchDev> b(new BatchDev());
+    std::vector<DevGate> allg;
+    std::vector<BindGate> allbind;
+    std::vector<BatchCirc> bc(ncirc);
+    std::vector<std::pair<double, int>> cost(ncirc);
+    int nmax = 0, maxp = 0, ncoef = 0;
+    for (int c = 0; c < ncirc; ++c) {
+        BatchCirc x{};
+        x.n = circuits[c].nqubits;
+        x.gate0 = (int)allg.size();
+        x.param0 = (int)param_offsets[c];
+        x.nparams = circuits[c].nparams;
+        int ncr = 0;
+        st = compile_gates(ctx, &circuits[c], 0, allg, allbind, (int)param_offsets[c], &ncoef, &ncr, true);
+        if (st != DQ_OK) return fail(ctx, st, "circuit %d: %s", c, ctx->err.c_str());
+        x.ngates = (int)allg.size() - x.gate0;
+        bc[c] = x;
+        nmax = std::max(nmax, x.n);
+        maxp = std::max(maxp, x.nparams);
+        cost[c] = {std::ldexp((double)std::max(1, x.ngates), x.n), c};
+    }
+    if (nmax > 20) return fail(ctx, DQ_ERR_UNSUPPORTED, "uneven batches support up to 20 qubits per circuit");
+    std::stable_sort(cost.begin(), cost.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+        return a.first > b.first;
+    });
+    std::vector<int32_t> order(ncirc);
+    for (int i = 0; i < ncirc; ++i) order[i] = cost[i].second;
+    b->ncirc = ncirc;
+    b->nmax = nmax;
+    b->maxparams = maxp;
+    b->ngates = (int)allg.size();
+    if ((st = upload(ctx, &b->d_circ, bc.data(), bc.size())) != DQ_OK) return st;
+    if ((st = upload(ctx, &b->d_order, order.data(), order.size())) != DQ_OK) return st;
+    if ((st = upload(ctx, &b->d_gates, allg.empty() ? nullptr : allg.data(), allg.size())) != DQ_OK) return st;
+    if ((st = upload(ctx, &b->d_bind, allbind.empty() ? nullptr : allbind.data(), allbind.size())) != DQ_OK)
+        return st;
+    *out = b.get();
+    ctx->batches.emplace(h, std::move(b));
+    return DQ_OK;
+}
+
+// Bind every gate angle, then the persistent kernel with launch choices `t`.
+dq_status batch_launch(dq_ctx *ctx, BatchDev *bd, ObsDev *o, const double *params, int64_t ptotal, int dtype,
+                       double *expect_out, double *grad_params, const BatchTune &t, cudaStream_t s) {
+    const int ab = amp_bytes(dtype);
+    const size_t mat = dtype == DQ_C128 ? sizeof(Mat2<double>) : sizeof(Mat2<float>);
+    Arena a;
+    a.measuring = true;
+    a.take(mat * (size_t)(bd->ngates + 1));
+    a.take(batch_scratch_bytes(bd->nmax, ab, ctx->nsm, ctx->smem_optin));
+    a.take(256);
+    dq_status st;
+    if ((st = reserve(ctx, a.used)) != DQ_OK) return st;
+    Arena w;
+    w.base = ctx->ws;
+    w.cap = ctx->ws_bytes;
+    void *coef = w.take(mat * (size_t)(bd->ngates + 1));
+    void *scratch = w.take(batch_scratch_bytes(bd->nmax, ab, ctx->nsm, ctx->smem_optin));
+    int *counter = (int *)w.take(256);
+    // bind all gate angles (global parameter indices, shared rows)
+    Plan bp;
+    bp.ngates = bd->ngates;
+    bp.d_bind = bd->d_bind;
+    bp.nparams = (int)ptotal;
+    if (bd->ngates > 0) {
+        if (dtype == DQ_C64) DQ_CUDA(plain_bind<float>(bp, params, nullptr, 1, coef, s, &ctx->launches), "bind");
+        else DQ_CUDA(plain_bind<double>(bp, params, nullptr, 1, coef, s, &ctx->launches), "bind");
+    }
+    const int nterms = (int)o->bits.size();
+    if (dtype == DQ_C64)
+        DQ_CUDA(batch_run<float>(bd->d_circ, bd->ncirc, bd->d_order, bd->d_gates, coef, o->d_wires, nterms, o->nobs,
+                                 bd->nmax, bd->maxparams, expect_out, grad_params, scratch, counter, ctx->nsm,
+                                 ctx->smem_optin, t, s, &ctx->launches),
+                "batch");
+    else
+        DQ_CUDA(batch_run<double>(bd->d_circ, bd->ncirc, bd->d_order, bd->d_gates, coef, o->d_wires, nterms,
+                                  o->nobs, bd->nmax, bd->maxparams, expect_out, grad_params, scratch, counter,
+                                  ctx->nsm, ctx->smem_optin, t, s, &ctx->launches),
+                "batch");
+    return DQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit *circuits, const double *params,
+                                const int64_t *param_offsets, const dq_observables *obs, int dtype,
+                                double *expect_out, double *grad_params, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (ncirc < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "ncirc < 0");
+    if (ncirc == 0) return DQ_OK;
+    uint64_t h = 0;
+    ObsDev *o = nullptr;
+    if ((st = batch_check(ctx, ncirc, circuits, params, param_offsets, obs, expect_out, &h, &o)) != DQ_OK) return st;
     cudaStream_t s0 = (cudaStream_t)stream;
     if (ctx->path == DQ_PATH_PLAIN) {
         // the per-gate path, circuit after circuit (the baseline for the
@@ -1905,87 +2269,81 @@ dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit *circui
         return DQ_OK;
     }
     BatchDev *bd = nullptr;
-    std::vector<BindGate> allbind;
-    auto it = ctx->batches.find(h);
-    int ncoef = 0;
-    if (it != ctx->batches.end()) {
-        bd = it->second.get();
-        ncoef = bd->ngates;
-    } else {
-        std::unique_ptr<BatchDev> b(new BatchDev());
-        std::vector<DevGate> allg;
-        std::vector<BatchCirc> bc(ncirc);
-        std::vector<std::pair<double, int>> cost(ncirc);
-        int nmax = 0, maxp = 0;
-        for (int c = 0; c < ncirc; ++c) {
-            BatchCirc x{};
-            x.n = circuits[c].nqubits;
-            x.gate0 = (int)allg.size();
-            x.param0 = (int)param_offsets[c];
-            x.nparams = circuits[c].nparams;
-            int ncr = 0;
-            st = compile_gates(ctx, &circuits[c], 0, allg, allbind, (int)param_offsets[c], &ncoef, &ncr, true);
-            if (st != DQ_OK) return fail(ctx, st, "circuit %d: %s", c, ctx->err.c_str());
-            x.ngates = (int)allg.size() - x.gate0;
-            bc[c] = x;
-            nmax = std::max(nmax, x.n);
-            maxp = std::max(maxp, x.nparams);
-            cost[c] = {std::ldexp((double)std::max(1, x.ngates), x.n), c};
-        }
-        if (nmax > 20) return fail(ctx, DQ_ERR_UNSUPPORTED, "uneven batches support up to 20 qubits per circuit");
-        std::stable_sort(cost.begin(), cost.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
-            return a.first > b.first;
-        });
-        std::vector<int32_t> order(ncirc);
-        for (int i = 0; i < ncirc; ++i) order[i] = cost[i].second;
-        b->ncirc = ncirc;
-        b->nmax = nmax;
-        b->maxparams = maxp;
-        b->ngates = (int)allg.size();
-        if ((st = upload(ctx, &b->d_circ, bc.data(), bc.size())) != DQ_OK) return st;
-        if ((st = upload(ctx, &b->d_order, order.data(), order.size())) != DQ_OK) return st;
-        if ((st = upload(ctx, &b->d_gates, allg.empty() ? nullptr : allg.data(), allg.size())) != DQ_OK) return st;
-        if ((st = upload(ctx, &b->d_bind, allbind.empty() ? nullptr : allbind.data(), allbind.size())) != DQ_OK)
-            return st;
-        bd = b.get();
-        ctx->batches.emplace(h, std::move(b));
-    }
+    if ((st = batch_tables(ctx, h, ncirc, circuits, param_offsets, &bd)) != DQ_OK) return st;
+    const BatchTune t = bd->tuned[dtype == DQ_C128] ? bd->tune[dtype == DQ_C128] : batch_default_tune(amp_bytes(dtype));
+    return batch_launch(ctx, bd, o, params, param_offsets[ncirc], dtype, expect_out, grad_params, t, s0);
+}
+
+dq_status dq_batch_autotune(dq_ctx *ctx, int ncirc, const dq_circuit *circuits, const double *params,
+                            const int64_t *param_offsets, const dq_observables *obs, int dtype, double *expect_out,
+                            double *grad_params, int *choice, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (ncirc < 0) return fail(ctx, DQ_ERR_INVALID_ARG, "ncirc < 0");
+    if (ncirc == 0) return DQ_OK;
+    uint64_t h = 0;
+    ObsDev *o = nullptr;
+    if ((st = batch_check(ctx, ncirc, circuits, params, param_offsets, obs, expect_out, &h, &o)) != DQ_OK) return st;
+    BatchDev *bd = nullptr;
+    if ((st = batch_tables(ctx, h, ncirc, circuits, param_offsets, &bd)) != DQ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const int ab = amp_bytes(dtype);
-    const size_t mat = dtype == DQ_C128 ? sizeof(Mat2<double>) : sizeof(Mat2<float>);
-    Arena a;
-    a.measuring = true;
-    a.take(mat * (size_t)(bd->ngates + 1));
-    a.take(batch_scratch_bytes(bd->nmax, ab, ctx->nsm, ctx->smem_optin));
-    a.take(256);
-    if ((st = reserve(ctx, a.used)) != DQ_OK) return st;
-    Arena w;
-    w.base = ctx->ws;
-    w.cap = ctx->ws_bytes;
-    void *coef = w.take(mat * (size_t)(bd->ngates + 1));
-    void *scratch = w.take(batch_scratch_bytes(bd->nmax, ab, ctx->nsm, ctx->smem_optin));
-    int *counter = (int *)w.take(256);
-    // bind all gate angles (global parameter indices, shared rows)
-    Plan bp;
-    bp.ngates = bd->ngates;
-    bp.d_bind = bd->d_bind;
-    bp.nparams = (int)ptotal;
-    if (bd->ngates > 0) {
-        if (dtype == DQ_C64) DQ_CUDA(plain_bind<float>(bp, params, nullptr, 1, coef, s, &ctx->launches), "bind");
-        else DQ_CUDA(plain_bind<double>(bp, params, nullptr, 1, coef, s, &ctx->launches), "bind");
+    const int c128 = dtype == DQ_C128;
+    std::vector<BatchTune> cand;
+    for (int nsmem : {10, 11, 12})
+        for (int threads : {128, 256, 512})
+            for (int per_sm : {2, 4, 8}) {
+                if (c128 && nsmem > 11) continue;
+                if (per_sm > batch_max_per_sm(bd->nmax)) continue;
+                BatchTune t;
+                t.nsmem = nsmem;
+                t.threads = threads;
+                t.per_sm = per_sm;
+                cand.push_back(t);
+            }
+    cudaEvent_t e0, e1;
+    DQ_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, DQ_ERR_CUDA, "cudaEventCreate");
     }
-    const int nterms = (int)o->bits.size();
-    if (dtype == DQ_C64)
-        DQ_CUDA(batch_run<float>(bd->d_circ, ncirc, bd->d_order, bd->d_gates, coef, o->d_wires, nterms, o->nobs,
-                                 bd->nmax, bd->maxparams, expect_out, grad_params, scratch, counter, ctx->nsm,
-                                 ctx->smem_optin, s, &ctx->launches),
-                "batch");
-    else
-        DQ_CUDA(batch_run<double>(bd->d_circ, ncirc, bd->d_order, bd->d_gates, coef, o->d_wires, nterms, o->nobs,
-                                  bd->nmax, bd->maxparams, expect_out, grad_params, scratch, counter, ctx->nsm,
-                                  ctx->smem_optin, s, &ctx->launches),
-                "batch");
-    return DQ_OK;
+    Tracer *saved = g_tracer;
+    g_tracer = nullptr;
+    float best = 1e30f;
+    BatchTune bt = batch_default_tune(amp_bytes(dtype));
+    for (const BatchTune &t : cand) {
+        // one warm-up run, then the fastest of two timed runs
+        if ((st = batch_launch(ctx, bd, o, params, param_offsets[ncirc], dtype, expect_out, grad_params, t, s)) != DQ_OK)
+            break;
+        float tbest = 1e30f;
+        for (int rep = 0; rep < 2 && st == DQ_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            st = batch_launch(ctx, bd, o, params, param_offsets[ncirc], dtype, expect_out, grad_params, t, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, DQ_ERR_CUDA, "timing a batch launch");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tbest = std::min(tbest, ms);
+        }
+        if (st != DQ_OK) break;
+        if (tbest < best) {
+            best = tbest;
+            bt = t;
+        }
+    }
+    g_tracer = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != DQ_OK) return st;
+    bd->tune[c128] = bt;
+    bd->tuned[c128] = true;
+    if (choice) {
+        choice[0] = bt.nsmem;
+        choice[1] = bt.threads;
+        choice[2] = bt.per_sm;
+    }
+    // leave the caller's outputs as the chosen configuration computes them
+    return batch_launch(ctx, bd, o, params, param_offsets[ncirc], dtype, expect_out, grad_params, bt, s);
 }
 
 dq_status dq_apply_dense(dq_ctx *ctx, int nqubits, int nw, const double *unitary, void *state, int batch, int dtype,
@@ -2039,13 +2397,20 @@ dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch, in
     if (!tile_supported(p->n, amp_bytes(dtype))) return DQ_OK;   // nothing to tune
     ctx->clear_graphs();
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t need = coef_bytes(*p, batch, dtype) + 512 + tile_workspace_bytes(*p, batch, amp_bytes(dtype));
-    if ((st = reserve(ctx, need)) != DQ_OK) return st;
+    Arena a;
+    a.measuring = true;
+    a.take(coef_bytes(*p, batch, dtype));
+    a.take(tile_workspace_bytes(*p, batch, amp_bytes(dtype)));
+    a.take(kDenseUnitaryBytes);
+    a.take(dense_image_bytes());
+    if ((st = reserve(ctx, a.used)) != DQ_OK) return st;
     Arena w;
     w.base = ctx->ws;
     w.cap = ctx->ws_bytes;
     void *coef = w.take(coef_bytes(*p, batch, dtype));
     void *tws = w.take(tile_workspace_bytes(*p, batch, amp_bytes(dtype)));
+    void *ubuf = w.take(kDenseUnitaryBytes);
+    void *image = w.take(dense_image_bytes());
     // Angles: all zero parameters are fine for timing (same sweeps run).
     double *zeros = nullptr;
     const size_t pb = sizeof(double) * (size_t)std::max(1, p->nparams) * 1;
@@ -2058,6 +2423,36 @@ dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch, in
     } else {
         e = bind_coef<double>(ctx, *p, zeros, zeros, batch, coef, s);
         if (e == cudaSuccess) e = tile_autotune<double>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+    }
+    // Dense blocks (complex64): with the tuned tile shape, time the circuit
+    // with its runs on the six lowest-order bits as tensor-core blocks against
+    // tile passes only, and keep the faster for DQ_OPT_DENSE_BLOCKS = 2.
+    DensePlan *dp = nullptr;
+    if (e == cudaSuccess && dtype == DQ_C64 && p->n > kDenseBits && dense_supported(p->n, batch) &&
+        get_dense_plan(ctx, *p, &dp) == DQ_OK && dp->nruns > 0) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        Tracer *saved = g_tracer;
+        g_tracer = nullptr;
+        float ms[2] = {0.f, 0.f};
+        for (int dense = 0; dense < 2 && e == cudaSuccess; ++dense) {
+            auto run = [&]() {
+                return dense ? dense_forward<float>(ctx, *p, *dp, coef, state, batch, tws, ubuf, image, s)
+                             : tile_apply<float>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s,
+                                                 &ctx->launches);
+            };
+            e = run();   // warm-up
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = run();
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms[dense], e0, e1);
+        }
+        g_tracer = saved;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e == cudaSuccess) ctx->tuned[p->key].dense = ms[1] < ms[0] ? 1 : 0;
     }
     cudaStreamSynchronize(s);
     cudaFree(zeros);

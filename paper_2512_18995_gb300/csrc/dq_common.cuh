@@ -212,4 +212,18 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Device-side error flag codes (written with atomicCAS so the first wins).
 enum DevErr : int { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1, DEVERR_BOUNDS = 2 };
 
+// The context's 256-byte flag block: the error flag at byte 0, the limit of
+// every device-side bounded wait (nanoseconds, uint64) at byte 64, the
+// multi-pass grid barrier's arrival counter at byte 128.
+constexpr int kFlagWaitLimitOffset = 64;
+constexpr int kFlagGridBarOffset = 128;
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long wait_limit_ns(const int *errflag) {
+    if (!errflag) return kDefaultWaitNs;
+    const unsigned long long v = *reinterpret_cast<const volatile unsigned long long *>(
+        reinterpret_cast<const char *>(errflag) + kFlagWaitLimitOffset);
+    return v ? v : kDefaultWaitNs;
+}
+
 }  // namespace dq

@@ -23,6 +23,17 @@ bool dense_supported(int n, int batch);
 // parts and laid out as the kernel's shared-memory operand image.
 cudaError_t dense_prepare(const void *unitary, int nw, void *image, cudaStream_t s, int64_t *launches);
 
+// The product of a run of gates on bits 0..5 (device DevGate records, their
+// blocks in the bound coefficient table of precision R) as a row-major 64 x
+// 64 complex128 unitary, ready for dense_prepare with nw = 6.
+struct DevGate;
+template <typename R>
+cudaError_t dense_compose(const DevGate *d_gates, int ngates, const void *coef, void *unitary, cudaStream_t s,
+                          int64_t *launches);
+// Shortest run of gates on the six lowest-order bits that the planner turns
+// into a dense block.
+constexpr int kDenseMinRun = 8;
+
 // Apply the prepared block to every row of a complex64 state, in place.
 cudaError_t dense_apply(TileCache &tc, const void *image, void *state, int n, int batch, int nsm,
                         cudaStream_t s, int64_t *launches);

@@ -160,6 +160,14 @@ cudaError_t grad_reduce(const Plan &p, const double *part, int batch, int nblk, 
 cudaError_t expect_finalize_nblk(const double *part, const DevTerm *d_terms, const int32_t *d_obs_ptr, int nobs,
                                  int batch, int nblk, double *out, cudaStream_t s, int64_t *launches);
 
+// ---- squared norms with FP64 accumulation; bounded-wait self-test ----------
+int norm_blocks_per_row(int n, int batch);
+size_t norm_part_bytes(int n, int batch);
+template <typename R>
+cudaError_t state_norm(const void *state, int n, int batch, double *part, double *out, cudaStream_t s,
+                       int64_t *launches);
+cudaError_t selftest_wait_expiry(int *errflag, cudaStream_t s, int64_t *launches);
+
 // ---- whole state in shared memory (small n) --------------------------------
 size_t wsv_smem_bytes(int n, int dtype_bytes, bool grad, int ngrad_acc);
 bool wsv_supported(int n, int amp_bytes, bool grad, size_t smem_optin, int ndouble);
@@ -184,11 +192,21 @@ struct BatchCirc {
     int32_t nparams;
     int32_t pad[3];
 };
+// Launch choices of the persistent uneven-batch kernel (autotuned per batch
+// signature by dq_batch_autotune, else batch_default_tune).
+struct BatchTune {
+    int nsmem = 0;       // circuits with at most this many qubits run in shared memory, larger ones in L2 scratch
+    int threads = 0;     // threads per circuit (power of two, 64 .. 512)
+    int per_sm = 0;      // CTAs per SM at most (1 .. kBatchMaxPerSm)
+};
+constexpr int kBatchMaxPerSm = 8;   // L2 scratch slices per SM (circuits of up to 16 qubits; 4 above)
+inline int batch_max_per_sm(int nmax) { return nmax <= 16 ? kBatchMaxPerSm : 4; }
+BatchTune batch_default_tune(int amp_bytes);
 template <typename R>
 cudaError_t batch_run(const BatchCirc *d_circ, int ncirc, const int32_t *d_order,
                       const DevGate *d_gates, const void *coef, const DevTerm *d_terms, int nterms,
                       int nobs, int nmax, int maxparams, double *expect_out, double *grad_params,
-                      void *scratch, int *d_counter, int nsm, size_t smem_optin,
+                      void *scratch, int *d_counter, int nsm, size_t smem_optin, const BatchTune &tune,
                       cudaStream_t s, int64_t *launches);
 size_t batch_scratch_bytes(int nmax, int amp_bytes, int nsm, size_t smem_optin);
 

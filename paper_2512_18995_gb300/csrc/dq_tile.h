@@ -23,6 +23,9 @@ namespace dq {
 constexpr int kTileMaxK = 14;
 constexpr int kTileLaneBits = 5;      // local bits 0..4 live across the 32 lanes of a warp
 constexpr int kTileMaxOps = 384;      // operations per pass (bounds the shared-memory program)
+// States up to this size (all rows) take the persistent multi-pass forward
+// kernel: they stay in L2 from one pass to the next.
+constexpr int64_t kMultiMaxStateBytes = int64_t(32) << 20;
 
 // Tile programs use the engine's operation and layout records.
 using TOp = EOp;
@@ -71,6 +74,12 @@ struct TileSchedule {
     std::vector<CUtensorMap> adj_psi, adj_lam;
     const void *adj_p = nullptr, *adj_l = nullptr;
     int adj_batch = -1;
+    // launch data of the persistent multi-pass kernel (chunks of passes) for
+    // the last state buffer seen
+    void *multi = nullptr;
+    const void *multi_state = nullptr;
+    int multi_batch = -1;
+    int multi_nte = -1;
     void release();
 };
 
@@ -79,6 +88,7 @@ struct TileTune {
     int k = 0;          // tile qubits (0 = default)
     int low = 0;        // always-resident low bits
     int M = 0;          // register bits per thread
+    int dense = 0;      // 1: runs of gates on the six lowest-order bits go to tensor-core dense blocks
 };
 
 // Host-side cache of schedules and the driver entry point used to encode
@@ -86,6 +96,8 @@ struct TileTune {
 struct TileCache {
     void *encode_fn = nullptr;
     int *errflag = nullptr;             // device error flag of the owning context
+    unsigned int *gridbar = nullptr;    // arrival counter of the multi-pass kernel's grid barrier (device)
+    bool multi_on = true;               // run all forward passes of an L2-resident state in one launch
     std::unordered_map<uint64_t, TileSchedule *> schedules;
     std::unordered_map<uint64_t, void *> obs;   // observable-pass schedules
     std::unordered_map<const void *, size_t> smem_set;   // dynamic shared memory limit set per kernel

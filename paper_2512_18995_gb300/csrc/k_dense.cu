@@ -172,6 +172,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // copies and products still in flight before TMEM is freed.
 __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ CUtensorMap tmap, DenseArgs a) {
     extern __shared__ unsigned char dsm_raw[];
+    const unsigned long long wlim = wait_limit_ns(a.errflag);
     const uint32_t raw = smem_u32(dsm_raw);
     unsigned char *sm = dsm_raw + (((raw + 1023u) & ~1023u) - raw);   // 1024-byte aligned operand area
     unsigned char *land = sm;                                         // DLAND tiles (hi after the split)
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
             tc_fence_before();
         }
         auto drain = [&](int64_t i) -> bool {
-            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mmad[i & 1], (uint32_t)((i >> 1) & 1)));
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mmad[i & 1], (uint32_t)((i >> 1) & 1), wlim));
             tc_fence_after();
             const int64_t row0 = tile_row(i);
             float *out = a.state + row0 * DKR + warp * 32 + lane;
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
         int64_t t = 0;
         for (; t < T; ++t) {
             const int s = (int)(t % DLAND);
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (uint32_t)((t / DLAND) & 1)))) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (uint32_t)((t / DLAND) & 1), wlim))) {
                 failed = true;
                 break;
             }
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
             int64_t i = 0;
             for (; i < T; ++i) {
                 const int s = (int)(i % DLAND);
-                if (i >= DLAND && !mbar_wait_bounded(&landfree[s], (uint32_t)(((i - DLAND) / DLAND) & 1))) {
+                if (i >= DLAND && !mbar_wait_bounded(&landfree[s], (uint32_t)(((i - DLAND) / DLAND) & 1), wlim)) {
                     failed = true;
                     break;
                 }
@@ -306,8 +307,8 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
         if (lane == 0) {
             const uint64_t dland0 = sdesc(smem_u32(land)), dlo0 = sdesc(smem_u32(lob));
             for (int64_t t = 0; t < T; ++t) {
-                if (!mbar_wait_bounded(&split[t & 1], (uint32_t)((t >> 1) & 1)) ||
-                    (t >= 2 && !mbar_wait_bounded(&accfree[t & 1], (uint32_t)(((t - 2) >> 1) & 1)))) {
+                if (!mbar_wait_bounded(&split[t & 1], (uint32_t)((t >> 1) & 1), wlim) ||
+                    (t >= 2 && !mbar_wait_bounded(&accfree[t & 1], (uint32_t)(((t - 2) >> 1) & 1), wlim))) {
                     failed = true;
                     break;
                 }
@@ -335,9 +336,9 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
     __syncthreads();
     if (tid == 0) {
         // copies and products still in flight after a failure (bounded waits)
-        for (int64_t i = cnt[1]; i < cnt[0]; ++i) mbar_wait_bounded(&full[i % DLAND], (uint32_t)((i / DLAND) & 1));
+        for (int64_t i = cnt[1]; i < cnt[0]; ++i) mbar_wait_bounded(&full[i % DLAND], (uint32_t)((i / DLAND) & 1), wlim);
         const int64_t c = cnt[2];
-        if (c >= 0) mbar_wait_bounded(&mmad[c & 1], (uint32_t)((c >> 1) & 1));
+        if (c >= 0) mbar_wait_bounded(&mmad[c & 1], (uint32_t)((c >> 1) & 1), wlim);
     }
     __syncthreads();
     tc_fence_after();
@@ -362,7 +363,50 @@ __global__ void k_dense_prepare(const double2 *__restrict__ U, int nw, float *__
     img[DKR * DKR + idx] = tf32_round((float)(v - (double)h));
 }
 
+// The product U = G_m ... G_1 of a run of gates on bits 0..5 (row-major 64 x
+// 64 complex128): block j forms column j by applying the run's gates, in
+// order, to the basis vector e_j in FP64, each gate's 2x2 block read from the
+// call's bound coefficient table (controlled blocks act where the control bit
+// is 1, a SWAP exchanges its two bits).
+template <typename R>
+__global__ void __launch_bounds__(64) k_dense_compose(const DevGate *__restrict__ g, int ngates,
+                                                      const Mat2<R> *__restrict__ coef, double2 *__restrict__ U) {
+    __shared__ double2 v[64];
+    const int j = blockIdx.x, i = threadIdx.x;
+    v[i] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    __syncthreads();
+    for (int k = 0; k < ngates; ++k) {
+        const DevGate G = g[k];
+        double2 r = v[i];
+        if (G.cls == CLS_SWAP) {
+            if (((i >> G.t) & 1) != ((i >> G.c) & 1)) r = v[i ^ ((1 << G.t) | (1 << G.c))];
+        } else if (G.c < 0 || ((i >> G.c) & 1)) {
+            const Mat2<R> m = coef[G.coef];
+            const int tb = (i >> G.t) & 1;
+            const double2 a0 = v[i & ~(1 << G.t)], a1 = v[i | (1 << G.t)];
+            const double u0x = (double)m.m[2 * tb].x, u0y = (double)m.m[2 * tb].y;
+            const double u1x = (double)m.m[2 * tb + 1].x, u1y = (double)m.m[2 * tb + 1].y;
+            r.x = u0x * a0.x - u0y * a0.y + u1x * a1.x - u1y * a1.y;
+            r.y = u0x * a0.y + u0y * a0.x + u1x * a1.y + u1y * a1.x;
+        }
+        __syncthreads();
+        v[i] = r;
+        __syncthreads();
+    }
+    U[(size_t)i * 64 + j] = v[i];
+}
+
 }  // namespace
+
+template <typename R>
+cudaError_t dense_compose(const DevGate *d_gates, int ngates, const void *coef, void *unitary, cudaStream_t s,
+                          int64_t *launches) {
+    LaunchScope ls(s, "k_dense_compose", launches);
+    k_dense_compose<R><<<64, 64, 0, s>>>(d_gates, ngates, (const Mat2<R> *)coef, (double2 *)unitary);
+    return cudaGetLastError();
+}
+template cudaError_t dense_compose<float>(const DevGate *, int, const void *, void *, cudaStream_t, int64_t *);
+template cudaError_t dense_compose<double>(const DevGate *, int, const void *, void *, cudaStream_t, int64_t *);
 
 bool dense_supported(int n, int batch) {
     if (n < kDenseBits || batch < 1) return false;

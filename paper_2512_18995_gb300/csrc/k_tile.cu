@@ -31,7 +31,12 @@
 
 namespace dq {
 
+static void release_multi(void *p);
+
 void TileSchedule::release() {
+    release_multi(multi);
+    multi = nullptr;
+    multi_state = nullptr;
     cudaFree(d_ops);
     cudaFree(d_segs);
     cudaFree(d_rops);
@@ -350,12 +355,86 @@ constexpr int tile_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) >= 256)
 template <typename R, int M>
 constexpr int tile_min_blocks() { return ((1 << M) * (int)sizeof(cx<R>) <= 64) ? 2 : 1; }
 
+// The scheduled ops of one pass on one tile held in shared memory: per
+// layout segment, load the register set, run the segment's ops, store back.
+template <typename R, int M, bool PD>
+__device__ __forceinline__ void tile_run_ops(cx<R> (&r)[1 << M], cx<R> *cur, const TOp *sops, const TSeg *ssegs,
+                                             const Mat2<R> *scoef, int nseg, int op0, int k, uint64_t base,
+                                             int lane, int warp) {
+    for (int si = 0; si < nseg; ++si) {
+        const TSeg sg = ssegs[si];
+        const Layout L = make_layout(sg, M, k, lane, warp);
+        eng_load<R, M>(r, cur, L);
+        for (int oi = sg.op0 - op0; oi < sg.op0 - op0 + sg.nops; ++oi) {
+            const TOp o = sops[oi];
+            if (o.h == H_FAN) {
+                oi += eng_fan<R, M>(r, sops + oi, scoef + oi, base, L) - 1;
+                continue;
+            }
+            eng_apply<R, M, PD>(r, o, scoef[oi], base, L, lane);
+        }
+        // each thread writes back exactly the addresses it read in this
+        // layout; the barrier orders them before the next layout's reads
+        eng_store<R, M>(r, cur, L);
+        __syncthreads();
+    }
+}
+
+// Diagonal (Z-string) observables of one finished tile: per-warp FP32 sums
+// of signed probabilities, folded into the CTA's FP64 accumulators.
+template <typename R>
+__device__ __forceinline__ void tile_epi_accum(const cx<R> *cur, const ETerm *sterm, int nte, double *eacc,
+                                               R *eaccw, int k, uint64_t base, int tid, int lane, int warp,
+                                               int nw) {
+    const int dim = 1 << k;
+    for (int j = 0; j < nte; ++j) {
+        const ETerm et = sterm[j];
+        const int bpar = __popcll(base & et.sout) & 1;
+        R e = R(0);
+        for (int l = tid; l < dim; l += blockDim.x) {
+            const cx<R> x = cur[l];
+            const R pr = x.x * x.x + x.y * x.y;
+            e += ((__popc((uint32_t)l & et.sloc) & 1) ^ bpar) ? -pr : pr;
+        }
+        e = warp_sum_t(e);
+        if (lane == 0) eaccw[warp * nte + j] += e;
+    }
+    __syncthreads();
+    for (int j = tid; j < nte; j += blockDim.x) {
+        double sum = 0.0;
+        for (int ww = 0; ww < nw; ++ww) {
+            sum += (double)eaccw[ww * nte + j];
+            eaccw[ww * nte + j] = R(0);
+        }
+        eacc[j] += sum;
+    }
+}
+
+// Stage ETerm records of the diagonal observables for a pass whose tile bits
+// are T (tile-local sign bits and the sign bits outside the tile).
+__device__ __forceinline__ void tile_epi_setup(const TileEpi &epi, int k, ETerm *sterm, double *eacc, int tid) {
+    for (int j = tid; j < epi.nterms; j += blockDim.x) {
+        const uint64_t sm = epi.terms[j].s;
+        ETerm e{};
+        uint64_t in = 0;
+        for (int i = 0; i < k; ++i)
+            if ((sm >> epi.T[i]) & 1) {
+                e.sloc |= 1u << i;
+                in |= uint64_t(1) << epi.T[i];
+            }
+        e.sout = sm & ~in;
+        sterm[j] = e;
+        eacc[j] = 0.0;
+    }
+}
+
 template <typename R, int M, bool PD>
 __global__ void __launch_bounds__(tile_max_threads<R, M>(), tile_min_blocks<R, M>())
 k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t tbytes = sizeof(cx<R>) << a.g.k;
+    const unsigned long long wlim = wait_limit_ns(a.errflag);
     cx<R> *buf0 = reinterpret_cast<cx<R> *>(smem);
     cx<R> *buf1 = reinterpret_cast<cx<R> *>(smem + tbytes);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * tbytes);
@@ -391,19 +470,7 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
         tma_load5(buf0, &tmap, c, &bar[0]);
     }
     for (int i = tid; i < a.nops; i += blockDim.x) scoef[i] = gcoef[sops[i].coef];
-    for (int j = tid; j < nte; j += blockDim.x) {
-        const uint64_t sm = a.epi.terms[j].s;
-        ETerm e{};
-        uint64_t in = 0;
-        for (int i = 0; i < a.g.k; ++i)
-            if ((sm >> a.epi.T[i]) & 1) {
-                e.sloc |= 1u << i;
-                in |= uint64_t(1) << a.epi.T[i];
-            }
-        e.sout = sm & ~in;
-        sterm[j] = e;
-        eacc[j] = 0.0;
-    }
+    tile_epi_setup(a.epi, a.g.k, sterm, eacc, tid);
     for (int i = tid; i < nw * nte; i += blockDim.x) eaccw[i] = R(0);
     __syncthreads();
     if (t0 >= t1) return;
@@ -431,7 +498,7 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
             mbar_expect_tx(nb, (uint32_t)tbytes);
             tma_load5(b ? buf0 : buf1, &tmap, cn, nb);
         }
-        const bool ok = mbar_wait_bounded(b ? &bar[1] : &bar[0], b ? phase1 : phase0);
+        const bool ok = mbar_wait_bounded(b ? &bar[1] : &bar[0], b ? phase1 : phase0, wlim);
         if (b) phase1 ^= 1; else phase0 ^= 1;
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -445,23 +512,7 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
             __syncthreads();
             crow = row;
         }
-        for (int si = 0; si < a.nseg; ++si) {
-            const TSeg sg = ssegs[si];
-            const Layout L = make_layout(sg, M, a.g.k, lane, warp);
-            eng_load<R, M>(r, cur, L);
-            for (int oi = sg.op0 - a.op0; oi < sg.op0 - a.op0 + sg.nops; ++oi) {
-                const TOp o = sops[oi];
-                if (o.h == H_FAN) {
-                    oi += eng_fan<R, M>(r, sops + oi, scoef + oi, base, L) - 1;
-                    continue;
-                }
-                eng_apply<R, M, PD>(r, o, scoef[oi], base, L, lane);
-            }
-            // each thread writes back exactly the addresses it read in this
-            // layout; the barrier orders them before the next layout's reads
-            eng_store<R, M>(r, cur, L);
-            __syncthreads();
-        }
+        tile_run_ops<R, M, PD>(r, cur, sops, ssegs, scoef, a.nseg, a.op0, a.g.k, base, lane, warp);
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -474,28 +525,7 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
                 if (erow >= 0) eflush(erow);
                 erow = row;
             }
-            const int dim = 1 << a.g.k;
-            for (int j = 0; j < nte; ++j) {
-                const ETerm et = sterm[j];
-                const int bpar = __popcll(base & et.sout) & 1;
-                R e = R(0);
-                for (int l = tid; l < dim; l += blockDim.x) {
-                    const cx<R> x = cur[l];
-                    const R pr = x.x * x.x + x.y * x.y;
-                    e += ((__popc((uint32_t)l & et.sloc) & 1) ^ bpar) ? -pr : pr;
-                }
-                e = warp_sum_t(e);
-                if (lane == 0) eaccw[warp * nte + j] += e;
-            }
-            __syncthreads();
-            for (int j = tid; j < nte; j += blockDim.x) {
-                double sum = 0.0;
-                for (int ww = 0; ww < nw; ++ww) {
-                    sum += (double)eaccw[ww * nte + j];
-                    eaccw[ww * nte + j] = R(0);
-                }
-                eacc[j] += sum;
-            }
+            tile_epi_accum<R>(cur, sterm, nte, eacc, eaccw, a.g.k, base, tid, lane, warp, nw);
         }
     }
     grid_dep_launch();   // the next kernel of the stream may start its prologue
@@ -506,8 +536,228 @@ k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
     if (failed && tid == 0) {
         atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
         // let any load still in flight land before the CTA exits (bounded)
-        mbar_wait_bounded(&bar[0], phase0);
-        mbar_wait_bounded(&bar[1], phase1);
+        mbar_wait_bounded(&bar[0], phase0, wlim);
+        mbar_wait_bounded(&bar[1], phase1, wlim);
+    }
+    if (tid == 0) bulk_wait0();
+}
+
+// ---------------------------------------------------------------------------
+// Persistent multi-pass forward kernel for states that stay in L2.
+//
+// All passes of a schedule (up to kMultiMaxPasses per launch) run in one
+// launch: each CTA streams its share of the tiles of pass p exactly as
+// k_tile_fwd does, waits until its bulk stores have completed, and then the
+// grid meets at a barrier before pass p + 1 reads the state in its new tile
+// layout.  Every CTA of the grid must be resident at once (the grid is sized
+// by the occupancy calculator, one wave); the barrier wait is bounded, and a
+// CTA that gives up sets the context's error flag, which the others see in
+// their own wait and leave too.
+// ---------------------------------------------------------------------------
+constexpr int kMultiMaxPasses = 20;
+
+struct MultiPass {
+    int op0, nops, seg0, nseg;
+    int any_row;
+    TileGeom g;
+};
+
+// Tensor maps travel as kernel parameters (so no device copy is needed and
+// the launch can be captured into a graph); __grid_constant__ keeps them in
+// parameter space, where TMA may read them.
+struct MultiArgs {
+    CUtensorMap map[kMultiMaxPasses];
+    MultiPass pass[kMultiMaxPasses];
+    int npass;
+    const TOp *ops;
+    const TSeg *segs;
+    const void *coef;
+    int *errflag;
+    unsigned int *bar;      // arrival counter, zero at launch
+    TileEpi epi;            // diagonal observables of the last pass (nterms == 0: none)
+};
+
+// Launch data of one chunk of passes for the last state buffer seen.
+struct MultiLaunch {
+    MultiArgs args;
+    size_t smem;
+    int grid;
+    bool pd;
+};
+
+}  // namespace
+
+static void release_multi(void *p) { delete reinterpret_cast<std::vector<MultiLaunch> *>(p); }
+
+namespace {
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void red_add_release_gpu(unsigned int *p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0 of every CTA: arrive (after this CTA's completed bulk stores) and
+// wait until `target` arrivals have been counted.  False when the wait ran
+// out (the error flag is then set) or another CTA has set the error flag.
+__device__ __forceinline__ bool grid_arrive_wait(unsigned int *bar, unsigned int target, int *errflag,
+                                                 unsigned long long limit_ns) {
+    fence_proxy_async_global();
+    red_add_release_gpu(bar, 1u);
+    if (ld_acquire_gpu(bar) < target) {
+        const uint64_t t0 = global_ns();
+        for (;;) {
+            __nanosleep(64);
+            if (ld_acquire_gpu(bar) >= target) break;
+            if (*reinterpret_cast<volatile int *>(errflag) != 0) return false;
+            if (global_ns() - t0 > limit_ns) {
+                atomicCAS(errflag, 0, DEVERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+    // the other CTAs' stores (made by the async proxy) before this CTA's
+    // next tensor loads
+    fence_proxy_async_global();
+    return true;
+}
+
+template <typename R, int M, bool PD>
+__global__ void __launch_bounds__(tile_max_threads<R, M>(), tile_min_blocks<R, M>())
+k_tile_multi(const __grid_constant__ MultiArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_stop;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long wlim = wait_limit_ns(a.errflag);
+    const int k = a.pass[0].g.k;
+    const size_t tbytes = sizeof(cx<R>) << k;
+    cx<R> *buf0 = reinterpret_cast<cx<R> *>(smem);
+    cx<R> *buf1 = reinterpret_cast<cx<R> *>(smem + tbytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * tbytes);
+    int maxops = 0, maxseg = 0;
+    for (int p = 0; p < a.npass; ++p) {
+        maxops = max(maxops, a.pass[p].nops);
+        maxseg = max(maxseg, a.pass[p].nseg);
+    }
+    TOp *sops = reinterpret_cast<TOp *>(smem + 2 * tbytes + 64);
+    TSeg *ssegs = reinterpret_cast<TSeg *>(sops + maxops);
+    Mat2<R> *scoef = reinterpret_cast<Mat2<R> *>(ssegs + maxseg);
+    const int nte = a.epi.nterms, nw = blockDim.x >> 5;
+    ETerm *sterm = reinterpret_cast<ETerm *>(scoef + maxops);     // [nte]
+    double *eacc = reinterpret_cast<double *>(sterm + nte);         // [nte]
+    R *eaccw = reinterpret_cast<R *>(eacc + nte);                   // [nw][nte]
+    const Mat2<R> *gcoef = reinterpret_cast<const Mat2<R> *>(a.coef);
+    const int64_t ntiles = a.pass[0].g.ntiles;
+    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t1 = min(ntiles, t0 + per);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_async_smem();
+        s_stop = 0;
+    }
+    for (int i = tid; i < nw * nte; i += blockDim.x) eaccw[i] = R(0);
+    grid_dep_wait();
+    uint32_t phase0 = 0, phase1 = 0;
+    bool failed = false;
+    int64_t erow = -1;
+    cx<R> r[1 << M];
+    for (int p = 0; p < a.npass && !failed; ++p) {
+        const MultiPass &P = a.pass[p];
+        const CUtensorMap *map = &a.map[p];
+        const bool last = p + 1 == a.npass;
+        int c[5];
+        uint64_t base;
+        int64_t row;
+        if (tid == 0 && t0 < t1) {
+            geom_coords(P.g, t0, c, base, row);
+            mbar_expect_tx(&bar[0], (uint32_t)tbytes);
+            tma_load5(buf0, map, c, &bar[0]);
+        }
+        // this pass's program and row-0 coefficient blocks
+        for (int i = tid; i < P.nops; i += blockDim.x) {
+            const TOp o = a.ops[P.op0 + i];
+            sops[i] = o;
+            scoef[i] = gcoef[o.coef];
+        }
+        for (int i = tid; i < P.nseg; i += blockDim.x) ssegs[i] = a.segs[P.seg0 + i];
+        if (last && nte) tile_epi_setup(a.epi, k, sterm, eacc, tid);
+        __syncthreads();
+        int64_t crow = 0;
+        for (int64_t t = t0, i = 0; t < t1; ++t, ++i) {
+            const int b = (int)(i & 1);
+            cx<R> *cur = b ? buf1 : buf0;
+            if (tid == 0 && t + 1 < t1) {
+                int cn[5];
+                uint64_t bn;
+                int64_t rn;
+                geom_coords(P.g, t + 1, cn, bn, rn);
+                bulk_wait_read0();
+                uint64_t *nb = b ? &bar[0] : &bar[1];
+                mbar_expect_tx(nb, (uint32_t)tbytes);
+                tma_load5(b ? buf0 : buf1, map, cn, nb);
+            }
+            const bool ok = mbar_wait_bounded(b ? &bar[1] : &bar[0], b ? phase1 : phase0, wlim);
+            if (b) phase1 ^= 1; else phase0 ^= 1;
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            geom_coords(P.g, t, c, base, row);
+            if (P.any_row && row != crow) {
+                for (int i2 = tid; i2 < P.nops; i2 += blockDim.x)
+                    if (sops[i2].rowstep) scoef[i2] = gcoef[sops[i2].coef + row * sops[i2].rowstep];
+                __syncthreads();
+                crow = row;
+            }
+            tile_run_ops<R, M, PD>(r, cur, sops, ssegs, scoef, P.nseg, P.op0, k, base, lane, warp);
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tma_store5(map, c, cur);
+                bulk_commit();
+            }
+            if (last && nte) {
+                if (row != erow) {
+                    if (erow >= 0)
+                        for (int j = tid; j < nte; j += blockDim.x) {
+                            a.epi.part[((int64_t)j * a.epi.batch + erow) * gridDim.x + blockIdx.x] = eacc[j];
+                            eacc[j] = 0.0;
+                        }
+                    erow = row;
+                }
+                tile_epi_accum<R>(cur, sterm, nte, eacc, eaccw, k, base, tid, lane, warp, nw);
+            }
+        }
+        if (failed) break;
+        if (!last) {
+            // every store of this pass has landed before any CTA reads the
+            // next layout
+            if (tid == 0) {
+                bulk_wait0();
+                if (!grid_arrive_wait(a.bar, (unsigned int)(p + 1) * gridDim.x, a.errflag, wlim)) s_stop = 1;
+            }
+            __syncthreads();
+            if (s_stop) return;   // no copies in flight: the stores were waited for, no load was issued
+        }
+    }
+    grid_dep_launch();
+    if (nte && !failed && erow >= 0) {
+        __syncthreads();
+        for (int j = tid; j < nte; j += blockDim.x)
+            a.epi.part[((int64_t)j * a.epi.batch + erow) * gridDim.x + blockIdx.x] = eacc[j];
+    }
+    if (failed && tid == 0) {
+        atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
+        mbar_wait_bounded(&bar[0], phase0, wlim);
+        mbar_wait_bounded(&bar[1], phase1, wlim);
     }
     if (tid == 0) bulk_wait0();
 }
@@ -613,10 +863,144 @@ TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, 
 namespace {
 
 template <typename R>
+const void *multi_kernel(int M, bool pd) {
+    switch (M) {
+    case 2: return pd ? (const void *)k_tile_multi<R, 2, true> : (const void *)k_tile_multi<R, 2, false>;
+    case 3: return pd ? (const void *)k_tile_multi<R, 3, true> : (const void *)k_tile_multi<R, 3, false>;
+    case 4: return pd ? (const void *)k_tile_multi<R, 4, true> : (const void *)k_tile_multi<R, 4, false>;
+    default:
+        return pd ? (const void *)k_tile_multi<R, (TileCfg<R>::Mmax), true>
+                  : (const void *)k_tile_multi<R, (TileCfg<R>::Mmax), false>;
+    }
+}
+
+// The persistent multi-pass kernel serves states that stay in L2 between
+// passes, with at least two passes to merge.
+bool multi_applies(const TileCache &tc, const TileSchedule &sc, int n, int64_t batch, int amp) {
+    return tc.multi_on && tc.gridbar && sc.passes.size() >= 2 && ((batch << n) * (int64_t)amp) <= kMultiMaxStateBytes;
+}
+
+template <typename R>
+cudaError_t run_forward_multi(TileCache &tc, const Plan &p, TileSchedule &sc, const void *coef, void *state,
+                              int batch, int nsm, cudaStream_t s, int64_t *launches, const TileEpi *epi,
+                              int *epi_grid) {
+    const int M = sc.M;
+    constexpr int wb = TileCfg<R>::wb;
+    const int amp = (int)sizeof(cx<R>);
+    const int threads = 1 << (sc.k - M);
+    const int npass = (int)sc.passes.size();
+    const int nchunk = (npass + kMultiMaxPasses - 1) / kMultiMaxPasses;
+    const int nte = epi ? epi->nterms : 0;
+    auto *cache = reinterpret_cast<std::vector<MultiLaunch> *>(sc.multi);
+    if (!cache) {
+        cache = new std::vector<MultiLaunch>();
+        sc.multi = cache;
+    }
+    if (sc.multi_state != state || sc.multi_batch != batch || sc.multi_nte != nte || (int)cache->size() != nchunk) {
+        cache->assign(nchunk, MultiLaunch{});
+        sc.multi_state = nullptr;
+        for (int ch = 0; ch < nchunk; ++ch) {
+            MultiLaunch &L = (*cache)[ch];
+            MultiArgs &a = L.args;
+            std::memset(&a, 0, sizeof(a));
+            const int p0 = ch * kMultiMaxPasses, p1 = std::min(npass, p0 + kMultiMaxPasses);
+            const bool last_chunk = ch + 1 == nchunk;
+            a.npass = p1 - p0;
+            int maxops = 0, maxseg = 0;
+            bool pd = false;
+            for (int pi = p0; pi < p1; ++pi) {
+                const TPass &ps = sc.passes[pi];
+                TileDims d;
+                if (!make_dims(ps.T, p.n, wb, d)) return cudaErrorInvalidValue;
+                if (!encode_map(tc.encode_fn, &a.map[pi - p0], d, state, batch, wb)) return cudaErrorInvalidValue;
+                MultiPass &mp = a.pass[pi - p0];
+                mp.op0 = ps.op0;
+                mp.nops = ps.nops;
+                mp.seg0 = ps.seg0;
+                mp.nseg = ps.nseg;
+                mp.any_row = 0;
+                for (int j = ps.op0; j < ps.op0 + ps.nops; ++j) mp.any_row |= sc.ops[j].rowstep != 0;
+                mp.g = make_geom(d, p.n, sc.k, wb, batch);
+                maxops = std::max(maxops, ps.nops);
+                maxseg = std::max(maxseg, ps.nseg);
+                pd |= ps.pdiag;
+            }
+            L.pd = pd;
+            L.smem = tile_smem_bytes(sc.k, amp, maxops, maxseg, last_chunk ? nte : 0, threads);
+            const void *kfn = multi_kernel<R>(M, pd);
+            if (tc.smem_set[kfn] < L.smem) {
+                cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+                if (e != cudaSuccess) return e;
+                tc.smem_set[kfn] = L.smem;
+            }
+            int per_sm = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, L.smem);
+            if (e != cudaSuccess) return e;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            const int64_t ntiles = (int64_t)batch << (p.n - sc.k);
+            // one wave: every CTA resident at once (the grid barrier needs it)
+            int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * nsm);
+            if (last_chunk && nte) grid = std::min<int64_t>(grid, 4 * (int64_t)nsm);   // epilogue partials
+            L.grid = (int)grid;
+        }
+        sc.multi_state = state;
+        sc.multi_batch = batch;
+        sc.multi_nte = nte;
+    }
+    for (int ch = 0; ch < nchunk; ++ch) {
+        MultiLaunch &L = (*cache)[ch];
+        MultiArgs &a = L.args;
+        const bool last_chunk = ch + 1 == nchunk;
+        a.ops = sc.d_ops;
+        a.segs = sc.d_segs;
+        a.coef = coef;
+        a.errflag = tc.errflag;
+        a.bar = tc.gridbar;
+        a.epi = TileEpi{};
+        if (last_chunk && epi) {
+            a.epi = *epi;
+            const TPass &ps = sc.passes[npass - 1];
+            for (int j = 0; j < 16; ++j) a.epi.T[j] = (int8_t)(j < (int)ps.T.size() ? ps.T[j] : 0);
+            if (epi_grid) *epi_grid = L.grid;
+        }
+        cudaError_t e = cudaMemsetAsync(tc.gridbar, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return e;
+        LaunchScope ls(s, "k_tile_multi", launches);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3((unsigned)L.grid);
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = L.smem;
+        cfg.stream = s;
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        switch (M * 2 + (L.pd ? 1 : 0)) {
+        case 4: e = cudaLaunchKernelEx(&cfg, k_tile_multi<R, 2, false>, a); break;
+        case 5: e = cudaLaunchKernelEx(&cfg, k_tile_multi<R, 2, true>, a); break;
+        case 6: e = cudaLaunchKernelEx(&cfg, k_tile_multi<R, 3, false>, a); break;
+        case 7: e = cudaLaunchKernelEx(&cfg, k_tile_multi<R, 3, true>, a); break;
+        case 8: e = cudaLaunchKernelEx(&cfg, k_tile_multi<R, 4, false>, a); break;
+        case 9: e = cudaLaunchKernelEx(&cfg, k_tile_multi<R, 4, true>, a); break;
+        default:
+            e = L.pd ? cudaLaunchKernelEx(&cfg, k_tile_multi<R, (TileCfg<R>::Mmax), true>, a)
+                     : cudaLaunchKernelEx(&cfg, k_tile_multi<R, (TileCfg<R>::Mmax), false>, a);
+            break;
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename R>
 cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const void *coef, void *state,
                         int batch, int nsm, cudaStream_t s, int64_t *launches, const TileEpi *epi = nullptr,
                         int *epi_grid = nullptr) {
     const int M = sc.M;
+    if (multi_applies(tc, sc, p.n, batch, (int)sizeof(cx<R>)))
+        return run_forward_multi<R>(tc, p, sc, coef, state, batch, nsm, s, launches, epi, epi_grid);
     constexpr int wb = TileCfg<R>::wb;
     const int amp = (int)sizeof(cx<R>);
     const int threads = 1 << (sc.k - M);

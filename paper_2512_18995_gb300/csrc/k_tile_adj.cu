@@ -198,6 +198,7 @@ template <typename R>
 __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_constant__ CUtensorMap mp,
                                                    const __grid_constant__ CUtensorMap ml, ObsArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
+    const unsigned long long wlim = wait_limit_ns(a.errflag);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int64_t dim = int64_t(1) << a.g.k;
     const size_t tbytes = sizeof(cx<R>) * (size_t)dim;
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
             tma_load5(bufP, &mp, c, &bar[0]);
             if (a.lam_mode == 2) tma_load5(bufL, &ml, c, &bar[0]);
         }
-        const bool ok = mbar_wait_bounded(&bar[0], phase);
+        const bool ok = mbar_wait_bounded(&bar[0], phase, wlim);
         phase ^= 1;
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
     }
     if (failed && tid == 0) {
         atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
-        mbar_wait_bounded(&bar[0], phase);
+        mbar_wait_bounded(&bar[0], phase, wlim);
     }
     if (tid == 0) bulk_wait0();
 }
@@ -364,6 +365,7 @@ __global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __gr
                                                                        const __grid_constant__ CUtensorMap ml,
                                                                        AdjArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
+    const unsigned long long wlim = wait_limit_ns(a.errflag);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const size_t tbytes = sizeof(cx<R>) << a.g.k;
     cx<R> *bufP = reinterpret_cast<cx<R> *>(smem);
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __gr
             tma_load5(bufP, &mp, c, &bar[0]);
             tma_load5(bufL, &ml, c, &bar[0]);
         }
-        const bool ok = mbar_wait_bounded(&bar[0], phase);
+        const bool ok = mbar_wait_bounded(&bar[0], phase, wlim);
         phase ^= 1;
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -499,7 +501,7 @@ __global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __gr
     }
     if (failed && tid == 0) {
         atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
-        mbar_wait_bounded(&bar[0], phase);
+        mbar_wait_bounded(&bar[0], phase, wlim);
     }
     if (tid == 0) bulk_wait0();
 }

@@ -456,15 +456,29 @@ cudaError_t wsv_launch(const Plan &p, const void *coef, const void *state_in, in
 
 size_t batch_scratch_bytes(int nmax, int amp_bytes, int nsm, size_t smem_optin) {
     (void)smem_optin;
-    return (size_t)nsm * 4 * 2 * ((size_t)amp_bytes << nmax);
+    return (size_t)nsm * batch_max_per_sm(nmax) * 2 * ((size_t)amp_bytes << nmax);
+}
+
+// Defaults of the persistent uneven-batch launch: circuits up to 12 qubits
+// (complex64; 11 for complex128) in shared memory, 512 threads per circuit,
+// at most four CTAs per SM.
+BatchTune batch_default_tune(int amp_bytes) {
+    BatchTune t;
+    t.nsmem = amp_bytes == 8 ? 12 : 11;
+    t.threads = kMaxThreads;
+    t.per_sm = 4;
+    return t;
 }
 
 template <typename R>
 cudaError_t batch_run(const BatchCirc *d_circ, int ncirc, const int32_t *d_order,
                       const DevGate *d_gates, const void *coef, const DevTerm *d_terms, int nterms,
                       int nobs, int nmax, int maxparams, double *expect_out, double *grad_params,
-                      void *scratch, int *d_counter, int nsm, size_t smem_optin,
+                      void *scratch, int *d_counter, int nsm, size_t smem_optin, const BatchTune &tune,
                       cudaStream_t s, int64_t *launches) {
+    if (tune.threads < 64 || tune.threads > kMaxThreads || (tune.threads & (tune.threads - 1)) ||
+        tune.per_sm < 1 || tune.per_sm > batch_max_per_sm(nmax) || tune.nsmem < 2)
+        return cudaErrorInvalidValue;
     BatchArgs a;
     a.circ = d_circ;
     a.ncirc = ncirc;
@@ -481,17 +495,17 @@ cudaError_t batch_run(const BatchCirc *d_circ, int ncirc, const int32_t *d_order
     a.scratch = scratch;
     a.counter = d_counter;
     // Shared memory for on-chip circuits: two vectors of 2^nsmem amplitudes.
-    int nsmem = std::min(nmax, sizeof(R) == 4 ? 12 : 11);
+    int nsmem = std::min(nmax, tune.nsmem);
     while (nsmem > 2 && wsv_smem_bytes(nsmem, (int)sizeof(cx<R>), true, a.maxparams + nobs + 8) > smem_optin) --nsmem;
     a.nsmem = nsmem;
     const size_t smem = wsv_smem_bytes(nsmem, (int)sizeof(cx<R>), true, a.maxparams + nobs + 8);
-    const int threads = kMaxThreads;
+    const int threads = tune.threads;
     cudaError_t e = cudaFuncSetAttribute(k_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<R>, threads, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
-    per_sm = std::min(per_sm, 4);   // scratch holds 4 slices per SM
+    per_sm = std::min(per_sm, tune.per_sm);   // scratch holds kBatchMaxPerSm slices per SM
     const int grid = std::max(1, std::min(ncirc, per_sm * nsm));
     e = cudaMemsetAsync(d_counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -507,7 +521,7 @@ cudaError_t batch_run(const BatchCirc *d_circ, int ncirc, const int32_t *d_order
                                        cudaStream_t, int64_t *);                                            \
     template cudaError_t batch_run<R>(const BatchCirc *, int, const int32_t *, const DevGate *, const void *, \
                                       const DevTerm *, int, int, int, int, double *, double *, void *, int *, \
-                                      int, size_t, cudaStream_t, int64_t *);
+                                      int, size_t, const BatchTune &, cudaStream_t, int64_t *);
 DQ_INST(float)
 DQ_INST(double)
 #undef DQ_INST

@@ -36,8 +36,13 @@ def test_reference_arm_other_ranks_print_nothing():
     assert run_reference({"RANK": "1", "WORLD_SIZE": "2"}) == []
 
 
-def test_single_thread_oracle_rate():
+def test_oracle_timing_in_a_fresh_process():
+    """The oracle baseline is timed in a child process, on all cores and on
+    one (OpenMP held to one thread), in full steps of the headline workload."""
     sys.path.insert(0, ROOT)
     import bench
-    r = bench.oracle_rate_single_thread(budget_s=1.0)
-    assert r["cores"] == 1 and r["value"] > 0 and "of 480 gates" in r["sample"], r
+    import workloads as W
+    one = bench.oracle_timing(1.0, threads=1)
+    assert one["cores"] == 1 and one["steps"] >= 1 and one["seconds"] > 0, one
+    v = bench.oracle_line_values(W.config_c2(), one["steps"], one["seconds"])
+    assert v["value"] > v["gate_equivalent"] > 0 and v["ms_per_step"] > 0

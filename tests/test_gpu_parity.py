@@ -368,6 +368,33 @@ def test_config_c4_uneven_batch(ctx, path):
     assert_rel(e[pick], e_ref, torch.complex64, "sampled circuits' expectations", zero_scale=obs_scale(obs))
 
 
+@pytest.mark.parametrize("dtype", sorted(DTYPES))
+def test_config_c4_autotuned_launch(ctx, dtype):
+    """The uneven batch with its autotuned launch: the tuner's own outputs and
+    a later call with the cached choice both match the oracle."""
+    ctx.set_path(dq.PATH_FUSED)
+    dt = DTYPES[dtype]
+    circs = W.config_c4(256)
+    obs = [W.obs_zz01_x0()]
+    dcs = [dq.Circuit(n, g, nparams=len(a)) for n, g, a in circs]
+    params = np.concatenate([a for _, _, a in circs])
+    offs = np.cumsum([0] + [len(a) for _, _, a in circs])
+    choice = ctx.batch_autotune(dcs, dev(params), dq.Observables(obs), dt)
+    assert choice[0] in (10, 11, 12) and choice[1] in (128, 256, 512) and choice[2] in (2, 4, 8), choice
+    e, gp = ctx.batch_forward_grad(dcs, dev(params), dq.Observables(obs), dt)
+    e = e.cpu().numpy()
+    gp = gp.cpu().numpy()
+    pick = sorted(set(range(0, 256, 8)) | {i for i, c in enumerate(circs) if c[0] >= 14})
+    e_ref = []
+    for i in pick:
+        n, g, a = circs[i]
+        er, gr, _ = oracle.adjoint(n, g, obs, a)
+        e_ref.append(er[0, 0])
+        assert_rel(gp[offs[i]:offs[i + 1]], gr, dt, f"circuit {i} gradient (tuned {choice})",
+                   zero_scale=obs_scale(obs))
+    assert_rel(e[pick], e_ref, dt, f"expectations (tuned {choice})", zero_scale=obs_scale(obs))
+
+
 @pytest.mark.parametrize("path", sorted(PATHS))
 @pytest.mark.parametrize("n", [14, 17])
 def test_config_c5_structure_reduced(ctx, path, n):
@@ -545,9 +572,13 @@ def test_launch_counter_counts_kernels(ctx):
 
 
 @pytest.mark.parametrize("n,batch,want", [(12, 64, {"k_rows"}),
-                                          (18, 2, {"k_tile_fwd", "k_tile_obs", "k_tile_adj"})])
+                                          (18, 2, {"k_tile_multi", "k_tile_obs", "k_tile_adj"}),
+                                          (23, 1, {"k_tile_fwd", "k_tile_obs", "k_tile_adj"})])
 def test_fused_path_runs_the_fused_kernels(ctx, n, batch, want):
-    """The fused path must not fall back to per-gate sweeps silently."""
+    """The fused path must not fall back to per-gate sweeps silently: whole
+    rows on chip, the persistent multi-pass forward for states that stay in
+    L2 (2 x 2^18 complex64 = 4 MiB), one launch per forward pass above
+    32 MiB (2^23 complex64 = 64 MiB)."""
     ctx.set_path(dq.PATH_FUSED)
     gates = W.encode_layer(n) + W.hea_layers(n, 2)
     circ = dq.Circuit(n, gates, nparams=4 * n, nfeatures=n)
