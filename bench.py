@@ -432,16 +432,22 @@ def our_arm(args, rank, world, dist):
 
     extras = {}
     if not args.no_extras:
-        extras["hbm_sweep"] = hbm_sweep(ctx, device, hbm_peak, peak_kind)
-        extras["grads"] = batched_grads(ctx, device)
-        extras["dense_block"] = dense_block(ctx, device, hbm_peak, peak_kind)
-        extras["uneven_batch"] = uneven_batch(ctx, device)
-        extras["qft_tfim30"] = qft_tfim30(ctx, device)
-        extras["qcnn"] = qcnn_batch(ctx, device)
-        extras["trotter30"] = trotter30(ctx, device)
-        extras["sample30"] = sample30(ctx, device, hbm_peak, peak_kind)
-        extras["hessian"] = hessian_hea(ctx, device)
-        extras["density"] = density_noisy(ctx, device)
+        runs = {
+            "hbm_sweep": lambda: hbm_sweep(ctx, device, hbm_peak, peak_kind),
+            "grads": lambda: batched_grads(ctx, device),
+            "dense_block": lambda: dense_block(ctx, device, hbm_peak, peak_kind),
+            "dense_planner": lambda: dense_planner(ctx, device, hbm_peak, peak_kind),
+            "uneven_batch": lambda: uneven_batch(ctx, device),
+            "qft_tfim30": lambda: qft_tfim30(ctx, device),
+            "qcnn": lambda: qcnn_batch(ctx, device),
+            "trotter30": lambda: trotter30(ctx, device),
+            "sample30": lambda: sample30(ctx, device, hbm_peak, peak_kind),
+            "hessian": lambda: hessian_hea(ctx, device),
+            "density": lambda: density_noisy(ctx, device),
+        }
+        pick = list(runs) if args.extras == "all" else [x for x in args.extras.split(",") if x]
+        for name in pick:
+            extras[name] = runs[name]()
         ctx.set_path({"auto": dq.PATH_AUTO, "plain": dq.PATH_PLAIN, "fused": dq.PATH_FUSED}[args.path])
 
     if rank == 0:
@@ -588,6 +594,63 @@ def dense_block(ctx, device, hbm_peak, peak_kind, n=30, reps=4):
             "peak_kind": peak_kind, "tflops_tf32x3": tflops,
             "tf32_peak": tf32_peak, "tensor_frac": tflops / tf32_peak,
             "tf32_peak_kind": "measured bf16 x nominal tf32/bf16" if bf16 else "fallback bf16 x nominal tf32/bf16"}
+
+
+def dense_planner(ctx, device, hbm_peak, peak_kind, n=28, layers=6):
+    """Dense blocks chosen by the planner on a forward-only call: 28 qubits
+    (2 GiB complex64), a brick wall of two-qubit gates on the six
+    lowest-order wires (six layers: RY, RZ on each wire, a CNOT chain and
+    CZ/CRY couplings -- 144 gates in one run) between two RY/RZ + CNOT-ring
+    layers on all wires.  Time with dense blocks on vs tile passes only."""
+    import torch
+    import paper_2512_18995_gb300 as dq
+    w = list(range(n - 6, n))
+    gates = W.hea_layers(n, 1)
+    p = 2 * n
+    for _ in range(layers):
+        for q in w:
+            gates += [W.Gate("ry", (q,), param=p), W.Gate("rz", (q,), param=p + 1)]
+            p += 2
+        gates += [W.Gate("cnot", (a, b)) for a, b in zip(w[:-1], w[1:])]
+        gates += [W.Gate("cz", (w[0], w[5])), W.Gate("cry", (w[2], w[4]), param=p), W.Gate("cry", (w[5], w[1]),
+                                                                                            param=p + 1)]
+        p += 2
+    gates += W.hea_layers(n, 1, first_param=p)
+    p += 2 * n
+    circ = dq.Circuit(n, gates, nparams=p)
+    params = torch.tensor(W.uniform_array(W._seed(28), p, 0.0, 2 * np.pi), device=device)
+    obs = dq.Observables([W.obs_sum_z(n)])
+    try:
+        st = torch.empty((1, 1 << n), dtype=torch.complex64, device=device)
+    except RuntimeError as exc:
+        return {"skipped": str(exc)[:120]}
+    ctx.set_path(dq.PATH_FUSED)
+    ctx.plan_autotune(circ, st)
+    out = {"workload": f"dense_brickwall{n}_c64", "gates": len(gates), "run_gates": 17 * layers}
+    for name, mode in (("tiles_only", 0), ("dense_blocks", 1)):
+        ctx.set_option(dq.OPT_DENSE_BLOCKS, mode)
+        ctx.forward_grad(circ, params, obs, 1, torch.complex64, want_grad=False, state_out=st)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            ctx.forward_grad(circ, params, obs, 1, torch.complex64, want_grad=False, state_out=st)
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_step": a.elapsed_time(b) / 3}
+        if mode == 1:
+            ctx.set_tracing(True)
+            ctx.forward_grad(circ, params, obs, 1, torch.complex64, want_grad=False, state_out=st)
+            out[name]["kernels"] = {k: [v[0], round(v[1], 3)] for k, v in ctx.trace().items()}
+            ctx.set_tracing(False)
+    ctx.set_option(dq.OPT_DENSE_BLOCKS, 2)
+    ctx.set_path(dq.PATH_AUTO)
+    out["speedup"] = out["tiles_only"]["ms_per_step"] / out["dense_blocks"]["ms_per_step"]
+    del st
+    ctx.release_workspace()
+    torch.cuda.empty_cache()
+    return out
 
 
 def qft_tfim30(ctx, device):
@@ -925,7 +988,26 @@ def profile_case(args):
     ctx = dq.Context(0)
     iters = args.warmup + args.steps
     t0 = time.perf_counter()
-    if args.profile_case == "tile":          # C2 forward on the fused tile path
+    if args.profile_case == "c2":            # the headline step as the bench runs it (autotuned schedule)
+        wl = W.config_c2()
+        circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
+        obs = dq.Observables(wl.observables)
+        params = torch.tensor(wl.params, device=dev)
+        st = torch.empty((1, 1 << wl.n), dtype=torch.complex64, device=dev)
+        e = torch.empty((1, 1), dtype=torch.float64, device=dev)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+        ctx.plan_autotune(circ, st)
+        for _ in range(args.warmup):
+            ctx.forward_grad(circ, params, obs, 1, torch.complex64, want_grad=False, state_out=st, expect_out=e)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()          # profilers started with capture off record from here
+        for _ in range(args.steps):
+            flush.zero_()
+            ctx.forward_grad(circ, params, obs, 1, torch.complex64, want_grad=False, state_out=st, expect_out=e)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print("tuned (k, low, M):", ctx.plan_tuned(circ), flush=True)
+    elif args.profile_case == "tile":        # C2 forward on the fused tile path
         wl = W.config_c2()
         ctx.set_path(dq.PATH_FUSED)
         circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
@@ -993,10 +1075,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", choices=["auto", "plain", "fused"], default="auto")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--extras", default="all", help="comma-separated extra workloads to run (default: all)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="issue kernels one by one (no CUDA-graph replay)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--profile-case", choices=["tile", "wsv", "sweep", "c5", "dense", "sample", "hessian"], default=None,
+    ap.add_argument("--profile-case", choices=["c2", "tile", "wsv", "sweep", "c5", "dense", "sample", "hessian"],
+                    default=None,
                     help="run one kernel family's workload for profiling and exit")
     args = ap.parse_args()
     if args.profile_case:

@@ -11,8 +11,8 @@
 //
 // with M = 128 (output floats l), K = 128 (input floats p) and N = 64 state
 // rows per tile.  W and each S tile are split into TF32 parts x ~ hi + lo
-// (hi the nearest TF32 value, lo the nearest TF32 value of the remainder, so
-// |x - hi - lo| <= 2^-22 |x|) and D = W_hi S_hi + W_lo S_hi + W_hi S_lo is
+// (hi the nearest TF32 value, lo the nearest TF32 value of the remainder,
+// ties away from zero, so |x - hi - lo| <= 2^-22 |x|) and D = W_hi S_hi + W_lo S_hi + W_hi S_lo is
 // accumulated in FP32 in tensor memory: FP32-level accuracy from TF32
 // tensor-core products (the three-pass TF32 scheme; the dropped W_lo S_lo
 // term is below 2^-22 of each product).
