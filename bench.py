@@ -492,7 +492,7 @@ def kernel_bytes(n, gates, passes, amp=8):
     multi-pass kernel does so once per pass, the state preparation writes it
     once, a per-gate expectation pass reads it once."""
     full = (1 << n) * amp
-    out = {"k_tile_fwd": 2 * full, "k_init_zero": full, "k_expect": full}
+    out = {"k_tile_fwd": 2 * full, "k_tile_fwd_jit": 2 * full, "k_init_zero": full, "k_expect": full}
     if passes:
         out["k_tile_multi"] = 2 * full * passes
     return out
@@ -513,6 +513,8 @@ def source_fingerprint(files):
 TRAFFIC_RECORDS = {
     "k_tile_multi": ("k_tile_multi_c2_hea20.md", ["k_tile.cu", "dq_engine.cuh", "dq_tma.cuh", "dq_common.cuh"]),
     "k_tile_fwd": ("k_tile_fwd_c2_hea20.md", ["k_tile.cu", "dq_engine.cuh", "dq_tma.cuh", "dq_common.cuh"]),
+    "k_tile_fwd_jit": ("k_tile_fwd_jit_c2_hea20.md", ["jit.cu", "dq_tile_fwd.cuh", "dq_engine.cuh", "dq_tma.cuh",
+                                                      "dq_common.cuh"]),
 }
 
 

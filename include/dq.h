@@ -48,8 +48,10 @@
 #ifndef DQ_H_INCLUDED
 #define DQ_H_INCLUDED
 
+#ifndef __CUDACC_RTC__   /* run-time compiled kernels bring their own integer types */
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #if defined(__GNUC__)
 #define DQ_API __attribute__((visibility("default")))
@@ -205,8 +207,16 @@ DQ_API dq_status dq_ctx_set_path(dq_ctx *ctx, int path);
  *   (disjoint wires) move past it, the rest run as tile passes.  0: never;
  *   1: whenever the circuit has such a run; 2: when dq_plan_autotune measured
  *   the blocks faster for this circuit.  Gradient calls always run gate by
- *   gate (the adjoint sweep needs every gate's generator). */
-enum dq_option { DQ_OPT_MULTIPASS = 1, DQ_OPT_WAIT_LIMIT_US = 2, DQ_OPT_DENSE_BLOCKS = 3 };
+ *   gate (the adjoint sweep needs every gate's generator).
+ * DQ_OPT_JIT (default 2): forward tile passes as run-time specialised
+ *   kernels -- each pass's ops compiled (NVRTC, loaded with the runtime's
+ *   library API) into direct calls of the same handlers the interpreting
+ *   kernel dispatches to, with every register position, control mask and
+ *   layout a literal; same arithmetic per element.  0: never; 1: always (the
+ *   schedule's passes are compiled on first use, which takes seconds); 2: when
+ *   dq_plan_autotune measured them faster for this circuit.  Without NVRTC,
+ *   or if a compile fails, the interpreting kernel runs. */
+enum dq_option { DQ_OPT_MULTIPASS = 1, DQ_OPT_WAIT_LIMIT_US = 2, DQ_OPT_DENSE_BLOCKS = 3, DQ_OPT_JIT = 4 };
 
 /* Set a context option; DQ_ERR_INVALID_ARG for an unknown option or value.
  * Captured graphs of the context are dropped (the next calls capture anew). */
@@ -614,6 +624,23 @@ DQ_API dq_status dq_lower_circuit(const dq_circuit *circuit, int density, dq_low
 DQ_API dq_status dq_tile_schedule(const dq_circuit *circuit, int dtype, int k, int low, int M, int adjoint,
                                   int capacity, int32_t *order, int32_t *pass_start, uint64_t *tile_bits,
                                   int32_t *op_flags, int *npasses);
+
+/* Host-only (no context, no device): the source of the run-time specialised
+ * forward passes of the tile schedule (k, low, M) that dq_tile_schedule
+ * describes -- one op runner and one kernel per pass (DQ_OPT_JIT).  buf (may
+ * be NULL) receives the NUL-terminated text when cap exceeds its length;
+ * *len receives the length.  DQ_ERR_UNSUPPORTED when no schedule exists for
+ * the shape.  No counterpart in the paper (an implementation choice of this
+ * library). */
+DQ_API dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, int M, char *buf,
+                               size_t cap, size_t *len);
+
+/* Host-only: compile that source with NVRTC for compute capability cc (103
+ * for sm_103a) without loading it.  DQ_OK when it compiles; DQ_ERR_CUDA with
+ * the compiler log in `log` (cap bytes) when it does not;
+ * DQ_ERR_UNSUPPORTED when NVRTC cannot be opened. */
+DQ_API dq_status dq_jit_compile_check(const dq_circuit *circuit, int dtype, int k, int low, int M, int cc,
+                                      char *log, size_t cap);
 
 /* The program of the whole-row kernel (the fused path for rows of up to 16
  * qubits held on chip) for the pure circuit's lowered ops: M register bits

@@ -22,7 +22,7 @@ STATUS = {0: "DQ_OK", 1: "DQ_ERR_INVALID_ARG", 2: "DQ_ERR_UNSUPPORTED", 3: "DQ_E
           4: "DQ_ERR_CUDA", 5: "DQ_ERR_TIMEOUT"}
 DQ_C64, DQ_C128 = 0, 1
 PATH_AUTO, PATH_PLAIN, PATH_FUSED = 0, 1, 2
-OPT_MULTIPASS, OPT_WAIT_LIMIT_US, OPT_DENSE_BLOCKS = 1, 2, 3
+OPT_MULTIPASS, OPT_WAIT_LIMIT_US, OPT_DENSE_BLOCKS, OPT_JIT = 1, 2, 3, 4
 ADJ_CLOBBER_STATE = 1
 
 KIND = {k: i for i, k in enumerate(
@@ -69,7 +69,8 @@ class dq_lowered_op(ctypes.Structure):
 
 
 EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path", "dq_ctx_set_option",
-           "dq_state_norm", "dq_selftest_wait_expiry", "dq_batch_autotune",
+           "dq_state_norm", "dq_selftest_wait_expiry", "dq_batch_autotune", "dq_jit_source",
+           "dq_jit_compile_check",
            "dq_ctx_set_workspace",
            "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_graphs", "dq_ctx_set_tracing",
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
@@ -101,6 +102,8 @@ def load_library(path: str = LIB_PATH):
         "dq_ctx_set_path": ([P, I], I),
         "dq_ctx_set_option": ([P, I, ctypes.c_int64], I),
         "dq_state_norm": ([P, I, P, I, I, P, P], I),
+        "dq_jit_source": ([C, I, I, I, I, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], I),
+        "dq_jit_compile_check": ([C, I, I, I, I, I, ctypes.c_char_p, ctypes.c_size_t], I),
         "dq_batch_autotune": ([P, I, C, P, ctypes.POINTER(ctypes.c_int64), O, I, P, P,
                                ctypes.POINTER(ctypes.c_int), P], I),
         "dq_selftest_wait_expiry": ([P, P], I),
@@ -340,6 +343,28 @@ def tile_schedule(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C6
              [int(x) for x in flags[start[p]:start[p + 1]]]) for p in range(npass.value)]
 
 
+def jit_source(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64) -> str:
+    """The run-time specialised forward passes of a tile schedule
+    (dq_jit_source): CUDA source, one op runner and kernel per pass."""
+    lib = load_library()
+    n = ctypes.c_size_t(0)
+    _inspect_check(lib.dq_jit_source(circuit.ref(), int(dtype), int(k), int(low), int(M), None, 0,
+                                     ctypes.byref(n)), "dq_jit_source")
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _inspect_check(lib.dq_jit_source(circuit.ref(), int(dtype), int(k), int(low), int(M), buf, n.value + 1,
+                                     ctypes.byref(n)), "dq_jit_source")
+    return buf.value.decode()
+
+
+def jit_compile_check(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64, cc: int = 103):
+    """dq_jit_compile_check: (status, compiler log) of compiling the
+    specialised passes with NVRTC for compute capability cc (no device)."""
+    lib = load_library()
+    log = ctypes.create_string_buffer(4096)
+    st = lib.dq_jit_compile_check(circuit.ref(), int(dtype), int(k), int(low), int(M), int(cc), log, 4096)
+    return int(st), log.value.decode(errors="replace")
+
+
 def row_program(circuit: Circuit, M: int = 0, dtype: int = DQ_C64) -> Tuple[int, List[int], List[int]]:
     """The whole-row kernel's program for ``circuit`` (dq_row_program):
     (register bits used, lowered-op index of every entry in execution order,
@@ -413,7 +438,7 @@ class Context:
         self.path = int(path)
 
     def set_option(self, option: int, value: int):
-        """dq_ctx_set_option (OPT_MULTIPASS, OPT_WAIT_LIMIT_US, OPT_DENSE_BLOCKS)."""
+        """dq_ctx_set_option (OPT_MULTIPASS, OPT_WAIT_LIMIT_US, OPT_DENSE_BLOCKS, OPT_JIT)."""
         self._check(self.lib.dq_ctx_set_option(self.h, int(option), int(value)), "dq_ctx_set_option")
 
     def selftest_wait_expiry(self):

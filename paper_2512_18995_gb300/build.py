@@ -29,7 +29,37 @@ def _nvcc() -> str:
 def cuda_flags():
     return [ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
             "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-            f"-I{INCLUDE}", f"-I{CSRC}"]
+            f"-I{INCLUDE}", f"-I{CSRC}", f"-I{BUILD}"]
+
+
+# Device headers the run-time specialised kernels are compiled from (csrc/jit.cu
+# hands their texts to NVRTC as in-memory headers).
+JIT_HEADERS = [(os.path.join(INCLUDE, "dq.h"), "dq.h")] + [
+    (os.path.join(CSRC, h), h) for h in ("dq_common.cuh", "dq_engine.cuh", "dq_tma.cuh", "dq_tile_fwd.cuh",
+                                         "dq_devterm.h")]
+
+
+def write_jit_headers():
+    """_build/jit_headers.inc: the device headers as C++ raw strings."""
+    os.makedirs(BUILD, exist_ok=True)
+    out = ["// generated by build.py from the device headers; do not edit", ""]
+    names, texts = [], []
+    for path, name in JIT_HEADERS:
+        text = open(path).read()
+        if ")DQJIT\"" in text:
+            raise RuntimeError(f"{name} contains the raw-string delimiter")
+        names.append(f'"{name}"')
+        texts.append('R"DQJIT(' + text + ')DQJIT"')
+    out.append(f"static const int kJitHeaderCount = {len(names)};")
+    out.append("static const char *const kJitHeaderNames[] = {" + ", ".join(names) + "};")
+    out.append("static const char *const kJitHeaderTexts[] = {")
+    out.append(",\n".join(texts))
+    out.append("};")
+    data = "\n".join(out) + "\n"
+    target = os.path.join(BUILD, "jit_headers.inc")
+    if not os.path.exists(target) or open(target).read() != data:
+        with open(target, "w") as f:
+            f.write(data)
 
 
 def _sources():
@@ -52,6 +82,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    write_jit_headers()
     nvcc = _nvcc()
 
     def compile_one(src):

@@ -18,6 +18,7 @@
 #include "dq.h"
 #include "dq_common.cuh"
 #include "dq_dense.h"
+#include "dq_jit.h"
 #include "dq_density.h"
 #include "dq_hessian.h"
 #include "dq_sample.h"
@@ -1300,6 +1301,7 @@ dq_status dq_ctx_create(dq_ctx **out, int device) {
                    cudaMemcpyHostToDevice) != cudaSuccess)
         return DQ_ERR_CUDA;
     c->tiles.errflag = c->d_flag;
+    c->tiles.device = device;
     c->tiles.gridbar = reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(c->d_flag) + kFlagGridBarOffset);
     *out = c.release();
     return DQ_OK;
@@ -1344,6 +1346,10 @@ dq_status dq_ctx_set_option(dq_ctx *ctx, int option, int64_t value) {
     case DQ_OPT_MULTIPASS:
         if (value != 0 && value != 1) return fail(ctx, DQ_ERR_INVALID_ARG, "DQ_OPT_MULTIPASS takes 0 or 1");
         ctx->tiles.multi_on = value != 0;
+        break;
+    case DQ_OPT_JIT:
+        if (value < 0 || value > 2) return fail(ctx, DQ_ERR_INVALID_ARG, "DQ_OPT_JIT takes 0, 1 or 2");
+        ctx->tiles.jit_mode = (int)value;
         break;
     case DQ_OPT_DENSE_BLOCKS:
         if (value < 0 || value > 2) return fail(ctx, DQ_ERR_INVALID_ARG, "DQ_OPT_DENSE_BLOCKS takes 0, 1 or 2");
@@ -2523,6 +2529,58 @@ dq_status dq_tile_schedule(const dq_circuit *circuit, int dtype, int k, int low,
     }
     pass_start[sc.passes.size()] = pos;
     *npasses = (int)sc.passes.size();
+    return DQ_OK;
+}
+
+namespace {
+dq_status jit_schedule(const dq_circuit *circuit, int dtype, int k, int low, int M, TileSchedule &sc) {
+    Plan p;
+    int ncs = 0, ncr = 0;
+    const dq_status st = compile_gates(nullptr, circuit, 0, p.gates, p.bind, 0, &ncs, &ncr, false);
+    if (st != DQ_OK) return st;
+    p.n = circuit->nqubits;
+    p.ngates = (int)p.gates.size();
+    p.slot_of_gate.assign(p.gates.size(), -1);
+    const int amp = amp_bytes(dtype);
+    if (M < 2 || M > (dtype == DQ_C64 ? 5 : 4) || k > kTileMaxK || !tile_supported(p.n, amp))
+        return DQ_ERR_UNSUPPORTED;
+    if (!tile_build_schedule(p, k, low, M, amp, sc, false)) return DQ_ERR_UNSUPPORTED;
+    return DQ_OK;
+}
+}  // namespace
+
+dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, int M, char *buf, size_t cap,
+                        size_t *len) {
+    if (!circuit || !len) return DQ_ERR_INVALID_ARG;
+    if (dtype != DQ_C64 && dtype != DQ_C128) return DQ_ERR_INVALID_ARG;
+    TileSchedule sc;
+    dq_status st = jit_schedule(circuit, dtype, k, low, M, sc);
+    if (st != DQ_OK) return st;
+    std::vector<std::string> names;
+    const std::string src = jit_source(sc, amp_bytes(dtype), names);
+    *len = src.size();
+    if (buf) {
+        if (cap < src.size() + 1) return DQ_ERR_INVALID_ARG;
+        std::memcpy(buf, src.c_str(), src.size() + 1);
+    }
+    return DQ_OK;
+}
+
+dq_status dq_jit_compile_check(const dq_circuit *circuit, int dtype, int k, int low, int M, int cc, char *log,
+                               size_t cap) {
+    if (!circuit) return DQ_ERR_INVALID_ARG;
+    if (dtype != DQ_C64 && dtype != DQ_C128) return DQ_ERR_INVALID_ARG;
+    if (log && cap) log[0] = 0;
+    TileSchedule sc;
+    dq_status st = jit_schedule(circuit, dtype, k, low, M, sc);
+    if (st != DQ_OK) return st;
+    std::vector<std::string> names;
+    const std::string src = jit_source(sc, amp_bytes(dtype), names);
+    std::string err;
+    if (!jit_compile(src, cc, nullptr, &err)) {
+        if (log && cap) std::snprintf(log, cap, "%s", err.c_str());
+        return jit_available() ? DQ_ERR_CUDA : DQ_ERR_UNSUPPORTED;
+    }
     return DQ_OK;
 }
 

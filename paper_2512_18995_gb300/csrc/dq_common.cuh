@@ -5,8 +5,10 @@
 // complex amplitude is float2 (DQ_C64) or double2 (DQ_C128).
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 #include "dq.h"
 

@@ -14,12 +14,14 @@
 // single switch into straight-line code.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
 #include <unordered_map>
 #include <vector>
+#endif
 
 #include "dq_common.cuh"
 
@@ -92,6 +94,7 @@ struct ESeg {
     int8_t B[8];
 };
 
+#ifndef __CUDACC_RTC__   // host-side decoding (not part of run-time compiled kernels)
 // Host decode of a gate against a layout with register bits B[0..M-1].
 inline EOp decode_op(const GOp &g, const int8_t *B, int M) {
     auto pos = [&](int j) {
@@ -405,6 +408,8 @@ inline bool pair_handlers_match(const EOp &real, const EOp &diag) {
                                   diag.cmc == ~0u;
     return false;
 }
+
+#endif  // __CUDACC_RTC__
 
 struct Layout {
     uint32_t tb;     // this thread's local index with register bits zero

@@ -1,0 +1,32 @@
+// Run-time specialised forward tile passes (internal interface).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+namespace dq {
+
+struct TileSchedule;
+
+// The compiled passes of one schedule (one library, one kernel per pass).
+struct JitModule {
+    std::vector<cudaLibrary_t> libs;   // one per chunk of passes
+    std::vector<cudaKernel_t> kernels;
+    std::vector<int> grid;        // launch grid per pass for the last state buffer (0: not computed)
+    std::vector<size_t> smem_set; // dynamic shared memory the kernel was opened up to
+    void release();
+};
+
+bool jit_available();
+// Source of the schedule's specialised passes [p0, p1) (all: p1 < 0); names
+// receives the kernels'.
+std::string jit_source(const TileSchedule &sc, int amp, std::vector<std::string> &names, int p0 = 0, int p1 = -1);
+// Compile a source of jit_source for compute capability cc (e.g. 103 for
+// sm_103a); cubin may be null (compile check only).
+bool jit_compile(const std::string &src, int cc, std::vector<char> *cubin, std::string *err);
+// Compile and load every pass of sc for `device` (sc.jit); false with *err on failure.
+bool jit_build(TileSchedule &sc, int amp, int device, std::string *err);
+
+}  // namespace dq

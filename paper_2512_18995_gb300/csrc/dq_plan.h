@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "dq.h"
+#include "dq_devterm.h"
 
 namespace dq {
 
@@ -41,15 +42,6 @@ struct BindGate {
 // from the plan's table, uncontrolled or controlled (c = control bit).
 constexpr int kKindFixed = 64;
 constexpr int kKindCFixed = 65;
-
-// One Pauli term in bit space.
-struct DevTerm {
-    uint64_t f;         // flip mask (bit space)
-    uint64_t s;         // sign mask (bit space)
-    int32_t nY;         // number of Y factors
-    int32_t obs;        // observable index
-    double coeff;
-};
 
 // Compiled circuit (cached by structure).
 struct Plan {

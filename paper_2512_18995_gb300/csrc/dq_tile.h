@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -74,6 +75,10 @@ struct TileSchedule {
     std::vector<CUtensorMap> adj_psi, adj_lam;
     const void *adj_p = nullptr, *adj_l = nullptr;
     int adj_batch = -1;
+    // run-time specialised passes (null: not compiled; jit_failed: compiling
+    // failed once, the interpreter stays in use)
+    struct JitModule *jit = nullptr;
+    bool jit_failed = false;
     // launch data of the persistent multi-pass kernel (chunks of passes) for
     // the last state buffer seen
     void *multi = nullptr;
@@ -89,6 +94,7 @@ struct TileTune {
     int low = 0;        // always-resident low bits
     int M = 0;          // register bits per thread
     int dense = 0;      // 1: runs of gates on the six lowest-order bits go to tensor-core dense blocks
+    int jit = 0;        // 1: forward passes run as run-time specialised kernels
 };
 
 // Host-side cache of schedules and the driver entry point used to encode
@@ -98,6 +104,9 @@ struct TileCache {
     int *errflag = nullptr;             // device error flag of the owning context
     unsigned int *gridbar = nullptr;    // arrival counter of the multi-pass kernel's grid barrier (device)
     bool multi_on = true;               // run all forward passes of an L2-resident state in one launch
+    int jit_mode = 2;                   // DQ_OPT_JIT: 0 never, 1 always, 2 when the autotuner measured it faster
+    int device = 0;                     // the owning context's device
+    std::string jit_err;                // why the last run-time compile failed (empty: none)
     std::unordered_map<uint64_t, TileSchedule *> schedules;
     std::unordered_map<uint64_t, void *> obs;   // observable-pass schedules
     std::unordered_map<const void *, size_t> smem_set;   // dynamic shared memory limit set per kernel

@@ -2,6 +2,7 @@
 // (internal).
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -13,9 +14,17 @@
 
 #include "dq_common.cuh"
 #include "dq_tile.h"
+#else
+#include "dq_common.cuh"
+// Run-time compiled kernels receive tensor maps by value; the layout is the
+// driver's opaque 128-byte, 128-byte-aligned descriptor.
+typedef struct alignas(128) CUtensorMap_st { unsigned long long opaque[16]; } CUtensorMap;
+#endif
 
 namespace dq {
 namespace {
+
+#ifndef __CUDACC_RTC__   // host-side descriptor encoding
 
 // ---------------------------------------------------------------------------
 // TMA descriptor for one pass
@@ -85,6 +94,8 @@ inline bool encode_map(void *fn, CUtensorMap *map, const TileDims &d, void *base
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return res == CUDA_SUCCESS;
 }
+
+#endif  // __CUDACC_RTC__
 
 // ---------------------------------------------------------------------------
 // device helpers: mbarrier and TMA
@@ -168,6 +179,7 @@ struct TileGeom {
     int rlen[5], glen[5], s[5];
 };
 
+#ifndef __CUDACC_RTC__
 inline TileGeom make_geom(const TileDims &d, int n, int k, int wb, int64_t batch) {
     TileGeom g;
     g.n = n;
@@ -182,6 +194,8 @@ inline TileGeom make_geom(const TileDims &d, int n, int k, int wb, int64_t batch
     }
     return g;
 }
+
+#endif  // __CUDACC_RTC__
 
 __device__ __forceinline__ void geom_coords(const TileGeom &a, int64_t t, int c[5], uint64_t &base, int64_t &row) {
     uint64_t rem = (uint64_t)t;
@@ -207,6 +221,7 @@ __device__ __forceinline__ void geom_coords(const TileGeom &a, int64_t t, int c[
     base = amp & ((uint64_t(1) << a.n) - 1);
 }
 
+#ifndef __CUDACC_RTC__
 inline bool ensure_encode_fn(TileCache &tc) {
     if (tc.encode_fn) return true;
     void *fn = nullptr;
@@ -220,9 +235,7 @@ inline bool ensure_encode_fn(TileCache &tc) {
     return true;
 }
 
-// Default tile: HBM-resident states (>= 2^25 amplitudes) take wide tiles and
-// wide register sets; L2-resident ones take narrower tiles and more warps per
-// tile so that every SM has work.
+#endif  // __CUDACC_RTC__
 
 }  // namespace
 }  // namespace dq

@@ -1,0 +1,302 @@
+// Run-time specialised forward tile passes.
+//
+// The forward tile kernel interprets each pass's op program from shared
+// memory: per op it reads the decoded record, dispatches on its handler and
+// forms control masks at run time.  For a circuit that runs many times the
+// same passes can be compiled instead: this file writes, for every pass of a
+// schedule, an op runner whose body is the pass's ops as direct calls into
+// the engine's handlers (dq_engine.cuh) with every register position,
+// control mask, lane bit and layout as a literal, instantiates the shared
+// kernel body (dq_tile_fwd.cuh) with it, compiles all passes of the schedule
+// in one NVRTC program for the device's architecture and loads the result
+// with the runtime's library API.  The arithmetic per element is the
+// interpreter's; only the dispatch is gone.  NVRTC is opened with dlopen on
+// first use: without it the interpreter simply stays in use.
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <vector>
+#include <algorithm>
+
+#include "dq_jit.h"
+#include "dq_tile.h"
+#include "jit_headers.inc"   // generated by build.py: the device headers' texts
+
+namespace dq {
+
+namespace {
+
+struct NvrtcApi {
+    bool ok = false;
+    nvrtcResult (*create)(nvrtcProgram *, const char *, const char *, int, const char *const *,
+                          const char *const *) = nullptr;
+    nvrtcResult (*compile)(nvrtcProgram, int, const char *const *) = nullptr;
+    nvrtcResult (*log_size)(nvrtcProgram, size_t *) = nullptr;
+    nvrtcResult (*log)(nvrtcProgram, char *) = nullptr;
+    nvrtcResult (*cubin_size)(nvrtcProgram, size_t *) = nullptr;
+    nvrtcResult (*cubin)(nvrtcProgram, char *) = nullptr;
+    nvrtcResult (*destroy)(nvrtcProgram *) = nullptr;
+};
+
+NvrtcApi &nvrtc_api() {
+    static NvrtcApi api;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *h = nullptr;
+        for (const char *name : {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13"}) {
+            h = dlopen(name, RTLD_NOW | RTLD_LOCAL);
+            if (h) break;
+        }
+        if (!h) return;
+        api.create = reinterpret_cast<decltype(api.create)>(dlsym(h, "nvrtcCreateProgram"));
+        api.compile = reinterpret_cast<decltype(api.compile)>(dlsym(h, "nvrtcCompileProgram"));
+        api.log_size = reinterpret_cast<decltype(api.log_size)>(dlsym(h, "nvrtcGetProgramLogSize"));
+        api.log = reinterpret_cast<decltype(api.log)>(dlsym(h, "nvrtcGetProgramLog"));
+        api.cubin_size = reinterpret_cast<decltype(api.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
+        api.cubin = reinterpret_cast<decltype(api.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
+        api.destroy = reinterpret_cast<decltype(api.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+        api.ok = api.create && api.compile && api.log_size && api.log && api.cubin_size && api.cubin && api.destroy;
+    });
+    return api;
+}
+
+std::string hex32(uint32_t v) {
+    char b[16];
+    std::snprintf(b, sizeof(b), "0x%08xu", v);
+    return b;
+}
+
+// The control mask expression of an op in its layout (the interpreter's
+// op_cmask with the mode resolved).
+std::string cmask_expr(const EOp &o) {
+    if (o.cmode == 0) return hex32(o.cmc);
+    if (o.cmode == 1) return "(((L.tb >> " + std::to_string((int)o.carg) + ") & 1u) ? ~0u : 0u)";
+    return "(((base >> " + std::to_string((int)o.carg) + ") & 1ull) ? ~0u : 0u)";
+}
+
+// An EOp literal for the handlers that read its fields.
+std::string eop_literal(const EOp &o) {
+    std::ostringstream s;
+    s << "EOp o{}; o.h = " << o.h << "; o.kind = " << o.kind << "; o.cmc = " << hex32(o.cmc)
+      << "; o.cmode = " << (int)o.cmode << "; o.carg = " << (int)o.carg << "; o.tmode = " << (int)o.tmode
+      << "; o.targ = " << (int)o.targ << ";";
+    return s.str();
+}
+
+// One op of a pass (index i in the pass's op list); returns the number of
+// ops it stands for (a controlled-phase fan consumes its members).
+int emit_op(std::ostringstream &s, const EOp *ops, int i, int nops, bool pd) {
+    const EOp &o = ops[i];
+    const std::string u = "scoef[" + std::to_string(i) + "]";
+    const int h = o.h;
+    if (h < H_GEN) {
+        s << "        pairs_at<R, M, " << h - H_REAL << ", CLS_REAL>(r, " << u << ");\n";
+        return 1;
+    }
+    if (h >= H_DIAG && h < H_CREAL) {
+        s << "        diag_at<R, M, " << h - H_DIAG << ">(r, " << u << ");\n";
+        return 1;
+    }
+    if (h == H_PDIAG) {
+        if (pd) s << "        { " << eop_literal(o) << " eng_pdiag<R, M>(r, o, " << u << ", base, L); }\n";
+        return 1;
+    }
+    if (h == H_FAN) {
+        s << "        eng_fan<R, M>(r, sops + " << i << ", scoef + " << i << ", base, L);\n";
+        return std::max(1, (int)o.pad[0]);
+    }
+    if (h >= H_FAN) return 1;   // a fan member outside its fan (not produced by the planner)
+    if (o.cmode == 0 && o.cmc == 0) return 1;   // the control is never set in this layout
+    std::string call;
+    if (h >= H_GEN && h < H_ANTI)
+        call = "pairs_sel<R, M, " + std::to_string(h - H_GEN) + ", CLS_GENERAL>(r, " + u + ", cm)";
+    else if (h >= H_ANTI && h < H_DIAG)
+        call = "pairs_sel<R, M, " + std::to_string(h - H_ANTI) + ", CLS_ANTI>(r, " + u + ", cm)";
+    else if (h >= H_CREAL && h < H_CDIAG)
+        call = "pairs_sel<R, M, " + std::to_string(h - H_CREAL) + ", CLS_REAL>(r, " + u + ", cm)";
+    else if (h >= H_CDIAG && h < H_LREAL)
+        call = "diag_sel<R, M, " + std::to_string(h - H_CDIAG) + ">(r, " + u + ", cm)";
+    else if (h == H_LREAL || h == H_LGEN || h == H_LANTI)
+        call = std::string("lane_at<R, M, ") + (h == H_LREAL ? "CLS_REAL" : h == H_LGEN ? "CLS_GENERAL" : "CLS_ANTI") +
+               ">(r, " + u + ", " + std::to_string((int)o.targ) + ", lane, cm)";
+    else
+        call = "diag_uni<R, M>(r, " + u + ", o, L, base, cm)";
+    s << "        { const uint32_t cm = " << cmask_expr(o) << ";";
+    if (h == H_DUNI) s << " " << eop_literal(o);
+    if (o.cmode != 0) s << " if (!__all_sync(0xffffffffu, cm == 0u))";
+    s << " " << call << "; }\n";
+    return 1;
+}
+
+}  // namespace
+
+// Source of passes [p0, p1) of the schedule (all when p1 < 0): op runner +
+// kernel per pass.
+std::string jit_source(const TileSchedule &sc, int amp, std::vector<std::string> &names, int p0, int p1) {
+    if (p1 < 0) p1 = (int)sc.passes.size();
+    const char *R = amp == 16 ? "double" : "float";
+    const int M = sc.M;
+    const int cxb = amp;   // bytes of one amplitude
+    const int maxt = ((1 << M) * cxb >= 256) ? 256 : 512;
+    const int minb = ((1 << M) * cxb <= 64) ? 2 : 1;
+    std::ostringstream s;
+    s << "typedef signed char int8_t; typedef unsigned char uint8_t; typedef short int16_t;\n"
+         "typedef unsigned short uint16_t; typedef int int32_t; typedef unsigned int uint32_t;\n"
+         "typedef long long int64_t; typedef unsigned long long uint64_t; typedef unsigned long long uintptr_t;\n"
+         "#include \"dq_tile_fwd.cuh\"\n"
+         "namespace dq {\nnamespace {\n";
+    for (int p = p0; p < p1; ++p) {
+        const TPass &ps = sc.passes[p];
+        const EOp *ops = sc.ops.data() + ps.op0;
+        s << "struct JitPass" << p << " {\n"
+             "    template <typename R, int M, bool PD>\n"
+             "    __device__ __forceinline__ static void run(cx<R> (&r)[1 << M], cx<R> *cur, const EOp *sops,\n"
+             "        const ESeg *, const Mat2<R> *scoef, int, int, int, uint64_t base, int lane, int warp) {\n";
+        for (int si = ps.seg0; si < ps.seg0 + ps.nseg; ++si) {
+            const TSeg &sg = sc.segs[si];
+            s << "    {\n        ESeg sg{}; ";
+            for (int b = 0; b < M; ++b) s << "sg.B[" << b << "] = " << (int)sg.B[b] << "; ";
+            s << "\n        const Layout L = make_layout(sg, M, " << sc.k << ", lane, warp);\n"
+                 "        eng_load<R, M>(r, cur, L);\n";
+            for (int i = sg.op0 - ps.op0; i < sg.op0 - ps.op0 + sg.nops;)
+                i += emit_op(s, ops, i, ps.nops, ps.pdiag);
+            s << "        eng_store<R, M>(r, cur, L);\n        __syncthreads();\n    }\n";
+        }
+        s << "    }\n};\n";
+    }
+    s << "}  // namespace\n}  // namespace dq\n";
+    names.clear();
+    for (int p = p0; p < p1; ++p) {
+        const std::string name = "dq_jit_fwd_" + std::to_string(p);
+        names.push_back(name);
+        s << "extern \"C\" __global__ void __launch_bounds__(" << maxt << ", " << minb << ") " << name
+          << "(const __grid_constant__ CUtensorMap tmap, dq::TileKArgs a) {\n"
+          << "    dq::tile_fwd_body<" << R << ", " << M << ", " << (sc.passes[p].pdiag ? "true" : "false")
+          << ", dq::JitPass" << p << ">(tmap, a);\n}\n";
+    }
+    return s.str();
+}
+
+void JitModule::release() {
+    for (cudaLibrary_t l : libs) cudaLibraryUnload(l);
+    libs.clear();
+    kernels.clear();
+}
+
+bool jit_available() { return nvrtc_api().ok; }
+
+bool jit_compile(const std::string &src, int cc, std::vector<char> *cubin, std::string *err) {
+    NvrtcApi &api = nvrtc_api();
+    if (!api.ok) {
+        if (err) *err = "NVRTC is not available";
+        return false;
+    }
+    const std::string arch = "-arch=sm_" + std::to_string(cc) + "a";
+    nvrtcProgram prog;
+    if (api.create(&prog, src.c_str(), "dq_jit_fwd.cu", kJitHeaderCount, kJitHeaderTexts, kJitHeaderNames) !=
+        NVRTC_SUCCESS) {
+        if (err) *err = "nvrtcCreateProgram failed";
+        return false;
+    }
+    const char *opts[] = {arch.c_str(), "-std=c++17", "-default-device", "-lineinfo"};
+    const nvrtcResult cr = api.compile(prog, 4, opts);
+    if (cr != NVRTC_SUCCESS) {
+        size_t n = 0;
+        api.log_size(prog, &n);
+        std::string log(n + 1, '\0');
+        api.log(prog, &log[0]);
+        if (err) *err = "NVRTC compile failed: " + log.substr(0, 2000);
+        api.destroy(&prog);
+        return false;
+    }
+    if (cubin) {
+        size_t n = 0;
+        api.cubin_size(prog, &n);
+        cubin->resize(n);
+        api.cubin(prog, cubin->data());
+    }
+    api.destroy(&prog);
+    return true;
+}
+
+bool jit_build(TileSchedule &sc, int amp, int device, std::string *err) {
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+    const int np = (int)sc.passes.size();
+    if (np == 0) {
+        if (err) *err = "empty schedule";
+        return false;
+    }
+    // passes split into chunks compiled by concurrent NVRTC programs
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nchunk = std::max(1, std::min({np, 8, (int)hw}));
+    const int per = (np + nchunk - 1) / nchunk;
+    struct Chunk {
+        int p0 = 0, p1 = 0;
+        std::vector<std::string> names;
+        std::vector<char> cubin;
+        std::string err;
+        bool ok = false;
+    };
+    std::vector<Chunk> chunks;
+    for (int p0 = 0; p0 < np; p0 += per) {
+        Chunk c;
+        c.p0 = p0;
+        c.p1 = std::min(np, p0 + per);
+        chunks.push_back(c);
+    }
+    std::vector<std::thread> workers;
+    for (Chunk &c : chunks)
+        workers.emplace_back([&sc, amp, &c, major, minor] {
+            const std::string src = jit_source(sc, amp, c.names, c.p0, c.p1);
+            c.ok = jit_compile(src, major * 10 + minor, &c.cubin, &c.err);
+        });
+    for (std::thread &t : workers) t.join();
+    for (const Chunk &c : chunks)
+        if (!c.ok) {
+            if (err) *err = c.err;
+            return false;
+        }
+    JitModule *m = new JitModule();
+    for (const Chunk &c : chunks) {
+        cudaLibrary_t lib = nullptr;
+        cudaError_t e = cudaLibraryLoadData(&lib, c.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            m->release();
+            delete m;
+            if (err) *err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);
+            return false;
+        }
+        m->libs.push_back(lib);
+        for (const std::string &name : c.names) {
+            cudaKernel_t k = nullptr;
+            e = cudaLibraryGetKernel(&k, lib, name.c_str());
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                m->release();
+                delete m;
+                if (err) *err = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e);
+                return false;
+            }
+            m->kernels.push_back(k);
+        }
+    }
+    m->grid.assign(m->kernels.size(), 0);
+    m->smem_set.assign(m->kernels.size(), 0);
+    if (sc.jit) {
+        sc.jit->release();
+        delete sc.jit;
+    }
+    sc.jit = m;
+    return true;
+}
+
+}  // namespace dq

@@ -28,12 +28,19 @@
 #include "dq_engine.cuh"
 #include "dq_tile.h"
 #include "dq_tma.cuh"
+#include "dq_tile_fwd.cuh"
+#include "dq_jit.h"
 
 namespace dq {
 
 static void release_multi(void *p);
 
 void TileSchedule::release() {
+    if (jit) {
+        jit->release();
+        delete jit;
+        jit = nullptr;
+    }
     release_multi(multi);
     multi = nullptr;
     multi_state = nullptr;
@@ -319,227 +326,10 @@ bool tile_build_schedule(const Plan &p, int k, int low, int M, int amp_bytes, Ti
 
 namespace {
 
-// Diagonal observables measured on the last pass's tiles (Z strings): the
-// pass's tile bits map each term's sign mask to tile-local and block parts.
-struct TileEpi {
-    const DevTerm *terms;   // device, all terms diagonal
-    int nterms;
-    double *part;           // [term][row][cta]
-    int batch;
-    int8_t T[16];           // tile bit -> amplitude bit
-};
-
-struct TileKArgs {
-    const TOp *ops;
-    const TSeg *segs;
-    int op0, nops, seg0, nseg;
-    const void *coef;
-    TileGeom g;
-    int *errflag;
-    int any_row;            // some op's coefficients depend on the batch row
-    TileEpi epi;            // epi.nterms == 0: none
-};
-
-struct ETerm {
-    uint32_t sloc;
-    uint32_t pad;
-    uint64_t sout;
-};
-
-// Threads per CTA are 2^(k - M); wide register sets (256 bytes of amplitudes
-// per thread) are limited to 256 threads so that they keep their registers.
-template <typename R, int M>
-constexpr int tile_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) >= 256) ? 256 : 512; }
-// Narrow register sets (<= 64 bytes of amplitudes per thread) are held to 64
-// registers, so that four 256-thread tiles fit on an SM.
-template <typename R, int M>
-constexpr int tile_min_blocks() { return ((1 << M) * (int)sizeof(cx<R>) <= 64) ? 2 : 1; }
-
-// The scheduled ops of one pass on one tile held in shared memory: per
-// layout segment, load the register set, run the segment's ops, store back.
-template <typename R, int M, bool PD>
-__device__ __forceinline__ void tile_run_ops(cx<R> (&r)[1 << M], cx<R> *cur, const TOp *sops, const TSeg *ssegs,
-                                             const Mat2<R> *scoef, int nseg, int op0, int k, uint64_t base,
-                                             int lane, int warp) {
-    for (int si = 0; si < nseg; ++si) {
-        const TSeg sg = ssegs[si];
-        const Layout L = make_layout(sg, M, k, lane, warp);
-        eng_load<R, M>(r, cur, L);
-        for (int oi = sg.op0 - op0; oi < sg.op0 - op0 + sg.nops; ++oi) {
-            const TOp o = sops[oi];
-            if (o.h == H_FAN) {
-                oi += eng_fan<R, M>(r, sops + oi, scoef + oi, base, L) - 1;
-                continue;
-            }
-            eng_apply<R, M, PD>(r, o, scoef[oi], base, L, lane);
-        }
-        // each thread writes back exactly the addresses it read in this
-        // layout; the barrier orders them before the next layout's reads
-        eng_store<R, M>(r, cur, L);
-        __syncthreads();
-    }
-}
-
-// Diagonal (Z-string) observables of one finished tile: per-warp FP32 sums
-// of signed probabilities, folded into the CTA's FP64 accumulators.
-template <typename R>
-__device__ __forceinline__ void tile_epi_accum(const cx<R> *cur, const ETerm *sterm, int nte, double *eacc,
-                                               R *eaccw, int k, uint64_t base, int tid, int lane, int warp,
-                                               int nw) {
-    const int dim = 1 << k;
-    for (int j = 0; j < nte; ++j) {
-        const ETerm et = sterm[j];
-        const int bpar = __popcll(base & et.sout) & 1;
-        R e = R(0);
-        for (int l = tid; l < dim; l += blockDim.x) {
-            const cx<R> x = cur[l];
-            const R pr = x.x * x.x + x.y * x.y;
-            e += ((__popc((uint32_t)l & et.sloc) & 1) ^ bpar) ? -pr : pr;
-        }
-        e = warp_sum_t(e);
-        if (lane == 0) eaccw[warp * nte + j] += e;
-    }
-    __syncthreads();
-    for (int j = tid; j < nte; j += blockDim.x) {
-        double sum = 0.0;
-        for (int ww = 0; ww < nw; ++ww) {
-            sum += (double)eaccw[ww * nte + j];
-            eaccw[ww * nte + j] = R(0);
-        }
-        eacc[j] += sum;
-    }
-}
-
-// Stage ETerm records of the diagonal observables for a pass whose tile bits
-// are T (tile-local sign bits and the sign bits outside the tile).
-__device__ __forceinline__ void tile_epi_setup(const TileEpi &epi, int k, ETerm *sterm, double *eacc, int tid) {
-    for (int j = tid; j < epi.nterms; j += blockDim.x) {
-        const uint64_t sm = epi.terms[j].s;
-        ETerm e{};
-        uint64_t in = 0;
-        for (int i = 0; i < k; ++i)
-            if ((sm >> epi.T[i]) & 1) {
-                e.sloc |= 1u << i;
-                in |= uint64_t(1) << epi.T[i];
-            }
-        e.sout = sm & ~in;
-        sterm[j] = e;
-        eacc[j] = 0.0;
-    }
-}
-
 template <typename R, int M, bool PD>
 __global__ void __launch_bounds__(tile_max_threads<R, M>(), tile_min_blocks<R, M>())
 k_tile_fwd(const __grid_constant__ CUtensorMap tmap, TileKArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const size_t tbytes = sizeof(cx<R>) << a.g.k;
-    const unsigned long long wlim = wait_limit_ns(a.errflag);
-    cx<R> *buf0 = reinterpret_cast<cx<R> *>(smem);
-    cx<R> *buf1 = reinterpret_cast<cx<R> *>(smem + tbytes);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * tbytes);
-    TOp *sops = reinterpret_cast<TOp *>(smem + 2 * tbytes + 64);
-    TSeg *ssegs = reinterpret_cast<TSeg *>(sops + a.nops);
-    Mat2<R> *scoef = reinterpret_cast<Mat2<R> *>(ssegs + a.nseg);
-    const int nte = a.epi.nterms, nw = blockDim.x >> 5;
-    ETerm *sterm = reinterpret_cast<ETerm *>(scoef + a.nops);     // [nte]
-    double *eacc = reinterpret_cast<double *>(sterm + nte);         // [nte]
-    R *eaccw = reinterpret_cast<R *>(eacc + nte);                   // [nw][nte]
-    const Mat2<R> *gcoef = reinterpret_cast<const Mat2<R> *>(a.coef);
-    const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * per;
-    const int64_t t1 = min(a.g.ntiles, t0 + per);
-    int c[5];
-    uint64_t base;
-    int64_t row;
-    // The pass's program (uploaded at planning time) is staged before waiting
-    // for the previous kernel of the stream (programmatic dependent launch:
-    // this prologue overlaps that kernel's tail); the state and the bound
-    // coefficients are read only after the wait.
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_async_smem();
-    }
-    for (int i = tid; i < a.nops; i += blockDim.x) sops[i] = a.ops[a.op0 + i];
-    for (int i = tid; i < a.nseg; i += blockDim.x) ssegs[i] = a.segs[a.seg0 + i];
-    grid_dep_wait();
-    if (tid == 0 && t0 < t1) {
-        geom_coords(a.g, t0, c, base, row);
-        mbar_expect_tx(&bar[0], (uint32_t)tbytes);
-        tma_load5(buf0, &tmap, c, &bar[0]);
-    }
-    for (int i = tid; i < a.nops; i += blockDim.x) scoef[i] = gcoef[sops[i].coef];
-    tile_epi_setup(a.epi, a.g.k, sterm, eacc, tid);
-    for (int i = tid; i < nw * nte; i += blockDim.x) eaccw[i] = R(0);
-    __syncthreads();
-    if (t0 >= t1) return;
-    int64_t erow = -1;
-    auto eflush = [&](int64_t rr) {
-        for (int j = tid; j < nte; j += blockDim.x) {
-            a.epi.part[((int64_t)j * a.epi.batch + rr) * gridDim.x + blockIdx.x] = eacc[j];
-            eacc[j] = 0.0;
-        }
-    };
-    uint32_t phase0 = 0, phase1 = 0;
-    int64_t crow = 0;   // the table holds row 0's coefficient blocks
-    cx<R> r[1 << M];
-    bool failed = false;
-    for (int64_t t = t0, i = 0; t < t1; ++t, ++i) {
-        const int b = (int)(i & 1);
-        cx<R> *cur = b ? buf1 : buf0;
-        if (tid == 0 && t + 1 < t1) {
-            int cn[5];
-            uint64_t bn;
-            int64_t rn;
-            geom_coords(a.g, t + 1, cn, bn, rn);
-            bulk_wait_read0();   // the other buffer's previous store has read its data
-            uint64_t *nb = b ? &bar[0] : &bar[1];
-            mbar_expect_tx(nb, (uint32_t)tbytes);
-            tma_load5(b ? buf0 : buf1, &tmap, cn, nb);
-        }
-        const bool ok = mbar_wait_bounded(b ? &bar[1] : &bar[0], b ? phase1 : phase0, wlim);
-        if (b) phase1 ^= 1; else phase0 ^= 1;
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        geom_coords(a.g, t, c, base, row);
-        if (a.any_row && row != crow) {
-            // row-dependent coefficient blocks of this tile's row into the table
-            for (int i = tid; i < a.nops; i += blockDim.x)
-                if (sops[i].rowstep) scoef[i] = gcoef[sops[i].coef + row * sops[i].rowstep];
-            __syncthreads();
-            crow = row;
-        }
-        tile_run_ops<R, M, PD>(r, cur, sops, ssegs, scoef, a.nseg, a.op0, a.g.k, base, lane, warp);
-        fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tma_store5(&tmap, c, cur);
-            bulk_commit();
-        }
-        if (nte) {
-            // diagonal observables of the final tile (read-only, beside the store)
-            if (row != erow) {
-                if (erow >= 0) eflush(erow);
-                erow = row;
-            }
-            tile_epi_accum<R>(cur, sterm, nte, eacc, eaccw, a.g.k, base, tid, lane, warp, nw);
-        }
-    }
-    grid_dep_launch();   // the next kernel of the stream may start its prologue
-    if (nte && !failed && erow >= 0) {
-        __syncthreads();
-        eflush(erow);
-    }
-    if (failed && tid == 0) {
-        atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
-        // let any load still in flight land before the CTA exits (bounded)
-        mbar_wait_bounded(&bar[0], phase0, wlim);
-        mbar_wait_bounded(&bar[1], phase1, wlim);
-    }
-    if (tid == 0) bulk_wait0();
+    tile_fwd_body<R, M, PD, InterpOps>(tmap, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -997,9 +787,10 @@ cudaError_t run_forward_multi(TileCache &tc, const Plan &p, TileSchedule &sc, co
 template <typename R>
 cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const void *coef, void *state,
                         int batch, int nsm, cudaStream_t s, int64_t *launches, const TileEpi *epi = nullptr,
-                        int *epi_grid = nullptr) {
+                        int *epi_grid = nullptr, bool use_jit = false) {
     const int M = sc.M;
-    if (multi_applies(tc, sc, p.n, batch, (int)sizeof(cx<R>)))
+    const bool jit = use_jit && sc.jit != nullptr;
+    if (!jit && multi_applies(tc, sc, p.n, batch, (int)sizeof(cx<R>)))
         return run_forward_multi<R>(tc, p, sc, coef, state, batch, nsm, s, launches, epi, epi_grid);
     constexpr int wb = TileCfg<R>::wb;
     const int amp = (int)sizeof(cx<R>);
@@ -1033,6 +824,7 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
         }
         sc.fwd_state = state;
         sc.fwd_batch = batch;
+        if (sc.jit) sc.jit->grid.assign(sc.passes.size(), 0);
     }
     for (size_t i = 0; i < sc.passes.size(); ++i) {
         const TPass &ps = sc.passes[i];
@@ -1043,16 +835,32 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
         a.epi = TileEpi{};
         size_t smem = L.smem;
         int grid = L.grid;
-        const void *kfn = tile_kernel<R>(M, ps.pdiag);
+        const void *kfn = jit ? (const void *)sc.jit->kernels[i] : tile_kernel<R>(M, ps.pdiag);
+        if (jit) {
+            // the specialised kernel has its own register count: its own grid
+            if (sc.jit->smem_set[i] < smem) {
+                cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                sc.jit->smem_set[i] = smem;
+            }
+            if (!sc.jit->grid[i]) {
+                int per_sm = 1;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem);
+                per_sm = std::max(1, per_sm);
+                sc.jit->grid[i] = (int)std::min<int64_t>((int64_t)batch << (p.n - sc.k), (int64_t)per_sm * nsm);
+            }
+            grid = sc.jit->grid[i];
+        }
         if (epi && i + 1 == sc.passes.size()) {
             // the last pass also measures the diagonal observables
             a.epi = *epi;
             for (int j = 0; j < 16; ++j) a.epi.T[j] = (int8_t)(j < (int)ps.T.size() ? ps.T[j] : 0);
             smem = tile_smem_bytes(sc.k, amp, ps.nops, ps.nseg, epi->nterms, threads);
-            if (tc.smem_set[kfn] < smem) {
+            size_t &opened = jit ? sc.jit->smem_set[i] : tc.smem_set[kfn];
+            if (opened < smem) {
                 cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
-                tc.smem_set[kfn] = smem;
+                opened = smem;
             }
             grid = std::min(grid, 4 * nsm);   // the partials hold at most 4 CTAs per SM
             if (epi_grid) *epi_grid = grid;
@@ -1068,7 +876,7 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
         a.errflag = tc.errflag;
         a.any_row = 0;
         for (int j = ps.op0; j < ps.op0 + ps.nops; ++j) a.any_row |= sc.ops[j].rowstep != 0;
-        LaunchScope ls(s, "k_tile_fwd", launches);
+        LaunchScope ls(s, jit ? "k_tile_fwd_jit" : "k_tile_fwd", launches);
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         cfg.gridDim = dim3((unsigned)grid);
@@ -1081,6 +889,13 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
         cfg.numAttrs = 1;
         cudaError_t e;
         const bool pd = ps.pdiag;
+        if (jit) {
+            void *args[] = {(void *)&L.map, (void *)&a};
+            e = cudaLaunchKernelExC(&cfg, kfn, args);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         switch (M * 2 + (pd ? 1 : 0)) {
         case 4: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 2, false>, L.map, a); break;
         case 5: e = cudaLaunchKernelEx(&cfg, k_tile_fwd<R, 2, true>, L.map, a); break;
@@ -1099,12 +914,35 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
     return cudaSuccess;
 }
 
+// Whether forward passes run as run-time specialised kernels: DQ_OPT_JIT on
+// (1), or automatic (2) with the autotuner having measured them faster; the
+// schedule's kernels are compiled on first use (a failed compile keeps the
+// interpreter for that schedule).
+bool jit_use(TileCache &tc, const std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p, int amp,
+             TileSchedule &sc) {
+    if (tc.jit_mode == 0 || sc.jit_failed) return false;
+    if (tc.jit_mode == 2) {
+        auto it = tuned.find(p.key ^ (amp == 16 ? 1ull : 0ull));
+        if (it == tuned.end() || it->second.jit != 1) return false;
+    }
+    if (!sc.jit) {
+        std::string err;
+        if (!jit_build(sc, amp, tc.device, &err)) {
+            sc.jit_failed = true;
+            tc.jit_err = err;
+            return false;
+        }
+    }
+    return true;
+}
+
 }  // namespace
 
 bool tile_supported(int n, int amp_bytes) {
     (void)amp_bytes;
     return n >= kTileLaneBits + 3 + 1 && n <= 34;
 }
+
 size_t tile_workspace_bytes(const Plan &, int, int) { return 0; }
 
 template <typename R>
@@ -1123,7 +961,8 @@ cudaError_t tile_apply(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tu
     }
     TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), false);
     if (!sc) return cudaErrorNotSupported;
-    return run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches);
+    const bool jit = jit_use(tc, tuned, p, (int)sizeof(cx<R>), *sc);
+    return run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches, nullptr, nullptr, jit);
 }
 
 template <typename R>
@@ -1154,7 +993,8 @@ cudaError_t tile_apply_expect(TileCache &tc, std::unordered_map<uint64_t, TileTu
     epi.part = part;
     epi.batch = batch;
     int grid = 0;
-    e = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches, &epi, &grid);
+    const bool jit = jit_use(tc, tuned, p, (int)sizeof(cx<R>), *sc);
+    e = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches, &epi, &grid, jit);
     if (e != cudaSuccess) return e;
     if (grid < 1 || grid > nsm4) return cudaErrorInvalidValue;
     return expect_finalize_nblk(part, d_bits, d_ptr, nobs, batch, grid, out, s, launches);
@@ -1198,6 +1038,30 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
                 bt.low = low;
                 bt.M = M;
             }
+        }
+    }
+    // the chosen shape's passes as run-time specialised kernels against the
+    // interpreter (DQ_OPT_JIT = 2 uses the faster)
+    if (bt.k && tc.jit_mode != 0 && jit_available()) {
+        TileSchedule *sc = get_schedule(tc, p, bt.k, bt.low, bt.M, (int)sizeof(cx<R>), false);
+        std::string err;
+        if (sc && (sc->jit || (!sc->jit_failed && jit_build(*sc, (int)sizeof(cx<R>), tc.device, &err)))) {
+            float ms[2] = {0.f, 0.f};
+            cudaError_t err2 = cudaSuccess;
+            for (int j = 0; j < 2 && err2 == cudaSuccess; ++j) {
+                err2 = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches, nullptr, nullptr, j == 1);
+                cudaEventRecord(e0, s);
+                for (int rep = 0; rep < 3 && err2 == cudaSuccess; ++rep)
+                    err2 = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches, nullptr, nullptr, j == 1);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms[j], e0, e1);
+            }
+            if (err2 == cudaSuccess) bt.jit = ms[1] < ms[0] ? 1 : 0;
+            else cudaGetLastError();
+        } else if (sc && !err.empty()) {
+            sc->jit_failed = true;
+            tc.jit_err = err;
         }
     }
     g_tracer = saved;

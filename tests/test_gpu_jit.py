@@ -1,0 +1,125 @@
+"""Run-time specialised forward passes (DQ_OPT_JIT): each pass's ops compiled
+into direct handler calls.  The arithmetic per element is the interpreter's,
+so states agree with the interpreting kernel to rounding and with the
+oracle within the parity tolerances, on every gate kind, both precisions,
+controls on register, lane, warp and block bits, controlled-phase fans,
+parity-diagonal ops, row-dependent angles and the diagonal-observable
+epilogue."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from tests.gpu_helpers import assert_amps, assert_rel, dev, np_state, obs_scale
+from tests.test_gpu_parity import edge_gates, random_gates
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("CUDA GPU required", allow_module_level=True)
+
+import paper_2512_18995_gb300 as dq  # noqa: E402
+from paper_2512_18995_gb300 import build as dqbuild  # noqa: E402
+
+dqbuild.build()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = dq.Context(0)
+    c.set_path(dq.PATH_FUSED)
+    yield c
+    c.set_option(dq.OPT_JIT, 2)
+    c.close()
+
+
+def forward(ctx, circ, params, data, batch, dt, n, obs, jit):
+    ctx.set_option(dq.OPT_JIT, jit)
+    st = torch.empty((batch, 1 << n), dtype=dt, device="cuda")
+    ctx.set_tracing(True)
+    e, _, _, _ = ctx.forward_grad(circ, params, dq.Observables(obs), batch, dt, data=data, want_grad=False,
+                                  state_out=st)
+    torch.cuda.synchronize()
+    names = set(ctx.trace())
+    ctx.set_tracing(False)
+    ctx.check()
+    return st, e, names
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+@pytest.mark.parametrize("n,batch", [(15, 2), (18, 1)])
+def test_jit_random_circuits_match_oracle_and_interpreter(ctx, dtype, n, batch):
+    rng = np.random.default_rng(1300 + n)
+    gates, npar = random_gates(n, 6 * n, rng, nfeat=3)
+    gates = edge_gates(n) + W.qft_gates(n) + gates + [W.Gate("rzz", (1, n - 2), angle=0.4)]
+    params = rng.uniform(-4, 4, npar)
+    data = rng.uniform(-3, 3, (batch, 3))
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=3)
+    obs = [W.obs_sum_z(n), [W.pauli_term(0.3, {0: "Z", n - 1: "Z"})]]
+    st1, e1, names1 = forward(ctx, circ, dev(params), dev(data), batch, dtype, n, obs, 1)
+    st0, e0, names0 = forward(ctx, circ, dev(params), dev(data), batch, dtype, n, obs, 0)
+    assert "k_tile_fwd_jit" in names1 and "k_tile_fwd" not in names1, names1
+    assert "k_tile_fwd_jit" not in names0, names0
+    ref = oracle.run(n, gates, params, data, batch=batch)
+    assert_amps(np_state(st1), ref, dtype, "specialised passes")
+    assert_rel(e1.cpu().numpy(), oracle.expect(n, ref, obs), dtype, "expectations (specialised)",
+               zero_scale=obs_scale(obs))
+    # the same arithmetic as the interpreter: agreement to rounding
+    tol = 1e-6 if dtype == torch.complex64 else 1e-13
+    assert float((st1 - st0).abs().max()) <= tol
+
+
+def test_jit_headline_workload(ctx):
+    """The 20-qubit ansatz with the tuned shape, specialised vs oracle."""
+    wl = W.config_c2()
+    circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
+    st = torch.empty((1, 1 << wl.n), dtype=torch.complex64, device="cuda")
+    ctx.plan_autotune(circ, st)
+    s1, e1, names = forward(ctx, circ, dev(wl.params), None, 1, torch.complex64, wl.n, wl.observables, 1)
+    assert "k_tile_fwd_jit" in names
+    ref = oracle.run(wl.n, wl.gates, wl.params)
+    assert_amps(np_state(s1), ref, torch.complex64, "C2 specialised state")
+    assert_rel(e1.cpu().numpy(), oracle.expect(wl.n, ref, wl.observables), torch.complex64, "C2 <sum Z>",
+               zero_scale=obs_scale(wl.observables))
+
+
+def test_jit_forward_then_adjoint(ctx):
+    """A gradient call: specialised forward passes, interpreted observable and
+    reverse passes; gradients against the oracle (QFT fans + ansatz)."""
+    n = 17
+    wl = W.config_c5(n)
+    circ = dq.Circuit(n, wl.gates, nparams=wl.nparams)
+    ctx.set_option(dq.OPT_JIT, 1)
+    ctx.set_tracing(True)
+    e, gp, _, _ = ctx.forward_grad(circ, dev(wl.params), dq.Observables(wl.observables), 1, torch.complex64)
+    torch.cuda.synchronize()
+    assert "k_tile_fwd_jit" in set(ctx.trace())
+    ctx.set_tracing(False)
+    e_ref, gp_ref, _ = oracle.adjoint(n, wl.gates, wl.observables, wl.params)
+    assert_rel(e.cpu().numpy(), e_ref, torch.complex64, "TFIM energy (specialised forward)")
+    assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, "TFIM gradient (specialised forward)")
+
+
+def test_jit_under_graph_replay(ctx):
+    n, batch = 16, 3
+    gates = W.encode_layer(n) + W.hea_layers(n, 2)
+    circ = dq.Circuit(n, gates, nparams=4 * n, nfeatures=n)
+    rng = np.random.default_rng(16)
+    params = dev(rng.uniform(0, 6, 4 * n))
+    data = dev(rng.uniform(-3, 3, (batch, n)))
+    st = torch.empty((batch, 1 << n), dtype=torch.complex64, device="cuda")
+    ctx.set_option(dq.OPT_JIT, 1)
+    ctx.set_graphs(True)
+    try:
+        for call in range(3):
+            params.copy_(dev(rng.uniform(0, 6, 4 * n)))
+            ctx.state_init(st, n)
+            ctx.apply_circuit(circ, params, st, data=data)
+            torch.cuda.synchronize()
+            ref = oracle.run(n, gates, params.cpu().numpy(), data.cpu().numpy(), batch=batch)
+            assert_amps(np_state(st), ref, torch.complex64, f"call {call}")
+    finally:
+        ctx.set_graphs(False)

@@ -495,3 +495,21 @@ def test_inspection_calls_reject_null_arguments(L):
     c3 = L.Circuit(3, [Gate("ccx", (0, 1, 2))])
     assert lib.dq_lower_circuit(c3.ref(), 0, ops, 1, ctypes.byref(n)) == 1 and n.value == 7
     assert ops[0].param_idx == 0 and ops[0].data_idx == 0     # untouched (a written op holds -1 there)
+
+
+def test_specialised_pass_source_compiles():
+    """The run-time specialised forward passes of a schedule: one op runner
+    and one kernel per pass in the source, and the source compiles for
+    sm_103a with NVRTC (no device needed)."""
+    from paper_2512_18995_gb300 import _lib
+    n = 11
+    gates = W.hea_layers(n, 2) + [W.Gate("cry", (0, n - 1), param=4 * n), W.Gate("rzz", (2, 7), angle=0.5),
+                                  W.Gate("swap", (1, 9))] + W.qft_gates(n)
+    c = _lib.Circuit(n, gates, nparams=4 * n + 1)
+    sched = _lib.tile_schedule(c, 9, 5, 3)
+    src = _lib.jit_source(c, 9, 5, 3)
+    assert src.count("struct JitPass") == len(sched) and src.count("__global__") == len(sched)
+    st, log = _lib.jit_compile_check(c, 9, 5, 3, cc=103)
+    if st == 2:
+        pytest.skip("NVRTC is not available here")
+    assert st == 0, log
