@@ -666,10 +666,12 @@ def qft_tfim30(ctx, device):
     obs = dq.Observables(wl.observables)
     params = torch.tensor(wl.params, device=device)
     out = {}
-    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+    for name, path, jit in (("fused", dq.PATH_FUSED, 1), ("fused_interpreted", dq.PATH_FUSED, 0),
+                            ("plain", dq.PATH_PLAIN, 0)):
         ctx.set_path(path)
+        ctx.set_option(dq.OPT_JIT, jit)
         try:
-            ctx.forward_grad(circ, params, obs, 1, torch.complex64)
+            ctx.forward_grad(circ, params, obs, 1, torch.complex64)   # warm-up (and the passes' compile)
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
@@ -679,14 +681,22 @@ def qft_tfim30(ctx, device):
             torch.cuda.synchronize()
         except RuntimeError as exc:   # not enough device memory
             ctx.set_path(dq.PATH_AUTO)
+            ctx.set_option(dq.OPT_JIT, 2)
             return {"skipped": str(exc)[:120]}
         ms = a.elapsed_time(b)
         out[name] = {"ms_per_step": ms, "grads_per_s": wl.nparams / (ms / 1e3)}
+        if name == "fused":
+            ctx.set_tracing(True)
+            ctx.forward_grad(circ, params, obs, 1, torch.complex64)
+            out[name]["kernel_ms"] = {k: [v[0], round(v[1], 2)] for k, v in ctx.trace().items()}
+            ctx.set_tracing(False)
     ctx.set_path(dq.PATH_AUTO)
+    ctx.set_option(dq.OPT_JIT, 2)
     ctx.release_workspace()
     torch.cuda.empty_cache()
     out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
     out["workload"] = "c5_qft_tfim30_c64"
+    out["fused_note"] = "forward and reverse tile passes as run-time specialised kernels (DQ_OPT_JIT = 1)"
     return out
 
 

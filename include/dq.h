@@ -626,21 +626,22 @@ DQ_API dq_status dq_tile_schedule(const dq_circuit *circuit, int dtype, int k, i
                                   int32_t *op_flags, int *npasses);
 
 /* Host-only (no context, no device): the source of the run-time specialised
- * forward passes of the tile schedule (k, low, M) that dq_tile_schedule
- * describes -- one op runner and one kernel per pass (DQ_OPT_JIT).  buf (may
+ * forward (adjoint = 0) or reverse-sweep (adjoint = 1) passes of the tile
+ * schedule (k, low, M) that dq_tile_schedule describes -- one op runner and
+ * one kernel per pass (DQ_OPT_JIT).  buf (may
  * be NULL) receives the NUL-terminated text when cap exceeds its length;
  * *len receives the length.  DQ_ERR_UNSUPPORTED when no schedule exists for
  * the shape.  No counterpart in the paper (an implementation choice of this
  * library). */
-DQ_API dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, int M, char *buf,
-                               size_t cap, size_t *len);
+DQ_API dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, int M, int adjoint,
+                               char *buf, size_t cap, size_t *len);
 
 /* Host-only: compile that source with NVRTC for compute capability cc (103
  * for sm_103a) without loading it.  DQ_OK when it compiles; DQ_ERR_CUDA with
  * the compiler log in `log` (cap bytes) when it does not;
  * DQ_ERR_UNSUPPORTED when NVRTC cannot be opened. */
-DQ_API dq_status dq_jit_compile_check(const dq_circuit *circuit, int dtype, int k, int low, int M, int cc,
-                                      char *log, size_t cap);
+DQ_API dq_status dq_jit_compile_check(const dq_circuit *circuit, int dtype, int k, int low, int M,
+                                      int adjoint, int cc, char *log, size_t cap);
 
 /* The program of the whole-row kernel (the fused path for rows of up to 16
  * qubits held on chip) for the pure circuit's lowered ops: M register bits

@@ -102,8 +102,8 @@ def load_library(path: str = LIB_PATH):
         "dq_ctx_set_path": ([P, I], I),
         "dq_ctx_set_option": ([P, I, ctypes.c_int64], I),
         "dq_state_norm": ([P, I, P, I, I, P, P], I),
-        "dq_jit_source": ([C, I, I, I, I, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], I),
-        "dq_jit_compile_check": ([C, I, I, I, I, I, ctypes.c_char_p, ctypes.c_size_t], I),
+        "dq_jit_source": ([C, I, I, I, I, I, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], I),
+        "dq_jit_compile_check": ([C, I, I, I, I, I, I, ctypes.c_char_p, ctypes.c_size_t], I),
         "dq_batch_autotune": ([P, I, C, P, ctypes.POINTER(ctypes.c_int64), O, I, P, P,
                                ctypes.POINTER(ctypes.c_int), P], I),
         "dq_selftest_wait_expiry": ([P, P], I),
@@ -343,25 +343,28 @@ def tile_schedule(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C6
              [int(x) for x in flags[start[p]:start[p + 1]]]) for p in range(npass.value)]
 
 
-def jit_source(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64) -> str:
-    """The run-time specialised forward passes of a tile schedule
-    (dq_jit_source): CUDA source, one op runner and kernel per pass."""
+def jit_source(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64, adjoint: bool = False) -> str:
+    """The run-time specialised forward (or reverse-sweep) passes of a tile
+    schedule (dq_jit_source): CUDA source, one op runner and kernel per pass."""
     lib = load_library()
     n = ctypes.c_size_t(0)
-    _inspect_check(lib.dq_jit_source(circuit.ref(), int(dtype), int(k), int(low), int(M), None, 0,
+    a = int(bool(adjoint))
+    _inspect_check(lib.dq_jit_source(circuit.ref(), int(dtype), int(k), int(low), int(M), a, None, 0,
                                      ctypes.byref(n)), "dq_jit_source")
     buf = ctypes.create_string_buffer(n.value + 1)
-    _inspect_check(lib.dq_jit_source(circuit.ref(), int(dtype), int(k), int(low), int(M), buf, n.value + 1,
+    _inspect_check(lib.dq_jit_source(circuit.ref(), int(dtype), int(k), int(low), int(M), a, buf, n.value + 1,
                                      ctypes.byref(n)), "dq_jit_source")
     return buf.value.decode()
 
 
-def jit_compile_check(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64, cc: int = 103):
+def jit_compile_check(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64, cc: int = 103,
+                      adjoint: bool = False):
     """dq_jit_compile_check: (status, compiler log) of compiling the
     specialised passes with NVRTC for compute capability cc (no device)."""
     lib = load_library()
     log = ctypes.create_string_buffer(4096)
-    st = lib.dq_jit_compile_check(circuit.ref(), int(dtype), int(k), int(low), int(M), int(cc), log, 4096)
+    st = lib.dq_jit_compile_check(circuit.ref(), int(dtype), int(k), int(low), int(M), int(bool(adjoint)), int(cc),
+                                  log, 4096)
     return int(st), log.value.decode(errors="replace")
 
 

@@ -2533,28 +2533,31 @@ dq_status dq_tile_schedule(const dq_circuit *circuit, int dtype, int k, int low,
 }
 
 namespace {
-dq_status jit_schedule(const dq_circuit *circuit, int dtype, int k, int low, int M, TileSchedule &sc) {
+dq_status jit_schedule(const dq_circuit *circuit, int dtype, int k, int low, int M, int adjoint, TileSchedule &sc) {
     Plan p;
     int ncs = 0, ncr = 0;
     const dq_status st = compile_gates(nullptr, circuit, 0, p.gates, p.bind, 0, &ncs, &ncr, false);
     if (st != DQ_OK) return st;
     p.n = circuit->nqubits;
     p.ngates = (int)p.gates.size();
+    // gradient slots: one per gate with an angle source (as the planner assigns them)
     p.slot_of_gate.assign(p.gates.size(), -1);
+    for (size_t i = 0; i < p.gates.size(); ++i)
+        if (p.gates[i].gkind != 0) p.slot_of_gate[i] = p.nslots++;
     const int amp = amp_bytes(dtype);
     if (M < 2 || M > (dtype == DQ_C64 ? 5 : 4) || k > kTileMaxK || !tile_supported(p.n, amp))
         return DQ_ERR_UNSUPPORTED;
-    if (!tile_build_schedule(p, k, low, M, amp, sc, false)) return DQ_ERR_UNSUPPORTED;
+    if (!tile_build_schedule(p, k, low, M, amp, sc, adjoint != 0)) return DQ_ERR_UNSUPPORTED;
     return DQ_OK;
 }
 }  // namespace
 
-dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, int M, char *buf, size_t cap,
-                        size_t *len) {
+dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, int M, int adjoint, char *buf,
+                        size_t cap, size_t *len) {
     if (!circuit || !len) return DQ_ERR_INVALID_ARG;
     if (dtype != DQ_C64 && dtype != DQ_C128) return DQ_ERR_INVALID_ARG;
     TileSchedule sc;
-    dq_status st = jit_schedule(circuit, dtype, k, low, M, sc);
+    dq_status st = jit_schedule(circuit, dtype, k, low, M, adjoint, sc);
     if (st != DQ_OK) return st;
     std::vector<std::string> names;
     const std::string src = jit_source(sc, amp_bytes(dtype), names);
@@ -2566,13 +2569,13 @@ dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, in
     return DQ_OK;
 }
 
-dq_status dq_jit_compile_check(const dq_circuit *circuit, int dtype, int k, int low, int M, int cc, char *log,
-                               size_t cap) {
+dq_status dq_jit_compile_check(const dq_circuit *circuit, int dtype, int k, int low, int M, int adjoint, int cc,
+                               char *log, size_t cap) {
     if (!circuit) return DQ_ERR_INVALID_ARG;
     if (dtype != DQ_C64 && dtype != DQ_C128) return DQ_ERR_INVALID_ARG;
     if (log && cap) log[0] = 0;
     TileSchedule sc;
-    dq_status st = jit_schedule(circuit, dtype, k, low, M, sc);
+    dq_status st = jit_schedule(circuit, dtype, k, low, M, adjoint, sc);
     if (st != DQ_OK) return st;
     std::vector<std::string> names;
     const std::string src = jit_source(sc, amp_bytes(dtype), names);

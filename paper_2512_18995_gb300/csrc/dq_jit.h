@@ -3,12 +3,18 @@
 
 #include <cuda_runtime.h>
 
+#include <stdint.h>
+
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 namespace dq {
 
 struct TileSchedule;
+struct TileCache;
+struct TileTune;
+struct Plan;
 
 // The compiled passes of one schedule (one library, one kernel per pass).
 struct JitModule {
@@ -26,6 +32,13 @@ std::string jit_source(const TileSchedule &sc, int amp, std::vector<std::string>
 // Compile a source of jit_source for compute capability cc (e.g. 103 for
 // sm_103a); cubin may be null (compile check only).
 bool jit_compile(const std::string &src, int cc, std::vector<char> *cubin, std::string *err);
+// Whether a schedule's passes run as specialised kernels (DQ_OPT_JIT on, or
+// automatic with the autotuner having measured them faster for the plan);
+// compiles them on first use.  A failed compile keeps the interpreter for
+// that schedule (the reason in tc.jit_err).  Reverse schedules follow the
+// circuit's forward verdict.
+bool jit_want(TileCache &tc, const std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p, int amp,
+              TileSchedule &sc);
 // Compile and load every pass of sc for `device` (sc.jit); false with *err on failure.
 bool jit_build(TileSchedule &sc, int amp, int device, std::string *err);
 

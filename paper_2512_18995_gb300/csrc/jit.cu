@@ -80,13 +80,52 @@ std::string cmask_expr(const EOp &o) {
     return "(((base >> " + std::to_string((int)o.carg) + ") & 1ull) ? ~0u : 0u)";
 }
 
-// An EOp literal for the handlers that read its fields.
-std::string eop_literal(const EOp &o) {
+// An EOp literal (variable `v`) for the handlers that read its fields.
+std::string eop_literal(const EOp &o, const char *v = "o") {
     std::ostringstream s;
-    s << "EOp o{}; o.h = " << o.h << "; o.kind = " << o.kind << "; o.cmc = " << hex32(o.cmc)
-      << "; o.cmode = " << (int)o.cmode << "; o.carg = " << (int)o.carg << "; o.tmode = " << (int)o.tmode
-      << "; o.targ = " << (int)o.targ << ";";
+    s << "EOp " << v << "{}; " << v << ".h = " << o.h << "; " << v << ".kind = " << o.kind << "; " << v
+      << ".cmc = " << hex32(o.cmc) << "; " << v << ".cmode = " << (int)o.cmode << "; " << v
+      << ".carg = " << (int)o.carg << "; " << v << ".tmode = " << (int)o.tmode << "; " << v
+      << ".targ = " << (int)o.targ << "; " << v << ".slot = " << o.slot << ";";
     return s.str();
+}
+
+// Gradient partial of an op with a local slot into the per-warp accumulators.
+void emit_acc(std::ostringstream &s, const char *g, int slot, int nslot) {
+    if (slot < 0) return;
+    s << " { const R gs = warp_sum_t(" << g << "); if (lane == 0) accw[warp * " << nslot << " + " << slot
+      << "] += gs; }";
+}
+
+// One reverse segment of a pass: gradient partials and un-application of
+// its ops, highest first (a rotation pair consumes its REAL op too).
+void emit_rev_segment(std::ostringstream &s, const TileSchedule &sc, const TPass &ps, const TSeg &sg) {
+    const int M = sc.M;
+    s << "    {\n        ESeg sg{}; ";
+    for (int b = 0; b < M; ++b) s << "sg.B[" << b << "] = " << (int)sg.B[b] << "; ";
+    s << "\n        const Layout L = make_layout(sg, M, " << sc.k << ", lane, warp);\n"
+         "        eng_load<R, M>(ps, bufP, L);\n        eng_load<R, M>(ls, bufL, L);\n";
+    for (int cc = 0; cc < sg.nops; ++cc) {
+        const int oi = sg.op0 - ps.op0 - cc;
+        const EOp &o = sc.rops[ps.op0 + oi];
+        if (o.pad[1]) {
+            const EOp &o2 = sc.rops[ps.op0 + oi - 1];
+            s << "        { " << eop_literal(o, "o") << " " << eop_literal(o2, "o2")
+              << " R gd, gr; eng_adjoint_pair<R, M>(ps, ls, o, dagger(scoef[" << oi << "]), o2, dagger(scoef["
+              << oi - 1 << "]), lane, gd, gr);";
+            emit_acc(s, "gd", o.slot, ps.nslot);
+            emit_acc(s, "gr", o2.slot, ps.nslot);
+            s << " }\n";
+            ++cc;
+            continue;
+        }
+        s << "        { " << eop_literal(o, "o") << " const R gv = eng_adjoint<R, M, false>(ps, ls, o, dagger(scoef["
+          << oi << "]), base, L, lane);";
+        emit_acc(s, "gv", o.slot, ps.nslot);
+        s << " }\n";
+    }
+    s << "        eng_store<R, M>(ps, bufP, L);\n        eng_store<R, M>(ls, bufL, L);\n        __syncthreads();\n"
+         "    }\n";
 }
 
 // One op of a pass (index i in the pass's op list); returns the number of
@@ -148,8 +187,33 @@ std::string jit_source(const TileSchedule &sc, int amp, std::vector<std::string>
     std::ostringstream s;
     s << "typedef signed char int8_t; typedef unsigned char uint8_t; typedef short int16_t;\n"
          "typedef unsigned short uint16_t; typedef int int32_t; typedef unsigned int uint32_t;\n"
-         "typedef long long int64_t; typedef unsigned long long uint64_t; typedef unsigned long long uintptr_t;\n"
-         "#include \"dq_tile_fwd.cuh\"\n"
+         "typedef long long int64_t; typedef unsigned long long uint64_t; typedef unsigned long long uintptr_t;\n";
+    if (sc.adjoint) {
+        // reverse passes: runner + kernel per pass
+        const int amax = ((1 << M) * cxb <= 64) ? 512 : 256;
+        s << "#include \"dq_tile_adj.cuh\"\nnamespace dq {\nnamespace {\n";
+        for (int p = p0; p < p1; ++p) {
+            const TPass &ps = sc.passes[p];
+            s << "struct JitRev" << p << " {\n"
+                 "    template <typename R, int M>\n"
+                 "    __device__ __forceinline__ static void run(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M],\n"
+                 "        cx<R> *bufP, cx<R> *bufL, const EOp *, const ESeg *, const Mat2<R> *scoef, R *accw,\n"
+                 "        int, int, int, int, uint64_t base, int lane, int warp) {\n";
+            for (int si = ps.rseg0; si < ps.rseg0 + ps.nrseg; ++si) emit_rev_segment(s, sc, ps, sc.rsegs[si]);
+            s << "    }\n};\n";
+        }
+        s << "}  // namespace\n}  // namespace dq\n";
+        names.clear();
+        for (int p = p0; p < p1; ++p) {
+            const std::string name = "dq_jit_adj_" + std::to_string(p);
+            names.push_back(name);
+            s << "extern \"C\" __global__ void __launch_bounds__(" << amax << ") " << name
+              << "(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap ml, dq::AdjArgs a) {\n"
+              << "    dq::tile_adj_body<" << R << ", " << M << ", dq::JitRev" << p << ">(mp, ml, a);\n}\n";
+        }
+        return s.str();
+    }
+    s << "#include \"dq_tile_fwd.cuh\"\n"
          "namespace dq {\nnamespace {\n";
     for (int p = p0; p < p1; ++p) {
         const TPass &ps = sc.passes[p];
@@ -181,6 +245,24 @@ std::string jit_source(const TileSchedule &sc, int amp, std::vector<std::string>
           << ", dq::JitPass" << p << ">(tmap, a);\n}\n";
     }
     return s.str();
+}
+
+bool jit_want(TileCache &tc, const std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p, int amp,
+              TileSchedule &sc) {
+    if (tc.jit_mode == 0 || sc.jit_failed) return false;
+    if (tc.jit_mode == 2) {
+        auto it = tuned.find(p.key ^ (amp == 16 ? 1ull : 0ull));
+        if (it == tuned.end() || it->second.jit != 1) return false;
+    }
+    if (!sc.jit) {
+        std::string err;
+        if (!jit_build(sc, amp, tc.device, &err)) {
+            sc.jit_failed = true;
+            tc.jit_err = err;
+            return false;
+        }
+    }
+    return true;
 }
 
 void JitModule::release() {

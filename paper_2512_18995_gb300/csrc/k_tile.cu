@@ -914,28 +914,6 @@ cudaError_t run_forward(TileCache &tc, const Plan &p, TileSchedule &sc, const vo
     return cudaSuccess;
 }
 
-// Whether forward passes run as run-time specialised kernels: DQ_OPT_JIT on
-// (1), or automatic (2) with the autotuner having measured them faster; the
-// schedule's kernels are compiled on first use (a failed compile keeps the
-// interpreter for that schedule).
-bool jit_use(TileCache &tc, const std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p, int amp,
-             TileSchedule &sc) {
-    if (tc.jit_mode == 0 || sc.jit_failed) return false;
-    if (tc.jit_mode == 2) {
-        auto it = tuned.find(p.key ^ (amp == 16 ? 1ull : 0ull));
-        if (it == tuned.end() || it->second.jit != 1) return false;
-    }
-    if (!sc.jit) {
-        std::string err;
-        if (!jit_build(sc, amp, tc.device, &err)) {
-            sc.jit_failed = true;
-            tc.jit_err = err;
-            return false;
-        }
-    }
-    return true;
-}
-
 }  // namespace
 
 bool tile_supported(int n, int amp_bytes) {
@@ -961,7 +939,7 @@ cudaError_t tile_apply(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tu
     }
     TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), false);
     if (!sc) return cudaErrorNotSupported;
-    const bool jit = jit_use(tc, tuned, p, (int)sizeof(cx<R>), *sc);
+    const bool jit = jit_want(tc, tuned, p, (int)sizeof(cx<R>), *sc);
     return run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches, nullptr, nullptr, jit);
 }
 
@@ -993,7 +971,7 @@ cudaError_t tile_apply_expect(TileCache &tc, std::unordered_map<uint64_t, TileTu
     epi.part = part;
     epi.batch = batch;
     int grid = 0;
-    const bool jit = jit_use(tc, tuned, p, (int)sizeof(cx<R>), *sc);
+    const bool jit = jit_want(tc, tuned, p, (int)sizeof(cx<R>), *sc);
     e = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches, &epi, &grid, jit);
     if (e != cudaSuccess) return e;
     if (grid < 1 || grid > nsm4) return cudaErrorInvalidValue;

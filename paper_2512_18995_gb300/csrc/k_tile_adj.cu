@@ -27,6 +27,8 @@
 #include "dq_plan.h"
 #include "dq_tile.h"
 #include "dq_tma.cuh"
+#include "dq_tile_adj.cuh"
+#include "dq_jit.h"
 
 namespace dq {
 
@@ -340,170 +342,11 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
     if (tid == 0) bulk_wait0();
 }
 
-// ---------------------------------------------------------------------------
-// reverse sweep
-// ---------------------------------------------------------------------------
-struct AdjArgs {
-    TileGeom g;
-    const EOp *ops;      // the pass's reverse decodings (op0 .. op0 + nops)
-    const ESeg *segs;    // the pass's reverse segments
-    int op0, nops, nseg;
-    const int32_t *slots;   // global slot of each local slot
-    int nslot;
-    const void *coef;
-    double *part;        // [slot][row][cta]
-    int batch;
-    int *errflag;
-    int any_row;       // some op's coefficients depend on the batch row
-};
-
-template <typename R, int M>
-constexpr int adj_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) <= 64) ? 512 : 256; }
-
 template <typename R, int M>
 __global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __grid_constant__ CUtensorMap mp,
                                                                        const __grid_constant__ CUtensorMap ml,
                                                                        AdjArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const unsigned long long wlim = wait_limit_ns(a.errflag);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const size_t tbytes = sizeof(cx<R>) << a.g.k;
-    cx<R> *bufP = reinterpret_cast<cx<R> *>(smem);
-    cx<R> *bufL = reinterpret_cast<cx<R> *>(smem + tbytes);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * tbytes);
-    EOp *sops = reinterpret_cast<EOp *>(smem + 2 * tbytes + 64);
-    ESeg *ssegs = reinterpret_cast<ESeg *>(sops + a.nops);
-    Mat2<R> *scoef = reinterpret_cast<Mat2<R> *>(ssegs + a.nseg);
-    double *acc = reinterpret_cast<double *>(scoef + a.nops);       // [nslot]
-    R *accw = reinterpret_cast<R *>(acc + a.nslot);                  // [nw][nslot]
-    const Mat2<R> *gcoef = reinterpret_cast<const Mat2<R> *>(a.coef);
-    const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * per;
-    const int64_t t1 = min(a.g.ntiles, t0 + per);
-    // the first tile's copies overlap the staging of the pass's ops
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        fence_async_smem();
-        if (t0 < t1) {
-            int c[5];
-            uint64_t base;
-            int64_t row;
-            geom_coords(a.g, t0, c, base, row);
-            mbar_expect_tx(&bar[0], (uint32_t)(2 * tbytes));
-            tma_load5(bufP, &mp, c, &bar[0]);
-            tma_load5(bufL, &ml, c, &bar[0]);
-        }
-    }
-    for (int i = tid; i < a.nops; i += blockDim.x) {
-        const EOp o = a.ops[i];
-        sops[i] = o;
-        scoef[i] = gcoef[o.coef];
-    }
-    for (int i = tid; i < a.nseg; i += blockDim.x) ssegs[i] = a.segs[i];
-    for (int i = tid; i < a.nslot; i += blockDim.x) acc[i] = 0.0;
-    for (int i = tid; i < nw * a.nslot; i += blockDim.x) accw[i] = R(0);
-    __syncthreads();
-    uint32_t phase = 0;
-    int64_t cur_row = -1;
-    bool failed = false;
-    auto flush = [&](int64_t row) {
-        for (int j = tid; j < a.nslot; j += blockDim.x) {
-            a.part[((int64_t)a.slots[j] * a.batch + row) * gridDim.x + blockIdx.x] = acc[j];
-            acc[j] = 0.0;
-        }
-    };
-    cx<R> ps[1 << M], ls[1 << M];
-    int64_t crow = 0;   // the table holds row 0's coefficient blocks
-    for (int64_t t = t0; t < t1; ++t) {
-        int c[5];
-        uint64_t base;
-        int64_t row;
-        geom_coords(a.g, t, c, base, row);
-        if (row != cur_row) {
-            if (cur_row >= 0) flush(cur_row);
-            cur_row = row;
-        }
-        if (a.any_row && row != crow) {
-            // row-dependent coefficient blocks of this tile's row into the table
-            __syncthreads();
-            for (int i = tid; i < a.nops; i += blockDim.x)
-                if (sops[i].rowstep) scoef[i] = gcoef[sops[i].coef + row * sops[i].rowstep];
-            __syncthreads();
-            crow = row;
-        }
-        if (tid == 0 && t > t0) {
-            mbar_expect_tx(&bar[0], (uint32_t)(2 * tbytes));
-            tma_load5(bufP, &mp, c, &bar[0]);
-            tma_load5(bufL, &ml, c, &bar[0]);
-        }
-        const bool ok = mbar_wait_bounded(&bar[0], phase, wlim);
-        phase ^= 1;
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        for (int si = 0; si < a.nseg; ++si) {
-            const ESeg sg = ssegs[si];
-            const Layout L = make_layout(sg, M, a.g.k, lane, warp);
-            eng_load<R, M>(ps, bufP, L);
-            eng_load<R, M>(ls, bufL, L);
-            for (int cc = 0; cc < sg.nops; ++cc) {
-                const int oi = sg.op0 - a.op0 - cc;
-                const EOp o = sops[oi];
-                const Mat2<R> u = scoef[oi];
-                if (o.pad[1]) {   // rotation pair: this DIAG op, then the REAL op before it
-                    const EOp o2 = sops[oi - 1];
-                    const Mat2<R> u2 = scoef[oi - 1];
-                    R gd, gr;
-                    eng_adjoint_pair<R, M>(ps, ls, o, dagger(u), o2, dagger(u2), lane, gd, gr);
-                    if (o.slot >= 0) {
-                        const R gs = warp_sum_t(gd);
-                        if (lane == 0) accw[warp * a.nslot + o.slot] += gs;
-                    }
-                    if (o2.slot >= 0) {
-                        const R gs = warp_sum_t(gr);
-                        if (lane == 0) accw[warp * a.nslot + o2.slot] += gs;
-                    }
-                    ++cc;
-                    continue;
-                }
-                const R gv = eng_adjoint<R, M, false>(ps, ls, o, dagger(u), base, L, lane);
-                if (o.slot >= 0) {
-                    const R gs = warp_sum_t(gv);
-                    if (lane == 0) accw[warp * a.nslot + o.slot] += gs;
-                }
-            }
-            eng_store<R, M>(ps, bufP, L);
-            eng_store<R, M>(ls, bufL, L);
-            __syncthreads();
-        }
-        for (int j = tid; j < a.nslot; j += blockDim.x) {
-            double sum = 0.0;
-            for (int ww = 0; ww < nw; ++ww) {
-                sum += (double)accw[ww * a.nslot + j];
-                accw[ww * a.nslot + j] = R(0);
-            }
-            acc[j] += sum;
-        }
-        fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tma_store5(&mp, c, bufP);
-            tma_store5(&ml, c, bufL);
-            bulk_commit();
-            bulk_wait_read0();
-        }
-        __syncthreads();
-    }
-    if (!failed && cur_row >= 0) {
-        __syncthreads();
-        flush(cur_row);
-    }
-    if (failed && tid == 0) {
-        atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
-        mbar_wait_bounded(&bar[0], phase, wlim);
-    }
-    if (tid == 0) bulk_wait0();
+    tile_adj_body<R, M, InterpRev>(mp, ml, a);
 }
 
 uint64_t obs_key(const std::vector<DevTerm> &bits, int n, int k, int low, int amp) {
@@ -617,7 +460,6 @@ template <typename R>
 cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
                          const void *coef, void *psi, void *lam, int batch, double *part, double *gp, double *gd,
                          int nsm, cudaStream_t s, int64_t *launches) {
-    (void)tuned;
     constexpr int wb = AdjCfg<R>::wb;
     if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
     int k, low, M;
@@ -659,9 +501,11 @@ cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &
         sc->adj_l = lam;
         sc->adj_batch = batch;
     }
-    const void *kfn = M == 3 ? (const void *)k_tile_adj<R, 3>
-                             : (M == 2 ? (const void *)k_tile_adj<R, 2> : (const void *)k_tile_adj<R, 4>);
+    const bool jit = jit_want(tc, tuned, p, (int)sizeof(cx<R>), *sc);
+    const void *ikfn = M == 3 ? (const void *)k_tile_adj<R, 3>
+                              : (M == 2 ? (const void *)k_tile_adj<R, 2> : (const void *)k_tile_adj<R, 4>);
     for (int pi = (int)sc->passes.size() - 1; pi >= pstop; --pi) {
+        const void *kfn = jit ? (const void *)sc->jit->kernels[pi] : ikfn;
         const TPass &ps = sc->passes[pi];
         TileDims d;
         if (!make_dims(ps.T, p.n, wb, d)) return cudaErrorInvalidValue;
@@ -684,16 +528,29 @@ cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &
         const size_t smem = 2 * (sizeof(cx<R>) << k) + 64 + (size_t)ps.nops * sizeof(EOp) +
                             (size_t)ps.nrseg * sizeof(ESeg) + (size_t)ps.nops * sizeof(Mat2<R>) +
                             (size_t)ps.nslot * sizeof(double) + (size_t)nw * ps.nslot * sizeof(R) + 64;
-        if (tc.smem_set[kfn] < smem) {
+        size_t &opened = jit ? sc->jit->smem_set[pi] : tc.smem_set[kfn];
+        if (opened < smem) {
             e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            tc.smem_set[kfn] = smem;
+            opened = smem;
         }
-        LaunchScope ls(s, "k_tile_adj", launches);
-        if (M == 3) k_tile_adj<R, 3><<<grid, threads, smem, s>>>(mp, ml, a);
-        else if (M == 2) k_tile_adj<R, 2><<<grid, threads, smem, s>>>(mp, ml, a);
-        else k_tile_adj<R, 4><<<grid, threads, smem, s>>>(mp, ml, a);
-        e = cudaGetLastError();
+        LaunchScope ls(s, jit ? "k_tile_adj_jit" : "k_tile_adj", launches);
+        if (jit) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)grid);
+            cfg.blockDim = dim3((unsigned)threads);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = s;
+            void *args[] = {(void *)&mp, (void *)&ml, (void *)&a};
+            e = cudaLaunchKernelExC(&cfg, kfn, args);
+        } else if (M == 3) {
+            k_tile_adj<R, 3><<<grid, threads, smem, s>>>(mp, ml, a);
+        } else if (M == 2) {
+            k_tile_adj<R, 2><<<grid, threads, smem, s>>>(mp, ml, a);
+        } else {
+            k_tile_adj<R, 4><<<grid, threads, smem, s>>>(mp, ml, a);
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return grad_reduce(p, part, batch, grid, gp, gd, s, launches);

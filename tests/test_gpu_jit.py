@@ -87,8 +87,8 @@ def test_jit_headline_workload(ctx):
 
 
 def test_jit_forward_then_adjoint(ctx):
-    """A gradient call: specialised forward passes, interpreted observable and
-    reverse passes; gradients against the oracle (QFT fans + ansatz)."""
+    """A gradient call: specialised forward and reverse passes (the observable
+    passes interpreted); gradients against the oracle (QFT fans + ansatz)."""
     n = 17
     wl = W.config_c5(n)
     circ = dq.Circuit(n, wl.gates, nparams=wl.nparams)
@@ -96,7 +96,8 @@ def test_jit_forward_then_adjoint(ctx):
     ctx.set_tracing(True)
     e, gp, _, _ = ctx.forward_grad(circ, dev(wl.params), dq.Observables(wl.observables), 1, torch.complex64)
     torch.cuda.synchronize()
-    assert "k_tile_fwd_jit" in set(ctx.trace())
+    names = set(ctx.trace())
+    assert "k_tile_fwd_jit" in names and "k_tile_adj_jit" in names and "k_tile_adj" not in names, names
     ctx.set_tracing(False)
     e_ref, gp_ref, _ = oracle.adjoint(n, wl.gates, wl.observables, wl.params)
     assert_rel(e.cpu().numpy(), e_ref, torch.complex64, "TFIM energy (specialised forward)")
@@ -123,3 +124,32 @@ def test_jit_under_graph_replay(ctx):
             assert_amps(np_state(st), ref, torch.complex64, f"call {call}")
     finally:
         ctx.set_graphs(False)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+@pytest.mark.parametrize("ppr", [False, True])
+def test_jit_gradients_random_circuits(ctx, dtype, ppr):
+    """Specialised reverse passes on random circuits over every kind, shared
+    or per-row parameters, data gradients: against the oracle."""
+    n, batch = 15, 2
+    rng = np.random.default_rng(1500 + ppr)
+    gates, npar = random_gates(n, 6 * n, rng, nfeat=2)
+    params = rng.uniform(-4, 4, size=(batch, npar) if ppr else npar)
+    data = rng.uniform(-3, 3, size=(batch, 2))
+    obs = [W.obs_tfim_open(n, 0.5), [(0.7, 1, (1 << n) - 1), (-0.4, 0, 1)]]
+    w = rng.normal(size=(batch, 2))
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=2)
+    ctx.set_option(dq.OPT_JIT, 1)
+    ctx.set_tracing(True)
+    e, gp, gd, _ = ctx.forward_grad(circ, dev(params), dq.Observables(obs), batch, dtype, data=dev(data),
+                                    row_weights=dev(w), params_per_row=ppr)
+    torch.cuda.synchronize()
+    names = set(ctx.trace())
+    ctx.set_tracing(False)
+    assert "k_tile_adj_jit" in names, names
+    e_ref, gp_ref, gd_ref = oracle.adjoint(n, gates, obs, params, data, batch=batch, params_per_row=ppr,
+                                           row_weights=w)
+    gscale = float(np.abs(w).max(axis=1).sum()) * obs_scale(obs)
+    assert_rel(e.cpu().numpy(), e_ref, dtype, "expectations", zero_scale=obs_scale(obs))
+    assert_rel(gp.cpu().numpy(), gp_ref, dtype, "grad params (specialised reverse)", zero_scale=gscale)
+    assert_rel(gd.cpu().numpy(), gd_ref, dtype, "grad data (specialised reverse)", zero_scale=gscale)

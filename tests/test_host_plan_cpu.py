@@ -513,3 +513,9 @@ def test_specialised_pass_source_compiles():
     if st == 2:
         pytest.skip("NVRTC is not available here")
     assert st == 0, log
+    # the reverse sweep's passes (gradients on the parametric gates)
+    rsched = _lib.tile_schedule(c, 9, 5, 3, adjoint=True)
+    rsrc = _lib.jit_source(c, 9, 5, 3, adjoint=True)
+    assert rsrc.count("struct JitRev") == len(rsched) and "eng_adjoint" in rsrc
+    st, log = _lib.jit_compile_check(c, 9, 5, 3, cc=103, adjoint=True)
+    assert st == 0, log
