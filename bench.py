@@ -970,8 +970,17 @@ def batched_grads(ctx, device, steps=5):
     params = torch.tensor(wl.params, device=device)
     data = torch.tensor(wl.data, device=device)
     out = {}
-    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+    # fused: the autotuner picks the interpreting or the specialised
+    # whole-row kernel (the latter compiled on first use); fused_interpreted
+    # forces the interpreting kernel
+    for name, path, jit in (("fused", dq.PATH_FUSED, 2), ("fused_interpreted", dq.PATH_FUSED, 0),
+                            ("plain", dq.PATH_PLAIN, 0)):
         ctx.set_path(path)
+        ctx.set_option(dq.OPT_JIT, jit)
+        if name == "fused":
+            tune = torch.empty((wl.batch, 1 << wl.n), dtype=torch.complex64, device=device)
+            ctx.plan_autotune(circ, tune)
+            del tune
         for _ in range(2):
             ctx.forward_grad(circ, params, obs, wl.batch, torch.complex64, data=data)
         torch.cuda.synchronize()
@@ -984,6 +993,13 @@ def batched_grads(ctx, device, steps=5):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
         out[name] = {"ms_per_step": ms, "grads_per_s": wl.batch * wl.nparams / (ms / 1e3)}
+        if name == "fused":
+            ctx.set_tracing(True)
+            ctx.forward_grad(circ, params, obs, wl.batch, torch.complex64, data=data)
+            out[name]["kernel_ms"] = {k: [v[0], round(v[1], 3)] for k, v in ctx.trace().items()}
+            ctx.set_tracing(False)
+    ctx.set_path(dq.PATH_AUTO)
+    ctx.set_option(dq.OPT_JIT, 2)
     out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
     out["workload"] = "c3_qml12x4096_c64"
     return out
@@ -1009,6 +1025,9 @@ def profile_case(args):
         e = torch.empty((1, 1), dtype=torch.float64, device=dev)
         flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
         ctx.plan_autotune(circ, st)
+        # under a profiler the tuner's timings change its choice; take the
+        # specialised per-pass kernels the bench's own tuned run uses
+        ctx.set_option(dq.OPT_JIT, 1)
         for _ in range(args.warmup):
             ctx.forward_grad(circ, params, obs, 1, torch.complex64, want_grad=False, state_out=st, expect_out=e)
         torch.cuda.synchronize()
@@ -1052,8 +1071,10 @@ def profile_case(args):
         U = torch.from_numpy(W.random_unitary(6, 6)).to(dev)
         for _ in range(iters):
             ctx.apply_dense(n, U, st)
-    elif args.profile_case == "c5":          # QFT + layers, forward + adjoint, 26 qubits
+    elif args.profile_case == "c5":          # QFT + layers, forward + adjoint, 26 qubits, specialised passes
         wl = W.config_c5(26)
+        ctx.set_path(dq.PATH_FUSED)
+        ctx.set_option(dq.OPT_JIT, 1)
         circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams)
         obs = dq.Observables(wl.observables)
         params = torch.tensor(wl.params, device=dev)

@@ -208,14 +208,16 @@ DQ_API dq_status dq_ctx_set_path(dq_ctx *ctx, int path);
  *   1: whenever the circuit has such a run; 2: when dq_plan_autotune measured
  *   the blocks faster for this circuit.  Gradient calls always run gate by
  *   gate (the adjoint sweep needs every gate's generator).
- * DQ_OPT_JIT (default 2): forward tile passes as run-time specialised
- *   kernels -- each pass's ops compiled (NVRTC, loaded with the runtime's
- *   library API) into direct calls of the same handlers the interpreting
- *   kernel dispatches to, with every register position, control mask and
- *   layout a literal; same arithmetic per element.  0: never; 1: always (the
- *   schedule's passes are compiled on first use, which takes seconds); 2: when
- *   dq_plan_autotune measured them faster for this circuit.  Without NVRTC,
- *   or if a compile fails, the interpreting kernel runs. */
+ * DQ_OPT_JIT (default 2): tile passes (forward and reverse sweep) and the
+ *   whole-row kernel as run-time specialised kernels -- each pass's (or the
+ *   row program's) ops compiled (NVRTC, loaded with the runtime's library
+ *   API) into direct calls of the same handlers the interpreting kernel
+ *   dispatches to, with every register position, control mask and layout a
+ *   literal; same arithmetic per element.  0: never; 1: always (compiled on
+ *   first use, which takes seconds); 2: when dq_plan_autotune measured them
+ *   faster for this circuit and precision (tile passes and the whole-row
+ *   kernel are measured separately).  Without NVRTC, or if a compile fails,
+ *   the interpreting kernel runs. */
 enum dq_option { DQ_OPT_MULTIPASS = 1, DQ_OPT_WAIT_LIMIT_US = 2, DQ_OPT_DENSE_BLOCKS = 3, DQ_OPT_JIT = 4 };
 
 /* Set a context option; DQ_ERR_INVALID_ARG for an unknown option or value.
@@ -545,10 +547,12 @@ DQ_API dq_status dq_sample(dq_ctx *ctx, int nqubits, const void *state, int batc
                            int64_t shots, const double *uniforms, uint64_t seed,
                            uint64_t wire_mask, int64_t *out, void *stream);
 
-/* Time the fused-path variants (fusion width k and tile schedule) for this
- * circuit shape on `state` (device, batch rows, contents destroyed) and
- * cache the fastest for later calls with the same circuit structure.
- * Synchronises `stream`. */
+/* Time the fused-path variants (fusion width k and tile schedule; the
+ * interpreting against the specialised tile passes; for rows of up to 16
+ * qubits, the interpreting against the specialised whole-row kernel; dense
+ * blocks against tile passes) for this circuit shape on `state` (device,
+ * batch rows, contents destroyed) and cache the fastest for later calls with
+ * the same circuit structure.  Synchronises `stream`. */
 DQ_API dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch,
                            int dtype, void *state, void *stream);
 
@@ -625,15 +629,17 @@ DQ_API dq_status dq_tile_schedule(const dq_circuit *circuit, int dtype, int k, i
                                   int capacity, int32_t *order, int32_t *pass_start, uint64_t *tile_bits,
                                   int32_t *op_flags, int *npasses);
 
-/* Host-only (no context, no device): the source of the run-time specialised
- * forward (adjoint = 0) or reverse-sweep (adjoint = 1) passes of the tile
- * schedule (k, low, M) that dq_tile_schedule describes -- one op runner and
- * one kernel per pass (DQ_OPT_JIT).  buf (may
- * be NULL) receives the NUL-terminated text when cap exceeds its length;
- * *len receives the length.  DQ_ERR_UNSUPPORTED when no schedule exists for
- * the shape.  No counterpart in the paper (an implementation choice of this
- * library). */
-DQ_API dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, int M, int adjoint,
+/* Host-only (no context, no device): the source of a run-time specialised
+ * program (DQ_OPT_JIT).  kind 0: the forward passes, kind 1: the reverse-sweep
+ * passes of the tile schedule (k, low, M) that dq_tile_schedule describes --
+ * one op runner and one kernel per pass; kind 2: the whole-row kernel of the
+ * program dq_row_program describes for M register bits (0: the kernel's own
+ * choice; k and low are ignored) -- one kernel.  buf (may be NULL) receives
+ * the NUL-terminated text when cap exceeds its length; *len receives the
+ * length.  DQ_ERR_INVALID_ARG for another kind; DQ_ERR_UNSUPPORTED when no
+ * schedule or row program exists for the shape.  No counterpart in the paper
+ * (an implementation choice of this library). */
+DQ_API dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, int M, int kind,
                                char *buf, size_t cap, size_t *len);
 
 /* Host-only: compile that source with NVRTC for compute capability cc (103
@@ -641,7 +647,7 @@ DQ_API dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int 
  * the compiler log in `log` (cap bytes) when it does not;
  * DQ_ERR_UNSUPPORTED when NVRTC cannot be opened. */
 DQ_API dq_status dq_jit_compile_check(const dq_circuit *circuit, int dtype, int k, int low, int M,
-                                      int adjoint, int cc, char *log, size_t cap);
+                                      int kind, int cc, char *log, size_t cap);
 
 /* The program of the whole-row kernel (the fused path for rows of up to 16
  * qubits held on chip) for the pure circuit's lowered ops: M register bits

@@ -343,12 +343,18 @@ def tile_schedule(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C6
              [int(x) for x in flags[start[p]:start[p + 1]]]) for p in range(npass.value)]
 
 
-def jit_source(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64, adjoint: bool = False) -> str:
-    """The run-time specialised forward (or reverse-sweep) passes of a tile
-    schedule (dq_jit_source): CUDA source, one op runner and kernel per pass."""
+JIT_FORWARD, JIT_REVERSE, JIT_ROWS = 0, 1, 2
+
+
+def jit_source(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64, adjoint: bool = False,
+               kind: Optional[int] = None) -> str:
+    """A run-time specialised program (dq_jit_source): the forward (or, with
+    adjoint, reverse-sweep) passes of a tile schedule, one op runner and
+    kernel per pass; or, with kind=JIT_ROWS, the whole-row kernel of the row
+    program for M register bits (k and low ignored)."""
     lib = load_library()
     n = ctypes.c_size_t(0)
-    a = int(bool(adjoint))
+    a = int(bool(adjoint)) if kind is None else int(kind)
     _inspect_check(lib.dq_jit_source(circuit.ref(), int(dtype), int(k), int(low), int(M), a, None, 0,
                                      ctypes.byref(n)), "dq_jit_source")
     buf = ctypes.create_string_buffer(n.value + 1)
@@ -358,13 +364,14 @@ def jit_source(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64, 
 
 
 def jit_compile_check(circuit: Circuit, k: int, low: int, M: int, dtype: int = DQ_C64, cc: int = 103,
-                      adjoint: bool = False):
+                      adjoint: bool = False, kind: Optional[int] = None):
     """dq_jit_compile_check: (status, compiler log) of compiling the
-    specialised passes with NVRTC for compute capability cc (no device)."""
+    specialised program (as jit_source selects it) with NVRTC for compute
+    capability cc (no device)."""
     lib = load_library()
     log = ctypes.create_string_buffer(4096)
-    st = lib.dq_jit_compile_check(circuit.ref(), int(dtype), int(k), int(low), int(M), int(bool(adjoint)), int(cc),
-                                  log, 4096)
+    a = int(bool(adjoint)) if kind is None else int(kind)
+    st = lib.dq_jit_compile_check(circuit.ref(), int(dtype), int(k), int(low), int(M), a, int(cc), log, 4096)
     return int(st), log.value.decode(errors="replace")
 
 

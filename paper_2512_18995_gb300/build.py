@@ -36,7 +36,7 @@ def cuda_flags():
 # hands their texts to NVRTC as in-memory headers).
 JIT_HEADERS = [(os.path.join(INCLUDE, "dq.h"), "dq.h")] + [
     (os.path.join(CSRC, h), h) for h in ("dq_common.cuh", "dq_engine.cuh", "dq_tma.cuh", "dq_tile_fwd.cuh",
-                                         "dq_tile_adj.cuh", "dq_devterm.h")]
+                                         "dq_tile_adj.cuh", "dq_rows_body.cuh", "dq_devterm.h")]
 
 
 def write_jit_headers():

@@ -741,6 +741,28 @@ RowProgram *get_rows(dq_ctx *ctx, const Plan &p, int amp, bool grad, int nobs) {
     return rp;
 }
 
+// Whether the whole-row kernel runs as the program's specialised kernel:
+// DQ_OPT_JIT on, or automatic with the autotuner having measured it faster
+// for this plan and precision.  Compiled on first use; a failed compile
+// keeps the interpreter for the program (the reason in the tile cache's
+// jit_err).
+bool rows_jit(dq_ctx *ctx, const Plan &p, RowProgram &rp, int amp) {
+    if (ctx->tiles.jit_mode == 0 || rp.jit_failed) return false;
+    if (ctx->tiles.jit_mode == 2) {
+        auto it = ctx->tuned.find(p.key ^ (amp == 16 ? 1ull : 0ull));
+        if (it == ctx->tuned.end() || it->second.rows_jit != 1) return false;
+    }
+    if (!rp.jit) {
+        std::string err;
+        if (!jit_rows_build(rp, amp, ctx->tiles.device, &err)) {
+            rp.jit_failed = true;
+            ctx->tiles.jit_err = err;
+            return false;
+        }
+    }
+    return true;
+}
+
 // Run `body(stream)` through the context's graph cache.  Returns true when the
 // call was served by a graph (captured now or earlier); *st is its status.
 // With tracing on, a replay is followed by a synchronisation and the
@@ -998,7 +1020,8 @@ dq_status apply_impl(dq_ctx *ctx, Plan &p, const double *params, const double *d
     DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
     if (rp) {
         DQ_CUDA(rows_launch<R>(*rp, p, coef, state, 1, nullptr, 0, 1, nullptr, batch, state, nullptr, nullptr, nullptr,
-                               nullptr, ctx->nsm, ctx->smem_optin, s, &ctx->launches),
+                               nullptr, ctx->nsm, ctx->smem_optin, s, &ctx->launches,
+                               rows_jit(ctx, p, *rp, (int)sizeof(cx<R>))),
                 "fused apply (rows)");
     } else if (small) {
         DQ_CUDA(wsv_launch<R>(p, coef, state, 1, nullptr, 0, 1, nullptr, batch, state, nullptr, nullptr, nullptr,
@@ -1033,7 +1056,8 @@ dq_status expect_impl(dq_ctx *ctx, int n, ObsDev &o, const void *state, int batc
     RowProgram *rp = use_fused(ctx) ? get_rows(ctx, p, (int)sizeof(cx<R>), false, o.nobs) : nullptr;
     if (rp) {
         DQ_CUDA(rows_launch<R>(*rp, p, nullptr, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, nullptr, batch,
-                               nullptr, out, nullptr, nullptr, nullptr, ctx->nsm, ctx->smem_optin, s, &ctx->launches),
+                               nullptr, out, nullptr, nullptr, nullptr, ctx->nsm, ctx->smem_optin, s, &ctx->launches,
+                               rows_jit(ctx, p, *rp, (int)sizeof(cx<R>))),
                 "fused expect (rows)");
         return DQ_OK;
     }
@@ -1096,7 +1120,8 @@ dq_status adjoint_impl(dq_ctx *ctx, Plan &p, ObsDev &o, const double *params, co
         double *part = (double *)w.take(std::max(wsv_part_bytes(p, ctx->nsm), rows_part_bytes(p, ctx->nsm)));
         if (rp)
             DQ_CUDA(rows_launch<R>(*rp, p, coef, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, rw, batch, nullptr,
-                                   nullptr, gp, gd, part, ctx->nsm, ctx->smem_optin, s, &ctx->launches),
+                                   nullptr, gp, gd, part, ctx->nsm, ctx->smem_optin, s, &ctx->launches,
+                                   rows_jit(ctx, p, *rp, (int)sizeof(cx<R>))),
                     "fused adjoint (rows)");
         else
             DQ_CUDA(wsv_launch<R>(p, coef, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, rw, batch, nullptr,
@@ -1163,7 +1188,7 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
         if (rp)
             DQ_CUDA(rows_launch<R>(*rp, p, coef, nullptr, 1, o ? o->d_wires : nullptr, o ? (int)o->bits.size() : 0,
                                    o ? o->nobs : 1, rw, batch, state_out, eo, gp, gd, part, ctx->nsm, ctx->smem_optin,
-                                   s, &ctx->launches),
+                                   s, &ctx->launches, rows_jit(ctx, p, *rp, (int)sizeof(cx<R>))),
                     "fused forward+adjoint (rows)");
         else
             DQ_CUDA(wsv_launch<R>(p, coef, nullptr, 1, o ? o->d_wires : nullptr, o ? (int)o->bits.size() : 0,
@@ -2239,6 +2264,48 @@ dq_status batch_launch(dq_ctx *ctx, BatchDev *bd, ObsDev *o, const double *param
     return DQ_OK;
 }
 
+// Whole-row kernel: time the forward over `batch` rows (written to state)
+// with the interpreting kernel and with the program's specialised kernel,
+// and keep the faster for DQ_OPT_JIT = 2.
+template <typename R>
+cudaError_t rows_autotune(dq_ctx *ctx, const Plan &p, RowProgram &rp, const void *coef, void *state, int batch,
+                          cudaStream_t s) {
+    const int amp = (int)sizeof(cx<R>);
+    if (!jit_available() || rp.jit_failed) return cudaSuccess;
+    if (!rp.jit) {
+        std::string err;
+        if (!jit_rows_build(rp, amp, ctx->tiles.device, &err)) {
+            rp.jit_failed = true;
+            ctx->tiles.jit_err = err;
+            return cudaSuccess;
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Tracer *saved = g_tracer;
+    g_tracer = nullptr;
+    float ms[2] = {0.f, 0.f};
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+        auto run = [&]() {
+            return rows_launch<R>(rp, p, coef, nullptr, 1, nullptr, 0, 1, nullptr, batch, state, nullptr, nullptr,
+                                  nullptr, nullptr, ctx->nsm, ctx->smem_optin, s, &ctx->launches, j == 1);
+        };
+        e = run();   // warm-up
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = run();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms[j], e0, e1);
+    }
+    g_tracer = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess) ctx->tuned[p.key ^ (amp == 16 ? 1ull : 0ull)].rows_jit = ms[1] < ms[0] ? 1 : 0;
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2400,7 +2467,9 @@ dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch, in
     if (!state || !aligned16(state)) return fail(ctx, DQ_ERR_INVALID_ARG, "state must be a 16-byte aligned device pointer");
     Plan *p = nullptr;
     if ((st = get_plan(ctx, circuit, 0, &p)) != DQ_OK) return st;
-    if (!tile_supported(p->n, amp_bytes(dtype))) return DQ_OK;   // nothing to tune
+    const bool tiles = tile_supported(p->n, amp_bytes(dtype));
+    RowProgram *rp = get_rows(ctx, *p, amp_bytes(dtype), false, 1);
+    if (!tiles && !rp) return DQ_OK;   // nothing to tune
     ctx->clear_graphs();
     cudaStream_t s = (cudaStream_t)stream;
     Arena a;
@@ -2425,10 +2494,12 @@ dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch, in
     cudaError_t e;
     if (dtype == DQ_C64) {
         e = bind_coef<float>(ctx, *p, zeros, zeros, batch, coef, s);
-        if (e == cudaSuccess) e = tile_autotune<float>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+        if (e == cudaSuccess && tiles) e = tile_autotune<float>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+        if (e == cudaSuccess && rp) e = rows_autotune<float>(ctx, *p, *rp, coef, state, batch, s);
     } else {
         e = bind_coef<double>(ctx, *p, zeros, zeros, batch, coef, s);
-        if (e == cudaSuccess) e = tile_autotune<double>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+        if (e == cudaSuccess && tiles) e = tile_autotune<double>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+        if (e == cudaSuccess && rp) e = rows_autotune<double>(ctx, *p, *rp, coef, state, batch, s);
     }
     // Dense blocks (complex64): with the tuned tile shape, time the circuit
     // with its runs on the six lowest-order bits as tensor-core blocks against
@@ -2550,17 +2621,46 @@ dq_status jit_schedule(const dq_circuit *circuit, int dtype, int k, int low, int
     if (!tile_build_schedule(p, k, low, M, amp, sc, adjoint != 0)) return DQ_ERR_UNSUPPORTED;
     return DQ_OK;
 }
+
+// The source of a specialised program: kind 0 / 1 the forward / reverse tile
+// passes of schedule (k, low, M), kind 2 the whole-row kernel (register bits
+// M, 0 for the library's choice).
+dq_status jit_program_source(const dq_circuit *circuit, int dtype, int k, int low, int M, int kind,
+                             std::string &src) {
+    if (kind == 2) {
+        Plan p;
+        int ncs = 0, ncr = 0;
+        const dq_status st = compile_gates(nullptr, circuit, 0, p.gates, p.bind, 0, &ncs, &ncr, false);
+        if (st != DQ_OK) return st;
+        p.n = circuit->nqubits;
+        p.ngates = (int)p.gates.size();
+        p.nparams = circuit->nparams;
+        p.nfeat = circuit->nfeatures;
+        const int m = M ? M : rows_pick_M(p.n, amp_bytes(dtype));
+        if (m < 2 || m > (dtype == DQ_C64 ? 4 : 3)) return DQ_ERR_UNSUPPORTED;
+        RowProgram rp;
+        if (!rows_build_program(p, m, rp)) return DQ_ERR_UNSUPPORTED;
+        src = jit_rows_source(rp, amp_bytes(dtype));
+        return DQ_OK;
+    }
+    TileSchedule sc;
+    const dq_status st = jit_schedule(circuit, dtype, k, low, M, kind, sc);
+    if (st != DQ_OK) return st;
+    std::vector<std::string> names;
+    src = jit_source(sc, amp_bytes(dtype), names);
+    return DQ_OK;
+}
+
 }  // namespace
 
-dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, int M, int adjoint, char *buf,
+dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, int M, int kind, char *buf,
                         size_t cap, size_t *len) {
     if (!circuit || !len) return DQ_ERR_INVALID_ARG;
     if (dtype != DQ_C64 && dtype != DQ_C128) return DQ_ERR_INVALID_ARG;
-    TileSchedule sc;
-    dq_status st = jit_schedule(circuit, dtype, k, low, M, adjoint, sc);
+    if (kind < 0 || kind > 2) return DQ_ERR_INVALID_ARG;
+    std::string src;
+    const dq_status st = jit_program_source(circuit, dtype, k, low, M, kind, src);
     if (st != DQ_OK) return st;
-    std::vector<std::string> names;
-    const std::string src = jit_source(sc, amp_bytes(dtype), names);
     *len = src.size();
     if (buf) {
         if (cap < src.size() + 1) return DQ_ERR_INVALID_ARG;
@@ -2569,16 +2669,15 @@ dq_status dq_jit_source(const dq_circuit *circuit, int dtype, int k, int low, in
     return DQ_OK;
 }
 
-dq_status dq_jit_compile_check(const dq_circuit *circuit, int dtype, int k, int low, int M, int adjoint, int cc,
+dq_status dq_jit_compile_check(const dq_circuit *circuit, int dtype, int k, int low, int M, int kind, int cc,
                                char *log, size_t cap) {
     if (!circuit) return DQ_ERR_INVALID_ARG;
     if (dtype != DQ_C64 && dtype != DQ_C128) return DQ_ERR_INVALID_ARG;
+    if (kind < 0 || kind > 2) return DQ_ERR_INVALID_ARG;
     if (log && cap) log[0] = 0;
-    TileSchedule sc;
-    dq_status st = jit_schedule(circuit, dtype, k, low, M, adjoint, sc);
+    std::string src;
+    const dq_status st = jit_program_source(circuit, dtype, k, low, M, kind, src);
     if (st != DQ_OK) return st;
-    std::vector<std::string> names;
-    const std::string src = jit_source(sc, amp_bytes(dtype), names);
     std::string err;
     if (!jit_compile(src, cc, nullptr, &err)) {
         if (log && cap) std::snprintf(log, cap, "%s", err.c_str());

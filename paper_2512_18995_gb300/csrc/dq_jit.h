@@ -1,4 +1,4 @@
-// Run-time specialised forward tile passes (internal interface).
+// Run-time specialised tile passes and whole-row kernels (internal interface).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -12,6 +12,7 @@
 namespace dq {
 
 struct TileSchedule;
+struct RowProgram;
 struct TileCache;
 struct TileTune;
 struct Plan;
@@ -41,5 +42,10 @@ bool jit_want(TileCache &tc, const std::unordered_map<uint64_t, TileTune> &tuned
               TileSchedule &sc);
 // Compile and load every pass of sc for `device` (sc.jit); false with *err on failure.
 bool jit_build(TileSchedule &sc, int amp, int device, std::string *err);
+// Source of the whole-row kernel with the program's ops compiled in (kernel
+// dq_jit_rows, taking RowArgs like the interpreting kernel).
+std::string jit_rows_source(const RowProgram &rp, int amp);
+// Compile and load it for `device` (rp.jit, one kernel); false with *err on failure.
+bool jit_rows_build(RowProgram &rp, int amp, int device, std::string *err);
 
 }  // namespace dq

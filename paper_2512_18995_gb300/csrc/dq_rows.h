@@ -11,6 +11,8 @@
 
 namespace dq {
 
+struct JitModule;
+
 // Engine program for whole rows of one circuit: ops in an execution order
 // that keeps every pair of non-commuting ops in gate order (SWAP as three
 // CNOTs), register layouts for the forward and the reverse sweep.
@@ -25,8 +27,13 @@ struct RowProgram {
     std::vector<ESeg> fsegs, rsegs;
     EOp *d_fops = nullptr, *d_rops = nullptr;
     ESeg *d_fsegs = nullptr, *d_rsegs = nullptr;
+    JitModule *jit = nullptr;      // the program compiled into a kernel (run-time specialisation)
+    bool jit_failed = false;
     void release();
 };
+
+// rows_launch with jit set runs rp.jit's kernel (built by jit_rows_build)
+// instead of the interpreting one; same arguments, same results.
 
 // Register bits the whole-row kernel uses for an n-qubit row (0: the row
 // does not fit the kernel).
@@ -39,6 +46,6 @@ template <typename R>
 cudaError_t rows_launch(const RowProgram &rp, const Plan &p, const void *coef, const void *state_in, int forward,
                         const DevTerm *d_wterms, int nterms, int nobs, const double *row_weights, int batch,
                         void *state_out, double *expect_out, double *grad_params, double *grad_data, double *part,
-                        int nsm, size_t smem_optin, cudaStream_t s, int64_t *launches);
+                        int nsm, size_t smem_optin, cudaStream_t s, int64_t *launches, bool jit = false);
 
 }  // namespace dq

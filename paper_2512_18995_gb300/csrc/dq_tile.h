@@ -95,6 +95,7 @@ struct TileTune {
     int M = 0;          // register bits per thread
     int dense = 0;      // 1: runs of gates on the six lowest-order bits go to tensor-core dense blocks
     int jit = 0;        // 1: forward passes run as run-time specialised kernels
+    int rows_jit = 0;   // 1: the whole-row kernel runs as the program's specialised kernel
 };
 
 // Host-side cache of schedules and the driver entry point used to encode

@@ -1,4 +1,4 @@
-// Run-time specialised forward tile passes.
+// Run-time specialised tile passes and whole-row kernels.
 //
 // The forward tile kernel interprets each pass's op program from shared
 // memory: per op it reads the decoded record, dispatches on its handler and
@@ -10,8 +10,10 @@
 // kernel body (dq_tile_fwd.cuh) with it, compiles all passes of the schedule
 // in one NVRTC program for the device's architecture and loads the result
 // with the runtime's library API.  The arithmetic per element is the
-// interpreter's; only the dispatch is gone.  NVRTC is opened with dlopen on
-// first use: without it the interpreter simply stays in use.
+// interpreter's; only the dispatch is gone.  Reverse-sweep tile passes
+// (dq_tile_adj.cuh) and the whole-row kernel (dq_rows_body.cuh, one kernel
+// per circuit program) are specialised the same way.  NVRTC is opened with
+// dlopen on first use: without it the interpreter simply stays in use.
 #include <dlfcn.h>
 #include <nvrtc.h>
 
@@ -25,6 +27,7 @@
 #include <algorithm>
 
 #include "dq_jit.h"
+#include "dq_rows.h"
 #include "dq_tile.h"
 #include "jit_headers.inc"   // generated by build.py: the device headers' texts
 
@@ -97,6 +100,85 @@ void emit_acc(std::ostringstream &s, const char *g, int slot, int nslot) {
       << "] += gs; }";
 }
 
+// One reverse op (coefficient scoef[i]) as a direct call of its adjoint
+// handler: eng_adjoint's dispatch resolved here, with the gradient partial
+// formed only for an op with a slot (added to accw[warp * nacc + slot]).
+// pd: parity-diagonal ops have their own handler (else they take the
+// uniform-diagonal one, as in a kernel compiled without them).
+void emit_adj_op(std::ostringstream &s, const EOp &o, int i, int M, bool pd, int nacc) {
+    const int h = o.h;
+    const char *G = o.slot >= 0 ? "true" : "false";
+    const std::string ud = "const Mat2<R> ud = dagger(scoef[" + std::to_string(i) + "]);";
+    std::string body;
+    if (h < H_GEN || (h >= H_DIAG && h < H_CREAL)) {
+        const int P = h < H_GEN ? h - H_REAL : h - H_DIAG;
+        if (P >= M) return;
+        if (h < H_GEN)
+            body = std::string("gv = adj_pairs_at<R, M, ") + std::to_string(P) + ", CLS_REAL, " + G + ">(ps, ls, ud);";
+        else
+            body = std::string("gv = adj_diag_at<R, M, ") + std::to_string(P) + ", " + G + ">(ps, ls, ud, " +
+                   std::to_string((int)o.kind) + ");";
+    } else if (pd && h == H_PDIAG) {
+        body = eop_literal(o) + std::string(" gv = adj_pdiag<R, M, ") + G + ">(ps, ls, o, ud, base, L);";
+    } else {
+        if (o.cmode == 0 && o.cmc == 0) return;   // the control is never set in this layout
+        std::string call;
+        auto reg = [&](int base_h, const char *tmpl, const char *cls, const char *g, bool kind) {
+            const int P = h - base_h;
+            if (P >= M) return false;
+            call = std::string(tmpl) + "<R, M, " + std::to_string(P) + (cls ? std::string(", ") + cls : "") + ", " +
+                   g + ">(ps, ls, ud, " + (kind ? std::to_string((int)o.kind) + ", " : "") + "cm)";
+            return true;
+        };
+        bool ok = true;
+        if (h >= H_GEN && h < H_ANTI) ok = reg(H_GEN, "adj_pairs_sel", "CLS_GENERAL", G, false);
+        else if (h >= H_ANTI && h < H_DIAG) ok = reg(H_ANTI, "adj_pairs_sel", "CLS_ANTI", "false", false);
+        else if (h >= H_CREAL && h < H_CDIAG) ok = reg(H_CREAL, "adj_pairs_sel", "CLS_REAL", G, false);
+        else if (h >= H_CDIAG && h < H_LREAL) ok = reg(H_CDIAG, "adj_diag_sel", nullptr, G, true);
+        else if (h == H_LREAL || h == H_LGEN || h == H_LANTI)
+            call = std::string("adj_lane_at<R, M, ") +
+                   (h == H_LREAL ? "CLS_REAL" : h == H_LGEN ? "CLS_GENERAL" : "CLS_ANTI") + ", " +
+                   (h == H_LANTI ? "false" : G) + ">(ps, ls, ud, " + std::to_string((int)o.targ) + ", lane, cm)";
+        else
+            call = eop_literal(o) + std::string(" gv = adj_diag_uni<R, M, ") + G + ">(ps, ls, ud, o, L, base, cm)";
+        if (!ok) return;
+        body = "const uint32_t cm = " + cmask_expr(o) + ";";
+        if (o.cmode != 0) body += " if (!__all_sync(0xffffffffu, cm == 0u))";
+        if (call.compare(0, 4, "EOp ") == 0) {
+            // the literal precedes the call inside its own block
+            const size_t at = call.find(" gv = ");
+            body = call.substr(0, at) + " " + body + " " + call.substr(at + 1) + ";";
+        } else {
+            body += " gv = " + call + ";";
+        }
+    }
+    s << "        { " << ud << " R gv = R(0); " << body;
+    emit_acc(s, "gv", o.slot, nacc);
+    s << " }\n";
+}
+
+// A rotation pair in the reverse sweep: the DIAG op d (coefficient
+// scoef[i]) and the REAL op r before it (scoef[i - 1]) un-applied in one
+// register sweep (eng_adjoint_pair's dispatch resolved here).
+void emit_adj_pair(std::ostringstream &s, const EOp &d, const EOp &r, int i, int M, int nacc) {
+    const char *G = (d.slot >= 0 || r.slot >= 0) ? "true" : "false";
+    std::string call;
+    if (r.h == H_LREAL) {
+        call = std::string("adj_pair_lane<R, M, ") + G + ">(ps, ls, dd, rr, " + std::to_string((int)d.kind) + ", " +
+               std::to_string((int)r.targ) + ", lane, gd, gr);";
+    } else {
+        const int P = r.h - H_REAL;
+        if (P >= 0 && P < 5 && P < M)
+            call = std::string("adj_pair_reg<R, M, ") + std::to_string(P) + ", " + G + ">(ps, ls, dd, rr, " +
+                   std::to_string((int)d.kind) + ", gd, gr);";
+    }
+    s << "        { const Mat2<R> dd = dagger(scoef[" << i << "]), rr = dagger(scoef[" << i - 1
+      << "]); R gd = R(0), gr = R(0); " << call;
+    emit_acc(s, "gd", d.slot, nacc);
+    emit_acc(s, "gr", r.slot, nacc);
+    s << " }\n";
+}
+
 // One reverse segment of a pass: gradient partials and un-application of
 // its ops, highest first (a rotation pair consumes its REAL op too).
 void emit_rev_segment(std::ostringstream &s, const TileSchedule &sc, const TPass &ps, const TSeg &sg) {
@@ -109,20 +191,11 @@ void emit_rev_segment(std::ostringstream &s, const TileSchedule &sc, const TPass
         const int oi = sg.op0 - ps.op0 - cc;
         const EOp &o = sc.rops[ps.op0 + oi];
         if (o.pad[1]) {
-            const EOp &o2 = sc.rops[ps.op0 + oi - 1];
-            s << "        { " << eop_literal(o, "o") << " " << eop_literal(o2, "o2")
-              << " R gd, gr; eng_adjoint_pair<R, M>(ps, ls, o, dagger(scoef[" << oi << "]), o2, dagger(scoef["
-              << oi - 1 << "]), lane, gd, gr);";
-            emit_acc(s, "gd", o.slot, ps.nslot);
-            emit_acc(s, "gr", o2.slot, ps.nslot);
-            s << " }\n";
+            emit_adj_pair(s, o, sc.rops[ps.op0 + oi - 1], oi, M, ps.nslot);
             ++cc;
             continue;
         }
-        s << "        { " << eop_literal(o, "o") << " const R gv = eng_adjoint<R, M, false>(ps, ls, o, dagger(scoef["
-          << oi << "]), base, L, lane);";
-        emit_acc(s, "gv", o.slot, ps.nslot);
-        s << " }\n";
+        emit_adj_op(s, o, oi, M, false, ps.nslot);
     }
     s << "        eng_store<R, M>(ps, bufP, L);\n        eng_store<R, M>(ls, bufL, L);\n        __syncthreads();\n"
          "    }\n";
@@ -173,7 +246,84 @@ int emit_op(std::ostringstream &s, const EOp *ops, int i, int nops, bool pd) {
     return 1;
 }
 
+// Fixed-width integer names for the device headers (NVRTC has no libc).
+const char *const kPrelude =
+    "typedef signed char int8_t; typedef unsigned char uint8_t; typedef short int16_t;\n"
+    "typedef unsigned short uint16_t; typedef int int32_t; typedef unsigned int uint32_t;\n"
+    "typedef long long int64_t; typedef unsigned long long uint64_t; typedef unsigned long long uintptr_t;\n";
+
+// Register-layout literal of a segment and the layout it makes.
+void emit_layout(std::ostringstream &s, const ESeg &sg, int M, int n, const char *assign) {
+    s << "        { ESeg sg{}; ";
+    for (int b = 0; b < M; ++b) s << "sg.B[" << b << "] = " << (int)sg.B[b] << "; ";
+    s << assign << "make_layout(sg, M, " << n << ", lane, warp); }\n";
+}
+
+// Whole-row reverse sweep: segments from the last op down (the first one in
+// the layout lambda was formed in), each op's gradient partial added to its
+// accumulator (stride nacc per warp); the sweep ends after `nrun` segments.
+void emit_rows_reverse(std::ostringstream &s, const RowProgram &rp, int nacc) {
+    for (size_t si = 0; si < rp.rsegs.size(); ++si) {
+        const ESeg &sg = rp.rsegs[si];
+        if (si > 0) {
+            s << "        if (nrun <= " << si << ") return;\n"
+                 "        eng_store<R, M>(ps, bufP, L);\n        eng_store<R, M>(ls, bufL, L);\n"
+                 "        __syncthreads();\n";
+            emit_layout(s, sg, rp.M, rp.n, "L = ");
+            s << "        eng_load<R, M>(ps, bufP, L);\n        eng_load<R, M>(ls, bufL, L);\n";
+        }
+        for (int c = 0; c < sg.nops; ++c) {
+            const int oi = sg.op0 - c;
+            const EOp &o = rp.rops[oi];
+            if (o.pad[1]) {
+                emit_adj_pair(s, o, rp.rops[oi - 1], oi, rp.M, nacc);
+                ++c;
+                continue;
+            }
+            emit_adj_op(s, o, oi, rp.M, rp.pdiag, nacc);
+        }
+    }
+}
+
 }  // namespace
+
+// Source of the whole-row kernel with the program's ops compiled in: one op
+// runner (forward segments; reverse segments with gradient partials) and the
+// kernel dq_jit_rows.
+std::string jit_rows_source(const RowProgram &rp, int amp) {
+    const char *R = amp == 16 ? "double" : "float";
+    const int M = rp.M;
+    const int maxt = ((1 << M) * amp <= 64) ? 512 : 256;
+    const int minb = amp == 8 ? 2 : 1;
+    const int nacc = rp.nacc_shared + rp.nacc_row;
+    std::ostringstream s;
+    s << kPrelude << "#include \"dq_rows_body.cuh\"\nnamespace dq {\nnamespace {\n"
+         "struct JitRows {\n"
+         "    template <typename R, int M, bool PD>\n"
+         "    __device__ __forceinline__ static void fwd(cx<R> (&r)[1 << M], cx<R> *bufP, Layout &L, const ESeg *,\n"
+         "        const EOp *sops, const Mat2<R> *scoef, int, int, int lane, int warp) {\n"
+         "        const uint64_t base = 0;\n";
+    for (size_t si = 0; si < rp.fsegs.size(); ++si) {
+        const ESeg &sg = rp.fsegs[si];
+        if (si > 0) {
+            s << "        eng_store<R, M>(r, bufP, L);\n        __syncthreads();\n";
+            emit_layout(s, sg, M, rp.n, "L = ");
+            s << "        eng_load<R, M>(r, bufP, L);\n";
+        }
+        for (int i = sg.op0; i < sg.op0 + sg.nops;) i += emit_op(s, rp.fops.data(), i, (int)rp.fops.size(), rp.pdiag);
+    }
+    s << "    }\n"
+         "    template <typename R, int M, bool PD>\n"
+         "    __device__ __forceinline__ static void rev(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], cx<R> *bufP,\n"
+         "        cx<R> *bufL, Layout &L, const ESeg *, const EOp *, const Mat2<R> *scoef, R *accw, int, int nrun,\n"
+         "        int, int lane, int warp) {\n"
+         "        const uint64_t base = 0;\n";
+    emit_rows_reverse(s, rp, nacc);
+    s << "    }\n};\n}  // namespace\n}  // namespace dq\n"
+      << "extern \"C\" __global__ void __launch_bounds__(" << maxt << ", " << minb << ") dq_jit_rows(dq::RowArgs a) {\n"
+      << "    dq::rows_body<" << R << ", " << M << ", " << (rp.pdiag ? "true" : "false") << ", dq::JitRows>(a);\n}\n";
+    return s.str();
+}
 
 // Source of passes [p0, p1) of the schedule (all when p1 < 0): op runner +
 // kernel per pass.
@@ -185,9 +335,7 @@ std::string jit_source(const TileSchedule &sc, int amp, std::vector<std::string>
     const int maxt = ((1 << M) * cxb >= 256) ? 256 : 512;
     const int minb = ((1 << M) * cxb <= 64) ? 2 : 1;
     std::ostringstream s;
-    s << "typedef signed char int8_t; typedef unsigned char uint8_t; typedef short int16_t;\n"
-         "typedef unsigned short uint16_t; typedef int int32_t; typedef unsigned int uint32_t;\n"
-         "typedef long long int64_t; typedef unsigned long long uint64_t; typedef unsigned long long uintptr_t;\n";
+    s << kPrelude;
     if (sc.adjoint) {
         // reverse passes: runner + kernel per pass
         const int amax = ((1 << M) * cxb <= 64) ? 512 : 256;
@@ -304,6 +452,38 @@ bool jit_compile(const std::string &src, int cc, std::vector<char> *cubin, std::
         api.cubin(prog, cubin->data());
     }
     api.destroy(&prog);
+    return true;
+}
+
+bool jit_rows_build(RowProgram &rp, int amp, int device, std::string *err) {
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+    std::vector<char> cubin;
+    if (!jit_compile(jit_rows_source(rp, amp), major * 10 + minor, &cubin, err)) return false;
+    JitModule *m = new JitModule();
+    cudaLibrary_t lib = nullptr;
+    cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    cudaKernel_t k = nullptr;
+    if (e == cudaSuccess) {
+        m->libs.push_back(lib);
+        e = cudaLibraryGetKernel(&k, lib, "dq_jit_rows");
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        m->release();
+        delete m;
+        if (err) *err = std::string("loading the whole-row kernel: ") + cudaGetErrorString(e);
+        return false;
+    }
+    m->kernels.push_back(k);
+    m->grid.assign(1, 0);
+    m->smem_set.assign(1, 0);
+    if (rp.jit) {
+        rp.jit->release();
+        delete rp.jit;
+    }
+    rp.jit = m;
     return true;
 }
 

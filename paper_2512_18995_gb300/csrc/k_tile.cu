@@ -1045,7 +1045,13 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
     g_tracer = saved;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (bt.k) tuned[p.key ^ (sizeof(R) == 8 ? 1ull : 0ull)] = bt;
+    if (bt.k) {
+        // keep what other tuners recorded for the plan (whole-row kernel, dense blocks)
+        TileTune &t = tuned[p.key ^ (sizeof(R) == 8 ? 1ull : 0ull)];
+        bt.rows_jit = t.rows_jit;
+        bt.dense = t.dense;
+        t = bt;
+    }
     return cudaSuccess;
 }
 

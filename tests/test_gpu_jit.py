@@ -1,10 +1,11 @@
-"""Run-time specialised forward passes (DQ_OPT_JIT): each pass's ops compiled
-into direct handler calls.  The arithmetic per element is the interpreter's,
-so states agree with the interpreting kernel to rounding and with the
-oracle within the parity tolerances, on every gate kind, both precisions,
-controls on register, lane, warp and block bits, controlled-phase fans,
-parity-diagonal ops, row-dependent angles and the diagonal-observable
-epilogue."""
+"""Run-time specialised kernels (DQ_OPT_JIT): each forward or reverse tile
+pass's ops, or a whole-row program, compiled into direct handler calls.  The
+arithmetic per element is the interpreter's, so states agree with the
+interpreting kernel to rounding and with the oracle within the parity
+tolerances, on every gate kind, both precisions, controls on register, lane,
+warp and block bits, controlled-phase fans, parity-diagonal ops,
+row-dependent angles, the diagonal-observable epilogue and the adjoint
+gradients."""
 import math
 
 import numpy as np
@@ -153,3 +154,69 @@ def test_jit_gradients_random_circuits(ctx, dtype, ppr):
     assert_rel(e.cpu().numpy(), e_ref, dtype, "expectations", zero_scale=obs_scale(obs))
     assert_rel(gp.cpu().numpy(), gp_ref, dtype, "grad params (specialised reverse)", zero_scale=gscale)
     assert_rel(gd.cpu().numpy(), gd_ref, dtype, "grad data (specialised reverse)", zero_scale=gscale)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+@pytest.mark.parametrize("ppr", [False, True])
+def test_jit_whole_row_kernel(ctx, dtype, ppr):
+    """The whole-row kernel with the row program compiled in (forward,
+    expectations, lambda and the reverse sweep in one kernel): random
+    circuits over every kind with parity-diagonal ops, SWAPs, encoded
+    features, shared or per-row parameters and a ragged batch, against the
+    oracle and the interpreting kernel."""
+    n, batch = 10, 37
+    rng = np.random.default_rng(1700 + ppr)
+    gates, npar = random_gates(n, 8 * n, rng, nfeat=2)
+    gates += [W.Gate("rzz", (2, 7), angle=0.6), W.Gate("swap", (0, n - 1)), W.Gate("rxx", (3, 5), angle=1.1)]
+    params = rng.uniform(-4, 4, size=(batch, npar) if ppr else npar)
+    data = rng.uniform(-3, 3, size=(batch, 2))
+    obs = [W.obs_tfim_open(n, 0.5), [(0.7, 1, (1 << n) - 1), (-0.4, 0, 1)]]
+    w = rng.normal(size=(batch, 2))
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=2)
+    out = {}
+    for jit in (1, 0):
+        ctx.set_option(dq.OPT_JIT, jit)
+        st = torch.empty((batch, 1 << n), dtype=dtype, device="cuda")
+        ctx.set_tracing(True)
+        e, gp, gd, _ = ctx.forward_grad(circ, dev(params), dq.Observables(obs), batch, dtype, data=dev(data),
+                                        row_weights=dev(w), params_per_row=ppr, state_out=st)
+        torch.cuda.synchronize()
+        names = set(ctx.trace())
+        ctx.set_tracing(False)
+        ctx.check()
+        assert ("k_rows_jit" in names) == (jit == 1) and ("k_rows" in names) == (jit == 0), names
+        out[jit] = (st, e, gp, gd)
+    st, e, gp, gd = out[1]
+    ref = oracle.run(n, gates, params, data, batch=batch, params_per_row=ppr)
+    assert_amps(np_state(st), ref, dtype, "whole-row kernel (specialised)")
+    e_ref, gp_ref, gd_ref = oracle.adjoint(n, gates, obs, params, data, batch=batch, params_per_row=ppr,
+                                           row_weights=w)
+    gscale = float(np.abs(w).max(axis=1).sum()) * obs_scale(obs)
+    assert_rel(e.cpu().numpy(), e_ref, dtype, "expectations (specialised rows)", zero_scale=obs_scale(obs))
+    assert_rel(gp.cpu().numpy(), gp_ref, dtype, "grad params (specialised rows)", zero_scale=gscale)
+    assert_rel(gd.cpu().numpy(), gd_ref, dtype, "grad data (specialised rows)", zero_scale=gscale)
+    tol = 1e-5 if dtype == torch.complex64 else 1e-12
+    assert float((out[1][0] - out[0][0]).abs().max()) <= tol
+
+
+def test_jit_whole_row_autotuned(ctx):
+    """DQ_OPT_JIT = 2: dq_plan_autotune times the whole-row kernel both ways
+    and keeps one; results hold either way, and a later tile tuning of the
+    same plan keeps the choice."""
+    wl = W.config_c3(batch=256)
+    circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams, nfeatures=wl.nfeatures)
+    ctx.set_option(dq.OPT_JIT, 2)
+    st = torch.empty((wl.batch, 1 << wl.n), dtype=torch.complex64, device="cuda")
+    ctx.plan_autotune(circ, st)
+    ctx.set_tracing(True)
+    e, gp, gd, _ = ctx.forward_grad(circ, dev(wl.params), dq.Observables(wl.observables), wl.batch, torch.complex64,
+                                    data=dev(wl.data))
+    torch.cuda.synchronize()
+    names = set(ctx.trace())
+    ctx.set_tracing(False)
+    assert ("k_rows_jit" in names) != ("k_rows" in names), names
+    e_ref, gp_ref, gd_ref = oracle.adjoint(wl.n, wl.gates, wl.observables, wl.params, wl.data, batch=wl.batch)
+    scale = obs_scale(wl.observables)
+    assert_rel(e.cpu().numpy(), e_ref, torch.complex64, "expectations (autotuned rows)", zero_scale=scale)
+    assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, "grad params (autotuned rows)", zero_scale=wl.batch * scale)
+    assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, "grad data (autotuned rows)", zero_scale=scale)

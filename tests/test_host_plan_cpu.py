@@ -516,6 +516,28 @@ def test_specialised_pass_source_compiles():
     # the reverse sweep's passes (gradients on the parametric gates)
     rsched = _lib.tile_schedule(c, 9, 5, 3, adjoint=True)
     rsrc = _lib.jit_source(c, 9, 5, 3, adjoint=True)
-    assert rsrc.count("struct JitRev") == len(rsched) and "eng_adjoint" in rsrc
+    assert rsrc.count("struct JitRev") == len(rsched) and "adj_pair" in rsrc and "eng_adjoint" not in rsrc
     st, log = _lib.jit_compile_check(c, 9, 5, 3, cc=103, adjoint=True)
+    assert st == 0, log
+
+
+def test_specialised_row_kernel_source_compiles():
+    """The whole-row kernel with a row program's ops compiled in: one kernel,
+    forward and reverse segments as direct handler calls (parity-diagonal
+    ops included), compiled for sm_103a with NVRTC (no device needed)."""
+    from paper_2512_18995_gb300 import _lib
+    n = 9
+    gates = W.encode_layer(n) + W.hea_layers(n, 1) + [W.Gate("rzz", (2, 7), param=2 * n),
+                                                       W.Gate("swap", (1, 8)), W.Gate("crx", (0, 5), angle=0.4)]
+    c = _lib.Circuit(n, gates, nparams=2 * n + 1, nfeatures=n)
+    _, order, flags = _lib.row_program(c)
+    src = _lib.jit_source(c, 0, 0, 0, kind=_lib.JIT_ROWS)
+    assert src.count("__global__") == 1 and "dq_jit_rows" in src and "struct JitRows" in src
+    assert "adj_pdiag" in src and "eng_pdiag" in src and any(f & 1 for f in flags)
+    assert "eng_adjoint" not in src and "eng_apply" not in src
+    with pytest.raises(_lib.DQError):
+        _lib.jit_source(c, 0, 0, 0, kind=3)
+    st, log = _lib.jit_compile_check(c, 0, 0, 0, kind=_lib.JIT_ROWS, cc=103)
+    if st == 2:
+        pytest.skip("NVRTC is not available here")
     assert st == 0, log
