@@ -243,8 +243,23 @@ DQ_API dq_status dq_batch_workspace_bytes(dq_ctx *ctx, int ncirc, const dq_circu
                                           int dtype, size_t *out);
 
 /* Synchronise `stream` and report device-side failures recorded by earlier
- * calls (DQ_ERR_TIMEOUT for a bounded wait that gave up), then clear them. */
+ * calls (DQ_ERR_TIMEOUT for a bounded wait that gave up; in the
+ * bounds-checking build, DQ_ERR_CUDA for indices outside their buffer, the
+ * message naming the first one and its source site), then clear them. */
 DQ_API dq_status dq_ctx_check(dq_ctx *ctx, void *stream);
+
+/* The bounds-checking build: libdq_debug.so, compiled with DQ_DEBUG_BOUNDS
+ * (build.build(debug=True); the Python binding loads it when the environment
+ * variable DQ_DEBUG_BOUNDS is 1).  The per-gate sweep kernels, the engine's
+ * register-layout loads and stores (tile passes, whole-row kernels), the
+ * observable passes' partner reads, the reverse passes' result stores and
+ * the whole-row kernels' global state and partner accesses check every index
+ * against its buffer (2^n amplitudes per row, 2^k per tile); an index outside
+ * skips its access and is counted for dq_ctx_check.  Run-time specialisation
+ * (DQ_OPT_JIT) is off in that build.  dq_selftest_bounds launches one check
+ * that fails without touching memory (the next dq_ctx_check reports it);
+ * DQ_ERR_UNSUPPORTED in the normal build. */
+DQ_API dq_status dq_selftest_bounds(dq_ctx *ctx, void *stream);
 
 /* Failure-detection self-test (no counterpart in the paper): launches on
  * `stream` one kernel whose bounded wait runs out on purpose -- it waits on

@@ -14,7 +14,8 @@ from typing import Iterable, List, Optional, Sequence, Tuple
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdq.so")
+# DQ_DEBUG_BOUNDS=1 selects the bounds-checking build (build.build(debug=True))
+LIB_PATH = os.path.join(_HERE, "libdq_debug.so" if os.environ.get("DQ_DEBUG_BOUNDS") == "1" else "libdq.so")
 
 # dq_status
 DQ_OK = 0
@@ -69,7 +70,7 @@ class dq_lowered_op(ctypes.Structure):
 
 
 EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path", "dq_ctx_set_option",
-           "dq_state_norm", "dq_selftest_wait_expiry", "dq_batch_autotune", "dq_jit_source",
+           "dq_state_norm", "dq_selftest_wait_expiry", "dq_selftest_bounds", "dq_batch_autotune", "dq_jit_source",
            "dq_jit_compile_check",
            "dq_ctx_set_workspace",
            "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_graphs", "dq_ctx_set_tracing",
@@ -107,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         "dq_batch_autotune": ([P, I, C, P, ctypes.POINTER(ctypes.c_int64), O, I, P, P,
                                ctypes.POINTER(ctypes.c_int), P], I),
         "dq_selftest_wait_expiry": ([P, P], I),
+        "dq_selftest_bounds": ([P, P], I),
         "dq_ctx_set_workspace": ([P, P, ctypes.c_size_t], I),
         "dq_workspace_bytes": ([P, C, O, I, I, ctypes.POINTER(ctypes.c_size_t)], I),
         "dq_batch_workspace_bytes": ([P, I, C, I, ctypes.POINTER(ctypes.c_size_t)], I),
@@ -455,6 +457,12 @@ class Context:
         """dq_selftest_wait_expiry: one bounded wait runs out on purpose; the
         next check() raises DQError(DQ_ERR_TIMEOUT)."""
         self._check(self.lib.dq_selftest_wait_expiry(self.h, _stream()), "dq_selftest_wait_expiry")
+
+    def selftest_bounds(self):
+        """dq_selftest_bounds (bounds-checking build only): one index check
+        fails without touching memory; the next check() raises DQError
+        (DQ_ERR_CUDA) naming it.  DQ_ERR_UNSUPPORTED in the normal build."""
+        self._check(self.lib.dq_selftest_bounds(self.h, _stream()), "dq_selftest_bounds")
 
     def state_norm(self, state: torch.Tensor, nqubits: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         """<psi|psi> of every row (FP64 accumulation), shape (batch,)."""

@@ -28,6 +28,24 @@
 
 using namespace dq;
 
+#ifdef DQ_BOUNDS_BUILD
+namespace dq {
+__device__ unsigned long long g_dq_bounds[4];   // see DQ_INB
+}  // namespace dq
+
+namespace {
+// The source file of a bounds-check site (the hash of its base name).
+const char *bounds_site_file(unsigned h) {
+    static const char *const files[] = {"k_plain.cu", "k_tile_adj.cu", "k_tile.cu", "k_rows.cu", "k_wsv.cu",
+                                        "dq_engine.cuh", "dq_tile_adj.cuh", "dq_tile_fwd.cuh", "dq_rows_body.cuh",
+                                        "k_norm.cu", "k_dense.cu", "k_sample.cu", "k_density.cu", "k_hessian.cu"};
+    for (const char *f : files)
+        if (dq_site_hash(f) == h) return f;
+    return "(unknown file)";
+}
+}  // namespace
+#endif
+
 namespace {
 
 struct ObsDev {
@@ -1474,6 +1492,19 @@ dq_status dq_ctx_check(dq_ctx *ctx, void *stream) {
     dq_status st = check_ctx(ctx);
     if (st != DQ_OK) return st;
     DQ_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+#ifdef DQ_BOUNDS_BUILD
+    {
+        unsigned long long rec[4] = {0, 0, 0, 0};
+        DQ_CUDA(cudaMemcpyFromSymbol(rec, g_dq_bounds, sizeof(rec)), "read bounds record");
+        if (rec[0]) {
+            const unsigned long long zero[4] = {0, 0, 0, 0};
+            cudaMemcpyToSymbol(g_dq_bounds, zero, sizeof(zero));
+            return fail(ctx, DQ_ERR_CUDA, "bounds check: %llu index(es) outside their buffer, first %llu >= %llu at %s:%u",
+                        rec[0], rec[1], rec[2], bounds_site_file((unsigned)(rec[3] >> 32)),
+                        (unsigned)(rec[3] & 0xffffffffu));
+        }
+    }
+#endif
     int flag = 0;
     DQ_CUDA(cudaMemcpy(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
     if (flag != DEVERR_NONE) {
@@ -1483,6 +1514,15 @@ dq_status dq_ctx_check(dq_ctx *ctx, void *stream) {
             return fail(ctx, DQ_ERR_CUDA, "a device-side bounds check found an index outside its buffer");
         return fail(ctx, DQ_ERR_CUDA, "device-side check failed (code %d)", flag);
     }
+    return DQ_OK;
+}
+
+dq_status dq_selftest_bounds(dq_ctx *ctx, void *stream) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    const cudaError_t e = selftest_bounds((cudaStream_t)stream, &ctx->launches);
+    if (e == cudaErrorNotSupported) return fail(ctx, DQ_ERR_UNSUPPORTED, "not a bounds-checking build");
+    DQ_CUDA(e, "k_bounds_selftest");
     return DQ_OK;
 }
 

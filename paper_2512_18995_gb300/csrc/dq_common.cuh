@@ -214,6 +214,38 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Device-side error flag codes (written with atomicCAS so the first wins).
 enum DevErr : int { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1, DEVERR_BOUNDS = 2 };
 
+// Bounds-checking build (DQ_DEBUG_BOUNDS, libdq_debug.so): DQ_INB(i, lim)
+// is false when index i is not below lim; the access it guards is skipped
+// and the failure is counted in g_dq_bounds (count, first index, its limit,
+// source site), which dq_ctx_check reports.  In the normal build it is the
+// constant true and guards nothing.
+#if defined(DQ_DEBUG_BOUNDS) && !defined(__CUDACC_RTC__)
+#define DQ_BOUNDS_BUILD 1
+extern __device__ unsigned long long g_dq_bounds[4];
+constexpr unsigned dq_site_hash(const char *f, unsigned h = 2166136261u) {
+    return *f ? dq_site_hash(f + 1, (h ^ (unsigned char)*f) * 16777619u) : h;
+}
+__device__ __forceinline__ bool dq_in_bounds(uint64_t i, uint64_t lim, unsigned long long site) {
+    if (i < lim) return true;
+    if (atomicAdd(&g_dq_bounds[0], 1ull) == 0) {
+        g_dq_bounds[1] = i;
+        g_dq_bounds[2] = lim;
+        g_dq_bounds[3] = site;
+    }
+    return false;
+}
+#ifdef __FILE_NAME__
+#define DQ_SITE_FILE __FILE_NAME__
+#else
+#define DQ_SITE_FILE __FILE__
+#endif
+#define DQ_INB(i, lim)                                                                                      \
+    ::dq::dq_in_bounds((uint64_t)(i), (uint64_t)(lim),                                                     \
+                       ((unsigned long long)::dq::dq_site_hash(DQ_SITE_FILE) << 32) | (unsigned long long)__LINE__)
+#else
+#define DQ_INB(i, lim) true
+#endif
+
 // The context's 256-byte flag block: the error flag at byte 0, the limit of
 // every device-side bounded wait (nanoseconds, uint64) at byte 64, the
 // multi-pass grid barrier's arrival counter at byte 128.

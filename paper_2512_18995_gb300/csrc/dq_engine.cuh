@@ -414,6 +414,9 @@ inline bool pair_handlers_match(const EOp &real, const EOp &diag) {
 struct Layout {
     uint32_t tb;     // this thread's local index with register bits zero
     uint32_t off[8]; // local offset of register bit i
+#ifdef DQ_BOUNDS_BUILD
+    uint32_t lim;    // 2^k: the buffer's amplitudes (bounds-checking build)
+#endif
 };
 
 __device__ __forceinline__ Layout make_layout(const ESeg &sg, int M, int k, int lane, int warp) {
@@ -432,6 +435,9 @@ __device__ __forceinline__ Layout make_layout(const ESeg &sg, int M, int k, int 
         ++wi;
     }
     L.tb = tb;
+#ifdef DQ_BOUNDS_BUILD
+    L.lim = 1u << k;
+#endif
     return L;
 }
 
@@ -447,13 +453,25 @@ __device__ __forceinline__ uint32_t reg_off(const Layout &L, int e) {
 template <typename R, int M>
 __device__ __forceinline__ void eng_load(cx<R> (&a)[1 << M], const cx<R> *buf, const Layout &L) {
 #pragma unroll
-    for (int e = 0; e < (1 << M); ++e) a[e] = buf[L.tb | reg_off<M>(L, e)];
+    for (int e = 0; e < (1 << M); ++e) {
+        const uint32_t i = L.tb | reg_off<M>(L, e);
+#ifdef DQ_BOUNDS_BUILD
+        if (!DQ_INB(i, L.lim)) continue;
+#endif
+        a[e] = buf[i];
+    }
 }
 
 template <typename R, int M>
 __device__ __forceinline__ void eng_store(const cx<R> (&a)[1 << M], cx<R> *buf, const Layout &L) {
 #pragma unroll
-    for (int e = 0; e < (1 << M); ++e) buf[L.tb | reg_off<M>(L, e)] = a[e];
+    for (int e = 0; e < (1 << M); ++e) {
+        const uint32_t i = L.tb | reg_off<M>(L, e);
+#ifdef DQ_BOUNDS_BUILD
+        if (!DQ_INB(i, L.lim)) continue;
+#endif
+        buf[i] = a[e];
+    }
 }
 
 template <typename T> __device__ __forceinline__ T shfl_xor_cx(T v, int m);

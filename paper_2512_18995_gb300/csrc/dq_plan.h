@@ -159,6 +159,8 @@ template <typename R>
 cudaError_t state_norm(const void *state, int n, int batch, double *part, double *out, cudaStream_t s,
                        int64_t *launches);
 cudaError_t selftest_wait_expiry(int *errflag, cudaStream_t s, int64_t *launches);
+// bounds-checking build: one failing check (cudaErrorNotSupported otherwise)
+cudaError_t selftest_bounds(cudaStream_t s, int64_t *launches);
 
 // ---- whole state in shared memory (small n) --------------------------------
 size_t wsv_smem_bytes(int n, int dtype_bytes, bool grad, int ngrad_acc);

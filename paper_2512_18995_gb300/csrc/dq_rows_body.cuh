@@ -155,7 +155,10 @@ __device__ __forceinline__ void rows_body(const RowArgs &a) {
         if (a.state_in) {
             const cx<R> *gi = reinterpret_cast<const cx<R> *>(a.state_in) + row * dim;
 #pragma unroll
-            for (int e = 0; e < (1 << M); ++e) ps[e] = gi[L.tb | reg_off<M>(L, e)];
+            for (int e = 0; e < (1 << M); ++e) {
+                const uint32_t i = L.tb | reg_off<M>(L, e);
+                ps[e] = DQ_INB(i, dim) ? gi[i] : mk<R>(R(0), R(0));
+            }
         } else {
 #pragma unroll
             for (int e = 0; e < (1 << M); ++e)
@@ -167,7 +170,10 @@ __device__ __forceinline__ void rows_body(const RowArgs &a) {
         if (a.state_out) {
             cx<R> *go = reinterpret_cast<cx<R> *>(a.state_out) + row * dim;
 #pragma unroll
-            for (int e = 0; e < (1 << M); ++e) go[L.tb | reg_off<M>(L, e)] = ps[e];
+            for (int e = 0; e < (1 << M); ++e) {
+                const uint32_t i = L.tb | reg_off<M>(L, e);
+                if (DQ_INB(i, dim)) go[i] = ps[e];
+            }
         }
         const bool need_smem_state = a.nterms > 0 || a.grad;
         if (need_smem_state) {
@@ -187,6 +193,7 @@ __device__ __forceinline__ void rows_body(const RowArgs &a) {
                     }
                 } else {
                     for (int64_t b = tid; b < dim; b += blockDim.x) {
+                        if (!DQ_INB(b ^ f, dim)) continue;
                         const cx<R> x = bufP[b], y = bufP[b ^ f];
                         const R re = re_conj_mul(y, x), im = im_conj_mul(y, x);
                         const int ph = (t.nY + 2 * parity64((uint64_t)b & sm)) & 3;
@@ -222,6 +229,7 @@ __device__ __forceinline__ void rows_body(const RowArgs &a) {
                 const DevTerm t = a.terms[k];
                 const uint64_t f = wire_bits(t.f, n), sm = wire_bits(t.s, n);
                 const uint64_t src = l ^ f;
+                if (!DQ_INB(src, dim)) continue;
                 float pr, pi;
                 pauli_phase(src, sm, t.nY, pr, pi);
                 const R wt = (R)((w ? w[t.obs] : 1.0) * t.coeff);

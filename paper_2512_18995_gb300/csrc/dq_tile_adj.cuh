@@ -2,10 +2,16 @@
 // interprets each pass's reverse program from shared memory, and the run-time
 // specialised kernels, which have each pass's ops compiled in (internal).
 //
-// A pass streams psi and lambda tiles in and out with TMA; inside a tile each
-// op's gradient partial 2 Im <lambda|G|psi> is formed (after its gate) and
-// the gate is un-applied on both vectors, segment by segment; per-warp FP32
-// partials are folded into the CTA's FP64 accumulators per tile.
+// A pass streams psi and lambda tiles in with TMA; inside a tile each op's
+// gradient partial 2 Im <lambda|G|psi> is formed (after its gate) and the
+// gate is un-applied on both vectors, segment by segment; per-warp FP32
+// partials are folded into the CTA's FP64 accumulators per tile.  Once the
+// last segment's register layout has been read from shared memory, the next
+// tile's copies are issued into the same buffers, and the results go from
+// registers straight to global memory (a warp's 32 lanes hold 32 consecutive
+// amplitudes: the low tile bits are the low amplitude bits), so the copy-in
+// of tile t + 1 overlaps the last segment of tile t and nothing waits for a
+// copy-out.
 #pragma once
 
 #include "dq_engine.cuh"
@@ -26,10 +32,83 @@ struct AdjArgs {
     int batch;
     int *errflag;
     int any_row;       // some op's coefficients depend on the batch row
+    void *psi, *lam;   // the vectors the tensor maps describe (direct stores)
+    // amplitude bit of tile bit i (ascending; the low ones are 0, 1, ...):
+    // byte i of tbit[0] for i < 8, byte i - 8 of tbit[1] otherwise
+    uint64_t tbit[2];
+};
+
+// Tile copy-in of the next tile and copy-out of the current one (see the
+// file comment).  Runners call prefetch() once every thread holds the last
+// segment's registers (all reads of the tile buffers done) and store() with
+// that segment's layout instead of writing the buffers back.
+// The per-tile values the copies need live in shared memory next to the
+// copy barrier (written by thread 0 before the tile's first barrier), so
+// nothing of them stays in registers through the tile's ops.
+struct AdjTileSlot {
+    uint64_t bar;       // copy barrier
+    uint64_t gbase;     // row * 2^n + base of the current tile (amplitudes)
+    int next_c[5];      // TMA coordinates of the next tile
+    int has_next;
+};
+static_assert(sizeof(AdjTileSlot) <= 64, "tile slot fits the reserved 64 bytes");
+
+template <typename R>
+struct AdjIo {
+    const AdjArgs *a;                 // the kernel's (grid-constant) arguments
+    const CUtensorMap *mp, *ml;
+    AdjTileSlot *slot;
+    cx<R> *bufP, *bufL;
+
+    __device__ __forceinline__ void prefetch() const {
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0 && slot->has_next) {
+            const uint32_t tbytes = (uint32_t)(sizeof(cx<R>) << a->g.k);
+            mbar_expect_tx(&slot->bar, 2 * tbytes);
+            tma_load5(bufP, mp, slot->next_c, &slot->bar);
+            tma_load5(bufL, ml, slot->next_c, &slot->bar);
+        }
+    }
+    // amplitude bit of tile bit i
+    __device__ __forceinline__ int tbit(int i) const { return (int)((a->tbit[i >> 3] >> (8 * (i & 7))) & 63); }
+    // amplitude offset of local index l within the row's state (the lane
+    // bits are the low amplitude bits)
+    __device__ __forceinline__ uint64_t scatter(uint32_t l) const {
+        uint64_t r = l & ((1u << kLaneBits) - 1);
+#pragma unroll
+        for (int i = kLaneBits; i < 16; ++i)
+            if (i < a->g.k && ((l >> i) & 1)) r |= uint64_t(1) << tbit(i);
+        return r;
+    }
+    template <int M>
+    __device__ __forceinline__ void store(const cx<R> (&ps)[1 << M], const cx<R> (&ls)[1 << M],
+                                          const Layout &L) const {
+        const uint64_t t0 = slot->gbase | scatter(L.tb);
+        cx<R> *gp = reinterpret_cast<cx<R> *>(a->psi) + t0;
+        const int64_t dl = reinterpret_cast<cx<R> *>(a->lam) - reinterpret_cast<cx<R> *>(a->psi);
+        uint64_t so[M];   // register bit i: one tile bit (L.off[i]) at its amplitude bit
+#pragma unroll
+        for (int i = 0; i < M; ++i) so[i] = uint64_t(1) << tbit(__ffs((int)L.off[i]) - 1);
+#pragma unroll
+        for (int e = 0; e < (1 << M); ++e) {
+            uint64_t o = 0;
+#pragma unroll
+            for (int i = 0; i < M; ++i)
+                if ((e >> i) & 1) o |= so[i];
+            if (!DQ_INB(t0 | o, (uint64_t)a->batch << a->g.n)) continue;
+            gp[o] = ps[e];
+            gp[o + dl] = ls[e];
+        }
+    }
 };
 
 template <typename R, int M>
 constexpr int adj_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) <= 64) ? 512 : 256; }
+// Two CTAs of 256 threads per SM for complex64 (the large-state shape: 12-qubit
+// tiles, four register bits): 128 registers a thread.
+template <typename R, int M>
+constexpr int adj_min_blocks() { return (sizeof(R) == 4 && adj_max_threads<R, M>() == 256) ? 2 : 1; }
 
 // The interpreter: every op dispatched from the staged reverse program.
 struct InterpRev {
@@ -37,12 +116,15 @@ struct InterpRev {
     __device__ __forceinline__ static void run(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M], cx<R> *bufP, cx<R> *bufL,
                                                const EOp *sops, const ESeg *ssegs, const Mat2<R> *scoef, R *accw,
                                                int nslot, int nseg, int op0, int k, uint64_t base, int lane,
-                                               int warp) {
+                                               int warp, const AdjIo<R> &io) {
+        if (nseg == 0) io.prefetch();   // nothing changes in this tile: no copy-out
         for (int si = 0; si < nseg; ++si) {
             const ESeg sg = ssegs[si];
             const Layout L = make_layout(sg, M, k, lane, warp);
             eng_load<R, M>(ps, bufP, L);
             eng_load<R, M>(ls, bufL, L);
+            const bool last = si == nseg - 1;
+            if (last) io.prefetch();
             for (int cc = 0; cc < sg.nops; ++cc) {
                 const int oi = sg.op0 - op0 - cc;
                 const EOp o = sops[oi];
@@ -69,9 +151,13 @@ struct InterpRev {
                     if (lane == 0) accw[warp * nslot + o.slot] += gs;
                 }
             }
-            eng_store<R, M>(ps, bufP, L);
-            eng_store<R, M>(ls, bufL, L);
-            __syncthreads();
+            if (last) {
+                io.template store<M>(ps, ls, L);
+            } else {
+                eng_store<R, M>(ps, bufP, L);
+                eng_store<R, M>(ls, bufL, L);
+                __syncthreads();
+            }
         }
     }
 };
@@ -86,7 +172,8 @@ __device__ __forceinline__ void tile_adj_body(const CUtensorMap &mp, const CUten
     const size_t tbytes = sizeof(cx<R>) << a.g.k;
     cx<R> *bufP = reinterpret_cast<cx<R> *>(smem);
     cx<R> *bufL = reinterpret_cast<cx<R> *>(smem + tbytes);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * tbytes);
+    AdjTileSlot *slot = reinterpret_cast<AdjTileSlot *>(smem + 2 * tbytes);
+    uint64_t *bar = &slot->bar;
     EOp *sops = reinterpret_cast<EOp *>(smem + 2 * tbytes + 64);
     ESeg *ssegs = reinterpret_cast<ESeg *>(sops + a.nops);
     Mat2<R> *scoef = reinterpret_cast<Mat2<R> *>(ssegs + a.nseg);
@@ -129,6 +216,13 @@ __device__ __forceinline__ void tile_adj_body(const CUtensorMap &mp, const CUten
         }
     };
     cx<R> ps[1 << M], ls[1 << M];
+    AdjIo<R> io;
+    io.a = &a;
+    io.mp = &mp;
+    io.ml = &ml;
+    io.slot = slot;
+    io.bufP = bufP;
+    io.bufL = bufL;
     int64_t crow = 0;   // the table holds row 0's coefficient blocks
     for (int64_t t = t0; t < t1; ++t) {
         int c[5];
@@ -147,11 +241,17 @@ __device__ __forceinline__ void tile_adj_body(const CUtensorMap &mp, const CUten
             __syncthreads();
             crow = row;
         }
-        if (tid == 0 && t > t0) {
-            mbar_expect_tx(&bar[0], (uint32_t)(2 * tbytes));
-            tma_load5(bufP, &mp, c, &bar[0]);
-            tma_load5(bufL, &ml, c, &bar[0]);
+        if (tid == 0) {
+            slot->gbase = ((uint64_t)row << a.g.n) | base;
+            slot->has_next = t + 1 < t1;
+            if (t + 1 < t1) {
+                uint64_t nb;
+                int64_t nr;
+                geom_coords(a.g, t + 1, slot->next_c, nb, nr);
+            }
         }
+        // this tile's copies were issued by the prologue or by the previous
+        // tile's prefetch
         const bool ok = mbar_wait_bounded(&bar[0], phase, wlim);
         phase ^= 1;
         if (__syncthreads_or(!ok)) {
@@ -159,7 +259,8 @@ __device__ __forceinline__ void tile_adj_body(const CUtensorMap &mp, const CUten
             break;
         }
         Runner::template run<R, M>(ps, ls, bufP, bufL, sops, ssegs, scoef, accw, a.nslot, a.nseg, a.op0, a.g.k,
-                                   base, lane, warp);
+                                   base, lane, warp, io);
+        __syncthreads();   // every warp's partials are in accw
         for (int j = tid; j < a.nslot; j += blockDim.x) {
             double sum = 0.0;
             for (int ww = 0; ww < nw; ++ww) {
@@ -168,15 +269,6 @@ __device__ __forceinline__ void tile_adj_body(const CUtensorMap &mp, const CUten
             }
             acc[j] += sum;
         }
-        fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tma_store5(&mp, c, bufP);
-            tma_store5(&ml, c, bufL);
-            bulk_commit();
-            bulk_wait_read0();
-        }
-        __syncthreads();
     }
     if (!failed && cur_row >= 0) {
         __syncthreads();
@@ -186,7 +278,6 @@ __device__ __forceinline__ void tile_adj_body(const CUtensorMap &mp, const CUten
         atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
         mbar_wait_bounded(&bar[0], phase, wlim);
     }
-    if (tid == 0) bulk_wait0();
 }
 
 }  // namespace

@@ -16,8 +16,11 @@
 // dlopen on first use: without it the interpreter simply stays in use.
 #include <dlfcn.h>
 #include <nvrtc.h>
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <sstream>
@@ -45,6 +48,7 @@ struct NvrtcApi {
     nvrtcResult (*cubin_size)(nvrtcProgram, size_t *) = nullptr;
     nvrtcResult (*cubin)(nvrtcProgram, char *) = nullptr;
     nvrtcResult (*destroy)(nvrtcProgram *) = nullptr;
+    nvrtcResult (*version)(int *, int *) = nullptr;
 };
 
 NvrtcApi &nvrtc_api() {
@@ -64,9 +68,77 @@ NvrtcApi &nvrtc_api() {
         api.cubin_size = reinterpret_cast<decltype(api.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
         api.cubin = reinterpret_cast<decltype(api.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
         api.destroy = reinterpret_cast<decltype(api.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+        api.version = reinterpret_cast<decltype(api.version)>(dlsym(h, "nvrtcVersion"));
         api.ok = api.create && api.compile && api.log_size && api.log && api.cubin_size && api.cubin && api.destroy;
     });
     return api;
+}
+
+// ---- compiled-program cache -------------------------------------------------
+// A compiled program is kept on disk under a key of everything that decides
+// its bytes: the generated source, the target architecture, the embedded
+// device headers and the NVRTC version.  The folder is DQ_JIT_CACHE when set
+// (empty or "0": no cache), else _jit_cache next to this library.
+uint64_t fnv64(uint64_t h, const void *p, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+std::string cache_dir() {
+    if (const char *env = std::getenv("DQ_JIT_CACHE")) {
+        if (!*env || std::strcmp(env, "0") == 0) return std::string();
+        return env;
+    }
+    Dl_info info;
+    if (!dladdr(reinterpret_cast<void *>(&cache_dir), &info) || !info.dli_fname) return std::string();
+    std::string lib = info.dli_fname;
+    const size_t slash = lib.rfind('/');
+    return (slash == std::string::npos ? std::string(".") : lib.substr(0, slash)) + "/_jit_cache";
+}
+
+std::string cache_path(const std::string &src, int cc) {
+    const std::string dir = cache_dir();
+    if (dir.empty()) return std::string();
+    int major = 0, minor = 0;
+    if (nvrtc_api().version) nvrtc_api().version(&major, &minor);
+    uint64_t h1 = 1469598103934665603ull, h2 = 7809847782465536322ull;
+    auto mix = [&](const void *p, size_t n) {
+        h1 = fnv64(h1, p, n);
+        h2 = fnv64(h2 ^ 0x9e3779b97f4a7c15ull, p, n);
+    };
+    mix(src.data(), src.size());
+    const int meta[3] = {cc, major, minor};
+    mix(meta, sizeof(meta));
+    for (int i = 0; i < kJitHeaderCount; ++i) mix(kJitHeaderTexts[i], std::strlen(kJitHeaderTexts[i]));
+    char name[64];
+    std::snprintf(name, sizeof(name), "/%016llx%016llx.cubin", (unsigned long long)h1, (unsigned long long)h2);
+    return dir + name;
+}
+
+bool cache_read(const std::string &path, std::vector<char> *cubin) {
+    FILE *f = path.empty() ? nullptr : std::fopen(path.c_str(), "rb");
+    if (!f) return false;
+    std::vector<char> buf;
+    char chunk[65536];
+    size_t got;
+    while ((got = std::fread(chunk, 1, sizeof(chunk), f)) > 0) buf.insert(buf.end(), chunk, chunk + got);
+    std::fclose(f);
+    if (buf.size() < 4 || std::memcmp(buf.data(), "\x7f" "ELF", 4) != 0) return false;   // not a cubin
+    cubin->swap(buf);
+    return true;
+}
+
+void cache_write(const std::string &path, const std::vector<char> &cubin) {
+    if (path.empty()) return;
+    const std::string dir = path.substr(0, path.rfind('/'));
+    mkdir(dir.c_str(), 0755);   // may exist
+    const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    const bool ok = std::fwrite(cubin.data(), 1, cubin.size(), f) == cubin.size();
+    std::fclose(f);
+    if (!ok || std::rename(tmp.c_str(), path.c_str()) != 0) std::remove(tmp.c_str());
 }
 
 std::string hex32(uint32_t v) {
@@ -181,12 +253,13 @@ void emit_adj_pair(std::ostringstream &s, const EOp &d, const EOp &r, int i, int
 
 // One reverse segment of a pass: gradient partials and un-application of
 // its ops, highest first (a rotation pair consumes its REAL op too).
-void emit_rev_segment(std::ostringstream &s, const TileSchedule &sc, const TPass &ps, const TSeg &sg) {
+void emit_rev_segment(std::ostringstream &s, const TileSchedule &sc, const TPass &ps, const TSeg &sg, bool last) {
     const int M = sc.M;
     s << "    {\n        ESeg sg{}; ";
     for (int b = 0; b < M; ++b) s << "sg.B[" << b << "] = " << (int)sg.B[b] << "; ";
     s << "\n        const Layout L = make_layout(sg, M, " << sc.k << ", lane, warp);\n"
          "        eng_load<R, M>(ps, bufP, L);\n        eng_load<R, M>(ls, bufL, L);\n";
+    if (last) s << "        io.prefetch();\n";
     for (int cc = 0; cc < sg.nops; ++cc) {
         const int oi = sg.op0 - ps.op0 - cc;
         const EOp &o = sc.rops[ps.op0 + oi];
@@ -197,8 +270,11 @@ void emit_rev_segment(std::ostringstream &s, const TileSchedule &sc, const TPass
         }
         emit_adj_op(s, o, oi, M, false, ps.nslot);
     }
-    s << "        eng_store<R, M>(ps, bufP, L);\n        eng_store<R, M>(ls, bufL, L);\n        __syncthreads();\n"
-         "    }\n";
+    if (last)
+        s << "        io.template store<M>(ps, ls, L);\n    }\n";
+    else
+        s << "        eng_store<R, M>(ps, bufP, L);\n        eng_store<R, M>(ls, bufL, L);\n        __syncthreads();\n"
+             "    }\n";
 }
 
 // One op of a pass (index i in the pass's op list); returns the number of
@@ -346,8 +422,10 @@ std::string jit_source(const TileSchedule &sc, int amp, std::vector<std::string>
                  "    template <typename R, int M>\n"
                  "    __device__ __forceinline__ static void run(cx<R> (&ps)[1 << M], cx<R> (&ls)[1 << M],\n"
                  "        cx<R> *bufP, cx<R> *bufL, const EOp *, const ESeg *, const Mat2<R> *scoef, R *accw,\n"
-                 "        int, int, int, int, uint64_t base, int lane, int warp) {\n";
-            for (int si = ps.rseg0; si < ps.rseg0 + ps.nrseg; ++si) emit_rev_segment(s, sc, ps, sc.rsegs[si]);
+                 "        int, int, int, int, uint64_t base, int lane, int warp, const AdjIo<R> &io) {\n";
+            if (ps.nrseg == 0) s << "        io.prefetch();\n";
+            for (int si = ps.rseg0; si < ps.rseg0 + ps.nrseg; ++si)
+                emit_rev_segment(s, sc, ps, sc.rsegs[si], si == ps.rseg0 + ps.nrseg - 1);
             s << "    }\n};\n";
         }
         s << "}  // namespace\n}  // namespace dq\n";
@@ -355,8 +433,10 @@ std::string jit_source(const TileSchedule &sc, int amp, std::vector<std::string>
         for (int p = p0; p < p1; ++p) {
             const std::string name = "dq_jit_adj_" + std::to_string(p);
             names.push_back(name);
-            s << "extern \"C\" __global__ void __launch_bounds__(" << amax << ") " << name
-              << "(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap ml, dq::AdjArgs a) {\n"
+            s << "extern \"C\" __global__ void __launch_bounds__(" << amax << ", " << (amp == 8 && amax == 256 ? 2 : 1)
+              << ") " << name
+              << "(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap ml,\n"
+              << "    const __grid_constant__ dq::AdjArgs a) {\n"
               << "    dq::tile_adj_body<" << R << ", " << M << ", dq::JitRev" << p << ">(mp, ml, a);\n}\n";
         }
         return s.str();
@@ -419,14 +499,22 @@ void JitModule::release() {
     kernels.clear();
 }
 
-bool jit_available() { return nvrtc_api().ok; }
+bool jit_available() {
+#ifdef DQ_BOUNDS_BUILD
+    return false;   // the bounds-checking build runs the (checked) interpreting kernels only
+#else
+    return nvrtc_api().ok;
+#endif
+}
 
 bool jit_compile(const std::string &src, int cc, std::vector<char> *cubin, std::string *err) {
     NvrtcApi &api = nvrtc_api();
-    if (!api.ok) {
-        if (err) *err = "NVRTC is not available";
+    if (!jit_available()) {
+        if (err) *err = api.ok ? "run-time specialisation is off in the bounds-checking build" : "NVRTC is not available";
         return false;
     }
+    const std::string cpath = cubin ? cache_path(src, cc) : std::string();
+    if (cubin && cache_read(cpath, cubin)) return true;
     const std::string arch = "-arch=sm_" + std::to_string(cc) + "a";
     nvrtcProgram prog;
     if (api.create(&prog, src.c_str(), "dq_jit_fwd.cu", kJitHeaderCount, kJitHeaderTexts, kJitHeaderNames) !=
@@ -450,6 +538,7 @@ bool jit_compile(const std::string &src, int cc, std::vector<char> *cubin, std::
         api.cubin_size(prog, &n);
         cubin->resize(n);
         api.cubin(prog, cubin->data());
+        cache_write(cpath, *cubin);
     }
     api.destroy(&prog);
     return true;

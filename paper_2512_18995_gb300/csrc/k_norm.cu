@@ -75,6 +75,14 @@ __global__ void k_wait_expiry(int *errflag) {
     if (!mbar_wait_bounded(&bar, 0u, wait_limit_ns(errflag))) atomicCAS(errflag, 0, DEVERR_TIMEOUT);
 }
 
+#ifdef DQ_BOUNDS_BUILD
+// One check that fails (index 1 against a limit of 0) and guards nothing:
+// the bounds-checking build records it as it would a bad index of a kernel.
+__global__ void k_bounds_selftest() {
+    if (threadIdx.x == 0 && !DQ_INB(1, 0)) return;
+}
+#endif
+
 }  // namespace
 
 int norm_blocks_per_row(int n, int batch) {
@@ -105,6 +113,18 @@ cudaError_t selftest_wait_expiry(int *errflag, cudaStream_t s, int64_t *launches
     LaunchScope ls(s, "k_wait_expiry", launches);
     k_wait_expiry<<<1, 32, 0, s>>>(errflag);
     return cudaGetLastError();
+}
+
+cudaError_t selftest_bounds(cudaStream_t s, int64_t *launches) {
+#ifdef DQ_BOUNDS_BUILD
+    LaunchScope ls(s, "k_bounds_selftest", launches);
+    k_bounds_selftest<<<1, 32, 0, s>>>();
+    return cudaGetLastError();
+#else
+    (void)s;
+    (void)launches;
+    return cudaErrorNotSupported;
+#endif
 }
 
 template cudaError_t state_norm<float>(const void *, int, int, double *, double *, cudaStream_t, int64_t *);

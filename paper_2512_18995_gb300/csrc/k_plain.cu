@@ -128,6 +128,8 @@ k_sweep(cx<R> *__restrict__ st, int n, UnitMap m, int64_t total, const Mat2<R> *
         if (!ok[k]) continue;
         const int64_t row = w >> m.ib;
         const uint64_t un = unit_of(m, (uint64_t)w & ((uint64_t(1) << m.ib) - 1));
+        ok[k] = DQ_INB(2 * un + 1, uint64_t(1) << n) && (!m.pbit || DQ_INB(2 * (un | m.pbit) + 1, uint64_t(1) << n));
+        if (!ok[k]) continue;
         cx<R> *rp = st + (row << n);
         pa[k] = rp + 2 * un;
         A[k] = ldu(pa[k]);
@@ -165,12 +167,14 @@ k_swap(cx<R> *__restrict__ v0, cx<R> *__restrict__ v1, int n, int a, int b, int 
         if (a >= 1) {
             const uint64_t u0 = insert0x2(j, a - 1, b - 1) | (uint64_t(1) << (a - 1));
             const uint64_t u1 = u0 ^ (uint64_t(1) << (a - 1)) ^ (uint64_t(1) << (b - 1));
+            if (!DQ_INB(2 * u0 + 1, uint64_t(1) << n) || !DQ_INB(2 * u1 + 1, uint64_t(1) << n)) continue;
             Unit<R> A = ldu(rp + 2 * u0), B = ldu(rp + 2 * u1);
             stu(rp + 2 * u0, B);
             stu(rp + 2 * u1, A);
         } else {
             const uint64_t u0 = insert0(j, b - 1);
             const uint64_t u1 = u0 | (uint64_t(1) << (b - 1));
+            if (!DQ_INB(2 * u1 + 1, uint64_t(1) << n)) continue;
             Unit<R> A = ldu(rp + 2 * u0), B = ldu(rp + 2 * u1);
             const cx<R> t = A.b; A.b = B.a; B.a = t;
             stu(rp + 2 * u0, A);
@@ -225,6 +229,7 @@ k_expect(const cx<R> *__restrict__ st, int n, uint64_t f, int lf, TermPack tp, i
         R re, im;
         if (f) {
             b = insert0(b, lf);
+            if (!DQ_INB(b, uint64_t(1) << n) || !DQ_INB(b ^ f, uint64_t(1) << n)) continue;
             const cx<R> x = rp[b], y = rp[b ^ f];     // z = conj(psi_{b^f}) psi_b
             re = re_conj_mul(y, x);
             im = im_conj_mul(y, x);
@@ -293,6 +298,7 @@ k_lambda_term(const cx<R> *__restrict__ psi, cx<R> *__restrict__ lam, int n, Dev
     const int64_t row = i >> n;
     const uint64_t b = (uint64_t)i & ((uint64_t(1) << n) - 1);
     const uint64_t src = b ^ t.f;
+    if (!DQ_INB(src, uint64_t(1) << n)) return;
     float pr, pim;
     pauli_phase(src, t.s, t.nY, pr, pim);
     const R wt = (R)((w ? w[row * nobs + t.obs] : 1.0) * t.coeff);
@@ -324,6 +330,8 @@ k_adj(cx<R> *__restrict__ psi, cx<R> *__restrict__ lam, int n, UnitMap m, int ki
     int run = 0;
     for (int64_t j = i0 + threadIdx.x; j < i1; j += kThreads) {
         const uint64_t un = unit_of(m, (uint64_t)j);
+        if (!DQ_INB(2 * un + 1, uint64_t(1) << n) || (m.pbit && !DQ_INB(2 * (un | m.pbit) + 1, uint64_t(1) << n)))
+            continue;
         Unit<R> PA = ldu(pp + 2 * un), LA = ldu(lp + 2 * un);
         if (m.pbit) {
             const uint64_t un1 = un | m.pbit;

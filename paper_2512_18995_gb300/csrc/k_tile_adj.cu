@@ -284,7 +284,8 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
 #pragma unroll
                 for (int i = 0; i < kObsJ; ++i) {
                     const int l = tid + i * (int)blockDim.x;
-                    const cx<R> y = bufP[(uint32_t)l ^ o.floc];
+                    const uint32_t src = (uint32_t)l ^ o.floc;
+                    const cx<R> y = DQ_INB(src, 1u << a.g.k) ? bufP[src] : mk<R>(R(0), R(0));
                     e += y.x * x[i].x + y.y * x[i].y;
                     lv[i].x += wc * y.x;
                     lv[i].y += wc * y.y;
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
                 for (int i = 0; i < kObsJ; ++i) {
                     const int l = tid + i * (int)blockDim.x;
                     const uint32_t src = (uint32_t)l ^ o.floc;
-                    const cx<R> y = bufP[src];
+                    const cx<R> y = DQ_INB(src, 1u << a.g.k) ? bufP[src] : mk<R>(R(0), R(0));
                     const int k4 = (o.nY + 2 * ((__popc((uint32_t)l & o.sloc) & 1) ^ bpar)) & 3;
                     const R re = re_conj_mul(y, x[i]), im = im_conj_mul(y, x[i]);
                     e += (k4 == 0) ? re : (k4 == 1 ? -im : (k4 == 2 ? -re : im));
@@ -343,9 +344,9 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
 }
 
 template <typename R, int M>
-__global__ void __launch_bounds__(adj_max_threads<R, M>()) k_tile_adj(const __grid_constant__ CUtensorMap mp,
+__global__ void __launch_bounds__(adj_max_threads<R, M>(), adj_min_blocks<R, M>()) k_tile_adj(const __grid_constant__ CUtensorMap mp,
                                                                        const __grid_constant__ CUtensorMap ml,
-                                                                       AdjArgs a) {
+                                                                       const __grid_constant__ AdjArgs a) {
     tile_adj_body<R, M, InterpRev>(mp, ml, a);
 }
 
@@ -525,6 +526,16 @@ cudaError_t tile_adjoint(TileCache &tc, std::unordered_map<uint64_t, TileTune> &
         a.errflag = tc.errflag;
         a.any_row = 0;
         for (int j = ps.op0; j < ps.op0 + ps.nops; ++j) a.any_row |= sc->rops[j].rowstep != 0;
+        a.psi = psi;
+        a.lam = lam;
+        // results leave the registers as 32 consecutive amplitudes per warp
+        // store: the lane bits must be the lowest amplitude bits
+        if ((int)ps.T.size() != k || k > 16) return cudaErrorInvalidValue;
+        a.tbit[0] = a.tbit[1] = 0;
+        for (int i = 0; i < k; ++i) {
+            if (i < kLaneBits && ps.T[i] != i) return cudaErrorInvalidValue;
+            a.tbit[i >> 3] |= (uint64_t)ps.T[i] << (8 * (i & 7));
+        }
         const size_t smem = 2 * (sizeof(cx<R>) << k) + 64 + (size_t)ps.nops * sizeof(EOp) +
                             (size_t)ps.nrseg * sizeof(ESeg) + (size_t)ps.nops * sizeof(Mat2<R>) +
                             (size_t)ps.nslot * sizeof(double) + (size_t)nw * ps.nslot * sizeof(R) + 64;

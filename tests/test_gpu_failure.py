@@ -155,3 +155,76 @@ def test_norm_drift_of_fp32_evolution():
             assert drift <= tol, (dt, drift)
     finally:
         ctx.close()
+
+
+BOUNDS_CHILD = r"""
+import os, sys
+import numpy as np, torch
+sys.path.insert(0, os.getcwd())
+from paper_2512_18995_gb300 import build as b
+b.build(debug=True)
+import paper_2512_18995_gb300 as dq
+from paper_2512_18995_gb300 import _lib
+import oracle, workloads as W
+assert _lib.LIB_PATH.endswith("libdq_debug.so"), _lib.LIB_PATH
+ctx = dq.Context(0)
+ctx.selftest_bounds()
+try:
+    ctx.check()
+    raise SystemExit("the failing check was not reported")
+except dq.DQError as e:
+    assert e.status == 4 and "bounds check" in str(e) and "k_norm.cu" in str(e), str(e)
+ctx.check()   # cleared
+rng = np.random.default_rng(7)
+def run(path, n, gates, npar, nfeat, batch, dtype, obs, tol):
+    ctx.set_path(path)
+    params = rng.uniform(-3, 3, npar)
+    data = rng.uniform(-3, 3, (batch, nfeat)) if nfeat else None
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=nfeat)
+    e, gp, gd, _ = ctx.forward_grad(circ, torch.tensor(params, device="cuda"), dq.Observables(obs), batch, dtype,
+                                    data=None if data is None else torch.tensor(data, device="cuda"))
+    ctx.check()   # no index outside its buffer
+    e_ref, gp_ref, gd_ref = oracle.adjoint(n, gates, obs, params, data, batch=batch)
+    scale = sum(abs(t[0]) for o in obs for t in o)
+    err = max(np.max(np.abs(e.cpu().numpy() - e_ref)), np.max(np.abs(gp.cpu().numpy() - gp_ref)) / batch)
+    assert err <= tol * scale, (path, n, err)
+# per-gate path, complex128: swaps, controlled rotations, a parity-diagonal gate, X/Y terms
+n = 9
+g = W.encode_layer(n) + W.hea_layers(n, 2, first_param=0) + [W.Gate("swap", (1, 7)), W.Gate("crx", (0, 5), angle=0.4),
+                                                           W.Gate("rzz", (2, 6), param=4 * n)]
+obs = [W.obs_tfim_open(n, 0.5), [W.pauli_term(0.3, {0: "X", 4: "Y"})]]
+run(dq.PATH_PLAIN, n, g, 4 * n + 1, n, 3, torch.complex128, obs, 1e-10)
+# whole-row kernel (fused, 10 qubits, complex64)
+n = 10
+g = W.encode_layer(n) + W.hea_layers(n, 2) + [W.Gate("rzz", (1, 8), angle=0.3)]
+run(dq.PATH_FUSED, n, g, 4 * n, n, 5, torch.complex64, [W.obs_tfim_open(n, 0.5)], 1e-4)
+# tile passes: forward, observable and reverse passes (16 qubits, complex64)
+n = 16
+g = W.qft_gates(n) + W.hea_layers(n, 2)
+run(dq.PATH_FUSED, n, g, 4 * n, 0, 1, torch.complex64, [W.obs_tfim_open(n, 0.5)], 1e-4)
+ctx.close()
+print("bounds ok")
+"""
+
+
+def test_bounds_checking_build():
+    """The bounds-checking build (libdq_debug.so, DQ_DEBUG_BOUNDS): a check
+    that fails on purpose (no memory touched) is reported by the next
+    check() with its source site, then the per-gate, whole-row and tile
+    paths run with every checked index inside its buffer and match the
+    oracle.  The normal build refuses the self-test."""
+    import os
+    import subprocess
+    import sys
+    ctx = dq.Context(0)
+    try:
+        with pytest.raises(dq.DQError) as ei:
+            ctx.selftest_bounds()
+        assert ei.value.status == 2
+    finally:
+        ctx.close()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, DQ_DEBUG_BOUNDS="1")
+    r = subprocess.run([sys.executable, "-c", BOUNDS_CHILD], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=900)
+    assert r.returncode == 0 and "bounds ok" in r.stdout, r.stdout[-3000:] + r.stderr[-3000:]
