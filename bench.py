@@ -395,7 +395,7 @@ def our_arm(args, rank, world, dist):
     if kname == "k_sweep":
         kbytes = sum(touched_bytes(n, g) for g in wl.gates if g.kind != "swap") / launches_step
     achieved = kbytes / (avg_ms / 1e3) / 1e9
-    traffic = recorded_traffic(kname)
+    traffic = recorded_traffic(kname, ctx.plan_tuned(circ) if kname == "k_tile_fwd_jit" else None)
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic.get("bytes"), "peak_kind": peak_kind,
                 "frac_of_nominal_8TBps": achieved / NOMINAL_HBM_GBS,
@@ -498,27 +498,47 @@ def kernel_bytes(n, gates, passes, amp=8):
     return out
 
 
-def source_fingerprint(files):
+def source_fingerprint(files, extra=b""):
     import hashlib
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_2512_18995_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
+    h.update(extra)
     return h.hexdigest()[:16]
 
 
 # DRAM traffic per launch recorded from one ncu capture of the kernel (the
 # profile summary states the figure and the fingerprint of the sources the
 # capture was built from); reported only while those sources are unchanged.
+# The specialised passes are fingerprinted by what they are compiled from:
+# the generated source of the headline schedule and the device headers it
+# includes.
+JIT_FWD_HEADERS = ["dq_tile_fwd.cuh", "dq_engine.cuh", "dq_tma.cuh", "dq_common.cuh", "dq_devterm.h"]
 TRAFFIC_RECORDS = {
     "k_tile_multi": ("k_tile_multi_c2_hea20.md", ["k_tile.cu", "dq_engine.cuh", "dq_tma.cuh", "dq_common.cuh"]),
     "k_tile_fwd": ("k_tile_fwd_c2_hea20.md", ["k_tile.cu", "dq_engine.cuh", "dq_tma.cuh", "dq_common.cuh"]),
-    "k_tile_fwd_jit": ("k_tile_fwd_jit_c2_hea20.md", ["jit.cu", "dq_tile_fwd.cuh", "dq_engine.cuh", "dq_tma.cuh",
-                                                      "dq_common.cuh"]),
+    "k_tile_fwd_jit": ("k_tile_fwd_jit_c2_hea20.md", JIT_FWD_HEADERS),
 }
 
 
-def recorded_traffic(kname):
+def headline_jit_source(shape=None):
+    """The generated source of the headline circuit's specialised forward
+    passes for tile shape (k, low, M) (default: the shape its tuner picks on
+    a GB300, 12 / 5 / 4)."""
+    import paper_2512_18995_gb300 as dq
+    from paper_2512_18995_gb300 import _lib
+    wl = W.config_c2()
+    k, low, M = shape if shape and shape[0] else (12, 5, 4)
+    return _lib.jit_source(dq.Circuit(wl.n, wl.gates, nparams=wl.nparams), k, low, M).encode()
+
+
+def traffic_fingerprint(kname, shape=None):
+    rec = TRAFFIC_RECORDS[kname]
+    return source_fingerprint(rec[1], headline_jit_source(shape) if kname == "k_tile_fwd_jit" else b"")
+
+
+def recorded_traffic(kname, shape=None):
     rec = TRAFFIC_RECORDS.get(kname)
     if not rec:
         return {}
@@ -529,7 +549,7 @@ def recorded_traffic(kname):
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+sources:\s*([0-9a-f]{16})", open(path).read())
     if not m:
         return {}
-    if m.group(2) != source_fingerprint(rec[1]):
+    if m.group(2) != traffic_fingerprint(kname, shape):
         return {"source": f"profiles/{rec[0]} (stale: kernel sources changed since the capture)"}
     return {"bytes": float(m.group(1)), "source": f"profiles/{rec[0]}"}
 
@@ -1112,10 +1132,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="issue kernels one by one (no CUDA-graph replay)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--traffic-fingerprint", action="store_true",
+                    help="print the source fingerprint of each kernel with a recorded DRAM traffic figure")
     ap.add_argument("--profile-case", choices=["c2", "tile", "wsv", "sweep", "c5", "dense", "sample", "hessian"],
                     default=None,
                     help="run one kernel family's workload for profiling and exit")
     args = ap.parse_args()
+    if args.traffic_fingerprint:
+        for kname in TRAFFIC_RECORDS:
+            print(kname, traffic_fingerprint(kname))
+        return
     if args.profile_case:
         profile_case(args)
         return

@@ -18,12 +18,12 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdq.so")
-# The bounds-checking build (DQ_DEBUG_BOUNDS): every translation unit shares
-# one device-side record of failed checks, so it is compiled as relocatable
-# device code and device-linked.
+# The bounds-checking build (DQ_DEBUG_BOUNDS): the same compilation with the
+# index checks compiled in (each translation unit keeps its own record of
+# failed checks, read by the library).
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libdq_debug.so")
-DEBUG_FLAGS = ["-DDQ_DEBUG_BOUNDS", "-rdc=true"]
+DEBUG_FLAGS = ["-DDQ_DEBUG_BOUNDS"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -108,7 +108,7 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = lib + f".tmp{os.getpid()}"
-    cmd = [nvcc, ARCH, *(["-rdc=true"] if debug else []), "-shared", "-cudart", "shared", "-o", tmp, *objs]
+    cmd = [nvcc, ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

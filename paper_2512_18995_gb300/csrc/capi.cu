@@ -29,8 +29,22 @@
 using namespace dq;
 
 #ifdef DQ_BOUNDS_BUILD
+namespace {
+// every translation unit's bounds record (see DQ_INB): reader and clearer
+struct BoundsTU {
+    bool (*read)(unsigned long long *);
+    void (*clear)();
+};
+std::vector<BoundsTU> &bounds_units() {
+    static std::vector<BoundsTU> units;
+    return units;
+}
+}  // namespace
+
 namespace dq {
-__device__ unsigned long long g_dq_bounds[4];   // see DQ_INB
+void dq_bounds_register(bool (*read)(unsigned long long *), void (*clear)()) {
+    bounds_units().push_back({read, clear});
+}
 }  // namespace dq
 
 namespace {
@@ -1494,14 +1508,18 @@ dq_status dq_ctx_check(dq_ctx *ctx, void *stream) {
     DQ_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
 #ifdef DQ_BOUNDS_BUILD
     {
-        unsigned long long rec[4] = {0, 0, 0, 0};
-        DQ_CUDA(cudaMemcpyFromSymbol(rec, g_dq_bounds, sizeof(rec)), "read bounds record");
-        if (rec[0]) {
-            const unsigned long long zero[4] = {0, 0, 0, 0};
-            cudaMemcpyToSymbol(g_dq_bounds, zero, sizeof(zero));
+        unsigned long long first[4] = {0, 0, 0, 0}, total = 0;
+        for (const BoundsTU &u : bounds_units()) {
+            unsigned long long rec[4] = {0, 0, 0, 0};
+            if (!u.read(rec)) return fail(ctx, DQ_ERR_CUDA, "cannot read a bounds record");
+            if (rec[0] && !total) std::memcpy(first, rec, sizeof(rec));
+            total += rec[0];
+        }
+        if (total) {
+            for (const BoundsTU &u : bounds_units()) u.clear();
             return fail(ctx, DQ_ERR_CUDA, "bounds check: %llu index(es) outside their buffer, first %llu >= %llu at %s:%u",
-                        rec[0], rec[1], rec[2], bounds_site_file((unsigned)(rec[3] >> 32)),
-                        (unsigned)(rec[3] & 0xffffffffu));
+                        total, first[1], first[2], bounds_site_file((unsigned)(first[3] >> 32)),
+                        (unsigned)(first[3] & 0xffffffffu));
         }
     }
 #endif

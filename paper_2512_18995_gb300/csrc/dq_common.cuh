@@ -217,11 +217,29 @@ enum DevErr : int { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1, DEVERR_BOUNDS = 2 };
 // Bounds-checking build (DQ_DEBUG_BOUNDS, libdq_debug.so): DQ_INB(i, lim)
 // is false when index i is not below lim; the access it guards is skipped
 // and the failure is counted in g_dq_bounds (count, first index, its limit,
-// source site), which dq_ctx_check reports.  In the normal build it is the
-// constant true and guards nothing.
+// source site), which dq_ctx_check reports.  Every translation unit has its
+// own record and registers a reader for it with the library (no relocatable
+// device code: the build differs from the normal one only by the checks).
+// DQ_SMEM_ALIGNED(p) checks, in that build, that dynamic shared memory has
+// the 128-byte alignment the TMA copies need before any copy is issued.  In
+// the normal build both are the constant true and guard nothing.
 #if defined(DQ_DEBUG_BOUNDS) && !defined(__CUDACC_RTC__)
 #define DQ_BOUNDS_BUILD 1
-extern __device__ unsigned long long g_dq_bounds[4];
+void dq_bounds_register(bool (*read)(unsigned long long *rec), void (*clear)());   // capi.cu
+namespace {
+__device__ unsigned long long g_dq_bounds[4];
+bool dq_bounds_read_tu(unsigned long long *rec) {
+    return cudaMemcpyFromSymbol(rec, g_dq_bounds, sizeof(unsigned long long) * 4) == cudaSuccess;
+}
+void dq_bounds_clear_tu() {
+    const unsigned long long zero[4] = {0, 0, 0, 0};
+    cudaMemcpyToSymbol(g_dq_bounds, zero, sizeof(zero));
+}
+struct DqBoundsRegistration {
+    DqBoundsRegistration() { dq_bounds_register(&dq_bounds_read_tu, &dq_bounds_clear_tu); }
+};
+const DqBoundsRegistration dq_bounds_registration;
+}  // namespace
 constexpr unsigned dq_site_hash(const char *f, unsigned h = 2166136261u) {
     return *f ? dq_site_hash(f + 1, (h ^ (unsigned char)*f) * 16777619u) : h;
 }
@@ -239,11 +257,12 @@ __device__ __forceinline__ bool dq_in_bounds(uint64_t i, uint64_t lim, unsigned 
 #else
 #define DQ_SITE_FILE __FILE__
 #endif
-#define DQ_INB(i, lim)                                                                                      \
-    ::dq::dq_in_bounds((uint64_t)(i), (uint64_t)(lim),                                                     \
-                       ((unsigned long long)::dq::dq_site_hash(DQ_SITE_FILE) << 32) | (unsigned long long)__LINE__)
+#define DQ_SITE ((unsigned long long)::dq::dq_site_hash(DQ_SITE_FILE) << 32 | (unsigned long long)__LINE__)
+#define DQ_INB(i, lim) ::dq::dq_in_bounds((uint64_t)(i), (uint64_t)(lim), DQ_SITE)
+#define DQ_SMEM_ALIGNED(p) ::dq::dq_in_bounds((uint64_t)(__cvta_generic_to_shared(p) & 127u), 1, DQ_SITE)
 #else
 #define DQ_INB(i, lim) true
+#define DQ_SMEM_ALIGNED(p) true
 #endif
 
 // The context's 256-byte flag block: the error flag at byte 0, the limit of

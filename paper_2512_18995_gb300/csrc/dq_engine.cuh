@@ -450,28 +450,31 @@ __device__ __forceinline__ uint32_t reg_off(const Layout &L, int e) {
     return o;
 }
 
+// Every index of a layout is tb with a subset of the register offsets set,
+// so none exceeds tb | (all offsets): the bounds-checking build checks that
+// one index per load or store.
+template <int M>
+__device__ __forceinline__ bool eng_layout_in_bounds(const Layout &L) {
+#ifdef DQ_BOUNDS_BUILD
+    return DQ_INB(L.tb | reg_off<M>(L, (1 << M) - 1), L.lim);
+#else
+    (void)L;
+    return true;
+#endif
+}
+
 template <typename R, int M>
 __device__ __forceinline__ void eng_load(cx<R> (&a)[1 << M], const cx<R> *buf, const Layout &L) {
+    if (!eng_layout_in_bounds<M>(L)) return;
 #pragma unroll
-    for (int e = 0; e < (1 << M); ++e) {
-        const uint32_t i = L.tb | reg_off<M>(L, e);
-#ifdef DQ_BOUNDS_BUILD
-        if (!DQ_INB(i, L.lim)) continue;
-#endif
-        a[e] = buf[i];
-    }
+    for (int e = 0; e < (1 << M); ++e) a[e] = buf[L.tb | reg_off<M>(L, e)];
 }
 
 template <typename R, int M>
 __device__ __forceinline__ void eng_store(const cx<R> (&a)[1 << M], cx<R> *buf, const Layout &L) {
+    if (!eng_layout_in_bounds<M>(L)) return;
 #pragma unroll
-    for (int e = 0; e < (1 << M); ++e) {
-        const uint32_t i = L.tb | reg_off<M>(L, e);
-#ifdef DQ_BOUNDS_BUILD
-        if (!DQ_INB(i, L.lim)) continue;
-#endif
-        buf[i] = a[e];
-    }
+    for (int e = 0; e < (1 << M); ++e) buf[L.tb | reg_off<M>(L, e)] = a[e];
 }
 
 template <typename T> __device__ __forceinline__ T shfl_xor_cx(T v, int m);

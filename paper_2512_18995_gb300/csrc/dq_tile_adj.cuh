@@ -90,13 +90,19 @@ struct AdjIo {
         uint64_t so[M];   // register bit i: one tile bit (L.off[i]) at its amplitude bit
 #pragma unroll
         for (int i = 0; i < M; ++i) so[i] = uint64_t(1) << tbit(__ffs((int)L.off[i]) - 1);
+#ifdef DQ_BOUNDS_BUILD
+        {   // the largest index has every register bit set
+            uint64_t top = t0;
+            for (int i = 0; i < M; ++i) top |= so[i];
+            if (!DQ_INB(top, (uint64_t)a->batch << a->g.n)) return;
+        }
+#endif
 #pragma unroll
         for (int e = 0; e < (1 << M); ++e) {
             uint64_t o = 0;
 #pragma unroll
             for (int i = 0; i < M; ++i)
                 if ((e >> i) & 1) o |= so[i];
-            if (!DQ_INB(t0 | o, (uint64_t)a->batch << a->g.n)) continue;
             gp[o] = ps[e];
             gp[o + dl] = ls[e];
         }
@@ -167,6 +173,7 @@ struct InterpRev {
 template <typename R, int M, typename Runner>
 __device__ __forceinline__ void tile_adj_body(const CUtensorMap &mp, const CUtensorMap &ml, const AdjArgs &a) {
     extern __shared__ __align__(128) unsigned char smem[];
+    if (!DQ_SMEM_ALIGNED(smem)) return;   // bounds-checking build: no copy into a misaligned buffer
     const unsigned long long wlim = wait_limit_ns(a.errflag);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const size_t tbytes = sizeof(cx<R>) << a.g.k;

@@ -140,6 +140,7 @@ struct InterpOps {
 template <typename R, int M, bool PD, typename Ops>
 __device__ __forceinline__ void tile_fwd_body(const CUtensorMap &tmap, const TileKArgs &a) {
     extern __shared__ __align__(128) unsigned char smem[];
+    if (!DQ_SMEM_ALIGNED(smem)) return;   // bounds-checking build: no copy into a misaligned buffer
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t tbytes = sizeof(cx<R>) << a.g.k;
     const unsigned long long wlim = wait_limit_ns(a.errflag);

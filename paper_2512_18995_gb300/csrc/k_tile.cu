@@ -423,6 +423,7 @@ __global__ void __launch_bounds__(tile_max_threads<R, M>(), tile_min_blocks<R, M
 k_tile_multi(const __grid_constant__ MultiArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_stop;
+    if (!DQ_SMEM_ALIGNED(smem)) return;   // bounds-checking build (every CTA alike): no misaligned copy
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long wlim = wait_limit_ns(a.errflag);
     const int k = a.pass[0].g.k;
@@ -569,7 +570,19 @@ uint64_t sched_key(const Plan &p, int k, int low, int amp, int M, bool adjoint =
 }
 
 template <typename R>
-void default_tile(int n, int &k, int &low, int &M) {
+void default_tile(int n, int &k, int &low, int &M, bool jit) {
+    if (n >= 25 && sizeof(R) == 4 && jit) {
+        // large complex64 states, passes compiled per circuit: 12-qubit tiles
+        // of 256 threads, four register bits, lane bits resident (fewer
+        // passes now that the ops cost no dispatch) -- measured on the
+        // 30-qubit QFT + ansatz circuit, forward passes: 45 in 190 ms against
+        // 66 in 245 ms for the one-warp 10-qubit tiles below (11 / 5 / 4: 54
+        // in 211 ms; 13 / 5 / 4: 39 in 215 ms)
+        k = 12;
+        M = 4;
+        low = kTileLaneBits;
+        return;
+    }
     if (n >= 25 && sizeof(R) == 4) {
         // large complex64 states: one-warp CTAs of 32 amplitudes per thread
         // (no inter-warp barriers at layout changes) on 10-qubit tiles with
@@ -667,6 +680,9 @@ const void *multi_kernel(int M, bool pd) {
 // The persistent multi-pass kernel serves states that stay in L2 between
 // passes, with at least two passes to merge.
 bool multi_applies(const TileCache &tc, const TileSchedule &sc, int n, int64_t batch, int amp) {
+#ifdef DQ_BOUNDS_BUILD
+    return false;   // the bounds-checking build runs one launch per pass
+#endif
     return tc.multi_on && tc.gridbar && sc.passes.size() >= 2 && ((batch << n) * (int64_t)amp) <= kMultiMaxStateBytes;
 }
 
@@ -930,7 +946,8 @@ cudaError_t tile_apply(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tu
     (void)tws;
     if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
     int k, low, M;
-    default_tile<R>(p.n, k, low, M);
+    // untuned plans take specialised passes only when DQ_OPT_JIT is 1
+    default_tile<R>(p.n, k, low, M, tc.jit_mode == 1 && jit_available());
     auto it = tuned.find(p.key ^ (sizeof(R) == 8 ? 1ull : 0ull));
     if (it != tuned.end() && it->second.k) {
         k = it->second.k;
@@ -953,7 +970,8 @@ cudaError_t tile_apply_expect(TileCache &tc, std::unordered_map<uint64_t, TileTu
         if (t.f != 0 || t.nY != 0) return cudaErrorNotSupported;   // diagonal terms only
     if (bits.empty() || bits.size() > 64) return cudaErrorNotSupported;
     int k, low, M;
-    default_tile<R>(p.n, k, low, M);
+    // untuned plans take specialised passes only when DQ_OPT_JIT is 1
+    default_tile<R>(p.n, k, low, M, tc.jit_mode == 1 && jit_available());
     auto it = tuned.find(p.key ^ (sizeof(R) == 8 ? 1ull : 0ull));
     if (it != tuned.end() && it->second.k) {
         k = it->second.k;

@@ -188,6 +188,8 @@ struct ObsArgs {
     double *part;     // [term][row][cta] or null
     int batch;
     int *errflag;
+    void *lam;        // lambda in global memory (results are stored from registers)
+    uint64_t tbit[2]; // amplitude bit of each tile bit, one byte each (as AdjArgs::tbit)
 };
 
 // Amplitudes each thread owns in an observable pass (threads = 2^k / kObsJ).
@@ -196,33 +198,68 @@ constexpr int kObsJ = 8;
 template <typename R>
 constexpr int obs_max_threads() { return sizeof(R) == 4 ? 1024 : 512; }
 
+// Every tile: psi (and, after the first pass, lambda) arrive by TMA; each
+// thread reads its amplitudes and their partners from shared memory; once
+// every read is done the next tile's copies are issued into the same
+// buffers (overlapping the partial sums and the stores), and lambda leaves
+// the registers by coalesced stores (consecutive threads hold consecutive
+// amplitudes, and the low tile bits are the low amplitude bits).
 template <typename R>
 __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_constant__ CUtensorMap mp,
-                                                   const __grid_constant__ CUtensorMap ml, ObsArgs a) {
+                                                   const __grid_constant__ CUtensorMap ml,
+                                                   const __grid_constant__ ObsArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
+    if (!DQ_SMEM_ALIGNED(smem)) return;   // bounds-checking build: no copy into a misaligned buffer
     const unsigned long long wlim = wait_limit_ns(a.errflag);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int64_t dim = int64_t(1) << a.g.k;
     const size_t tbytes = sizeof(cx<R>) * (size_t)dim;
+    const uint32_t load_bytes = (uint32_t)(a.lam_mode == 2 ? 2 * tbytes : tbytes);
     cx<R> *bufP = reinterpret_cast<cx<R> *>(smem);
     cx<R> *bufL = reinterpret_cast<cx<R> *>(smem + tbytes);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * tbytes);
+    AdjTileSlot *slot = reinterpret_cast<AdjTileSlot *>(smem + 2 * tbytes);
+    uint64_t *bar = &slot->bar;
     OTerm *st = reinterpret_cast<OTerm *>(smem + 2 * tbytes + 64);
     double *acc = reinterpret_cast<double *>(st + a.nt);            // [nt]
     R *accw = reinterpret_cast<R *>(acc + a.nt);                     // [nw][nt]
+    const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t1 = min(a.g.ntiles, t0 + per);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_async_smem();
+        if (t0 < t1) {
+            int c[5];
+            uint64_t base;
+            int64_t row;
+            geom_coords(a.g, t0, c, base, row);
+            mbar_expect_tx(bar, load_bytes);
+            tma_load5(bufP, &mp, c, bar);
+            if (a.lam_mode == 2) tma_load5(bufL, &ml, c, bar);
+        }
+    }
     for (int i = tid; i < a.nt; i += blockDim.x) {
         st[i] = a.terms[i];
         acc[i] = 0.0;
     }
     for (int i = tid; i < nw * a.nt; i += blockDim.x) accw[i] = R(0);
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        fence_async_smem();
-    }
     __syncthreads();
-    const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * per;
-    const int64_t t1 = min(a.g.ntiles, t0 + per);
+    // scattered offset of this thread's amplitudes l_i = tid + i * blockDim:
+    // the bits of tid and those of i * blockDim are disjoint
+    auto scatter = [&](uint32_t l) {
+        uint64_t r = l & ((1u << kLaneBits) - 1);
+        for (int i = kLaneBits; i < a.g.k; ++i)
+            if ((l >> i) & 1) r |= uint64_t(1) << ((a.tbit[i >> 3] >> (8 * (i & 7))) & 63);
+        return r;
+    };
+    const uint64_t s_tid = scatter((uint32_t)tid);
+    // l_i = tid + i * blockDim: i sits on the top three tile bits (blockDim = 2^k / 8)
+    uint64_t s_hi[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const int i = a.g.k - 3 + b;
+        s_hi[b] = uint64_t(1) << ((a.tbit[i >> 3] >> (8 * (i & 7))) & 63);
+    }
     uint32_t phase = 0;
     int64_t cur_row = -1;
     bool failed = false;
@@ -242,12 +279,8 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
             if (cur_row >= 0) flush(cur_row);
             cur_row = row;
         }
-        if (tid == 0) {
-            mbar_expect_tx(&bar[0], (uint32_t)(a.lam_mode == 2 ? 2 * tbytes : tbytes));
-            tma_load5(bufP, &mp, c, &bar[0]);
-            if (a.lam_mode == 2) tma_load5(bufL, &ml, c, &bar[0]);
-        }
-        const bool ok = mbar_wait_bounded(&bar[0], phase, wlim);
+        // this tile's copies were issued by the prologue or by the previous tile
+        const bool ok = mbar_wait_bounded(bar, phase, wlim);
         phase ^= 1;
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -310,7 +343,17 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
             e = warp_sum_t(e);
             if (lane == 0) accw[warp * a.nt + j] += e;
         }
-        __syncthreads();   // every partner read of this tile is done
+        fence_async_smem();
+        __syncthreads();   // every read of this tile's buffers is done; every warp's partials are in accw
+        if (tid == 0 && t + 1 < t1) {
+            int cn[5];
+            uint64_t bn;
+            int64_t rn;
+            geom_coords(a.g, t + 1, cn, bn, rn);
+            mbar_expect_tx(bar, load_bytes);
+            tma_load5(bufP, &mp, cn, bar);
+            if (a.lam_mode == 2) tma_load5(bufL, &ml, cn, bar);
+        }
         for (int j = tid; j < a.nt; j += blockDim.x) {
             double sum = 0.0;
             for (int ww = 0; ww < nw; ++ww) {
@@ -320,17 +363,17 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
             acc[j] += sum;
         }
         if (a.lam_mode) {
+            const uint64_t t0 = ((uint64_t)row << a.g.n) | base | s_tid;
+            cx<R> *gl = reinterpret_cast<cx<R> *>(a.lam) + t0;
+            // the largest index has the three high bits set
+            if (DQ_INB(t0 | s_hi[0] | s_hi[1] | s_hi[2], (uint64_t)a.batch << a.g.n)) {
 #pragma unroll
-            for (int i = 0; i < kObsJ; ++i) bufL[tid + i * (int)blockDim.x] = lv[i];
-            fence_async_smem();
-            __syncthreads();
-            if (tid == 0) {
-                tma_store5(&ml, c, bufL);
-                bulk_commit();
-                bulk_wait_read0();
+                for (int i = 0; i < kObsJ; ++i) {
+                    const uint64_t o = ((i & 1) ? s_hi[0] : 0) | ((i & 2) ? s_hi[1] : 0) | ((i & 4) ? s_hi[2] : 0);
+                    gl[o] = lv[i];
+                }
             }
         }
-        __syncthreads();
     }
     if (!failed && cur_row >= 0) {
         __syncthreads();
@@ -338,9 +381,8 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
     }
     if (failed && tid == 0) {
         atomicCAS(a.errflag, 0, DEVERR_TIMEOUT);
-        mbar_wait_bounded(&bar[0], phase, wlim);
+        mbar_wait_bounded(bar, phase, wlim);
     }
-    if (tid == 0) bulk_wait0();
 }
 
 template <typename R, int M>
@@ -440,6 +482,15 @@ cudaError_t tile_observe(TileCache &tc, int n, const std::vector<DevTerm> &bits,
         a.part = out ? part : nullptr;
         a.batch = batch;
         a.errflag = tc.errflag;
+        a.lam = lam;
+        // lambda leaves the registers as 32 consecutive amplitudes per warp
+        // store: the lane bits must be the lowest amplitude bits
+        if ((int)ps.T.size() != k || k > 16) return cudaErrorInvalidValue;
+        a.tbit[0] = a.tbit[1] = 0;
+        for (int i = 0; i < k; ++i) {
+            if (i < kLaneBits && ps.T[i] != i) return cudaErrorInvalidValue;
+            a.tbit[i >> 3] |= (uint64_t)ps.T[i] << (8 * (i & 7));
+        }
         const size_t smem = 2 * (sizeof(cx<R>) << k) + 64 + ps.nt * sizeof(OTerm) + ps.nt * sizeof(double) +
                             (size_t)nw * ps.nt * sizeof(R) + 64;
         const void *ofn = (const void *)k_tile_obs<R>;
