@@ -114,7 +114,7 @@ constexpr int adj_max_threads() { return ((1 << M) * (int)sizeof(cx<R>) <= 64) ?
 // Two CTAs of 256 threads per SM for complex64 (the large-state shape: 12-qubit
 // tiles, four register bits): 128 registers a thread.
 template <typename R, int M>
-constexpr int adj_min_blocks() { return (sizeof(R) == 4 && adj_max_threads<R, M>() == 256) ? 2 : 1; }
+constexpr int adj_min_blocks() { return (sizeof(R) == 4 && M == 4) ? 2 : 1; }
 
 // The interpreter: every op dispatched from the staged reverse program.
 struct InterpRev {

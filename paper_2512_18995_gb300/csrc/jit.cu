@@ -433,7 +433,7 @@ std::string jit_source(const TileSchedule &sc, int amp, std::vector<std::string>
         for (int p = p0; p < p1; ++p) {
             const std::string name = "dq_jit_adj_" + std::to_string(p);
             names.push_back(name);
-            s << "extern \"C\" __global__ void __launch_bounds__(" << amax << ", " << (amp == 8 && amax == 256 ? 2 : 1)
+            s << "extern \"C\" __global__ void __launch_bounds__(" << amax << ", " << (amp == 8 && M == 4 ? 2 : 1)
               << ") " << name
               << "(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap ml,\n"
               << "    const __grid_constant__ dq::AdjArgs a) {\n"

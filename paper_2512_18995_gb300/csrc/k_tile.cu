@@ -1002,13 +1002,29 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
                           int64_t *launches) {
     (void)tws;
     if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
-    float best = 1e30f;
+    struct Cand {
+        float ms;
+        int k, low, M;
+    };
+    std::vector<Cand> cands;
     TileTune bt;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     Tracer *saved = g_tracer;
     g_tracer = nullptr;
+    // time three forwards after a warm-up one (j: specialised passes)
+    auto timed = [&](TileSchedule &sc, bool j, float &ms) {
+        cudaError_t err = run_forward<R>(tc, p, sc, coef, state, batch, nsm, s, launches, nullptr, nullptr, j);
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
+            err = run_forward<R>(tc, p, sc, coef, state, batch, nsm, s, launches, nullptr, nullptr, j);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) cudaGetLastError();
+        return err == cudaSuccess;
+    };
     for (int M = 2; M <= TileCfg<R>::Mmax; ++M)
     for (int k = kTileLaneBits + M; k <= std::min(p.n - 1, sizeof(R) == 4 ? 13 : 12); ++k) {
         const int maxt = ((1 << M) * (int)sizeof(cx<R>) >= 256) ? 256 : 512;
@@ -1016,48 +1032,40 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
         for (int low : {5, 7}) {
             if (low > k - 2) continue;
             TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), false);
-            if (!sc) continue;
-            cudaError_t err = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches);   // warm
-            if (err != cudaSuccess) {
-                cudaGetLastError();
-                continue;
-            }
-            cudaEventRecord(e0, s);
-            for (int rep = 0; rep < 3; ++rep) run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                bt.k = k;
-                bt.low = low;
-                bt.M = M;
-            }
+            if (sc && timed(*sc, false, ms)) cands.push_back({ms, k, low, M});
         }
     }
-    // the chosen shape's passes as run-time specialised kernels against the
-    // interpreter (DQ_OPT_JIT = 2 uses the faster)
-    if (bt.k && tc.jit_mode != 0 && jit_available()) {
-        TileSchedule *sc = get_schedule(tc, p, bt.k, bt.low, bt.M, (int)sizeof(cx<R>), false);
-        std::string err;
-        if (sc && (sc->jit || (!sc->jit_failed && jit_build(*sc, (int)sizeof(cx<R>), tc.device, &err)))) {
-            float ms[2] = {0.f, 0.f};
-            cudaError_t err2 = cudaSuccess;
-            for (int j = 0; j < 2 && err2 == cudaSuccess; ++j) {
-                err2 = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches, nullptr, nullptr, j == 1);
-                cudaEventRecord(e0, s);
-                for (int rep = 0; rep < 3 && err2 == cudaSuccess; ++rep)
-                    err2 = run_forward<R>(tc, p, *sc, coef, state, batch, nsm, s, launches, nullptr, nullptr, j == 1);
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&ms[j], e0, e1);
+    std::sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) { return a.ms < b.ms; });
+    float best = 1e30f;
+    if (!cands.empty()) {
+        best = cands[0].ms;
+        bt.k = cands[0].k;
+        bt.low = cands[0].low;
+        bt.M = cands[0].M;
+    }
+    // the three fastest shapes' passes as run-time specialised kernels: a
+    // pass without dispatch may favour another shape (DQ_OPT_JIT = 2 uses
+    // the fastest of all)
+    if (tc.jit_mode != 0 && jit_available()) {
+        for (size_t ci = 0; ci < cands.size() && ci < 3; ++ci) {
+            const Cand &cd = cands[ci];
+            TileSchedule *sc = get_schedule(tc, p, cd.k, cd.low, cd.M, (int)sizeof(cx<R>), false);
+            std::string err;
+            if (!sc || sc->jit_failed) continue;
+            if (!sc->jit && !jit_build(*sc, (int)sizeof(cx<R>), tc.device, &err)) {
+                sc->jit_failed = true;
+                tc.jit_err = err;
+                continue;
             }
-            if (err2 == cudaSuccess) bt.jit = ms[1] < ms[0] ? 1 : 0;
-            else cudaGetLastError();
-        } else if (sc && !err.empty()) {
-            sc->jit_failed = true;
-            tc.jit_err = err;
+            float ms = 0.f;
+            if (timed(*sc, true, ms) && ms < best) {
+                best = ms;
+                bt.k = cd.k;
+                bt.low = cd.low;
+                bt.M = cd.M;
+                bt.jit = 1;
+            }
         }
     }
     g_tracer = saved;
