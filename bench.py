@@ -395,7 +395,8 @@ def our_arm(args, rank, world, dist):
     if kname == "k_sweep":
         kbytes = sum(touched_bytes(n, g) for g in wl.gates if g.kind != "swap") / launches_step
     achieved = kbytes / (avg_ms / 1e3) / 1e9
-    traffic = recorded_traffic(kname, ctx.plan_tuned(circ) if kname == "k_tile_fwd_jit" else None)
+    tuned = ctx.plan_tuned(circ)
+    traffic = recorded_traffic(kname, tuned if kname == "k_tile_fwd_jit" else None)
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic.get("bytes"), "peak_kind": peak_kind,
                 "frac_of_nominal_8TBps": achieved / NOMINAL_HBM_GBS,
@@ -403,6 +404,7 @@ def our_arm(args, rank, world, dist):
                 "share_of_step": share, "passes_per_step": passes,
                 "timing": "untraced step time x the kernel's share of a traced repetition of the same steps",
                 "traffic_source": traffic.get("source"),
+                "tile_shape": {"k": tuned[0], "low": tuned[1], "M": tuned[2]},
                 "note": "20-qubit state (8 MiB) is L2-resident within a step"}
     kernels_step = {k: {"launches": c / args.steps, "share": t / traced_total} for k, (c, t) in trace.items()}
 
@@ -546,12 +548,14 @@ def recorded_traffic(kname, shape=None):
     if not os.path.exists(path):
         return {}
     import re
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+sources:\s*([0-9a-f]{16})", open(path).read())
-    if not m:
+    found = re.findall(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+sources:\s*([0-9a-f]{16})", open(path).read())
+    if not found:
         return {}
-    if m.group(2) != traffic_fingerprint(kname, shape):
-        return {"source": f"profiles/{rec[0]} (stale: kernel sources changed since the capture)"}
-    return {"bytes": float(m.group(1)), "source": f"profiles/{rec[0]}"}
+    fp = traffic_fingerprint(kname, shape)
+    for bytes_, fp_rec in found:   # one record per captured schedule
+        if fp_rec == fp:
+            return {"bytes": float(bytes_), "source": f"profiles/{rec[0]}"}
+    return {"source": f"profiles/{rec[0]} (stale: no capture of the kernels as built now)"}
 
 
 def hbm_sweep(ctx, device, hbm_peak, peak_kind, n=30, reps=3):
@@ -734,8 +738,12 @@ def trotter30(ctx, device, steps=5):
     H = dq.Observables([[W.pauli_term(-1.0, {i: "Z", (i + 1) % n: "Z"}) for i in range(n)]
                         + [W.pauli_term(-1.2, {i: "X"}) for i in range(n)]])
     out = {}
-    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+    # fused: tile passes compiled per circuit (DQ_OPT_JIT = 1; the compile is
+    # part of the untimed warm-up call); fused_interpreted: the interpreting kernels
+    for name, path, jit in (("fused", dq.PATH_FUSED, 1), ("fused_interpreted", dq.PATH_FUSED, 0),
+                            ("plain", dq.PATH_PLAIN, 0)):
         ctx.set_path(path)
+        ctx.set_option(dq.OPT_JIT, jit)
         try:
             ctx.forward_grad(circ, None, H, 1, torch.complex64, want_grad=False)
             torch.cuda.synchronize()
@@ -747,11 +755,13 @@ def trotter30(ctx, device, steps=5):
             torch.cuda.synchronize()
         except RuntimeError as exc:   # not enough device memory
             ctx.set_path(dq.PATH_AUTO)
+            ctx.set_option(dq.OPT_JIT, 2)
             return {"skipped": str(exc)[:120]}
         ms = a.elapsed_time(b)
         out[name] = {"ms_per_step": ms,
                      "gate_equiv_GBps": len(gates) * 2 * (8 << n) / (ms / 1e3) / 1e9}
     ctx.set_path(dq.PATH_AUTO)
+    ctx.set_option(dq.OPT_JIT, 2)
     ctx.release_workspace()
     torch.cuda.empty_cache()
     out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
@@ -805,6 +815,13 @@ def hessian_workload(n=22, layers=2):
                       [W.obs_sum_z(n)], True, False)
 
 
+def _arms():
+    import paper_2512_18995_gb300 as dq
+    # fused: passes compiled per circuit (DQ_OPT_JIT = 1, the compile falls in
+    # the untimed warm-up call); fused_interpreted: the interpreting kernels
+    return (("fused", dq.PATH_FUSED, 1), ("fused_interpreted", dq.PATH_FUSED, 0), ("plain", dq.PATH_PLAIN, 0))
+
+
 def hessian_hea(ctx, device):
     """Full 88 x 88 Hessian of <sum Z> for the 22-qubit, 2-layer ansatz: 176
     shifted points of the fused forward + adjoint as one batch, vs the same
@@ -816,8 +833,9 @@ def hessian_hea(ctx, device):
     obs = dq.Observables(wl.observables)
     params = torch.tensor(wl.params, device=device)
     out = {}
-    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+    for name, path, jit in _arms():
         ctx.set_path(path)
+        ctx.set_option(dq.OPT_JIT, jit)
         try:
             ctx.hessian(circ, params, obs, want_grad=False)
             torch.cuda.synchronize()
@@ -829,6 +847,7 @@ def hessian_hea(ctx, device):
             torch.cuda.synchronize()
         except RuntimeError as exc:
             ctx.set_path(dq.PATH_AUTO)
+            ctx.set_option(dq.OPT_JIT, 2)
             return {"skipped": str(exc)[:120]}
         ms = a.elapsed_time(b)
         out[name] = {"ms_per_hessian": ms, "entries_per_s": wl.nparams ** 2 / (ms / 1e3)}
@@ -838,6 +857,7 @@ def hessian_hea(ctx, device):
             out[name]["kernel_ms"] = {k: [v[0], round(v[1], 3)] for k, v in ctx.trace().items()}
             ctx.set_tracing(False)
     ctx.set_path(dq.PATH_AUTO)
+    ctx.set_option(dq.OPT_JIT, 2)
     ctx.release_workspace()
     torch.cuda.empty_cache()
     out["speedup"] = out["plain"]["ms_per_hessian"] / out["fused"]["ms_per_hessian"]
@@ -866,8 +886,9 @@ def density_noisy(ctx, device, n=13, layers=4):
     obs = dq.Observables([W.obs_sum_z(n)])
     params = torch.tensor(W.uniform_array(W._seed(13), 2 * n * layers, 0.0, 2 * np.pi), device=device)
     out = {}
-    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+    for name, path, jit in _arms():
         ctx.set_path(path)
+        ctx.set_option(dq.OPT_JIT, jit)
         try:
             ctx.density_forward(circ, params, obs, 1, torch.complex64)
             torch.cuda.synchronize()
@@ -879,6 +900,7 @@ def density_noisy(ctx, device, n=13, layers=4):
             torch.cuda.synchronize()
         except RuntimeError as exc:
             ctx.set_path(dq.PATH_AUTO)
+            ctx.set_option(dq.OPT_JIT, 2)
             return {"skipped": str(exc)[:120]}
         out[name] = {"ms_per_step": a.elapsed_time(b)}
     ctx.set_path(dq.PATH_AUTO)
@@ -893,8 +915,9 @@ def density_noisy(ctx, device, n=13, layers=4):
     og = dq.Observables([W.obs_sum_z(ng)])
     pg = torch.tensor(W.uniform_array(W._seed(10), 2 * ng * lg, 0.0, 2 * np.pi), device=device)
     grad = {}
-    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+    for name, path, jit in _arms():
         ctx.set_path(path)
+        ctx.set_option(dq.OPT_JIT, jit)
         ctx.density_grad(cg, pg, og, dtype=torch.complex64)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -905,6 +928,7 @@ def density_noisy(ctx, device, n=13, layers=4):
         torch.cuda.synchronize()
         grad[name] = {"ms_per_gradient": a.elapsed_time(b)}
     ctx.set_path(dq.PATH_AUTO)
+    ctx.set_option(dq.OPT_JIT, 2)
     grad["speedup"] = grad["plain"]["ms_per_gradient"] / grad["fused"]["ms_per_gradient"]
     grad["workload"] = f"density_grad_hea{ng}x{lg}_depolarizing_c64"
     out["grad"] = grad
@@ -923,8 +947,9 @@ def qcnn_batch(ctx, device, batch=4096, steps=5):
     params = torch.tensor(W.uniform_array(71, npar, 0.0, 2 * np.pi), device=device)
     data = torch.tensor(W.uniform_array(72, batch * nfeat, -np.pi, np.pi).reshape(batch, nfeat), device=device)
     out = {}
-    for name, path in (("fused", dq.PATH_FUSED), ("plain", dq.PATH_PLAIN)):
+    for name, path, jit in _arms():
         ctx.set_path(path)
+        ctx.set_option(dq.OPT_JIT, jit)
         for _ in range(2):
             ctx.forward_grad(circ, params, obs, batch, torch.complex64, data=data)
         torch.cuda.synchronize()
@@ -938,6 +963,7 @@ def qcnn_batch(ctx, device, batch=4096, steps=5):
         ms = a.elapsed_time(b) / steps
         out[name] = {"ms_per_step": ms, "grads_per_s": batch * (npar + nfeat) / (ms / 1e3)}
     ctx.set_path(dq.PATH_AUTO)
+    ctx.set_option(dq.OPT_JIT, 2)
     out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
     out["workload"] = "qcnn12x4096_c64"
     return out
@@ -1044,10 +1070,14 @@ def profile_case(args):
         st = torch.empty((1, 1 << wl.n), dtype=torch.complex64, device=dev)
         e = torch.empty((1, 1), dtype=torch.float64, device=dev)
         flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-        ctx.plan_autotune(circ, st)
-        # under a profiler the tuner's timings change its choice; take the
-        # specialised per-pass kernels the bench's own tuned run uses
-        ctx.set_option(dq.OPT_JIT, 1)
+        if args.tile:
+            # under a profiler the tuner's timings change its choice: pin the
+            # shape the bench's own tuned run reports (roofline.tile_shape),
+            # with specialised passes
+            k, low, M = (int(x) for x in args.tile.split(","))
+            ctx.plan_set_tile(circ, k, low, M, jit=True)
+        else:
+            ctx.plan_autotune(circ, st)
         for _ in range(args.warmup):
             ctx.forward_grad(circ, params, obs, 1, torch.complex64, want_grad=False, state_out=st, expect_out=e)
         torch.cuda.synchronize()
@@ -1132,6 +1162,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="issue kernels one by one (no CUDA-graph replay)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--tile", default="", help="profile case c2: pin the tile shape k,low,M (specialised passes)")
     ap.add_argument("--traffic-fingerprint", action="store_true",
                     help="print the source fingerprint of each kernel with a recorded DRAM traffic figure")
     ap.add_argument("--profile-case", choices=["c2", "tile", "wsv", "sweep", "c5", "dense", "sample", "hessian"],
@@ -1140,7 +1171,7 @@ def main():
     args = ap.parse_args()
     if args.traffic_fingerprint:
         for kname in TRAFFIC_RECORDS:
-            print(kname, traffic_fingerprint(kname))
+            print(kname, traffic_fingerprint(kname, tuple(int(x) for x in args.tile.split(",")) if args.tile else None))
         return
     if args.profile_case:
         profile_case(args)

@@ -577,6 +577,19 @@ DQ_API dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int ba
  * size-based default applies). */
 DQ_API dq_status dq_plan_tuned(dq_ctx *ctx, const dq_circuit *circuit, int dtype, int *k, int *low, int *M);
 
+/* Pin the fused forward configuration of this circuit structure and dtype
+ * without timing anything (a shape measured before, on this or another run):
+ * tile qubits k, always-resident low bits low, register bits per thread M
+ * (the ranges dq_tile_schedule takes; 2^(k - M) threads at most 512, 256
+ * for wide register sets), and jit 1 for run-time specialised passes under
+ * DQ_OPT_JIT = 2 (0: interpreted).  Later forward calls use it as they use a
+ * dq_plan_autotune result; the whole-row and dense-block choices of the plan
+ * are kept.  DQ_ERR_INVALID_ARG for values out of range; DQ_ERR_UNSUPPORTED
+ * when no tile schedule of that shape exists for the circuit.  Captured
+ * graphs of the context are dropped. */
+DQ_API dq_status dq_plan_set_tile(dq_ctx *ctx, const dq_circuit *circuit, int dtype, int k, int low, int M,
+                                  int jit);
+
 /* ---- host-side plan inspection (no context, no GPU) ----------------------
  * These calls run only the host code that the compute calls run before any
  * launch -- argument validation, lowering to kernel-level gates, the tile

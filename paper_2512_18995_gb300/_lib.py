@@ -70,7 +70,7 @@ class dq_lowered_op(ctypes.Structure):
 
 
 EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path", "dq_ctx_set_option",
-           "dq_state_norm", "dq_selftest_wait_expiry", "dq_selftest_bounds", "dq_batch_autotune", "dq_jit_source",
+           "dq_state_norm", "dq_selftest_wait_expiry", "dq_selftest_bounds", "dq_plan_set_tile", "dq_batch_autotune", "dq_jit_source",
            "dq_jit_compile_check",
            "dq_ctx_set_workspace",
            "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_graphs", "dq_ctx_set_tracing",
@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH):
                                ctypes.POINTER(ctypes.c_int), P], I),
         "dq_selftest_wait_expiry": ([P, P], I),
         "dq_selftest_bounds": ([P, P], I),
+        "dq_plan_set_tile": ([P, C, I, I, I, I, I], I),
         "dq_ctx_set_workspace": ([P, P, ctypes.c_size_t], I),
         "dq_workspace_bytes": ([P, C, O, I, I, ctypes.POINTER(ctypes.c_size_t)], I),
         "dq_batch_workspace_bytes": ([P, I, C, I, ctypes.POINTER(ctypes.c_size_t)], I),
@@ -778,6 +779,13 @@ class Context:
         self._check(self.lib.dq_plan_tuned(self.h, circuit.ref(), dtype_code(dtype), ctypes.byref(k),
                                            ctypes.byref(low), ctypes.byref(m)), "dq_plan_tuned")
         return k.value, low.value, m.value
+
+    def plan_set_tile(self, circuit: Circuit, k: int, low: int, M: int, jit: bool = True,
+                      dtype: torch.dtype = torch.complex64):
+        """dq_plan_set_tile: pin the forward tile shape (and the specialised
+        passes) for this circuit structure without tuning."""
+        self._check(self.lib.dq_plan_set_tile(self.h, circuit.ref(), dtype_code(dtype), int(k), int(low), int(M),
+                                              int(bool(jit))), "dq_plan_set_tile")
 
     def plan_autotune(self, circuit: Circuit, state: torch.Tensor):
         batch = _state_rows(state, circuit.nqubits, "state", self.device)

@@ -2517,6 +2517,31 @@ dq_status dq_plan_tuned(dq_ctx *ctx, const dq_circuit *circuit, int dtype, int *
     return DQ_OK;
 }
 
+dq_status dq_plan_set_tile(dq_ctx *ctx, const dq_circuit *circuit, int dtype, int k, int low, int M, int jit) {
+    dq_status st = check_ctx(ctx);
+    if (st != DQ_OK) return st;
+    if ((st = check_dtype(ctx, dtype)) != DQ_OK) return st;
+    if (jit != 0 && jit != 1) return fail(ctx, DQ_ERR_INVALID_ARG, "jit must be 0 or 1");
+    const int amp = amp_bytes(dtype);
+    const int mmax = dtype == DQ_C64 ? 5 : 4;
+    if (M < 2 || M > mmax || k < kTileLaneBits + M || k > kTileMaxK || low < kTileLaneBits || low > k - 2)
+        return fail(ctx, DQ_ERR_INVALID_ARG, "tile shape (k %d, low %d, M %d) out of range", k, low, M);
+    if ((1 << (k - M)) > (((1 << M) * amp >= 256) ? 256 : 512))
+        return fail(ctx, DQ_ERR_INVALID_ARG, "tile shape (k %d, M %d) needs too many threads per tile", k, M);
+    Plan *p = nullptr;
+    if ((st = get_plan(ctx, circuit, 0, &p)) != DQ_OK) return st;
+    if (!tile_supported(p->n, amp) || k > p->n - 1 ||
+        !get_schedule(ctx->tiles, *p, k, low, M, amp, false))
+        return fail(ctx, DQ_ERR_UNSUPPORTED, "no tile schedule of this shape for the circuit");
+    ctx->clear_graphs();
+    TileTune &t = ctx->tuned[p->key ^ (dtype == DQ_C128 ? 1ull : 0ull)];
+    t.k = k;
+    t.low = low;
+    t.M = M;
+    t.jit = jit;
+    return DQ_OK;
+}
+
 dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch, int dtype, void *state, void *stream) {
     dq_status st = check_ctx(ctx);
     if (st != DQ_OK) return st;

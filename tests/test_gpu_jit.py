@@ -220,3 +220,39 @@ def test_jit_whole_row_autotuned(ctx):
     assert_rel(e.cpu().numpy(), e_ref, torch.complex64, "expectations (autotuned rows)", zero_scale=scale)
     assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, "grad params (autotuned rows)", zero_scale=wl.batch * scale)
     assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, "grad data (autotuned rows)", zero_scale=scale)
+
+
+def test_pinned_tile_shape():
+    """dq_plan_set_tile: a pinned shape with specialised passes is what later
+    forward calls run (DQ_OPT_JIT = 2, no tuning), reported by plan_tuned,
+    with results against the oracle; shapes out of range or without a
+    schedule are refused."""
+    n = 17
+    rng = np.random.default_rng(1717)
+    gates, npar = random_gates(n, 5 * n, rng)
+    params = rng.uniform(-4, 4, npar)
+    circ = dq.Circuit(n, gates, nparams=npar)
+    obs = [W.obs_sum_z(n)]
+    ctx = dq.Context(0)
+    ctx.set_path(dq.PATH_FUSED)
+    try:
+        ctx.set_option(dq.OPT_JIT, 2)
+        ctx.plan_set_tile(circ, 11, 5, 4, jit=True)
+        assert ctx.plan_tuned(circ) == (11, 5, 4)
+        st, e, names = forward(ctx, circ, dev(params), None, 1, torch.complex64, n, obs, 2)
+        assert "k_tile_fwd_jit" in names, names
+        ref = oracle.run(n, gates, params)
+        assert_amps(np_state(st), ref, torch.complex64, "pinned shape, specialised")
+        ctx.plan_set_tile(circ, 12, 5, 3, jit=False)
+        st, e, names = forward(ctx, circ, dev(params), None, 1, torch.complex64, n, obs, 2)
+        assert "k_tile_fwd_jit" not in names and ctx.plan_tuned(circ) == (12, 5, 3), names
+        assert_amps(np_state(st), ref, torch.complex64, "pinned shape, interpreted")
+        for bad in ((4, 5, 4), (12, 5, 9), (12, 11, 4), (16, 5, 2)):
+            with pytest.raises(dq.DQError) as ei:
+                ctx.plan_set_tile(circ, *bad)
+            assert ei.value.status == 1, bad
+        lib = dq.load_library()   # the C check of the jit flag (the binding passes a bool)
+        assert lib.dq_plan_set_tile(ctx.h, circ.ref(), 0, 11, 5, 4, 2) == 1
+    finally:
+        ctx.set_option(dq.OPT_JIT, 2)
+        ctx.close()
