@@ -1097,9 +1097,11 @@ def profile_case(args):
         st = torch.empty((1, 1 << wl.n), dtype=torch.complex64, device=dev)
         for _ in range(iters):
             ctx.forward_grad(circ, params, obs, 1, torch.complex64, want_grad=False, state_out=st)
-    elif args.profile_case == "wsv":         # C3 fused forward + adjoint
+    elif args.profile_case == "wsv":         # C3 fused forward + adjoint (--jit 1: the specialised whole-row kernel)
         wl = W.config_c3()
         ctx.set_path(dq.PATH_FUSED)
+        if args.jit >= 0:
+            ctx.set_option(dq.OPT_JIT, args.jit)
         circ = dq.Circuit(wl.n, wl.gates, nparams=wl.nparams, nfeatures=wl.nfeatures)
         obs = dq.Observables(wl.observables)
         params = torch.tensor(wl.params, device=dev)
@@ -1162,6 +1164,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="issue kernels one by one (no CUDA-graph replay)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--jit", type=int, default=-1, help="profile cases: DQ_OPT_JIT value (default: the library's)")
     ap.add_argument("--tile", default="", help="profile case c2: pin the tile shape k,low,M (specialised passes)")
     ap.add_argument("--traffic-fingerprint", action="store_true",
                     help="print the source fingerprint of each kernel with a recorded DRAM traffic figure")

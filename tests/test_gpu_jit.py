@@ -256,3 +256,49 @@ def test_pinned_tile_shape():
     finally:
         ctx.set_option(dq.OPT_JIT, 2)
         ctx.close()
+
+
+CACHE_CHILD = r"""
+import os, sys, time, json
+import numpy as np, torch
+sys.path.insert(0, os.getcwd())
+import workloads as W, paper_2512_18995_gb300 as dq
+n = 10
+gates = W.hea_layers(n, 2) + [W.Gate("rzz", (1, 8), angle=0.4)]
+circ = dq.Circuit(n, gates, nparams=4 * n)
+ctx = dq.Context(0)
+ctx.set_path(dq.PATH_FUSED)
+ctx.set_option(dq.OPT_JIT, 1)
+params = torch.linspace(0.1, 3.0, 4 * n, dtype=torch.float64, device="cuda")
+ctx.set_tracing(True)
+t0 = time.time()
+e, gp, _, _ = ctx.forward_grad(circ, params, dq.Observables([W.obs_sum_z(n)]), 3, torch.complex64)
+torch.cuda.synchronize()
+dt = time.time() - t0
+names = sorted(ctx.trace())
+ctx.check()
+print("RESULT", json.dumps({"s": dt, "names": names, "e": float(e[0, 0]), "g": gp.cpu().tolist()}))
+"""
+
+
+def test_compiled_program_cache(tmp_path):
+    """Specialised programs are kept on disk (DQ_JIT_CACHE): the first process
+    compiles and writes the cubin, a second process with the same circuit
+    loads it (no new file) and gets identical results."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, DQ_JIT_CACHE=str(tmp_path))
+    runs = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", CACHE_CHILD], cwd=root, env=env, capture_output=True, text=True,
+                           timeout=600)
+        line = [x for x in r.stdout.splitlines() if x.startswith("RESULT ")]
+        assert r.returncode == 0 and line, r.stdout[-2000:] + r.stderr[-2000:]
+        runs.append((json.loads(line[0][7:]), sorted(p.name for p in tmp_path.iterdir())))
+    (first, files1), (second, files2) = runs
+    assert "k_rows_jit" in first["names"] and "k_rows_jit" in second["names"], first["names"]
+    assert len(files1) == 1 and files1[0].endswith(".cubin") and files2 == files1
+    assert first["e"] == second["e"] and first["g"] == second["g"]
