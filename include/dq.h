@@ -217,8 +217,22 @@ DQ_API dq_status dq_ctx_set_path(dq_ctx *ctx, int path);
  *   first use, which takes seconds); 2: when dq_plan_autotune measured them
  *   faster for this circuit and precision (tile passes and the whole-row
  *   kernel are measured separately).  Without NVRTC, or if a compile fails,
- *   the interpreting kernel runs. */
-enum dq_option { DQ_OPT_MULTIPASS = 1, DQ_OPT_WAIT_LIMIT_US = 2, DQ_OPT_DENSE_BLOCKS = 3, DQ_OPT_JIT = 4 };
+ *   the interpreting kernel runs.
+ * DQ_OPT_ROWS_PER_CTA (default 0): complex64 rows of up to 16 qubits held
+ *   on chip run one (1) or two (2) rows per CTA; 0 chooses two for rows of at
+ *   most 128 threads when the batch gives every SM at least four rows and two
+ *   rows' buffers fit in shared memory.  The two halves of a CTA run the same
+ *   program in step (one instruction stream for both rows).  Expectations,
+ *   states and per-row gradients are identical either way, shared-parameter
+ *   gradients up to the order of their FP64 sums; complex128 rows and a
+ *   choice that does not fit run one row per CTA. */
+enum dq_option {
+    DQ_OPT_MULTIPASS = 1,
+    DQ_OPT_WAIT_LIMIT_US = 2,
+    DQ_OPT_DENSE_BLOCKS = 3,
+    DQ_OPT_JIT = 4,
+    DQ_OPT_ROWS_PER_CTA = 5
+};
 
 /* Set a context option; DQ_ERR_INVALID_ARG for an unknown option or value.
  * Captured graphs of the context are dropped (the next calls capture anew). */

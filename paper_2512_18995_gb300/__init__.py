@@ -12,7 +12,7 @@ Typical use::
     e = dq.expectation(circ, params, obs, context=ctx)   # differentiable
     e.sum().backward()                                   # adjoint method
 """
-from ._lib import (ADJ_CLOBBER_STATE, DQ_C64, DQ_C128, OPT_DENSE_BLOCKS, OPT_JIT, OPT_MULTIPASS, OPT_WAIT_LIMIT_US, PATH_AUTO, PATH_FUSED, PATH_PLAIN, Circuit,
+from ._lib import (ADJ_CLOBBER_STATE, DQ_C64, DQ_C128, OPT_DENSE_BLOCKS, OPT_JIT, OPT_MULTIPASS, OPT_ROWS_PER_CTA, OPT_WAIT_LIMIT_US, PATH_AUTO, PATH_FUSED, PATH_PLAIN, Circuit,
                    Context,
                    DQError, Observables, load_library, lower_circuit, row_program, shift_rules, tile_schedule)
 from .autograd import (DensityExpectationFunction, ExpectationFunction, density_expectation, expectation,
@@ -20,4 +20,4 @@ from .autograd import (DensityExpectationFunction, ExpectationFunction, density_
 
 __all__ = ["Circuit", "Context", "DQError", "Observables", "expectation", "ExpectationFunction",
            "density_expectation", "DensityExpectationFunction", "measure",
-           "load_library", "lower_circuit", "tile_schedule", "row_program", "shift_rules", "PATH_AUTO", "PATH_PLAIN", "PATH_FUSED", "OPT_MULTIPASS", "OPT_WAIT_LIMIT_US", "OPT_DENSE_BLOCKS", "OPT_JIT", "DQ_C64", "DQ_C128", "ADJ_CLOBBER_STATE"]
+           "load_library", "lower_circuit", "tile_schedule", "row_program", "shift_rules", "PATH_AUTO", "PATH_PLAIN", "PATH_FUSED", "OPT_MULTIPASS", "OPT_WAIT_LIMIT_US", "OPT_DENSE_BLOCKS", "OPT_JIT", "OPT_ROWS_PER_CTA", "DQ_C64", "DQ_C128", "ADJ_CLOBBER_STATE"]

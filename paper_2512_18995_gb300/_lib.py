@@ -23,7 +23,7 @@ STATUS = {0: "DQ_OK", 1: "DQ_ERR_INVALID_ARG", 2: "DQ_ERR_UNSUPPORTED", 3: "DQ_E
           4: "DQ_ERR_CUDA", 5: "DQ_ERR_TIMEOUT"}
 DQ_C64, DQ_C128 = 0, 1
 PATH_AUTO, PATH_PLAIN, PATH_FUSED = 0, 1, 2
-OPT_MULTIPASS, OPT_WAIT_LIMIT_US, OPT_DENSE_BLOCKS, OPT_JIT = 1, 2, 3, 4
+OPT_MULTIPASS, OPT_WAIT_LIMIT_US, OPT_DENSE_BLOCKS, OPT_JIT, OPT_ROWS_PER_CTA = 1, 2, 3, 4, 5
 ADJ_CLOBBER_STATE = 1
 
 KIND = {k: i for i, k in enumerate(
@@ -451,7 +451,7 @@ class Context:
         self.path = int(path)
 
     def set_option(self, option: int, value: int):
-        """dq_ctx_set_option (OPT_MULTIPASS, OPT_WAIT_LIMIT_US, OPT_DENSE_BLOCKS, OPT_JIT)."""
+        """dq_ctx_set_option (OPT_MULTIPASS, OPT_WAIT_LIMIT_US, OPT_DENSE_BLOCKS, OPT_JIT, OPT_ROWS_PER_CTA)."""
         self._check(self.lib.dq_ctx_set_option(self.h, int(option), int(value)), "dq_ctx_set_option")
 
     def selftest_wait_expiry(self):

@@ -144,6 +144,7 @@ struct DensePlan {
 
 struct dq_ctx {
     int device = 0;
+    int rows_rpc = 0;   // DQ_OPT_ROWS_PER_CTA: 0 automatic, 1, 2
     int nsm = 0;
     size_t smem_optin = 0;
     int path = DQ_PATH_AUTO;
@@ -778,21 +779,26 @@ RowProgram *get_rows(dq_ctx *ctx, const Plan &p, int amp, bool grad, int nobs) {
 // for this plan and precision.  Compiled on first use; a failed compile
 // keeps the interpreter for the program (the reason in the tile cache's
 // jit_err).
-bool rows_jit(dq_ctx *ctx, const Plan &p, RowProgram &rp, int amp) {
-    if (ctx->tiles.jit_mode == 0 || rp.jit_failed) return false;
+bool rows_jit(dq_ctx *ctx, const Plan &p, RowProgram &rp, int amp, int rpc) {
+    if (ctx->tiles.jit_mode == 0 || rp.jit_failed[rpc - 1]) return false;
     if (ctx->tiles.jit_mode == 2) {
         auto it = ctx->tuned.find(p.key ^ (amp == 16 ? 1ull : 0ull));
         if (it == ctx->tuned.end() || it->second.rows_jit != 1) return false;
     }
-    if (!rp.jit) {
+    if (!rp.jit[rpc - 1]) {
         std::string err;
-        if (!jit_rows_build(rp, amp, ctx->tiles.device, &err)) {
-            rp.jit_failed = true;
+        if (!jit_rows_build(rp, amp, ctx->tiles.device, &err, rpc)) {
+            rp.jit_failed[rpc - 1] = true;
             ctx->tiles.jit_err = err;
             return false;
         }
     }
     return true;
+}
+
+// Rows per CTA of a whole-row call (DQ_OPT_ROWS_PER_CTA, within what fits).
+int rows_rpc(dq_ctx *ctx, const RowProgram &rp, int amp, bool grad, int nobs, int batch) {
+    return rows_pick_rpc(rp, amp, grad, std::max(1, nobs), batch, ctx->nsm, ctx->smem_optin, ctx->rows_rpc);
 }
 
 // Run `body(stream)` through the context's graph cache.  Returns true when the
@@ -1051,9 +1057,10 @@ dq_status apply_impl(dq_ctx *ctx, Plan &p, const double *params, const double *d
     void *coef = w.take(coef_bytes(p, batch, sizeof(R) == 8 ? DQ_C128 : DQ_C64));
     DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
     if (rp) {
+        const int rpc = rows_rpc(ctx, *rp, (int)sizeof(cx<R>), false, 1, batch);
         DQ_CUDA(rows_launch<R>(*rp, p, coef, state, 1, nullptr, 0, 1, nullptr, batch, state, nullptr, nullptr, nullptr,
                                nullptr, ctx->nsm, ctx->smem_optin, s, &ctx->launches,
-                               rows_jit(ctx, p, *rp, (int)sizeof(cx<R>))),
+                               rows_jit(ctx, p, *rp, (int)sizeof(cx<R>), rpc), rpc),
                 "fused apply (rows)");
     } else if (small) {
         DQ_CUDA(wsv_launch<R>(p, coef, state, 1, nullptr, 0, 1, nullptr, batch, state, nullptr, nullptr, nullptr,
@@ -1087,9 +1094,10 @@ dq_status expect_impl(dq_ctx *ctx, int n, ObsDev &o, const void *state, int batc
     p.key = 0x5bd1e995ull * (uint64_t)(n + 1);
     RowProgram *rp = use_fused(ctx) ? get_rows(ctx, p, (int)sizeof(cx<R>), false, o.nobs) : nullptr;
     if (rp) {
+        const int rpc = rows_rpc(ctx, *rp, (int)sizeof(cx<R>), false, o.nobs, batch);
         DQ_CUDA(rows_launch<R>(*rp, p, nullptr, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, nullptr, batch,
                                nullptr, out, nullptr, nullptr, nullptr, ctx->nsm, ctx->smem_optin, s, &ctx->launches,
-                               rows_jit(ctx, p, *rp, (int)sizeof(cx<R>))),
+                               rows_jit(ctx, p, *rp, (int)sizeof(cx<R>), rpc), rpc),
                 "fused expect (rows)");
         return DQ_OK;
     }
@@ -1150,10 +1158,11 @@ dq_status adjoint_impl(dq_ctx *ctx, Plan &p, ObsDev &o, const double *params, co
     DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
     if (small) {
         double *part = (double *)w.take(std::max(wsv_part_bytes(p, ctx->nsm), rows_part_bytes(p, ctx->nsm)));
+        const int rpc = rp ? rows_rpc(ctx, *rp, (int)sizeof(cx<R>), true, o.nobs, batch) : 1;
         if (rp)
             DQ_CUDA(rows_launch<R>(*rp, p, coef, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, rw, batch, nullptr,
                                    nullptr, gp, gd, part, ctx->nsm, ctx->smem_optin, s, &ctx->launches,
-                                   rows_jit(ctx, p, *rp, (int)sizeof(cx<R>))),
+                                   rows_jit(ctx, p, *rp, (int)sizeof(cx<R>), rpc), rpc),
                     "fused adjoint (rows)");
         else
             DQ_CUDA(wsv_launch<R>(p, coef, state, 0, o.d_wires, (int)o.bits.size(), o.nobs, rw, batch, nullptr,
@@ -1217,10 +1226,11 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
         void *coef = w.take(coef_bytes(p, batch, dt));
         double *part = (double *)w.take(std::max(wsv_part_bytes(p, ctx->nsm), rows_part_bytes(p, ctx->nsm)));
         DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
+        const int rpc = rp ? rows_rpc(ctx, *rp, (int)sizeof(cx<R>), grad, o ? o->nobs : 1, batch) : 1;
         if (rp)
             DQ_CUDA(rows_launch<R>(*rp, p, coef, nullptr, 1, o ? o->d_wires : nullptr, o ? (int)o->bits.size() : 0,
                                    o ? o->nobs : 1, rw, batch, state_out, eo, gp, gd, part, ctx->nsm, ctx->smem_optin,
-                                   s, &ctx->launches, rows_jit(ctx, p, *rp, (int)sizeof(cx<R>))),
+                                   s, &ctx->launches, rows_jit(ctx, p, *rp, (int)sizeof(cx<R>), rpc), rpc),
                     "fused forward+adjoint (rows)");
         else
             DQ_CUDA(wsv_launch<R>(p, coef, nullptr, 1, o ? o->d_wires : nullptr, o ? (int)o->bits.size() : 0,
@@ -1407,6 +1417,10 @@ dq_status dq_ctx_set_option(dq_ctx *ctx, int option, int64_t value) {
     case DQ_OPT_JIT:
         if (value < 0 || value > 2) return fail(ctx, DQ_ERR_INVALID_ARG, "DQ_OPT_JIT takes 0, 1 or 2");
         ctx->tiles.jit_mode = (int)value;
+        break;
+    case DQ_OPT_ROWS_PER_CTA:
+        if (value < 0 || value > 2) return fail(ctx, DQ_ERR_INVALID_ARG, "DQ_OPT_ROWS_PER_CTA takes 0, 1 or 2");
+        ctx->rows_rpc = (int)value;
         break;
     case DQ_OPT_DENSE_BLOCKS:
         if (value < 0 || value > 2) return fail(ctx, DQ_ERR_INVALID_ARG, "DQ_OPT_DENSE_BLOCKS takes 0, 1 or 2");
@@ -2329,11 +2343,12 @@ template <typename R>
 cudaError_t rows_autotune(dq_ctx *ctx, const Plan &p, RowProgram &rp, const void *coef, void *state, int batch,
                           cudaStream_t s) {
     const int amp = (int)sizeof(cx<R>);
-    if (!jit_available() || rp.jit_failed) return cudaSuccess;
-    if (!rp.jit) {
+    const int rpc = rows_rpc(ctx, rp, amp, false, 1, batch);
+    if (!jit_available() || rp.jit_failed[rpc - 1]) return cudaSuccess;
+    if (!rp.jit[rpc - 1]) {
         std::string err;
-        if (!jit_rows_build(rp, amp, ctx->tiles.device, &err)) {
-            rp.jit_failed = true;
+        if (!jit_rows_build(rp, amp, ctx->tiles.device, &err, rpc)) {
+            rp.jit_failed[rpc - 1] = true;
             ctx->tiles.jit_err = err;
             return cudaSuccess;
         }
@@ -2348,7 +2363,7 @@ cudaError_t rows_autotune(dq_ctx *ctx, const Plan &p, RowProgram &rp, const void
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
         auto run = [&]() {
             return rows_launch<R>(rp, p, coef, nullptr, 1, nullptr, 0, 1, nullptr, batch, state, nullptr, nullptr,
-                                  nullptr, nullptr, ctx->nsm, ctx->smem_optin, s, &ctx->launches, j == 1);
+                                  nullptr, nullptr, ctx->nsm, ctx->smem_optin, s, &ctx->launches, j == 1, rpc);
         };
         e = run();   // warm-up
         cudaEventRecord(e0, s);

@@ -43,9 +43,10 @@ bool jit_want(TileCache &tc, const std::unordered_map<uint64_t, TileTune> &tuned
 // Compile and load every pass of sc for `device` (sc.jit); false with *err on failure.
 bool jit_build(TileSchedule &sc, int amp, int device, std::string *err);
 // Source of the whole-row kernel with the program's ops compiled in (kernel
-// dq_jit_rows, taking RowArgs like the interpreting kernel).
-std::string jit_rows_source(const RowProgram &rp, int amp);
-// Compile and load it for `device` (rp.jit, one kernel); false with *err on failure.
-bool jit_rows_build(RowProgram &rp, int amp, int device, std::string *err);
+// dq_jit_rows, taking RowArgs like the interpreting kernel; rpc rows per CTA).
+std::string jit_rows_source(const RowProgram &rp, int amp, int rpc = 1);
+// Compile and load it for `device` and rpc rows per CTA (rp.jit[rpc - 1], one
+// kernel); false with *err on failure.
+bool jit_rows_build(RowProgram &rp, int amp, int device, std::string *err, int rpc = 1);
 
 }  // namespace dq

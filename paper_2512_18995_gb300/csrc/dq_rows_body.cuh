@@ -108,29 +108,41 @@ struct InterpRows {
     }
 };
 
-template <typename R, int M, bool PD, typename Runner>
+// RPC rows per CTA: the CTA's warps split into RPC halves, half h holding
+// row rbase + h with its own state buffers and coefficient table.  Every half
+// runs the same instructions (the same program, the same barriers), so the
+// SM's schedulers fetch one instruction stream for RPC rows; a half without a
+// row (the batch's ragged end) computes on zeros and writes nothing.
+template <typename R, int M, bool PD, typename Runner, int RPC = 1>
 __device__ __forceinline__ void rows_body(const RowArgs &a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int hthreads = blockDim.x / RPC, nwh = nw / RPC;
+    const int half = RPC == 1 ? 0 : warp / nwh;
+    const int hwarp = RPC == 1 ? warp : warp % nwh;
+    const int htid = RPC == 1 ? tid : tid % hthreads;
     const int n = a.n;
     const int64_t dim = int64_t(1) << n;
-    cx<R> *bufP = reinterpret_cast<cx<R> *>(smem);
+    const int nbuf = a.grad ? 2 : 1;
+    cx<R> *bufP = reinterpret_cast<cx<R> *>(smem) + (int64_t)half * nbuf * dim;
     cx<R> *bufL = bufP + dim;
-    unsigned char *q = smem + (a.grad ? 2 : 1) * dim * sizeof(cx<R>);
+    unsigned char *q = smem + (size_t)RPC * nbuf * dim * sizeof(cx<R>);
     EOp *sops = reinterpret_cast<EOp *>(q);          // forward decodings
     EOp *srops = sops + a.nops;                        // reverse decodings
     ESeg *sf = reinterpret_cast<ESeg *>(srops + a.nops);
     ESeg *sr = sf + a.nfseg;
-    Mat2<R> *scoef = reinterpret_cast<Mat2<R> *>(sr + a.nrseg);
+    Mat2<R> *scoef_all = reinterpret_cast<Mat2<R> *>(sr + a.nrseg);   // [RPC][nops]
+    Mat2<R> *scoef = scoef_all + (size_t)half * a.nops;
     const int nacc = a.nacc_shared + a.nacc_row;
-    double *acc = reinterpret_cast<double *>(scoef + a.nops);     // [nacc] FP64 per CTA
+    double *acc = reinterpret_cast<double *>(scoef_all + (size_t)RPC * a.nops);   // [nacc] FP64 per CTA
     double *expw = acc + nacc;                                     // [nw][nobs]
     R *accw = reinterpret_cast<R *>(expw + (size_t)nw * a.nobs);   // [nw][nacc] per-row partials (state precision)
+    R *accwh = accw + (size_t)half * nwh * nacc;                   // this half's warps
     const Mat2<R> *gcoef = reinterpret_cast<const Mat2<R> *>(a.coef);
     for (int i = tid; i < a.nops; i += blockDim.x) {
         sops[i] = a.fops[i];
         srops[i] = a.rops[i];
-        scoef[i] = gcoef[sops[i].coef];
+        for (int h = 0; h < RPC; ++h) scoef_all[(size_t)h * a.nops + i] = gcoef[a.fops[i].coef];
     }
     for (int i = tid; i < a.nfseg; i += blockDim.x) sf[i] = a.fsegs[i];
     for (int i = tid; i < a.nrseg; i += blockDim.x) sr[i] = a.rsegs[i];
@@ -140,24 +152,27 @@ __device__ __forceinline__ void rows_body(const RowArgs &a) {
 
     cx<R> ps[1 << M], ls[1 << M];
     // ops whose coefficients depend on the row (per-row parameters, encoded
-    // features) have their block refreshed in the shared table for every row,
+    // features) have their block refreshed in the half's table for every row,
     // so every op reads its coefficients from shared memory
     bool any_row = false;
     for (int i = 0; i < a.nops; ++i) any_row |= sops[i].rowstep != 0;
-    for (int row = blockIdx.x; row < a.batch; row += gridDim.x) {
+    for (int64_t rbase = (int64_t)blockIdx.x * RPC; rbase < a.batch; rbase += (int64_t)gridDim.x * RPC) {
+        const int64_t row = rbase + half;
+        const bool valid = row < a.batch;
+        const int64_t crow = valid ? row : rbase;   // a row that exists, for the half without one
         if (any_row) {
-            for (int i = tid; i < a.nops; i += blockDim.x)
-                if (sops[i].rowstep) scoef[i] = gcoef[sops[i].coef + (int64_t)row * sops[i].rowstep];
+            for (int i = htid; i < a.nops; i += hthreads)
+                if (sops[i].rowstep) scoef[i] = gcoef[sops[i].coef + crow * sops[i].rowstep];
             __syncthreads();
         }
         // ---- state preparation ------------------------------------------------
-        Layout L = make_layout(sf[0], M, n, lane, warp);
+        Layout L = make_layout(sf[0], M, n, lane, hwarp);
         if (a.state_in) {
-            const cx<R> *gi = reinterpret_cast<const cx<R> *>(a.state_in) + row * dim;
+            const cx<R> *gi = reinterpret_cast<const cx<R> *>(a.state_in) + crow * dim;
 #pragma unroll
             for (int e = 0; e < (1 << M); ++e) {
                 const uint32_t i = L.tb | reg_off<M>(L, e);
-                ps[e] = DQ_INB(i, dim) ? gi[i] : mk<R>(R(0), R(0));
+                ps[e] = (valid && DQ_INB(i, dim)) ? gi[i] : mk<R>(R(0), R(0));
             }
         } else {
 #pragma unroll
@@ -165,9 +180,9 @@ __device__ __forceinline__ void rows_body(const RowArgs &a) {
                 ps[e] = mk<R>((L.tb | reg_off<M>(L, e)) == 0 ? R(1) : R(0), R(0));
         }
         // ---- forward ----------------------------------------------------------
-        if (a.forward) Runner::template fwd<R, M, PD>(ps, bufP, L, sf, sops, scoef, a.nfseg, n, lane, warp);
+        if (a.forward) Runner::template fwd<R, M, PD>(ps, bufP, L, sf, sops, scoef, a.nfseg, n, lane, hwarp);
         __syncthreads();   // every thread has finished reading this row's input
-        if (a.state_out) {
+        if (a.state_out && valid) {
             cx<R> *go = reinterpret_cast<cx<R> *>(a.state_out) + row * dim;
 #pragma unroll
             for (int e = 0; e < (1 << M); ++e) {
@@ -186,13 +201,13 @@ __device__ __forceinline__ void rows_body(const RowArgs &a) {
                 const uint64_t f = wire_bits(t.f, n), sm = wire_bits(t.s, n);
                 R v = R(0);
                 if (f == 0) {
-                    for (int64_t b = tid; b < dim; b += blockDim.x) {
+                    for (int64_t b = htid; b < dim; b += hthreads) {
                         const cx<R> x = bufP[b];
                         const R pr = x.x * x.x + x.y * x.y;
                         v += parity64((uint64_t)b & sm) ? -pr : pr;
                     }
                 } else {
-                    for (int64_t b = tid; b < dim; b += blockDim.x) {
+                    for (int64_t b = htid; b < dim; b += hthreads) {
                         if (!DQ_INB(b ^ f, dim)) continue;
                         const cx<R> x = bufP[b], y = bufP[b ^ f];
                         const R re = re_conj_mul(y, x), im = im_conj_mul(y, x);
@@ -204,13 +219,13 @@ __device__ __forceinline__ void rows_body(const RowArgs &a) {
                 if (lane == 0) expw[warp * a.nobs + t.obs] += t.coeff * (double)v;
             }
             __syncthreads();
-            if (tid < a.nobs) {
+            if (htid < a.nobs) {
                 double s = 0.0;
-                for (int w = 0; w < nw; ++w) {
-                    s += expw[w * a.nobs + tid];
-                    expw[w * a.nobs + tid] = 0.0;
+                for (int w = half * nwh; w < (half + 1) * nwh; ++w) {
+                    s += expw[w * a.nobs + htid];
+                    expw[w * a.nobs + htid] = 0.0;
                 }
-                if (a.expect_out) a.expect_out[(int64_t)row * a.nobs + tid] = s;
+                if (a.expect_out && valid) a.expect_out[row * a.nobs + htid] = s;
             }
         }
         if (!a.grad) {
@@ -218,9 +233,9 @@ __device__ __forceinline__ void rows_body(const RowArgs &a) {
             continue;
         }
         // ---- lambda = sum_o w_o O_o psi in the first reverse layout ------------
-        L = make_layout(sr[0], M, n, lane, warp);
+        L = make_layout(sr[0], M, n, lane, hwarp);
         eng_load<R, M>(ps, bufP, L);
-        const double *w = a.row_weights ? a.row_weights + (int64_t)row * a.nobs : nullptr;
+        const double *w = a.row_weights ? a.row_weights + crow * a.nobs : nullptr;
 #pragma unroll
         for (int e = 0; e < (1 << M); ++e) {
             const uint64_t l = L.tb | reg_off<M>(L, e);
@@ -241,29 +256,31 @@ __device__ __forceinline__ void rows_body(const RowArgs &a) {
         }
         __syncthreads();   // bufP is rewritten by the first layout change
         // ---- reverse sweep -----------------------------------------------------
-        Runner::template rev<R, M, PD>(ps, ls, bufP, bufL, L, sr, srops, scoef, accw, nacc, a.nrseg_run, n, lane,
-                                       warp);
+        Runner::template rev<R, M, PD>(ps, ls, bufP, bufL, L, sr, srops, scoef, accwh, nacc, a.nrseg_run, n, lane,
+                                       hwarp);
         __syncthreads();
-        // fold this row's warp partials into FP64: shared parameters
-        // accumulate over the CTA's rows, per-row outputs are written out
+        // fold the rows' warp partials into FP64: shared parameters
+        // accumulate over the CTA's rows (halves with a row), per-row outputs
+        // are written out
         for (int i = tid; i < a.nacc_shared; i += blockDim.x) {
             double s = 0.0;
             for (int ww = 0; ww < nw; ++ww) {
-                s += (double)accw[ww * nacc + i];
+                if (rbase + ww / nwh < a.batch) s += (double)accw[ww * nacc + i];
                 accw[ww * nacc + i] = R(0);
             }
             acc[i] += s;
         }
-        for (int i = tid; i < a.nacc_row; i += blockDim.x) {
+        for (int i = htid; i < a.nacc_row; i += hthreads) {
             double s = 0.0;
-            for (int ww = 0; ww < nw; ++ww) {
-                s += (double)accw[ww * nacc + a.nacc_shared + i];
-                accw[ww * nacc + a.nacc_shared + i] = R(0);
+            for (int ww = 0; ww < nwh; ++ww) {
+                s += (double)accwh[ww * nacc + a.nacc_shared + i];
+                accwh[ww * nacc + a.nacc_shared + i] = R(0);
             }
+            if (!valid) continue;
             if (i < a.nfeat) {
-                if (a.grad_data) a.grad_data[(int64_t)row * a.nfeat + i] = s;
+                if (a.grad_data) a.grad_data[row * a.nfeat + i] = s;
             } else if (a.grad_params) {
-                a.grad_params[(int64_t)row * a.nparams + (i - a.nfeat)] = s;
+                a.grad_params[row * a.nparams + (i - a.nfeat)] = s;
             }
         }
         __syncthreads();

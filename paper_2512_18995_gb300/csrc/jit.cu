@@ -366,11 +366,11 @@ void emit_rows_reverse(std::ostringstream &s, const RowProgram &rp, int nacc) {
 // Source of the whole-row kernel with the program's ops compiled in: one op
 // runner (forward segments; reverse segments with gradient partials) and the
 // kernel dq_jit_rows.
-std::string jit_rows_source(const RowProgram &rp, int amp) {
+std::string jit_rows_source(const RowProgram &rp, int amp, int rpc) {
     const char *R = amp == 16 ? "double" : "float";
     const int M = rp.M;
-    const int maxt = ((1 << M) * amp <= 64) ? 512 : 256;
-    const int minb = amp == 8 ? 2 : 1;
+    const int maxt = (((1 << M) * amp <= 64) ? 512 : 256) * rpc;
+    const int minb = (amp == 8 && rpc == 1) ? 2 : 1;
     const int nacc = rp.nacc_shared + rp.nacc_row;
     std::ostringstream s;
     s << kPrelude << "#include \"dq_rows_body.cuh\"\nnamespace dq {\nnamespace {\n"
@@ -397,7 +397,8 @@ std::string jit_rows_source(const RowProgram &rp, int amp) {
     emit_rows_reverse(s, rp, nacc);
     s << "    }\n};\n}  // namespace\n}  // namespace dq\n"
       << "extern \"C\" __global__ void __launch_bounds__(" << maxt << ", " << minb << ") dq_jit_rows(dq::RowArgs a) {\n"
-      << "    dq::rows_body<" << R << ", " << M << ", " << (rp.pdiag ? "true" : "false") << ", dq::JitRows>(a);\n}\n";
+      << "    dq::rows_body<" << R << ", " << M << ", " << (rp.pdiag ? "true" : "false") << ", dq::JitRows, " << rpc
+      << ">(a);\n}\n";
     return s.str();
 }
 
@@ -544,12 +545,16 @@ bool jit_compile(const std::string &src, int cc, std::vector<char> *cubin, std::
     return true;
 }
 
-bool jit_rows_build(RowProgram &rp, int amp, int device, std::string *err) {
+bool jit_rows_build(RowProgram &rp, int amp, int device, std::string *err, int rpc) {
+    if (rpc != 1 && rpc != 2) {
+        if (err) *err = "rows per CTA must be 1 or 2";
+        return false;
+    }
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
     std::vector<char> cubin;
-    if (!jit_compile(jit_rows_source(rp, amp), major * 10 + minor, &cubin, err)) return false;
+    if (!jit_compile(jit_rows_source(rp, amp, rpc), major * 10 + minor, &cubin, err)) return false;
     JitModule *m = new JitModule();
     cudaLibrary_t lib = nullptr;
     cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
@@ -568,11 +573,11 @@ bool jit_rows_build(RowProgram &rp, int amp, int device, std::string *err) {
     m->kernels.push_back(k);
     m->grid.assign(1, 0);
     m->smem_set.assign(1, 0);
-    if (rp.jit) {
-        rp.jit->release();
-        delete rp.jit;
+    if (rp.jit[rpc - 1]) {
+        rp.jit[rpc - 1]->release();
+        delete rp.jit[rpc - 1];
     }
-    rp.jit = m;
+    rp.jit[rpc - 1] = m;
     return true;
 }
 

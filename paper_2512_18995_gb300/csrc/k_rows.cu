@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdlib>
 #include <vector>
 
@@ -27,10 +28,11 @@
 namespace dq {
 
 void RowProgram::release() {
-    if (jit) {
-        jit->release();
-        delete jit;
-        jit = nullptr;
+    for (JitModule *&m : jit) {
+        if (!m) continue;
+        m->release();
+        delete m;
+        m = nullptr;
     }
     cudaFree(d_fops);
     cudaFree(d_rops);
@@ -183,9 +185,10 @@ bool rows_build_program(const Plan &p, int M, RowProgram &out) {
 
 namespace {
 
-template <typename R, int M, bool PD>
-__global__ void __launch_bounds__(rows_max_threads<R, M>(), sizeof(R) == 4 ? 2 : 1) k_rows(RowArgs a) {
-    rows_body<R, M, PD, InterpRows>(a);
+template <typename R, int M, bool PD, int RPC>
+__global__ void __launch_bounds__(rows_max_threads<R, M>() * RPC, (sizeof(R) == 4 && RPC == 1) ? 2 : 1)
+k_rows(RowArgs a) {
+    rows_body<R, M, PD, InterpRows, RPC>(a);
 }
 
 __global__ void k_rows_part_reduce(const double *__restrict__ part, int nblk, int np, double *__restrict__ out) {
@@ -198,13 +201,28 @@ __global__ void k_rows_part_reduce(const double *__restrict__ part, int nblk, in
 
 }  // namespace
 
-size_t rows_smem_bytes(const RowProgram &rp, int amp, bool grad, int nobs, int threads) {
+size_t rows_smem_bytes(const RowProgram &rp, int amp, bool grad, int nobs, int threads, int rpc) {
     const int nw = threads / 32;
     const size_t matb = amp == 8 ? sizeof(Mat2<float>) : sizeof(Mat2<double>);
-    return (size_t)(grad ? 2 : 1) * ((size_t)amp << rp.n) + 2 * rp.fops.size() * sizeof(EOp) +
-           (rp.fsegs.size() + rp.rsegs.size()) * sizeof(ESeg) + rp.fops.size() * matb +
+    return (size_t)rpc * (grad ? 2 : 1) * ((size_t)amp << rp.n) + 2 * rp.fops.size() * sizeof(EOp) +
+           (rp.fsegs.size() + rp.rsegs.size()) * sizeof(ESeg) + (size_t)rpc * rp.fops.size() * matb +
            (size_t)(rp.nacc_shared + rp.nacc_row + nw * nobs) * sizeof(double) +
            (size_t)nw * (rp.nacc_shared + rp.nacc_row) * (amp == 8 ? sizeof(float) : sizeof(double)) + 64;
+}
+
+int rows_pick_rpc(const RowProgram &rp, int amp, bool grad, int nobs, int batch, int nsm, size_t smem_optin,
+                  int want) {
+    const int threads = 1 << (rp.n - rp.M);
+    const int maxt = ((1 << rp.M) * amp <= 64) ? 512 : 256;
+    const bool two_fit = 2 * threads <= 2 * maxt && 2 * threads <= 1024 &&
+                         rows_smem_bytes(rp, amp, grad, nobs, 2 * threads, 2) <= smem_optin;
+    if (want == 1 || !two_fit || amp != 8) return 1;   // complex64 only: two complex128 rows spill
+    if (want == 2) return 2;
+    // automatic: two rows per CTA for rows of at most 128 threads when the
+    // batch still gives every SM four rows -- measured on 4096-row batches:
+    // 10 qubits (64 threads a row) 1.19 -> 0.87 ms specialised, 1.23 -> 1.03 ms
+    // interpreted; 12 qubits (256 threads) 2.70 -> 2.81 ms specialised
+    return (batch >= 4 * nsm && threads <= 128) ? 2 : 1;
 }
 
 size_t rows_part_bytes(const Plan &p, int nsm) {
@@ -215,11 +233,13 @@ template <typename R>
 cudaError_t rows_launch(const RowProgram &rp, const Plan &p, const void *coef, const void *state_in, int forward,
                         const DevTerm *d_wterms, int nterms, int nobs, const double *row_weights, int batch,
                         void *state_out, double *expect_out, double *grad_params, double *grad_data, double *part,
-                        int nsm, size_t smem_optin, cudaStream_t s, int64_t *launches, bool jit) {
+                        int nsm, size_t smem_optin, cudaStream_t s, int64_t *launches, bool jit, int rpc) {
     const bool grad = grad_params || grad_data;
-    jit = jit && rp.jit && !rp.jit->kernels.empty();
-    const int threads = 1 << (rp.n - rp.M);
-    const size_t smem = rows_smem_bytes(rp, (int)sizeof(cx<R>), grad, nobs, threads);
+    if (rpc != 1 && rpc != 2) return cudaErrorInvalidValue;
+    JitModule *jm = rp.jit[rpc - 1];
+    jit = jit && jm && !jm->kernels.empty();
+    const int threads = rpc << (rp.n - rp.M);
+    const size_t smem = rows_smem_bytes(rp, (int)sizeof(cx<R>), grad, nobs, threads, rpc);
     if (smem > smem_optin) return cudaErrorInvalidValue;
     RowArgs a;
     a.fops = rp.d_fops;
@@ -270,20 +290,29 @@ cudaError_t rows_launch(const RowProgram &rp, const Plan &p, const void *coef, c
         }
     }
     constexpr int Mmax = sizeof(R) == 4 ? 4 : 3;
-    const void *kfn = nullptr;
     const bool pd = rp.pdiag;
-    switch (rp.M) {
-    case 2: kfn = pd ? (const void *)k_rows<R, 2, true> : (const void *)k_rows<R, 2, false>; break;
-    case 3: kfn = pd ? (const void *)k_rows<R, 3, true> : (const void *)k_rows<R, 3, false>; break;
-    default: kfn = pd ? (const void *)k_rows<R, Mmax, true> : (const void *)k_rows<R, Mmax, false>; break;
+    auto pick = [&](auto rpc_tag) -> const void * {
+        constexpr int C = decltype(rpc_tag)::value;
+        switch (rp.M) {
+        case 2: return pd ? (const void *)k_rows<R, 2, true, C> : (const void *)k_rows<R, 2, false, C>;
+        case 3: return pd ? (const void *)k_rows<R, 3, true, C> : (const void *)k_rows<R, 3, false, C>;
+        default: return pd ? (const void *)k_rows<R, Mmax, true, C> : (const void *)k_rows<R, Mmax, false, C>;
+        }
+    };
+    // two rows per CTA for complex64 only (complex128 rows would not keep their registers)
+    const void *kfn = pick(std::integral_constant<int, 1>());
+    if constexpr (sizeof(R) == 4) {
+        if (rpc == 2) kfn = pick(std::integral_constant<int, 2>());
+    } else {
+        if (rpc == 2) return cudaErrorInvalidValue;
     }
-    if (jit) kfn = (const void *)rp.jit->kernels[0];
+    if (jit) kfn = (const void *)jm->kernels[0];
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
-    const int grid = std::max(1, std::min(batch, std::min(per_sm, 4) * nsm));
+    const int grid = std::max(1, std::min((batch + rpc - 1) / rpc, std::min(per_sm, 4) * nsm));
     if (jit) {
         LaunchScope ls(s, "k_rows_jit", launches);
         cudaLaunchConfig_t cfg = {};
@@ -296,16 +325,9 @@ cudaError_t rows_launch(const RowProgram &rp, const Plan &p, const void *coef, c
         if (e != cudaSuccess) return e;
     } else {
         LaunchScope ls(s, "k_rows", launches);
-        switch (rp.M * 2 + (pd ? 1 : 0)) {
-        case 4: k_rows<R, 2, false><<<grid, threads, smem, s>>>(a); break;
-        case 5: k_rows<R, 2, true><<<grid, threads, smem, s>>>(a); break;
-        case 6: k_rows<R, 3, false><<<grid, threads, smem, s>>>(a); break;
-        case 7: k_rows<R, 3, true><<<grid, threads, smem, s>>>(a); break;
-        default:
-            if (pd) k_rows<R, Mmax, true><<<grid, threads, smem, s>>>(a);
-            else k_rows<R, Mmax, false><<<grid, threads, smem, s>>>(a);
-            break;
-        }
+        void *args[] = {(void *)&a};
+        e = cudaLaunchKernel(kfn, dim3((unsigned)grid), dim3((unsigned)threads), args, smem, s);
+        if (e != cudaSuccess) return e;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -320,7 +342,8 @@ cudaError_t rows_launch(const RowProgram &rp, const Plan &p, const void *coef, c
 #define DQ_INST(R)                                                                                          \
     template cudaError_t rows_launch<R>(const RowProgram &, const Plan &, const void *, const void *, int,  \
                                         const DevTerm *, int, int, const double *, int, void *, double *,   \
-                                        double *, double *, double *, int, size_t, cudaStream_t, int64_t *, bool);
+                                        double *, double *, double *, int, size_t, cudaStream_t, int64_t *, bool, \
+                                        int);
 DQ_INST(float)
 DQ_INST(double)
 #undef DQ_INST

@@ -302,3 +302,54 @@ def test_compiled_program_cache(tmp_path):
     assert "k_rows_jit" in first["names"] and "k_rows_jit" in second["names"], first["names"]
     assert len(files1) == 1 and files1[0].endswith(".cubin") and files2 == files1
     assert first["e"] == second["e"] and first["g"] == second["g"]
+
+
+@pytest.mark.parametrize("jit", [0, 1])
+def test_two_rows_per_cta(jit):
+    """DQ_OPT_ROWS_PER_CTA = 2: the CTA's two halves run two rows of the
+    whole-row kernel in step (interpreting or specialised), a ragged batch
+    leaves the last CTA's second half without a row; expectations, shared and
+    per-row gradients and the states against the oracle and against one row
+    per CTA."""
+    n, batch = 10, 37
+    rng = np.random.default_rng(2100 + jit)
+    gates, npar = random_gates(n, 6 * n, rng, nfeat=2)
+    gates += [W.Gate("rzz", (2, 7), angle=0.6), W.Gate("swap", (0, n - 1))]
+    params = rng.uniform(-4, 4, npar)
+    data = rng.uniform(-3, 3, size=(batch, 2))
+    obs = [W.obs_tfim_open(n, 0.5), [(0.7, 1, (1 << n) - 1), (-0.4, 0, 1)]]
+    w = rng.normal(size=(batch, 2))
+    circ = dq.Circuit(n, gates, nparams=npar, nfeatures=2)
+    ctx = dq.Context(0)
+    ctx.set_path(dq.PATH_FUSED)
+    ctx.set_option(dq.OPT_JIT, jit)
+    out = {}
+    try:
+        for rpc in (2, 1):
+            ctx.set_option(dq.OPT_ROWS_PER_CTA, rpc)
+            st = torch.empty((batch, 1 << n), dtype=torch.complex64, device="cuda")
+            ctx.set_tracing(True)
+            e, gp, gd, _ = ctx.forward_grad(circ, dev(params), dq.Observables(obs), batch, torch.complex64,
+                                            data=dev(data), row_weights=dev(w), state_out=st)
+            torch.cuda.synchronize()
+            names = set(ctx.trace())
+            ctx.set_tracing(False)
+            ctx.check()
+            assert ("k_rows_jit" if jit else "k_rows") in names, names
+            out[rpc] = (st, e, gp, gd)
+        st, e, gp, gd = out[2]
+        ref = oracle.run(n, gates, params, data, batch=batch)
+        assert_amps(np_state(st), ref, torch.complex64, "two rows per CTA")
+        e_ref, gp_ref, gd_ref = oracle.adjoint(n, gates, obs, params, data, batch=batch, row_weights=w)
+        gscale = float(np.abs(w).max(axis=1).sum()) * obs_scale(obs)
+        assert_rel(e.cpu().numpy(), e_ref, torch.complex64, "expectations (two rows per CTA)", zero_scale=obs_scale(obs))
+        assert_rel(gp.cpu().numpy(), gp_ref, torch.complex64, "grad params (two rows per CTA)", zero_scale=gscale)
+        assert_rel(gd.cpu().numpy(), gd_ref, torch.complex64, "grad data (two rows per CTA)", zero_scale=gscale)
+        # the same rows as one row per CTA (only the FP64 fold order of the shared sums differs)
+        assert torch.equal(out[2][0], out[1][0]) and torch.equal(out[2][1], out[1][1])
+        assert torch.equal(out[2][3], out[1][3])
+        assert float((out[2][2] - out[1][2]).abs().max()) <= 1e-12 * max(1.0, float(out[1][2].abs().max()))
+        with pytest.raises(dq.DQError):
+            ctx.set_option(dq.OPT_ROWS_PER_CTA, 3)
+    finally:
+        ctx.close()
