@@ -1108,6 +1108,14 @@ def profile_case(args):
         data = torch.tensor(wl.data, device=dev)
         for _ in range(iters):
             ctx.forward_grad(circ, params, obs, wl.batch, torch.complex64, data=data)
+    elif args.profile_case == "c4":          # uneven batch: 1024 circuits of 8..16 qubits, fwd + adjoint
+        circs = W.config_c4(1024)
+        dcs = [dq.Circuit(n, g, nparams=len(a)) for n, g, a in circs]
+        params = torch.tensor(np.concatenate([a for _, _, a in circs]), device=dev)
+        obs = dq.Observables([W.obs_zz01_x0()])
+        ctx.set_path(dq.PATH_FUSED)
+        for _ in range(iters):
+            ctx.batch_forward_grad(dcs, params, obs, torch.complex64)
     elif args.profile_case == "sweep":       # one-qubit sweeps on a 2 GiB state
         n = 28
         ctx.set_path(dq.PATH_PLAIN)
@@ -1168,7 +1176,7 @@ def main():
     ap.add_argument("--tile", default="", help="profile case c2: pin the tile shape k,low,M (specialised passes)")
     ap.add_argument("--traffic-fingerprint", action="store_true",
                     help="print the source fingerprint of each kernel with a recorded DRAM traffic figure")
-    ap.add_argument("--profile-case", choices=["c2", "tile", "wsv", "sweep", "c5", "dense", "sample", "hessian"],
+    ap.add_argument("--profile-case", choices=["c2", "tile", "wsv", "c4", "sweep", "c5", "dense", "sample", "hessian"],
                     default=None,
                     help="run one kernel family's workload for profiling and exit")
     args = ap.parse_args()
