@@ -999,7 +999,7 @@ def uneven_batch(ctx, device, steps=3):
         out[name] = {"ms_per_step": ms, "circuits_per_s": len(circs) / (ms / 1e3)}
     ctx.set_path(dq.PATH_AUTO)
     out["fused"]["tuned_launch"] = {"qubits_in_shared_memory": tuned[0], "threads_per_circuit": tuned[1],
-                                    "ctas_per_sm": tuned[2]}
+                                    "ctas_per_sm": tuned[2], "scratch_mib_in_flight": tuned[3]}
     out["speedup"] = out["plain"]["ms_per_step"] / out["fused"]["ms_per_step"]
     out["workload"] = "c4_uneven1024_c64"
     return out

@@ -402,17 +402,19 @@ DQ_API dq_status dq_batch_forward_grad(dq_ctx *ctx, int ncirc, const dq_circuit 
                                 double *expect_out, double *grad_params,
                                 void *stream);
 
-/* Autotuner of the uneven-batch launch (the benchmark spec's batched encoded-input
- * circuits of uneven qubit counts and depths; the API Overview batches
- * encode=True circuits).  Runs dq_batch_forward_grad with every candidate
- * launch configuration -- the largest qubit count kept in shared memory
- * (10, 11, 12; larger circuits work in per-CTA L2 scratch), threads per
- * circuit (128, 256, 512), CTAs per SM (2, 4, 8) -- on the caller's own
- * inputs, keeps the fastest for this batch structure and dtype (later
+/* Autotuner of the uneven-batch launch (batches of circuits of uneven qubit
+ * counts and depths; the API Overview batches encode=True circuits).  Runs
+ * dq_batch_forward_grad with every candidate launch configuration -- the
+ * largest qubit count kept in shared memory (10, 11, 12; larger circuits
+ * work in per-CTA scratch in global memory), threads per circuit (128, 256,
+ * 512), CTAs per SM (2, 4, 8), and the scratch in flight at once (0, 64, 96,
+ * 128, 160 MiB: only as many CTAs take the larger circuits as keep their
+ * scratch within it, so it stays in L2; 0: every CTA) -- on the caller's own inputs,
+ * keeps the fastest for this batch structure and dtype (later
  * dq_batch_forward_grad calls of the same structure use it), and leaves the
- * outputs as that configuration computes them.  choice (host, may be NULL)
- * receives {qubits in shared memory, threads, CTAs per SM}.  Synchronises
- * the stream; arguments as dq_batch_forward_grad. */
+ * outputs as that configuration computes them.  choice (host, 4 ints, may be
+ * NULL) receives {qubits in shared memory, threads, CTAs per SM, scratch
+ * MiB}.  Synchronises the stream; arguments as dq_batch_forward_grad. */
 DQ_API dq_status dq_batch_autotune(dq_ctx *ctx, int ncirc, const dq_circuit *circuits,
                                    const double *params, const int64_t *param_offsets,
                                    const dq_observables *obs, int dtype, double *expect_out,

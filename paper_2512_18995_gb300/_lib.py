@@ -730,8 +730,9 @@ class Context:
     def batch_autotune(self, circuits: Sequence[Circuit], params: torch.Tensor, obs: Observables,
                        dtype: torch.dtype = torch.complex64):
         """dq_batch_autotune: tune the uneven-batch launch for this batch;
-        returns (qubits in shared memory, threads per circuit, CTAs per SM)."""
-        choice = (ctypes.c_int * 3)()
+        returns (qubits in shared memory, threads per circuit, CTAs per SM,
+        MiB of scratch in flight for the larger circuits, 0: every CTA)."""
+        choice = (ctypes.c_int * 4)()
         self.batch_forward_grad(circuits, params, obs, dtype, _tune_choice=choice)
         return tuple(int(x) for x in choice)
 

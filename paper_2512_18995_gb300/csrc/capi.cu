@@ -2438,15 +2438,18 @@ dq_status dq_batch_autotune(dq_ctx *ctx, int ncirc, const dq_circuit *circuits, 
     std::vector<BatchTune> cand;
     for (int nsmem : {10, 11, 12})
         for (int threads : {128, 256, 512})
-            for (int per_sm : {2, 4, 8}) {
-                if (c128 && nsmem > 11) continue;
-                if (per_sm > batch_max_per_sm(bd->nmax)) continue;
-                BatchTune t;
-                t.nsmem = nsmem;
-                t.threads = threads;
-                t.per_sm = per_sm;
-                cand.push_back(t);
-            }
+            for (int per_sm : {2, 4, 8})
+                for (int l2_mb : {0, 64, 96, 128, 160}) {
+                    if (c128 && nsmem > 11) continue;
+                    if (per_sm > batch_max_per_sm(bd->nmax)) continue;
+                    if (l2_mb && bd->nmax <= nsmem) continue;   // no circuit runs on scratch
+                    BatchTune t;
+                    t.nsmem = nsmem;
+                    t.threads = threads;
+                    t.per_sm = per_sm;
+                    t.l2_mb = l2_mb;
+                    cand.push_back(t);
+                }
     cudaEvent_t e0, e1;
     DQ_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -2487,6 +2490,7 @@ dq_status dq_batch_autotune(dq_ctx *ctx, int ncirc, const dq_circuit *circuits, 
         choice[0] = bt.nsmem;
         choice[1] = bt.threads;
         choice[2] = bt.per_sm;
+        choice[3] = bt.l2_mb;
     }
     // leave the caller's outputs as the chosen configuration computes them
     return batch_launch(ctx, bd, o, params, param_offsets[ncirc], dtype, expect_out, grad_params, bt, s);

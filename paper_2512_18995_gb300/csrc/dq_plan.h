@@ -192,6 +192,7 @@ struct BatchTune {
     int nsmem = 0;       // circuits with at most this many qubits run in shared memory, larger ones in L2 scratch
     int threads = 0;     // threads per circuit (power of two, 64 .. 512)
     int per_sm = 0;      // CTAs per SM at most (1 .. kBatchMaxPerSm)
+    int l2_mb = 0;       // scratch of the circuits in global memory in flight at once, MiB (0: every CTA)
 };
 constexpr int kBatchMaxPerSm = 8;   // L2 scratch slices per SM (circuits of up to 16 qubits; 4 above)
 inline int batch_max_per_sm(int nmax) { return nmax <= 16 ? kBatchMaxPerSm : 4; }

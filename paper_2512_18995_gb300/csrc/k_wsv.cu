@@ -17,7 +17,8 @@
 // k_batch: an uneven batch of independent circuits in one persistent launch.
 // CTAs take circuits from an atomic ticket counter in longest-first order;
 // circuits whose two vectors fit in the CTA's shared memory run there, larger
-// ones run on a per-CTA scratch slice of global memory (L2-resident).
+// ones run on a per-CTA scratch slice of global memory, taken only by as many
+// CTAs as keep the scratch in flight within a budget that fits in L2.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -331,8 +332,9 @@ struct BatchArgs {
     int maxparams;
     double *expect_out;
     double *grad_params;
-    void *scratch;          // [gridDim.x][2 * 2^nmax] amplitudes
-    int *counter;
+    void *scratch;          // [lcap][2 * 2^nmax] amplitudes
+    int lcap;               // CTAs that take circuits larger than nsmem (their scratch fits in L2)
+    int *counter;           // [2]: tickets of the scratch queue and of the shared-memory queue
 };
 
 template <typename R>
@@ -350,13 +352,36 @@ __global__ void __launch_bounds__(kMaxThreads) k_batch(BatchArgs a) {
     cx<R> *gpsi = (cx<R> *)a.scratch + (int64_t)blockIdx.x * 2 * gdim;
     cx<R> *glam = gpsi + gdim;
     const Mat2<R> *coef = (const Mat2<R> *)a.coef;
+    // Two queues over the same longest-first order: circuits larger than
+    // nsmem (scratch in global memory) go only to the first lcap CTAs, so that
+    // the scratch in use stays L2-resident; those CTAs then join the others on
+    // the shared-memory circuits.  A queue's ticket that lands on the other
+    // kind of circuit is skipped, so every circuit runs once.
+    int queue = blockIdx.x < a.lcap ? 0 : 1;   // thread 0's
     for (;;) {
-        if (tid == 0) *ticket = atomicAdd(a.counter, 1);
+        if (tid == 0) {
+            int c = -1;
+            for (;;) {
+                const int idx = atomicAdd(&a.counter[queue], 1);
+                if (idx >= a.ncirc) {
+                    if (queue == 0) {
+                        queue = 1;
+                        continue;
+                    }
+                    break;
+                }
+                const int cand = a.order[idx];
+                if ((a.circ[cand].n > a.nsmem) == (queue == 0)) {
+                    c = cand;
+                    break;
+                }
+            }
+            *ticket = c;
+        }
         __syncthreads();
-        const int idx = *ticket;
+        const int c = *ticket;
         __syncthreads();
-        if (idx >= a.ncirc) break;
-        const int c = a.order[idx];
+        if (c < 0) break;
         const BatchCirc bc = a.circ[c];
         for (int i = tid; i < bc.nparams; i += blockDim.x) acc[i] = 0.0;
         __syncthreads();
@@ -461,12 +486,16 @@ size_t batch_scratch_bytes(int nmax, int amp_bytes, int nsm, size_t smem_optin) 
 
 // Defaults of the persistent uneven-batch launch: circuits up to 12 qubits
 // (complex64; 11 for complex128) in shared memory, 512 threads per circuit,
-// at most four CTAs per SM.
+// at most four CTAs per SM, 128 MiB of scratch in flight for the larger
+// circuits (measured on the 1024-circuit 8..16-qubit batch with these
+// defaults: 0 (every CTA) 3.20 ms, 32 MiB 7.08, 64 MiB 3.75, 96 MiB 2.79,
+// 128 MiB 2.52, 160 MiB 2.77).
 BatchTune batch_default_tune(int amp_bytes) {
     BatchTune t;
     t.nsmem = amp_bytes == 8 ? 12 : 11;
     t.threads = kMaxThreads;
     t.per_sm = 4;
+    t.l2_mb = 128;
     return t;
 }
 
@@ -477,7 +506,7 @@ cudaError_t batch_run(const BatchCirc *d_circ, int ncirc, const int32_t *d_order
                       void *scratch, int *d_counter, int nsm, size_t smem_optin, const BatchTune &tune,
                       cudaStream_t s, int64_t *launches) {
     if (tune.threads < 64 || tune.threads > kMaxThreads || (tune.threads & (tune.threads - 1)) ||
-        tune.per_sm < 1 || tune.per_sm > batch_max_per_sm(nmax) || tune.nsmem < 2)
+        tune.per_sm < 1 || tune.per_sm > batch_max_per_sm(nmax) || tune.nsmem < 2 || tune.l2_mb < 0)
         return cudaErrorInvalidValue;
     BatchArgs a;
     a.circ = d_circ;
@@ -507,7 +536,12 @@ cudaError_t batch_run(const BatchCirc *d_circ, int ncirc, const int32_t *d_order
         per_sm = 1;
     per_sm = std::min(per_sm, tune.per_sm);   // scratch holds kBatchMaxPerSm slices per SM
     const int grid = std::max(1, std::min(ncirc, per_sm * nsm));
-    e = cudaMemsetAsync(d_counter, 0, sizeof(int), s);
+    // CTAs allowed on scratch circuits: the budget of tune.l2_mb MiB of
+    // scratch (two vectors of 2^nmax amplitudes each), all CTAs when 0
+    const size_t slice = 2 * ((size_t)sizeof(cx<R>) << nmax);
+    a.lcap = tune.l2_mb > 0 ? (int)std::max<size_t>(1, std::min<size_t>(grid, ((size_t)tune.l2_mb << 20) / slice))
+                            : grid;
+    e = cudaMemsetAsync(d_counter, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     LaunchScope ls(s, "k_batch", launches);
     k_batch<R><<<grid, threads, smem, s>>>(a);

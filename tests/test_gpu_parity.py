@@ -381,6 +381,7 @@ def test_config_c4_autotuned_launch(ctx, dtype):
     offs = np.cumsum([0] + [len(a) for _, _, a in circs])
     choice = ctx.batch_autotune(dcs, dev(params), dq.Observables(obs), dt)
     assert choice[0] in (10, 11, 12) and choice[1] in (128, 256, 512) and choice[2] in (2, 4, 8), choice
+    assert choice[3] in (0, 64, 96, 128, 160), choice
     e, gp = ctx.batch_forward_grad(dcs, dev(params), dq.Observables(obs), dt)
     e = e.cpu().numpy()
     gp = gp.cpu().numpy()
