@@ -773,8 +773,9 @@ def trotter30(ctx, device, steps=5):
 def sample30(ctx, device, hbm_peak, peak_kind, n=30, shots=1 << 20, reps=3):
     """2^20 shots from a 30-qubit complex64 state (8 GiB): one streaming pass
     for the cumulative sums, then per shot a search over group prefixes, a
-    scan of up to 1024 chunk sums and of one 256-amplitude chunk.  Algorithmic
-    HBM bytes: the state once plus 2 KiB of amplitudes per shot."""
+    search of up to 1024 chunk prefixes and a scan of one 32-amplitude chunk.
+    Algorithmic HBM bytes: the state once, the chunk prefixes written (8 B per
+    32 amplitudes) and 256 B of amplitudes per shot."""
     import torch
     try:
         gen = torch.Generator(device=device).manual_seed(30)
@@ -792,7 +793,7 @@ def sample30(ctx, device, hbm_peak, peak_kind, n=30, shots=1 << 20, reps=3):
     except RuntimeError as exc:
         return {"skipped": str(exc)[:120]}
     ms = a.elapsed_time(b) / reps
-    nbytes = (8 << n) + shots * 256 * 8
+    nbytes = (8 << n) + (8 << (n - 5)) + shots * 32 * 8
     ctx.set_tracing(True)
     ctx.sample(n, st, shots, seed=9, out=out)
     kernels = {k: round(v[1], 3) for k, v in ctx.trace().items()}

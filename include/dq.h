@@ -571,8 +571,10 @@ DQ_API dq_status dq_hessian(dq_ctx *ctx, const dq_circuit *circuit, const double
  *              those wires).  Bits at or above nqubits are invalid.
  *   out:       device int64, batch * shots outcomes.
  * Uses sample_workspace_bytes of workspace (dq_sample_workspace_bytes); the
- * state is streamed once, then each shot reads 2^8 amplitudes and up to 2^10
- * partial sums.  A row of zeros returns 2^nqubits - 1. */
+ * state is streamed once, then each shot reads 2^5 amplitudes and a few
+ * partial sums.  A row of zeros returns 2^nqubits - 1.  For complex64 states
+ * a uniform below 2^-126 (or negative) acts as 0 and one of 1 or more (or
+ * NaN) as 1. */
 DQ_API dq_status dq_sample_workspace_bytes(dq_ctx *ctx, int nqubits, int batch, size_t *out);
 DQ_API dq_status dq_sample(dq_ctx *ctx, int nqubits, const void *state, int batch, int dtype,
                            int64_t shots, const double *uniforms, uint64_t seed,
