@@ -427,6 +427,7 @@ class Context:
             raise DQError(st, f"dq_ctx_create(device={device}) failed")
         self.h = h
         self._ws = None
+        self._batch_arrays = None
         self.set_path(path)
 
     def close(self):
@@ -434,6 +435,7 @@ class Context:
             self.lib.dq_ctx_destroy(self.h)
             self.h = None
             self._ws = None
+            self._batch_arrays = None
 
     def __del__(self):
         try:
@@ -741,11 +743,18 @@ class Context:
                            expect_out: Optional[torch.Tensor] = None, grad_params: Optional[torch.Tensor] = None,
                            _tune_choice=None):
         nc = len(circuits)
-        arr = (dq_circuit * max(1, nc))()
-        offs = (ctypes.c_int64 * (nc + 1))()
-        for i, c in enumerate(circuits):
-            arr[i] = c.c
-            offs[i + 1] = offs[i] + c.nparams
+        # the C arrays of the batch, reused while the call passes the same
+        # Circuit objects in the same order (held here, so their ids stay theirs)
+        cached = self._batch_arrays
+        if cached is not None and len(cached[0]) == nc and all(a is b for a, b in zip(cached[0], circuits)):
+            arr, offs = cached[1], cached[2]
+        else:
+            arr = (dq_circuit * max(1, nc))()
+            offs = (ctypes.c_int64 * (nc + 1))()
+            for i, c in enumerate(circuits):
+                arr[i] = c.c
+                offs[i + 1] = offs[i] + c.nparams
+            self._batch_arrays = (tuple(circuits), arr, offs)
         dev = torch.device(f"cuda:{self.device}")
         params = _f64_in(params, int(offs[nc]), "params", self.device)
         expect_out = _out(expect_out, nc * obs.nobs, torch.float64, "expect_out", self.device)
