@@ -387,6 +387,27 @@ DQ_API dq_status dq_forward_grad(dq_ctx *ctx, const dq_circuit *circuit,
                           double *expect_out, double *grad_params,
                           double *grad_data, void *state_out, void *stream);
 
+/* The forward path with host buffers, for callers that hold their inputs
+ * and want their results in host memory (Sec. "Quantum Computing with
+ * Qubits", API Overview: a parameterised circuit run to expectation values).
+ *   params:     host FP64, the circuit's nparams shared parameters (NULL
+ *               when nparams == 0); read during the call.
+ *   expect_out: host FP64, batch * nobs expectations, written before the
+ *               call returns (may be NULL when batch == 0).
+ * The call copies params to the device, prepares |0...0> for every row,
+ * runs the circuit and the expectations as dq_forward_grad does, copies the
+ * expectations back and synchronises `stream`.  With graphs on
+ * (dq_ctx_set_graphs) and both buffers in pinned host memory (cudaHostAlloc
+ * or cudaHostRegister), the two copies and the kernels of a repeated call
+ * are one CUDA graph replay; pageable buffers work, with the copies issued
+ * one by one.  Circuits with encoded data (data_idx gates) return
+ * DQ_ERR_UNSUPPORTED: use dq_forward_grad.  The device copies live in a
+ * context-owned buffer (grown with cudaMalloc when a call needs more,
+ * DQ_ERR_OOM if that fails); the rest uses the context workspace. */
+DQ_API dq_status dq_forward_host(dq_ctx *ctx, const dq_circuit *circuit, const double *params,
+                                 const dq_observables *obs, int batch, int dtype, double *expect_out,
+                                 void *stream);
+
 /* Uneven batch: ncirc independent circuits (own qubit count, depth and
  * parameters) run to expectations and per-circuit adjoint gradients in one
  * persistent launch.  circuits: host array.  params: device FP64, circuit c's

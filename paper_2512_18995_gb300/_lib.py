@@ -75,7 +75,8 @@ EXPORTS = ("dq_ctx_create", "dq_ctx_destroy", "dq_last_error", "dq_ctx_set_path"
            "dq_ctx_set_workspace",
            "dq_workspace_bytes", "dq_batch_workspace_bytes", "dq_ctx_check", "dq_ctx_launch_count", "dq_ctx_set_graphs", "dq_ctx_set_tracing",
            "dq_ctx_trace_count", "dq_ctx_trace_get", "dq_state_init", "dq_apply_circuit",
-           "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_batch_forward_grad", "dq_plan_autotune",
+           "dq_expect", "dq_adjoint_grad", "dq_forward_grad", "dq_forward_host", "dq_batch_forward_grad",
+           "dq_plan_autotune",
            "dq_forward_grad_noalloc", "dq_apply_dense", "dq_sample_workspace_bytes", "dq_sample",
            "dq_hessian", "dq_density_workspace_bytes", "dq_density_forward",
            "dq_density_grad", "dq_plan_tuned", "dq_lower_circuit", "dq_tile_schedule", "dq_row_program",
@@ -125,6 +126,7 @@ def load_library(path: str = LIB_PATH):
         "dq_expect": ([P, I, O, P, I, I, P, P], I),
         "dq_adjoint_grad": ([P, C, P, I, P, O, P, P, I, I, I, P, P, P], I),
         "dq_forward_grad": ([P, C, P, I, P, O, P, I, I, P, P, P, P, P], I),
+        "dq_forward_host": ([P, C, P, O, I, I, P, P], I),
         "dq_batch_forward_grad": ([P, I, C, P, ctypes.POINTER(ctypes.c_int64), O, I, P, P, P], I),
         "dq_plan_autotune": ([P, C, I, I, P, P], I),
         "dq_forward_grad_noalloc": ([C, P, I, P, O, P, I, I, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t], I),
@@ -728,6 +730,28 @@ class Context:
                                              dt, _ptr(expect_out), _ptr(grad_params), _ptr(grad_data),
                                              _ptr(state_out), _stream()), "dq_forward_grad")
         return expect_out, grad_params, grad_data, state_out
+
+    def forward_host(self, circuit: Circuit, params: Optional[torch.Tensor], obs: Observables, batch: int,
+                     dtype: torch.dtype = torch.complex64, expect_out: Optional[torch.Tensor] = None):
+        """dq_forward_host: the forward path with host buffers.  params and
+        expect_out are CPU float64 tensors (pinned ones let the copies join
+        the call's CUDA graph); returns expect_out, filled when the call
+        returns."""
+        def host(t, count, what):
+            if not isinstance(t, torch.Tensor) or t.device.type != "cpu" or t.dtype != torch.float64 \
+                    or not t.is_contiguous() or t.numel() < count:
+                _bad(f"{what} must be a contiguous CPU float64 tensor of at least {count} values")
+            return t
+        if params is not None:
+            params = host(params, circuit.nparams, "params")
+        if expect_out is None:
+            expect_out = torch.empty((batch, obs.nobs), dtype=torch.float64).pin_memory()
+        expect_out = host(expect_out, batch * obs.nobs, "expect_out")
+        dt = dtype_code(dtype)
+        self.ensure_workspace(circuit, obs, batch, dt)
+        self._check(self.lib.dq_forward_host(self.h, circuit.ref(), _ptr(params), obs.ref(), int(batch), dt,
+                                             _ptr(expect_out), _stream()), "dq_forward_host")
+        return expect_out
 
     def batch_autotune(self, circuits: Sequence[Circuit], params: torch.Tensor, obs: Observables,
                        dtype: torch.dtype = torch.complex64):

@@ -102,6 +102,7 @@ def test_null_context_is_rejected(libdq):
     c = _lib.Circuit(2, [W.Gate("h", (0,))])
     st = libdq.dq_apply_circuit(None, c.ref(), None, 0, None, None, 1, 0, None)
     assert st == 1   # DQ_ERR_INVALID_ARG
+    assert libdq.dq_forward_host(None, c.ref(), None, None, 1, 0, None, None) == 1
 
 
 
