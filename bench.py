@@ -494,7 +494,8 @@ def kernel_bytes(n, gates, passes, amp=8):
     multi-pass kernel does so once per pass, the state preparation writes it
     once, a per-gate expectation pass reads it once."""
     full = (1 << n) * amp
-    out = {"k_tile_fwd": 2 * full, "k_tile_fwd_jit": 2 * full, "k_init_zero": full, "k_expect": full}
+    out = {"k_tile_fwd": 2 * full, "k_tile_fwd_jit": 2 * full, "k_init_zero": full, "k_bind_init": full,
+           "k_expect": full}
     if passes:
         out["k_tile_multi"] = 2 * full * passes
     return out

@@ -1312,13 +1312,17 @@ dq_status forward_grad_impl(dq_ctx *ctx, Plan &p, ObsDev *o, const double *param
     void *tws = tile ? w.take(tile_workspace_bytes(p, batch, (int)sizeof(cx<R>))) : nullptr;
     void *ubuf = dense ? w.take(kDenseUnitaryBytes) : nullptr;
     void *image = dense ? w.take(dense_image_bytes()) : nullptr;
-    DQ_CUDA(bind_coef<R>(ctx, p, params, data, batch, coef, s), "bind");
-    DQ_CUDA(plain_init_zero<R>(psi, p.n, batch, s, &ctx->launches), "init");
+    // the last forward pass measures diagonal observables itself; its partial
+    // sums are cleared by the launch that binds the gates and prepares |0...0>
+    const bool epi = tile && o && eo && !grad && !dense;
+    const int64_t nzero =
+        epi ? (int64_t)(tile_expect_part_bytes(p.n, (int)o->bits.size(), batch, ctx->nsm) / sizeof(double)) : 0;
+    DQ_CUDA(plain_bind_init<R>(p, params, data, batch, coef, psi, epi ? epart : nullptr, nzero, s, &ctx->launches),
+            "bind and init");
     bool done_obs = false, done_grad = false;
-    if (tile && o && eo && !grad && !dense) {
-        // diagonal observables measured by the last forward pass itself
+    if (epi) {
         cudaError_t e = tile_apply_expect<R>(ctx->tiles, ctx->tuned, p, coef, psi, batch, o->bits, o->d_bits,
-                                             o->d_ptr, o->nobs, epart, eo, ctx->nsm, s, &ctx->launches);
+                                             o->d_ptr, o->nobs, epart, eo, ctx->nsm, s, &ctx->launches, true);
         if (e == cudaSuccess) done_obs = true;
         else if (e != cudaErrorNotSupported) DQ_CUDA(e, "tiled apply with expectations");
         else cudaGetLastError();

@@ -126,6 +126,11 @@ cudaError_t plain_bind(const Plan &p, const double *params, const double *data, 
                        void *coef, cudaStream_t s, int64_t *launches);
 template <typename R>
 cudaError_t plain_init_zero(void *state, int n, int batch, cudaStream_t s, int64_t *launches);
+// plain_bind, the clearing of nzero doubles at `zero` (may be NULL) and
+// plain_init_zero of `state` (p.n qubits), in one launch
+template <typename R>
+cudaError_t plain_bind_init(const Plan &p, const double *params, const double *data, int batch, void *coef,
+                            void *state, double *zero, int64_t nzero, cudaStream_t s, int64_t *launches);
 template <typename R>
 cudaError_t plain_apply(const Plan &p, const void *coef, void *state, int batch, int dagger,
                         cudaStream_t s, int64_t *launches);

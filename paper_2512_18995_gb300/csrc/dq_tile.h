@@ -145,7 +145,7 @@ template <typename R>
 cudaError_t tile_apply_expect(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
                               const void *coef, void *state, int batch, const std::vector<DevTerm> &bits,
                               const DevTerm *d_bits, const int32_t *d_ptr, int nobs, double *part, double *out,
-                              int nsm, cudaStream_t s, int64_t *launches);
+                              int nsm, cudaStream_t s, int64_t *launches, bool part_zeroed = false);
 template <typename R>
 cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
                           const void *coef, void *state, int batch, void *tws, int nsm, cudaStream_t s,

@@ -74,6 +74,26 @@ __device__ __forceinline__ uint64_t unit_of(const UnitMap &m, uint64_t j) {
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
+// The 2x2 block of gate record bg for row r.
+template <typename R>
+__device__ __forceinline__ void bind_one(const BindGate &bg, int r, const double *__restrict__ params, int nparams,
+                                         int ppr, const double *__restrict__ data, int nfeat,
+                                         const Mat2<double> *__restrict__ fixed, Mat2<R> *__restrict__ coef) {
+    Mat2<R> m;
+    if (bg.aux >> 1) {   // a fixed block from the plan's table
+        const Mat2<double> &f = fixed[(bg.aux >> 1) - 1];
+        for (int i = 0; i < 4; ++i) m.m[i] = mk<R>((R)f.m[i].x, (R)f.m[i].y);
+    } else {
+        double t = bg.angle;
+        if (bg.pidx >= 0) t = ppr ? params[(int64_t)r * nparams + bg.pidx] : params[bg.pidx];
+        else if (bg.didx >= 0) t = data[(int64_t)r * nfeat + bg.didx];
+        m = gate_matrix<R>(bg.kind, t);
+    }
+    if (bg.aux & 1)
+        for (int i = 0; i < 4; ++i) m.m[i] = cconj(m.m[i]);
+    coef[bg.coef + (int64_t)r * bg.rowstep] = m;
+}
+
 template <typename R>
 __global__ void k_bind(const BindGate *__restrict__ g, int ngates, const double *__restrict__ params,
                        int nparams, int ppr, const double *__restrict__ data, int nfeat,
@@ -81,22 +101,43 @@ __global__ void k_bind(const BindGate *__restrict__ g, int ngates, const double 
     for (int gi = blockIdx.y; gi < ngates; gi += gridDim.y) {
         const BindGate bg = g[gi];
         const int rows = bg.rowstep ? batch : 1;
-        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
-            Mat2<R> m;
-            if (bg.aux >> 1) {   // a fixed block from the plan's table
-                const Mat2<double> &f = fixed[(bg.aux >> 1) - 1];
-                for (int i = 0; i < 4; ++i) m.m[i] = mk<R>((R)f.m[i].x, (R)f.m[i].y);
-            } else {
-                double t = bg.angle;
-                if (bg.pidx >= 0) t = ppr ? params[(int64_t)r * nparams + bg.pidx] : params[bg.pidx];
-                else if (bg.didx >= 0) t = data[(int64_t)r * nfeat + bg.didx];
-                m = gate_matrix<R>(bg.kind, t);
-            }
-            if (bg.aux & 1)
-                for (int i = 0; i < 4; ++i) m.m[i] = cconj(m.m[i]);
-            coef[bg.coef + (int64_t)r * bg.rowstep] = m;
-        }
+        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x)
+            bind_one<R>(bg, r, params, nparams, ppr, data, nfeat, fixed, coef);
     }
+}
+
+// k_bind and the preparation of |0...0> in one launch, for calls that run
+// them back to back: the first `bind_blocks` blocks bind (item i = gate
+// i / rows, row i % rows, rows = the batch when some gate's block depends on
+// the row, else 1), the next `zero_blocks` clear `nzero` doubles (partial
+// sums that later kernels accumulate into), the others write the state as
+// k_init_zero does.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_bind_init(const BindGate *__restrict__ g, int ngates, const double *__restrict__ params, int nparams, int ppr,
+            const double *__restrict__ data, int nfeat, int batch, int rows, const Mat2<double> *__restrict__ fixed,
+            Mat2<R> *__restrict__ coef, int bind_blocks, double *__restrict__ zero, int64_t nzero, int zero_blocks,
+            cx<R> *__restrict__ st, int n, int64_t units) {
+    if ((int)blockIdx.x < bind_blocks) {
+        const int64_t items = (int64_t)ngates * rows;
+        for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < items; i += (int64_t)bind_blocks * kThreads) {
+            const int gi = (int)(i / rows), r = (int)(i - (int64_t)gi * rows);
+            const BindGate bg = g[gi];
+            if (r < (bg.rowstep ? batch : 1)) bind_one<R>(bg, r, params, nparams, ppr, data, nfeat, fixed, coef);
+        }
+        return;
+    }
+    if ((int)blockIdx.x < bind_blocks + zero_blocks) {
+        const int64_t i = (int64_t)(blockIdx.x - bind_blocks) * kThreads + threadIdx.x;
+        if (i < nzero) zero[i] = 0.0;
+        return;
+    }
+    const int64_t i = (int64_t)(blockIdx.x - bind_blocks - zero_blocks) * kThreads + threadIdx.x;
+    if (i >= units) return;
+    Unit<R> u;
+    u.a = mk<R>(((i << 1) & ((int64_t(1) << n) - 1)) == 0 ? R(1) : R(0), R(0));
+    u.b = mk<R>(R(0), R(0));
+    stu(st + 2 * i, u);
 }
 
 template <typename R>
@@ -265,6 +306,9 @@ k_expect(const cx<R> *__restrict__ st, int n, uint64_t f, int lf, TermPack tp, i
 __global__ void k_expect_finalize(const double *__restrict__ part, const DevTerm *__restrict__ terms,
                                   const int32_t *__restrict__ obs_ptr, int nobs, int nbatch, int nblk,
                                   double *__restrict__ out) {
+    // launched as a programmatic dependent of the kernel that writes `part`
+    // (a no-op otherwise): wait for it to complete before reading
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     __shared__ double red[kThreads / 32];
     const int row = blockIdx.x / nobs, o = blockIdx.x % nobs;
     const int k0 = obs_ptr[o], k1 = obs_ptr[o + 1];
@@ -440,6 +484,28 @@ cudaError_t plain_bind(const Plan &p, const double *params, const double *data, 
 }
 
 template <typename R>
+cudaError_t plain_bind_init(const Plan &p, const double *params, const double *data, int batch, void *coef,
+                            void *state, double *zero, int64_t nzero, cudaStream_t s, int64_t *launches) {
+    if (p.n == 0) return cudaErrorInvalidValue;
+    const int rows = p.ncoef_rows ? batch : 1;
+    const int64_t items = (int64_t)p.ngates * rows;
+    const int bind_blocks = (int)std::min<int64_t>(cdiv(items, kThreads), 4096);
+    const int64_t zb = zero ? cdiv(nzero, kThreads) : 0;
+    const int64_t units = (int64_t)batch << (p.n - 1);
+    const int64_t blocks = bind_blocks + zb + cdiv(units, kThreads);
+    if (blocks > INT32_MAX) {   // more than one launch's blocks: separate kernels
+        cudaError_t e = plain_bind<R>(p, params, data, batch, coef, s, launches);
+        if (e == cudaSuccess && zero && nzero) e = cudaMemsetAsync(zero, 0, (size_t)nzero * sizeof(double), s);
+        return e != cudaSuccess ? e : plain_init_zero<R>(state, p.n, batch, s, launches);
+    }
+    LaunchScope ls(s, "k_bind_init", launches);
+    k_bind_init<R><<<(unsigned)blocks, kThreads, 0, s>>>(p.d_bind, p.ngates, params, p.nparams, p.ppr, data, p.nfeat,
+                                                         batch, rows, p.d_fixed, (Mat2<R> *)coef, bind_blocks, zero,
+                                                         nzero, (int)zb, (cx<R> *)state, p.n, units);
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t plain_init_zero(void *state, int n, int batch, cudaStream_t s, int64_t *launches) {
     const int64_t units = (int64_t)batch << (n - 1);
     if (n == 0) return cudaErrorInvalidValue;
@@ -597,10 +663,20 @@ cudaError_t grad_reduce(const Plan &p, const double *part, int batch, int nblk, 
 
 cudaError_t expect_finalize_nblk(const double *part, const DevTerm *d_terms, const int32_t *d_obs_ptr, int nobs,
                                  int batch, int nblk, double *out, cudaStream_t s, int64_t *launches) {
+    // a programmatic dependent launch: its launch overlaps the tail of the
+    // forward pass that writes the partials (the kernel waits for it first)
     LaunchScope ls(s, "k_expect_finalize", launches);
-    k_expect_finalize<<<(unsigned)((int64_t)batch * nobs), kThreads, 0, s>>>(part, d_terms, d_obs_ptr, nobs, batch,
-                                                                            nblk, out);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)((int64_t)batch * nobs));
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_expect_finalize, part, d_terms, d_obs_ptr, nobs, batch, nblk, out);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // explicit instantiations
@@ -608,6 +684,8 @@ cudaError_t expect_finalize_nblk(const double *part, const DevTerm *d_terms, con
     template cudaError_t plain_bind<R>(const Plan &, const double *, const double *, int, void *,        \
                                        cudaStream_t, int64_t *);                                        \
     template cudaError_t plain_init_zero<R>(void *, int, int, cudaStream_t, int64_t *);                 \
+    template cudaError_t plain_bind_init<R>(const Plan &, const double *, const double *, int, void *, void *, \
+                                            double *, int64_t, cudaStream_t, int64_t *);                 \
     template cudaError_t plain_apply<R>(const Plan &, const void *, void *, int, int, cudaStream_t,      \
                                         int64_t *);                                                     \
     template cudaError_t plain_expect<R>(int, const std::vector<DevTerm> &, int, const void *, int,     \

@@ -964,7 +964,7 @@ template <typename R>
 cudaError_t tile_apply_expect(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
                               const void *coef, void *state, int batch, const std::vector<DevTerm> &bits,
                               const DevTerm *d_bits, const int32_t *d_ptr, int nobs, double *part, double *out,
-                              int nsm, cudaStream_t s, int64_t *launches) {
+                              int nsm, cudaStream_t s, int64_t *launches, bool part_zeroed) {
     if (!ensure_encode_fn(tc)) return cudaErrorNotSupported;
     for (const DevTerm &t : bits)
         if (t.f != 0 || t.nY != 0) return cudaErrorNotSupported;   // diagonal terms only
@@ -981,8 +981,11 @@ cudaError_t tile_apply_expect(TileCache &tc, std::unordered_map<uint64_t, TileTu
     TileSchedule *sc = get_schedule(tc, p, k, low, M, (int)sizeof(cx<R>), false);
     if (!sc || sc->passes.empty()) return cudaErrorNotSupported;
     const int nsm4 = 4 * nsm;
-    cudaError_t e = cudaMemsetAsync(part, 0, sizeof(double) * bits.size() * (size_t)batch * nsm4, s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!part_zeroed) {   // CTAs without a tile of a row leave its partial slots alone
+        e = cudaMemsetAsync(part, 0, sizeof(double) * bits.size() * (size_t)batch * nsm4, s);
+        if (e != cudaSuccess) return e;
+    }
     TileEpi epi{};
     epi.terms = d_bits;
     epi.nterms = (int)bits.size();
@@ -1089,7 +1092,7 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
     template cudaError_t tile_apply_expect<R>(TileCache &, std::unordered_map<uint64_t, TileTune> &,             \
                                               const Plan &, const void *, void *, int,                         \
                                               const std::vector<DevTerm> &, const DevTerm *, const int32_t *,  \
-                                              int, double *, double *, int, cudaStream_t, int64_t *);
+                                              int, double *, double *, int, cudaStream_t, int64_t *, bool);
 DQ_INST(float)
 DQ_INST(double)
 #undef DQ_INST
