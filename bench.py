@@ -324,9 +324,9 @@ def our_arm(args, rank, world, dist):
     state = torch.empty((1, 1 << n), dtype=torch.complex64, device=device)
     expect = torch.empty((1, 1), dtype=torch.float64, device=device)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
+    ctx.set_graphs(not args.no_graphs)   # before tuning: the tuner times the way the context runs
     if args.path != "plain":
         ctx.plan_autotune(circ, state)
-    ctx.set_graphs(not args.no_graphs)
 
     def step():
         ctx.forward_grad(circ, params, obs, 1, torch.complex64, want_grad=False, state_out=state, expect_out=expect)

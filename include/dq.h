@@ -606,7 +606,10 @@ DQ_API dq_status dq_sample(dq_ctx *ctx, int nqubits, const void *state, int batc
  * qubits, the interpreting against the specialised whole-row kernel; dense
  * blocks against tile passes) for this circuit shape on `state` (device,
  * batch rows, contents destroyed) and cache the fastest for later calls with
- * the same circuit structure.  Synchronises `stream`. */
+ * the same circuit structure.  With graphs on (dq_ctx_set_graphs) the
+ * specialised tile passes are timed as CUDA-graph replays, the way the
+ * context then runs repeated calls; call dq_ctx_set_graphs first.
+ * Synchronises `stream`. */
 DQ_API dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch,
                            int dtype, void *state, void *stream);
 

@@ -2690,11 +2690,13 @@ dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch, in
     cudaError_t e;
     if (dtype == DQ_C64) {
         e = bind_coef<float>(ctx, *p, zeros, zeros, batch, coef, s);
-        if (e == cudaSuccess && tiles) e = tile_autotune<float>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+        if (e == cudaSuccess && tiles) e = tile_autotune<float>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches,
+                                                               ctx->graphs_on);
         if (e == cudaSuccess && rp) e = rows_autotune<float>(ctx, *p, *rp, coef, state, batch, s);
     } else {
         e = bind_coef<double>(ctx, *p, zeros, zeros, batch, coef, s);
-        if (e == cudaSuccess && tiles) e = tile_autotune<double>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches);
+        if (e == cudaSuccess && tiles) e = tile_autotune<double>(ctx->tiles, ctx->tuned, *p, coef, state, batch, tws, ctx->nsm, s, &ctx->launches,
+                                                               ctx->graphs_on);
         if (e == cudaSuccess && rp) e = rows_autotune<double>(ctx, *p, *rp, coef, state, batch, s);
     }
     // Dense blocks (complex64): with the tuned tile shape, time the circuit

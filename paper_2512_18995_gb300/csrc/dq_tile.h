@@ -147,9 +147,11 @@ cudaError_t tile_apply_expect(TileCache &tc, std::unordered_map<uint64_t, TileTu
                               const DevTerm *d_bits, const int32_t *d_ptr, int nobs, double *part, double *out,
                               int nsm, cudaStream_t s, int64_t *launches, bool part_zeroed = false);
 template <typename R>
+// graphs: time the specialised candidates as CUDA-graph replays (the way a
+// context with graphs on runs repeated calls), else as stream launches.
 cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p,
                           const void *coef, void *state, int batch, void *tws, int nsm, cudaStream_t s,
-                          int64_t *launches);
+                          int64_t *launches, bool graphs = false);
 
 // g0: first gate of the circuit to schedule (adjoint sweeps that stop early).
 TileSchedule *get_schedule(TileCache &tc, const Plan &p, int k, int low, int M, int amp, bool adjoint, int g0 = 0);

@@ -78,21 +78,50 @@ __device__ __forceinline__ void tile_run_ops(cx<R> (&r)[1 << M], cx<R> *cur, con
 }
 
 // Diagonal (Z-string) observables of one finished tile: per-warp FP32 sums
-// of signed probabilities, folded into the CTA's FP64 accumulators.
-template <typename R>
+// of signed probabilities, folded into the CTA's FP64 accumulators.  The
+// CTA has 2^(k-M) threads and thread t reads tile amplitudes t + i 2^(k-M),
+// i < 2^M, so the sign of amplitude i under a term with tile-local mask s is
+// (-1)^(parity(t & s) + parity(i & (s >> (k-M)))): the thread's signed sum is
+// +-W[s >> (k-M)], W the Walsh-Hadamard transform of its 2^M probabilities
+// (w_h = sum_i (-1)^popc(i & h) p_i).  The amplitudes are read and squared
+// once per tile, however many terms there are.
+template <typename R, int M>
 __device__ __forceinline__ void tile_epi_accum(const cx<R> *cur, const ETerm *sterm, int nte, double *eacc,
                                                R *eaccw, int k, uint64_t base, int tid, int lane, int warp,
                                                int nw) {
-    const int dim = 1 << k;
+    constexpr int P = 1 << M;
+    const int lb = k - M;
+    R w[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        const cx<R> x = cur[tid + (i << lb)];
+        w[i] = x.x * x.x + x.y * x.y;
+    }
+#pragma unroll
+    for (int st = 1; st < P; st <<= 1) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            if (!(i & st)) {
+                const R a0 = w[i], a1 = w[i | st];
+                w[i] = a0 + a1;
+                w[i | st] = a0 - a1;
+            }
+        }
+    }
     for (int j = 0; j < nte; ++j) {
         const ETerm et = sterm[j];
-        const int bpar = __popcll(base & et.sout) & 1;
-        R e = R(0);
-        for (int l = tid; l < dim; l += blockDim.x) {
-            const cx<R> x = cur[l];
-            const R pr = x.x * x.x + x.y * x.y;
-            e += ((__popc((uint32_t)l & et.sloc) & 1) ^ bpar) ? -pr : pr;
+        const int h = (int)(et.sloc >> lb) & (P - 1);
+        // w[h] by halving on the bits of h (selects, no indexed registers)
+        R v[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) v[i] = w[i];
+#pragma unroll
+        for (int half = P >> 1; half >= 1; half >>= 1) {
+#pragma unroll
+            for (int i = 0; i < half; ++i) v[i] = (h & half) ? v[i + half] : v[i];
         }
+        const int neg = (__popcll(base & et.sout) + __popc((uint32_t)tid & et.sloc)) & 1;
+        R e = neg ? -v[0] : v[0];
         e = warp_sum_t(e);
         if (lane == 0) eaccw[warp * nte + j] += e;
     }
@@ -234,7 +263,7 @@ __device__ __forceinline__ void tile_fwd_body(const CUtensorMap &tmap, const Til
                 if (erow >= 0) eflush(erow);
                 erow = row;
             }
-            tile_epi_accum<R>(cur, sterm, nte, eacc, eaccw, a.g.k, base, tid, lane, warp, nw);
+            tile_epi_accum<R, M>(cur, sterm, nte, eacc, eaccw, a.g.k, base, tid, lane, warp, nw);
         }
     }
     grid_dep_launch();   // the next kernel of the stream may start its prologue
