@@ -608,7 +608,9 @@ DQ_API dq_status dq_sample(dq_ctx *ctx, int nqubits, const void *state, int batc
  * batch rows, contents destroyed) and cache the fastest for later calls with
  * the same circuit structure.  With graphs on (dq_ctx_set_graphs) the
  * specialised tile passes are timed as CUDA-graph replays, the way the
- * context then runs repeated calls; call dq_ctx_set_graphs first.
+ * context then runs repeated calls; call dq_ctx_set_graphs first.  They are
+ * timed from a cleared L2 (a temporary 256 MiB buffer is filled before each
+ * timed forward).
  * Synchronises `stream`. */
 DQ_API dq_status dq_plan_autotune(dq_ctx *ctx, const dq_circuit *circuit, int batch,
                            int dtype, void *state, void *stream);

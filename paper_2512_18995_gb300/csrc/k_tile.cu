@@ -1050,24 +1050,36 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
     // the three fastest shapes' passes as run-time specialised kernels: a
     // pass without dispatch may favour another shape (DQ_OPT_JIT = 2 uses
     // the fastest of all).  Their times can lie within a few percent of one
-    // another, so short forwards (under 10 ms) are timed in five rounds, the
+    // another, so short forwards (under 10 ms) are timed in seven rounds, the
     // shapes taken in turn, and each keeps its fastest round.
     if (tc.jit_mode != 0 && jit_available()) {
+        // Also up to three of the next five shapes whose schedules have no
+        // more passes than the fewest of the first three: the interpreter's
+        // per-op dispatch can rank a wider tile (fewer, longer passes), or
+        // another register split of it, below shapes that its specialised
+        // passes beat.
         std::vector<std::pair<TileSchedule *, Cand>> js;
-        for (size_t ci = 0; ci < cands.size() && ci < 3; ++ci) {
+        size_t fewest = SIZE_MAX;
+        int extra = 0;
+        for (size_t ci = 0; ci < cands.size() && ci < 8; ++ci) {
             const Cand &cd = cands[ci];
             TileSchedule *sc = get_schedule(tc, p, cd.k, cd.low, cd.M, (int)sizeof(cx<R>), false);
-            std::string err;
             if (!sc || sc->jit_failed) continue;
+            if (ci >= 3) {
+                if (extra >= 3 || sc->passes.size() > fewest) continue;
+                ++extra;
+            }
+            std::string err;
             if (!sc->jit && !jit_build(*sc, (int)sizeof(cx<R>), tc.device, &err)) {
                 sc->jit_failed = true;
                 tc.jit_err = err;
                 continue;
             }
+            if (ci < 3) fewest = std::min(fewest, sc->passes.size());
             js.push_back({sc, cd});
         }
         // with graphs on, each candidate's forward is captured once (after a
-        // stream run that loads its module) and replayed: three replays timed
+        // stream run that loads its module) and replayed
         std::vector<cudaGraphExec_t> gx(js.size(), nullptr);
         cudaStream_t cs = nullptr;
         if (graphs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1094,10 +1106,22 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
             if (g) cudaGraphDestroy(g);
             cudaGetLastError();
         }
-        auto timed_graph = [&](cudaGraphExec_t x, float &ms) {
-            cudaError_t err = cudaGraphLaunch(x, s);
+        // Each timed forward starts from a cleared L2 (a 256 MiB fill), as a
+        // call between other work finds it: back-to-back runs of one circuit
+        // keep its kernels' code and tables cached and favour schedules with
+        // more, smaller passes, which a cold start makes slower.
+        const size_t flush_bytes = size_t(256) << 20;
+        void *flush = nullptr;
+        if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            flush = nullptr;
+        }
+        auto timed_one = [&](size_t q, int round, float &ms) {
+            if (flush) cudaMemsetAsync(flush, (int)(q + round) & 0xff, flush_bytes, s);
             cudaEventRecord(e0, s);
-            for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) err = cudaGraphLaunch(x, s);
+            cudaError_t err = gx[q] ? cudaGraphLaunch(gx[q], s)
+                                    : run_forward<R>(tc, p, *js[q].first, coef, state, batch, nsm, s, launches,
+                                                     nullptr, nullptr, true);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             cudaEventElapsedTime(&ms, e0, e1);
@@ -1105,15 +1129,20 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
             return err == cudaSuccess;
         };
         std::vector<float> fastest(js.size(), 1e30f);
+        for (size_t q = 0; q < js.size(); ++q) {   // warm-up: modules loaded, graphs uploaded
+            float ms = 0.f;
+            timed_one(q, 0, ms);
+        }
         int rounds = 1;
         for (int round = 0; round < rounds; ++round) {
             for (size_t q = 0; q < js.size(); ++q) {
                 float ms = 0.f;
-                if (!(gx[q] ? timed_graph(gx[q], ms) : timed(*js[q].first, true, ms))) continue;
+                if (!timed_one(q, round + 1, ms)) continue;
                 fastest[q] = std::min(fastest[q], ms);
-                if (round == 0 && ms < 10.f) rounds = 5;
+                if (round == 0 && ms < 10.f) rounds = 7;
             }
         }
+        if (flush) cudaFree(flush);
         for (cudaGraphExec_t x : gx)
             if (x) cudaGraphExecDestroy(x);
         if (cs) cudaStreamDestroy(cs);
