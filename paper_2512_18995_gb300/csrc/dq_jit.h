@@ -37,7 +37,7 @@ bool jit_compile(const std::string &src, int cc, std::vector<char> *cubin, std::
 // automatic with the autotuner having measured them faster for the plan);
 // compiles them on first use.  A failed compile keeps the interpreter for
 // that schedule (the reason in tc.jit_err).  Reverse schedules follow the
-// circuit's forward verdict.
+// circuit's forward decision.
 bool jit_want(TileCache &tc, const std::unordered_map<uint64_t, TileTune> &tuned, const Plan &p, int amp,
               TileSchedule &sc);
 // Compile and load every pass of sc for `device` (sc.jit); false with *err on failure.
