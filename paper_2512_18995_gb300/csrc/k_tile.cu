@@ -1098,8 +1098,9 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
                 cudaGetLastError();
                 continue;
             }
+            int64_t captured = 0;   // captured launches run only when replayed
             const cudaError_t re =
-                run_forward<R>(tc, p, *js[q].first, coef, state, batch, nsm, cs, launches, nullptr, nullptr, true);
+                run_forward<R>(tc, p, *js[q].first, coef, state, batch, nsm, cs, &captured, nullptr, nullptr, true);
             const cudaError_t ce = cudaStreamEndCapture(cs, &g);
             if (re != cudaSuccess || ce != cudaSuccess || !g || cudaGraphInstantiate(&gx[q], g, 0) != cudaSuccess)
                 gx[q] = nullptr;
@@ -1122,6 +1123,7 @@ cudaError_t tile_autotune(TileCache &tc, std::unordered_map<uint64_t, TileTune> 
             cudaError_t err = gx[q] ? cudaGraphLaunch(gx[q], s)
                                     : run_forward<R>(tc, p, *js[q].first, coef, state, batch, nsm, s, launches,
                                                      nullptr, nullptr, true);
+            if (gx[q] && err == cudaSuccess && launches) *launches += (int64_t)js[q].first->passes.size();
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             cudaEventElapsedTime(&ms, e0, e1);
