@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
     OTerm *st = reinterpret_cast<OTerm *>(smem + 2 * tbytes + 64);
     double *acc = reinterpret_cast<double *>(st + a.nt);            // [nt]
     R *accw = reinterpret_cast<R *>(acc + a.nt);                     // [nw][nt]
+    R *wzs = reinterpret_cast<R *>(((uintptr_t)(accw + nw * a.nt) + 15) & ~uintptr_t(15));   // [kObsJ][threads]
     const int64_t per = (a.g.ntiles + gridDim.x - 1) / gridDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * per;
     const int64_t t1 = min(a.g.ntiles, t0 + per);
@@ -295,19 +296,42 @@ __global__ void __launch_bounds__(obs_max_threads<R>()) k_tile_obs(const __grid_
             lv[i] = a.lam_mode == 2 ? bufL[l] : mk<R>(R(0), R(0));
         }
         const double *w = a.rw ? a.rw + row * a.nobs : nullptr;
+        // Z strings: amplitude i of this thread sits at l = tid + i 2^lb
+        // (lb = k - 3), so the sign of its probability under a term with mask
+        // s is (-1)^(parity(tid & s) + parity(i & (s >> lb))) times that of the
+        // tile base: a term's expectation is +-wz[s >> lb], wz the
+        // Walsh-Hadamard transform of the thread's probabilities, kept in its
+        // shared-memory column.
+        const int lb = a.g.k - 3;
+        {
+            R *col = wzs + tid;
+            const int ld = (int)blockDim.x;
+#pragma unroll
+            for (int i = 0; i < kObsJ; ++i) col[i * ld] = x[i].x * x[i].x + x[i].y * x[i].y;
+#pragma unroll 1
+            for (int st = 1; st < kObsJ; st <<= 1) {
+                for (int i = 0; i < kObsJ; ++i) {
+                    if (!(i & st)) {
+                        const R a0 = col[i * ld], a1 = col[(i | st) * ld];
+                        col[i * ld] = a0 + a1;
+                        col[(i | st) * ld] = a0 - a1;
+                    }
+                }
+            }
+        }
         for (int j = 0; j < a.nt; ++j) {
             const OTerm o = st[j];
             const int bpar = __popcll(base & o.sout) & 1;
             const R wc = (R)((w ? w[o.obs] : 1.0) * o.coeff);
             R e = R(0);
             if (o.floc == 0) {
-                // Z string: sign (-1)^(parity of l & sloc, and of the tile base)
+                const bool tneg = (__popc((uint32_t)tid & o.sloc) ^ bpar) & 1;
+                const R v = wzs[((o.sloc >> lb) & (kObsJ - 1)) * blockDim.x + tid];
+                e = tneg ? -v : v;
+                // lambda[l] += wc (-1)^(parity(l & s) + bpar) psi[l]
 #pragma unroll
                 for (int i = 0; i < kObsJ; ++i) {
-                    const int l = tid + i * (int)blockDim.x;
-                    const bool neg = (__popc((uint32_t)l & o.sloc) & 1) ^ bpar;
-                    const R pr = x[i].x * x[i].x + x[i].y * x[i].y;
-                    e += neg ? -pr : pr;
+                    const bool neg = tneg ^ (__popc((uint32_t)i & (o.sloc >> lb)) & 1);
                     const R f = neg ? -wc : wc;
                     lv[i].x += f * x[i].x;
                     lv[i].y += f * x[i].y;
@@ -492,7 +516,7 @@ cudaError_t tile_observe(TileCache &tc, int n, const std::vector<DevTerm> &bits,
             a.tbit[i >> 3] |= (uint64_t)ps.T[i] << (8 * (i & 7));
         }
         const size_t smem = 2 * (sizeof(cx<R>) << k) + 64 + ps.nt * sizeof(OTerm) + ps.nt * sizeof(double) +
-                            (size_t)nw * ps.nt * sizeof(R) + 64;
+                            (size_t)nw * ps.nt * sizeof(R) + 16 + (size_t)kObsJ * threads * sizeof(R) + 64;
         const void *ofn = (const void *)k_tile_obs<R>;
         if (tc.smem_set[ofn] < smem) {
             cudaError_t e = cudaFuncSetAttribute(ofn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
